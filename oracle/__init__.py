@@ -1,0 +1,354 @@
+"""Plain FP64 CPU oracle of the penalized pseudo-spectral Navier-Stokes step.
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, by ``__graft_entry__.smoke()``
+and by the CPU-baseline leg of ``bench.py``.  The product path (the CUDA
+library and its binding) never imports, links or runs anything here.
+
+The arithmetic lives in plain C (``fft.c``, ``insect.c``, ``solver.c``); this
+module compiles it with gcc and marshals numpy arrays through ctypes.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_SOURCES = ["fft.c", "insect.c", "solver.c"]
+
+MAX_FOURIER = 8
+ROW_COLS = 22
+NSUMS = 39
+SUM_EKIN, SUM_UMAX, SUM_NONFINITE = 36, 37, 38
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so with gcc (no fast-math, no FMA contraction)."""
+    srcs = [os.path.join(_HERE, s) for s in _SOURCES] + [os.path.join(_HERE, "oracle.h")]
+    if not force and os.path.exists(_LIB_PATH):
+        newest = max(os.path.getmtime(s) for s in srcs)
+        if os.path.getmtime(_LIB_PATH) >= newest:
+            return _LIB_PATH
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+           "-o", _LIB_PATH + ".tmp"] + [os.path.join(_HERE, s) for s in _SOURCES] + ["-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(_LIB_PATH + ".tmp", _LIB_PATH)
+    return _LIB_PATH
+
+
+class Params(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("dealias_strict", C.c_int),
+                ("Lx", C.c_double), ("Ly", C.c_double), ("Lz", C.c_double),
+                ("nu", C.c_double), ("eta", C.c_double), ("cfl", C.c_double),
+                ("dt_fixed", C.c_double), ("dt_max", C.c_double),
+                ("mean_mode", C.c_int), ("pad_", C.c_int),
+                ("u_inf", C.c_double * 3)]
+
+
+_F = C.c_double * MAX_FOURIER
+
+
+class Insect(C.Structure):
+    _fields_ = [("body_type", C.c_int), ("nwings", C.c_int), ("profile", C.c_int),
+                ("nfourier", C.c_int), ("c_smth", C.c_double),
+                ("x_cntr", C.c_double * 3), ("u_cntr", C.c_double * 3),
+                ("psi", C.c_double), ("beta", C.c_double), ("gamma", C.c_double),
+                ("psi_dot", C.c_double), ("beta_dot", C.c_double), ("gamma_dot", C.c_double),
+                ("body_a", C.c_double), ("body_b", C.c_double),
+                ("pivot_l", C.c_double * 3), ("pivot_r", C.c_double * 3),
+                ("eta_stroke", C.c_double),
+                ("wing_c_le", C.c_double), ("wing_c_te", C.c_double),
+                ("wing_R", C.c_double), ("wing_h", C.c_double), ("freq", C.c_double),
+                ("phi_a0", C.c_double), ("phi_a", _F), ("phi_b", _F),
+                ("alpha_a0", C.c_double), ("alpha_a", _F), ("alpha_b", _F),
+                ("theta_a0", C.c_double), ("theta_a", _F), ("theta_b", _F)]
+
+
+class Scalars(C.Structure):
+    _fields_ = [("t", C.c_double), ("dt_prev", C.c_double), ("n", C.c_int64),
+                ("Is_prev", (C.c_double * 3) * 3), ("Js_prev", (C.c_double * 3) * 3)]
+
+
+class Frames(C.Structure):
+    _fields_ = [("M_body", C.c_double * 9), ("Omega_b_g", C.c_double * 3),
+                ("M_stroke", (C.c_double * 9) * 2), ("M_wing", (C.c_double * 9) * 2),
+                ("Omega_w_b", (C.c_double * 3) * 2), ("Omega_w_w", (C.c_double * 3) * 2),
+                ("pivot_g", (C.c_double * 3) * 2),
+                ("phi", C.c_double), ("alpha", C.c_double), ("theta", C.c_double),
+                ("phi_dot", C.c_double), ("alpha_dot", C.c_double), ("theta_dot", C.c_double)]
+
+
+_lib = None
+_dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+_cp = np.ctypeslib.ndpointer(dtype=np.complex128, flags="C_CONTIGUOUS")
+_ip = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        L = _lib
+        L.orc_fft1.argtypes = [C.c_int, _cp, C.c_int]
+        L.orc_fft3_r2c.argtypes = [C.c_int, C.c_int, C.c_int, _dp, _cp]
+        L.orc_fft3_c2r.argtypes = [C.c_int, C.c_int, C.c_int, _cp, _dp]
+        L.orc_dft3_r2c.argtypes = [C.c_int, C.c_int, C.c_int, _dp, _cp]
+        L.orc_rot_x.argtypes = [C.c_double, _dp]
+        L.orc_rot_y.argtypes = [C.c_double, _dp]
+        L.orc_rot_z.argtypes = [C.c_double, _dp]
+        L.orc_frames_at.argtypes = [C.POINTER(Insect), C.c_double, C.POINTER(Frames)]
+        L.orc_mask_profile.argtypes = [C.c_int, C.c_double, C.c_double]
+        L.orc_mask_profile.restype = C.c_double
+        L.orc_solid_at.argtypes = [C.POINTER(Insect), C.POINTER(Frames), C.c_double, _dp,
+                                   C.POINTER(C.c_double), C.POINTER(C.c_int), _dp]
+        L.orc_mask_grid.argtypes = [C.POINTER(Params), C.POINTER(Insect), C.c_double,
+                                    _dp, _ip, _dp]
+        L.orc_dealias.argtypes = [C.POINTER(Params), _cp, C.c_int]
+        L.orc_project.argtypes = [C.POINTER(Params), _cp]
+        L.orc_curl.argtypes = [C.POINTER(Params), _cp, _cp]
+        L.orc_forward.argtypes = [C.POINTER(Params), _dp, _cp, C.c_int]
+        L.orc_inverse.argtypes = [C.POINTER(Params), _cp, _dp, C.c_int]
+        L.orc_set_state.argtypes = [C.POINTER(Params), _dp, _cp, _cp, C.POINTER(Scalars)]
+        L.orc_get_state.argtypes = [C.POINTER(Params), _cp, _dp]
+        L.orc_rhs.argtypes = [C.POINTER(Params), C.POINTER(Insect), C.c_double, _cp, _cp, _dp]
+        L.orc_rhs.restype = C.c_int
+        L.orc_ab2_update.argtypes = [C.POINTER(Params), _cp, _cp, _cp, C.c_double,
+                                     C.c_double, C.c_int64]
+        L.orc_step.argtypes = [C.POINTER(Params), C.POINTER(Insect), _cp, _cp,
+                               C.POINTER(Scalars), _dp]
+        L.orc_step.restype = C.c_int
+    return _lib
+
+
+# ---------------------------------------------------------------- marshalling
+
+def make_params(cfg: dict) -> Params:
+    p = Params()
+    p.nx, p.ny, p.nz = cfg["n"]
+    p.Lx, p.Ly, p.Lz = cfg["L"]
+    p.nu = cfg["nu"]
+    p.eta = cfg["eta"]
+    p.cfl = cfg.get("cfl", 0.1)
+    p.dt_fixed = cfg.get("dt_fixed", 0.0)
+    p.dt_max = cfg.get("dt_max", 0.0)
+    p.dealias_strict = int(cfg.get("dealias_strict", 0))
+    p.mean_mode = 1 if cfg.get("mean_mode", "fixed") == "free" else 0
+    p.u_inf[:] = cfg.get("u_inf", (0.0, 0.0, 0.0))
+    return p
+
+
+def make_insect(d: dict | None) -> Insect | None:
+    if d is None:
+        return None
+    s = Insect()
+    s.body_type = {"none": 0, "sphere": 1, "ellipsoid": 2}[d.get("body", "none")]
+    s.nwings = d.get("nwings", 0)
+    s.profile = {"cos": 0, "tanh": 1}[d.get("profile", "cos")]
+    s.c_smth = d.get("c_smth", 1.0)
+    s.x_cntr[:] = d.get("x_cntr", (0, 0, 0))
+    s.u_cntr[:] = d.get("u_cntr", (0, 0, 0))
+    s.psi, s.beta, s.gamma = d.get("body_angles", (0, 0, 0))
+    s.psi_dot, s.beta_dot, s.gamma_dot = d.get("body_rates", (0, 0, 0))
+    s.body_a, s.body_b = d.get("body_axes", (0.0, 0.0))
+    s.pivot_l[:] = d.get("pivot_l", (0, 0, 0))
+    s.pivot_r[:] = d.get("pivot_r", (0, 0, 0))
+    s.eta_stroke = d.get("eta_stroke", 0.0)
+    s.wing_c_le, s.wing_c_te, s.wing_R, s.wing_h = d.get("wing", (0, 0, 0, 0))
+    s.freq = d.get("freq", 1.0)
+    kin = d.get("kinematics", {})
+    nf = 0
+    for name in ("phi", "alpha", "theta"):
+        a0, a, b = kin.get(name, (0.0, [], []))
+        setattr(s, name + "_a0", a0)
+        arr_a, arr_b = getattr(s, name + "_a"), getattr(s, name + "_b")
+        for i, v in enumerate(a):
+            arr_a[i] = v
+        for i, v in enumerate(b):
+            arr_b[i] = v
+        nf = max(nf, len(a), len(b))
+    s.nfourier = nf
+    return s
+
+
+def _ins_ptr(ins):
+    return C.byref(ins) if ins is not None else None
+
+
+def half_shape(n):
+    nx, ny, nz = n
+    return (nz, ny, nx // 2 + 1)
+
+
+def fft3_r2c(u: np.ndarray) -> np.ndarray:
+    nz, ny, nx = u.shape
+    out = np.zeros((nz, ny, nx // 2 + 1), np.complex128)
+    lib().orc_fft3_r2c(nx, ny, nz, np.ascontiguousarray(u, np.float64), out)
+    return out
+
+
+def fft3_c2r(uh: np.ndarray, nx: int) -> np.ndarray:
+    nz, ny, _ = uh.shape
+    out = np.zeros((nz, ny, nx), np.float64)
+    lib().orc_fft3_c2r(nx, ny, nz, np.ascontiguousarray(uh, np.complex128), out)
+    return out
+
+
+def dft3_r2c(u: np.ndarray) -> np.ndarray:
+    nz, ny, nx = u.shape
+    out = np.zeros((nz, ny, nx // 2 + 1), np.complex128)
+    lib().orc_dft3_r2c(nx, ny, nz, np.ascontiguousarray(u, np.float64), out)
+    return out
+
+
+def fft1(x: np.ndarray, sign: int) -> np.ndarray:
+    a = np.ascontiguousarray(x, np.complex128).copy()
+    lib().orc_fft1(a.size, a, sign)
+    return a
+
+
+def rot(axis: str, xi: float) -> np.ndarray:
+    R = np.zeros(9)
+    getattr(lib(), "orc_rot_" + axis)(xi, R)
+    return R.reshape(3, 3)
+
+
+def frames(insect: dict, t: float) -> dict:
+    ins = make_insect(insect)
+    fr = Frames()
+    lib().orc_frames_at(C.byref(ins), t, C.byref(fr))
+    m = lambda a: np.array(a[:]).reshape(3, 3)
+    return {
+        "M_body": m(fr.M_body), "Omega_b_g": np.array(fr.Omega_b_g[:]),
+        "M_stroke": [m(fr.M_stroke[i]) for i in range(2)],
+        "M_wing": [m(fr.M_wing[i]) for i in range(2)],
+        "Omega_w_b": [np.array(fr.Omega_w_b[i][:]) for i in range(2)],
+        "Omega_w_w": [np.array(fr.Omega_w_w[i][:]) for i in range(2)],
+        "pivot_g": [np.array(fr.pivot_g[i][:]) for i in range(2)],
+        "angles": (fr.phi, fr.alpha, fr.theta),
+        "rates": (fr.phi_dot, fr.alpha_dot, fr.theta_dot),
+    }
+
+
+def mask_profile(profile: str, delta: float, h: float) -> float:
+    return lib().orc_mask_profile({"cos": 0, "tanh": 1}[profile], delta, h)
+
+
+def solid_at(insect: dict, t: float, h: float, x) -> tuple:
+    ins = make_insect(insect)
+    fr = Frames()
+    lib().orc_frames_at(C.byref(ins), t, C.byref(fr))
+    chi, col = C.c_double(), C.c_int()
+    us = np.zeros(3)
+    lib().orc_solid_at(C.byref(ins), C.byref(fr), h, np.asarray(x, np.float64), C.byref(chi),
+                       C.byref(col), us)
+    return chi.value, col.value, us
+
+
+def mask_grid(cfg: dict, insect: dict, t: float):
+    p, ins = make_params(cfg), make_insect(insect)
+    nx, ny, nz = cfg["n"]
+    chi = np.zeros((nz, ny, nx))
+    col = np.zeros((nz, ny, nx), np.int32)
+    us = np.zeros((3, nz, ny, nx))
+    lib().orc_mask_grid(C.byref(p), C.byref(ins), t, chi, col, us)
+    return chi, col, us
+
+
+class Spectral:
+    """Operators on half-spectrum fields uh[c][z][y][x] of a configuration."""
+
+    def __init__(self, cfg: dict):
+        self.cfg = cfg
+        self.p = make_params(cfg)
+        self.n = tuple(cfg["n"])
+
+    def shape(self, ncomp=3):
+        return (ncomp,) + half_shape(self.n)
+
+    def forward(self, u):
+        ncomp = u.shape[0]
+        out = np.zeros(self.shape(ncomp), np.complex128)
+        lib().orc_forward(C.byref(self.p), np.ascontiguousarray(u, np.float64), out, ncomp)
+        return out
+
+    def inverse(self, uh):
+        ncomp = uh.shape[0]
+        nx, ny, nz = self.n
+        out = np.zeros((ncomp, nz, ny, nx))
+        lib().orc_inverse(C.byref(self.p), np.ascontiguousarray(uh), out, ncomp)
+        return out
+
+    def dealias(self, fh):
+        f = np.ascontiguousarray(fh).copy()
+        lib().orc_dealias(C.byref(self.p), f, f.shape[0])
+        return f
+
+    def project(self, fh):
+        f = np.ascontiguousarray(fh).copy()
+        lib().orc_project(C.byref(self.p), f)
+        return f
+
+    def curl(self, uh):
+        out = np.zeros_like(uh)
+        lib().orc_curl(C.byref(self.p), np.ascontiguousarray(uh), out)
+        return out
+
+    def rhs(self, uh, t=0.0, insect=None):
+        nh = np.zeros_like(uh)
+        sums = np.zeros(NSUMS)
+        ins = make_insect(insect)
+        lib().orc_rhs(C.byref(self.p), _ins_ptr(ins), t, np.ascontiguousarray(uh), nh, sums)
+        return nh, sums
+
+    def ab2_update(self, uh, nh, nh_prev, dt, dt_prev, n):
+        u = np.ascontiguousarray(uh).copy()
+        lib().orc_ab2_update(C.byref(self.p), u, np.ascontiguousarray(nh),
+                             np.ascontiguousarray(nh_prev), dt, dt_prev, n)
+        return u
+
+
+class Simulation:
+    """The oracle's time stepper: state u_hat, N_hat^{n-1}, t, dt_{n-1}, n."""
+
+    def __init__(self, cfg: dict, insect: dict | None = None):
+        self.cfg = cfg
+        self.p = make_params(cfg)
+        self.ins = make_insect(insect)
+        self.sp = Spectral(cfg)
+        self.uh = np.zeros(self.sp.shape(), np.complex128)
+        self.nh_prev = np.zeros_like(self.uh)
+        self.s = Scalars()
+        self.rows = []
+
+    def set_state(self, u: np.ndarray):
+        lib().orc_set_state(C.byref(self.p), np.ascontiguousarray(u, np.float64), self.uh,
+                            self.nh_prev, C.byref(self.s))
+        self.rows = []
+
+    def get_state(self) -> np.ndarray:
+        nx, ny, nz = self.cfg["n"]
+        out = np.zeros((3, nz, ny, nx))
+        lib().orc_get_state(C.byref(self.p), self.uh, out)
+        return out
+
+    def step(self, n: int = 1):
+        for _ in range(n):
+            row = np.zeros(ROW_COLS)
+            rc = lib().orc_step(C.byref(self.p), _ins_ptr(self.ins), self.uh, self.nh_prev,
+                                C.byref(self.s), row)
+            if rc != 0:
+                raise FloatingPointError("oracle: non-finite value in the step")
+            self.rows.append(row)
+        return np.array(self.rows[-n:])
+
+    @property
+    def t(self):
+        return self.s.t
+
+    @property
+    def nstep(self):
+        return self.s.n

@@ -1,0 +1,324 @@
+/*
+ * Oracle fluid module: Fourier pseudo-spectral discretization (Sec. 2.4) of
+ * the penalized Navier-Stokes equations in rotational form
+ * (Eq. PNST_org_momentum, without the sponge term), advanced by Algorithm 1
+ * with Adams-Bashforth 2 and an integrating factor for the viscous term.
+ *
+ * TEST INFRASTRUCTURE ONLY (see oracle.h).
+ *
+ * Readings where the paper is silent:
+ *  - 2/3 rule: cubic truncation per axis, keep |m_i| <= floor(n_i/3)
+ *    (the Fig. BB-Spectra caption gives k_max = 256 (2 pi/4) for n = 768);
+ *    `dealias_strict` keeps |m_i| < n_i/3 instead;
+ *  - AB2 with integrating factor (Sec. 2.4 names it without the formula):
+ *    AB2 on v = exp(nu |k|^2 t) u_hat with variable steps, mapped back; the
+ *    first step is the integrating-factor Euler step;
+ *  - time step: min(CFL min(dx,dy,dz) / max|u|, C_eta, dt_max), or fixed;
+ *  - mean mode: held at u_inf (N_hat(0) = 0) or left free to evolve;
+ *  - force (Eq. force_with_unst_corrections) and moment (Eq. moment_of_love)
+ *    per colour; the unsteady correction is the backward difference of
+ *    sum chi u_s dV over the previous step, zero on the first step; moments
+ *    are taken about the body centre (body) or the wing pivot (wings).
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+static const double PI = 3.14159265358979323846;
+
+static long n_half(const orc_params *p) { return (long)p->nz * p->ny * (p->nx / 2 + 1); }
+static long n_phys(const orc_params *p) { return (long)p->nz * p->ny * p->nx; }
+
+/* signed mode number along y or z: 0..n/2-1, then -n/2..-1 */
+static int signed_mode(int j, int n) { return j < n / 2 ? j : j - n; }
+
+static int cutoff(int n, int strict)
+{
+    if (strict && n % 3 == 0) return n / 3 - 1;
+    return n / 3;
+}
+
+static void wavevector(const orc_params *p, int ix, int iy, int iz, double k[3])
+{
+    k[0] = 2.0 * PI * ix / p->Lx;
+    k[1] = 2.0 * PI * signed_mode(iy, p->ny) / p->Ly;
+    k[2] = 2.0 * PI * signed_mode(iz, p->nz) / p->Lz;
+}
+
+/* 2/3 rule (Sec. 2.4): zero every mode outside the retained cube. */
+void orc_dealias(const orc_params *p, double complex *fh, int ncomp)
+{
+    int hx = p->nx / 2 + 1;
+    int Kx = cutoff(p->nx, p->dealias_strict);
+    int Ky = cutoff(p->ny, p->dealias_strict);
+    int Kz = cutoff(p->nz, p->dealias_strict);
+    long nh = n_half(p);
+    for (int c = 0; c < ncomp; ++c)
+        for (int iz = 0; iz < p->nz; ++iz)
+            for (int iy = 0; iy < p->ny; ++iy)
+                for (int ix = 0; ix < hx; ++ix) {
+                    int my = abs(signed_mode(iy, p->ny));
+                    int mz = abs(signed_mode(iz, p->nz));
+                    if (ix > Kx || my > Ky || mz > Kz)
+                        fh[c * nh + ((long)iz * p->ny + iy) * hx + ix] = 0;
+                }
+}
+
+/* Leray projection, Algorithm 1 step (d): F <- F - k (k.F)/|k|^2, k != 0.
+ * This is the Fourier-space solution of Eq. PNST_UP_pressure_poisson_eqn. */
+void orc_project(const orc_params *p, double complex *fh)
+{
+    int hx = p->nx / 2 + 1;
+    long nh = n_half(p);
+    for (int iz = 0; iz < p->nz; ++iz)
+        for (int iy = 0; iy < p->ny; ++iy)
+            for (int ix = 0; ix < hx; ++ix) {
+                double k[3];
+                wavevector(p, ix, iy, iz, k);
+                double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+                if (k2 == 0.0) continue;
+                long i = ((long)iz * p->ny + iy) * hx + ix;
+                double complex kf = k[0] * fh[i] + k[1] * fh[nh + i] + k[2] * fh[2 * nh + i];
+                for (int c = 0; c < 3; ++c) fh[c * nh + i] -= k[c] * kf / k2;
+            }
+}
+
+/* Vorticity omega_hat = i k x u_hat (Sec. 2.4: grad -> i k). */
+void orc_curl(const orc_params *p, const double complex *uh, double complex *wh)
+{
+    int hx = p->nx / 2 + 1;
+    long nh = n_half(p);
+    for (int iz = 0; iz < p->nz; ++iz)
+        for (int iy = 0; iy < p->ny; ++iy)
+            for (int ix = 0; ix < hx; ++ix) {
+                double k[3];
+                wavevector(p, ix, iy, iz, k);
+                long i = ((long)iz * p->ny + iy) * hx + ix;
+                double complex ux = uh[i], uy = uh[nh + i], uz = uh[2 * nh + i];
+                wh[i] = I * (k[1] * uz - k[2] * uy);
+                wh[nh + i] = I * (k[2] * ux - k[0] * uz);
+                wh[2 * nh + i] = I * (k[0] * uy - k[1] * ux);
+            }
+}
+
+void orc_forward(const orc_params *p, const double *u, double complex *uh, int ncomp)
+{
+    long N = n_phys(p), nh = n_half(p);
+    for (int c = 0; c < ncomp; ++c) {
+        orc_fft3_r2c(p->nx, p->ny, p->nz, u + c * N, uh + c * nh);
+        for (long i = 0; i < nh; ++i) uh[c * nh + i] /= (double)N;
+    }
+}
+
+void orc_inverse(const orc_params *p, const double complex *uh, double *u, int ncomp)
+{
+    long N = n_phys(p), nh = n_half(p);
+    for (int c = 0; c < ncomp; ++c)
+        orc_fft3_c2r(p->nx, p->ny, p->nz, uh + c * nh, u + c * N);
+}
+
+int orc_set_state(const orc_params *p, const double *u, double complex *uh,
+                  double complex *nh_prev, orc_scalars *s)
+{
+    long nh = n_half(p);
+    orc_forward(p, u, uh, 3);
+    orc_dealias(p, uh, 3);
+    orc_project(p, uh);
+    if (p->mean_mode == 0)
+        for (int c = 0; c < 3; ++c) uh[c * nh] = p->u_inf[c];
+    memset(nh_prev, 0, sizeof(double complex) * (size_t)(3 * nh));
+    memset(s, 0, sizeof *s);
+    return 0;
+}
+
+void orc_get_state(const orc_params *p, const double complex *uh, double *u)
+{
+    orc_inverse(p, uh, u, 3);
+}
+
+static double grid_h(const orc_params *p, const orc_insect *ins)
+{
+    double dx = p->Lx / p->nx, dy = p->Ly / p->ny, dz = p->Lz / p->nz;
+    double d = dx > dy ? dx : dy;
+    if (dz > d) d = dz;
+    return ins->c_smth * d;
+}
+
+/*
+ * Right-hand side of Algorithm 1 steps (a), (c), (d) at time t:
+ * nh = P D FFT(u x omega - chi/C_eta (u - u_s)) / N, plus the FP64 sums.
+ * Returns 1 if a non-finite value was met, else 0.
+ */
+int orc_rhs(const orc_params *p, const orc_insect *ins, double t,
+            const double complex *uh, double complex *nh, double *sums)
+{
+    long N = n_phys(p), nhs = n_half(p);
+    double complex *wh = malloc(sizeof(double complex) * (size_t)(3 * nhs));
+    double *u = malloc(sizeof(double) * (size_t)(3 * N));
+    double *w = malloc(sizeof(double) * (size_t)(3 * N));
+    double *nl = malloc(sizeof(double) * (size_t)(3 * N));
+
+    orc_curl(p, uh, wh);
+    orc_inverse(p, uh, u, 3);
+    orc_inverse(p, wh, w, 3);
+
+    orc_frames fr;
+    if (ins) orc_frames_at(ins, t, &fr);
+    double h = ins ? grid_h(p, ins) : 0.0;
+    double dx = p->Lx / p->nx, dy = p->Ly / p->ny, dz = p->Lz / p->nz;
+    double dV = dx * dy * dz;
+    memset(sums, 0, sizeof(double) * ORC_NSUMS);
+    int bad = 0;
+
+    for (long iz = 0; iz < p->nz; ++iz)
+        for (long iy = 0; iy < p->ny; ++iy)
+            for (long ix = 0; ix < p->nx; ++ix) {
+                long i = (iz * p->ny + iy) * p->nx + ix;
+                double X[3] = {ix * dx, iy * dy, iz * dz};
+                double uu[3] = {u[i], u[N + i], u[2 * N + i]};
+                double ww[3] = {w[i], w[N + i], w[2 * N + i]};
+                double chi = 0.0, us[3] = {0, 0, 0};
+                int col = 0;
+                if (ins) orc_solid_at(ins, &fr, h, X, &chi, &col, us);
+                /* u x omega - chi/C_eta (u - u_s) */
+                double lamb[3] = {uu[1] * ww[2] - uu[2] * ww[1],
+                                  uu[2] * ww[0] - uu[0] * ww[2],
+                                  uu[0] * ww[1] - uu[1] * ww[0]};
+                for (int c = 0; c < 3; ++c) {
+                    double v = lamb[c] - chi / p->eta * (uu[c] - us[c]);
+                    nl[c * N + i] = v;
+                    if (!isfinite(v) || !isfinite(uu[c])) bad = 1;
+                }
+                double u2 = uu[0] * uu[0] + uu[1] * uu[1] + uu[2] * uu[2];
+                sums[ORC_SUM_EKIN] += 0.5 * u2 * dV;
+                if (sqrt(u2) > sums[ORC_SUM_UMAX]) sums[ORC_SUM_UMAX] = sqrt(u2);
+                if (col > 0) {
+                    int c0 = col - 1;
+                    const double *xr = col == 1 ? ins->x_cntr : fr.pivot_g[col - 2];
+                    double r[3] = {X[0] - xr[0], X[1] - xr[1], X[2] - xr[2]};
+                    double pen[3], cus[3], m1[3], m2[3];
+                    for (int c = 0; c < 3; ++c) {
+                        pen[c] = chi * (uu[c] - us[c]);
+                        cus[c] = chi * us[c];
+                    }
+                    m1[0] = r[1] * pen[2] - r[2] * pen[1];
+                    m1[1] = r[2] * pen[0] - r[0] * pen[2];
+                    m1[2] = r[0] * pen[1] - r[1] * pen[0];
+                    m2[0] = r[1] * cus[2] - r[2] * cus[1];
+                    m2[1] = r[2] * cus[0] - r[0] * cus[2];
+                    m2[2] = r[0] * cus[1] - r[1] * cus[0];
+                    for (int c = 0; c < 3; ++c) {
+                        sums[ORC_SUM_FP(c0) + c] += pen[c] * dV / p->eta;
+                        sums[ORC_SUM_MP(c0) + c] += m1[c] * dV / p->eta;
+                        sums[ORC_SUM_IS(c0) + c] += cus[c] * dV;
+                        sums[ORC_SUM_JS(c0) + c] += m2[c] * dV;
+                    }
+                }
+            }
+    sums[ORC_SUM_NONFINITE] = bad;
+
+    orc_forward(p, nl, nh, 3);
+    orc_dealias(p, nh, 3);
+    orc_project(p, nh);
+    if (p->mean_mode == 0)
+        for (int c = 0; c < 3; ++c) nh[c * nhs] = 0;
+
+    free(nl);
+    free(w);
+    free(u);
+    free(wh);
+    return bad;
+}
+
+/*
+ * Integrating-factor AB2 (Algorithm 1 step (e)).  With v = e^{nu k^2 t} u_hat,
+ * dv/dt = e^{nu k^2 t} N_hat; variable-step AB2 on v with r = dt/dt_prev,
+ * multiplied back by e^{-nu k^2 t^{n+1}}:
+ *   u^{n+1} = E1 u^n + dt [ (1 + r/2) E1 N^n - (r/2) E2 N^{n-1} ],
+ *   E1 = e^{-nu k^2 dt},  E2 = e^{-nu k^2 (dt + dt_prev)};
+ * on the first step (n = 0): u^1 = E1 (u^0 + dt N^0).
+ */
+void orc_ab2_update(const orc_params *p, double complex *uh,
+                    const double complex *nh, const double complex *nh_prev,
+                    double dt, double dt_prev, int64_t n)
+{
+    int hx = p->nx / 2 + 1;
+    long nhs = n_half(p);
+    for (int iz = 0; iz < p->nz; ++iz)
+        for (int iy = 0; iy < p->ny; ++iy)
+            for (int ix = 0; ix < hx; ++ix) {
+                double k[3];
+                wavevector(p, ix, iy, iz, k);
+                double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+                double E1 = exp(-p->nu * k2 * dt);
+                long i = ((long)iz * p->ny + iy) * hx + ix;
+                for (int c = 0; c < 3; ++c) {
+                    long j = c * nhs + i;
+                    if (n == 0) {
+                        uh[j] = E1 * (uh[j] + dt * nh[j]);
+                    } else {
+                        double r = dt / dt_prev;
+                        double E2 = exp(-p->nu * k2 * (dt + dt_prev));
+                        uh[j] = E1 * uh[j] +
+                                dt * ((1.0 + 0.5 * r) * E1 * nh[j] - 0.5 * r * E2 * nh_prev[j]);
+                    }
+                }
+            }
+}
+
+/* One step of Algorithm 1 (without sponge, free flight and output). */
+int orc_step(const orc_params *p, const orc_insect *ins, double complex *uh,
+             double complex *nh_prev, orc_scalars *s, double *row)
+{
+    long nhs = n_half(p);
+    double complex *nh = malloc(sizeof(double complex) * (size_t)(3 * nhs));
+    double sums[ORC_NSUMS];
+    int bad = orc_rhs(p, ins, s->t, uh, nh, sums);
+    if (bad) {
+        free(nh);
+        return 1;
+    }
+
+    /* Algorithm 1 step (b): the time step */
+    double dt;
+    if (p->dt_fixed > 0) {
+        dt = p->dt_fixed;
+    } else {
+        double dx = p->Lx / p->nx, dy = p->Ly / p->ny, dz = p->Lz / p->nz;
+        double dmin = dx < dy ? dx : dy;
+        if (dz < dmin) dmin = dz;
+        dt = p->eta;
+        double umax = sums[ORC_SUM_UMAX];
+        if (umax > 0 && p->cfl * dmin / umax < dt) dt = p->cfl * dmin / umax;
+        if (p->dt_max > 0 && p->dt_max < dt) dt = p->dt_max;
+    }
+
+    orc_ab2_update(p, uh, nh, nh_prev, dt, s->dt_prev, s->n);
+
+    row[0] = s->t;
+    row[1] = dt;
+    for (int c = 0; c < ORC_NCOLOURS; ++c)
+        for (int i = 0; i < 3; ++i) {
+            double F = sums[ORC_SUM_FP(c) + i], M = sums[ORC_SUM_MP(c) + i];
+            double Is = sums[ORC_SUM_IS(c) + i], Js = sums[ORC_SUM_JS(c) + i];
+            if (s->n > 0) {
+                F += (Is - s->Is_prev[c][i]) / s->dt_prev;
+                M += (Js - s->Js_prev[c][i]) / s->dt_prev;
+            }
+            row[2 + c * 6 + i] = F;
+            row[2 + c * 6 + 3 + i] = M;
+            s->Is_prev[c][i] = Is;
+            s->Js_prev[c][i] = Js;
+        }
+    row[20] = sums[ORC_SUM_EKIN];
+    row[21] = sums[ORC_SUM_UMAX];
+
+    memcpy(nh_prev, nh, sizeof(double complex) * (size_t)(3 * nhs));
+    s->t += dt;
+    s->dt_prev = dt;
+    s->n += 1;
+    free(nh);
+    return 0;
+}

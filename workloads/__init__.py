@@ -1,0 +1,214 @@
+"""Seeded synthetic inputs and run configurations.
+
+This module is shared by the tests, the benchmark and the oracle harness.  It
+holds parameters and input fields only -- none of the method's arithmetic --
+so that neither the CUDA path nor the oracle depends on the other through it.
+
+Configurations (grid n = (nx, ny, nz), box L, viscosity nu, penalization
+constant eta = C_eta, time-step options) and insect descriptors are plain
+dicts.  Angles are in radians; kinematic angles are Fourier series
+``a0/2 + sum_i a_i cos(2 pi i f t) + b_i sin(2 pi i f t)`` given as
+``(a0, [a_1..], [b_1..])``.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+DEG = math.pi / 180.0
+
+
+# ------------------------------------------------------------------ helpers
+
+def grid(n, L):
+    """Coordinates x_i = i L/n of the periodic grid, as (x, y, z) arrays."""
+    nx, ny, nz = n
+    Lx, Ly, Lz = L
+    x = np.arange(nx) * (Lx / nx)
+    y = np.arange(ny) * (Ly / ny)
+    z = np.arange(nz) * (Lz / nz)
+    return x, y, z
+
+
+def mean_tip_speed(phi_m, freq=1.0, R=1.0):
+    """U_tip = 2 Phi R f with stroke amplitude Phi = 2 phi_m (mean tip speed)."""
+    return 4.0 * phi_m * freq * R
+
+
+def peak_tip_speed(phi_m, freq=1.0, R=1.0):
+    """U_tip = 2 pi phi_m f R, the peak speed of phi = phi_m sin(2 pi f t)."""
+    return 2.0 * math.pi * phi_m * freq * R
+
+
+def nu_from_re(re, U, length):
+    return U * length / re
+
+
+def boundary_layer_points(nu, eta, dx):
+    """K = delta_eta / dx with delta_eta = sqrt(nu C_eta), the number of grid
+    points across the penalization boundary layer (recommended 0.1 - 0.4)."""
+    return math.sqrt(nu * eta) / dx
+
+
+# -------------------------------------------------------------- input fields
+
+def taylor_green_3d(n, L=(2 * math.pi,) * 3):
+    """u = (sin x cos y cos z, -cos x sin y cos z, 0) scaled to the box."""
+    x, y, z = grid(n, L)
+    X = 2 * math.pi * x / L[0]
+    Y = 2 * math.pi * y / L[1]
+    Z = 2 * math.pi * z / L[2]
+    Zg, Yg, Xg = np.meshgrid(Z, Y, X, indexing="ij")
+    u = np.zeros((3,) + Xg.shape)
+    u[0] = np.sin(Xg) * np.cos(Yg) * np.cos(Zg)
+    u[1] = -np.cos(Xg) * np.sin(Yg) * np.cos(Zg)
+    return u
+
+
+def taylor_green_2d(n, L=(2 * math.pi,) * 3, amplitude=1.0):
+    """z-invariant u = A (sin x cos y, -cos x sin y, 0)."""
+    x, y, z = grid(n, L)
+    X = 2 * math.pi * x / L[0]
+    Y = 2 * math.pi * y / L[1]
+    Zg, Yg, Xg = np.meshgrid(z, Y, X, indexing="ij")
+    u = np.zeros((3,) + Xg.shape)
+    u[0] = amplitude * np.sin(Xg) * np.cos(Yg)
+    u[1] = -amplitude * np.cos(Xg) * np.sin(Yg)
+    return u
+
+
+def uniform(n, u0):
+    nx, ny, nz = n
+    u = np.zeros((3, nz, ny, nx))
+    for c in range(3):
+        u[c] = u0[c]
+    return u
+
+
+def random_field(n, seed, amplitude=1.0, mean=(0.0, 0.0, 0.0)):
+    """Gaussian white noise on the grid, seeded; band limiting and the
+    divergence-free projection are left to the solver's set_state."""
+    nx, ny, nz = n
+    rng = np.random.default_rng(seed)
+    u = amplitude * rng.standard_normal((3, nz, ny, nx))
+    for c in range(3):
+        u[c] += mean[c]
+    return u
+
+
+def random_smooth_field(n, seed, amplitude=1.0, kmax=4, mean=(0.0, 0.0, 0.0)):
+    """Sum of a few random Fourier modes with integer wavenumbers |m| <= kmax,
+    built directly in physical space (cosines with random phases)."""
+    nx, ny, nz = n
+    rng = np.random.default_rng(seed)
+    zi, yi, xi = np.meshgrid(np.arange(nz) / nz, np.arange(ny) / ny, np.arange(nx) / nx,
+                             indexing="ij")
+    u = np.zeros((3, nz, ny, nx))
+    for c in range(3):
+        for _ in range(12):
+            m = rng.integers(-kmax, kmax + 1, size=3)
+            ph = rng.uniform(0, 2 * math.pi)
+            a = rng.standard_normal() * amplitude / 4
+            u[c] += a * np.cos(2 * math.pi * (m[0] * xi + m[1] * yi + m[2] * zi) + ph)
+        u[c] += mean[c]
+    return u
+
+
+# ------------------------------------------------------------ insect shapes
+
+def sphere(center, radius, profile="tanh", c_smth=1.0):
+    """Fixed sphere, u_s = 0 (config "plain method, 32^3")."""
+    return {"body": "sphere", "nwings": 0, "profile": profile, "c_smth": c_smth,
+            "x_cntr": tuple(center), "body_axes": (radius, 0.0)}
+
+
+def flapping_kinematics(phi_m=60 * DEG, alpha_m=45 * DEG, freq=1.0):
+    """phi = phi_m sin(2 pi f t), alpha = alpha_m cos(2 pi f t), theta = 0."""
+    return {"phi": (0.0, [0.0], [phi_m]), "alpha": (0.0, [alpha_m], [0.0]),
+            "theta": (0.0, [0.0], [0.0])}
+
+
+def plate_wing(dx, chord=0.3, span=1.0, thickness_cells=4.0):
+    """Rectangular plate: (c_le, c_te, R, h); feathering axis at mid-chord."""
+    return (0.5 * chord, 0.5 * chord, span, thickness_cells * dx)
+
+
+def single_wing(L=(4.0, 4.0, 4.0), n=(256, 256, 256), phi_m=60 * DEG, alpha_m=45 * DEG,
+                freq=1.0):
+    """One rigid flat-plate wing pivoting at its root in the box centre."""
+    dx = max(L[i] / n[i] for i in range(3))
+    return {"body": "none", "nwings": 1, "profile": "cos", "c_smth": 1.0,
+            "x_cntr": tuple(0.5 * l for l in L), "eta_stroke": -90 * DEG,
+            "pivot_l": (0.0, 0.0, 0.0), "wing": plate_wing(dx), "freq": freq,
+            "kinematics": flapping_kinematics(phi_m, alpha_m, freq)}
+
+
+def model_insect(L=(4.0, 4.0, 4.0), n=(512, 512, 512)):
+    """Ellipsoidal body (0.5, 0.12, 0.12) plus two mirror-symmetric plates."""
+    dx = max(L[i] / n[i] for i in range(3))
+    return {"body": "ellipsoid", "nwings": 2, "profile": "cos", "c_smth": 1.0,
+            "x_cntr": tuple(0.5 * l for l in L), "body_axes": (0.5, 0.12),
+            "eta_stroke": -90 * DEG, "pivot_l": (0.0, 0.15, 0.0),
+            "pivot_r": (0.0, -0.15, 0.0), "wing": plate_wing(dx), "freq": 1.0,
+            "kinematics": flapping_kinematics()}
+
+
+# ------------------------------------------------------------ configurations
+
+def config_tg_sphere(n=32):
+    """Plain method, FP64: Taylor-Green in a 2 pi box with a fixed sphere."""
+    L = (2 * math.pi,) * 3
+    cfg = {"name": f"tg_sphere_{n}", "n": (n, n, n), "L": L, "nu": 0.01, "eta": 1e-2,
+           "dt_fixed": 1e-3, "steps": 20, "mean_mode": "fixed"}
+    cfg["init"] = ("taylor_green_3d",)
+    ins = sphere((math.pi, math.pi, math.pi), 0.5, profile="tanh")
+    return cfg, ins
+
+
+def config_single_wing(n=256):
+    """One flapping plate at Re = 100 (chord, mean tip speed), 4^3 box."""
+    L = (4.0, 4.0, 4.0)
+    U = mean_tip_speed(60 * DEG)
+    cfg = {"name": f"single_wing_{n}", "n": (n, n, n), "L": L,
+           "nu": nu_from_re(100.0, U, 0.3), "eta": 2.5e-3, "cfl": 0.1, "mean_mode": "fixed"}
+    cfg["init"] = ("uniform", (0.0, 0.0, 0.0))
+    ins = single_wing(L, cfg["n"])
+    return cfg, ins
+
+
+def config_model_insect(n=512):
+    """Model insect at Re = 300 in uniform inflow (0.25, 0, 0), 4^3 box."""
+    L = (4.0, 4.0, 4.0)
+    U = mean_tip_speed(60 * DEG)
+    cfg = {"name": f"model_insect_{n}", "n": (n, n, n), "L": L,
+           "nu": nu_from_re(300.0, U, 0.3), "eta": 1e-3, "cfl": 0.1, "mean_mode": "fixed",
+           "u_inf": (0.25, 0.0, 0.0)}
+    cfg["init"] = ("uniform", (0.25, 0.0, 0.0))
+    ins = model_insect(L, cfg["n"])
+    return cfg, ins
+
+
+def initial_field(cfg, dtype=np.float64):
+    """The configuration's initial velocity on the grid, [3][nz][ny][nx]."""
+    kind = cfg["init"][0]
+    if kind == "taylor_green_3d":
+        u = taylor_green_3d(cfg["n"], cfg["L"])
+    elif kind == "uniform":
+        nx, ny, nz = cfg["n"]
+        u = np.empty((3, nz, ny, nx), dtype)
+        for c in range(3):
+            u[c] = cfg["init"][1][c]
+        return u
+    elif kind == "random_smooth":
+        u = random_smooth_field(cfg["n"], cfg["init"][1], mean=cfg.get("u_inf", (0, 0, 0)))
+    else:
+        raise ValueError(kind)
+    return u.astype(dtype, copy=False)
+
+
+def steps_per_wingbeat(cfg, peak_speed=2 * math.pi * 60 * DEG):
+    """Rough step count of one wingbeat under the CFL limit at peak tip speed."""
+    dx = min(cfg["L"][i] / cfg["n"][i] for i in range(3))
+    dt = min(cfg.get("cfl", 0.1) * dx / peak_speed, cfg["eta"])
+    return int(math.ceil(1.0 / dt))
