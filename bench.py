@@ -1,0 +1,417 @@
+#!/usr/bin/env python
+"""Benchmark of the penalized pseudo-spectral Navier-Stokes AB2 step on GB300.
+
+Workload: the model insect (ellipsoidal body + two flapping plates, Re 300,
+inflow 0.25, C_eta = 1e-3, CFL 0.1 adaptive dt) on a 512^3 grid over a 4^3
+box, FP32 state; the same step in FP64 is timed beside it.  Reported: grid-point
+steps/s of the whole job, the dominant kernel against the measured HBM peak,
+the stage-model fraction, an end-to-end figure through the C-ABI with host
+buffers, and the CPU oracle timed on a bounded sample.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank runs an independent replica on its own GPU
+(the step has no exchange) and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "AB2 grid-point steps/s at 512³, FP32 vs FP64 on 1 GB300; % of HBM roofline"
+UNIT = "grid-point steps/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="flusi", choices=["flusi", "reference"])
+    ap.add_argument("--grid", type=int, default=512)
+    ap.add_argument("--fp64-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
+
+
+# ------------------------------------------------------------------ workload
+
+def cutoff(n):
+    return n // 3
+
+
+def spectral_sizes(n):
+    nx, ny, nz = n
+    Mx, My, Mz = cutoff(nx) + 1, 2 * cutoff(ny) + 1, 2 * cutoff(nz) + 1
+    return Mx, My, Mz
+
+
+def kernel_bytes(n, s):
+    """Algorithmic bytes per launch of each kernel: every input it must read
+    and every output it must write once, complex values of 2s bytes over the
+    kept modes (x: Mx of nx/2+1; y: My of ny; z: Mz of nz)."""
+    nx, ny, nz = n
+    Mx, My, Mz = spectral_sizes(n)
+    c = 2 * s
+    A = nz * My * Mx * c          # one field after the z transform
+    B = nz * ny * Mx * c          # one field after the y transform
+    S = Mz * My * Mx * c          # one state field
+    return {
+        "zinv_curl": 3 * S + 6 * A,
+        "yinv": 6 * A + 6 * B,
+        "xpass_phys": 6 * B + 3 * B,
+        "yfwd": 3 * B + 3 * A,
+        "zfwd_update": 3 * A + 2 * 3 * S + 2 * 3 * S,
+        "kinematics": 0,
+        "scalars": 0,
+    }
+
+
+def stage_model_bytes(n, s):
+    """Stage-model bytes per step: 6 inverse + 3 forward full FFTs read and
+    written once, the physical pass and the spectral pass over the full half
+    spectrum: B = 24 F_c + 18 F_r."""
+    nx, ny, nz = n
+    Fr = s * nx * ny * nz
+    Fc = 2 * s * (nx // 2 + 1) * ny * nz
+    return 24 * Fc + 18 * Fr
+
+
+def bench_field(cfg):
+    """Uniform inflow plus band-limited divergence-free waves (float32)."""
+    return workloads.shear_waves(cfg["n"], cfg["L"], mean=cfg["u_inf"]).astype(np.float32)
+
+
+# ------------------------------------------------------------------- clocks
+
+class Clocks:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        if self.uuid:
+            cmd[1:1] = ["-i", self.uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+                power.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------- CPU oracle
+
+def oracle_sample(n_sample=128, steps=3):
+    """The oracle (single-threaded C, FP64) on the same workload at a reduced
+    grid, as it stands: grid-point steps/s."""
+    import oracle
+    cfg, ins = workloads.config_model_insect(n_sample)
+    sim = oracle.Simulation(cfg, ins)
+    sim.set_state(workloads.shear_waves(cfg["n"], cfg["L"], mean=cfg["u_inf"]))
+    t0 = time.perf_counter()
+    sim.step(steps)
+    el = time.perf_counter() - t0
+    return {"value": n_sample ** 3 * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"model insect at {n_sample}^3 (same box, body, wings, Re, C_eta), {steps} "
+                      f"steps, FP64 single-threaded C, {el:.1f} s"}
+
+
+# ------------------------------------------------------------------ own arm
+
+def run_flusi(args):
+    import torch
+    import paper_1506_06513_gb300 as fl
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def allmax(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    n = args.grid
+    cfg, ins = workloads.config_model_insect(n)
+    N = n ** 3
+    u0 = bench_field(cfg)
+    peaks, peak_src = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+
+    # ---- FP32, device-resident timed region
+    sim = fl.Solver(cfg, ins, precision="fp32", device=local)
+    sim.set_state(u0)
+    sim.step(args.warmup)
+    sim.sync()
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+        if uuid and not uuid.startswith("GPU-"):
+            uuid = "GPU-" + uuid
+    except Exception:
+        uuid = None
+    clocks = Clocks(uuid)
+    clocks.start()
+    time.sleep(0.3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    ev0.record(sim.stream)
+    sim.step(args.steps)
+    ev1.record(sim.stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    sim.sync()
+    ms_max = allmax(ms)
+    value = N * args.steps * world / (ms_max * 1e-3)
+    ms_per_step = ms_max / args.steps
+    kps = fl.flusi_kernels_per_step(sim.h)
+
+    # ---- per-kernel durations (CUDA events on the solver stream)
+    prof = sim.profile(10)
+    kb = kernel_bytes(cfg["n"], 4)
+    dom = max(prof, key=prof.get)
+    ach = kb[dom] / (prof[dom] * 1e-3) / 1e9
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            tr = json.load(f)
+        ent = tr.get(f"{dom}@{n}^3/fp32")
+        if ent and ent.get("source_hash") == source_hash():
+            traffic = ent["bytes_per_launch"]
+    except (OSError, ValueError):
+        pass
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": hbm,
+                "unit": "GB/s", "frac": round(ach / hbm, 4), "traffic": traffic,
+                "algorithmic_bytes": kb[dom], "peak_source": f"{peak_src} (hbm_gbs, copy)"}
+    kernels = {k: {"ms": round(v, 4), "GB_s": round(kb[k] / (v * 1e-3) / 1e9, 1) if kb[k] else None}
+               for k, v in prof.items()}
+    stage = stage_model_bytes(cfg["n"], 4)
+    step_bytes = sum(kb.values())
+
+    # ---- end to end through the C-ABI with pinned host buffers
+    e2e_steps = args.e2e_steps
+    host_in = torch.from_numpy(u0).pin_memory().numpy()
+    host_out = torch.empty(u0.shape, dtype=torch.float32).pin_memory().numpy()
+    rows_total = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    fl.flusi_set_state(sim.h, host_in, fl.FLUSI_HOST_FP32)
+    for _ in range(e2e_steps):
+        fl.flusi_set_kinematics(sim.h, sim.insect)
+        fl.flusi_step(sim.h, 1)
+        rows, _ = fl.flusi_forces(sim.h, 4)
+        rows_total += rows.shape[0]
+    fl.flusi_get_state(sim.h, host_out, fl.FLUSI_HOST_FP32)
+    e2e_s = time.perf_counter() - t0
+    assert rows_total == e2e_steps and np.isfinite(host_out[:, ::64, ::64, ::64]).all()
+    e2e_s = allmax(e2e_s)
+    state_bytes = u0.nbytes
+    e2e = {"value": N * e2e_steps * world / e2e_s, "unit": UNIT, "steps": e2e_steps,
+           "h2d_bytes_per_step": (state_bytes + e2e_steps * 1536) / e2e_steps,
+           "d2h_bytes_per_step": (state_bytes + e2e_steps * 22 * 8) / e2e_steps,
+           "what": "set_state from pinned host FP32, per step set_kinematics (H2D) + step + "
+                   "force-row drain (D2H), get_state to pinned host FP32"}
+    sim.close()
+    del host_in, host_out
+
+    # ---- FP64 beside it
+    fp64 = None
+    if not args.no_fp64:
+        sim64 = fl.Solver(cfg, ins, precision="fp64", device=local)
+        sim64.set_state(u0)
+        sim64.step(2)
+        sim64.sync()
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(sim64.stream)
+        sim64.step(args.fp64_steps)
+        ev1.record(sim64.stream)
+        torch.cuda.synchronize()
+        ms64 = allmax(ev0.elapsed_time(ev1))
+        sim64.sync()
+        prof64 = sim64.profile(2)
+        sim64.close()
+        v64 = N * args.fp64_steps * world / (ms64 * 1e-3)
+        fp64 = {"value": v64, "unit": UNIT, "ms_per_step": ms64 / args.fp64_steps,
+                "steps": args.fp64_steps, "fp32_speedup": value / v64,
+                "kernels_ms": {k: round(v, 3) for k, v in prof64.items()}}
+    del u0
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = oracle_sample()
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"model insect {n}^3 FP32: ellipsoid body (0.5, 0.12) + 2 flapping "
+                               "plates (c 0.3, R 1, 4dx thick, phi 60deg sin, alpha 45deg cos), "
+                               "Re 300, u_inf (0.25,0,0), C_eta 1e-3, CFL 0.1 adaptive dt",
+                   "grid": [n, n, n], "box": [4.0, 4.0, 4.0], "precision": "fp32",
+                   "initial": "inflow + band-limited divergence-free waves",
+                   "l2": f"inputs larger than L2: {step_bytes / 1e9:.1f} GB moved per step",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": roofline,
+        "stage_model": {"bytes_per_step": stage, "frac_of_peak": round(stage / (ms_per_step * 1e-3) / 1e9 / hbm, 4),
+                        "frac_of_nominal_8TBs": round(stage / (ms_per_step * 1e-3) / 8e12, 4),
+                        "kernel_bytes_per_step": step_bytes,
+                        "kernel_bytes_frac_of_peak": round(step_bytes / (ms_per_step * 1e-3) / 1e9 / hbm, 4)},
+        "kernels_ms": kernels,
+        "fp64": fp64,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": kps * args.steps,
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1506_06513_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+# ----------------------------------------------------------- reference arm
+
+def run_reference(args):
+    """The oracle as it stands, on the host cores: each step is one oracle
+    step of the same workload at a grid small enough that the whole run ends
+    in about two minutes."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    # choose the sample grid from a timed probe step
+    pick = 32
+    for n in (32, 48, 64, 96, 128):
+        cfg, ins = workloads.config_model_insect(n)
+        sim = oracle.Simulation(cfg, ins)
+        sim.set_state(workloads.shear_waves(cfg["n"], cfg["L"], mean=cfg["u_inf"]))
+        t0 = time.perf_counter()
+        sim.step(1)
+        per = time.perf_counter() - t0
+        if per * (args.steps + args.warmup) > 120.0:
+            break
+        pick = n
+    cfg, ins = workloads.config_model_insect(pick)
+    sim = oracle.Simulation(cfg, ins)
+    sim.set_state(workloads.shear_waves(cfg["n"], cfg["L"], mean=cfg["u_inf"]))
+    sim.step(args.warmup)
+    t0 = time.perf_counter()
+    sim.step(args.steps)
+    el = time.perf_counter() - t0
+    value = pick ** 3 * args.steps / el
+    sample = (f"model insect at {pick}^3 (same box, body, wings, Re, C_eta), FP64 "
+              f"single-threaded C oracle, {args.steps} steps in {el:.1f} s")
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "impl": "reference",
+           "config": {"workload": f"model insect {args.grid}^3 (oracle sample at {pick}^3)",
+                      "grid": [pick] * 3, "box": [4.0, 4.0, 4.0], "precision": "fp64"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_flusi(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,188 @@
+/*
+ * libflusi -- one time step of the volume-penalized incompressible
+ * Navier-Stokes equations in rotational form, solved by a Fourier
+ * pseudo-spectral method in a periodic box, on one GB300 GPU (sm_103a).
+ *
+ * Method: Engels, Kolomenskiy, Schneider, Sesterhenn, "FluSI: a novel
+ * parallel simulation tool for flapping insect flight using a Fourier method
+ * with volume penalization" (arXiv 1506.06513): Eq. PNST_org_momentum without
+ * the sponge term, Sec. 2.4 (discretization, 2/3 rule, AB2 with integrating
+ * factor), Sec. 3 (insect geometry and kinematics), Algorithm 1 (one step).
+ *
+ * Conventions shared by every entry point
+ *  - Grid x_i = i*Lx/nx (same for y, z); physical fields are [3][nz][ny][nx],
+ *    x fastest, component-major.
+ *  - Spectral fields returned to the caller are the half spectrum
+ *    [3][nz][ny][nx/2+1] of u_hat = FFT(u)/N, so u(x) = sum_k u_hat_k e^{i k.x};
+ *    k = 2 pi m / L with m_x in 0..nx/2 and m_y, m_z in {0..n/2-1, -n/2..-1}.
+ *  - Every call returns a status code (flusi_status); nothing aborts or throws
+ *    across the ABI.  flusi_last_error() describes the last failure.
+ *  - A handle is not thread-safe; use one host thread per handle.
+ *  - Host arrays are owned by the caller and copied synchronously on the bound
+ *    stream.  Device pointers passed in are owned by the caller.
+ *  - Errors found on the device (a non-finite velocity or nonlinear term) land
+ *    in a device status word; they surface at the next call that synchronizes
+ *    (flusi_forces, flusi_get_state, flusi_get_spectrum, flusi_sync), after
+ *    which flusi_step returns FLUSI_ESTATE until the next flusi_set_state.
+ */
+#ifndef FLUSI_H
+#define FLUSI_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct flusi_s *flusi_t;
+
+typedef enum {
+    FLUSI_OK = 0,
+    FLUSI_EINVAL = 1,    /* bad argument (size, pointer, option, call order)   */
+    FLUSI_ENOMEM = 2,    /* bound workspace smaller than flusi_workspace_bytes */
+    FLUSI_ECUDA = 3,     /* a CUDA runtime call failed                         */
+    FLUSI_ENONFINITE = 4,/* a non-finite u or u x omega - chi/C_eta (u - u_s)  */
+    FLUSI_ETIMEOUT = 5,  /* a device-side wait gave up                        */
+    FLUSI_ESTATE = 6     /* no state set, not bound, or poisoned by an error   */
+} flusi_status;
+
+/* Arithmetic of the state, the FFTs and the pointwise products.  Force,
+ * energy and CFL reductions and the kinematics are FP64 in both. */
+typedef enum { FLUSI_FP64 = 0, FLUSI_FP32 = 1 } flusi_precision;
+
+/* Where an array passed to set_state / get_state lives. */
+typedef enum { FLUSI_HOST_FP64 = 0, FLUSI_HOST_FP32 = 1, FLUSI_DEVICE = 2 } flusi_where;
+
+#define FLUSI_MAX_FOURIER 8
+#define FLUSI_FORCE_COLS 22
+
+/* Columns of one force row (Eqs. force_with_unst_corrections and
+ * moment_of_love, one block per mask colour: 0 body, 1 left wing, 2 right). */
+#define FLUSI_COL_T 0
+#define FLUSI_COL_DT 1
+#define FLUSI_COL_F(colour) (2 + 6 * (colour))
+#define FLUSI_COL_M(colour) (5 + 6 * (colour))
+#define FLUSI_COL_EKIN 20
+#define FLUSI_COL_UMAX 21
+
+typedef struct flusi_options {
+    double cfl;            /* CFL number of the adaptive step (default 0.1)            */
+    double dt_fixed;       /* > 0: fixed step; 0: adaptive (default 0)                  */
+    double dt_max;         /* > 0: cap on the adaptive step (default 0 = none)          */
+    double u_inf[3];       /* mean flow held at k = 0 when mean_mode = 0 (default 0)    */
+    int mean_mode;         /* 0: k = 0 mode held at u_inf; 1: evolves freely            */
+    int dealias_strict;    /* 0: keep |m| <= floor(n/3); 1: keep |m| < n/3              */
+    int force_ring;        /* device rows kept between flusi_forces calls (default 4096)*/
+    int use_graph;         /* 1: replay a captured CUDA graph per step (default 1)      */
+} flusi_options;
+
+/* Insect geometry and kinematics (Sec. 3).  Angles in radians.  Kinematic
+ * angles are Fourier series a0/2 + sum_i a[i] cos(2 pi (i+1) f t)
+ * + b[i] sin(2 pi (i+1) f t), i < nfourier. */
+typedef struct flusi_insect {
+    int body_type;             /* 0 none, 1 sphere (radius body_a), 2 ellipsoid thorax */
+    int nwings;                /* 0, 1 (left wing only) or 2                            */
+    int profile;               /* 0: cosine layer (Sec. 2.2); 1: 1/2 (1 - tanh(delta/h)) */
+    int nfourier;              /* harmonics used, <= FLUSI_MAX_FOURIER                  */
+    double c_smth;             /* layer half-width h = c_smth * max(dx, dy, dz)          */
+    double x_cntr[3], u_cntr[3];           /* body centre and its velocity (global)    */
+    double psi, beta, gamma;               /* roll, pitch, yaw (Eq. M_body_yawpitchroll) */
+    double psi_dot, beta_dot, gamma_dot;   /* their rates (body angular velocity)       */
+    double body_a, body_b;                 /* thorax semi-axes (x; y and z)             */
+    double pivot_l[3], pivot_r[3];         /* wing pivots in the body frame             */
+    double eta_stroke;                     /* anatomical stroke-plane angle             */
+    double wing_c_le, wing_c_te, wing_R, wing_h; /* plate: chord extents, span, thickness */
+    double freq;
+    double phi_a0, phi_a[FLUSI_MAX_FOURIER], phi_b[FLUSI_MAX_FOURIER];
+    double alpha_a0, alpha_a[FLUSI_MAX_FOURIER], alpha_b[FLUSI_MAX_FOURIER];
+    double theta_a0, theta_a[FLUSI_MAX_FOURIER], theta_b[FLUSI_MAX_FOURIER];
+} flusi_insect;
+
+/* Create a solver for an nx x ny x nz periodic grid over the box L[3], with
+ * kinematic viscosity nu and penalization constant eta (C_eta of Eq.
+ * PNST_org_momentum).  Each n_i must be 2^a 3^b with 8 <= n_i <= 1024 and nx
+ * even.  precision is a flusi_precision.  Allocates only a small host struct;
+ * device memory is bound later (flusi_bind).  Returns FLUSI_EINVAL for bad
+ * sizes or a NULL `out`. */
+int flusi_create(int nx, int ny, int nz, const double L[3], double nu, double eta,
+                 int precision, flusi_t *out);
+
+/* Fill *opt with the defaults listed in flusi_options. */
+void flusi_default_options(flusi_options *opt);
+
+/* Replace the options (Algorithm 1 step b time-step rule, mean mode, 2/3-rule
+ * variant, force ring size, graph use).  Allowed before flusi_bind; after it,
+ * only options that keep the workspace size.  Invalidates a captured graph. */
+int flusi_set_options(flusi_t h, const flusi_options *opt);
+
+/* Bytes of device workspace the handle needs with its current options. */
+int flusi_workspace_bytes(flusi_t h, size_t *bytes);
+
+/* Bind a caller-owned device workspace (>= flusi_workspace_bytes, 256-byte
+ * aligned, outliving the handle) and a CUDA stream (cudaStream_t; NULL is the
+ * legacy default stream).  All later work is enqueued on that stream.  Zeroes
+ * the workspace and builds the FFT twiddle tables.  FLUSI_ENOMEM if too small. */
+int flusi_bind(flusi_t h, void *dev_workspace, size_t bytes, void *cuda_stream);
+
+/* Set the velocity u [3][nz][ny][nx] (Algorithm 1 step 1, initial condition):
+ * where = FLUSI_HOST_FP64 / FLUSI_HOST_FP32 (host array) or FLUSI_DEVICE (a
+ * device array in the handle's precision).  The field is transformed,
+ * truncated by the 2/3 rule and projected onto divergence-free fields; with
+ * mean_mode 0 its mean is replaced by u_inf.  Resets t = 0, the step count,
+ * the AB2 history, the force rows and the device status word. */
+int flusi_set_state(flusi_t h, const void *u, int where);
+
+/* Set the insect (Sec. 3): body, wings, kinematics.  Without a call (or with
+ * NULL) there is no mask.  May be called between steps. */
+int flusi_set_kinematics(flusi_t h, const flusi_insect *insect);
+
+/* Enqueue n time steps (Algorithm 1 steps a-e) on the bound stream and
+ * return without waiting.  Only argument and call-order errors are reported
+ * here; device errors surface at the next synchronizing call. */
+int flusi_step(flusi_t h, int n);
+
+/* Wait for the enqueued work and check the device status word. */
+int flusi_sync(flusi_t h);
+
+/* Drain the force rows produced since the last call (in step order) into
+ * rows[count][FLUSI_FORCE_COLS] (host, capacity `cap` rows).  Row columns:
+ * t, dt, then per colour F[3], M[3], then E_kin = 1/2 sum |u|^2 dV and
+ * max |u|.  Synchronizes.  Rows beyond force_ring since the last call are
+ * lost; *lost (may be NULL) receives their number. */
+int flusi_forces(flusi_t h, double *rows, int cap, int *count, long long *lost);
+
+/* Copy the velocity u [3][nz][ny][nx] to host FP64 (where = FLUSI_HOST_FP64),
+ * host FP32, or a caller device array in the handle's precision, with the
+ * time t and step count (either may be NULL).  Synchronizes. */
+int flusi_get_state(flusi_t h, void *u_out, int where, double *t, long long *step);
+
+/* Copy u_hat to host FP64 complex, half-spectrum layout [3][nz][ny][nx/2+1]
+ * (interleaved re, im), zero outside the 2/3-rule set.  Synchronizes. */
+int flusi_get_spectrum(flusi_t h, double *uh_out);
+
+/* Diagnostic: evaluate the physical-space fields of the current state at the
+ * current time into the caller's device array out [14][nz][ny][nx] in the
+ * handle's precision: u[3], omega[3], chi, colour, u_s[3], and the term
+ * u x omega - chi/C_eta (u - u_s) [3] (Sec. 2.1, Algorithm 1 step c).
+ * Enqueued on the bound stream. */
+int flusi_debug_fields(flusi_t h, void *out_dev);
+
+/* Diagnostic: time each kernel of one step with CUDA events on the bound
+ * stream over n un-captured steps (which advance the state).  ms[i] gets the
+ * mean duration of kernel i, names[i] its name; *nk the number of kernels
+ * (at most 16).  Synchronizes. */
+int flusi_profile_step(flusi_t h, int n, double *ms, const char **names, int *nk);
+
+/* Kernels launched per step (for launch accounting). */
+int flusi_kernels_per_step(flusi_t h, int *count);
+
+/* Release the handle (not the caller's workspace).  NULL is a no-op. */
+int flusi_destroy(flusi_t h);
+
+/* Message of the last failed call on h (or of flusi_create when h is NULL). */
+const char *flusi_last_error(flusi_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -116,6 +116,8 @@ def lib():
         L.orc_get_state.argtypes = [C.POINTER(Params), _cp, _dp]
         L.orc_rhs.argtypes = [C.POINTER(Params), C.POINTER(Insect), C.c_double, _cp, _cp, _dp]
         L.orc_rhs.restype = C.c_int
+        L.orc_physical_fields.argtypes = [C.POINTER(Params), C.POINTER(Insect), C.c_double, _cp,
+                                          _dp]
         L.orc_ab2_update.argtypes = [C.POINTER(Params), _cp, _cp, _cp, C.c_double,
                                      C.c_double, C.c_int64]
         L.orc_step.argtypes = [C.POINTER(Params), C.POINTER(Insect), _cp, _cp,
@@ -303,6 +305,14 @@ class Spectral:
         ins = make_insect(insect)
         lib().orc_rhs(C.byref(self.p), _ins_ptr(ins), t, np.ascontiguousarray(uh), nh, sums)
         return nh, sums
+
+    def physical_fields(self, uh, t=0.0, insect=None):
+        """[14][nz][ny][nx]: u, omega, chi, colour, u_s, u x omega - chi/C_eta (u - u_s)."""
+        nx, ny, nz = self.n
+        out = np.zeros((14, nz, ny, nx))
+        ins = make_insect(insect)
+        lib().orc_physical_fields(C.byref(self.p), _ins_ptr(ins), t, np.ascontiguousarray(uh), out)
+        return out
 
     def ab2_update(self, uh, nh, nh_prev, dt, dt_prev, n):
         u = np.ascontiguousarray(uh).copy()

@@ -109,6 +109,10 @@ int orc_set_state(const orc_params *p, const double *u, double complex *uh,
 void orc_get_state(const orc_params *p, const double complex *uh, double *u);
 int orc_rhs(const orc_params *p, const orc_insect *ins, double t,
             const double complex *uh, double complex *nh, double *sums);
+/* fields [14][nz][ny][nx]: u(3), omega(3), chi, colour, u_s(3),
+ * u x omega - chi/C_eta (u - u_s) (3) */
+void orc_physical_fields(const orc_params *p, const orc_insect *ins, double t,
+                         const double complex *uh, double *fields);
 void orc_ab2_update(const orc_params *p, double complex *uh,
                     const double complex *nh, const double complex *nh_prev,
                     double dt, double dt_prev, int64_t n);

@@ -147,18 +147,19 @@ static double grid_h(const orc_params *p, const orc_insect *ins)
 }
 
 /*
- * Right-hand side of Algorithm 1 steps (a), (c), (d) at time t:
- * nh = P D FFT(u x omega - chi/C_eta (u - u_s)) / N, plus the FP64 sums.
+ * Algorithm 1 steps (a) and (c) in physical space at time t: u and omega from
+ * u_hat, then per grid point chi, colour, u_s and
+ * nl = u x omega - chi/C_eta (u - u_s), plus the FP64 sums.  When `fields` is
+ * not NULL it receives [u(3), omega(3), chi, colour, u_s(3), nl(3)] per point.
  * Returns 1 if a non-finite value was met, else 0.
  */
-int orc_rhs(const orc_params *p, const orc_insect *ins, double t,
-            const double complex *uh, double complex *nh, double *sums)
+static int physical_terms(const orc_params *p, const orc_insect *ins, double t,
+                          const double complex *uh, double *nl, double *sums, double *fields)
 {
     long N = n_phys(p), nhs = n_half(p);
     double complex *wh = malloc(sizeof(double complex) * (size_t)(3 * nhs));
     double *u = malloc(sizeof(double) * (size_t)(3 * N));
     double *w = malloc(sizeof(double) * (size_t)(3 * N));
-    double *nl = malloc(sizeof(double) * (size_t)(3 * N));
 
     orc_curl(p, uh, wh);
     orc_inverse(p, uh, u, 3);
@@ -191,6 +192,16 @@ int orc_rhs(const orc_params *p, const orc_insect *ins, double t,
                     nl[c * N + i] = v;
                     if (!isfinite(v) || !isfinite(uu[c])) bad = 1;
                 }
+                if (fields) {
+                    for (int c = 0; c < 3; ++c) {
+                        fields[c * N + i] = uu[c];
+                        fields[(3 + c) * N + i] = ww[c];
+                        fields[(8 + c) * N + i] = us[c];
+                        fields[(11 + c) * N + i] = nl[c * N + i];
+                    }
+                    fields[6 * N + i] = chi;
+                    fields[7 * N + i] = col;
+                }
                 double u2 = uu[0] * uu[0] + uu[1] * uu[1] + uu[2] * uu[2];
                 sums[ORC_SUM_EKIN] += 0.5 * u2 * dV;
                 if (sqrt(u2) > sums[ORC_SUM_UMAX]) sums[ORC_SUM_UMAX] = sqrt(u2);
@@ -218,6 +229,33 @@ int orc_rhs(const orc_params *p, const orc_insect *ins, double t,
                 }
             }
     sums[ORC_SUM_NONFINITE] = bad;
+    free(w);
+    free(u);
+    free(wh);
+    return bad;
+}
+
+void orc_physical_fields(const orc_params *p, const orc_insect *ins, double t,
+                         const double complex *uh, double *fields)
+{
+    long N = n_phys(p);
+    double *nl = malloc(sizeof(double) * (size_t)(3 * N));
+    double sums[ORC_NSUMS];
+    physical_terms(p, ins, t, uh, nl, sums, fields);
+    free(nl);
+}
+
+/*
+ * Right-hand side of Algorithm 1 steps (a), (c), (d) at time t:
+ * nh = P D FFT(u x omega - chi/C_eta (u - u_s)) / N, plus the FP64 sums.
+ * Returns 1 if a non-finite value was met, else 0.
+ */
+int orc_rhs(const orc_params *p, const orc_insect *ins, double t,
+            const double complex *uh, double complex *nh, double *sums)
+{
+    long N = n_phys(p), nhs = n_half(p);
+    double *nl = malloc(sizeof(double) * (size_t)(3 * N));
+    int bad = physical_terms(p, ins, t, uh, nl, sums, NULL);
 
     orc_forward(p, nl, nh, 3);
     orc_dealias(p, nh, 3);
@@ -226,9 +264,6 @@ int orc_rhs(const orc_params *p, const orc_insect *ins, double t,
         for (int c = 0; c < 3; ++c) nh[c * nhs] = 0;
 
     free(nl);
-    free(w);
-    free(u);
-    free(wh);
     return bad;
 }
 

@@ -1,0 +1,322 @@
+"""Python binding of libflusi (include/flusi.h).
+
+The ``flusi_*`` functions below have the C names and marshal arguments only;
+every step of the solver runs in the CUDA kernels of ``libflusi.so``.
+PyTorch supplies device memory (the workspace) and the stream.  There is no
+fallback: importing the binding fails loudly when the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libflusi.so")
+
+FLUSI_OK, FLUSI_EINVAL, FLUSI_ENOMEM, FLUSI_ECUDA, FLUSI_ENONFINITE, FLUSI_ETIMEOUT, FLUSI_ESTATE = range(7)
+FLUSI_FP64, FLUSI_FP32 = 0, 1
+FLUSI_HOST_FP64, FLUSI_HOST_FP32, FLUSI_DEVICE = 0, 1, 2
+MAX_FOURIER = 8
+FORCE_COLS = 22
+STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENONFINITE", "ETIMEOUT", "ESTATE"]
+
+
+class FlusiError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"flusi {STATUS_NAMES[code] if 0 <= code < 7 else code}: {msg}")
+        self.code = code
+
+
+class Options(C.Structure):
+    _fields_ = [("cfl", C.c_double), ("dt_fixed", C.c_double), ("dt_max", C.c_double),
+                ("u_inf", C.c_double * 3), ("mean_mode", C.c_int), ("dealias_strict", C.c_int),
+                ("force_ring", C.c_int), ("use_graph", C.c_int)]
+
+
+_F = C.c_double * MAX_FOURIER
+
+
+class Insect(C.Structure):
+    _fields_ = [("body_type", C.c_int), ("nwings", C.c_int), ("profile", C.c_int),
+                ("nfourier", C.c_int), ("c_smth", C.c_double),
+                ("x_cntr", C.c_double * 3), ("u_cntr", C.c_double * 3),
+                ("psi", C.c_double), ("beta", C.c_double), ("gamma", C.c_double),
+                ("psi_dot", C.c_double), ("beta_dot", C.c_double), ("gamma_dot", C.c_double),
+                ("body_a", C.c_double), ("body_b", C.c_double),
+                ("pivot_l", C.c_double * 3), ("pivot_r", C.c_double * 3),
+                ("eta_stroke", C.c_double),
+                ("wing_c_le", C.c_double), ("wing_c_te", C.c_double), ("wing_R", C.c_double),
+                ("wing_h", C.c_double), ("freq", C.c_double),
+                ("phi_a0", C.c_double), ("phi_a", _F), ("phi_b", _F),
+                ("alpha_a0", C.c_double), ("alpha_a", _F), ("alpha_b", _F),
+                ("theta_a0", C.c_double), ("theta_a", _F), ("theta_b", _F)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libflusi.so is not built ({LIB_PATH}); run __graft_entry__.build() "
+                          "or python -m paper_1506_06513_gb300._build")
+    lib = C.CDLL(LIB_PATH)
+    h, vp, dp, ip = C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.c_int
+    sig = {
+        "flusi_create": ([ip, ip, ip, dp, C.c_double, C.c_double, ip, C.POINTER(h)], ip),
+        "flusi_default_options": ([C.POINTER(Options)], None),
+        "flusi_set_options": ([h, C.POINTER(Options)], ip),
+        "flusi_workspace_bytes": ([h, C.POINTER(C.c_size_t)], ip),
+        "flusi_bind": ([h, vp, C.c_size_t, vp], ip),
+        "flusi_set_state": ([h, vp, ip], ip),
+        "flusi_set_kinematics": ([h, C.POINTER(Insect)], ip),
+        "flusi_step": ([h, ip], ip),
+        "flusi_sync": ([h], ip),
+        "flusi_forces": ([h, dp, ip, C.POINTER(C.c_int), C.POINTER(C.c_longlong)], ip),
+        "flusi_get_state": ([h, vp, ip, dp, C.POINTER(C.c_longlong)], ip),
+        "flusi_get_spectrum": ([h, dp], ip),
+        "flusi_debug_fields": ([h, vp], ip),
+        "flusi_profile_step": ([h, ip, dp, C.POINTER(C.c_char_p), C.POINTER(C.c_int)], ip),
+        "flusi_kernels_per_step": ([h, C.POINTER(C.c_int)], ip),
+        "flusi_destroy": ([h], ip),
+        "flusi_last_error": ([h], C.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+lib = _load()
+
+
+def _check(handle, rc):
+    if rc != FLUSI_OK:
+        raise FlusiError(rc, lib.flusi_last_error(handle).decode())
+    return rc
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+# ------------------------------------------------------------- C-ABI calls
+
+def flusi_create(n, L, nu, eta, precision):
+    out = C.c_void_p()
+    Ls = (C.c_double * 3)(*L)
+    rc = lib.flusi_create(int(n[0]), int(n[1]), int(n[2]), Ls, float(nu), float(eta),
+                          int(precision), C.byref(out))
+    _check(None, rc)
+    return out
+
+
+def flusi_default_options():
+    o = Options()
+    lib.flusi_default_options(C.byref(o))
+    return o
+
+
+def flusi_set_options(h, opt: Options):
+    return _check(h, lib.flusi_set_options(h, C.byref(opt)))
+
+
+def flusi_workspace_bytes(h):
+    b = C.c_size_t()
+    _check(h, lib.flusi_workspace_bytes(h, C.byref(b)))
+    return b.value
+
+
+def flusi_bind(h, dev_ptr: int, nbytes: int, stream: int):
+    return _check(h, lib.flusi_bind(h, C.c_void_p(dev_ptr), nbytes, C.c_void_p(stream)))
+
+
+def flusi_set_state(h, u, where):
+    """u: numpy float64/float32 array (host) or an int device pointer."""
+    ptr = C.c_void_p(u) if isinstance(u, int) else C.c_void_p(u.ctypes.data)
+    return _check(h, lib.flusi_set_state(h, ptr, where))
+
+
+def flusi_set_kinematics(h, insect: Insect | None):
+    return _check(h, lib.flusi_set_kinematics(h, C.byref(insect) if insect is not None else None))
+
+
+def flusi_step(h, n):
+    return _check(h, lib.flusi_step(h, int(n)))
+
+
+def flusi_sync(h):
+    return _check(h, lib.flusi_sync(h))
+
+
+def flusi_forces(h, cap=4096):
+    rows = np.zeros((cap, FORCE_COLS))
+    count, lost = C.c_int(), C.c_longlong()
+    _check(h, lib.flusi_forces(h, _dptr(rows), cap, C.byref(count), C.byref(lost)))
+    return rows[: count.value].copy(), lost.value
+
+
+def flusi_get_state(h, out, where):
+    """out: numpy array (host) or an int device pointer; returns (t, step)."""
+    ptr = C.c_void_p(out) if isinstance(out, int) else C.c_void_p(out.ctypes.data)
+    t, step = C.c_double(), C.c_longlong()
+    _check(h, lib.flusi_get_state(h, ptr, where, C.byref(t), C.byref(step)))
+    return t.value, step.value
+
+
+def flusi_get_spectrum(h, shape):
+    nz, ny, hx = shape
+    out = np.zeros((3, nz, ny, hx, 2))
+    _check(h, lib.flusi_get_spectrum(h, _dptr(out)))
+    return out[..., 0] + 1j * out[..., 1]
+
+
+def flusi_debug_fields(h, dev_ptr: int):
+    return _check(h, lib.flusi_debug_fields(h, C.c_void_p(dev_ptr)))
+
+
+def flusi_profile_step(h, n):
+    ms = (C.c_double * 16)()
+    names = (C.c_char_p * 16)()
+    nk = C.c_int()
+    _check(h, lib.flusi_profile_step(h, int(n), ms, names, C.byref(nk)))
+    return {names[i].decode(): ms[i] for i in range(nk.value)}
+
+
+def flusi_kernels_per_step(h):
+    c = C.c_int()
+    _check(h, lib.flusi_kernels_per_step(h, C.byref(c)))
+    return c.value
+
+
+def flusi_destroy(h):
+    return lib.flusi_destroy(h)
+
+
+def flusi_last_error(h):
+    return lib.flusi_last_error(h).decode()
+
+
+# ------------------------------------------------------------ descriptors
+
+def make_insect(d: dict | None) -> Insect | None:
+    """flusi_insect from a plain descriptor dict (see workloads)."""
+    if d is None:
+        return None
+    s = Insect()
+    s.body_type = {"none": 0, "sphere": 1, "ellipsoid": 2}[d.get("body", "none")]
+    s.nwings = d.get("nwings", 0)
+    s.profile = {"cos": 0, "tanh": 1}[d.get("profile", "cos")]
+    s.c_smth = d.get("c_smth", 1.0)
+    s.x_cntr[:] = d.get("x_cntr", (0, 0, 0))
+    s.u_cntr[:] = d.get("u_cntr", (0, 0, 0))
+    s.psi, s.beta, s.gamma = d.get("body_angles", (0, 0, 0))
+    s.psi_dot, s.beta_dot, s.gamma_dot = d.get("body_rates", (0, 0, 0))
+    s.body_a, s.body_b = d.get("body_axes", (0.0, 0.0))
+    s.pivot_l[:] = d.get("pivot_l", (0, 0, 0))
+    s.pivot_r[:] = d.get("pivot_r", (0, 0, 0))
+    s.eta_stroke = d.get("eta_stroke", 0.0)
+    s.wing_c_le, s.wing_c_te, s.wing_R, s.wing_h = d.get("wing", (0, 0, 0, 0))
+    s.freq = d.get("freq", 1.0)
+    nf = 0
+    for name in ("phi", "alpha", "theta"):
+        a0, a, b = d.get("kinematics", {}).get(name, (0.0, [], []))
+        setattr(s, name + "_a0", a0)
+        for i, v in enumerate(a):
+            getattr(s, name + "_a")[i] = v
+        for i, v in enumerate(b):
+            getattr(s, name + "_b")[i] = v
+        nf = max(nf, len(a), len(b))
+    s.nfourier = nf
+    return s
+
+
+def make_options(cfg: dict) -> Options:
+    o = flusi_default_options()
+    o.cfl = cfg.get("cfl", 0.1)
+    o.dt_fixed = cfg.get("dt_fixed", 0.0)
+    o.dt_max = cfg.get("dt_max", 0.0)
+    o.u_inf[:] = cfg.get("u_inf", (0.0, 0.0, 0.0))
+    o.mean_mode = 1 if cfg.get("mean_mode", "fixed") == "free" else 0
+    o.dealias_strict = int(cfg.get("dealias_strict", 0))
+    o.force_ring = int(cfg.get("force_ring", 4096))
+    o.use_graph = int(cfg.get("use_graph", 1))
+    return o
+
+
+class Solver:
+    """A bound handle: torch owns the workspace and the stream."""
+
+    def __init__(self, cfg: dict, insect: dict | None = None, precision: str = "fp64",
+                 device: int = 0, stream=None):
+        import torch
+        self.torch = torch
+        self.cfg = cfg
+        self.prec = FLUSI_FP64 if precision == "fp64" else FLUSI_FP32
+        self.n = tuple(cfg["n"])
+        self.h = flusi_create(self.n, cfg["L"], cfg["nu"], cfg["eta"], self.prec)
+        flusi_set_options(self.h, make_options(cfg))
+        self.device = torch.device("cuda", device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
+        nbytes = flusi_workspace_bytes(self.h)
+        self.ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        base = self.ws.data_ptr()
+        aligned = (base + 255) // 256 * 256
+        flusi_bind(self.h, aligned, nbytes, self.stream.cuda_stream)
+        self.insect = make_insect(insect)
+        if self.insect is not None:
+            flusi_set_kinematics(self.h, self.insect)
+
+    def set_state(self, u):
+        """u: numpy [3][nz][ny][nx] (float64 or float32) or a torch CUDA tensor
+        in the solver's precision."""
+        if isinstance(u, np.ndarray):
+            where = FLUSI_HOST_FP64 if u.dtype == np.float64 else FLUSI_HOST_FP32
+            flusi_set_state(self.h, np.ascontiguousarray(u), where)
+        else:
+            self.stream.wait_stream(self.torch.cuda.current_stream(self.device))
+            flusi_set_state(self.h, u.data_ptr(), FLUSI_DEVICE)
+
+    def step(self, n=1):
+        flusi_step(self.h, n)
+
+    def sync(self):
+        flusi_sync(self.h)
+
+    def forces(self, cap=4096):
+        return flusi_forces(self.h, cap)
+
+    def get_state(self, dtype=np.float64):
+        nx, ny, nz = self.n
+        out = np.zeros((3, nz, ny, nx), dtype)
+        t, step = flusi_get_state(self.h, out, FLUSI_HOST_FP64 if dtype == np.float64 else FLUSI_HOST_FP32)
+        return out, t, step
+
+    def get_state_device(self, out):
+        return flusi_get_state(self.h, out.data_ptr(), FLUSI_DEVICE)
+
+    def get_spectrum(self):
+        nx, ny, nz = self.n
+        return flusi_get_spectrum(self.h, (nz, ny, nx // 2 + 1))
+
+    def debug_fields(self):
+        torch = self.torch
+        nx, ny, nz = self.n
+        dt = torch.float64 if self.prec == FLUSI_FP64 else torch.float32
+        out = torch.empty((14, nz, ny, nx), dtype=dt, device=self.device)
+        flusi_debug_fields(self.h, out.data_ptr())
+        self.stream.synchronize()
+        return out
+
+    def profile(self, n=3):
+        return flusi_profile_step(self.h, n)
+
+    def close(self):
+        if self.h:
+            flusi_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,131 @@
+// Shared device types of libflusi: complex arithmetic, the grid geometry
+// passed to every kernel, the per-step frame block written by the kinematics
+// kernel, and the device-side step state.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace flusi {
+
+template <typename T> struct cplx_of;
+template <> struct cplx_of<float> { using type = float2; };
+template <> struct cplx_of<double> { using type = double2; };
+template <typename T> using cplx = typename cplx_of<T>::type;
+
+template <typename T> __host__ __device__ __forceinline__ cplx<T> mkc(T r, T i)
+{
+    cplx<T> c;
+    c.x = r;
+    c.y = i;
+    return c;
+}
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { a.x += b.x; a.y += b.y; return a; }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { a.x -= b.x; a.y -= b.y; return a; }
+template <typename C> __device__ __forceinline__ C cconj(C a) { a.y = -a.y; return a; }
+// a * i
+template <typename C> __device__ __forceinline__ C cmuli(C a) { C r; r.x = -a.y; r.y = a.x; return r; }
+// a * (-i)
+template <typename C> __device__ __forceinline__ C cmulmi(C a) { C r; r.x = a.y; r.y = -a.x; return r; }
+template <typename C, typename S> __device__ __forceinline__ C cscale(C a, S s) { a.x *= s; a.y *= s; return a; }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b)
+{
+    C r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+
+// Largest FFT length along any axis (the x transform runs at nx/2).
+constexpr int kMaxN = 1024;
+constexpr int kMaxStages = 10;
+constexpr int kNumSums = 40;     // per-CTA partial sums of the physical pass
+constexpr int kRowCols = 22;     // one force row
+
+// Partial-sum slots: per colour c (0 body, 1 left, 2 right) 12 doubles:
+// [0..2] sum chi (u - u_s), [3..5] sum r x chi (u - u_s),
+// [6..8] sum chi u_s, [9..11] sum r x chi u_s, with r = x - x_ref the arm
+// from the body centre (body) or the wing pivot (wings); all without dV.
+constexpr int kSumEkin = 36;     // sum |u|^2
+constexpr int kSumUmax2 = 37;    // max |u|^2
+constexpr int kSumBad = 38;      // 1 if a non-finite value was met
+
+// Radix plan of one 1-D transform (mixed radix 2, 3, 4, 8; in-place
+// decimation in frequency / time, see fft.cuh).
+struct FftPlan {
+    int n;                   // transform length
+    int nst;                 // number of stages
+    int radix[kMaxStages];
+    int m[kMaxStages];       // butterfly span: rows b*ls + k + t*m
+    int mshift[kMaxStages];  // log2(m) when m is a power of two, else -1
+    int ls[kMaxStages];      // block length radix*m
+    int tstep[kMaxStages];   // twiddle index step (n/ls times the table stride)
+};
+
+// Grid and spectral truncation, shared by all kernels.
+struct Geom {
+    int nx, ny, nz;
+    int Kx, Ky, Kz;          // 2/3-rule cutoffs: kept |m| <= K
+    int Mx, My, Mz;          // retained modes: Kx + 1, 2 Ky + 1, 2 Kz + 1
+    int Mxp;                 // Mx padded to a multiple of 4 (row pitch of spectral rows)
+    double Lx, Ly, Lz;
+    double dx, dy, dz;
+    double nu, eta;
+};
+
+// Per-step geometry of the insect, written by the kinematics kernel (FP64).
+struct Frame {
+    double t;
+    double xc[3];            // body centre (global)
+    double uc[3];            // centre velocity
+    double Ob[3];            // body angular velocity (global frame)
+    double Mb[9];            // global -> body frame (row major)
+    double Mw[2][9];         // global -> wing frame, per wing
+    double pv[2][3];         // wing pivots (global)
+    double Ow[2][3];         // wing angular velocity relative to the body (global frame)
+    double box[3][6];        // bounding box per part: xmin xmax ymin ymax zmin zmax
+    int active[3];           // part present
+    int pad;
+};
+
+// Insect parameters needed per grid point (set with the kinematics).
+struct Shape {
+    int body_type;           // 0 none, 1 sphere, 2 ellipsoid
+    int nwings;
+    int profile;             // 0 cosine layer, 1 tanh layer
+    int pad;
+    double h;                // smoothing half-width
+    double body_a, body_b;
+    double c_le, c_te, R, ht;
+};
+
+// Device-resident step state (persists across steps).
+struct StepState {
+    double t;
+    double dt_prev;
+    long long n;             // steps taken
+    int status;              // flusi_status of the first device-side failure
+    int pad;
+    double Is_prev[3][3];
+    double Js_prev[3][3];
+};
+
+// Coefficients of the current step, written by the scalar kernel and read by
+// the spectral update.
+struct StepCoef {
+    double dt;
+    double c_now;            // dt (1 + r/2), or dt on the first step
+    double c_old;            // dt r/2, or 0 on the first step
+    long long n;
+    int first;
+    int skip;                // 1 when the step is abandoned (status set)
+};
+
+__host__ __device__ inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+// Signed mode of a stored spectral index j in [0, M) with M = 2K + 1.
+__host__ __device__ __forceinline__ int mode_of(int j, int K) { return j <= K ? j : j - (2 * K + 1); }
+// FFT frequency slot of a stored index j for a length-n transform.
+__host__ __device__ __forceinline__ int slot_of(int j, int K, int n) { return j <= K ? j : n - (2 * K + 1) + j; }
+
+}  // namespace flusi

@@ -1,0 +1,175 @@
+// Batched 1-D FFT in shared memory: mixed-radix (2, 3, 4, 8) in-place
+// Cooley-Tukey transforms of C columns of length n held as buf[row*ld + col].
+//
+// Radices r_0..r_{S-1} (plan order).  Stage s works on blocks of length
+// Ls = n / (r_0 ... r_{s-1}); a butterfly (block b, k < m_s = Ls / r_s) owns
+// rows b Ls + k + t m_s, t < r_s, so each butterfly reads and writes its own
+// rows and a stage needs only one barrier.
+//   fft_dif: natural order in -> digit-reversed out.  Stage s = 0..S-1:
+//            R-point DFT, then output q times w_Ls^{k q}.
+//   fft_dit: digit-reversed in -> natural order out.  Stage s = S-1..0:
+//            input t times w_Ls^{k t}, then the R-point DFT.
+// (fft_dit is the transpose of fft_dif; the DFT matrix is symmetric.)
+// Frequency f = d_0 + r_0 (d_1 + r_1 (...)) sits at row pos[f] = sum_s d_s m_s.
+// w = exp(-2 pi i / n) forward, exp(+2 pi i / n) inverse; unnormalized.
+// The twiddle w_Ls^{k t} is tw[k t tstep_s], tstep_s = (n / Ls) * (table stride).
+//
+// Threads own one column (col = tid % C) and stride over its butterflies
+// (P = blockDim / C threads per column).
+#pragma once
+
+#include "common.cuh"
+
+namespace flusi {
+
+// R-point DFT in registers: forward uses exp(-2 pi i/R), inverse exp(+2 pi i/R).
+template <typename T, int R, bool INV> struct Dft;
+
+template <typename T, bool INV> struct Dft<T, 2, INV> {
+    __device__ __forceinline__ static void run(cplx<T>* v)
+    {
+        cplx<T> a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    }
+};
+
+template <typename T, bool INV> struct Dft<T, 4, INV> {
+    __device__ __forceinline__ static void run(cplx<T>* v)
+    {
+        cplx<T> a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]);
+        cplx<T> a2 = cadd(v[1], v[3]);
+        cplx<T> d = csub(v[1], v[3]);
+        cplx<T> a3 = INV ? cmuli(d) : cmulmi(d);
+        v[0] = cadd(a0, a2);
+        v[2] = csub(a0, a2);
+        v[1] = cadd(a1, a3);
+        v[3] = csub(a1, a3);
+    }
+};
+
+template <typename T, bool INV> struct Dft<T, 8, INV> {
+    __device__ __forceinline__ static void run(cplx<T>* v)
+    {
+        // even and odd 4-point transforms, recombined with w8^q
+        cplx<T> e[4] = {v[0], v[2], v[4], v[6]};
+        cplx<T> o[4] = {v[1], v[3], v[5], v[7]};
+        Dft<T, 4, INV>::run(e);
+        Dft<T, 4, INV>::run(o);
+        const T r = T(0.70710678118654752440084436210484903928);
+        // w8 = (1 -+ i)/sqrt2 ; w8^2 = -+i ; w8^3 = (-1 -+ i)/sqrt2
+        cplx<T> o1, o2, o3;
+        if (INV) {
+            o1 = mkc<T>(r * (o[1].x - o[1].y), r * (o[1].x + o[1].y));
+            o2 = cmuli(o[2]);
+            o3 = mkc<T>(-r * (o[3].x + o[3].y), r * (o[3].x - o[3].y));
+        } else {
+            o1 = mkc<T>(r * (o[1].x + o[1].y), r * (o[1].y - o[1].x));
+            o2 = cmulmi(o[2]);
+            o3 = mkc<T>(r * (o[3].y - o[3].x), -r * (o[3].x + o[3].y));
+        }
+        v[0] = cadd(e[0], o[0]);
+        v[4] = csub(e[0], o[0]);
+        v[1] = cadd(e[1], o1);
+        v[5] = csub(e[1], o1);
+        v[2] = cadd(e[2], o2);
+        v[6] = csub(e[2], o2);
+        v[3] = cadd(e[3], o3);
+        v[7] = csub(e[3], o3);
+    }
+};
+
+template <typename T, bool INV> struct Dft<T, 3, INV> {
+    __device__ __forceinline__ static void run(cplx<T>* v)
+    {
+        // w3 = -1/2 -+ i sqrt(3)/2
+        const T s = T(0.86602540378443864676372317075293618347);
+        cplx<T> t1 = cadd(v[1], v[2]);
+        cplx<T> t2 = csub(v[0], cscale(t1, T(0.5)));
+        cplx<T> d = cscale(csub(v[1], v[2]), s);
+        cplx<T> t3 = INV ? cmuli(d) : cmulmi(d);
+        v[0] = cadd(v[0], t1);
+        v[1] = cadd(t2, t3);
+        v[2] = csub(t2, t3);
+    }
+};
+
+template <typename T, int R, bool INV, bool DIF>
+__device__ __forceinline__ void fft_stage(cplx<T>* buf, int ld, int col, int jt, int P, int nbf,
+                                          int m, int msh, int ls, int tstep, const cplx<T>* tw)
+{
+#pragma unroll 2
+    for (int j = jt; j < nbf; j += P) {
+        const int b = msh >= 0 ? (j >> msh) : (j / m);
+        const int k = j - b * m;
+        cplx<T>* p = buf + (b * ls + k) * ld + col;
+        const int step = m * ld;
+        cplx<T> v[R];
+#pragma unroll
+        for (int t = 0; t < R; ++t) v[t] = p[t * step];
+        if (DIF) Dft<T, R, INV>::run(v);
+        if (k != 0) {
+#pragma unroll
+            for (int t = 1; t < R; ++t) {
+                cplx<T> w = tw[k * t * tstep];
+                if (INV) w.y = -w.y;
+                v[t] = cmul(v[t], w);
+            }
+        }
+        if (!DIF) Dft<T, R, INV>::run(v);
+#pragma unroll
+        for (int t = 0; t < R; ++t) p[t * step] = v[t];
+    }
+    __syncthreads();
+}
+
+template <typename T, bool INV, bool DIF>
+__device__ __forceinline__ void fft_run(cplx<T>* buf, int C, int ld, const FftPlan& plan,
+                                        const cplx<T>* tw)
+{
+    const int P = blockDim.x / C;
+    const int col = threadIdx.x % C;
+    const int jt = threadIdx.x / C;
+    for (int i = 0; i < plan.nst; ++i) {
+        const int s = DIF ? i : plan.nst - 1 - i;
+        const int R = plan.radix[s];
+        const int nbf = plan.n / R;
+        const int m = plan.m[s], msh = plan.mshift[s], ls = plan.ls[s], ts = plan.tstep[s];
+        switch (R) {
+        case 8: fft_stage<T, 8, INV, DIF>(buf, ld, col, jt, P, nbf, m, msh, ls, ts, tw); break;
+        case 4: fft_stage<T, 4, INV, DIF>(buf, ld, col, jt, P, nbf, m, msh, ls, ts, tw); break;
+        case 3: fft_stage<T, 3, INV, DIF>(buf, ld, col, jt, P, nbf, m, msh, ls, ts, tw); break;
+        default: fft_stage<T, 2, INV, DIF>(buf, ld, col, jt, P, nbf, m, msh, ls, ts, tw); break;
+        }
+    }
+}
+
+// Natural order in, digit-reversed out (row pos[f] holds frequency/point f).
+// Columns 0..C-1, C must divide blockDim.x; all threads must call.
+template <typename T, bool INV>
+__device__ void fft_dif(cplx<T>* buf, int C, int ld, const FftPlan& plan, const cplx<T>* tw)
+{
+    fft_run<T, INV, true>(buf, C, ld, plan, tw);
+}
+
+// Digit-reversed in (row pos[f] holds f), natural order out.
+template <typename T, bool INV>
+__device__ void fft_dit(cplx<T>* buf, int C, int ld, const FftPlan& plan, const cplx<T>* tw)
+{
+    fft_run<T, INV, false>(buf, C, ld, plan, tw);
+}
+
+// Copy the twiddle table (FP64, global; ntw entries exp(-2 pi i j / ntw))
+// and the n-entry digit-reversal table into shared memory.
+template <typename T>
+__device__ __forceinline__ void load_tables(cplx<T>* dst, int* pos_dst, const double2* src,
+                                            const int* pos_src, int ntw, int n)
+{
+    for (int i = threadIdx.x; i < ntw; i += blockDim.x) {
+        double2 w = src[i];
+        dst[i] = mkc<T>(T(w.x), T(w.y));
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) pos_dst[i] = pos_src[i];
+}
+
+}  // namespace flusi

@@ -1,0 +1,703 @@
+// C-ABI of libflusi (include/flusi.h): handle, workspace layout, FFT plans
+// and twiddle tables, the kernel sequence of one step (Algorithm 1 steps
+// a-e) and its capture into a CUDA graph, and the host<->device marshalling
+// of states and force rows.  Host code only; all arithmetic of the step runs
+// in the kernels.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/flusi.h"
+#include "kernels.cuh"
+
+using namespace flusi;
+
+struct flusi_s {
+    int nx = 0, ny = 0, nz = 0, prec = 0;
+    double L[3] = {0, 0, 0}, nu = 0, eta = 0;
+    flusi_options opt{};
+    flusi_insect ins{};
+    int have_ins = 0;
+    Geom g{};
+    FftPlan px{}, py{}, pz{};
+    // workspace
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    cudaStream_t stream = nullptr;
+    int bound = 0;
+    size_t oU = 0, oH = 0, oW = 0, otx = 0, oty = 0, otz = 0, opx = 0, opy = 0, opz = 0,
+           oframe = 0, oins = 0, ostate = 0, ocoef = 0, oetab = 0, opart = 0, orows = 0, total = 0;
+    int part_cap = 0, xgrid = 0;
+    // run state
+    int has_state = 0, poisoned = 0;
+    long long rows_read = 0;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int graph_ok = 0;
+    std::string err;
+};
+
+namespace {
+
+std::string g_create_err;
+
+int fail(flusi_t h, int code, const std::string& msg)
+{
+    if (h) h->err = msg;
+    else g_create_err = msg;
+    return code;
+}
+
+int cuda_fail(flusi_t h, cudaError_t e, const char* what)
+{
+    return fail(h, FLUSI_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, what); \
+    } while (0)
+
+bool smooth_size(int n)
+{
+    if (n < 8 || n > kMaxN) return false;
+    while (n % 2 == 0) n /= 2;
+    while (n % 3 == 0) n /= 3;
+    return n == 1;
+}
+
+// Radix order: 3s first (their stages divide), then 8s, then a 4 or 4*4 or 2.
+// `tws` is the stride of the twiddle table the transform reads (its table has
+// n*tws entries), folded into the per-stage twiddle steps.
+FftPlan make_plan(int n, int tws)
+{
+    FftPlan p{};
+    p.n = n;
+    std::vector<int> r;
+    int m = n;
+    while (m % 3 == 0) { r.push_back(3); m /= 3; }
+    int a = 0;
+    while (m % 2 == 0) { ++a; m /= 2; }
+    int q = a / 3, rem = a % 3;
+    if (rem == 1 && q >= 1) { q -= 1; rem = 4; }
+    for (int i = 0; i < q; ++i) r.push_back(8);
+    if (rem == 2) r.push_back(4);
+    if (rem == 1) r.push_back(2);
+    if (rem == 4) { r.push_back(4); r.push_back(4); }
+    p.nst = (int)r.size();
+    int Ls = n;
+    for (int s = 0; s < p.nst; ++s) {
+        p.radix[s] = r[s];
+        p.ls[s] = Ls;
+        p.m[s] = Ls / r[s];
+        p.mshift[s] = (p.m[s] & (p.m[s] - 1)) == 0 ? __builtin_ctz(p.m[s]) : -1;
+        p.tstep[s] = (n / Ls) * tws;
+        Ls = p.m[s];
+    }
+    return p;
+}
+
+// Row of frequency f after the in-place decimation-in-frequency transform:
+// f = d_0 + r_0 (d_1 + r_1 (...))  ->  sum_s d_s m_s.
+std::vector<int> digit_reversal(const FftPlan& p)
+{
+    std::vector<int> pos(p.n);
+    for (int f = 0; f < p.n; ++f) {
+        int ff = f, at = 0;
+        for (int s = 0; s < p.nst; ++s) {
+            at += (ff % p.radix[s]) * p.m[s];
+            ff /= p.radix[s];
+        }
+        pos[f] = at;
+    }
+    return pos;
+}
+
+// exp(-2 pi i j / n), j < n, from long double sines and cosines.
+std::vector<double2> twiddles(int n)
+{
+    std::vector<double2> t(n);
+    const long double two_pi = 6.283185307179586476925286766559005768L;
+    for (int j = 0; j < n; ++j) {
+        long double a = two_pi * (long double)j / (long double)n;
+        t[j].x = (double)cosl(a);
+        t[j].y = -(double)sinl(a);
+    }
+    return t;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+int cutoff(int n, int strict) { return (strict && n % 3 == 0) ? n / 3 - 1 : n / 3; }
+
+void layout(flusi_t h)
+{
+    Geom& g = h->g;
+    const int strict = h->opt.dealias_strict;
+    g.nx = h->nx;
+    g.ny = h->ny;
+    g.nz = h->nz;
+    g.Kx = cutoff(h->nx, strict);
+    g.Ky = cutoff(h->ny, strict);
+    g.Kz = cutoff(h->nz, strict);
+    g.Mx = g.Kx + 1;
+    g.My = 2 * g.Ky + 1;
+    g.Mz = 2 * g.Kz + 1;
+    g.Mxp = (g.Mx + 3) / 4 * 4;
+    g.Lx = h->L[0];
+    g.Ly = h->L[1];
+    g.Lz = h->L[2];
+    g.dx = h->L[0] / h->nx;
+    g.dy = h->L[1] / h->ny;
+    g.dz = h->L[2] / h->nz;
+    g.nu = h->nu;
+    g.eta = h->eta;
+
+    const size_t cs = h->prec == FLUSI_FP64 ? 16 : 8;
+    const size_t spec = (size_t)3 * g.Mz * g.My * g.Mxp * cs;
+    const size_t work = (size_t)6 * g.nz * g.ny * g.Mxp * cs;
+    const int rb_min = 1;
+    h->part_cap = std::min(8192, (g.nz * g.ny + rb_min - 1) / rb_min);
+    size_t o = 0;
+    h->oU = o; o = align256(o + spec);
+    h->oH = o; o = align256(o + spec);
+    h->oW = o; o = align256(o + work);
+    h->otx = o; o = align256(o + sizeof(double2) * g.nx);
+    h->oty = o; o = align256(o + sizeof(double2) * g.ny);
+    h->otz = o; o = align256(o + sizeof(double2) * g.nz);
+    h->opx = o; o = align256(o + sizeof(int) * (g.nx / 2));
+    h->opy = o; o = align256(o + sizeof(int) * g.ny);
+    h->opz = o; o = align256(o + sizeof(int) * g.nz);
+    h->oframe = o; o = align256(o + sizeof(Frame));
+    h->oins = o; o = align256(o + sizeof(flusi_insect));
+    h->ostate = o; o = align256(o + sizeof(StepState));
+    h->ocoef = o; o = align256(o + sizeof(StepCoef));
+    h->oetab = o; o = align256(o + sizeof(double) * 2 * (g.Mx + g.My + g.Mz));
+    h->opart = o; o = align256(o + sizeof(double) * kNumSums * h->part_cap);
+    h->orows = o; o = align256(o + sizeof(double) * kRowCols * h->opt.force_ring);
+    h->total = o;
+    h->px = make_plan(h->nx / 2, 2);
+    h->py = make_plan(h->ny, 1);
+    h->pz = make_plan(h->nz, 1);
+}
+
+template <typename P> P* at(flusi_t h, size_t off) { return reinterpret_cast<P*>(h->ws + off); }
+
+Shape make_shape(flusi_t h)
+{
+    Shape s{};
+    if (!h->have_ins) return s;
+    const flusi_insect& I = h->ins;
+    s.body_type = I.body_type;
+    s.nwings = I.nwings;
+    s.profile = I.profile;
+    double d = std::max(h->g.dx, std::max(h->g.dy, h->g.dz));
+    s.h = I.c_smth * d;
+    s.body_a = I.body_a;
+    s.body_b = I.body_b;
+    s.c_le = I.wing_c_le;
+    s.c_te = I.wing_c_te;
+    s.R = I.wing_R;
+    s.ht = I.wing_h;
+    return s;
+}
+
+// Half-width used to grow the bounding boxes: the cosine layer vanishes
+// beyond h; the tanh layer never does, so its boxes cover everything.
+double box_margin(flusi_t h)
+{
+    Shape s = make_shape(h);
+    return s.profile == 1 ? 1e300 : s.h;
+}
+
+const char* kKernelNames[] = {"kinematics", "zinv_curl", "yinv", "xpass_phys", "scalars", "yfwd",
+                              "zfwd_update"};
+constexpr int kStepKernels = 7;
+
+// Enqueue one step; with `ev` (kStepKernels + 1 events) records an event
+// before each kernel and after the last.
+cudaError_t enqueue_step(flusi_t h, cudaStream_t s, cudaEvent_t* ev)
+{
+    const Geom& g = h->g;
+    const int fp64 = h->prec == FLUSI_FP64;
+    StepState* st = at<StepState>(h, h->ostate);
+    void* W = h->ws + h->oW;
+    const double2* tx = at<double2>(h, h->otx);
+    const double2* ty = at<double2>(h, h->oty);
+    const double2* tz = at<double2>(h, h->otz);
+    cudaError_t e;
+    int k = 0;
+    auto mark = [&]() {
+        if (ev) cudaEventRecord(ev[k], s);
+        ++k;
+    };
+    mark();
+    k_kinematics<<<1, 32, 0, s>>>(at<flusi_insect>(h, h->oins), st, at<Frame>(h, h->oframe), box_margin(h));
+    if ((e = cudaGetLastError())) return e;
+    mark();
+    if ((e = launch_zinv(fp64, h->ws + h->oU, W, g, h->pz, tz, at<int>(h, h->opz), 6, st, s))) return e;
+    mark();
+    if ((e = launch_ypass(fp64, true, W, g, h->py, ty, at<int>(h, h->opy), 6, st, s))) return e;
+    mark();
+    XExtra xe{};
+    xe.frame = at<Frame>(h, h->oframe);
+    xe.shape = make_shape(h);
+    xe.part = at<double>(h, h->opart);
+    xe.comp0 = 0;
+    if ((e = launch_xpass(fp64, XP_PHYS, W, g, h->px, tx, at<int>(h, h->opx), xe, st, s))) return e;
+    mark();
+    double3 opts = make_double3(h->opt.cfl, h->opt.dt_fixed, h->opt.dt_max);
+    k_scalars<<<1, 256, 0, s>>>(g, at<double>(h, h->opart), h->xgrid, st, at<StepCoef>(h, h->ocoef),
+                                at<double>(h, h->orows), h->opt.force_ring, at<double>(h, h->oetab), opts);
+    if ((e = cudaGetLastError())) return e;
+    mark();
+    if ((e = launch_ypass(fp64, false, W, g, h->py, ty, at<int>(h, h->opy), 3, st, s))) return e;
+    mark();
+    ZfwdExtra ze{};
+    ze.coef = at<StepCoef>(h, h->ocoef);
+    ze.etab = at<double>(h, h->oetab);
+    for (int i = 0; i < 3; ++i) ze.u_inf[i] = h->opt.u_inf[i];
+    ze.mean_free = h->opt.mean_mode;
+    if ((e = launch_zfwd(fp64, 0, W, h->ws + h->oU, h->ws + h->oH, g, h->pz, tz, at<int>(h, h->opz), ze, st, s))) return e;
+    mark();
+    return cudaSuccess;
+}
+
+int check_ready(flusi_t h, bool need_state)
+{
+    if (!h) return FLUSI_EINVAL;
+    if (!h->bound) return fail(h, FLUSI_ESTATE, "no workspace bound (flusi_bind)");
+    if (need_state && !h->has_state) return fail(h, FLUSI_ESTATE, "no state set (flusi_set_state)");
+    return FLUSI_OK;
+}
+
+void drop_graph(flusi_t h)
+{
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+    h->graph_ok = 0;
+}
+
+int read_status(flusi_t h, StepState* out)
+{
+    StepState st;
+    CK(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    CK(cudaMemcpy(&st, h->ws + h->ostate, sizeof st, cudaMemcpyDeviceToHost), "read step state");
+    if (out) *out = st;
+    if (st.status != 0) {
+        h->poisoned = 1;
+        return fail(h, st.status, st.status == FLUSI_ENONFINITE
+                                      ? "non-finite velocity or nonlinear term on the device"
+                                      : "device-side failure");
+    }
+    return FLUSI_OK;
+}
+
+bool same_shape(const Shape& a, const Shape& b)
+{
+    return a.body_type == b.body_type && a.nwings == b.nwings && a.profile == b.profile &&
+           a.h == b.h && a.body_a == b.body_a && a.body_b == b.body_b && a.c_le == b.c_le &&
+           a.c_te == b.c_te && a.R == b.R && a.ht == b.ht;
+}
+
+size_t real_size(int where, int prec)
+{
+    if (where == FLUSI_HOST_FP64) return 8;
+    if (where == FLUSI_HOST_FP32) return 4;
+    return prec == FLUSI_FP64 ? 8 : 4;
+}
+
+}  // namespace
+
+extern "C" {
+
+void flusi_default_options(flusi_options* o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->cfl = 0.1;
+    o->force_ring = 4096;
+    o->use_graph = 1;
+}
+
+int flusi_create(int nx, int ny, int nz, const double L[3], double nu, double eta, int precision,
+                 flusi_t* out)
+{
+    if (!out) return fail(nullptr, FLUSI_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!smooth_size(nx) || !smooth_size(ny) || !smooth_size(nz) || nx % 2 != 0)
+        return fail(nullptr, FLUSI_EINVAL, "each n must be 2^a 3^b in [8, 1024], nx even");
+    if (!L || !(L[0] > 0) || !(L[1] > 0) || !(L[2] > 0)) return fail(nullptr, FLUSI_EINVAL, "box sides must be > 0");
+    if (!(nu >= 0) || !(eta > 0)) return fail(nullptr, FLUSI_EINVAL, "need nu >= 0 and eta > 0");
+    if (precision != FLUSI_FP64 && precision != FLUSI_FP32) return fail(nullptr, FLUSI_EINVAL, "bad precision");
+    flusi_t h = new (std::nothrow) flusi_s();
+    if (!h) return fail(nullptr, FLUSI_ENOMEM, "host allocation failed");
+    h->nx = nx;
+    h->ny = ny;
+    h->nz = nz;
+    h->prec = precision;
+    for (int i = 0; i < 3; ++i) h->L[i] = L[i];
+    h->nu = nu;
+    h->eta = eta;
+    flusi_default_options(&h->opt);
+    layout(h);
+    *out = h;
+    return FLUSI_OK;
+}
+
+int flusi_set_options(flusi_t h, const flusi_options* o)
+{
+    if (!h || !o) return fail(h, FLUSI_EINVAL, "NULL argument");
+    if (!(o->cfl > 0) || o->dt_fixed < 0 || o->dt_max < 0 || o->force_ring < 1 ||
+        (o->mean_mode != 0 && o->mean_mode != 1) || (o->dealias_strict != 0 && o->dealias_strict != 1))
+        return fail(h, FLUSI_EINVAL, "bad option value");
+    if (h->bound && (o->force_ring != h->opt.force_ring || o->dealias_strict != h->opt.dealias_strict))
+        return fail(h, FLUSI_EINVAL, "force_ring and dealias_strict cannot change after flusi_bind");
+    h->opt = *o;
+    layout(h);
+    drop_graph(h);
+    return FLUSI_OK;
+}
+
+int flusi_workspace_bytes(flusi_t h, size_t* bytes)
+{
+    if (!h || !bytes) return fail(h, FLUSI_EINVAL, "NULL argument");
+    *bytes = h->total;
+    return FLUSI_OK;
+}
+
+int flusi_bind(flusi_t h, void* ws, size_t bytes, void* stream)
+{
+    if (!h || !ws) return fail(h, FLUSI_EINVAL, "NULL argument");
+    if ((reinterpret_cast<uintptr_t>(ws) & 255) != 0) return fail(h, FLUSI_EINVAL, "workspace not 256-byte aligned");
+    if (bytes < h->total) return fail(h, FLUSI_ENOMEM, "workspace smaller than flusi_workspace_bytes");
+    static int configured = 0;
+    if (!configured) {
+        CK(configure_ypass(), "configure y pass");
+        CK(configure_zpass(), "configure z pass");
+        CK(configure_xpass(), "configure x pass");
+        configured = 1;
+    }
+    drop_graph(h);
+    h->ws = static_cast<char*>(ws);
+    h->ws_bytes = bytes;
+    h->stream = static_cast<cudaStream_t>(stream);
+    h->xgrid = xpass_grid(h->prec == FLUSI_FP64, h->g);
+    if (h->xgrid > h->part_cap) h->xgrid = h->part_cap;
+    CK(cudaMemsetAsync(h->ws, 0, h->total, h->stream), "clear workspace");
+    auto tx = twiddles(h->nx), ty = twiddles(h->ny), tz = twiddles(h->nz);
+    auto px = digit_reversal(h->px), py = digit_reversal(h->py), pz = digit_reversal(h->pz);
+    CK(cudaMemcpyAsync(h->ws + h->otx, tx.data(), sizeof(double2) * tx.size(), cudaMemcpyHostToDevice, h->stream), "twiddles");
+    CK(cudaMemcpyAsync(h->ws + h->oty, ty.data(), sizeof(double2) * ty.size(), cudaMemcpyHostToDevice, h->stream), "twiddles");
+    CK(cudaMemcpyAsync(h->ws + h->otz, tz.data(), sizeof(double2) * tz.size(), cudaMemcpyHostToDevice, h->stream), "twiddles");
+    CK(cudaMemcpyAsync(h->ws + h->opx, px.data(), sizeof(int) * px.size(), cudaMemcpyHostToDevice, h->stream), "digit reversal");
+    CK(cudaMemcpyAsync(h->ws + h->opy, py.data(), sizeof(int) * py.size(), cudaMemcpyHostToDevice, h->stream), "digit reversal");
+    CK(cudaMemcpyAsync(h->ws + h->opz, pz.data(), sizeof(int) * pz.size(), cudaMemcpyHostToDevice, h->stream), "digit reversal");
+    // the host tables must outlive the asynchronous copies
+    CK(cudaStreamSynchronize(h->stream), "bind tables");
+    if (h->have_ins)
+        CK(cudaMemcpyAsync(h->ws + h->oins, &h->ins, sizeof h->ins, cudaMemcpyHostToDevice, h->stream), "insect");
+    CK(cudaStreamSynchronize(h->stream), "bind");
+    if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking), "capture stream");
+    h->bound = 1;
+    h->has_state = 0;
+    return FLUSI_OK;
+}
+
+int flusi_set_kinematics(flusi_t h, const flusi_insect* ins)
+{
+    if (!h) return FLUSI_EINVAL;
+    const Shape before = make_shape(h);
+    if (ins) {
+        if (ins->body_type < 0 || ins->body_type > 2 || ins->nwings < 0 || ins->nwings > 2 ||
+            ins->profile < 0 || ins->profile > 1 || ins->nfourier < 0 ||
+            ins->nfourier > FLUSI_MAX_FOURIER || !(ins->c_smth > 0) ||
+            (ins->body_type == 1 && !(ins->body_a > 0)) ||
+            (ins->body_type == 2 && !(ins->body_a > 0 && ins->body_b > 0)))
+            return fail(h, FLUSI_EINVAL, "bad insect descriptor");
+        h->ins = *ins;
+        h->have_ins = 1;
+    } else {
+        std::memset(&h->ins, 0, sizeof h->ins);
+        h->have_ins = 0;
+    }
+    // the step kernels read the descriptor from device memory in stream order;
+    // only the mask shape is baked into the captured kernel arguments
+    if (h->bound)
+        CK(cudaMemcpyAsync(h->ws + h->oins, &h->ins, sizeof h->ins, cudaMemcpyHostToDevice, h->stream), "insect");
+    if (!same_shape(before, make_shape(h))) drop_graph(h);
+    return FLUSI_OK;
+}
+
+
+int flusi_set_state(flusi_t h, const void* u, int where)
+{
+    int rc = check_ready(h, false);
+    if (rc) return rc;
+    if (!u) return fail(h, FLUSI_EINVAL, "u is NULL");
+    if (where < FLUSI_HOST_FP64 || where > FLUSI_DEVICE) return fail(h, FLUSI_EINVAL, "bad `where`");
+    const Geom& g = h->g;
+    const int fp64 = h->prec == FLUSI_FP64;
+    const size_t N = (size_t)g.nx * g.ny * g.nz;
+    void* W = h->ws + h->oW;
+    const double2* tx = at<double2>(h, h->otx);
+    cudaStream_t s = h->stream;
+    CK(cudaStreamSynchronize(s), "sync before set_state");
+    k_reset_state<<<1, 1, 0, s>>>(at<StepState>(h, h->ostate), at<StepCoef>(h, h->ocoef));
+    CK(cudaGetLastError(), "reset");
+    XExtra xe{};
+    xe.cstride = (long long)N;
+    if (where == FLUSI_DEVICE) {
+        xe.rin = u;
+        xe.real_fp64 = fp64;
+        xe.ncomp = 3;
+        xe.comp0 = 0;
+        CK(launch_xpass(fp64, XP_R2C, W, g, h->px, tx, at<int>(h, h->opx), xe, nullptr, s), "x r2c");
+    } else {
+        const size_t es = real_size(where, h->prec);
+        char* stage = h->ws + h->oW + (size_t)3 * g.nz * g.ny * g.Mxp * (fp64 ? 16 : 8);
+        for (int c = 0; c < 3; ++c) {
+            CK(cudaMemcpyAsync(stage, static_cast<const char*>(u) + c * N * es, N * es,
+                               cudaMemcpyHostToDevice, s), "copy state in");
+            xe.rin = stage;
+            xe.real_fp64 = where == FLUSI_HOST_FP64;
+            xe.ncomp = 1;
+            xe.comp0 = c;
+            CK(launch_xpass(fp64, XP_R2C, W, g, h->px, tx, at<int>(h, h->opx), xe, nullptr, s), "x r2c");
+        }
+    }
+    CK(launch_ypass(fp64, false, W, g, h->py, at<double2>(h, h->oty), at<int>(h, h->opy), 3, nullptr, s), "y forward");
+    ZfwdExtra ze{};
+    for (int i = 0; i < 3; ++i) ze.u_inf[i] = h->opt.u_inf[i];
+    ze.mean_free = h->opt.mean_mode;
+    CK(launch_zfwd(fp64, 1, W, h->ws + h->oU, h->ws + h->oH, g, h->pz, at<double2>(h, h->otz),
+                   at<int>(h, h->opz), ze, nullptr, s), "z forward");
+    CK(cudaStreamSynchronize(s), "set_state");
+    h->has_state = 1;
+    h->poisoned = 0;
+    h->rows_read = 0;
+    return FLUSI_OK;
+}
+
+int flusi_step(flusi_t h, int n)
+{
+    int rc = check_ready(h, true);
+    if (rc) return rc;
+    if (n < 0) return fail(h, FLUSI_EINVAL, "n < 0");
+    if (h->poisoned) return fail(h, FLUSI_ESTATE, "a device error poisoned the handle; set a new state");
+    if (n == 0) return FLUSI_OK;
+    if (!h->opt.use_graph) {
+        for (int i = 0; i < n; ++i) CK(enqueue_step(h, h->stream, nullptr), "enqueue step");
+        return FLUSI_OK;
+    }
+    if (!h->graph_ok) {
+        cudaGraph_t graph = nullptr;
+        CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+        cudaError_t e = enqueue_step(h, h->cap_stream, nullptr);
+        cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &graph);
+        if (e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return cuda_fail(h, e, "capture step");
+        }
+        CK(e2, "end capture");
+        e = cudaGraphInstantiate(&h->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        CK(e, "instantiate graph");
+        h->graph_ok = 1;
+    }
+    for (int i = 0; i < n; ++i) CK(cudaGraphLaunch(h->gexec, h->stream), "graph launch");
+    return FLUSI_OK;
+}
+
+int flusi_sync(flusi_t h)
+{
+    int rc = check_ready(h, false);
+    if (rc) return rc;
+    return read_status(h, nullptr);
+}
+
+int flusi_forces(flusi_t h, double* rows, int cap, int* count, long long* lost)
+{
+    int rc = check_ready(h, true);
+    if (rc) return rc;
+    if (!rows || !count || cap < 0) return fail(h, FLUSI_EINVAL, "bad argument");
+    *count = 0;
+    if (lost) *lost = 0;
+    StepState st;
+    rc = read_status(h, &st);
+    if (rc) return rc;
+    const long long ring = h->opt.force_ring;
+    long long avail = st.n - h->rows_read;
+    long long dropped = avail > ring ? avail - ring : 0;
+    long long first = h->rows_read + dropped;
+    long long take = std::min<long long>(avail - dropped, cap);
+    const double* dev = at<double>(h, h->orows);
+    long long done = 0;
+    while (done < take) {
+        long long idx = (first + done) % ring;
+        long long chunk = std::min(take - done, ring - idx);
+        CK(cudaMemcpy(rows + done * kRowCols, dev + idx * kRowCols, sizeof(double) * kRowCols * chunk,
+                      cudaMemcpyDeviceToHost), "read force rows");
+        done += chunk;
+    }
+    h->rows_read = first + take;
+    *count = (int)take;
+    if (lost) *lost = dropped;
+    return FLUSI_OK;
+}
+
+int flusi_get_state(flusi_t h, void* u_out, int where, double* t, long long* step)
+{
+    int rc = check_ready(h, true);
+    if (rc) return rc;
+    if (!u_out) return fail(h, FLUSI_EINVAL, "u_out is NULL");
+    if (where < FLUSI_HOST_FP64 || where > FLUSI_DEVICE) return fail(h, FLUSI_EINVAL, "bad `where`");
+    StepState st;
+    rc = read_status(h, &st);
+    if (rc) return rc;
+    const Geom& g = h->g;
+    const int fp64 = h->prec == FLUSI_FP64;
+    const size_t N = (size_t)g.nx * g.ny * g.nz;
+    void* W = h->ws + h->oW;
+    cudaStream_t s = h->stream;
+    CK(launch_zinv(fp64, h->ws + h->oU, W, g, h->pz, at<double2>(h, h->otz), at<int>(h, h->opz), 3, nullptr, s), "z inverse");
+    CK(launch_ypass(fp64, true, W, g, h->py, at<double2>(h, h->oty), at<int>(h, h->opy), 3, nullptr, s), "y inverse");
+    XExtra xe{};
+    xe.cstride = (long long)N;
+    if (where == FLUSI_DEVICE) {
+        xe.rout = u_out;
+        xe.real_fp64 = fp64;
+        xe.ncomp = 3;
+        xe.comp0 = 0;
+        CK(launch_xpass(fp64, XP_C2R, W, g, h->px, at<double2>(h, h->otx), at<int>(h, h->opx), xe, nullptr, s), "x c2r");
+        CK(cudaStreamSynchronize(s), "get_state");
+    } else {
+        const size_t es = real_size(where, h->prec);
+        char* stage = h->ws + h->oW + (size_t)3 * g.nz * g.ny * g.Mxp * (fp64 ? 16 : 8);
+        for (int c = 0; c < 3; ++c) {
+            xe.rout = stage;
+            xe.real_fp64 = where == FLUSI_HOST_FP64;
+            xe.ncomp = 1;
+            xe.comp0 = c;
+            CK(launch_xpass(fp64, XP_C2R, W, g, h->px, at<double2>(h, h->otx), at<int>(h, h->opx), xe, nullptr, s), "x c2r");
+            CK(cudaMemcpyAsync(static_cast<char*>(u_out) + c * N * es, stage, N * es,
+                               cudaMemcpyDeviceToHost, s), "copy state out");
+        }
+        CK(cudaStreamSynchronize(s), "get_state");
+    }
+    if (t) *t = st.t;
+    if (step) *step = st.n;
+    return FLUSI_OK;
+}
+
+int flusi_get_spectrum(flusi_t h, double* uh_out)
+{
+    int rc = check_ready(h, true);
+    if (rc) return rc;
+    if (!uh_out) return fail(h, FLUSI_EINVAL, "uh_out is NULL");
+    rc = read_status(h, nullptr);
+    if (rc) return rc;
+    const Geom& g = h->g;
+    const int fp64 = h->prec == FLUSI_FP64;
+    const size_t cnt = (size_t)3 * g.Mz * g.My * g.Mxp;
+    std::vector<double> host(cnt * 2);
+    if (fp64) {
+        CK(cudaMemcpy(host.data(), h->ws + h->oU, cnt * 16, cudaMemcpyDeviceToHost), "read spectrum");
+    } else {
+        std::vector<float> f(cnt * 2);
+        CK(cudaMemcpy(f.data(), h->ws + h->oU, cnt * 8, cudaMemcpyDeviceToHost), "read spectrum");
+        for (size_t i = 0; i < f.size(); ++i) host[i] = f[i];
+    }
+    const int hx = g.nx / 2 + 1;
+    const size_t full = (size_t)g.nz * g.ny * hx;
+    std::memset(uh_out, 0, sizeof(double) * 2 * 3 * full);
+    for (int c = 0; c < 3; ++c)
+        for (int jz = 0; jz < g.Mz; ++jz)
+            for (int jy = 0; jy < g.My; ++jy)
+                for (int x = 0; x < g.Mx; ++x) {
+                    const int iz = slot_of(jz, g.Kz, g.nz), iy = slot_of(jy, g.Ky, g.ny);
+                    const size_t src = (((size_t)c * g.Mz + jz) * g.My + jy) * g.Mxp + x;
+                    const size_t dst = c * full + ((size_t)iz * g.ny + iy) * hx + x;
+                    uh_out[2 * dst] = host[2 * src];
+                    uh_out[2 * dst + 1] = host[2 * src + 1];
+                }
+    return FLUSI_OK;
+}
+
+int flusi_debug_fields(flusi_t h, void* out_dev)
+{
+    int rc = check_ready(h, true);
+    if (rc) return rc;
+    if (!out_dev) return fail(h, FLUSI_EINVAL, "out_dev is NULL");
+    const Geom& g = h->g;
+    const int fp64 = h->prec == FLUSI_FP64;
+    cudaStream_t s = h->stream;
+    void* W = h->ws + h->oW;
+    StepState* st = at<StepState>(h, h->ostate);
+    k_kinematics<<<1, 32, 0, s>>>(at<flusi_insect>(h, h->oins), st, at<Frame>(h, h->oframe), box_margin(h));
+    CK(cudaGetLastError(), "kinematics");
+    CK(launch_zinv(fp64, h->ws + h->oU, W, g, h->pz, at<double2>(h, h->otz), at<int>(h, h->opz), 6, nullptr, s), "z inverse");
+    CK(launch_ypass(fp64, true, W, g, h->py, at<double2>(h, h->oty), at<int>(h, h->opy), 6, nullptr, s), "y inverse");
+    XExtra xe{};
+    xe.frame = at<Frame>(h, h->oframe);
+    xe.shape = make_shape(h);
+    xe.rout = out_dev;
+    xe.comp0 = 0;
+    CK(launch_xpass(fp64, XP_DUMP, W, g, h->px, at<double2>(h, h->otx), at<int>(h, h->opx), xe, nullptr, s), "x dump");
+    return FLUSI_OK;
+}
+
+int flusi_profile_step(flusi_t h, int n, double* ms, const char** names, int* nk)
+{
+    int rc = check_ready(h, true);
+    if (rc) return rc;
+    if (n < 1 || !ms || !nk) return fail(h, FLUSI_EINVAL, "bad argument");
+    if (h->poisoned) return fail(h, FLUSI_ESTATE, "handle poisoned");
+    cudaEvent_t ev[kStepKernels + 1];
+    for (auto& e : ev) CK(cudaEventCreate(&e), "event");
+    std::vector<double> acc(kStepKernels, 0.0);
+    for (int i = 0; i < n; ++i) {
+        CK(enqueue_step(h, h->stream, ev), "enqueue step");
+        CK(cudaEventSynchronize(ev[kStepKernels]), "event sync");
+        for (int k = 0; k < kStepKernels; ++k) {
+            float t = 0;
+            CK(cudaEventElapsedTime(&t, ev[k], ev[k + 1]), "elapsed");
+            acc[k] += t;
+        }
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    for (int k = 0; k < kStepKernels; ++k) {
+        ms[k] = acc[k] / n;
+        if (names) names[k] = kKernelNames[k];
+    }
+    *nk = kStepKernels;
+    return read_status(h, nullptr);
+}
+
+int flusi_kernels_per_step(flusi_t h, int* count)
+{
+    if (!h || !count) return FLUSI_EINVAL;
+    *count = kStepKernels;
+    return FLUSI_OK;
+}
+
+int flusi_destroy(flusi_t h)
+{
+    if (!h) return FLUSI_OK;
+    drop_graph(h);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    delete h;
+    return FLUSI_OK;
+}
+
+const char* flusi_last_error(flusi_t h)
+{
+    return h ? h->err.c_str() : g_create_err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,71 @@
+// Kernels of libflusi and their host-side launchers.
+//
+// Device data layout (complex of the state precision T; N_r = nz*ny rows):
+//   U, H   state u_hat and AB2 history N_hat^{n-1}: [3][Mz][My][Mxp], only the
+//          modes kept by the 2/3 rule (m_y, m_z stored as 0..K, -K..-1)
+//   W      work: [6][nz][ny][Mxp]; per z plane the first My rows hold
+//          y-modes ("A" form, after the z transform) or all ny rows hold grid
+//          y values ("B" form, after the y transform); each row carries the
+//          Mx kept x-modes padded with zeros to Mxp.
+// One step: kinematics -> zinv (u, curl) -> yinv -> xpass (c2r, physics, r2c)
+//           -> scalars -> yfwd -> zfwd (projection, IF-AB2).
+#pragma once
+
+#include "../../include/flusi.h"
+#include "common.cuh"
+
+namespace flusi {
+
+// kinematics / scalars (scalars.cu)
+__global__ void k_kinematics(const flusi_insect* ins, const StepState* st, Frame* fr, double h);
+__global__ void k_reset_state(StepState* st, StepCoef* coef);
+__global__ void k_scalars(Geom g, const double* part, int nparts, StepState* st, StepCoef* coef,
+                          double* rows, int ring, double* etab, double3 opts);
+
+// y transform (ypass.cu): W[c] for c < ncomp, between A and B form.
+// tw: twiddle table of the axis; pos: digit-reversal table of its plan.
+cudaError_t launch_ypass(int fp64, bool inverse, void* W, const Geom& g, const FftPlan& plan,
+                         const double2* tw, const int* pos, int ncomp, const StepState* st,
+                         cudaStream_t s);
+
+// z transforms (zpass.cu)
+//   zinv: U -> W[0..nf) in A form; nf = 3 (u) or 6 (u and omega = i k x u).
+cudaError_t launch_zinv(int fp64, const void* U, void* W, const Geom& g, const FftPlan& plan,
+                        const double2* tw, const int* pos, int nf, const StepState* st,
+                        cudaStream_t s);
+//   zfwd: W[0..3) in A form -> FFT -> projection ->
+//   mode 0: IF-AB2 update of U with history H;  mode 1: U = result, H = 0.
+struct ZfwdExtra {
+    const StepCoef* coef;     // mode 0
+    const double* etab;       // mode 0: [E1x Mx][E1y My][E1z Mz][E2x][E2y][E2z]
+    double u_inf[3];
+    int mean_free;
+};
+cudaError_t launch_zfwd(int fp64, int mode, const void* W, void* U, void* H, const Geom& g,
+                        const FftPlan& plan, const double2* tw, const int* pos, const ZfwdExtra& ex,
+                        const StepState* st, cudaStream_t s);
+
+// x pass (xpass.cu)
+enum XMode { XP_PHYS = 0, XP_R2C = 1, XP_C2R = 2, XP_DUMP = 3 };
+struct XExtra {
+    const Frame* frame;
+    Shape shape;
+    double* part;            // XP_PHYS: [grid][kNumSums]
+    const void* rin;         // XP_R2C: real input [ncomp][nz][ny][nx]
+    void* rout;              // XP_C2R: real output; XP_DUMP: [14][nz][ny][nx]
+    int real_fp64;           // element type of rin / rout: 1 double, 0 float
+    int ncomp;               // XP_R2C / XP_C2R: components
+    int comp0;               // first W component written (R2C) or read (C2R)
+    long long cstride;       // elements between components of rin / rout
+};
+int xpass_grid(int fp64, const Geom& g);   // CTAs of the persistent physical pass
+cudaError_t launch_xpass(int fp64, int mode, void* W, const Geom& g, const FftPlan& plan,
+                         const double2* tw, const int* pos, const XExtra& ex, const StepState* st,
+                         cudaStream_t s);
+
+// Shared-memory limits of every instantiation (once per process and device).
+cudaError_t configure_ypass();
+cudaError_t configure_zpass();
+cudaError_t configure_xpass();
+
+}  // namespace flusi

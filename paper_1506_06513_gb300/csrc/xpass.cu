@@ -1,0 +1,510 @@
+// x-axis pass: real-to-complex and complex-to-real transforms along x, fused
+// with the physical-space work of Algorithm 1 step c.
+//
+// A tile is RB consecutive (z, y) rows.  Each real line of length nx is
+// transformed through a complex transform of length nh = nx/2 on
+// z[p] = x[2p] + i x[2p+1]:
+//   c2r: Z[k] = (X[k] + X*[nh-k]) + i (X[k] - X*[nh-k]) w^{-k},  z = iFFT_nh(Z)
+//   r2c: X[k] = E + w^k O,  E = (Z[k] + Z*[nh-k])/2,  O = -i (Z[k] - Z*[nh-k])/2
+// with w = exp(-2 pi i / nx); only the kept x-modes k < Mx are read/written.
+//
+// XP_PHYS, per grid point (Sec. 2.1, Sec. 3):
+//   chi, colour, u_s from the body and wing signed distances (Eq.
+//   smoothing_mask_as_function_of_delta), u_s = u_b + Omega_w x (x - x_pivot)
+//   (Eqs. body_velocity_field, wing_velocity_field), and
+//   NL = u x omega - chi/C_eta (u - u_s)  (Eq. PNST_org_momentum),
+//   plus FP64 partial sums of chi (u - u_s), r x chi (u - u_s), chi u_s,
+//   r x chi u_s per colour, |u|^2, max |u|^2 and a non-finite flag.
+// The grid is persistent (a multiple of the SM count); each CTA writes one
+// row of partial sums, reduced in a fixed order by the scalar kernel.
+#include "fft.cuh"
+#include "kernels.cuh"
+
+namespace flusi {
+
+namespace {
+
+constexpr int kThreadsX = 192;
+constexpr int kWarpsX = kThreadsX / 32;
+// complex elements per tile: 48 KiB of shared memory
+template <typename T> constexpr int tile_elems() { return sizeof(T) == 4 ? 6144 : 3072; }
+
+template <typename T> struct FrameT {
+    T xc[3], uc[3], Ob[3], Mb[9], Mw[2][9], pv[2][3], Ow[2][3], box[3][6];
+    int active[3];
+    T h, a, b, c_le, c_te, R, ht, inv_eta;
+    int body_type, profile;
+};
+
+template <typename T> __device__ __forceinline__ T profile_chi(int profile, T d, T h)
+{
+    if (profile == 1) return T(0.5) * (T(1) - tanh(d / h));
+    if (d <= -h) return T(1);
+    if (d >= h) return T(0);
+    return T(0.5) * (T(1) + cospi((d + h) / (T(2) * h)));
+}
+
+template <typename T>
+__device__ __forceinline__ void cross3(const T* a, const T* b, T* c)
+{
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// Mask, colour (0 fluid, 1 body, 2/3 wings) and solid velocity at X.
+template <typename T>
+__device__ __forceinline__ void solid_at(const FrameT<T>& F, const T* X, const bool* inrow, T& chi,
+                                         int& col, T* us)
+{
+    chi = T(0);
+    col = 0;
+    us[0] = us[1] = us[2] = T(0);
+    if (!(inrow[0] | inrow[1] | inrow[2])) return;
+    T d[3] = {X[0] - F.xc[0], X[1] - F.xc[1], X[2] - F.xc[2]};
+    if (inrow[0] && X[0] >= F.box[0][0] && X[0] <= F.box[0][1]) {
+        T delta;
+        if (F.body_type == 1) {
+            delta = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) - F.a;
+        } else {
+            T xb0 = F.Mb[0] * d[0] + F.Mb[1] * d[1] + F.Mb[2] * d[2];
+            T xb1 = F.Mb[3] * d[0] + F.Mb[4] * d[1] + F.Mb[5] * d[2];
+            T xb2 = F.Mb[6] * d[0] + F.Mb[7] * d[1] + F.Mb[8] * d[2];
+            T rr = sqrt(xb1 * xb1 + xb2 * xb2), ax = fabs(xb0);
+            if (ax <= F.a) {
+                T q = xb0 / F.a;
+                delta = rr - F.b * sqrt(fmax(T(0), T(1) - q * q));
+            } else {
+                delta = sqrt(rr * rr + (ax - F.a) * (ax - F.a));
+            }
+        }
+        T c = profile_chi(F.profile, delta, F.h);
+        if (c > chi) {
+            chi = c;
+            col = 1;
+            T w[3];
+            cross3(F.Ob, d, w);
+            for (int i = 0; i < 3; ++i) us[i] = F.uc[i] + w[i];
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        if (!(inrow[1 + s] && X[0] >= F.box[1 + s][0] && X[0] <= F.box[1 + s][1])) continue;
+        const T* M = F.Mw[s];
+        T e[3] = {X[0] - F.pv[s][0], X[1] - F.pv[s][1], X[2] - F.pv[s][2]};
+        T xw0 = M[0] * e[0] + M[1] * e[1] + M[2] * e[2];
+        T xw1 = M[3] * e[0] + M[4] * e[1] + M[5] * e[2];
+        T xw2 = M[6] * e[0] + M[7] * e[1] + M[8] * e[2];
+        T delta = fmax(fmax(xw0 - F.c_le, -xw0 - F.c_te), fmax(fmax(xw1 - F.R, -xw1),
+                                                               fabs(xw2) - T(0.5) * F.ht));
+        T c = profile_chi(F.profile, delta, F.h);
+        if (c > chi) {
+            chi = c;
+            col = 2 + s;
+            T w[3], v[3];
+            cross3(F.Ob, d, w);
+            cross3(F.Ow[s], e, v);
+            for (int i = 0; i < 3; ++i) us[i] = F.uc[i] + w[i] + v[i];
+        }
+    }
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kThreadsX)
+k_xpass(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict__ tw,
+        const int* __restrict__ pos, XExtra ex, int lgRB, const StepState* __restrict__ st)
+{
+    if (st && st->status != 0) return;
+    constexpr bool kPhys = (MODE == XP_PHYS || MODE == XP_DUMP);
+    const int RB = 1 << lgRB;
+    const int NF = kPhys ? 6 : ex.ncomp;
+    const int C = NF * RB;
+    const int ld = C | 1;
+    const int nh = g.nx / 2, nx = g.nx;
+    const int nrows = g.nz * g.ny;
+    const int ntiles = ceil_div(nrows, RB);
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* wacc = reinterpret_cast<double*>(smem_raw);                    // [warps][36]
+    FrameT<T>* Fs = reinterpret_cast<FrameT<T>*>(wacc + kWarpsX * 36);
+    cplx<T>* tws = reinterpret_cast<cplx<T>*>(
+        reinterpret_cast<unsigned char*>(Fs) + ((sizeof(FrameT<T>) + 15) / 16) * 16);
+    cplx<T>* buf = tws + nx;
+    int* spos = reinterpret_cast<int*>(buf + (size_t)nh * ld);
+
+    const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+    load_tables<T>(tws, spos, tw, pos, nx, nh);
+    if (kPhys) {
+        for (int i = tid; i < kWarpsX * 36; i += kThreadsX) wacc[i] = 0.0;
+        if (tid == 0) {
+            const Frame& F = *ex.frame;
+            FrameT<T> f;
+            for (int i = 0; i < 3; ++i) {
+                f.xc[i] = T(F.xc[i]);
+                f.uc[i] = T(F.uc[i]);
+                f.Ob[i] = T(F.Ob[i]);
+                f.active[i] = F.active[i];
+                for (int s = 0; s < 2; ++s) {
+                    f.pv[s][i] = T(F.pv[s][i]);
+                    f.Ow[s][i] = T(F.Ow[s][i]);
+                }
+                for (int j = 0; j < 6; ++j) f.box[i][j] = T(F.box[i][j]);
+            }
+            for (int i = 0; i < 9; ++i) {
+                f.Mb[i] = T(F.Mb[i]);
+                f.Mw[0][i] = T(F.Mw[0][i]);
+                f.Mw[1][i] = T(F.Mw[1][i]);
+            }
+            const Shape& S = ex.shape;
+            f.h = T(S.h);
+            f.a = T(S.body_a);
+            f.b = T(S.body_b);
+            f.c_le = T(S.c_le);
+            f.c_te = T(S.c_te);
+            f.R = T(S.R);
+            f.ht = T(S.ht);
+            f.inv_eta = T(1.0 / g.eta);
+            f.body_type = S.body_type;
+            f.profile = S.profile;
+            if (S.body_type == 0) f.active[0] = 0;
+            if (S.nwings < 1) f.active[1] = 0;
+            if (S.nwings < 2) f.active[2] = 0;
+            *Fs = f;
+        }
+    }
+    __syncthreads();
+
+    double e_acc = 0.0, m_acc = 0.0;
+    int bad = 0;
+    const T dxT = T(g.dx), dyT = T(g.dy), dzT = T(g.dz);
+
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int row0 = tile * RB;
+
+        // ---- load: spectral rows -> Z (c2r input) or real rows -> z (r2c input)
+        if (MODE == XP_R2C) {
+            for (int i = tid; i < C * nh; i += kThreadsX) {
+                const int col = i / nh, p = i - col * nh;
+                const int f = col >> lgRB, r = row0 + (col & (RB - 1));
+                cplx<T> z = mkc<T>(0, 0);
+                if (r < nrows) {
+                    const long long o = f * ex.cstride + (long long)r * nx + 2 * p;
+                    if (ex.real_fp64) {
+                        const double* s = (const double*)ex.rin;
+                        z = mkc<T>(T(s[o]), T(s[o + 1]));
+                    } else {
+                        const float* s = (const float*)ex.rin;
+                        z = mkc<T>(T(s[o]), T(s[o + 1]));
+                    }
+                }
+                buf[spos[p] * ld + col] = z;
+            }
+        } else {
+            const int half = nh / 2 + 1;
+            for (int i = tid; i < C * half; i += kThreadsX) {
+                const int col = i / half, k = i - col * half;
+                const int f = col >> lgRB, r = row0 + (col & (RB - 1));
+                const int m = nh - k;
+                cplx<T> Xk = mkc<T>(0, 0), Xm = mkc<T>(0, 0);
+                if (r < nrows) {
+                    const cplx<T>* src = W + ((size_t)(ex.comp0 + f) * nrows + r) * g.Mxp;
+                    if (k < g.Mx) Xk = src[k];
+                    if (k == 0) Xk.y = T(0);            // a real line has a real mean
+                    else if (m < g.Mx) Xm = src[m];
+                }
+                const cplx<T> wk = tws[k];
+                cplx<T> s1 = cadd(Xk, cconj(Xm)), d1 = csub(Xk, cconj(Xm));
+                buf[k * ld + col] = cadd(s1, cmuli(cmul(d1, cconj(wk))));
+                if (k > 0 && m != k) {
+                    const cplx<T> wm = tws[m];
+                    cplx<T> s2 = cadd(Xm, cconj(Xk)), d2 = csub(Xm, cconj(Xk));
+                    buf[m * ld + col] = cadd(s2, cmuli(cmul(d2, cconj(wm))));
+                }
+            }
+        }
+        __syncthreads();
+
+        if (MODE != XP_R2C) fft_dif<T, true>(buf, C, ld, plan, tws);   // z[p] at row pos[p]
+
+        if (MODE == XP_C2R) {
+            for (int i = tid; i < C * nh; i += kThreadsX) {
+                const int col = i / nh, p = i - col * nh;
+                const int f = col >> lgRB, r = row0 + (col & (RB - 1));
+                if (r >= nrows) continue;
+                const cplx<T> z = buf[spos[p] * ld + col];
+                const long long o = f * ex.cstride + (long long)r * nx + 2 * p;
+                if (ex.real_fp64) {
+                    double* d = (double*)ex.rout;
+                    d[o] = double(z.x);
+                    d[o + 1] = double(z.y);
+                } else {
+                    float* d = (float*)ex.rout;
+                    d[o] = float(z.x);
+                    d[o + 1] = float(z.y);
+                }
+            }
+            __syncthreads();
+            continue;
+        }
+
+        if (kPhys) {
+            const FrameT<T>& F = *Fs;
+            const int items = RB * nh;
+            const int niter = ceil_div(items, kThreadsX);
+            for (int it = 0; it < niter; ++it) {
+                const int i = tid + it * kThreadsX;
+                const int rr = i / nh, p = i - rr * nh;
+                const int r = row0 + rr;
+                const bool valid = (i < items) && (r < nrows);
+                T nl[2][3], chi2[2], us2[2][3];
+                int colr[2] = {0, 0};
+                T u[2][3], om[2][3], X[2][3];
+                if (valid) {
+                    const int z = r / g.ny, y = r - z * g.ny;
+                    const T Y = T(y) * dyT, Z = T(z) * dzT;
+                    bool inrow[3];
+                    for (int q = 0; q < 3; ++q)
+                        inrow[q] = F.active[q] && Y >= F.box[q][2] && Y <= F.box[q][3] &&
+                                   Z >= F.box[q][4] && Z <= F.box[q][5];
+                    cplx<T> uv[3], wv[3];
+                    const int row = spos[p];
+                    for (int c = 0; c < 3; ++c) {
+                        uv[c] = buf[row * ld + c * RB + rr];
+                        wv[c] = buf[row * ld + (3 + c) * RB + rr];
+                    }
+                    for (int h = 0; h < 2; ++h) {
+                        for (int c = 0; c < 3; ++c) {
+                            u[h][c] = h ? uv[c].y : uv[c].x;
+                            om[h][c] = h ? wv[c].y : wv[c].x;
+                        }
+                        X[h][0] = T(2 * p + h) * dxT;
+                        X[h][1] = Y;
+                        X[h][2] = Z;
+                        solid_at(F, X[h], inrow, chi2[h], colr[h], us2[h]);
+                        T lamb[3];
+                        cross3(u[h], om[h], lamb);
+                        const T pen = chi2[h] * F.inv_eta;
+                        T uu = T(0);
+                        for (int c = 0; c < 3; ++c) {
+                            nl[h][c] = lamb[c] - pen * (u[h][c] - us2[h][c]);
+                            uu += u[h][c] * u[h][c];
+                            if (!isfinite(nl[h][c]) || !isfinite(u[h][c])) bad = 1;
+                        }
+                        e_acc += double(uu);
+                        m_acc = fmax(m_acc, double(uu));
+                    }
+                    if (MODE == XP_DUMP) {
+                        T* out = (T*)ex.rout;
+                        const long long Nn = (long long)nrows * nx;
+                        for (int h = 0; h < 2; ++h) {
+                            const long long o = (long long)r * nx + 2 * p + h;
+                            for (int c = 0; c < 3; ++c) {
+                                out[c * Nn + o] = u[h][c];
+                                out[(3 + c) * Nn + o] = om[h][c];
+                                out[(8 + c) * Nn + o] = us2[h][c];
+                                out[(11 + c) * Nn + o] = nl[h][c];
+                            }
+                            out[6 * Nn + o] = chi2[h];
+                            out[7 * Nn + o] = T(colr[h]);
+                        }
+                    } else {
+                        const int row = spos[p];
+                        for (int c = 0; c < 3; ++c)
+                            buf[row * ld + c * RB + rr] = mkc<T>(nl[0][c], nl[1][c]);
+                    }
+                }
+                if (MODE == XP_PHYS) {
+                    // penalization sums per colour, only in warps that touch the solid
+                    for (int cc = 0; cc < 3; ++cc) {
+                        const bool has = valid && (colr[0] == cc + 1 || colr[1] == cc + 1);
+                        if (!__any_sync(0xffffffffu, has)) continue;
+                        double v[12];
+                        for (int k = 0; k < 12; ++k) v[k] = 0.0;
+                        if (has) {
+                            for (int h = 0; h < 2; ++h) {
+                                if (colr[h] != cc + 1) continue;
+                                const T* ref = cc == 0 ? F.xc : F.pv[cc - 1];
+                                T rv[3] = {X[h][0] - ref[0], X[h][1] - ref[1], X[h][2] - ref[2]};
+                                T pu[3], cu[3], m1[3], m2[3];
+                                for (int c = 0; c < 3; ++c) {
+                                    pu[c] = chi2[h] * (u[h][c] - us2[h][c]);
+                                    cu[c] = chi2[h] * us2[h][c];
+                                }
+                                cross3(rv, pu, m1);
+                                cross3(rv, cu, m2);
+                                for (int c = 0; c < 3; ++c) {
+                                    v[c] += double(pu[c]);
+                                    v[3 + c] += double(m1[c]);
+                                    v[6 + c] += double(cu[c]);
+                                    v[9 + c] += double(m2[c]);
+                                }
+                            }
+                        }
+                        for (int k = 0; k < 12; ++k) v[k] = warp_sum(v[k]);
+                        if (lane == 0)
+                            for (int k = 0; k < 12; ++k) wacc[warp * 36 + cc * 12 + k] += v[k];
+                    }
+                }
+            }
+            __syncthreads();
+            if (MODE == XP_DUMP) continue;
+        }
+
+        // ---- r2c of the first 3 (or ncomp) fields and store the kept x-modes
+        const int Cf = kPhys ? 3 * RB : C;
+        fft_dit<T, false>(buf, Cf, ld, plan, tws);   // digit-reversed in, natural out
+        const int Mxp = g.Mxp, Mx = g.Mx;
+        for (int i = tid; i < Cf * Mxp; i += kThreadsX) {
+            const int col = i / Mxp, k = i - col * Mxp;
+            const int f = col >> lgRB, r = row0 + (col & (RB - 1));
+            if (r >= nrows) continue;
+            cplx<T> Xk = mkc<T>(0, 0);
+            if (k < Mx) {
+                const int m = k == 0 ? 0 : nh - k;
+                const cplx<T> Zk = buf[k * ld + col], Zm = cconj(buf[m * ld + col]);
+                const cplx<T> E = cscale(cadd(Zk, Zm), T(0.5));
+                const cplx<T> O = cscale(cmulmi(csub(Zk, Zm)), T(0.5));
+                Xk = cadd(E, cmul(tws[k], O));
+            }
+            W[((size_t)(ex.comp0 + f) * nrows + r) * Mxp + k] = Xk;
+        }
+        __syncthreads();
+    }
+
+    if (MODE == XP_PHYS) {
+        __shared__ double red[kWarpsX][3];
+        e_acc = warp_sum(e_acc);
+        for (int o = 16; o > 0; o >>= 1) m_acc = fmax(m_acc, __shfl_xor_sync(0xffffffffu, m_acc, o));
+        const int anybad = __any_sync(0xffffffffu, bad);
+        if (lane == 0) {
+            red[warp][0] = e_acc;
+            red[warp][1] = m_acc;
+            red[warp][2] = anybad ? 1.0 : 0.0;
+        }
+        __syncthreads();
+        double* out = ex.part + (size_t)blockIdx.x * kNumSums;
+        if (tid < 36) {
+            double s = 0.0;
+            for (int w = 0; w < kWarpsX; ++w) s += wacc[w * 36 + tid];
+            out[tid] = s;
+        } else if (tid == kSumEkin) {
+            double s = 0.0;
+            for (int w = 0; w < kWarpsX; ++w) s += red[w][0];
+            out[tid] = s;
+        } else if (tid == kSumUmax2) {
+            double s = 0.0;
+            for (int w = 0; w < kWarpsX; ++w) s = fmax(s, red[w][1]);
+            out[tid] = s;
+        } else if (tid == kSumBad) {
+            double s = 0.0;
+            for (int w = 0; w < kWarpsX; ++w) s = fmax(s, red[w][2]);
+            out[tid] = s;
+        } else if (tid < kNumSums) {
+            out[tid] = 0.0;
+        }
+    }
+}
+
+template <typename T> int x_lgrb(const Geom& g)
+{
+    const int nh = g.nx / 2;
+    int RB = 32;
+    while (RB > 1 && nh * 6 * RB > tile_elems<T>()) RB >>= 1;
+    return __builtin_ctz(RB);
+}
+
+template <typename T> size_t x_smem(const Geom& g, int lgRB, int NF)
+{
+    const int C = NF << lgRB;
+    const int ld = C | 1;
+    size_t s = sizeof(double) * kWarpsX * 36 + ((sizeof(FrameT<T>) + 15) / 16) * 16;
+    s += sizeof(cplx<T>) * ((size_t)g.nx + (size_t)(g.nx / 2) * ld) + sizeof(int) * (g.nx / 2);
+    return s;
+}
+
+int g_sm_count = 0;
+
+template <typename T> int x_grid(const Geom& g)
+{
+    const int lg = x_lgrb<T>(g);
+    const int ntiles = ceil_div(g.nz * g.ny, 1 << lg);
+    if (g_sm_count == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev);
+        if (g_sm_count <= 0) g_sm_count = 1;
+    }
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_xpass<T, XP_PHYS>, kThreadsX,
+                                                  x_smem<T>(g, lg, 6));
+    if (per_sm <= 0) per_sm = 1;
+    int grid = g_sm_count * per_sm;
+    return grid < ntiles ? grid : ntiles;
+}
+
+template <typename T>
+cudaError_t launch_x(int mode, void* W, const Geom& g, const FftPlan& plan, const double2* tw,
+                     const int* pos, const XExtra& ex, const StepState* st, cudaStream_t s)
+{
+    const int lg = x_lgrb<T>(g);
+    const int RB = 1 << lg;
+    const int ntiles = ceil_div(g.nz * g.ny, RB);
+    const int NF = (mode == XP_PHYS || mode == XP_DUMP) ? 6 : ex.ncomp;
+    if (NF < 1 || NF > 6 || (g.nx / 2) * NF * RB > tile_elems<T>()) return cudaErrorInvalidValue;
+    if (kThreadsX % (NF * RB) != 0) return cudaErrorInvalidValue;
+    const size_t smem = x_smem<T>(g, lg, NF);
+    cplx<T>* w = (cplx<T>*)W;
+    switch (mode) {
+    case XP_PHYS:
+        k_xpass<T, XP_PHYS><<<x_grid<T>(g), kThreadsX, smem, s>>>(w, g, plan, tw, pos, ex, lg, st);
+        break;
+    case XP_R2C:
+        k_xpass<T, XP_R2C><<<ntiles, kThreadsX, smem, s>>>(w, g, plan, tw, pos, ex, lg, st);
+        break;
+    case XP_C2R:
+        k_xpass<T, XP_C2R><<<ntiles, kThreadsX, smem, s>>>(w, g, plan, tw, pos, ex, lg, st);
+        break;
+    default:
+        k_xpass<T, XP_DUMP><<<ntiles, kThreadsX, smem, s>>>(w, g, plan, tw, pos, ex, lg, st);
+        break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int xpass_grid(int fp64, const Geom& g) { return fp64 ? x_grid<double>(g) : x_grid<float>(g); }
+
+cudaError_t launch_xpass(int fp64, int mode, void* W, const Geom& g, const FftPlan& plan,
+                         const double2* tw, const int* pos, const XExtra& ex, const StepState* st,
+                         cudaStream_t s)
+{
+    return fp64 ? launch_x<double>(mode, W, g, plan, tw, pos, ex, st, s)
+                : launch_x<float>(mode, W, g, plan, tw, pos, ex, st, s);
+}
+
+cudaError_t configure_xpass()
+{
+    const int big = 100 * 1024;
+    cudaError_t e;
+#define FLUSI_SMEM(fn) \
+    if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    FLUSI_SMEM((k_xpass<float, XP_PHYS>))
+    FLUSI_SMEM((k_xpass<float, XP_R2C>))
+    FLUSI_SMEM((k_xpass<float, XP_C2R>))
+    FLUSI_SMEM((k_xpass<float, XP_DUMP>))
+    FLUSI_SMEM((k_xpass<double, XP_PHYS>))
+    FLUSI_SMEM((k_xpass<double, XP_R2C>))
+    FLUSI_SMEM((k_xpass<double, XP_C2R>))
+    FLUSI_SMEM((k_xpass<double, XP_DUMP>))
+#undef FLUSI_SMEM
+    return cudaSuccess;
+}
+
+}  // namespace flusi

@@ -1,0 +1,129 @@
+// y-axis transform pass (part of the 3-D FFTs of Algorithm 1 step c).
+//
+// A tile is TX consecutive x-mode columns of NP consecutive z planes of one
+// component: every global access is a run of TX complex values (128 bytes),
+// the column FFT runs in shared memory, and the pass works in place (a tile
+// reads all of its rows before it writes any).
+//   inverse: rows j < My hold the kept y-modes 0..Ky, -Ky..-1 -> ny grid rows
+//   forward: ny grid rows -> the My kept y-modes (2/3 rule, pruned output)
+#include "fft.cuh"
+#include "kernels.cuh"
+
+namespace flusi {
+
+namespace {
+
+constexpr int kThreads = 256;
+// complex elements per tile (64 KiB of shared memory)
+template <typename T> constexpr int tile_elems() { return sizeof(T) == 4 ? 8192 : 4096; }
+
+template <typename T, bool INV>
+__global__ void __launch_bounds__(kThreads)
+k_ypass(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict__ tw,
+        const int* __restrict__ pos, int ncomp, int lgTX, int lgNP, const StepState* __restrict__ st)
+{
+    if (st && st->status != 0) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int TX = 1 << lgTX, lgC = lgTX + lgNP, C = 1 << lgC;
+    cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
+    cplx<T>* tws = buf + (g.ny << lgC);
+    int* spos = reinterpret_cast<int*>(tws + g.ny);
+    const int nxb = ceil_div(g.Mxp, TX), nzb = ceil_div(g.nz, 1 << lgNP);
+    int b = blockIdx.x;
+    const int xb = b % nxb;
+    b /= nxb;
+    const int zb = b % nzb;
+    const int c = b / nzb;
+    if (c >= ncomp) return;
+    const int x0 = xb * TX, z0 = zb << lgNP;
+    const size_t plane = (size_t)g.ny * g.Mxp;
+    cplx<T>* base = W + (size_t)c * g.nz * plane;
+
+    load_tables<T>(tws, spos, tw, pos, g.ny, g.ny);
+    const int ny = g.ny, My = g.My, Ky = g.Ky;
+    const int total_in = ny << lgC;
+    for (int e = threadIdx.x; e < total_in; e += kThreads) {
+        const int s = e >> lgC, col = e & (C - 1);
+        const int z = z0 + (col >> lgTX), x = x0 + (col & (TX - 1));
+        cplx<T> v = mkc<T>(0, 0);
+        if (z < g.nz && x < g.Mxp) {
+            if (INV) {
+                // slot s holds mode m = s (s <= Ky) or m = s - ny (s >= ny - Ky)
+                int j = s <= Ky ? s : (s >= ny - Ky ? s - ny + My : -1);
+                if (j >= 0) v = base[z * plane + (size_t)j * g.Mxp + x];
+            } else {
+                v = base[z * plane + (size_t)s * g.Mxp + x];
+            }
+        }
+        buf[e] = v;
+    }
+    __syncthreads();
+    fft_dif<T, INV>(buf, C, C, plan, tws);
+    const int rows_out = INV ? ny : My;
+    const int total_out = rows_out << lgC;
+    for (int e = threadIdx.x; e < total_out; e += kThreads) {
+        const int r = e >> lgC, col = e & (C - 1);
+        const int z = z0 + (col >> lgTX), x = x0 + (col & (TX - 1));
+        if (z < g.nz && x < g.Mxp) {
+            const int s = spos[INV ? r : slot_of(r, Ky, ny)];
+            base[z * plane + (size_t)r * g.Mxp + x] = buf[(s << lgC) + col];
+        }
+    }
+}
+
+struct YTile {
+    int lgTX, lgNP, blocks;
+    size_t smem;
+};
+
+template <typename T> YTile y_tile(const Geom& g, int ncomp)
+{
+    YTile t;
+    const int cap = tile_elems<T>();
+    int TX = sizeof(T) == 4 ? 16 : 8;               // 128-byte runs
+    while (TX > 1 && g.ny * TX > cap) TX >>= 1;
+    int NP = 1;
+    while (2 * NP * TX * g.ny <= cap && 2 * NP * TX <= kThreads && 2 * NP <= g.nz) NP *= 2;
+    t.lgTX = __builtin_ctz(TX);
+    t.lgNP = __builtin_ctz(NP);
+    t.blocks = ceil_div(g.Mxp, TX) * ceil_div(g.nz, NP) * ncomp;
+    t.smem = sizeof(cplx<T>) * ((size_t)g.ny + (size_t)g.ny * TX * NP) + sizeof(int) * g.ny;
+    return t;
+}
+
+template <typename T>
+cudaError_t launch_y(bool inverse, void* W, const Geom& g, const FftPlan& plan, const double2* tw,
+                     const int* pos, int ncomp, const StepState* st, cudaStream_t s)
+{
+    YTile t = y_tile<T>(g, ncomp);
+    if ((size_t)g.ny << (t.lgTX + t.lgNP) > (size_t)tile_elems<T>()) return cudaErrorInvalidValue;
+    if (inverse)
+        k_ypass<T, true><<<t.blocks, kThreads, t.smem, s>>>((cplx<T>*)W, g, plan, tw, pos, ncomp,
+                                                              t.lgTX, t.lgNP, st);
+    else
+        k_ypass<T, false><<<t.blocks, kThreads, t.smem, s>>>((cplx<T>*)W, g, plan, tw, pos, ncomp,
+                                                               t.lgTX, t.lgNP, st);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_ypass(int fp64, bool inverse, void* W, const Geom& g, const FftPlan& plan,
+                         const double2* tw, const int* pos, int ncomp, const StepState* st,
+                         cudaStream_t s)
+{
+    return fp64 ? launch_y<double>(inverse, W, g, plan, tw, pos, ncomp, st, s)
+                : launch_y<float>(inverse, W, g, plan, tw, pos, ncomp, st, s);
+}
+
+cudaError_t configure_ypass()
+{
+    const int big = 100 * 1024;
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_ypass<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_ypass<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_ypass<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    return cudaFuncSetAttribute(k_ypass<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+}
+
+}  // namespace flusi

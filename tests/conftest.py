@@ -23,3 +23,11 @@ def orc():
     import oracle
     oracle.lib()
     return oracle
+
+
+def build_flusi():
+    """Build libflusi.so if needed, then import the binding."""
+    import __graft_entry__
+    __graft_entry__._build_module().build()
+    import paper_1506_06513_gb300
+    return paper_1506_06513_gb300

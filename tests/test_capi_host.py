@@ -1,0 +1,124 @@
+"""Host-side checks of the C-ABI (no GPU): the library loads, exports every
+entry point declared in include/flusi.h, and rejects bad arguments before any
+device work."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def fl():
+    from conftest import build_flusi
+    return build_flusi()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "flusi.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(flusi_[a-z_]+)\s*\(", src)))
+
+
+def test_header_symbols_exported(fl):
+    names = _declared()
+    assert "flusi_create" in names and "flusi_step" in names and len(names) >= 15
+    lib = C.CDLL(fl.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), f"{n} declared in flusi.h but not exported"
+
+
+def test_create_validates_sizes(fl):
+    L = (1.0, 1.0, 1.0)
+    for n in [(7, 8, 8), (8, 10, 8), (9, 8, 8), (2048, 8, 8), (4, 8, 8), (8, 8, 5)]:
+        with pytest.raises(fl.FlusiError) as e:
+            fl.flusi_create(n, L, 0.1, 1e-2, fl.FLUSI_FP64)
+        assert e.value.code == fl.FLUSI_EINVAL
+    with pytest.raises(fl.FlusiError):
+        fl.flusi_create((8, 8, 8), (1.0, -1.0, 1.0), 0.1, 1e-2, fl.FLUSI_FP64)
+    with pytest.raises(fl.FlusiError):
+        fl.flusi_create((8, 8, 8), L, 0.1, 0.0, fl.FLUSI_FP64)
+    with pytest.raises(fl.FlusiError):
+        fl.flusi_create((8, 8, 8), L, 0.1, 1e-2, 7)
+    h = fl.flusi_create((96, 12, 1024), L, 0.1, 1e-2, fl.FLUSI_FP32)
+    fl.flusi_destroy(h)
+
+
+def test_workspace_size_scales_with_grid_and_precision(fl):
+    L = (1.0, 1.0, 1.0)
+    sizes = {}
+    for prec in (fl.FLUSI_FP32, fl.FLUSI_FP64):
+        for n in (32, 64):
+            h = fl.flusi_create((n, n, n), L, 0.1, 1e-2, prec)
+            sizes[(prec, n)] = fl.flusi_workspace_bytes(h)
+            fl.flusi_destroy(h)
+    assert sizes[(fl.FLUSI_FP64, 64)] > 1.6 * sizes[(fl.FLUSI_FP32, 64)]
+    assert sizes[(fl.FLUSI_FP32, 64)] > 4 * sizes[(fl.FLUSI_FP32, 32)]
+    # 512^3 FP32: state, history and the six-field work buffer of pruned rows
+    h = fl.flusi_create((512, 512, 512), (4.0, 4.0, 4.0), 0.1, 1e-3, fl.FLUSI_FP32)
+    b = fl.flusi_workspace_bytes(h)
+    fl.flusi_destroy(h)
+    spec = 3 * 341 * 341 * 172 * 8
+    work = 6 * 512 * 512 * 172 * 8
+    assert spec * 2 + work <= b <= spec * 2 + work + 64 * 2 ** 20
+
+
+def test_options_validation(fl):
+    h = fl.flusi_create((16, 16, 16), (1.0, 1.0, 1.0), 0.1, 1e-2, fl.FLUSI_FP64)
+    o = fl.flusi_default_options()
+    assert o.cfl == 0.1 and o.force_ring == 4096 and o.use_graph == 1
+    fl.flusi_set_options(h, o)
+    for field, bad in (("cfl", 0.0), ("dt_fixed", -1.0), ("force_ring", 0), ("mean_mode", 2)):
+        b = fl.flusi_default_options()
+        setattr(b, field, bad)
+        with pytest.raises(fl.FlusiError) as e:
+            fl.flusi_set_options(h, b)
+        assert e.value.code == fl.FLUSI_EINVAL
+    fl.flusi_destroy(h)
+
+
+def test_calls_before_bind_fail_cleanly(fl):
+    h = fl.flusi_create((16, 16, 16), (1.0, 1.0, 1.0), 0.1, 1e-2, fl.FLUSI_FP64)
+    u = np.zeros((3, 16, 16, 16))
+    for call in (lambda: fl.flusi_set_state(h, u, fl.FLUSI_HOST_FP64),
+                 lambda: fl.flusi_step(h, 1), lambda: fl.flusi_forces(h, 4),
+                 lambda: fl.flusi_sync(h)):
+        with pytest.raises(fl.FlusiError) as e:
+            call()
+        assert e.value.code == fl.FLUSI_ESTATE
+    assert "bind" in fl.flusi_last_error(h)
+    # bind with a NULL, misaligned or short workspace is rejected on the host
+    assert fl.lib.flusi_bind(h, None, 10, None) == fl.FLUSI_EINVAL
+    assert fl.lib.flusi_bind(h, C.c_void_p(0x1001), 1 << 40, None) == fl.FLUSI_EINVAL
+    assert fl.lib.flusi_bind(h, C.c_void_p(0x100000), 16, None) == fl.FLUSI_ENOMEM
+    assert fl.flusi_destroy(h) == fl.FLUSI_OK
+    assert fl.lib.flusi_destroy(None) == fl.FLUSI_OK
+
+
+def test_insect_descriptor_validation(fl):
+    import workloads
+    h = fl.flusi_create((16, 16, 16), (4.0, 4.0, 4.0), 0.1, 1e-2, fl.FLUSI_FP64)
+    good = fl.make_insect(workloads.model_insect((4.0, 4.0, 4.0), (16, 16, 16)))
+    fl.flusi_set_kinematics(h, good)
+    fl.flusi_set_kinematics(h, None)
+    for field, bad in (("nwings", 3), ("body_type", 5), ("c_smth", 0.0), ("nfourier", 9)):
+        ins = fl.make_insect(workloads.model_insect((4.0, 4.0, 4.0), (16, 16, 16)))
+        setattr(ins, field, bad)
+        with pytest.raises(fl.FlusiError):
+            fl.flusi_set_kinematics(h, ins)
+    fl.flusi_destroy(h)
+
+
+def test_struct_layouts_match_header(fl):
+    """The ctypes mirrors have the sizes the C compiler gives the structs."""
+    assert C.sizeof(fl.Options) == 3 * 8 + 3 * 8 + 4 * 4
+    assert C.sizeof(fl.Insect) == 4 * 4 + 8 * (1 + 3 + 3 + 6 + 2 + 3 + 3 + 1 + 4 + 1 + 3 * 17)
+
+
+def test_kernels_per_step(fl):
+    h = fl.flusi_create((16, 16, 16), (1.0, 1.0, 1.0), 0.1, 1e-2, fl.FLUSI_FP64)
+    assert fl.flusi_kernels_per_step(h) == 7
+    fl.flusi_destroy(h)

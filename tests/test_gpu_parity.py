@@ -1,0 +1,300 @@
+"""Parity of the CUDA path (through the C-ABI) with the FP64 oracle.
+
+FP64 tolerances follow from double rounding through O(log N) FFT stages and
+20 time steps: 1e-11 relative L2 for the state, 1e-10 for force rows.  FP32
+results are compared at 1e-5 relative L2 per step (single-precision FFTs of
+length <= 1024 accumulate ~log2(N) * 6e-8 relative error per transform).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fl():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    from conftest import build_flusi
+    return build_flusi()
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def rows_err(a, b):
+    """max deviation of force/moment/energy columns relative to each column's scale"""
+    a, b = np.asarray(a), np.asarray(b)
+    err = 0.0
+    for j in range(b.shape[1]):
+        scale = max(np.abs(b[:, j]).max(), 1e-300)
+        err = max(err, np.abs(a[:, j] - b[:, j]).max() / scale if scale > 1e-12 else
+                  np.abs(a[:, j] - b[:, j]).max())
+    return err
+
+
+def free_cfg(n, L, **kw):
+    c = {"n": n, "L": L, "nu": 0.02, "eta": 1e-2, "dt_fixed": 1e-3, "mean_mode": "fixed"}
+    c.update(kw)
+    return c
+
+
+GRIDS = [((16, 16, 16), (2 * math.pi,) * 3), ((24, 16, 12), (3.0, 2.0, 1.5)),
+         ((48, 36, 24), (4.0, 3.0, 2.0)), ((8, 32, 18), (1.0, 4.0, 2.25))]
+
+
+@pytest.mark.parametrize("n,L", GRIDS)
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_transform_round_trip(fl, n, L, prec):
+    """set_state (r2c x, y, z + 2/3 rule + projection) and get_state (c2r)."""
+    cfg = free_cfg(n, L)
+    u0 = workloads.random_field(n, seed=sum(n))
+    ref = oracle.Simulation(cfg, None)
+    ref.set_state(u0)
+    sim = fl.Solver(cfg, None, precision=prec)
+    sim.set_state(u0)
+    uh = sim.get_spectrum()
+    u, t, step = sim.get_state()
+    sim.close()
+    tol = 1e-13 if prec == "fp64" else 3e-6
+    assert rel_l2(uh, ref.uh) <= tol
+    assert rel_l2(u, ref.get_state()) <= tol
+    assert t == 0.0 and step == 0
+
+
+def test_device_in_and_out(fl):
+    """set_state / get_state with device arrays; the field's modes are all
+    inside the 2/3-rule set of this grid, so it comes back unchanged."""
+    import torch
+    n, L = (24, 32, 18), (3.0, 4.0, 2.25)
+    cfg = free_cfg(n, L)
+    u0 = workloads.shear_waves(n, L)
+    for prec, dt in (("fp64", torch.float64), ("fp32", torch.float32)):
+        sim = fl.Solver(cfg, None, precision=prec)
+        sim.set_state(torch.tensor(u0, dtype=dt, device="cuda"))
+        out = torch.empty((3,) + tuple(reversed(n)), dtype=dt, device="cuda")
+        sim.get_state_device(out)
+        sim.close()
+        tol = 1e-13 if prec == "fp64" else 3e-6
+        assert rel_l2(out.cpu().numpy(), u0) <= tol
+
+
+CASES = {
+    "tg_sphere_16": lambda: workloads.config_tg_sphere(16),
+    "insect_32": lambda: (dict(workloads.config_model_insect(32)[0]),
+                          workloads.model_insect((4.0, 4.0, 4.0), (32, 32, 32))),
+    "wing_48x36x24": lambda: ({"n": (48, 36, 24), "L": (4.0, 3.0, 2.0), "nu": 0.0125664,
+                               "eta": 2.5e-3, "cfl": 0.1, "mean_mode": "fixed",
+                               "init": ("random_smooth", 5)},
+                              dict(workloads.single_wing((4.0, 3.0, 2.0), (48, 36, 24)),
+                                   x_cntr=(2.0, 1.5, 1.0))),
+}
+
+
+def _initial(cfg):
+    if cfg["init"][0] == "uniform":
+        return workloads.initial_field(cfg) + 0.05 * workloads.random_smooth_field(cfg["n"], 1)
+    return workloads.initial_field(cfg)
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_physical_fields(fl, case):
+    """u, omega, chi, colour, u_s and u x omega - chi/C_eta (u - u_s) on the
+    grid (the fused x pass) against the oracle, at t = 0 and after 3 steps."""
+    cfg, ins = CASES[case]()
+    u0 = _initial(cfg)
+    sim = fl.Solver(cfg, ins, precision="fp64")
+    sim.set_state(u0)
+    ref = oracle.Simulation(cfg, ins)
+    ref.set_state(u0)
+    for nsteps in (0, 3):
+        if nsteps:
+            sim.step(nsteps)
+            ref.step(nsteps)
+        got = sim.debug_fields().cpu().numpy()
+        exp = oracle.Spectral(cfg).physical_fields(ref.uh, ref.t, ins)
+        for sl, name in ((slice(0, 3), "u"), (slice(3, 6), "omega"), (slice(11, 14), "nl")):
+            assert rel_l2(got[sl], exp[sl]) <= 1e-11, name
+        assert np.abs(got[6] - exp[6]).max() <= 1e-12, "chi"
+        solid = exp[6] > 1e-9
+        # where two parts give the same chi (the mirror plane) either colour is valid
+        assert (got[7][solid] == exp[7][solid]).mean() > 0.995, "colour"
+        same = solid & (got[7] == exp[7])
+        for c in range(3):
+            assert np.abs(got[8 + c][same] - exp[8 + c][same]).max(initial=0) <= 1e-12, "u_s"
+    sim.close()
+
+
+def test_c0_full_step_fp64(fl):
+    """Taylor-Green + fixed sphere, 32^3, FP64, dt = 1e-3, 20 steps."""
+    cfg, ins = workloads.config_tg_sphere(32)
+    u0 = workloads.initial_field(cfg)
+    sim = fl.Solver(cfg, ins, precision="fp64")
+    sim.set_state(u0)
+    sim.step(20)
+    rows, lost = sim.forces()
+    u, t, step = sim.get_state()
+    sim.close()
+    ref = oracle.Simulation(cfg, ins)
+    ref.set_state(u0)
+    ref_rows = ref.step(20)
+    assert step == 20 and lost == 0 and rows.shape == (20, 22)
+    assert abs(t - ref.t) <= 1e-15
+    assert rel_l2(u, ref.get_state()) <= 1e-11
+    assert rows_err(rows, ref_rows) <= 1e-10
+
+
+@pytest.mark.parametrize("case", ["insect_32", "wing_48x36x24"])
+def test_flapping_steps_fp64(fl, case):
+    """Moving wings, adaptive dt (CFL and dt <= C_eta), unsteady corrections."""
+    cfg, ins = CASES[case]()
+    u0 = _initial(cfg)
+    sim = fl.Solver(cfg, ins, precision="fp64")
+    sim.set_state(u0)
+    sim.step(12)
+    rows, _ = sim.forces()
+    u, t, step = sim.get_state()
+    sim.close()
+    ref = oracle.Simulation(cfg, ins)
+    ref.set_state(u0)
+    ref_rows = ref.step(12)
+    assert np.abs(rows[:, 1] - ref_rows[:, 1]).max() <= 1e-13 * ref_rows[:, 1].max()
+    assert rel_l2(u, ref.get_state()) <= 1e-10
+    assert rows_err(rows, ref_rows) <= 1e-8
+
+
+def test_fp32_matches_oracle(fl):
+    cfg, ins = CASES["insect_32"]()
+    u0 = _initial(cfg)
+    sim = fl.Solver(cfg, ins, precision="fp32")
+    sim.set_state(u0)
+    ref = oracle.Simulation(cfg, ins)
+    ref.set_state(u0)
+    sim.step(1)
+    ref_rows = ref.step(1)
+    assert rel_l2(sim.get_state()[0], ref.get_state()) <= 1e-5
+    sim.step(9)
+    ref_rows = np.vstack([ref_rows, ref.step(9)])
+    rows, _ = sim.forces()
+    assert rel_l2(sim.get_state()[0], ref.get_state()) <= 1e-4
+    assert rel_l2(rows[:, 2:20], ref_rows[:, 2:20]) <= 1e-4
+    sim.close()
+
+
+def test_relaxation_free_mean(fl):
+    """chi = 1 everywhere, u_s = 0, free mean: the AB2 relaxation recurrence."""
+    cfg = {"n": (8, 8, 8), "L": (2 * math.pi,) * 3, "nu": 0.01, "eta": 0.05, "dt_fixed": 0.004,
+           "mean_mode": "free"}
+    ins = workloads.sphere((0.0, 0.0, 0.0), 100.0, profile="cos")
+    u0 = np.array([0.3, -0.2, 0.5])
+    sim = fl.Solver(cfg, ins, precision="fp64")
+    sim.set_state(workloads.uniform(cfg["n"], u0))
+    sim.step(10)
+    hist = [u0, u0 * (1 - 0.004 / 0.05)]
+    for _ in range(9):
+        hist.append(hist[-1] - 0.08 * (1.5 * hist[-1] - 0.5 * hist[-2]))
+    got = sim.get_state()[0].mean(axis=(1, 2, 3))
+    sim.close()
+    assert np.abs(got - hist[10]).max() <= 1e-14
+
+
+def test_graph_and_eager_are_identical(fl):
+    cfg, ins = CASES["insect_32"]()
+    u0 = _initial(cfg)
+    out = []
+    for g in (1, 0):
+        c = dict(cfg, use_graph=g)
+        sim = fl.Solver(c, ins, precision="fp32")
+        sim.set_state(u0)
+        sim.step(5)
+        out.append(sim.get_state()[0])
+        sim.close()
+    assert np.array_equal(out[0], out[1])
+
+
+def test_nonfinite_state_is_reported(fl):
+    cfg, ins = CASES["insect_32"]()
+    u0 = _initial(cfg)
+    bad = u0.copy()
+    bad[1, 3, 4, 5] = np.nan
+    sim = fl.Solver(cfg, ins, precision="fp32")
+    sim.set_state(bad)
+    sim.step(2)
+    with pytest.raises(fl.FlusiError) as e:
+        sim.sync()
+    assert e.value.code == fl.FLUSI_ENONFINITE
+    with pytest.raises(fl.FlusiError) as e:
+        sim.step(1)
+    assert e.value.code == fl.FLUSI_ESTATE
+    sim.set_state(u0)
+    sim.step(1)
+    sim.sync()
+    rows, _ = sim.forces()
+    assert rows.shape[0] == 1 and np.isfinite(rows).all()
+    sim.close()
+
+
+def test_force_ring_drain(fl):
+    cfg, ins = CASES["insect_32"]()
+    cfg = dict(cfg, force_ring=4)
+    u0 = _initial(cfg)
+    sim = fl.Solver(cfg, ins, precision="fp32")
+    sim.set_state(u0)
+    sim.step(3)
+    rows, lost = sim.forces()
+    assert rows.shape[0] == 3 and lost == 0
+    sim.step(10)
+    rows2, lost2 = sim.forces()
+    assert rows2.shape[0] == 4 and lost2 == 6
+    assert np.all(np.diff(rows2[:, 0]) > 0) and rows2[0, 0] > rows[-1, 0]
+    rows3, lost3 = sim.forces()
+    assert rows3.shape[0] == 0 and lost3 == 0
+    sim.close()
+
+
+def test_bench_configuration_sampled(fl):
+    """The 512^3 FP32 model-insect step in the benchmark's launch
+    configuration, checked where the oracle can follow point by point:
+    the mask and solid velocity at sampled grid points near the insect, the
+    band-limited initial field at sampled points, and the kinetic energy of
+    the first force row against its closed form."""
+    import torch
+    cfg, ins = workloads.config_model_insect(512)
+    n, L = cfg["n"], cfg["L"]
+    u0 = workloads.shear_waves(n, L, mean=cfg["u_inf"]).astype(np.float32)
+    sim = fl.Solver(cfg, ins, precision="fp32")
+    sim.set_state(u0)
+    del u0
+    rng = np.random.default_rng(512)
+    pts = np.column_stack([rng.integers(0, 512, 4000) for _ in range(3)])
+    # the insect sits at the box centre: body |x - 2| <= 0.5, wings |y - 2| <= 1.15
+    near = np.column_stack([rng.integers(lo, hi, 4000)
+                            for lo, hi in ((192, 320), (128, 384), (236, 276))])
+    pts = np.vstack([pts, near])
+    f = sim.debug_fields()
+    vals = f[:, pts[:, 2], pts[:, 1], pts[:, 0]].double().cpu().numpy()
+    del f
+    torch.cuda.empty_cache()
+    exact = workloads.shear_waves(n, L, mean=cfg["u_inf"], points=pts)
+    assert np.abs(vals[0:3] - exact).max() <= 2e-5
+    dx = L[0] / n[0]
+    h = dx
+    for i, (ix, iy, iz) in enumerate(pts):
+        chi, col, us = oracle.solid_at(ins, 0.0, h, (ix * dx, iy * dx, iz * dx))
+        assert abs(vals[6, i] - chi) <= 2e-5
+        if chi > 1e-3 and vals[7, i] == col:
+            assert np.abs(vals[8:11, i] - us).max() <= 1e-4
+    assert (vals[6] > 0.5).sum() > 20
+    sim.step(1)
+    rows, _ = sim.forces()
+    ek = workloads.shear_waves_energy(L, mean=cfg["u_inf"])
+    assert abs(rows[0, 20] - ek) <= 1e-5 * ek
+    assert rows[0, 1] == pytest.approx(min(0.1 * dx / rows[0, 21], cfg["eta"]), rel=1e-12)
+    sim.close()

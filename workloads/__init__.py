@@ -78,6 +78,39 @@ def taylor_green_2d(n, L=(2 * math.pi,) * 3, amplitude=1.0):
     return u
 
 
+SHEAR_WAVES = ((0.6, (0, 3, 5), 0.3), (0.4, (7, 0, -2), 1.1), (0.5, (4, 9, 0), -0.7))
+
+
+def shear_waves(n, L, mean=(0.0, 0.0, 0.0), points=None):
+    """Divergence-free band-limited field: component c is a single Fourier mode
+    that does not depend on coordinate c, amplitude a_c, integer wavenumbers
+    SHEAR_WAVES[c][1], phase SHEAR_WAVES[c][2], plus a uniform mean.  With
+    `points` (an (m, 3) integer array of (ix, iy, iz)) it returns the values
+    there, shape (3, m); otherwise the whole grid [3][nz][ny][nx]."""
+    nx, ny, nz = n
+    if points is not None:
+        fx = points[:, 0] / nx
+        fy = points[:, 1] / ny
+        fz = points[:, 2] / nz
+    else:
+        fz = (np.arange(nz) / nz)[:, None, None]
+        fy = (np.arange(ny) / ny)[None, :, None]
+        fx = (np.arange(nx) / nx)[None, None, :]
+    shape = (len(points),) if points is not None else (nz, ny, nx)
+    out = np.empty((3,) + shape)
+    trig = (np.sin, np.cos, np.sin)
+    for c, (a, m, ph) in enumerate(SHEAR_WAVES):
+        arg = 2 * math.pi * (m[0] * fx + m[1] * fy + m[2] * fz) + ph
+        out[c] = mean[c] + a * trig[c](arg)
+    return out
+
+
+def shear_waves_energy(L, mean=(0.0, 0.0, 0.0)):
+    """1/2 integral |u|^2 over the box for shear_waves: each mode averages a^2/2."""
+    vol = L[0] * L[1] * L[2]
+    return 0.5 * vol * sum(mean[c] ** 2 + SHEAR_WAVES[c][0] ** 2 / 2 for c in range(3))
+
+
 def uniform(n, u0):
     nx, ny, nz = n
     u = np.zeros((3, nz, ny, nx))
