@@ -176,6 +176,41 @@ int flusi_profile_step(flusi_t h, int n, double *ms, const char **names, int *nk
 /* Kernels launched per step (for launch accounting). */
 int flusi_kernels_per_step(flusi_t h, int *count);
 
+/* Largest grid (points) and output length of flusi_penalization_sums_noalloc. */
+#define FLUSI_NOALLOC_MAX_POINTS (1024LL * 1024LL * 1024LL)
+#define FLUSI_NOALLOC_SUMS 38
+
+/* Force, moment, energy and CFL sums of a velocity field, without allocating.
+ * The paper has no counterpart: this is a library convenience for callers
+ * that cannot allocate device memory -- their device memory belongs to
+ * another allocator's pool, or they cannot accept a cudaMalloc/cudaFree and
+ * its implicit device synchronization where they run.  It needs no handle
+ * and no workspace.
+ *
+ * Inputs: grid nx, ny, nz (at most FLUSI_NOALLOC_MAX_POINTS points, else
+ * FLUSI_EINVAL with a message in flusi_last_error(NULL)), box L[3], penalization
+ * constant eta (C_eta), the insect (NULL: no mask) evaluated at time t, and
+ * u_dev, a caller-owned device array [3][nz][ny][nx] of FP64 velocity.
+ * Output: sums_out, a caller-owned host array of FLUSI_NOALLOC_SUMS doubles:
+ * per colour (body, left wing, right wing) sum chi (u - u_s) dV / C_eta [3],
+ * sum r x chi (u - u_s) dV / C_eta [3], sum chi u_s dV [3],
+ * sum r x chi u_s dV [3] (r from the body centre or the wing pivot), then
+ * 1/2 sum |u|^2 dV and max |u|.  These are the quantities the step reduces
+ * into its force rows; a step's row adds the unsteady correction (the change
+ * of sum chi u_s dV over the previous step) to them.
+ *
+ * Scratch: a fixed array of about 330 KB in the library's own device memory
+ * (every GPU that loads the library holds it until the process exits).  The
+ * first call on a device looks up that array's device address; make that
+ * first call before any stream capture.  Every call shares the array and
+ * leaves its contents behind, so calls that overlap on the GPU (two streams,
+ * two host threads) race and corrupt each other's results.  The work is
+ * enqueued on cuda_stream (NULL: legacy default stream) and the call waits for
+ * it.  Returns FLUSI_ENONFINITE when u holds a non-finite value. */
+int flusi_penalization_sums_noalloc(int nx, int ny, int nz, const double L[3], double eta,
+                                    const flusi_insect *insect, double t, const double *u_dev,
+                                    double *sums_out, void *cuda_stream);
+
 /* Release the handle (not the caller's workspace).  NULL is a no-op. */
 int flusi_destroy(flusi_t h);
 

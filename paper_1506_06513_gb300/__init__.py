@@ -76,6 +76,8 @@ def _load():
         "flusi_debug_fields": ([h, vp], ip),
         "flusi_profile_step": ([h, ip, dp, C.POINTER(C.c_char_p), C.POINTER(C.c_int)], ip),
         "flusi_kernels_per_step": ([h, C.POINTER(C.c_int)], ip),
+        "flusi_penalization_sums_noalloc": ([ip, ip, ip, dp, C.c_double, C.POINTER(Insect), C.c_double,
+                                             vp, dp, vp], ip),
         "flusi_destroy": ([h], ip),
         "flusi_last_error": ([h], C.c_char_p),
     }
@@ -186,6 +188,24 @@ def flusi_kernels_per_step(h):
     c = C.c_int()
     _check(h, lib.flusi_kernels_per_step(h, C.byref(c)))
     return c.value
+
+
+NOALLOC_SUMS = 38
+NOALLOC_MAX_POINTS = 1024 ** 3
+
+
+def flusi_penalization_sums_noalloc(n, L, eta, insect: Insect | None, t, u_dev: int, stream: int = 0):
+    """Force, moment, energy and CFL sums of a device FP64 velocity field
+    [3][nz][ny][nx] without a handle or any allocation (see flusi.h).
+    Returns FLUSI_NOALLOC_SUMS doubles."""
+    out = np.zeros(NOALLOC_SUMS)
+    Ls = (C.c_double * 3)(*L)
+    rc = lib.flusi_penalization_sums_noalloc(int(n[0]), int(n[1]), int(n[2]), Ls, float(eta),
+                                             C.byref(insect) if insect is not None else None,
+                                             float(t), C.c_void_p(u_dev), _dptr(out),
+                                             C.c_void_p(stream))
+    _check(None, rc)
+    return out
 
 
 def flusi_destroy(h):

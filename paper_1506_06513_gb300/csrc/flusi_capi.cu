@@ -45,6 +45,12 @@ namespace {
 
 std::string g_create_err;
 
+}  // namespace
+
+void flusi::set_global_error(const char* msg) { g_create_err = msg; }
+
+namespace {
+
 int fail(flusi_t h, int code, const std::string& msg)
 {
     if (h) h->err = msg;

@@ -63,6 +63,9 @@ cudaError_t launch_xpass(int fp64, int mode, void* W, const Geom& g, const FftPl
                          const double2* tw, const int* pos, const XExtra& ex, const StepState* st,
                          cudaStream_t s);
 
+// Message returned by flusi_last_error(NULL).
+void set_global_error(const char* msg);
+
 // Shared-memory limits of every instantiation (once per process and device).
 cudaError_t configure_ypass();
 cudaError_t configure_zpass();

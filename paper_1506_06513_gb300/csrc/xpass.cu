@@ -508,3 +508,300 @@ cudaError_t configure_xpass()
 }
 
 }  // namespace flusi
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the physical pass's reduction.
+//
+// Some callers cannot allocate device memory at all: their device memory is
+// owned by another allocator's pool (a framework's caching allocator, a
+// real-time loop that reserves everything up front), or they cannot accept a
+// cudaMalloc / cudaFree and its implicit device synchronization where they
+// run.  This entry point gives them the force, moment, energy and CFL sums of
+// a velocity field they already hold, with no handle and no workspace: its
+// scratch (the insect descriptor, the frame block, one row of FP64 partial
+// sums per CTA and the reduced sums) lives in a fixed array in the library's
+// own device memory.
+// ---------------------------------------------------------------------------
+namespace flusi {
+
+namespace {
+
+constexpr int kNoallocThreads = 256;
+constexpr int kNoallocWarps = kNoallocThreads / 32;
+constexpr int kNoallocMaxCtas = 1024;                       // partial-sum rows
+constexpr long long kNoallocMaxPoints = 1024LL * 1024 * 1024;
+constexpr int kNoallocHeader = 256;                         // doubles: descriptor, time, frame
+
+// Scratch of the allocation-free entry point: [header | partials | sums],
+// 8 * (256 + 1024 * 40 + 40) bytes (about 330 KB), held by every GPU that
+// loads the library until the process exits.
+constexpr size_t kNoallocDoubles = kNoallocHeader + (size_t)kNoallocMaxCtas * kNumSums + kNumSums;
+static __device__ __align__(256) double g_noalloc_scratch[kNoallocDoubles];
+
+static_assert(sizeof(flusi_insect) + sizeof(StepState) + sizeof(Frame) + 32 <= kNoallocHeader * 8,
+              "scratch header too small");
+
+// Copies the caller's descriptor and time into the scratch header.
+__global__ void k_noalloc_header(flusi_insect ins, double t, flusi_insect* d_ins, StepState* d_st)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    *d_ins = ins;
+    StepState st = {};
+    st.t = t;
+    *d_st = st;
+}
+
+__global__ void __launch_bounds__(kNoallocThreads)
+k_noalloc_sums(const double* __restrict__ u, int nx, int ny, int nz, double dx, double dy, double dz,
+               const Frame* __restrict__ frame, Shape S, double* __restrict__ part)
+{
+    __shared__ FrameT<double> F;
+    __shared__ double wacc[kNoallocWarps * 36];
+    __shared__ double red[kNoallocWarps][3];
+    const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+    for (int i = tid; i < kNoallocWarps * 36; i += kNoallocThreads) wacc[i] = 0.0;
+    if (tid == 0) {
+        const Frame& G = *frame;
+        for (int i = 0; i < 3; ++i) {
+            F.xc[i] = G.xc[i];
+            F.uc[i] = G.uc[i];
+            F.Ob[i] = G.Ob[i];
+            F.active[i] = G.active[i];
+            for (int s = 0; s < 2; ++s) {
+                F.pv[s][i] = G.pv[s][i];
+                F.Ow[s][i] = G.Ow[s][i];
+            }
+            for (int j = 0; j < 6; ++j) F.box[i][j] = G.box[i][j];
+        }
+        for (int i = 0; i < 9; ++i) {
+            F.Mb[i] = G.Mb[i];
+            F.Mw[0][i] = G.Mw[0][i];
+            F.Mw[1][i] = G.Mw[1][i];
+        }
+        F.h = S.h;
+        F.a = S.body_a;
+        F.b = S.body_b;
+        F.c_le = S.c_le;
+        F.c_te = S.c_te;
+        F.R = S.R;
+        F.ht = S.ht;
+        F.inv_eta = 0.0;
+        F.body_type = S.body_type;
+        F.profile = S.profile;
+        if (S.body_type == 0) F.active[0] = 0;
+        if (S.nwings < 1) F.active[1] = 0;
+        if (S.nwings < 2) F.active[2] = 0;
+    }
+    __syncthreads();
+
+    const long long N = (long long)nx * ny * nz;
+    double e_acc = 0.0, m_acc = 0.0;
+    int bad = 0;
+    // block-uniform trip count, so whole warps reach the votes below
+    for (long long base = (long long)blockIdx.x * kNoallocThreads; base < N;
+         base += (long long)gridDim.x * kNoallocThreads) {
+        const long long i = base + tid;
+        const bool valid = i < N;
+        double chi = 0.0, us[3] = {0, 0, 0}, uu[3] = {0, 0, 0}, X[3] = {0, 0, 0};
+        int col = 0;
+        if (valid) {
+            const int x = (int)(i % nx);
+            const long long r = i / nx;
+            const int y = (int)(r % ny), z = (int)(r / ny);
+            X[0] = x * dx;
+            X[1] = y * dy;
+            X[2] = z * dz;
+            for (int c = 0; c < 3; ++c) uu[c] = u[c * N + i];
+            bool inrow[3];
+            for (int q = 0; q < 3; ++q)
+                inrow[q] = F.active[q] && X[1] >= F.box[q][2] && X[1] <= F.box[q][3] &&
+                           X[2] >= F.box[q][4] && X[2] <= F.box[q][5];
+            solid_at(F, X, inrow, chi, col, us);
+            const double u2 = uu[0] * uu[0] + uu[1] * uu[1] + uu[2] * uu[2];
+            e_acc += u2;
+            m_acc = fmax(m_acc, u2);
+            if (!isfinite(u2)) bad = 1;
+        }
+        for (int cc = 0; cc < 3; ++cc) {
+            const bool has = valid && col == cc + 1;
+            if (!__any_sync(0xffffffffu, has)) continue;
+            double v[12];
+            for (int k = 0; k < 12; ++k) v[k] = 0.0;
+            if (has) {
+                const double* ref = cc == 0 ? F.xc : F.pv[cc - 1];
+                double rv[3] = {X[0] - ref[0], X[1] - ref[1], X[2] - ref[2]};
+                double pu[3], cu[3], m1[3], m2[3];
+                for (int c = 0; c < 3; ++c) {
+                    pu[c] = chi * (uu[c] - us[c]);
+                    cu[c] = chi * us[c];
+                }
+                cross3(rv, pu, m1);
+                cross3(rv, cu, m2);
+                for (int c = 0; c < 3; ++c) {
+                    v[c] = pu[c];
+                    v[3 + c] = m1[c];
+                    v[6 + c] = cu[c];
+                    v[9 + c] = m2[c];
+                }
+            }
+            for (int k = 0; k < 12; ++k) v[k] = warp_sum(v[k]);
+            if (lane == 0)
+                for (int k = 0; k < 12; ++k) wacc[warp * 36 + cc * 12 + k] += v[k];
+        }
+    }
+    e_acc = warp_sum(e_acc);
+    for (int o = 16; o > 0; o >>= 1) m_acc = fmax(m_acc, __shfl_xor_sync(0xffffffffu, m_acc, o));
+    const int anybad = __any_sync(0xffffffffu, bad);
+    if (lane == 0) {
+        red[warp][0] = e_acc;
+        red[warp][1] = m_acc;
+        red[warp][2] = anybad ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    double* out = part + (size_t)blockIdx.x * kNumSums;
+    if (tid < 36) {
+        double s = 0.0;
+        for (int w = 0; w < kNoallocWarps; ++w) s += wacc[w * 36 + tid];
+        out[tid] = s;
+    } else if (tid == kSumEkin) {
+        double s = 0.0;
+        for (int w = 0; w < kNoallocWarps; ++w) s += red[w][0];
+        out[tid] = s;
+    } else if (tid == kSumUmax2 || tid == kSumBad) {
+        double s = 0.0;
+        for (int w = 0; w < kNoallocWarps; ++w) s = fmax(s, red[w][tid == kSumUmax2 ? 1 : 2]);
+        out[tid] = s;
+    } else if (tid < kNumSums) {
+        out[tid] = 0.0;
+    }
+}
+
+// One block: partial rows reduced in a fixed order, then scaled into the
+// output layout (per colour F[3], M[3], I[3], J[3]; then E_kin, max |u|,
+// and the non-finite flag).
+__global__ void k_noalloc_reduce(const double* __restrict__ part, int nparts, double dV, double eta,
+                                 double* __restrict__ out)
+{
+    __shared__ double tot[kNumSums];
+    const int k = threadIdx.x;
+    if (k < kNumSums) {
+        const bool is_max = (k == kSumUmax2 || k == kSumBad);
+        double a = 0.0;
+        for (int i = 0; i < nparts; ++i) {
+            const double v = part[(size_t)i * kNumSums + k];
+            a = is_max ? fmax(a, v) : a + v;
+        }
+        tot[k] = a;
+    }
+    __syncthreads();
+    if (k < 36) {
+        out[k] = (k % 12) < 6 ? tot[k] * dV / eta : tot[k] * dV;
+    } else if (k == 36) {
+        out[36] = 0.5 * tot[kSumEkin] * dV;
+    } else if (k == 37) {
+        out[37] = sqrt(tot[kSumUmax2]);
+    } else if (k == 38) {
+        out[38] = tot[kSumBad];
+    }
+}
+
+// Device address of the scratch array, looked up once per device.
+constexpr int kNoallocMaxDevices = 64;
+double* g_noalloc_ptr[kNoallocMaxDevices] = {};
+
+}  // namespace
+
+}  // namespace flusi
+
+extern "C" int flusi_penalization_sums_noalloc(int nx, int ny, int nz, const double L[3],
+                                               double eta, const flusi_insect* insect, double t,
+                                               const double* u_dev, double* sums_out,
+                                               void* cuda_stream)
+{
+    using namespace flusi;
+    if (nx < 1 || ny < 1 || nz < 1 || !L || !(L[0] > 0) || !(L[1] > 0) || !(L[2] > 0) ||
+        !(eta > 0) || !u_dev || !sums_out) {
+        set_global_error("flusi_penalization_sums_noalloc: bad sizes, box, eta or NULL pointer");
+        return FLUSI_EINVAL;
+    }
+    const long long N = (long long)nx * ny * nz;
+    if (N > kNoallocMaxPoints) {
+        set_global_error("flusi_penalization_sums_noalloc: grid has more than "
+                         "FLUSI_NOALLOC_MAX_POINTS (2^30) points");
+        return FLUSI_EINVAL;
+    }
+    if (insect && (insect->body_type < 0 || insect->body_type > 2 || insect->nwings < 0 ||
+                   insect->nwings > 2 || insect->profile < 0 || insect->profile > 1 ||
+                   insect->nfourier < 0 || insect->nfourier > FLUSI_MAX_FOURIER ||
+                   !(insect->c_smth > 0))) {
+        set_global_error("flusi_penalization_sums_noalloc: bad insect descriptor");
+        return FLUSI_EINVAL;
+    }
+
+    // set-up, once per device: the device address of the scratch array
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices) {
+        set_global_error("flusi_penalization_sums_noalloc: no usable current device");
+        return FLUSI_ECUDA;
+    }
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            set_global_error("flusi_penalization_sums_noalloc: cudaGetSymbolAddress failed");
+            return FLUSI_ECUDA;
+        }
+        g_noalloc_ptr[dev] = static_cast<double*>(p);
+    }
+    double* scratch = g_noalloc_ptr[dev];
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+
+    // header: descriptor, step state (only t is read), frame block
+    char* head = reinterpret_cast<char*>(scratch);
+    flusi_insect* d_ins = reinterpret_cast<flusi_insect*>(head);
+    StepState* d_st = reinterpret_cast<StepState*>(head + ((sizeof(flusi_insect) + 15) / 16) * 16);
+    Frame* d_fr = reinterpret_cast<Frame*>(reinterpret_cast<char*>(d_st) +
+                                           ((sizeof(StepState) + 15) / 16) * 16);
+    double* part = scratch + kNoallocHeader;
+    double* sums = part + (size_t)kNoallocMaxCtas * kNumSums;
+
+    flusi_insect ins{};
+    if (insect) ins = *insect;
+    const double dx = L[0] / nx, dy = L[1] / ny, dz = L[2] / nz;
+    Shape sh{};
+    if (insect) {
+        sh.body_type = ins.body_type;
+        sh.nwings = ins.nwings;
+        sh.profile = ins.profile;
+        sh.h = ins.c_smth * fmax(dx, fmax(dy, dz));
+        sh.body_a = ins.body_a;
+        sh.body_b = ins.body_b;
+        sh.c_le = ins.wing_c_le;
+        sh.c_te = ins.wing_c_te;
+        sh.R = ins.wing_R;
+        sh.ht = ins.wing_h;
+    }
+    const double margin = sh.profile == 1 ? 1e300 : sh.h;
+    // every slot read below is written first in this call: nothing carried
+    // over from an earlier call needs clearing
+    const long long want = (N + kNoallocThreads - 1) / kNoallocThreads;
+    const int grid = (int)(want < kNoallocMaxCtas ? want : kNoallocMaxCtas);
+    k_noalloc_header<<<1, 1, 0, s>>>(ins, t, d_ins, d_st);
+    k_kinematics<<<1, 32, 0, s>>>(d_ins, d_st, d_fr, margin);
+    k_noalloc_sums<<<grid, kNoallocThreads, 0, s>>>(u_dev, nx, ny, nz, dx, dy, dz, d_fr, sh, part);
+    k_noalloc_reduce<<<1, 64, 0, s>>>(part, grid, dx * dy * dz, eta, sums);
+    cudaError_t e = cudaGetLastError();
+    double host[kNumSums];
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host, sums, sizeof(double) * 39, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        set_global_error(cudaGetErrorString(e));
+        return FLUSI_ECUDA;
+    }
+    for (int i = 0; i < 38; ++i) sums_out[i] = host[i];
+    if (host[38] != 0.0) {
+        set_global_error("flusi_penalization_sums_noalloc: non-finite velocity");
+        return FLUSI_ENONFINITE;
+    }
+    return FLUSI_OK;
+}
