@@ -123,6 +123,20 @@ struct StepCoef {
 
 __host__ __device__ inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
 
+// Asynchronous global -> shared copies of one complex value (8 or 16 bytes):
+// a tile's loads are all issued back to back, then waited for at once.
+template <typename T>
+__device__ __forceinline__ void cp_async_cplx(cplx<T>* smem_dst, const cplx<T>* gmem_src)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    if (sizeof(cplx<T>) == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src));
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem_src));
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // Signed mode of a stored spectral index j in [0, M) with M = 2K + 1.
 __host__ __device__ __forceinline__ int mode_of(int j, int K) { return j <= K ? j : j - (2 * K + 1); }
 // FFT frequency slot of a stored index j for a length-n transform.

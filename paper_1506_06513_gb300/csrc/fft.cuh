@@ -94,6 +94,19 @@ template <typename T, bool INV> struct Dft<T, 3, INV> {
     }
 };
 
+// v[t] *= w^(k t) for t = 1..R-1 from the table (conjugated for the inverse):
+// tw[k * step] holds w^k.
+template <typename T, int R, bool INV>
+__device__ __forceinline__ void twiddle_table(cplx<T>* v, const cplx<T>* tw, int kstep)
+{
+#pragma unroll
+    for (int t = 1; t < R; ++t) {
+        cplx<T> w = tw[kstep * t];
+        if (INV) w.y = -w.y;
+        v[t] = cmul(v[t], w);
+    }
+}
+
 template <typename T, int R, bool INV, bool DIF>
 __device__ __forceinline__ void fft_stage(cplx<T>* buf, int ld, int col, int jt, int P, int nbf,
                                           int m, int msh, int ls, int tstep, const cplx<T>* tw)
@@ -108,14 +121,7 @@ __device__ __forceinline__ void fft_stage(cplx<T>* buf, int ld, int col, int jt,
 #pragma unroll
         for (int t = 0; t < R; ++t) v[t] = p[t * step];
         if (DIF) Dft<T, R, INV>::run(v);
-        if (k != 0) {
-#pragma unroll
-            for (int t = 1; t < R; ++t) {
-                cplx<T> w = tw[k * t * tstep];
-                if (INV) w.y = -w.y;
-                v[t] = cmul(v[t], w);
-            }
-        }
+        if (k != 0) twiddle_table<T, R, INV>(v, tw, k * tstep);
         if (!DIF) Dft<T, R, INV>::run(v);
 #pragma unroll
         for (int t = 0; t < R; ++t) p[t * step] = v[t];
@@ -123,15 +129,16 @@ __device__ __forceinline__ void fft_stage(cplx<T>* buf, int ld, int col, int jt,
     __syncthreads();
 }
 
+// Stages s in [s0, s1): ascending for DIF, descending for DIT.
 template <typename T, bool INV, bool DIF>
 __device__ __forceinline__ void fft_run(cplx<T>* buf, int C, int ld, const FftPlan& plan,
-                                        const cplx<T>* tw)
+                                        const cplx<T>* tw, int s0, int s1)
 {
     const int P = blockDim.x / C;
     const int col = threadIdx.x % C;
     const int jt = threadIdx.x / C;
-    for (int i = 0; i < plan.nst; ++i) {
-        const int s = DIF ? i : plan.nst - 1 - i;
+    for (int i = s0; i < s1; ++i) {
+        const int s = DIF ? i : s0 + s1 - 1 - i;
         const int R = plan.radix[s];
         const int nbf = plan.n / R;
         const int m = plan.m[s], msh = plan.mshift[s], ls = plan.ls[s], ts = plan.tstep[s];
@@ -147,16 +154,18 @@ __device__ __forceinline__ void fft_run(cplx<T>* buf, int C, int ld, const FftPl
 // Natural order in, digit-reversed out (row pos[f] holds frequency/point f).
 // Columns 0..C-1, C must divide blockDim.x; all threads must call.
 template <typename T, bool INV>
-__device__ void fft_dif(cplx<T>* buf, int C, int ld, const FftPlan& plan, const cplx<T>* tw)
+__device__ void fft_dif(cplx<T>* buf, int C, int ld, const FftPlan& plan, const cplx<T>* tw,
+                        int s0 = 0, int s1 = -1)
 {
-    fft_run<T, INV, true>(buf, C, ld, plan, tw);
+    fft_run<T, INV, true>(buf, C, ld, plan, tw, s0, s1 < 0 ? plan.nst : s1);
 }
 
 // Digit-reversed in (row pos[f] holds f), natural order out.
 template <typename T, bool INV>
-__device__ void fft_dit(cplx<T>* buf, int C, int ld, const FftPlan& plan, const cplx<T>* tw)
+__device__ void fft_dit(cplx<T>* buf, int C, int ld, const FftPlan& plan, const cplx<T>* tw,
+                        int s0 = 0, int s1 = -1)
 {
-    fft_run<T, INV, false>(buf, C, ld, plan, tw);
+    fft_run<T, INV, false>(buf, C, ld, plan, tw, s0, s1 < 0 ? plan.nst : s1);
 }
 
 // Copy the twiddle table (FP64, global; ntw entries exp(-2 pi i j / ntw))

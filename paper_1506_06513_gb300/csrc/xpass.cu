@@ -115,8 +115,147 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
+// c2r pre-processing: Z[k] = (X[k] + X*[m]) + i (X[k] - X*[m]) w^{-k} with the
+// mirror value Xm = X[nh - k].
+template <typename T>
+__device__ __forceinline__ cplx<T> c2r_pre(cplx<T> Xk, cplx<T> Xm, cplx<T> wk)
+{
+    const cplx<T> s = cadd(Xk, cconj(Xm)), d = csub(Xk, cconj(Xm));
+    return cadd(s, cmuli(cmul(d, cconj(wk))));
+}
+
+// r2c post-processing: X[k] = E + w^k O, E = (Z[k] + Z*[m])/2, O = -i (Z[k] - Z*[m])/2.
+template <typename T>
+__device__ __forceinline__ cplx<T> r2c_post(cplx<T> Zk, cplx<T> Zm, cplx<T> wk)
+{
+    const cplx<T> zc = cconj(Zm);
+    const cplx<T> E = cscale(cadd(Zk, zc), T(0.5));
+    const cplx<T> O = cscale(cmulmi(csub(Zk, zc)), T(0.5));
+    return cadd(E, cmul(wk, O));
+}
+
+// The first inverse (DIF) stage of the length-nh transforms fused with the
+// c2r pre-processing.  Stage 0 has butterflies j < m0 on rows j + m0 t; the
+// mirror rows nh - (j + m0 t) belong to butterfly m0 - j, so one thread takes
+// the pair (j, m0 - j) and reads only rows k < Mx (the kept modes; buf rows
+// beyond Mx are not read).  tws is the length-nx table w^k = exp(-2 pi i k/nx).
+template <typename T, int R>
+__device__ __forceinline__ void x_first_inverse(cplx<T>* buf, int C, int ld, int Mx,
+                                                const FftPlan& plan, const cplx<T>* tws)
+{
+    const int m0 = plan.m[0], ts = plan.tstep[0];
+    const int npairs = m0 / 2 + 1;
+    for (int i = threadIdx.x; i < C * npairs; i += blockDim.x) {
+        const int col = i / npairs, j = i - col * npairs;
+        const int jp = m0 - j;
+        const bool two = (jp != j) && (jp < m0);
+        cplx<T> xj[R], xp[R], a[R], b[R];
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            const int k = j + m0 * t;
+            xj[t] = k < Mx ? buf[k * ld + col] : mkc<T>(0, 0);
+            const int kp = jp + m0 * t;
+            xp[t] = (two && kp < Mx) ? buf[kp * ld + col] : mkc<T>(0, 0);
+        }
+        if (j == 0) xj[0].y = T(0);   // a real line has a real mean
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            cplx<T> xm;
+            if (j == 0) xm = t == 0 ? mkc<T>(0, 0) : xj[R - t];
+            else xm = two ? xp[R - 1 - t] : xj[R - 1 - t];
+            a[t] = c2r_pre<T>(xj[t], xm, tws[j + m0 * t]);
+            b[t] = c2r_pre<T>(xp[t], xj[R - 1 - t], tws[(two ? jp : 0) + m0 * t]);
+        }
+        Dft<T, R, true>::run(a);
+        if (j != 0) twiddle_table<T, R, true>(a, tws, j * ts);
+#pragma unroll
+        for (int q = 0; q < R; ++q) buf[(j + m0 * q) * ld + col] = a[q];
+        if (two) {
+            Dft<T, R, true>::run(b);
+            twiddle_table<T, R, true>(b, tws, jp * ts);
+#pragma unroll
+            for (int q = 0; q < R; ++q) buf[(jp + m0 * q) * ld + col] = b[q];
+        }
+    }
+    __syncthreads();
+}
+
+// The last forward (DIT) stage fused with the r2c post-processing and the
+// store of the kept x-modes (zeros in the row padding Mx..Mxp-1).
+template <typename T, int R>
+__device__ __forceinline__ void x_last_forward(const cplx<T>* buf, int C, int ld, int Mx, int Mxp,
+                                               const FftPlan& plan, const cplx<T>* tws,
+                                               cplx<T>* W, int comp0, int lgRB, int row0,
+                                               int nrows)
+{
+    const int m0 = plan.m[0], ts = plan.tstep[0];
+    const int npairs = m0 / 2 + 1;
+    const int RB = 1 << lgRB;
+    for (int i = threadIdx.x; i < C * npairs; i += blockDim.x) {
+        const int col = i / npairs, j = i - col * npairs;
+        const int f = col >> lgRB, r = row0 + (col & (RB - 1));
+        if (r >= nrows) continue;
+        const int jp = m0 - j;
+        const bool two = (jp != j) && (jp < m0);
+        cplx<T> a[R], b[R];
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            a[t] = buf[(j + m0 * t) * ld + col];
+            b[t] = two ? buf[(jp + m0 * t) * ld + col] : mkc<T>(0, 0);
+        }
+        if (j != 0) twiddle_table<T, R, false>(a, tws, j * ts);
+        Dft<T, R, false>::run(a);
+        if (two) {
+            twiddle_table<T, R, false>(b, tws, jp * ts);
+            Dft<T, R, false>::run(b);
+        }
+        cplx<T>* out = W + ((size_t)(comp0 + f) * nrows + r) * Mxp;
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const int k = j + m0 * q;
+            if (k < Mxp) {
+                cplx<T> zm;
+                if (j == 0) zm = q == 0 ? a[0] : a[R - q];
+                else zm = two ? b[R - 1 - q] : a[R - 1 - q];
+                out[k] = k < Mx ? r2c_post<T>(a[q], zm, tws[k]) : mkc<T>(0, 0);
+            }
+            if (two) {
+                const int kp = jp + m0 * q;
+                if (kp < Mxp) out[kp] = kp < Mx ? r2c_post<T>(b[q], a[R - 1 - q], tws[kp]) : mkc<T>(0, 0);
+            }
+        }
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__device__ __forceinline__ void x_first_inverse_any(cplx<T>* buf, int C, int ld, int Mx,
+                                                    const FftPlan& plan, const cplx<T>* tws)
+{
+    switch (plan.radix[0]) {
+    case 8: x_first_inverse<T, 8>(buf, C, ld, Mx, plan, tws); break;
+    case 4: x_first_inverse<T, 4>(buf, C, ld, Mx, plan, tws); break;
+    case 3: x_first_inverse<T, 3>(buf, C, ld, Mx, plan, tws); break;
+    default: x_first_inverse<T, 2>(buf, C, ld, Mx, plan, tws); break;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void x_last_forward_any(const cplx<T>* buf, int C, int ld, int Mx,
+                                                   int Mxp, const FftPlan& plan,
+                                                   const cplx<T>* tws, cplx<T>* W, int comp0,
+                                                   int lgRB, int row0, int nrows)
+{
+    switch (plan.radix[0]) {
+    case 8: x_last_forward<T, 8>(buf, C, ld, Mx, Mxp, plan, tws, W, comp0, lgRB, row0, nrows); break;
+    case 4: x_last_forward<T, 4>(buf, C, ld, Mx, Mxp, plan, tws, W, comp0, lgRB, row0, nrows); break;
+    case 3: x_last_forward<T, 3>(buf, C, ld, Mx, Mxp, plan, tws, W, comp0, lgRB, row0, nrows); break;
+    default: x_last_forward<T, 2>(buf, C, ld, Mx, Mxp, plan, tws, W, comp0, lgRB, row0, nrows); break;
+    }
+}
+
 template <typename T, int MODE>
-__global__ void __launch_bounds__(kThreadsX)
+__global__ void __launch_bounds__(kThreadsX, sizeof(T) == 4 ? 3 : 1)
 k_xpass(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict__ tw,
         const int* __restrict__ pos, XExtra ex, int lgRB, const StepState* __restrict__ st)
 {
@@ -137,6 +276,7 @@ k_xpass(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict
         reinterpret_cast<unsigned char*>(Fs) + ((sizeof(FrameT<T>) + 15) / 16) * 16);
     cplx<T>* buf = tws + nx;
     int* spos = reinterpret_cast<int*>(buf + (size_t)nh * ld);
+    int* ipos = spos + nh;                       // row -> point pair p (inverse of pos)
 
     const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
     load_tables<T>(tws, spos, tw, pos, nx, nh);
@@ -179,13 +319,31 @@ k_xpass(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict
         }
     }
     __syncthreads();
+    for (int p = tid; p < nh; p += kThreadsX) ipos[spos[p]] = p;
+    __syncthreads();
 
-    double e_acc = 0.0, m_acc = 0.0;
+    __shared__ int rowmask[32];     // per tile row: bit q set if part q's box meets the row
+    double e_acc = 0.0;             // FP64 across tiles; FP32 partials within a tile
+    T m_acc = T(0);                 // max |u|^2 (a max is exact in any precision)
     int bad = 0;
     const T dxT = T(g.dx), dyT = T(g.dy), dzT = T(g.dz);
 
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int row0 = tile * RB;
+        if (kPhys && tid < RB) {
+            const int r = row0 + tid;
+            int mask = 0;
+            if (r < nrows) {
+                const FrameT<T>& F = *Fs;
+                const int z = r / g.ny, y = r - z * g.ny;
+                const T Y = T(y) * dyT, Z = T(z) * dzT;
+                for (int q = 0; q < 3; ++q)
+                    if (F.active[q] && Y >= F.box[q][2] && Y <= F.box[q][3] && Z >= F.box[q][4] &&
+                        Z <= F.box[q][5])
+                        mask |= 1 << q;
+            }
+            rowmask[tid] = mask;
+        }
 
         // ---- load: spectral rows -> Z (c2r input) or real rows -> z (r2c input)
         if (MODE == XP_R2C) {
@@ -206,31 +364,26 @@ k_xpass(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict
                 buf[spos[p] * ld + col] = z;
             }
         } else {
-            const int half = nh / 2 + 1;
-            for (int i = tid; i < C * half; i += kThreadsX) {
-                const int col = i / half, k = i - col * half;
+            // kept x-modes of each row straight into column (field, row) of buf
+            const int Mx = g.Mx;
+            for (int i = tid; i < C * Mx; i += kThreadsX) {
+                const int col = i / Mx, k = i - col * Mx;
                 const int f = col >> lgRB, r = row0 + (col & (RB - 1));
-                const int m = nh - k;
-                cplx<T> Xk = mkc<T>(0, 0), Xm = mkc<T>(0, 0);
-                if (r < nrows) {
-                    const cplx<T>* src = W + ((size_t)(ex.comp0 + f) * nrows + r) * g.Mxp;
-                    if (k < g.Mx) Xk = src[k];
-                    if (k == 0) Xk.y = T(0);            // a real line has a real mean
-                    else if (m < g.Mx) Xm = src[m];
-                }
-                const cplx<T> wk = tws[k];
-                cplx<T> s1 = cadd(Xk, cconj(Xm)), d1 = csub(Xk, cconj(Xm));
-                buf[k * ld + col] = cadd(s1, cmuli(cmul(d1, cconj(wk))));
-                if (k > 0 && m != k) {
-                    const cplx<T> wm = tws[m];
-                    cplx<T> s2 = cadd(Xm, cconj(Xk)), d2 = csub(Xm, cconj(Xk));
-                    buf[m * ld + col] = cadd(s2, cmuli(cmul(d2, cconj(wm))));
-                }
+                if (r < nrows)
+                    cp_async_cplx<T>(buf + k * ld + col,
+                                     W + ((size_t)(ex.comp0 + f) * nrows + r) * g.Mxp + k);
+                else
+                    buf[k * ld + col] = mkc<T>(0, 0);
             }
+            cp_async_wait_all();
         }
         __syncthreads();
 
-        if (MODE != XP_R2C) fft_dif<T, true>(buf, C, ld, plan, tws);   // z[p] at row pos[p]
+        if (MODE != XP_R2C) {                 // z[p] ends at row pos[p]
+            x_first_inverse_any<T>(buf, C, ld, g.Mx, plan, tws);
+            fft_dif<T, true>(buf, C, ld, plan, tws, 1, plan.nst);
+        }
+
 
         if (MODE == XP_C2R) {
             for (int i = tid; i < C * nh; i += kThreadsX) {
@@ -257,23 +410,23 @@ k_xpass(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict
             const FrameT<T>& F = *Fs;
             const int items = RB * nh;
             const int niter = ceil_div(items, kThreadsX);
+            T e_tile = T(0);
             for (int it = 0; it < niter; ++it) {
+                // consecutive lanes take consecutive buffer rows (conflict-free);
+                // row holds the point pair p = ipos[row] after the inverse transform
                 const int i = tid + it * kThreadsX;
-                const int rr = i / nh, p = i - rr * nh;
+                const int rr = i / nh, row = i - rr * nh;
+                const bool valid = (i < items) && (row0 + rr < nrows);
+                const int p = valid ? ipos[row] : 0;
                 const int r = row0 + rr;
-                const bool valid = (i < items) && (r < nrows);
-                T nl[2][3], chi2[2], us2[2][3];
+                const int mask = valid ? rowmask[rr] : 0;
+                T nl[2][3], chi2[2] = {T(0), T(0)}, us2[2][3] = {{T(0), T(0), T(0)}, {T(0), T(0), T(0)}};
                 int colr[2] = {0, 0};
                 T u[2][3], om[2][3], X[2][3];
                 if (valid) {
                     const int z = r / g.ny, y = r - z * g.ny;
                     const T Y = T(y) * dyT, Z = T(z) * dzT;
-                    bool inrow[3];
-                    for (int q = 0; q < 3; ++q)
-                        inrow[q] = F.active[q] && Y >= F.box[q][2] && Y <= F.box[q][3] &&
-                                   Z >= F.box[q][4] && Z <= F.box[q][5];
                     cplx<T> uv[3], wv[3];
-                    const int row = spos[p];
                     for (int c = 0; c < 3; ++c) {
                         uv[c] = buf[row * ld + c * RB + rr];
                         wv[c] = buf[row * ld + (3 + c) * RB + rr];
@@ -286,7 +439,10 @@ k_xpass(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict
                         X[h][0] = T(2 * p + h) * dxT;
                         X[h][1] = Y;
                         X[h][2] = Z;
-                        solid_at(F, X[h], inrow, chi2[h], colr[h], us2[h]);
+                        if (mask != 0) {
+                            const bool inrow[3] = {(mask & 1) != 0, (mask & 2) != 0, (mask & 4) != 0};
+                            solid_at(F, X[h], inrow, chi2[h], colr[h], us2[h]);
+                        }
                         T lamb[3];
                         cross3(u[h], om[h], lamb);
                         const T pen = chi2[h] * F.inv_eta;
@@ -296,8 +452,8 @@ k_xpass(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict
                             uu += u[h][c] * u[h][c];
                             if (!isfinite(nl[h][c]) || !isfinite(u[h][c])) bad = 1;
                         }
-                        e_acc += double(uu);
-                        m_acc = fmax(m_acc, double(uu));
+                        e_tile += uu;
+                        m_acc = fmax(m_acc, uu);
                     }
                     if (MODE == XP_DUMP) {
                         T* out = (T*)ex.rout;
@@ -314,13 +470,12 @@ k_xpass(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict
                             out[7 * Nn + o] = T(colr[h]);
                         }
                     } else {
-                        const int row = spos[p];
                         for (int c = 0; c < 3; ++c)
                             buf[row * ld + c * RB + rr] = mkc<T>(nl[0][c], nl[1][c]);
                     }
                 }
-                if (MODE == XP_PHYS) {
-                    // penalization sums per colour, only in warps that touch the solid
+                // penalization sums per colour, only in warps whose rows meet a part
+                if (MODE == XP_PHYS && __any_sync(0xffffffffu, mask != 0)) {
                     for (int cc = 0; cc < 3; ++cc) {
                         const bool has = valid && (colr[0] == cc + 1 || colr[1] == cc + 1);
                         if (!__any_sync(0xffffffffu, has)) continue;
@@ -352,39 +507,26 @@ k_xpass(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict
                     }
                 }
             }
+            e_acc += double(e_tile);
             __syncthreads();
             if (MODE == XP_DUMP) continue;
         }
 
-        // ---- r2c of the first 3 (or ncomp) fields and store the kept x-modes
+        // ---- r2c of the first 3 (or ncomp) fields and store of the kept x-modes
         const int Cf = kPhys ? 3 * RB : C;
-        fft_dit<T, false>(buf, Cf, ld, plan, tws);   // digit-reversed in, natural out
-        const int Mxp = g.Mxp, Mx = g.Mx;
-        for (int i = tid; i < Cf * Mxp; i += kThreadsX) {
-            const int col = i / Mxp, k = i - col * Mxp;
-            const int f = col >> lgRB, r = row0 + (col & (RB - 1));
-            if (r >= nrows) continue;
-            cplx<T> Xk = mkc<T>(0, 0);
-            if (k < Mx) {
-                const int m = k == 0 ? 0 : nh - k;
-                const cplx<T> Zk = buf[k * ld + col], Zm = cconj(buf[m * ld + col]);
-                const cplx<T> E = cscale(cadd(Zk, Zm), T(0.5));
-                const cplx<T> O = cscale(cmulmi(csub(Zk, Zm)), T(0.5));
-                Xk = cadd(E, cmul(tws[k], O));
-            }
-            W[((size_t)(ex.comp0 + f) * nrows + r) * Mxp + k] = Xk;
-        }
-        __syncthreads();
+        fft_dit<T, false>(buf, Cf, ld, plan, tws, 1, plan.nst);
+        x_last_forward_any<T>(buf, Cf, ld, g.Mx, g.Mxp, plan, tws, W, ex.comp0, lgRB, row0, nrows);
     }
 
     if (MODE == XP_PHYS) {
         __shared__ double red[kWarpsX][3];
         e_acc = warp_sum(e_acc);
-        for (int o = 16; o > 0; o >>= 1) m_acc = fmax(m_acc, __shfl_xor_sync(0xffffffffu, m_acc, o));
+        double m_d = double(m_acc);
+        for (int o = 16; o > 0; o >>= 1) m_d = fmax(m_d, __shfl_xor_sync(0xffffffffu, m_d, o));
         const int anybad = __any_sync(0xffffffffu, bad);
         if (lane == 0) {
             red[warp][0] = e_acc;
-            red[warp][1] = m_acc;
+            red[warp][1] = m_d;
             red[warp][2] = anybad ? 1.0 : 0.0;
         }
         __syncthreads();
@@ -424,7 +566,7 @@ template <typename T> size_t x_smem(const Geom& g, int lgRB, int NF)
     const int C = NF << lgRB;
     const int ld = C | 1;
     size_t s = sizeof(double) * kWarpsX * 36 + ((sizeof(FrameT<T>) + 15) / 16) * 16;
-    s += sizeof(cplx<T>) * ((size_t)g.nx + (size_t)(g.nx / 2) * ld) + sizeof(int) * (g.nx / 2);
+    s += sizeof(cplx<T>) * ((size_t)g.nx + (size_t)(g.nx / 2) * ld) + 2 * sizeof(int) * (g.nx / 2);
     return s;
 }
 

@@ -45,18 +45,14 @@ k_ypass(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict
     for (int e = threadIdx.x; e < total_in; e += kThreads) {
         const int s = e >> lgC, col = e & (C - 1);
         const int z = z0 + (col >> lgTX), x = x0 + (col & (TX - 1));
-        cplx<T> v = mkc<T>(0, 0);
-        if (z < g.nz && x < g.Mxp) {
-            if (INV) {
-                // slot s holds mode m = s (s <= Ky) or m = s - ny (s >= ny - Ky)
-                int j = s <= Ky ? s : (s >= ny - Ky ? s - ny + My : -1);
-                if (j >= 0) v = base[z * plane + (size_t)j * g.Mxp + x];
-            } else {
-                v = base[z * plane + (size_t)s * g.Mxp + x];
-            }
-        }
-        buf[e] = v;
+        // slot s holds mode m = s (s <= Ky) or m = s - ny (s >= ny - Ky)
+        const int j = INV ? (s <= Ky ? s : (s >= ny - Ky ? s - ny + My : -1)) : s;
+        if (z < g.nz && x < g.Mxp && j >= 0)
+            cp_async_cplx<T>(buf + e, base + z * plane + (size_t)j * g.Mxp + x);
+        else
+            buf[e] = mkc<T>(0, 0);
     }
+    cp_async_wait_all();
     __syncthreads();
     fft_dif<T, INV>(buf, C, C, plan, tws);
     const int rows_out = INV ? ny : My;

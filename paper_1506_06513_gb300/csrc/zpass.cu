@@ -61,27 +61,55 @@ k_zinv(const cplx<T>* __restrict__ U, cplx<T>* __restrict__ W, Geom g, FftPlan p
     const int nz = g.nz, Kz = g.Kz, Mz = g.Mz;
 
     for (int f = 0; f < nf; ++f) {
-        for (int e = threadIdx.x; e < (nz << lgTX); e += kThreadsInv) {
-            const int s = e >> lgTX;
-            const int jz = s <= Kz ? s : (s >= nz - Kz ? s - nz + Mz : -1);
-            cplx<T> v = mkc<T>(0, 0);
-            if (kept && jz >= 0) {
-                const cplx<T>* u = U + (size_t)jz * Q + q;
-                if (f < 3) {
-                    v = u[f * Ustride];
-                } else {
-                    const T kz = two_pi * T(mode_of(jz, Kz)) / T(g.Lz);
-                    // omega = i (k x u)
-                    cplx<T> a, b;
-                    T ka, kb;
-                    if (f == 3) { a = u[2 * Ustride]; b = u[Ustride];     ka = ky; kb = kz; }
-                    else if (f == 4) { a = u[0];      b = u[2 * Ustride]; ka = kz; kb = kx; }
-                    else { a = u[Ustride];            b = u[0];           ka = kx; kb = ky; }
-                    cplx<T> d = mkc<T>(ka * a.x - kb * b.x, ka * a.y - kb * b.y);
-                    v = cmuli(d);
+        if (f < 3) {
+            for (int e = threadIdx.x; e < (nz << lgTX); e += kThreadsInv) {
+                const int s = e >> lgTX;
+                const int jz = s <= Kz ? s : (s >= nz - Kz ? s - nz + Mz : -1);
+                if (kept && jz >= 0)
+                    cp_async_cplx<T>(buf + e, U + f * Ustride + (size_t)jz * Q + q);
+                else
+                    buf[e] = mkc<T>(0, 0);
+            }
+            cp_async_wait_all();
+        } else {
+            // omega = i (k x u): two velocity components per value; loads are
+            // issued in batches of kB before their results are used
+            constexpr int kB = 4;
+            const int cA = f == 3 ? 2 : f == 4 ? 0 : 1;
+            const int cB = f == 3 ? 1 : f == 4 ? 2 : 0;
+            const T kb = f == 3 ? T(0) : f == 4 ? kx : ky;   // kz enters per mode
+            const T ka = f == 3 ? ky : f == 4 ? T(0) : kx;
+            for (int e0 = threadIdx.x; e0 < (nz << lgTX); e0 += kB * kThreadsInv) {
+                cplx<T> a[kB], b[kB];
+                int jzs[kB];
+#pragma unroll
+                for (int r = 0; r < kB; ++r) {
+                    const int e = e0 + r * kThreadsInv;
+                    const int s = e >> lgTX;
+                    int jz = s <= Kz ? s : (s >= nz - Kz ? s - nz + Mz : -1);
+                    if (e >= (nz << lgTX) || !kept) jz = -1;
+                    jzs[r] = jz;
+                    a[r] = b[r] = mkc<T>(0, 0);
+                    if (jz >= 0) {
+                        a[r] = U[cA * Ustride + (size_t)jz * Q + q];
+                        b[r] = U[cB * Ustride + (size_t)jz * Q + q];
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < kB; ++r) {
+                    const int e = e0 + r * kThreadsInv;
+                    if (e >= (nz << lgTX)) break;
+                    cplx<T> v = mkc<T>(0, 0);
+                    if (jzs[r] >= 0) {
+                        const T kz = two_pi * T(mode_of(jzs[r], Kz)) / T(g.Lz);
+                        // f=3: ky uz - kz uy; f=4: kz ux - kx uz; f=5: kx uy - ky ux
+                        const T k1 = f == 4 ? kz : ka;
+                        const T k2 = f == 3 ? kz : kb;
+                        v = cmuli(mkc<T>(k1 * a[r].x - k2 * b[r].x, k1 * a[r].y - k2 * b[r].y));
+                    }
+                    buf[e] = v;
                 }
             }
-            buf[e] = v;
         }
         __syncthreads();
         fft_dif<T, true>(buf, TX, TX, plan, tws);
@@ -117,10 +145,12 @@ k_zfwd(const cplx<T>* __restrict__ W, cplx<T>* __restrict__ U, cplx<T>* __restri
     for (int e = threadIdx.x; e < nz * C; e += kThreadsFwd) {
         const int z = e / C, col = e - z * C;
         const int c = col >> lgTX, q = q0 + (col & (TX - 1));
-        cplx<T> v = mkc<T>(0, 0);
-        if (q < Q) v = W[((size_t)c * nz + z) * Wplane + q];
-        buf[e] = v;
+        if (q < Q)
+            cp_async_cplx<T>(buf + e, W + ((size_t)c * nz + z) * Wplane + q);
+        else
+            buf[e] = mkc<T>(0, 0);
     }
+    cp_async_wait_all();
     __syncthreads();
     fft_dif<T, false>(buf, C, C, plan, tws);
 
@@ -163,19 +193,21 @@ k_zfwd(const cplx<T>* __restrict__ W, cplx<T>* __restrict__ U, cplx<T>* __restri
         const T k2 = kx * kx + ky * ky + kz * kz;
         const bool zero_mode = (x == 0 && jy == 0 && jz == 0);
         if (!zero_mode) {
-            const T kNr = kx * N[0].x + ky * N[1].x + kz * N[2].x;
-            const T kNi = kx * N[0].y + ky * N[1].y + kz * N[2].y;
+            const T inv_k2 = T(1) / k2;
+            const T kNr = (kx * N[0].x + ky * N[1].x + kz * N[2].x) * inv_k2;
+            const T kNi = (kx * N[0].y + ky * N[1].y + kz * N[2].y) * inv_k2;
             const T kk[3] = {kx, ky, kz};
             for (int c = 0; c < 3; ++c) {
-                N[c].x -= kk[c] * kNr / k2;
-                N[c].y -= kk[c] * kNi / k2;
+                N[c].x -= kk[c] * kNr;
+                N[c].y -= kk[c] * kNi;
             }
         } else if (!ex.mean_free) {
             N[0] = N[1] = N[2] = mkc<T>(0, 0);
         }
         if (MODE == 0) {
-            const T e1 = T(E1x[x] * E1y[jy] * E1z[jz]);
-            const T e2 = first ? T(0) : T(E2x[x] * E2y[jy] * E2z[jz]);
+            // products of the per-axis factors in the state precision
+            const T e1 = T(E1x[x]) * T(E1y[jy]) * T(E1z[jz]);
+            const T e2 = first ? T(0) : T(E2x[x]) * T(E2y[jy]) * T(E2z[jz]);
             for (int c = 0; c < 3; ++c) {
                 cplx<T> u = U[c * Ustride + o];
                 cplx<T> r;
