@@ -79,6 +79,46 @@ template <typename T, bool INV> struct Dft<T, 8, INV> {
     }
 };
 
+// 16-point DFT as 4 x 4: X[k1 + 4 k2] = sum_n2 w16^{n2 k1} (sum_n1 x[4 n1 + n2] w4^{n1 k1}) w4^{n2 k2}.
+template <typename T, bool INV> struct Dft<T, 16, INV> {
+    __device__ __forceinline__ static void run(cplx<T>* v)
+    {
+        // cos and sin of 2 pi k / 16, k = 0..3
+        const T c1 = T(0.92387953251128675612818318939678828682);
+        const T s1 = T(0.38268343236508977172845998403039886676);
+        const T r = T(0.70710678118654752440084436210484903928);
+        cplx<T> y[4][4];
+#pragma unroll
+        for (int n2 = 0; n2 < 4; ++n2) {
+            cplx<T> a[4] = {v[n2], v[4 + n2], v[8 + n2], v[12 + n2]};
+            Dft<T, 4, INV>::run(a);
+#pragma unroll
+            for (int k1 = 0; k1 < 4; ++k1) y[n2][k1] = a[k1];
+        }
+        // y[n2][k1] *= w16^{n2 k1}; exponents 1, 2, 3, 2, 4, 6, 3, 6, 9
+        const T sg = INV ? T(1) : T(-1);
+        auto rot = [&](cplx<T> x, T c, T s) {   // x * (c + i sg s)
+            return mkc<T>(x.x * c - sg * x.y * s, x.y * c + sg * x.x * s);
+        };
+        y[1][1] = rot(y[1][1], c1, s1);
+        y[1][2] = rot(y[1][2], r, r);
+        y[1][3] = rot(y[1][3], s1, c1);
+        y[2][1] = rot(y[2][1], r, r);
+        y[2][2] = INV ? cmuli(y[2][2]) : cmulmi(y[2][2]);
+        y[2][3] = rot(y[2][3], -r, r);
+        y[3][1] = rot(y[3][1], s1, c1);
+        y[3][2] = rot(y[3][2], -r, r);
+        y[3][3] = rot(y[3][3], -c1, -s1);
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) {
+            cplx<T> a[4] = {y[0][k1], y[1][k1], y[2][k1], y[3][k1]};
+            Dft<T, 4, INV>::run(a);
+#pragma unroll
+            for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = a[k2];
+        }
+    }
+};
+
 template <typename T, bool INV> struct Dft<T, 3, INV> {
     __device__ __forceinline__ static void run(cplx<T>* v)
     {

@@ -553,6 +553,354 @@ k_xpass(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict
     }
 }
 
+// ---------------------------------------------------------------------------
+// x pass for nh = nx/2 = R*R (R = 16: nx = 512; R = 8: nx = 128).  Each line
+// (one field of one row) belongs to R consecutive lanes, which hold R values
+// each: the length-nh transforms are two register-resident radix-R passes
+// (DIF stage 0 then stage 1 for the inverse, their transposes in reverse for
+// the forward transform) exchanging through the line's own shared-memory
+// slice, so they need __syncwarp only.  A line's slice stores logical row r at
+// r + r/R (one pad slot per R rows) so both passes are free of bank conflicts.
+// The c2r mirror values X[nh - k] and the r2c mirror values Z[nh - k] are
+// exchanged between lanes j and R - j with warp shuffles; inputs are loaded
+// from global memory straight into registers and outputs are stored from
+// registers.  After the inverse passes logical row R q + d holds the point
+// pair p = q + R d.
+// ---------------------------------------------------------------------------
+template <int R> constexpr int sq_rows() { return 192 / (6 * R); }   // rows per tile
+
+template <typename T, int R>
+__device__ __forceinline__ void sq_exchange_pre(cplx<T>* x, int j, int width, const cplx<T>* twx)
+{
+    // x[t] holds X[j + R t]; on return x[t] = Z[j + R t] (c2r pre-processing)
+#pragma unroll
+    for (int s = 0; s < R / 2; ++s) {
+        cplx<T> a, b;   // partner's X[s] and X[R-1-s]
+        a.x = __shfl_sync(0xffffffffu, x[s].x, (R - j) & (R - 1), width);
+        a.y = __shfl_sync(0xffffffffu, x[s].y, (R - j) & (R - 1), width);
+        b.x = __shfl_sync(0xffffffffu, x[R - 1 - s].x, (R - j) & (R - 1), width);
+        b.y = __shfl_sync(0xffffffffu, x[R - 1 - s].y, (R - j) & (R - 1), width);
+        if (j != 0) {
+            // mirror of element t is the partner's element R-1-t
+            const cplx<T> zs = c2r_pre<T>(x[s], b, twx[j + R * s]);
+            const cplx<T> zt = c2r_pre<T>(x[R - 1 - s], a, twx[j + R * (R - 1 - s)]);
+            x[s] = zs;
+            x[R - 1 - s] = zt;
+        }
+    }
+    if (j == 0) {
+        // mirror of element t is own element R - t (element 0 mirrors X[nh] = 0)
+        const cplx<T> z0 = c2r_pre<T>(x[0], mkc<T>(0, 0), twx[0]);
+        const cplx<T> zh = c2r_pre<T>(x[R / 2], x[R / 2], twx[R * (R / 2)]);
+#pragma unroll
+        for (int t = 1; t < R / 2; ++t) {
+            const cplx<T> za = c2r_pre<T>(x[t], x[R - t], twx[R * t]);
+            const cplx<T> zb = c2r_pre<T>(x[R - t], x[t], twx[R * (R - t)]);
+            x[t] = za;
+            x[R - t] = zb;
+        }
+        x[0] = z0;
+        x[R / 2] = zh;
+    }
+}
+
+template <typename T, int R>
+__global__ void __launch_bounds__(192, sizeof(T) == 4 ? 4 : 1)
+k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExtra ex,
+           const StepState* __restrict__ st)
+{
+    if (st && st->status != 0) return;
+    constexpr int RB = sq_rows<R>();
+    constexpr int NH = R * R;
+    constexpr int CS = NH + R;             // padded line slice
+    const int nx = g.nx, Mx = g.Mx, Mxp = g.Mxp;
+    const int nrows = g.nz * g.ny;
+    const int ntiles = ceil_div(nrows, RB);
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* wacc = reinterpret_cast<double*>(smem_raw);                    // [warps][36]
+    FrameT<T>* Fs = reinterpret_cast<FrameT<T>*>(wacc + kWarpsX * 36);
+    cplx<T>* twx = reinterpret_cast<cplx<T>*>(
+        reinterpret_cast<unsigned char*>(Fs) + ((sizeof(FrameT<T>) + 15) / 16) * 16);
+    cplx<T>* tw2 = twx + nx;               // tw2[q R + j] = w_nh^{j q}
+    cplx<T>* buf = tw2 + NH;               // C line slices of CS values
+    __shared__ int rowmask[RB];
+
+    const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+    const int c = tid / R, j = tid % R;    // this lane's line and index within it
+    for (int i = tid; i < nx; i += blockDim.x) twx[i] = mkc<T>(T(tw[i].x), T(tw[i].y));
+    for (int i = tid; i < NH; i += blockDim.x) {
+        const int q = i / R, jj = i % R;
+        const double2 w = tw[(2 * jj * q) % nx];
+        tw2[i] = mkc<T>(T(w.x), T(w.y));
+    }
+    for (int i = tid; i < kWarpsX * 36; i += blockDim.x) wacc[i] = 0.0;
+    if (tid == 0) {
+        const Frame& F = *ex.frame;
+        FrameT<T> f;
+        for (int i = 0; i < 3; ++i) {
+            f.xc[i] = T(F.xc[i]);
+            f.uc[i] = T(F.uc[i]);
+            f.Ob[i] = T(F.Ob[i]);
+            f.active[i] = F.active[i];
+            for (int s2 = 0; s2 < 2; ++s2) {
+                f.pv[s2][i] = T(F.pv[s2][i]);
+                f.Ow[s2][i] = T(F.Ow[s2][i]);
+            }
+            for (int k = 0; k < 6; ++k) f.box[i][k] = T(F.box[i][k]);
+        }
+        for (int i = 0; i < 9; ++i) {
+            f.Mb[i] = T(F.Mb[i]);
+            f.Mw[0][i] = T(F.Mw[0][i]);
+            f.Mw[1][i] = T(F.Mw[1][i]);
+        }
+        const Shape& S = ex.shape;
+        f.h = T(S.h);
+        f.a = T(S.body_a);
+        f.b = T(S.body_b);
+        f.c_le = T(S.c_le);
+        f.c_te = T(S.c_te);
+        f.R = T(S.R);
+        f.ht = T(S.ht);
+        f.inv_eta = T(1.0 / g.eta);
+        f.body_type = S.body_type;
+        f.profile = S.profile;
+        if (S.body_type == 0) f.active[0] = 0;
+        if (S.nwings < 1) f.active[1] = 0;
+        if (S.nwings < 2) f.active[2] = 0;
+        *Fs = f;
+    }
+    __syncthreads();
+
+    double e_acc = 0.0;
+    T m_acc = T(0);
+    int bad = 0;
+    const T dxT = T(g.dx), dyT = T(g.dy), dzT = T(g.dz);
+    const FrameT<T>& F = *Fs;
+    cplx<T>* line = buf + c * CS;
+    const int fld = c / RB, lrr = c % RB;
+
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int row0 = tile * RB;
+        // ---- loads of this lane's kept x-modes, straight into registers
+        cplx<T> v[R];
+        {
+            const int r = row0 + lrr;
+            const cplx<T>* src = W + ((size_t)fld * nrows + (r < nrows ? r : 0)) * Mxp;
+#pragma unroll
+            for (int t = 0; t < R; ++t) {
+                const int k = j + R * t;
+                v[t] = (r < nrows && k < Mx) ? src[k] : mkc<T>(0, 0);
+            }
+            if (j == 0) v[0].y = T(0);     // a real line has a real mean
+        }
+        if (tid < RB) {
+            const int r = row0 + tid;
+            int mask = 0;
+            if (r < nrows) {
+                const int z = r / g.ny, y = r - z * g.ny;
+                const T Y = T(y) * dyT, Z = T(z) * dzT;
+                for (int q = 0; q < 3; ++q)
+                    if (F.active[q] && Y >= F.box[q][2] && Y <= F.box[q][3] && Z >= F.box[q][4] &&
+                        Z <= F.box[q][5])
+                        mask |= 1 << q;
+            }
+            rowmask[tid] = mask;
+        }
+        // ---- inverse: c2r pre-processing, DIF stage 0 (radix R + twiddles), stage 1
+        sq_exchange_pre<T, R>(v, j, R, twx);
+        Dft<T, R, true>::run(v);
+#pragma unroll
+        for (int q = 1; q < R; ++q) v[q] = cmul(v[q], cconj(tw2[q * R + j]));
+#pragma unroll
+        for (int q = 0; q < R; ++q) line[j + R * q + q] = v[q];
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < R; ++i) v[i] = line[R * j + i + j];
+        Dft<T, R, true>::run(v);
+#pragma unroll
+        for (int d = 0; d < R; ++d) line[R * j + d + j] = v[d];
+        __syncthreads();
+
+        // ---- physical space: chi, u_s, NL = u x omega - chi/C_eta (u - u_s), sums
+        {
+            const int items = RB * NH;
+            T e_tile = T(0);
+            for (int it = 0; it < (items + 191) / 192; ++it) {
+                const int i = tid + it * 192;
+                const int rr = i / NH, lrow = i % NH;
+                const bool valid = (i < items) && (row0 + rr < nrows);
+                const int p = lrow / R + R * (lrow % R);
+                const int slot = lrow + lrow / R;
+                const int r = row0 + rr;
+                const int mask = valid ? rowmask[rr] : 0;
+                T chi2[2] = {T(0), T(0)}, us2[2][3] = {{T(0), T(0), T(0)}, {T(0), T(0), T(0)}};
+                int colr[2] = {0, 0};
+                T u[2][3], X[2][3];
+                if (valid) {
+                    const int z = r / g.ny, y = r - z * g.ny;
+                    const T Y = T(y) * dyT, Z = T(z) * dzT;
+                    cplx<T> uv[3], wv[3];
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        uv[q] = buf[(q * RB + rr) * CS + slot];
+                        wv[q] = buf[((3 + q) * RB + rr) * CS + slot];
+                    }
+                    T nl[2][3];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        T om[3];
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) {
+                            u[h][q] = h ? uv[q].y : uv[q].x;
+                            om[q] = h ? wv[q].y : wv[q].x;
+                        }
+                        X[h][0] = T(2 * p + h) * dxT;
+                        X[h][1] = Y;
+                        X[h][2] = Z;
+                        if (mask != 0) {
+                            const bool inrow[3] = {(mask & 1) != 0, (mask & 2) != 0, (mask & 4) != 0};
+                            solid_at(F, X[h], inrow, chi2[h], colr[h], us2[h]);
+                        }
+                        T lamb[3];
+                        cross3(u[h], om, lamb);
+                        const T pen = chi2[h] * F.inv_eta;
+                        T uu = T(0);
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) {
+                            nl[h][q] = lamb[q] - pen * (u[h][q] - us2[h][q]);
+                            uu += u[h][q] * u[h][q];
+                            if (!isfinite(nl[h][q]) || !isfinite(u[h][q])) bad = 1;
+                        }
+                        e_tile += uu;
+                        m_acc = fmax(m_acc, uu);
+                    }
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) buf[(q * RB + rr) * CS + slot] = mkc<T>(nl[0][q], nl[1][q]);
+                }
+                if (__any_sync(0xffffffffu, mask != 0)) {
+                    for (int cc = 0; cc < 3; ++cc) {
+                        const bool has = valid && (colr[0] == cc + 1 || colr[1] == cc + 1);
+                        if (!__any_sync(0xffffffffu, has)) continue;
+                        double acc[12];
+                        for (int k = 0; k < 12; ++k) acc[k] = 0.0;
+                        if (has) {
+                            for (int h = 0; h < 2; ++h) {
+                                if (colr[h] != cc + 1) continue;
+                                const T* ref = cc == 0 ? F.xc : F.pv[cc - 1];
+                                T rv[3] = {X[h][0] - ref[0], X[h][1] - ref[1], X[h][2] - ref[2]};
+                                T pu[3], cu[3], m1[3], m2[3];
+                                for (int q = 0; q < 3; ++q) {
+                                    pu[q] = chi2[h] * (u[h][q] - us2[h][q]);
+                                    cu[q] = chi2[h] * us2[h][q];
+                                }
+                                cross3(rv, pu, m1);
+                                cross3(rv, cu, m2);
+                                for (int q = 0; q < 3; ++q) {
+                                    acc[q] += double(pu[q]);
+                                    acc[3 + q] += double(m1[q]);
+                                    acc[6 + q] += double(cu[q]);
+                                    acc[9 + q] += double(m2[q]);
+                                }
+                            }
+                        }
+                        for (int k = 0; k < 12; ++k) acc[k] = warp_sum(acc[k]);
+                        if (lane == 0)
+                            for (int k = 0; k < 12; ++k) wacc[warp * 36 + cc * 12 + k] += acc[k];
+                    }
+                }
+            }
+            e_acc += double(e_tile);
+        }
+        __syncthreads();
+
+        // ---- forward on the three NL lines of each row: DIT stage 1, stage 0, r2c post
+        if (c < 3 * RB) {
+#pragma unroll
+            for (int i = 0; i < R; ++i) v[i] = line[R * j + i + j];
+            Dft<T, R, false>::run(v);
+#pragma unroll
+            for (int d = 0; d < R; ++d) line[R * j + d + j] = v[d];
+            __syncwarp();   // the three NL rows' lanes fill whole warps
+#pragma unroll
+            for (int t = 0; t < R; ++t) v[t] = line[j + R * t + t];
+#pragma unroll
+            for (int t = 1; t < R; ++t) v[t] = cmul(v[t], tw2[t * R + j]);
+            Dft<T, R, false>::run(v);      // v[q] = Z[j + R q]
+            const int r = row0 + lrr;
+            cplx<T>* out = W + ((size_t)fld * nrows + (r < nrows ? r : 0)) * Mxp;
+            const int width = R;
+#pragma unroll
+            for (int s2 = 0; s2 < R / 2; ++s2) {
+                cplx<T> a, b;   // partner's Z[s2] and Z[R-1-s2]
+                a.x = __shfl_sync(0xffffffffu, v[s2].x, (R - j) & (R - 1), width);
+                a.y = __shfl_sync(0xffffffffu, v[s2].y, (R - j) & (R - 1), width);
+                b.x = __shfl_sync(0xffffffffu, v[R - 1 - s2].x, (R - j) & (R - 1), width);
+                b.y = __shfl_sync(0xffffffffu, v[R - 1 - s2].y, (R - j) & (R - 1), width);
+                if (r < nrows) {
+                    const int q1 = s2, q2 = R - 1 - s2;
+                    const int k1 = j + R * q1, k2 = j + R * q2;
+                    cplx<T> m1, m2;
+                    if (j != 0) {
+                        m1 = b;    // Z[nh - k1] = partner's Z[R-1-q1]
+                        m2 = a;
+                    } else {
+                        m1 = v[(R - q1) & (R - 1)];
+                        m2 = v[(R - q2) & (R - 1)];
+                    }
+                    if (k1 < Mxp) out[k1] = k1 < Mx ? r2c_post<T>(v[q1], m1, twx[k1]) : mkc<T>(0, 0);
+                    if (k2 < Mxp) out[k2] = k2 < Mx ? r2c_post<T>(v[q2], m2, twx[k2]) : mkc<T>(0, 0);
+                }
+            }
+        }
+        __syncthreads();
+    }
+
+    __shared__ double red[kWarpsX][3];
+    e_acc = warp_sum(e_acc);
+    double m_d = double(m_acc);
+    for (int o = 16; o > 0; o >>= 1) m_d = fmax(m_d, __shfl_xor_sync(0xffffffffu, m_d, o));
+    const int anybad = __any_sync(0xffffffffu, bad);
+    if (lane == 0) {
+        red[warp][0] = e_acc;
+        red[warp][1] = m_d;
+        red[warp][2] = anybad ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    double* outp = ex.part + (size_t)blockIdx.x * kNumSums;
+    if (tid < 36) {
+        double s2 = 0.0;
+        for (int w = 0; w < kWarpsX; ++w) s2 += wacc[w * 36 + tid];
+        outp[tid] = s2;
+    } else if (tid == kSumEkin) {
+        double s2 = 0.0;
+        for (int w = 0; w < kWarpsX; ++w) s2 += red[w][0];
+        outp[tid] = s2;
+    } else if (tid == kSumUmax2 || tid == kSumBad) {
+        double s2 = 0.0;
+        for (int w = 0; w < kWarpsX; ++w) s2 = fmax(s2, red[w][tid == kSumUmax2 ? 1 : 2]);
+        outp[tid] = s2;
+    } else if (tid < kNumSums) {
+        outp[tid] = 0.0;
+    }
+}
+
+template <typename T, int R> size_t sq_smem(const Geom& g)
+{
+    const int RB = sq_rows<R>(), NH = R * R;
+    size_t s = sizeof(double) * kWarpsX * 36 + ((sizeof(FrameT<T>) + 15) / 16) * 16;
+    s += sizeof(cplx<T>) * ((size_t)g.nx + NH + (size_t)6 * RB * (NH + R));
+    return s;
+}
+
+// radix of the square half-length kernel for this grid, or 0 for the generic one
+template <typename T> int sq_radix(const Geom& g)
+{
+    if (g.nx == 512) return 16;
+    if (g.nx == 128) return 8;
+    return 0;
+}
+
 template <typename T> int x_lgrb(const Geom& g)
 {
     const int nh = g.nx / 2;
@@ -574,17 +922,26 @@ int g_sm_count = 0;
 
 template <typename T> int x_grid(const Geom& g)
 {
-    const int lg = x_lgrb<T>(g);
-    const int ntiles = ceil_div(g.nz * g.ny, 1 << lg);
     if (g_sm_count == 0) {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev);
         if (g_sm_count <= 0) g_sm_count = 1;
     }
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_xpass<T, XP_PHYS>, kThreadsX,
-                                                  x_smem<T>(g, lg, 6));
+    int per_sm = 0, ntiles = 0;
+    const int R = sq_radix<T>(g);
+    if (R == 16) {
+        ntiles = ceil_div(g.nz * g.ny, sq_rows<16>());
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_xpass_sq<T, 16>, 192, sq_smem<T, 16>(g));
+    } else if (R == 8) {
+        ntiles = ceil_div(g.nz * g.ny, sq_rows<8>());
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_xpass_sq<T, 8>, 192, sq_smem<T, 8>(g));
+    } else {
+        const int lg = x_lgrb<T>(g);
+        ntiles = ceil_div(g.nz * g.ny, 1 << lg);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_xpass<T, XP_PHYS>, kThreadsX,
+                                                      x_smem<T>(g, lg, 6));
+    }
     if (per_sm <= 0) per_sm = 1;
     int grid = g_sm_count * per_sm;
     return grid < ntiles ? grid : ntiles;
@@ -604,7 +961,12 @@ cudaError_t launch_x(int mode, void* W, const Geom& g, const FftPlan& plan, cons
     cplx<T>* w = (cplx<T>*)W;
     switch (mode) {
     case XP_PHYS:
-        k_xpass<T, XP_PHYS><<<x_grid<T>(g), kThreadsX, smem, s>>>(w, g, plan, tw, pos, ex, lg, st);
+        if (sq_radix<T>(g) == 16)
+            k_xpass_sq<T, 16><<<x_grid<T>(g), 192, sq_smem<T, 16>(g), s>>>(w, g, tw, ex, st);
+        else if (sq_radix<T>(g) == 8)
+            k_xpass_sq<T, 8><<<x_grid<T>(g), 192, sq_smem<T, 8>(g), s>>>(w, g, tw, ex, st);
+        else
+            k_xpass<T, XP_PHYS><<<x_grid<T>(g), kThreadsX, smem, s>>>(w, g, plan, tw, pos, ex, lg, st);
         break;
     case XP_R2C:
         k_xpass<T, XP_R2C><<<ntiles, kThreadsX, smem, s>>>(w, g, plan, tw, pos, ex, lg, st);
@@ -645,6 +1007,10 @@ cudaError_t configure_xpass()
     FLUSI_SMEM((k_xpass<double, XP_R2C>))
     FLUSI_SMEM((k_xpass<double, XP_C2R>))
     FLUSI_SMEM((k_xpass<double, XP_DUMP>))
+    FLUSI_SMEM((k_xpass_sq<float, 16>))
+    FLUSI_SMEM((k_xpass_sq<float, 8>))
+    FLUSI_SMEM((k_xpass_sq<double, 16>))
+    FLUSI_SMEM((k_xpass_sq<double, 8>))
 #undef FLUSI_SMEM
     return cudaSuccess;
 }

@@ -298,3 +298,31 @@ def test_bench_configuration_sampled(fl):
     assert abs(rows[0, 20] - ek) <= 1e-5 * ek
     assert rows[0, 1] == pytest.approx(min(0.1 * dx / rows[0, 21], cfg["eta"]), rel=1e-12)
     sim.close()
+
+
+WIDE = {"x512": ((512, 16, 12), (8.0, 1.0, 0.75)), "x128": ((128, 24, 16), (4.0, 0.75, 0.5))}
+
+
+@pytest.mark.parametrize("name", sorted(WIDE))
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_square_half_length_x_pass(fl, name, prec):
+    """Grids with nx = 512 and nx = 128 take the x pass whose half-length
+    transform is two register-resident radix-16 (radix-8) passes; full steps
+    with a sphere, adaptive dt and a mean flow against the oracle."""
+    n, L = WIDE[name]
+    cfg = {"n": n, "L": L, "nu": 0.01, "eta": 1e-2, "cfl": 0.1, "mean_mode": "fixed",
+           "u_inf": (0.3, 0.0, 0.0)}
+    ins = workloads.sphere((L[0] / 2, L[1] / 2, L[2] / 2), 0.35 * min(L[1], L[2]), profile="cos")
+    u0 = workloads.random_smooth_field(n, 7, mean=(0.3, 0.0, 0.0))
+    sim = fl.Solver(cfg, ins, precision=prec)
+    sim.set_state(u0)
+    sim.step(5)
+    rows, _ = sim.forces()
+    u = sim.get_state()[0]
+    sim.close()
+    ref = oracle.Simulation(cfg, ins)
+    ref.set_state(u0)
+    ref_rows = ref.step(5)
+    tol_u, tol_f = (1e-11, 1e-9) if prec == "fp64" else (2e-5, 1e-4)
+    assert rel_l2(u, ref.get_state()) <= tol_u
+    assert rows_err(rows, ref_rows) <= tol_f
