@@ -135,6 +135,13 @@ __device__ __forceinline__ void cp_async_cplx(cplx<T>* smem_dst, const cplx<T>* 
         asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem_src));
 }
 
+// 16-byte asynchronous copy (two FP32 complex values or one FP64 value).
+__device__ __forceinline__ void cp_async_16(void* smem_dst, const void* gmem_src)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src));
+}
+
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // Signed mode of a stored spectral index j in [0, M) with M = 2K + 1.

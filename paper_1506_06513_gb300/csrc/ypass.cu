@@ -41,28 +41,35 @@ k_ypass(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict
 
     load_tables<T>(tws, spos, tw, pos, g.ny, g.ny);
     const int ny = g.ny, My = g.My, Ky = g.Ky;
-    const int total_in = ny << lgC;
-    for (int e = threadIdx.x; e < total_in; e += kThreads) {
-        const int s = e >> lgC, col = e & (C - 1);
-        const int z = z0 + (col >> lgTX), x = x0 + (col & (TX - 1));
+    // each lane moves VEC adjacent columns (16 bytes) of a fixed column group;
+    // TX is a multiple of VEC, so the lane's column, plane and x stay fixed
+    constexpr int VEC = 16 / sizeof(cplx<T>);
+    const int lanes_per_row = C / VEC;
+    const int rstep = kThreads / lanes_per_row;
+    const int col = (threadIdx.x % lanes_per_row) * VEC;
+    const int z = z0 + (col >> lgTX), x = x0 + (col & (TX - 1));
+    const bool colok = z < g.nz && x < g.Mxp;   // Mxp and TX are multiples of VEC
+    cplx<T>* gcol = base + (size_t)(colok ? z : 0) * plane + (colok ? x : 0);
+    for (int s = threadIdx.x / lanes_per_row; s < ny; s += rstep) {
         // slot s holds mode m = s (s <= Ky) or m = s - ny (s >= ny - Ky)
         const int j = INV ? (s <= Ky ? s : (s >= ny - Ky ? s - ny + My : -1)) : s;
-        if (z < g.nz && x < g.Mxp && j >= 0)
-            cp_async_cplx<T>(buf + e, base + z * plane + (size_t)j * g.Mxp + x);
-        else
-            buf[e] = mkc<T>(0, 0);
+        cplx<T>* dst = buf + (s << lgC) + col;
+        if (colok && j >= 0) {
+            cp_async_16(dst, gcol + (size_t)j * g.Mxp);
+        } else {
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) dst[v] = mkc<T>(0, 0);
+        }
     }
     cp_async_wait_all();
     __syncthreads();
     fft_dif<T, INV>(buf, C, C, plan, tws);
     const int rows_out = INV ? ny : My;
-    const int total_out = rows_out << lgC;
-    for (int e = threadIdx.x; e < total_out; e += kThreads) {
-        const int r = e >> lgC, col = e & (C - 1);
-        const int z = z0 + (col >> lgTX), x = x0 + (col & (TX - 1));
-        if (z < g.nz && x < g.Mxp) {
-            const int s = spos[INV ? r : slot_of(r, Ky, ny)];
-            base[z * plane + (size_t)r * g.Mxp + x] = buf[(s << lgC) + col];
+    if (colok) {
+        for (int r = threadIdx.x / lanes_per_row; r < rows_out; r += rstep) {
+            const int srow = spos[INV ? r : slot_of(r, Ky, ny)];
+            const float4 v = *reinterpret_cast<const float4*>(buf + (srow << lgC) + col);
+            *reinterpret_cast<float4*>(gcol + (size_t)r * g.Mxp) = v;
         }
     }
 }

@@ -123,7 +123,7 @@ k_zinv(const cplx<T>* __restrict__ U, cplx<T>* __restrict__ W, Geom g, FftPlan p
 }
 
 template <typename T, int MODE>
-__global__ void __launch_bounds__(kThreadsFwd)
+__global__ void __launch_bounds__(kThreadsFwd, 2)
 k_zfwd(const cplx<T>* __restrict__ W, cplx<T>* __restrict__ U, cplx<T>* __restrict__ H, Geom g,
        FftPlan plan, const double2* __restrict__ tw, const int* __restrict__ pos, int lgTX,
        ZfwdExtra ex, const StepState* __restrict__ st)
@@ -171,62 +171,82 @@ k_zfwd(const cplx<T>* __restrict__ W, cplx<T>* __restrict__ U, cplx<T>* __restri
     const double* E2y = E2x + g.Mx;
     const double* E2z = E2y + g.My;
 
-    for (int e = threadIdx.x; e < (g.Mz << lgTX); e += kThreadsFwd) {
-        const int jz = e >> lgTX, tx = e & (TX - 1);
-        const int q = q0 + tx;
-        if (q >= Q) continue;
-        const int jy = q / g.Mxp, x = q - jy * g.Mxp;
-        const size_t o = (size_t)jz * Q + q;
-        if (x >= g.Mx) {   // row padding stays zero
+    // two modes per batch: the twelve global loads of U and H are issued before
+    // any of the arithmetic that needs them
+    constexpr int kB = 2;
+    const int total = g.Mz << lgTX;
+    for (int e0 = threadIdx.x; e0 < total; e0 += kB * kThreadsFwd) {
+        cplx<T> uo[kB][3], ho[kB][3];
+        int jzs[kB], qs[kB];
+#pragma unroll
+        for (int bb = 0; bb < kB; ++bb) {
+            const int e = e0 + bb * kThreadsFwd;
+            const int jz = e >> lgTX, q = q0 + (e & (TX - 1));
+            jzs[bb] = jz;
+            qs[bb] = (e < total && q < Q) ? q : -1;
+            const size_t o = (size_t)jz * Q + q;
+#pragma unroll
             for (int c = 0; c < 3; ++c) {
-                U[c * Ustride + o] = mkc<T>(0, 0);
-                H[c * Ustride + o] = mkc<T>(0, 0);
+                uo[bb][c] = mkc<T>(0, 0);
+                ho[bb][c] = mkc<T>(0, 0);
+                if (qs[bb] >= 0) {
+                    if (MODE == 0) uo[bb][c] = U[c * Ustride + o];
+                    if (MODE == 0 && !first) ho[bb][c] = H[c * Ustride + o];
+                }
             }
-            continue;
         }
-        const int s = spos[slot_of(jz, g.Kz, nz)];
-        cplx<T> N[3];
-        for (int c = 0; c < 3; ++c) N[c] = cscale(buf[s * C + c * TX + tx], inv_n);
-        const T kx = two_pi * T(x) / T(g.Lx);
-        const T ky = two_pi * T(mode_of(jy, g.Ky)) / T(g.Ly);
-        const T kz = two_pi * T(mode_of(jz, g.Kz)) / T(g.Lz);
-        const T k2 = kx * kx + ky * ky + kz * kz;
-        const bool zero_mode = (x == 0 && jy == 0 && jz == 0);
-        if (!zero_mode) {
-            const T inv_k2 = T(1) / k2;
-            const T kNr = (kx * N[0].x + ky * N[1].x + kz * N[2].x) * inv_k2;
-            const T kNi = (kx * N[0].y + ky * N[1].y + kz * N[2].y) * inv_k2;
-            const T kk[3] = {kx, ky, kz};
-            for (int c = 0; c < 3; ++c) {
-                N[c].x -= kk[c] * kNr;
-                N[c].y -= kk[c] * kNi;
+#pragma unroll
+        for (int bb = 0; bb < kB; ++bb) {
+            if (qs[bb] < 0) continue;
+            const int jz = jzs[bb], q = qs[bb], tx = q - q0;
+            const int jy = q / g.Mxp, x = q - jy * g.Mxp;
+            const size_t o = (size_t)jz * Q + q;
+            if (x >= g.Mx) {   // row padding stays zero
+                for (int c = 0; c < 3; ++c) {
+                    U[c * Ustride + o] = mkc<T>(0, 0);
+                    H[c * Ustride + o] = mkc<T>(0, 0);
+                }
+                continue;
             }
-        } else if (!ex.mean_free) {
-            N[0] = N[1] = N[2] = mkc<T>(0, 0);
-        }
-        if (MODE == 0) {
-            // products of the per-axis factors in the state precision
-            const T e1 = T(E1x[x]) * T(E1y[jy]) * T(E1z[jz]);
-            const T e2 = first ? T(0) : T(E2x[x]) * T(E2y[jy]) * T(E2z[jz]);
-            for (int c = 0; c < 3; ++c) {
-                cplx<T> u = U[c * Ustride + o];
-                cplx<T> r;
-                if (first) {
-                    r = cscale(cadd(u, cscale(N[c], cn)), e1);
-                } else {
-                    cplx<T> h = H[c * Ustride + o];
+            const int s = spos[slot_of(jz, g.Kz, nz)];
+            cplx<T> N[3];
+            for (int c = 0; c < 3; ++c) N[c] = cscale(buf[s * C + c * TX + tx], inv_n);
+            const T kx = two_pi * T(x) / T(g.Lx);
+            const T ky = two_pi * T(mode_of(jy, g.Ky)) / T(g.Ly);
+            const T kz = two_pi * T(mode_of(jz, g.Kz)) / T(g.Lz);
+            const T k2 = kx * kx + ky * ky + kz * kz;
+            const bool zero_mode = (x == 0 && jy == 0 && jz == 0);
+            if (!zero_mode) {
+                const T inv_k2 = T(1) / k2;
+                const T kNr = (kx * N[0].x + ky * N[1].x + kz * N[2].x) * inv_k2;
+                const T kNi = (kx * N[0].y + ky * N[1].y + kz * N[2].y) * inv_k2;
+                const T kk[3] = {kx, ky, kz};
+                for (int c = 0; c < 3; ++c) {
+                    N[c].x -= kk[c] * kNr;
+                    N[c].y -= kk[c] * kNi;
+                }
+            } else if (!ex.mean_free) {
+                N[0] = N[1] = N[2] = mkc<T>(0, 0);
+            }
+            if (MODE == 0) {
+                // products of the per-axis factors in the state precision
+                const T e1 = T(E1x[x]) * T(E1y[jy]) * T(E1z[jz]);
+                const T e2 = first ? T(0) : T(E2x[x]) * T(E2y[jy]) * T(E2z[jz]);
+                for (int c = 0; c < 3; ++c) {
+                    const cplx<T> u = uo[bb][c], h = ho[bb][c];
+                    cplx<T> r;
                     r.x = e1 * (u.x + cn * N[c].x) - co * e2 * h.x;
                     r.y = e1 * (u.y + cn * N[c].y) - co * e2 * h.y;
+                    U[c * Ustride + o] = r;
+                    H[c * Ustride + o] = N[c];
                 }
-                U[c * Ustride + o] = r;
-                H[c * Ustride + o] = N[c];
-            }
-        } else {
-            for (int c = 0; c < 3; ++c) {
-                cplx<T> u = N[c];
-                if (zero_mode && !ex.mean_free) u = mkc<T>(T(ex.u_inf[c]), 0);
-                U[c * Ustride + o] = u;
-                H[c * Ustride + o] = mkc<T>(0, 0);
+            } else {
+                for (int c = 0; c < 3; ++c) {
+                    cplx<T> u = N[c];
+                    if (zero_mode && !ex.mean_free) u = mkc<T>(T(ex.u_inf[c]), 0);
+                    U[c * Ustride + o] = u;
+                    H[c * Ustride + o] = mkc<T>(0, 0);
+                }
             }
         }
     }
