@@ -59,16 +59,25 @@ k_zinv(const cplx<T>* __restrict__ U, cplx<T>* __restrict__ W, Geom g, FftPlan p
     const T kx = two_pi * T(x) / T(g.Lx);
     const T ky = two_pi * T(mode_of(jy, g.Ky)) / T(g.Ly);
     const int nz = g.nz, Kz = g.Kz, Mz = g.Mz;
+    constexpr int VEC = 16 / sizeof(cplx<T>);
+    const int lpr = TX / VEC;                  // lanes per row of the tile
+    const int rstep = kThreadsInv / lpr;
+    const int txv = (threadIdx.x % lpr) * VEC;
+    const int qv = q0 + txv;                   // Q is a multiple of VEC
 
     for (int f = 0; f < nf; ++f) {
         if (f < 3) {
-            for (int e = threadIdx.x; e < (nz << lgTX); e += kThreadsInv) {
-                const int s = e >> lgTX;
+            // 16-byte copies of VEC adjacent columns; U's row padding is zero,
+            // so pairs that straddle Mx copy zeros
+            for (int s = threadIdx.x / lpr; s < nz; s += rstep) {
                 const int jz = s <= Kz ? s : (s >= nz - Kz ? s - nz + Mz : -1);
-                if (kept && jz >= 0)
-                    cp_async_cplx<T>(buf + e, U + f * Ustride + (size_t)jz * Q + q);
-                else
-                    buf[e] = mkc<T>(0, 0);
+                cplx<T>* dst = buf + (s << lgTX) + txv;
+                if (qv < Q && jz >= 0) {
+                    cp_async_16(dst, U + f * Ustride + (size_t)jz * Q + qv);
+                } else {
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) dst[v] = mkc<T>(0, 0);
+                }
             }
             cp_async_wait_all();
         } else {
@@ -113,10 +122,11 @@ k_zinv(const cplx<T>* __restrict__ U, cplx<T>* __restrict__ W, Geom g, FftPlan p
         }
         __syncthreads();
         fft_dif<T, true>(buf, TX, TX, plan, tws);
-        if (qok) {
-            cplx<T>* out = W + (size_t)f * nz * Wplane + q;
-            for (int e = threadIdx.x; e < (nz << lgTX); e += kThreadsInv)
-                out[(size_t)(e >> lgTX) * Wplane] = buf[(spos[e >> lgTX] << lgTX) + tx];
+        if (qv < Q) {
+            cplx<T>* out = W + (size_t)f * nz * Wplane + qv;
+            for (int z = threadIdx.x / lpr; z < nz; z += rstep)
+                *reinterpret_cast<float4*>(out + (size_t)z * Wplane) =
+                    *reinterpret_cast<const float4*>(buf + (spos[z] << lgTX) + txv);
         }
         __syncthreads();
     }
@@ -142,13 +152,21 @@ k_zfwd(const cplx<T>* __restrict__ W, cplx<T>* __restrict__ U, cplx<T>* __restri
     const int nz = g.nz;
     load_tables<T>(tws, spos, tw, pos, nz, nz);
 
-    for (int e = threadIdx.x; e < nz * C; e += kThreadsFwd) {
-        const int z = e / C, col = e - z * C;
+    {
+        constexpr int VEC = 16 / sizeof(cplx<T>);
+        const int lpr = C / VEC;               // lanes per row of the tile
+        const int rstep = kThreadsFwd / lpr;
+        const int col = (threadIdx.x % lpr) * VEC;
         const int c = col >> lgTX, q = q0 + (col & (TX - 1));
-        if (q < Q)
-            cp_async_cplx<T>(buf + e, W + ((size_t)c * nz + z) * Wplane + q);
-        else
-            buf[e] = mkc<T>(0, 0);
+        for (int z = threadIdx.x / lpr; z < nz; z += rstep) {
+            cplx<T>* dst = buf + z * C + col;
+            if (q < Q) {
+                cp_async_16(dst, W + ((size_t)c * nz + z) * Wplane + q);
+            } else {
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) dst[v] = mkc<T>(0, 0);
+            }
+        }
     }
     cp_async_wait_all();
     __syncthreads();
