@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="flusi", choices=["flusi", "reference"])
     ap.add_argument("--grid", type=int, default=512)
+    ap.add_argument("--shape", default=None,
+                    help="nx,ny,nz: a reduced grid of the same box and insect (profiling)")
     ap.add_argument("--fp64-steps", type=int, default=10)
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -211,7 +213,11 @@ def run_flusi(args):
 
     n = args.grid
     cfg, ins = workloads.config_model_insect(n)
-    N = n ** 3
+    if args.shape:
+        shape = tuple(int(v) for v in args.shape.split(","))
+        cfg = dict(cfg, n=shape)
+        ins = workloads.model_insect(cfg["L"], shape)
+    N = int(np.prod(cfg["n"]))
     u0 = bench_field(cfg)
     peaks, peak_src = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
@@ -256,7 +262,7 @@ def run_flusi(args):
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             tr = json.load(f)
-        ent = tr.get(f"{dom}@{n}^3/fp32")
+        ent = tr.get(f"{dom}@{'x'.join(map(str, cfg['n']))}/fp32")
         if ent and ent.get("source_hash") == source_hash():
             traffic = ent["bytes_per_launch"]
     except (OSError, ValueError):
@@ -326,10 +332,10 @@ def run_flusi(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"model insect {n}^3 FP32: ellipsoid body (0.5, 0.12) + 2 flapping "
+        "config": {"workload": f"model insect {'x'.join(map(str, cfg['n']))} FP32: ellipsoid body (0.5, 0.12) + 2 flapping "
                                "plates (c 0.3, R 1, 4dx thick, phi 60deg sin, alpha 45deg cos), "
                                "Re 300, u_inf (0.25,0,0), C_eta 1e-3, CFL 0.1 adaptive dt",
-                   "grid": [n, n, n], "box": [4.0, 4.0, 4.0], "precision": "fp32",
+                   "grid": list(cfg["n"]), "box": [4.0, 4.0, 4.0], "precision": "fp32",
                    "initial": "inflow + band-limited divergence-free waves",
                    "l2": f"inputs larger than L2: {step_bytes / 1e9:.1f} GB moved per step",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
