@@ -208,6 +208,106 @@ __device__ void fft_dit(cplx<T>* buf, int C, int ld, const FftPlan& plan, const 
     fft_run<T, INV, false>(buf, C, ld, plan, tw, s0, s1 < 0 ? plan.nst : s1);
 }
 
+// ---------------------------------------------------------------------------
+// Column transforms with their first stage fed from registers loaded by a
+// functor and (optionally) their last stage handing results to a functor, so
+// the tile goes through shared memory only between stages.
+//   load(row) -> cplx<T>   input row `row` (natural order) of this thread's column
+//   store(f, v)            output frequency f of this thread's column
+// The thread-to-column map is fft_run's: column threadIdx.x % C.
+
+// DIF stage 0: butterfly j takes rows j + m t (m = n / R) and, after the
+// twiddles w^{j t}, leaves them where fft_stage would.
+template <typename T, int R, bool INV, class Load>
+__device__ __forceinline__ void fft_stage_first(cplx<T>* buf, int ld, int col, int jt, int P, int m,
+                                                int tstep, const cplx<T>* tw, Load& load)
+{
+#pragma unroll 2
+    for (int j = jt; j < m; j += P) {
+        cplx<T> v[R];
+#pragma unroll
+        for (int t = 0; t < R; ++t) v[t] = load(j + t * m);
+        Dft<T, R, INV>::run(v);
+        if (j != 0) twiddle_table<T, R, INV>(v, tw, j * tstep);
+        cplx<T>* p = buf + j * ld + col;
+#pragma unroll
+        for (int t = 0; t < R; ++t) p[t * m * ld] = v[t];
+    }
+    __syncthreads();
+}
+
+// DIF last stage (span 1, no twiddles): butterfly j holds rows j R + t, which
+// are frequencies f0 + t fstep with f0 the frequency of row j R and fstep = n / R.
+template <typename T, int R, bool INV, class Store>
+__device__ __forceinline__ void fft_stage_last(const cplx<T>* buf, int ld, int col, int jt, int P,
+                                               int nbf, int fstep, const int* sinv, Store& store)
+{
+#pragma unroll 2
+    for (int j = jt; j < nbf; j += P) {
+        cplx<T> v[R];
+        const cplx<T>* p = buf + j * R * ld + col;
+#pragma unroll
+        for (int t = 0; t < R; ++t) v[t] = p[t * ld];
+        Dft<T, R, INV>::run(v);
+        const int f0 = sinv[j * R];
+#pragma unroll
+        for (int t = 0; t < R; ++t) store(f0 + t * fstep, v[t]);
+    }
+}
+
+// Stage 0 from `load`, the middle stages in shared memory, the last stage to
+// `store` (sinv[row] = frequency held by that row).  All threads must call.
+template <typename T, bool INV, class Load, class Store>
+__device__ void fft_dif_io(cplx<T>* buf, int C, int ld, const FftPlan& plan, const cplx<T>* tw,
+                           const int* sinv, Load load, Store store)
+{
+    const int P = blockDim.x / C, col = threadIdx.x % C, jt = threadIdx.x / C;
+    const int m = plan.m[0], ts = plan.tstep[0];
+    switch (plan.radix[0]) {
+    case 8: fft_stage_first<T, 8, INV>(buf, ld, col, jt, P, m, ts, tw, load); break;
+    case 4: fft_stage_first<T, 4, INV>(buf, ld, col, jt, P, m, ts, tw, load); break;
+    case 3: fft_stage_first<T, 3, INV>(buf, ld, col, jt, P, m, ts, tw, load); break;
+    default: fft_stage_first<T, 2, INV>(buf, ld, col, jt, P, m, ts, tw, load); break;
+    }
+    const int last = plan.nst - 1;
+    if (last == 0) {   // a one-stage transform is in natural order already
+        for (int f = jt; f < plan.n; f += P) store(f, buf[f * ld + col]);
+        return;
+    }
+    fft_run<T, INV, true>(buf, C, ld, plan, tw, 1, last);
+    const int R = plan.radix[last], nbf = plan.n / R, fstep = plan.n / R;
+    switch (R) {
+    case 8: fft_stage_last<T, 8, INV>(buf, ld, col, jt, P, nbf, fstep, sinv, store); break;
+    case 4: fft_stage_last<T, 4, INV>(buf, ld, col, jt, P, nbf, fstep, sinv, store); break;
+    case 3: fft_stage_last<T, 3, INV>(buf, ld, col, jt, P, nbf, fstep, sinv, store); break;
+    default: fft_stage_last<T, 2, INV>(buf, ld, col, jt, P, nbf, fstep, sinv, store); break;
+    }
+}
+
+// All stages but the last in shared memory (input tile in natural order), the
+// last stage to `store`.  All threads must call.
+template <typename T, bool INV, class Store>
+__device__ void fft_dif_out(cplx<T>* buf, int C, int ld, const FftPlan& plan, const cplx<T>* tw,
+                            const int* sinv, Store store)
+{
+    const int P = blockDim.x / C, col = threadIdx.x % C, jt = threadIdx.x / C;
+    const int last = plan.nst - 1;
+    fft_run<T, INV, true>(buf, C, ld, plan, tw, 0, last);
+    const int R = plan.radix[last], nbf = plan.n / R, fstep = plan.n / R;
+    switch (R) {
+    case 8: fft_stage_last<T, 8, INV>(buf, ld, col, jt, P, nbf, fstep, sinv, store); break;
+    case 4: fft_stage_last<T, 4, INV>(buf, ld, col, jt, P, nbf, fstep, sinv, store); break;
+    case 3: fft_stage_last<T, 3, INV>(buf, ld, col, jt, P, nbf, fstep, sinv, store); break;
+    default: fft_stage_last<T, 2, INV>(buf, ld, col, jt, P, nbf, fstep, sinv, store); break;
+    }
+}
+
+// Inverse digit-reversal table in shared memory: sinv[pos[f]] = f.
+__device__ __forceinline__ void load_inverse_pos(int* sinv, const int* pos_src, int n)
+{
+    for (int f = threadIdx.x; f < n; f += blockDim.x) sinv[pos_src[f]] = f;
+}
+
 // Copy the twiddle table (FP64, global; ntw entries exp(-2 pi i j / ntw))
 // and the n-entry digit-reversal table into shared memory.
 template <typename T>

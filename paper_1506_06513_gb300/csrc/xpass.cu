@@ -115,6 +115,16 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
+// Sum over the warp in the pass's own precision; the force and moment partials
+// of one warp's 64 points are added in T and only the warp totals in FP64
+// (FP64 adds are scarce on this part: a per-point FP64 accumulation cost as
+// much as the transforms of the rows that meet the insect).
+template <typename T> __device__ __forceinline__ T warp_sum_t(T v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 // c2r pre-processing: Z[k] = (X[k] + X*[m]) + i (X[k] - X*[m]) w^{-k} with the
 // mirror value Xm = X[nh - k].
 template <typename T>
@@ -479,8 +489,8 @@ k_xpass(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict
                     for (int cc = 0; cc < 3; ++cc) {
                         const bool has = valid && (colr[0] == cc + 1 || colr[1] == cc + 1);
                         if (!__any_sync(0xffffffffu, has)) continue;
-                        double v[12];
-                        for (int k = 0; k < 12; ++k) v[k] = 0.0;
+                        T v[12];   // partial over this warp's points, in T
+                        for (int k = 0; k < 12; ++k) v[k] = T(0);
                         if (has) {
                             for (int h = 0; h < 2; ++h) {
                                 if (colr[h] != cc + 1) continue;
@@ -494,16 +504,16 @@ k_xpass(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict
                                 cross3(rv, pu, m1);
                                 cross3(rv, cu, m2);
                                 for (int c = 0; c < 3; ++c) {
-                                    v[c] += double(pu[c]);
-                                    v[3 + c] += double(m1[c]);
-                                    v[6 + c] += double(cu[c]);
-                                    v[9 + c] += double(m2[c]);
+                                    v[c] += pu[c];
+                                    v[3 + c] += m1[c];
+                                    v[6 + c] += cu[c];
+                                    v[9 + c] += m2[c];
                                 }
                             }
                         }
-                        for (int k = 0; k < 12; ++k) v[k] = warp_sum(v[k]);
+                        for (int k = 0; k < 12; ++k) v[k] = warp_sum_t(v[k]);
                         if (lane == 0)
-                            for (int k = 0; k < 12; ++k) wacc[warp * 36 + cc * 12 + k] += v[k];
+                            for (int k = 0; k < 12; ++k) wacc[warp * 36 + cc * 12 + k] += double(v[k]);
                     }
                 }
             }
@@ -567,7 +577,9 @@ k_xpass(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict
 // registers.  After the inverse passes logical row R q + d holds the point
 // pair p = q + R d.
 // ---------------------------------------------------------------------------
-template <int R> constexpr int sq_rows() { return 192 / (6 * R); }   // rows per tile
+// rows per tile: each group of R lanes inverse-transforms two lines (u and
+// omega fields) and forward-transforms one (the three NL fields)
+template <int R> constexpr int sq_rows() { return 384 / (6 * R); }
 
 template <typename T, int R>
 __device__ __forceinline__ void sq_exchange_pre(cplx<T>* x, int j, int width, const cplx<T>* twx)
@@ -605,7 +617,7 @@ __device__ __forceinline__ void sq_exchange_pre(cplx<T>* x, int j, int width, co
 }
 
 template <typename T, int R>
-__global__ void __launch_bounds__(192, sizeof(T) == 4 ? 4 : 1)
+__global__ void __launch_bounds__(192, sizeof(T) == 4 ? 3 : 1)
 k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExtra ex,
            const StepState* __restrict__ st)
 {
@@ -677,23 +689,11 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
     int bad = 0;
     const T dxT = T(g.dx), dyT = T(g.dy), dzT = T(g.dz);
     const FrameT<T>& F = *Fs;
-    cplx<T>* line = buf + c * CS;
-    const int fld = c / RB, lrr = c % RB;
+    constexpr int NG = 192 / R;            // lane groups; group c owns lines c and c + NG
 
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int row0 = tile * RB;
-        // ---- loads of this lane's kept x-modes, straight into registers
         cplx<T> v[R];
-        {
-            const int r = row0 + lrr;
-            const cplx<T>* src = W + ((size_t)fld * nrows + (r < nrows ? r : 0)) * Mxp;
-#pragma unroll
-            for (int t = 0; t < R; ++t) {
-                const int k = j + R * t;
-                v[t] = (r < nrows && k < Mx) ? src[k] : mkc<T>(0, 0);
-            }
-            if (j == 0) v[0].y = T(0);     // a real line has a real mean
-        }
         if (tid < RB) {
             const int r = row0 + tid;
             int mask = 0;
@@ -707,19 +707,34 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
             }
             rowmask[tid] = mask;
         }
-        // ---- inverse: c2r pre-processing, DIF stage 0 (radix R + twiddles), stage 1
-        sq_exchange_pre<T, R>(v, j, R, twx);
-        Dft<T, R, true>::run(v);
+#pragma unroll 1
+        for (int li = 0; li < 2; ++li) {
+            const int cl = c + li * NG;
+            const int fld = cl / RB, lrr = cl % RB;
+            cplx<T>* line = buf + cl * CS;
+            // ---- this lane's kept x-modes, straight from global memory into registers
+            const int r = row0 + lrr;
+            const cplx<T>* src = W + ((size_t)fld * nrows + (r < nrows ? r : 0)) * Mxp;
 #pragma unroll
-        for (int q = 1; q < R; ++q) v[q] = cmul(v[q], cconj(tw2[q * R + j]));
+            for (int t = 0; t < R; ++t) {
+                const int k = j + R * t;
+                v[t] = (r < nrows && k < Mx) ? src[k] : mkc<T>(0, 0);
+            }
+            if (j == 0) v[0].y = T(0);     // a real line has a real mean
+            // ---- inverse: c2r pre-processing, DIF stage 0 (radix R + twiddles), stage 1
+            sq_exchange_pre<T, R>(v, j, R, twx);
+            Dft<T, R, true>::run(v);
 #pragma unroll
-        for (int q = 0; q < R; ++q) line[j + R * q + q] = v[q];
-        __syncwarp();
+            for (int q = 1; q < R; ++q) v[q] = cmul(v[q], cconj(tw2[q * R + j]));
 #pragma unroll
-        for (int i = 0; i < R; ++i) v[i] = line[R * j + i + j];
-        Dft<T, R, true>::run(v);
+            for (int q = 0; q < R; ++q) line[j + R * q + q] = v[q];
+            __syncwarp();
 #pragma unroll
-        for (int d = 0; d < R; ++d) line[R * j + d + j] = v[d];
+            for (int i = 0; i < R; ++i) v[i] = line[R * j + i + j];
+            Dft<T, R, true>::run(v);
+#pragma unroll
+            for (int d = 0; d < R; ++d) line[R * j + d + j] = v[d];
+        }
         __syncthreads();
 
         // ---- physical space: chi, u_s, NL = u x omega - chi/C_eta (u - u_s), sums
@@ -782,8 +797,8 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
                     for (int cc = 0; cc < 3; ++cc) {
                         const bool has = valid && (colr[0] == cc + 1 || colr[1] == cc + 1);
                         if (!__any_sync(0xffffffffu, has)) continue;
-                        double acc[12];
-                        for (int k = 0; k < 12; ++k) acc[k] = 0.0;
+                        T acc[12];   // partial over this warp's points, in T
+                        for (int k = 0; k < 12; ++k) acc[k] = T(0);
                         if (has) {
                             for (int h = 0; h < 2; ++h) {
                                 if (colr[h] != cc + 1) continue;
@@ -797,16 +812,16 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
                                 cross3(rv, pu, m1);
                                 cross3(rv, cu, m2);
                                 for (int q = 0; q < 3; ++q) {
-                                    acc[q] += double(pu[q]);
-                                    acc[3 + q] += double(m1[q]);
-                                    acc[6 + q] += double(cu[q]);
-                                    acc[9 + q] += double(m2[q]);
+                                    acc[q] += pu[q];
+                                    acc[3 + q] += m1[q];
+                                    acc[6 + q] += cu[q];
+                                    acc[9 + q] += m2[q];
                                 }
                             }
                         }
-                        for (int k = 0; k < 12; ++k) acc[k] = warp_sum(acc[k]);
+                        for (int k = 0; k < 12; ++k) acc[k] = warp_sum_t(acc[k]);
                         if (lane == 0)
-                            for (int k = 0; k < 12; ++k) wacc[warp * 36 + cc * 12 + k] += acc[k];
+                            for (int k = 0; k < 12; ++k) wacc[warp * 36 + cc * 12 + k] += double(acc[k]);
                     }
                 }
             }
@@ -814,14 +829,17 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
         }
         __syncthreads();
 
-        // ---- forward on the three NL lines of each row: DIT stage 1, stage 0, r2c post
-        if (c < 3 * RB) {
+        // ---- forward on the three NL lines of each row (one per lane group):
+        //      DIT stage 1, stage 0, r2c post-processing and store
+        {
+            cplx<T>* line = buf + c * CS;
+            const int fld = c / RB, lrr = c % RB;
 #pragma unroll
             for (int i = 0; i < R; ++i) v[i] = line[R * j + i + j];
             Dft<T, R, false>::run(v);
 #pragma unroll
             for (int d = 0; d < R; ++d) line[R * j + d + j] = v[d];
-            __syncwarp();   // the three NL rows' lanes fill whole warps
+            __syncwarp();
 #pragma unroll
             for (int t = 0; t < R; ++t) v[t] = line[j + R * t + t];
 #pragma unroll
@@ -995,7 +1013,7 @@ cudaError_t launch_xpass(int fp64, int mode, void* W, const Geom& g, const FftPl
 
 cudaError_t configure_xpass()
 {
-    const int big = 100 * 1024;
+    const int big = 200 * 1024;
     cudaError_t e;
 #define FLUSI_SMEM(fn) \
     if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;

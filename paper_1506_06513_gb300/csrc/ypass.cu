@@ -1,9 +1,11 @@
 // y-axis transform pass (part of the 3-D FFTs of Algorithm 1 step c).
 //
 // A tile is TX consecutive x-mode columns of NP consecutive z planes of one
-// component: every global access is a run of TX complex values (128 bytes),
-// the column FFT runs in shared memory, and the pass works in place (a tile
-// reads all of its rows before it writes any).
+// component: every global access is a run of TX complex values (128 bytes).
+// Rows arrive by 16-byte asynchronous copies, all FFT stages but the last run
+// in shared memory and the last one stores its results to global memory from
+// registers; the pass works in place (a tile reads all of its rows before its
+// first barrier and writes after its last).
 //   inverse: rows j < My hold the kept y-modes 0..Ky, -Ky..-1 -> ny grid rows
 //   forward: ny grid rows -> the My kept y-modes (2/3 rule, pruned output)
 #include "fft.cuh"
@@ -27,7 +29,7 @@ k_ypass(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict
     const int TX = 1 << lgTX, lgC = lgTX + lgNP, C = 1 << lgC;
     cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
     cplx<T>* tws = buf + (g.ny << lgC);
-    int* spos = reinterpret_cast<int*>(tws + g.ny);
+    int* sinv = reinterpret_cast<int*>(tws + g.ny);
     const int nxb = ceil_div(g.Mxp, TX), nzb = ceil_div(g.nz, 1 << lgNP);
     int b = blockIdx.x;
     const int xb = b % nxb;
@@ -39,38 +41,49 @@ k_ypass(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict
     const size_t plane = (size_t)g.ny * g.Mxp;
     cplx<T>* base = W + (size_t)c * g.nz * plane;
 
-    load_tables<T>(tws, spos, tw, pos, g.ny, g.ny);
+    load_tables<T>(tws, nullptr, tw, nullptr, g.ny, 0);
+    load_inverse_pos(sinv, pos, g.ny);
     const int ny = g.ny, My = g.My, Ky = g.Ky;
-    // each lane moves VEC adjacent columns (16 bytes) of a fixed column group;
-    // TX is a multiple of VEC, so the lane's column, plane and x stay fixed
-    constexpr int VEC = 16 / sizeof(cplx<T>);
-    const int lanes_per_row = C / VEC;
-    const int rstep = kThreads / lanes_per_row;
-    const int col = (threadIdx.x % lanes_per_row) * VEC;
+    const int ld = g.Mxp;   // row stride; a plane holds fewer than 2^31 values
+    // this thread's column for the transform stages (fft_run's map)
+    const int col = threadIdx.x % C;
     const int z = z0 + (col >> lgTX), x = x0 + (col & (TX - 1));
-    const bool colok = z < g.nz && x < g.Mxp;   // Mxp and TX are multiples of VEC
+    const bool colok = z < g.nz && x < g.Mxp;
     cplx<T>* gcol = base + (size_t)(colok ? z : 0) * plane + (colok ? x : 0);
-    for (int s = threadIdx.x / lanes_per_row; s < ny; s += rstep) {
-        // slot s holds mode m = s (s <= Ky) or m = s - ny (s >= ny - Ky)
-        const int j = INV ? (s <= Ky ? s : (s >= ny - Ky ? s - ny + My : -1)) : s;
-        cplx<T>* dst = buf + (s << lgC) + col;
-        if (colok && j >= 0) {
-            cp_async_16(dst, gcol + (size_t)j * g.Mxp);
-        } else {
+    {
+        // 16-byte asynchronous copies: each lane moves VEC adjacent columns
+        constexpr int VEC = 16 / sizeof(cplx<T>);
+        const int lanes_per_row = C / VEC;
+        const int rstep = kThreads / lanes_per_row;
+        const int cv = (threadIdx.x % lanes_per_row) * VEC;
+        const int zv = z0 + (cv >> lgTX), xv = x0 + (cv & (TX - 1));
+        const bool okv = zv < g.nz && xv < g.Mxp;   // Mxp and TX are multiples of VEC
+        const cplx<T>* gv = base + (size_t)(okv ? zv : 0) * plane + (okv ? xv : 0);
+        for (int s = threadIdx.x / lanes_per_row; s < ny; s += rstep) {
+            // grid slot s <- row j(s) (inverse: modes 0..Ky, -Ky..-1 in rows j < My)
+            const int j = INV ? (s <= Ky ? s : (s >= ny - Ky ? s - ny + My : -1)) : s;
+            cplx<T>* dst = buf + (s << lgC) + cv;
+            if (okv && j >= 0) {
+                cp_async_16(dst, gv + j * ld);
+            } else {
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) dst[v] = mkc<T>(0, 0);
+                for (int v = 0; v < VEC; ++v) dst[v] = mkc<T>(0, 0);
+            }
         }
+        cp_async_wait_all();
     }
-    cp_async_wait_all();
     __syncthreads();
-    fft_dif<T, INV>(buf, C, C, plan, tws);
-    const int rows_out = INV ? ny : My;
-    if (colok) {
-        for (int r = threadIdx.x / lanes_per_row; r < rows_out; r += rstep) {
-            const int srow = spos[INV ? r : slot_of(r, Ky, ny)];
-            const float4 v = *reinterpret_cast<const float4*>(buf + (srow << lgC) + col);
-            *reinterpret_cast<float4*>(gcol + (size_t)r * g.Mxp) = v;
-        }
+    if (INV) {
+        auto store = [&](int f, cplx<T> v) {
+            if (colok) gcol[f * ld] = v;
+        };
+        fft_dif_out<T, true>(buf, C, C, plan, tws, sinv, store);
+    } else {
+        auto store = [&](int f, cplx<T> v) {   // keep modes |m| <= Ky only
+            const int r = f <= Ky ? f : (f >= ny - Ky ? f - ny + My : -1);
+            if (colok && r >= 0) gcol[r * ld] = v;
+        };
+        fft_dif_out<T, false>(buf, C, C, plan, tws, sinv, store);
     }
 }
 

@@ -2,6 +2,9 @@
 //
 // Columns along z are indexed by q = jy * Mxp + x over the kept y-modes: a
 // tile is TX consecutive q, so every global access is a run of TX complex.
+// Stored fields arrive by 16-byte asynchronous copies; the vorticity is formed
+// in registers as the first FFT stage loads it.  The inverse pass stores its
+// last stage's results from registers.
 //
 // zinv (Algorithm 1 step c, first half): loads the state u_hat, forms
 //   omega_hat = i k x u_hat on the fly (Sec. 2.4: grad -> i k), fills the
@@ -41,12 +44,13 @@ k_zinv(const cplx<T>* __restrict__ U, cplx<T>* __restrict__ W, Geom g, FftPlan p
     const int TX = 1 << lgTX;
     cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
     cplx<T>* tws = buf + (g.nz << lgTX);
-    int* spos = reinterpret_cast<int*>(tws + g.nz);
+    int* sinv = reinterpret_cast<int*>(tws + g.nz);
     const int Q = g.My * g.Mxp;
     const int q0 = blockIdx.x * TX;
     const size_t Ustride = (size_t)g.Mz * Q;           // between components of U
     const size_t Wplane = (size_t)g.ny * g.Mxp;        // between z planes of W
-    load_tables<T>(tws, spos, tw, pos, g.nz, g.nz);
+    load_tables<T>(tws, nullptr, tw, nullptr, g.nz, 0);
+    load_inverse_pos(sinv, pos, g.nz);
 
     // this thread's column is fixed across the strided loops (TX divides blockDim)
     const int tx = threadIdx.x & (TX - 1);
@@ -59,16 +63,21 @@ k_zinv(const cplx<T>* __restrict__ U, cplx<T>* __restrict__ W, Geom g, FftPlan p
     const T kx = two_pi * T(x) / T(g.Lx);
     const T ky = two_pi * T(mode_of(jy, g.Ky)) / T(g.Ly);
     const int nz = g.nz, Kz = g.Kz, Mz = g.Mz;
-    constexpr int VEC = 16 / sizeof(cplx<T>);
-    const int lpr = TX / VEC;                  // lanes per row of the tile
-    const int rstep = kThreadsInv / lpr;
-    const int txv = (threadIdx.x % lpr) * VEC;
-    const int qv = q0 + txv;                   // Q is a multiple of VEC
+    __syncthreads();
 
     for (int f = 0; f < nf; ++f) {
+        cplx<T>* out = W + (size_t)f * nz * Wplane + (qok ? q : 0);
+        auto store = [&](int z, cplx<T> v) {
+            if (qok) out[(size_t)z * Wplane] = v;
+        };
         if (f < 3) {
-            // 16-byte copies of VEC adjacent columns; U's row padding is zero,
-            // so pairs that straddle Mx copy zeros
+            // U's row padding (x >= Mx) is zero
+            // 16-byte asynchronous copies of VEC adjacent columns
+            constexpr int VEC = 16 / sizeof(cplx<T>);
+            const int lpr = TX / VEC;                  // lanes per row of the tile
+            const int rstep = kThreadsInv / lpr;
+            const int txv = (threadIdx.x % lpr) * VEC;
+            const int qv = q0 + txv;                   // Q is a multiple of VEC
             for (int s = threadIdx.x / lpr; s < nz; s += rstep) {
                 const int jz = s <= Kz ? s : (s >= nz - Kz ? s - nz + Mz : -1);
                 cplx<T>* dst = buf + (s << lgTX) + txv;
@@ -80,53 +89,27 @@ k_zinv(const cplx<T>* __restrict__ U, cplx<T>* __restrict__ W, Geom g, FftPlan p
                 }
             }
             cp_async_wait_all();
+            __syncthreads();
+            fft_dif_out<T, true>(buf, TX, TX, plan, tws, sinv, store);
         } else {
-            // omega = i (k x u): two velocity components per value; loads are
-            // issued in batches of kB before their results are used
-            constexpr int kB = 4;
+            // omega = i (k x u) from two velocity components
             const int cA = f == 3 ? 2 : f == 4 ? 0 : 1;
             const int cB = f == 3 ? 1 : f == 4 ? 2 : 0;
             const T kb = f == 3 ? T(0) : f == 4 ? kx : ky;   // kz enters per mode
             const T ka = f == 3 ? ky : f == 4 ? T(0) : kx;
-            for (int e0 = threadIdx.x; e0 < (nz << lgTX); e0 += kB * kThreadsInv) {
-                cplx<T> a[kB], b[kB];
-                int jzs[kB];
-#pragma unroll
-                for (int r = 0; r < kB; ++r) {
-                    const int e = e0 + r * kThreadsInv;
-                    const int s = e >> lgTX;
-                    int jz = s <= Kz ? s : (s >= nz - Kz ? s - nz + Mz : -1);
-                    if (e >= (nz << lgTX) || !kept) jz = -1;
-                    jzs[r] = jz;
-                    a[r] = b[r] = mkc<T>(0, 0);
-                    if (jz >= 0) {
-                        a[r] = U[cA * Ustride + (size_t)jz * Q + q];
-                        b[r] = U[cB * Ustride + (size_t)jz * Q + q];
-                    }
-                }
-#pragma unroll
-                for (int r = 0; r < kB; ++r) {
-                    const int e = e0 + r * kThreadsInv;
-                    if (e >= (nz << lgTX)) break;
-                    cplx<T> v = mkc<T>(0, 0);
-                    if (jzs[r] >= 0) {
-                        const T kz = two_pi * T(mode_of(jzs[r], Kz)) / T(g.Lz);
-                        // f=3: ky uz - kz uy; f=4: kz ux - kx uz; f=5: kx uy - ky ux
-                        const T k1 = f == 4 ? kz : ka;
-                        const T k2 = f == 3 ? kz : kb;
-                        v = cmuli(mkc<T>(k1 * a[r].x - k2 * b[r].x, k1 * a[r].y - k2 * b[r].y));
-                    }
-                    buf[e] = v;
-                }
-            }
-        }
-        __syncthreads();
-        fft_dif<T, true>(buf, TX, TX, plan, tws);
-        if (qv < Q) {
-            cplx<T>* out = W + (size_t)f * nz * Wplane + qv;
-            for (int z = threadIdx.x / lpr; z < nz; z += rstep)
-                *reinterpret_cast<float4*>(out + (size_t)z * Wplane) =
-                    *reinterpret_cast<const float4*>(buf + (spos[z] << lgTX) + txv);
+            const cplx<T>* srcA = U + cA * Ustride + (qok ? q : 0);
+            const cplx<T>* srcB = U + cB * Ustride + (qok ? q : 0);
+            auto load = [&](int s) -> cplx<T> {
+                const int jz = s <= Kz ? s : (s >= nz - Kz ? s - nz + Mz : -1);
+                if (!kept || jz < 0) return mkc<T>(0, 0);
+                const cplx<T> a = srcA[(size_t)jz * Q], b = srcB[(size_t)jz * Q];
+                const T kz = two_pi * T(mode_of(jz, Kz)) / T(g.Lz);
+                // f=3: ky uz - kz uy; f=4: kz ux - kx uz; f=5: kx uy - ky ux
+                const T k1 = f == 4 ? kz : ka;
+                const T k2 = f == 3 ? kz : kb;
+                return cmuli(mkc<T>(k1 * a.x - k2 * b.x, k1 * a.y - k2 * b.y));
+            };
+            fft_dif_io<T, true>(buf, TX, TX, plan, tws, sinv, load, store);
         }
         __syncthreads();
     }
@@ -151,7 +134,7 @@ k_zfwd(const cplx<T>* __restrict__ W, cplx<T>* __restrict__ U, cplx<T>* __restri
     const size_t Ustride = (size_t)g.Mz * Q;
     const int nz = g.nz;
     load_tables<T>(tws, spos, tw, pos, nz, nz);
-
+    __syncthreads();
     {
         constexpr int VEC = 16 / sizeof(cplx<T>);
         const int lpr = C / VEC;               // lanes per row of the tile
