@@ -120,8 +120,11 @@ int flusi_workspace_bytes(flusi_t h, size_t *bytes);
 
 /* Bind a caller-owned device workspace (>= flusi_workspace_bytes, 256-byte
  * aligned, outliving the handle) and a CUDA stream (cudaStream_t; NULL is the
- * legacy default stream).  All later work is enqueued on that stream.  Zeroes
- * the workspace and builds the FFT twiddle tables.  FLUSI_ENOMEM if too small. */
+ * legacy default stream).  All later work is enqueued on that stream: a step
+ * runs its two single-block kernels on a private stream that forks from it
+ * and joins back into it within the step, so work ordered on the bound stream
+ * before and after a step sees the whole step.  Zeroes the workspace and
+ * builds the FFT twiddle tables.  FLUSI_ENOMEM if too small. */
 int flusi_bind(flusi_t h, void *dev_workspace, size_t bytes, void *cuda_stream);
 
 /* Set the velocity u [3][nz][ny][nx] (Algorithm 1 step 1, initial condition):

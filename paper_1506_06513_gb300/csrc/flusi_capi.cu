@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <initializer_list>
 #include <new>
 #include <string>
 #include <vector>
@@ -36,6 +37,10 @@ struct flusi_s {
     int has_state = 0, poisoned = 0;
     long long rows_read = 0;
     cudaStream_t cap_stream = nullptr;
+    // side branch of the step: the kinematics run beside the inverse z and y
+    // passes, the scalar kernel beside the forward y pass
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_kin = nullptr, ev_x = nullptr, ev_sc = nullptr;
     cudaGraphExec_t gexec = nullptr;
     int graph_ok = 0;
     std::string err;
@@ -242,14 +247,25 @@ cudaError_t enqueue_step(flusi_t h, cudaStream_t s, cudaEvent_t* ev)
         if (ev) cudaEventRecord(ev[k], s);
         ++k;
     };
+    // Without per-kernel events the two single-block kernels run on the side
+    // stream: the kinematics only have to finish before the x pass, the
+    // scalars (dt, IF-AB2 coefficients, force row) only before the z update.
+    const bool branch = ev == nullptr;
+    cudaStream_t sk = branch ? h->side : s;
     mark();
-    k_kinematics<<<1, 32, 0, s>>>(at<flusi_insect>(h, h->oins), st, at<Frame>(h, h->oframe), box_margin(h));
+    if (branch) {
+        if ((e = cudaEventRecord(h->ev_fork, s))) return e;
+        if ((e = cudaStreamWaitEvent(sk, h->ev_fork, 0))) return e;
+    }
+    k_kinematics<<<1, 32, 0, sk>>>(at<flusi_insect>(h, h->oins), st, at<Frame>(h, h->oframe), box_margin(h));
     if ((e = cudaGetLastError())) return e;
+    if (branch && (e = cudaEventRecord(h->ev_kin, sk))) return e;
     mark();
     if ((e = launch_zinv(fp64, h->ws + h->oU, W, g, h->pz, tz, at<int>(h, h->opz), 6, st, s))) return e;
     mark();
     if ((e = launch_ypass(fp64, true, W, g, h->py, ty, at<int>(h, h->opy), 6, st, s))) return e;
     mark();
+    if (branch && (e = cudaStreamWaitEvent(s, h->ev_kin, 0))) return e;
     XExtra xe{};
     xe.frame = at<Frame>(h, h->oframe);
     xe.shape = make_shape(h);
@@ -257,13 +273,19 @@ cudaError_t enqueue_step(flusi_t h, cudaStream_t s, cudaEvent_t* ev)
     xe.comp0 = 0;
     if ((e = launch_xpass(fp64, XP_PHYS, W, g, h->px, tx, at<int>(h, h->opx), xe, st, s))) return e;
     mark();
+    if (branch) {
+        if ((e = cudaEventRecord(h->ev_x, s))) return e;
+        if ((e = cudaStreamWaitEvent(sk, h->ev_x, 0))) return e;
+    }
     double3 opts = make_double3(h->opt.cfl, h->opt.dt_fixed, h->opt.dt_max);
-    k_scalars<<<1, 256, 0, s>>>(g, at<double>(h, h->opart), h->xgrid, st, at<StepCoef>(h, h->ocoef),
-                                at<double>(h, h->orows), h->opt.force_ring, at<double>(h, h->oetab), opts);
+    k_scalars<<<1, 256, 0, sk>>>(g, at<double>(h, h->opart), h->xgrid, st, at<StepCoef>(h, h->ocoef),
+                                 at<double>(h, h->orows), h->opt.force_ring, at<double>(h, h->oetab), opts);
     if ((e = cudaGetLastError())) return e;
+    if (branch && (e = cudaEventRecord(h->ev_sc, sk))) return e;
     mark();
     if ((e = launch_ypass(fp64, false, W, g, h->py, ty, at<int>(h, h->opy), 3, st, s))) return e;
     mark();
+    if (branch && (e = cudaStreamWaitEvent(s, h->ev_sc, 0))) return e;
     ZfwdExtra ze{};
     ze.coef = at<StepCoef>(h, h->ocoef);
     ze.etab = at<double>(h, h->oetab);
@@ -410,6 +432,9 @@ int flusi_bind(flusi_t h, void* ws, size_t bytes, void* stream)
         CK(cudaMemcpyAsync(h->ws + h->oins, &h->ins, sizeof h->ins, cudaMemcpyHostToDevice, h->stream), "insect");
     CK(cudaStreamSynchronize(h->stream), "bind");
     if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking), "capture stream");
+    if (!h->side) CK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking), "side stream");
+    for (cudaEvent_t* ev : {&h->ev_fork, &h->ev_kin, &h->ev_x, &h->ev_sc})
+        if (!*ev) CK(cudaEventCreateWithFlags(ev, cudaEventDisableTiming), "step events");
     h->bound = 1;
     h->has_state = 0;
     return FLUSI_OK;
@@ -697,6 +722,9 @@ int flusi_destroy(flusi_t h)
     if (!h) return FLUSI_OK;
     drop_graph(h);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->side) cudaStreamDestroy(h->side);
+    for (cudaEvent_t ev : {h->ev_fork, h->ev_kin, h->ev_x, h->ev_sc})
+        if (ev) cudaEventDestroy(ev);
     delete h;
     return FLUSI_OK;
 }
