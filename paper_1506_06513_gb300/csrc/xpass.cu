@@ -737,24 +737,16 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
         }
         __syncthreads();
 
-        // ---- physical space: chi, u_s, NL = u x omega - chi/C_eta (u - u_s), sums
+        // ---- physical space, every point: NL = u x omega into the omega lines,
+        //      energy and max |u|^2; a non-finite value makes a sum non-finite
         {
             const int items = RB * NH;
-            T e_tile = T(0);
+            T e_tile = T(0), chk = T(0);
             for (int it = 0; it < (items + 191) / 192; ++it) {
                 const int i = tid + it * 192;
                 const int rr = i / NH, lrow = i % NH;
-                const bool valid = (i < items) && (row0 + rr < nrows);
-                const int p = lrow / R + R * (lrow % R);
-                const int slot = lrow + lrow / R;
-                const int r = row0 + rr;
-                const int mask = valid ? rowmask[rr] : 0;
-                T chi2[2] = {T(0), T(0)}, us2[2][3] = {{T(0), T(0), T(0)}, {T(0), T(0), T(0)}};
-                int colr[2] = {0, 0};
-                T u[2][3], X[2][3];
-                if (valid) {
-                    const int z = r / g.ny, y = r - z * g.ny;
-                    const T Y = T(y) * dyT, Z = T(z) * dzT;
+                if (i < items && row0 + rr < nrows) {
+                    const int slot = lrow + lrow / R;
                     cplx<T> uv[3], wv[3];
 #pragma unroll
                     for (int q = 0; q < 3; ++q) {
@@ -764,75 +756,105 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
                     T nl[2][3];
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
-                        T om[3];
+                        T u[3], om[3];
 #pragma unroll
                         for (int q = 0; q < 3; ++q) {
-                            u[h][q] = h ? uv[q].y : uv[q].x;
+                            u[q] = h ? uv[q].y : uv[q].x;
                             om[q] = h ? wv[q].y : wv[q].x;
                         }
-                        X[h][0] = T(2 * p + h) * dxT;
-                        X[h][1] = Y;
-                        X[h][2] = Z;
-                        if (mask != 0) {
-                            const bool inrow[3] = {(mask & 1) != 0, (mask & 2) != 0, (mask & 4) != 0};
-                            solid_at(F, X[h], inrow, chi2[h], colr[h], us2[h]);
-                        }
-                        T lamb[3];
-                        cross3(u[h], om, lamb);
-                        const T pen = chi2[h] * F.inv_eta;
-                        T uu = T(0);
-#pragma unroll
-                        for (int q = 0; q < 3; ++q) {
-                            nl[h][q] = lamb[q] - pen * (u[h][q] - us2[h][q]);
-                            uu += u[h][q] * u[h][q];
-                            if (!isfinite(nl[h][q]) || !isfinite(u[h][q])) bad = 1;
-                        }
+                        cross3(u, om, nl[h]);
+                        const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
                         e_tile += uu;
                         m_acc = fmax(m_acc, uu);
+                        chk += nl[h][0] + nl[h][1] + nl[h][2];
                     }
 #pragma unroll
-                    for (int q = 0; q < 3; ++q) buf[(q * RB + rr) * CS + slot] = mkc<T>(nl[0][q], nl[1][q]);
-                }
-                if (__any_sync(0xffffffffu, mask != 0)) {
-                    for (int cc = 0; cc < 3; ++cc) {
-                        const bool has = valid && (colr[0] == cc + 1 || colr[1] == cc + 1);
-                        if (!__any_sync(0xffffffffu, has)) continue;
-                        T acc[12];   // partial over this warp's points, in T
-                        for (int k = 0; k < 12; ++k) acc[k] = T(0);
-                        if (has) {
-                            for (int h = 0; h < 2; ++h) {
-                                if (colr[h] != cc + 1) continue;
-                                const T* ref = cc == 0 ? F.xc : F.pv[cc - 1];
-                                T rv[3] = {X[h][0] - ref[0], X[h][1] - ref[1], X[h][2] - ref[2]};
-                                T pu[3], cu[3], m1[3], m2[3];
-                                for (int q = 0; q < 3; ++q) {
-                                    pu[q] = chi2[h] * (u[h][q] - us2[h][q]);
-                                    cu[q] = chi2[h] * us2[h][q];
-                                }
-                                cross3(rv, pu, m1);
-                                cross3(rv, cu, m2);
-                                for (int q = 0; q < 3; ++q) {
-                                    acc[q] += pu[q];
-                                    acc[3 + q] += m1[q];
-                                    acc[6 + q] += cu[q];
-                                    acc[9 + q] += m2[q];
-                                }
-                            }
-                        }
-                        for (int k = 0; k < 12; ++k) acc[k] = warp_sum_t(acc[k]);
-                        if (lane == 0)
-                            for (int k = 0; k < 12; ++k) wacc[warp * 36 + cc * 12 + k] += double(acc[k]);
-                    }
+                    for (int q = 0; q < 3; ++q)
+                        buf[((3 + q) * RB + rr) * CS + slot] = mkc<T>(nl[0][q], nl[1][q]);
                 }
             }
             e_acc += double(e_tile);
+            if (!isfinite(e_tile) || !isfinite(chk)) bad = 1;
+        }
+
+        // ---- penalization, only in tiles with a row that meets a part's box:
+        //      chi, u_s, NL -= chi/C_eta (u - u_s) and the per-colour sums
+        int tile_any = 0;
+#pragma unroll
+        for (int rr = 0; rr < RB; ++rr) tile_any |= rowmask[rr];
+        if (tile_any) {   // uniform over the block
+            __syncthreads();
+            constexpr int NX = 2 * NH;
+            for (int i0 = 0; i0 < RB * NX; i0 += 192) {
+                const int i = i0 + tid;
+                const int rr = i / NX, xi = i % NX;
+                const int r = row0 + rr;
+                const int mask = (i < RB * NX && r < nrows) ? rowmask[rr] : 0;
+                T chi = T(0), us[3] = {T(0), T(0), T(0)}, X[3] = {T(0), T(0), T(0)};
+                T u[3] = {T(0), T(0), T(0)};
+                int colr = 0;
+                if (mask != 0) {
+                    const int z = r / g.ny, y = r - z * g.ny;
+                    X[0] = T(xi) * dxT;
+                    X[1] = T(y) * dyT;
+                    X[2] = T(z) * dzT;
+                    const bool inrow[3] = {(mask & 1) != 0, (mask & 2) != 0, (mask & 4) != 0};
+                    solid_at(F, X, inrow, chi, colr, us);
+                    if (chi > T(0)) {
+                        // point xi is half h of pair p, held at logical row R (p % R) + p / R
+                        const int pp = xi >> 1, h = xi & 1;
+                        const int lrow = R * (pp % R) + pp / R;
+                        const int slot = lrow + lrow / R;
+                        const T pen = chi * F.inv_eta;
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) {
+                            const T* ul = reinterpret_cast<const T*>(buf + (q * RB + rr) * CS + slot);
+                            T* nl = reinterpret_cast<T*>(buf + ((3 + q) * RB + rr) * CS + slot);
+                            u[q] = ul[h];
+                            nl[h] -= pen * (u[q] - us[q]);
+                        }
+                    }
+                }
+                if (__any_sync(0xffffffffu, colr != 0)) {
+                    for (int cc = 0; cc < 3; ++cc) {
+                        const bool has = colr == cc + 1;
+                        if (!__any_sync(0xffffffffu, has)) continue;
+                        T acc[12];   // partial over this warp's points, in T
+#pragma unroll
+                        for (int k2 = 0; k2 < 12; ++k2) acc[k2] = T(0);
+                        if (has) {
+                            const T* ref = cc == 0 ? F.xc : F.pv[cc - 1];
+                            T rv[3] = {X[0] - ref[0], X[1] - ref[1], X[2] - ref[2]};
+                            T pu[3], cu[3], m1[3], m2[3];
+#pragma unroll
+                            for (int q = 0; q < 3; ++q) {
+                                pu[q] = chi * (u[q] - us[q]);
+                                cu[q] = chi * us[q];
+                            }
+                            cross3(rv, pu, m1);
+                            cross3(rv, cu, m2);
+#pragma unroll
+                            for (int q = 0; q < 3; ++q) {
+                                acc[q] = pu[q];
+                                acc[3 + q] = m1[q];
+                                acc[6 + q] = cu[q];
+                                acc[9 + q] = m2[q];
+                            }
+                        }
+#pragma unroll
+                        for (int k2 = 0; k2 < 12; ++k2) acc[k2] = warp_sum_t(acc[k2]);
+                        if (lane == 0)
+                            for (int k2 = 0; k2 < 12; ++k2) wacc[warp * 36 + cc * 12 + k2] += double(acc[k2]);
+                    }
+                }
+            }
         }
         __syncthreads();
 
         // ---- forward on the three NL lines of each row (one per lane group):
         //      DIT stage 1, stage 0, r2c post-processing and store
         {
-            cplx<T>* line = buf + c * CS;
+            cplx<T>* line = buf + (3 * RB + c) * CS;
             const int fld = c / RB, lrr = c % RB;
 #pragma unroll
             for (int i = 0; i < R; ++i) v[i] = line[R * j + i + j];
