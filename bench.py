@@ -332,13 +332,7 @@ def run_flusi(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"model insect {'x'.join(map(str, cfg['n']))} FP32: ellipsoid body (0.5, 0.12) + 2 flapping "
-                               "plates (c 0.3, R 1, 4dx thick, phi 60deg sin, alpha 45deg cos), "
-                               "Re 300, u_inf (0.25,0,0), C_eta 1e-3, CFL 0.1 adaptive dt",
-                   "grid": list(cfg["n"]), "box": [4.0, 4.0, 4.0], "precision": "fp32",
-                   "initial": "inflow + band-limited divergence-free waves",
-                   "l2": f"inputs larger than L2: {step_bytes / 1e9:.1f} GB moved per step",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "config": workload_config(cfg["n"], world),
         "roofline": roofline,
         "stage_model": {"bytes_per_step": stage, "frac_of_peak": round(stage / (ms_per_step * 1e-3) / 1e9 / hbm, 4),
                         "frac_of_nominal_8TBs": round(stage / (ms_per_step * 1e-3) / 8e12, 4),
@@ -365,6 +359,18 @@ def source_hash():
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
+
+
+def workload_config(n, world):
+    """The `config` object of both arms: the workload as the GPU arm runs it."""
+    step_bytes = sum(kernel_bytes(n, 4).values())
+    return {"workload": f"model insect {'x'.join(map(str, n))} FP32: ellipsoid body (0.5, 0.12) + 2 flapping "
+                        "plates (c 0.3, R 1, 4dx thick, phi 60deg sin, alpha 45deg cos), "
+                        "Re 300, u_inf (0.25,0,0), C_eta 1e-3, CFL 0.1 adaptive dt",
+            "grid": list(n), "box": [4.0, 4.0, 4.0], "precision": "fp32",
+            "initial": "inflow + band-limited divergence-free waves",
+            "l2": f"inputs larger than L2: {step_bytes / 1e9:.1f} GB moved per step",
+            "parallelism": "replicas" if world > 1 else "single GPU"}
 
 
 # ----------------------------------------------------------- reference arm
@@ -397,14 +403,14 @@ def run_reference(args):
     sim.step(args.steps)
     el = time.perf_counter() - t0
     value = pick ** 3 * args.steps / el
-    sample = (f"model insect at {pick}^3 (same box, body, wings, Re, C_eta), FP64 "
-              f"single-threaded C oracle, {args.steps} steps in {el:.1f} s")
+    sample = (f"the same workload at {pick}^3 (same box, body, wings, Re, C_eta, inflow), FP64 "
+              f"single-threaded C oracle, {args.steps} steps in {el:.1f} s; value in grid-point "
+              f"steps/s of that sample")
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "impl": "reference",
-           "config": {"workload": f"model insect {args.grid}^3 (oracle sample at {pick}^3)",
-                      "grid": [pick] * 3, "box": [4.0, 4.0, 4.0], "precision": "fp64"},
+           "config": workload_config((args.grid,) * 3, world),
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                             "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
