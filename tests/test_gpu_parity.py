@@ -259,11 +259,27 @@ def test_force_ring_drain(fl):
     sim.close()
 
 
+def shear_waves_curl(n, L, pts):
+    """Closed-form curl of workloads.shear_waves at integer grid points: component
+    c is a_c f_c(k_c . x + phase_c) with f = (sin, cos, sin), so
+    d_j u_c = a_c f_c'(arg) k_cj."""
+    X = [pts[:, j] * L[j] / n[j] for j in range(3)]
+    grad = np.zeros((3, 3, len(pts)))     # grad[c, j] = d u_c / d x_j
+    deriv = (np.cos, lambda a: -np.sin(a), np.cos)
+    for c, (a, m, ph) in enumerate(workloads.SHEAR_WAVES):
+        k = [2 * math.pi * m[j] / L[j] for j in range(3)]
+        arg = k[0] * X[0] + k[1] * X[1] + k[2] * X[2] + ph
+        for j in range(3):
+            grad[c, j] = a * deriv[c](arg) * k[j]
+    return np.array([grad[2, 1] - grad[1, 2], grad[0, 2] - grad[2, 0], grad[1, 0] - grad[0, 1]])
+
+
 def test_bench_configuration_sampled(fl):
     """The 512^3 FP32 model-insect step in the benchmark's launch
     configuration, checked where the oracle can follow point by point:
     the mask and solid velocity at sampled grid points near the insect, the
-    band-limited initial field at sampled points, and the kinetic energy of
+    band-limited initial field, its vorticity and the nonlinear term
+    u x omega - chi/C_eta (u - u_s) at sampled points, and the kinetic energy of
     the first force row against its closed form."""
     import torch
     cfg, ins = workloads.config_model_insect(512)
@@ -292,6 +308,19 @@ def test_bench_configuration_sampled(fl):
         if chi > 1e-3 and vals[7, i] == col:
             assert np.abs(vals[8:11, i] - us).max() <= 1e-4
     assert (vals[6] > 0.5).sum() > 20
+    # vorticity and nonlinear term at t = 0 against the closed-form curl of the waves
+    om = shear_waves_curl(n, L, pts)
+    assert np.abs(vals[3:6] - om).max() <= 1e-4 * np.abs(om).max()
+    nl = np.cross(exact.T, om.T).T
+    solid_pts = np.zeros(len(pts), bool)
+    for i, (ix, iy, iz) in enumerate(pts):
+        chi, col, us = oracle.solid_at(ins, 0.0, h, (ix * dx, iy * dx, iz * dx))
+        if chi > 0:
+            solid_pts[i] = True
+            nl[:, i] -= chi / cfg["eta"] * (exact[:, i] - np.asarray(us))
+    fluid = ~solid_pts
+    assert np.abs(vals[11:14, fluid] - nl[:, fluid]).max() <= 1e-4 * np.abs(nl[:, fluid]).max()
+    assert np.abs(vals[11:14, solid_pts] - nl[:, solid_pts]).max() <= 1e-4 * np.abs(nl[:, solid_pts]).max()
     sim.step(1)
     rows, _ = sim.forces()
     ek = workloads.shear_waves_energy(L, mean=cfg["u_inf"])
