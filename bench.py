@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true",
+                    help="skip the 40-run uneven ensemble, batched against one by one")
     return ap.parse_args()
 
 
@@ -324,6 +326,11 @@ def run_flusi(args):
                 "kernels_ms": {k: round(v, 3) for k, v in prof64.items()}}
     del u0
 
+    ensemble = None
+    if not args.no_ensemble:
+        from paper_1506_06513_gb300.ensemble import run as run_ensemble
+        ensemble = run_ensemble(40, 200)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = oracle_sample()
@@ -340,6 +347,7 @@ def run_flusi(args):
                         "kernel_bytes_frac_of_peak": round(step_bytes / (ms_per_step * 1e-3) / 1e9 / hbm, 4)},
         "kernels_ms": kernels,
         "fp64": fp64,
+        "ensemble": ensemble,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": kps * args.steps,

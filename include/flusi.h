@@ -214,6 +214,41 @@ int flusi_penalization_sums_noalloc(int nx, int ny, int nz, const double L[3], d
                                     const flusi_insect *insect, double t, const double *u_dev,
                                     double *sums_out, void *cuda_stream);
 
+/* ---- Ensembles of independent runs (uneven grids, kinematics, Reynolds
+ * numbers).  The paper runs one simulation at a time; this batches many small
+ * ones into one CUDA graph per ensemble step so that their kernels fill the
+ * GPU together.
+ *
+ * flusi_ensemble_create: `members` are `count` (1..FLUSI_ENSEMBLE_MAX) bound
+ * handles with a state, each with its own workspace; the array is copied and
+ * the handles stay owned by the caller (they must outlive the ensemble and
+ * must not be destroyed or re-bound while it exists).  `cuda_stream` is the
+ * stream the ensemble's steps are enqueued on (NULL: legacy default stream).
+ * FLUSI_EINVAL for a NULL or repeated member, FLUSI_ESTATE for one that is not
+ * bound or has no state.  Ensemble calls leave their failure message in
+ * flusi_last_error(NULL).
+ *
+ * flusi_ensemble_step: enqueue n steps of every member (Algorithm 1 steps
+ * a-e, each member with its own adaptive dt) and return without waiting.  The
+ * first call captures one graph holding one step of all members, forked from
+ * and joined back into the ensemble stream; later calls launch it n times.
+ * Work already enqueued on a member's bound stream runs before, and work
+ * enqueued there afterwards runs after, so flusi_forces / flusi_get_state on a
+ * member see the ensemble's steps.  A member with a device error stops
+ * stepping (its kernels return at entry) and reports it at its next
+ * synchronizing call; the others are unaffected.  Options and kinematics of
+ * the members are those at the first call; changing a member's options or the
+ * shape of its insect afterwards needs a new ensemble (FLUSI_ESTATE).
+ *
+ * flusi_ensemble_destroy: release the ensemble (not the members).  NULL is a
+ * no-op. */
+#define FLUSI_ENSEMBLE_MAX 1024
+typedef struct flusi_ensemble_s *flusi_ensemble_t;
+int flusi_ensemble_create(const flusi_t *members, int count, void *cuda_stream,
+                          flusi_ensemble_t *out);
+int flusi_ensemble_step(flusi_ensemble_t e, int n);
+int flusi_ensemble_destroy(flusi_ensemble_t e);
+
 /* Release the handle (not the caller's workspace).  NULL is a no-op. */
 int flusi_destroy(flusi_t h);
 

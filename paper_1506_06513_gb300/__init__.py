@@ -78,6 +78,9 @@ def _load():
         "flusi_kernels_per_step": ([h, C.POINTER(C.c_int)], ip),
         "flusi_penalization_sums_noalloc": ([ip, ip, ip, dp, C.c_double, C.POINTER(Insect), C.c_double,
                                              vp, dp, vp], ip),
+        "flusi_ensemble_create": ([C.POINTER(h), ip, vp, C.POINTER(h)], ip),
+        "flusi_ensemble_step": ([h, ip], ip),
+        "flusi_ensemble_destroy": ([h], ip),
         "flusi_destroy": ([h], ip),
         "flusi_last_error": ([h], C.c_char_p),
     }
@@ -208,6 +211,21 @@ def flusi_penalization_sums_noalloc(n, L, eta, insect: Insect | None, t, u_dev: 
     return out
 
 
+def flusi_ensemble_create(handles, stream: int):
+    arr = (C.c_void_p * len(handles))(*[h.value if isinstance(h, C.c_void_p) else h for h in handles])
+    out = C.c_void_p()
+    _check(None, lib.flusi_ensemble_create(arr, len(handles), C.c_void_p(stream), C.byref(out)))
+    return out
+
+
+def flusi_ensemble_step(e, n):
+    return _check(None, lib.flusi_ensemble_step(e, int(n)))
+
+
+def flusi_ensemble_destroy(e):
+    return lib.flusi_ensemble_destroy(e)
+
+
 def flusi_destroy(h):
     return lib.flusi_destroy(h)
 
@@ -334,6 +352,35 @@ class Solver:
         if self.h:
             flusi_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Ensemble:
+    """Independent solvers stepped together: one CUDA graph holds one step of
+    every member (flusi_ensemble_*).  The solvers stay owned by the caller."""
+
+    def __init__(self, solvers, stream=None):
+        import torch
+        self.solvers = list(solvers)
+        dev = self.solvers[0].device
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=dev)
+        self.e = flusi_ensemble_create([s.h for s in self.solvers], self.stream.cuda_stream)
+
+    def step(self, n=1):
+        flusi_ensemble_step(self.e, n)
+
+    def sync(self):
+        self.stream.synchronize()
+
+    def close(self):
+        if self.e:
+            flusi_ensemble_destroy(self.e)
+            self.e = None
 
     def __del__(self):
         try:

@@ -43,6 +43,7 @@ struct flusi_s {
     cudaEvent_t ev_fork = nullptr, ev_kin = nullptr, ev_x = nullptr, ev_sc = nullptr;
     cudaGraphExec_t gexec = nullptr;
     int graph_ok = 0;
+    long long generation = 0;   // bumped whenever captured step graphs go stale
     std::string err;
 };
 
@@ -309,6 +310,7 @@ void drop_graph(flusi_t h)
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     h->gexec = nullptr;
     h->graph_ok = 0;
+    ++h->generation;
 }
 
 int read_status(flusi_t h, StepState* out)
@@ -714,6 +716,149 @@ int flusi_kernels_per_step(flusi_t h, int* count)
 {
     if (!h || !count) return FLUSI_EINVAL;
     *count = kStepKernels;
+    return FLUSI_OK;
+}
+
+// ---------------------------------------------------------------- ensembles
+
+struct flusi_ensemble_s {
+    std::vector<flusi_t> m;
+    std::vector<long long> gen;            // member generations at capture
+    cudaStream_t stream = nullptr;         // the caller's stream
+    cudaStream_t cap = nullptr;            // private capture origin
+    cudaEvent_t fork = nullptr, done = nullptr;
+    std::vector<cudaEvent_t> join, pre;
+    cudaGraphExec_t gexec = nullptr;
+};
+
+namespace {
+
+int ens_fail(int code, const std::string& msg) { return fail(nullptr, code, msg); }
+
+int ens_cuda(cudaError_t e, const char* what)
+{
+    return ens_fail(FLUSI_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CKE(call, what)                                 \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return ens_cuda(e_, what); \
+    } while (0)
+
+void ens_release(flusi_ensemble_t e)
+{
+    if (e->gexec) cudaGraphExecDestroy(e->gexec);
+    if (e->cap) cudaStreamDestroy(e->cap);
+    if (e->fork) cudaEventDestroy(e->fork);
+    if (e->done) cudaEventDestroy(e->done);
+    for (cudaEvent_t ev : e->join)
+        if (ev) cudaEventDestroy(ev);
+    for (cudaEvent_t ev : e->pre)
+        if (ev) cudaEventDestroy(ev);
+    delete e;
+}
+
+// One graph: fork from the capture origin, one step of every member on the
+// member's own capture stream, join back.
+int ens_capture(flusi_ensemble_t e)
+{
+    cudaGraph_t graph = nullptr;
+    CKE(cudaStreamBeginCapture(e->cap, cudaStreamCaptureModeThreadLocal), "ensemble: begin capture");
+    cudaError_t err = cudaEventRecord(e->fork, e->cap);
+    for (size_t i = 0; i < e->m.size() && err == cudaSuccess; ++i) {
+        flusi_t h = e->m[i];
+        err = cudaStreamWaitEvent(h->cap_stream, e->fork, 0);
+        if (err == cudaSuccess) err = enqueue_step(h, h->cap_stream, nullptr);
+        if (err == cudaSuccess) err = cudaEventRecord(e->join[i], h->cap_stream);
+        if (err == cudaSuccess) err = cudaStreamWaitEvent(e->cap, e->join[i], 0);
+    }
+    cudaError_t err2 = cudaStreamEndCapture(e->cap, &graph);
+    if (err != cudaSuccess || err2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return ens_cuda(err != cudaSuccess ? err : err2, "ensemble: capture step");
+    }
+    err = cudaGraphInstantiate(&e->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    CKE(err, "ensemble: instantiate graph");
+    for (size_t i = 0; i < e->m.size(); ++i) e->gen[i] = e->m[i]->generation;
+    return FLUSI_OK;
+}
+
+}  // namespace
+
+int flusi_ensemble_create(const flusi_t* members, int count, void* cuda_stream,
+                          flusi_ensemble_t* out)
+{
+    if (!out) return ens_fail(FLUSI_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!members || count < 1 || count > FLUSI_ENSEMBLE_MAX)
+        return ens_fail(FLUSI_EINVAL, "members must be 1.." + std::to_string(FLUSI_ENSEMBLE_MAX) + " handles");
+    for (int i = 0; i < count; ++i) {
+        if (!members[i]) return ens_fail(FLUSI_EINVAL, "member " + std::to_string(i) + " is NULL");
+        for (int j = 0; j < i; ++j)
+            if (members[j] == members[i])
+                return ens_fail(FLUSI_EINVAL, "member " + std::to_string(i) + " repeats member " + std::to_string(j));
+    }
+    for (int i = 0; i < count; ++i) {
+        flusi_t h = members[i];
+        if (!h->bound) return ens_fail(FLUSI_ESTATE, "member " + std::to_string(i) + " has no workspace (flusi_bind)");
+        if (!h->has_state) return ens_fail(FLUSI_ESTATE, "member " + std::to_string(i) + " has no state (flusi_set_state)");
+    }
+    flusi_ensemble_t e = new (std::nothrow) flusi_ensemble_s;
+    if (!e) return ens_fail(FLUSI_ENOMEM, "out of host memory");
+    e->m.assign(members, members + count);
+    e->gen.assign(count, -1);
+    e->stream = (cudaStream_t)cuda_stream;
+    e->join.assign(count, nullptr);
+    e->pre.assign(count, nullptr);
+    cudaError_t err = cudaStreamCreateWithFlags(&e->cap, cudaStreamNonBlocking);
+    if (err == cudaSuccess) err = cudaEventCreateWithFlags(&e->fork, cudaEventDisableTiming);
+    if (err == cudaSuccess) err = cudaEventCreateWithFlags(&e->done, cudaEventDisableTiming);
+    for (int i = 0; i < count && err == cudaSuccess; ++i) {
+        err = cudaEventCreateWithFlags(&e->join[i], cudaEventDisableTiming);
+        if (err == cudaSuccess) err = cudaEventCreateWithFlags(&e->pre[i], cudaEventDisableTiming);
+    }
+    if (err != cudaSuccess) {
+        ens_release(e);
+        return ens_cuda(err, "ensemble: streams and events");
+    }
+    *out = e;
+    return FLUSI_OK;
+}
+
+int flusi_ensemble_step(flusi_ensemble_t e, int n)
+{
+    if (!e) return ens_fail(FLUSI_EINVAL, "ensemble is NULL");
+    if (n < 0) return ens_fail(FLUSI_EINVAL, "n < 0");
+    for (size_t i = 0; i < e->m.size(); ++i) {
+        flusi_t h = e->m[i];
+        if (!h->bound || !h->has_state)
+            return ens_fail(FLUSI_ESTATE, "member " + std::to_string(i) + " is not bound or has no state");
+        if (e->gexec && e->gen[i] != h->generation)
+            return ens_fail(FLUSI_ESTATE, "member " + std::to_string(i) +
+                                              " changed options, workspace or insect shape; create a new ensemble");
+    }
+    if (n == 0) return FLUSI_OK;
+    if (!e->gexec) {
+        int rc = ens_capture(e);
+        if (rc) return rc;
+    }
+    // order after the members' streams, run, and order the members' streams after
+    for (size_t i = 0; i < e->m.size(); ++i) {
+        CKE(cudaEventRecord(e->pre[i], e->m[i]->stream), "ensemble: order after members");
+        CKE(cudaStreamWaitEvent(e->stream, e->pre[i], 0), "ensemble: order after members");
+    }
+    for (int k = 0; k < n; ++k) CKE(cudaGraphLaunch(e->gexec, e->stream), "ensemble: graph launch");
+    CKE(cudaEventRecord(e->done, e->stream), "ensemble: order members after");
+    for (flusi_t h : e->m) CKE(cudaStreamWaitEvent(h->stream, e->done, 0), "ensemble: order members after");
+    return FLUSI_OK;
+}
+
+int flusi_ensemble_destroy(flusi_ensemble_t e)
+{
+    if (!e) return FLUSI_OK;
+    ens_release(e);
     return FLUSI_OK;
 }
 

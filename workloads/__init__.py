@@ -222,6 +222,32 @@ def config_model_insect(n=512):
     return cfg, ins
 
 
+ENSEMBLE_GRIDS = ((64, 64, 64), (96, 96, 96), (128, 128, 128), (96, 96, 192))
+
+
+def config_ensemble(count=40, seed=1506):
+    """Uneven ensemble of independent single-wing runs.  Per run, drawn in this
+    order from default_rng(seed): a grid index into ENSEMBLE_GRIDS, phi_0 ~
+    U[40, 80] deg, f ~ U[0.8, 1.2], Re ~ U[50, 400] (chord and mean tip speed
+    4 phi_0 f R).  Box 4^3 (4 x 4 x 8 for the 96 x 96 x 192 grid), C_eta =
+    2.5e-3, quiescent start, CFL 0.1 adaptive."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        g = int(rng.integers(0, len(ENSEMBLE_GRIDS)))
+        phi0 = float(rng.uniform(40.0, 80.0)) * DEG
+        f = float(rng.uniform(0.8, 1.2))
+        re = float(rng.uniform(50.0, 400.0))
+        n = ENSEMBLE_GRIDS[g]
+        L = (4.0, 4.0, 8.0) if n[2] == 192 else (4.0, 4.0, 4.0)
+        cfg = {"name": f"ensemble_{i}", "n": n, "L": L,
+               "nu": nu_from_re(re, mean_tip_speed(phi0, f), 0.3), "eta": 2.5e-3, "cfl": 0.1,
+               "mean_mode": "fixed", "init": ("uniform", (0.0, 0.0, 0.0)),
+               "draw": {"grid": g, "phi0_deg": phi0 / DEG, "freq": f, "re": re}}
+        out.append((cfg, single_wing(L, n, phi_m=phi0, freq=f)))
+    return out
+
+
 def initial_field(cfg, dtype=np.float64):
     """The configuration's initial velocity on the grid, [3][nz][ny][nx]."""
     kind = cfg["init"][0]
