@@ -39,6 +39,7 @@ def run(count=40, steps=200, warmup=3, precision="fp32", seed=1506):
     fields = [workloads.initial_field(cfg, np.float32 if precision == "fp32" else np.float64)
               for cfg, _ in members]
     points = [int(np.prod(cfg["n"])) for cfg, _ in members]
+    _zero_states(solvers, fields)
     ens = fl.Ensemble(solvers)
 
     def sync_all():
@@ -47,7 +48,6 @@ def run(count=40, steps=200, warmup=3, precision="fp32", seed=1506):
         ens.sync()
 
     # warm-up: capture every member's own graph and the ensemble graph
-    _zero_states(solvers, fields)
     for s in solvers:
         s.step(warmup)
     ens.step(warmup)
