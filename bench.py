@@ -43,7 +43,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="flusi", choices=["flusi", "reference"])
-    ap.add_argument("--grid", type=int, default=512)
+    ap.add_argument("--workload", default="model_insect", choices=["model_insect", "turbulent_insect"],
+                    help="model insect in uniform inflow plus waves (512^3 by default), or the "
+                         "model insect in seeded isotropic turbulent inflow (1024^3 by default)")
+    ap.add_argument("--grid", type=int, default=None)
     ap.add_argument("--shape", default=None,
                     help="nx,ny,nz: a reduced grid of the same box and insect (profiling)")
     ap.add_argument("--fp64-steps", type=int, default=10)
@@ -113,8 +116,25 @@ def stage_model_bytes(n, s):
     return 24 * Fc + 18 * Fr
 
 
-def bench_field(cfg):
-    """Uniform inflow plus band-limited divergence-free waves (float32)."""
+def workload_setup(args):
+    if args.workload == "turbulent_insect":
+        cfg, ins = workloads.config_turbulent_insect(args.grid or 1024)
+    else:
+        cfg, ins = workloads.config_model_insect(args.grid or 512)
+    if args.shape:
+        shape = tuple(int(v) for v in args.shape.split(","))
+        cfg = dict(cfg, n=shape)
+        ins = workloads.model_insect(cfg["L"], shape)
+    return cfg, ins
+
+
+def bench_field(cfg, device):
+    """The workload's initial velocity in float32: uniform inflow plus
+    band-limited divergence-free waves (host numpy), or the seeded turbulent
+    inflow (built on the device, a torch tensor)."""
+    if cfg["init"][0] == "turbulent":
+        return workloads.turbulent_field(cfg["n"], cfg["L"], mean=cfg["u_inf"], seed=cfg["init"][1],
+                                         device=f"cuda:{device}")
     return workloads.shear_waves(cfg["n"], cfg["L"], mean=cfg["u_inf"]).astype(np.float32)
 
 
@@ -174,19 +194,30 @@ class Clocks:
 
 # --------------------------------------------------------------- CPU oracle
 
-def oracle_sample(n_sample=128, steps=3):
+def oracle_workload(workload, n):
+    """The workload at a reduced grid n^3 for the oracle: (cfg, insect, u0 FP64)."""
+    if workload == "turbulent_insect":
+        cfg, ins = workloads.config_turbulent_insect(n)
+        u0 = workloads.turbulent_field(cfg["n"], cfg["L"], mean=cfg["u_inf"], seed=cfg["init"][1])
+    else:
+        cfg, ins = workloads.config_model_insect(n)
+        u0 = workloads.shear_waves(cfg["n"], cfg["L"], mean=cfg["u_inf"])
+    return cfg, ins, u0
+
+
+def oracle_sample(workload, n_sample=128, steps=3):
     """The oracle (single-threaded C, FP64) on the same workload at a reduced
     grid, as it stands: grid-point steps/s."""
     import oracle
-    cfg, ins = workloads.config_model_insect(n_sample)
+    cfg, ins, u0 = oracle_workload(workload, n_sample)
     sim = oracle.Simulation(cfg, ins)
-    sim.set_state(workloads.shear_waves(cfg["n"], cfg["L"], mean=cfg["u_inf"]))
+    sim.set_state(u0)
     t0 = time.perf_counter()
     sim.step(steps)
     el = time.perf_counter() - t0
     return {"value": n_sample ** 3 * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"model insect at {n_sample}^3 (same box, body, wings, Re, C_eta), {steps} "
-                      f"steps, FP64 single-threaded C, {el:.1f} s"}
+            "sample": f"the same workload at {n_sample}^3 (same box, body, wings, Re, C_eta, inflow), "
+                      f"{steps} steps, FP64 single-threaded C, {el:.1f} s"}
 
 
 # ------------------------------------------------------------------ own arm
@@ -213,14 +244,9 @@ def run_flusi(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
-    n = args.grid
-    cfg, ins = workloads.config_model_insect(n)
-    if args.shape:
-        shape = tuple(int(v) for v in args.shape.split(","))
-        cfg = dict(cfg, n=shape)
-        ins = workloads.model_insect(cfg["L"], shape)
+    cfg, ins = workload_setup(args)
     N = int(np.prod(cfg["n"]))
-    u0 = bench_field(cfg)
+    u0 = bench_field(cfg, local)
     peaks, peak_src = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
 
@@ -279,8 +305,11 @@ def run_flusi(args):
 
     # ---- end to end through the C-ABI with pinned host buffers
     e2e_steps = args.e2e_steps
-    host_in = torch.from_numpy(u0).pin_memory().numpy()
-    host_out = torch.empty(u0.shape, dtype=torch.float32).pin_memory().numpy()
+    if isinstance(u0, np.ndarray):
+        host_in = torch.from_numpy(u0).pin_memory().numpy()
+    else:
+        host_in = u0.cpu().pin_memory().numpy()
+    host_out = torch.empty(tuple(u0.shape), dtype=torch.float32).pin_memory().numpy()
     rows_total = 0
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -294,7 +323,7 @@ def run_flusi(args):
     e2e_s = time.perf_counter() - t0
     assert rows_total == e2e_steps and np.isfinite(host_out[:, ::64, ::64, ::64]).all()
     e2e_s = allmax(e2e_s)
-    state_bytes = u0.nbytes
+    state_bytes = host_in.nbytes
     e2e = {"value": N * e2e_steps * world / e2e_s, "unit": UNIT, "steps": e2e_steps,
            "h2d_bytes_per_step": (state_bytes + e2e_steps * 1536) / e2e_steps,
            "d2h_bytes_per_step": (state_bytes + e2e_steps * 22 * 8) / e2e_steps,
@@ -333,13 +362,13 @@ def run_flusi(args):
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = oracle_sample()
+        cpu = oracle_sample(args.workload)
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": workload_config(cfg["n"], world),
+        "config": workload_config(cfg["n"], world, args.workload),
         "roofline": roofline,
         "stage_model": {"bytes_per_step": stage, "frac_of_peak": round(stage / (ms_per_step * 1e-3) / 1e9 / hbm, 4),
                         "frac_of_nominal_8TBs": round(stage / (ms_per_step * 1e-3) / 8e12, 4),
@@ -369,14 +398,22 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
-def workload_config(n, world):
+def workload_config(n, world, workload="model_insect"):
     """The `config` object of both arms: the workload as the GPU arm runs it."""
     step_bytes = sum(kernel_bytes(n, 4).values())
-    return {"workload": f"model insect {'x'.join(map(str, n))} FP32: ellipsoid body (0.5, 0.12) + 2 flapping "
-                        "plates (c 0.3, R 1, 4dx thick, phi 60deg sin, alpha 45deg cos), "
-                        "Re 300, u_inf (0.25,0,0), C_eta 1e-3, CFL 0.1 adaptive dt",
-            "grid": list(n), "box": [4.0, 4.0, 4.0], "precision": "fp32",
-            "initial": "inflow + band-limited divergence-free waves",
+    insect = ("ellipsoid body (0.5, 0.12) + 2 flapping plates (c 0.3, R 1, 4dx thick, "
+              "phi 60deg sin, alpha 45deg cos)")
+    if workload == "turbulent_insect":
+        what = (f"model insect {'x'.join(map(str, n))} FP32 in turbulent inflow: {insect}, Re 1000, "
+                "u_inf (0.25,0,0), C_eta 5e-4, CFL 0.1 adaptive dt")
+        init = ("inflow + seeded isotropic divergence-free field, E(k) ~ k^-5/3 on 2 <= |k| <= 8, "
+                "u_rms 0.1 (seed 6513)")
+    else:
+        what = (f"model insect {'x'.join(map(str, n))} FP32: {insect}, Re 300, u_inf (0.25,0,0), "
+                "C_eta 1e-3, CFL 0.1 adaptive dt")
+        init = "inflow + band-limited divergence-free waves"
+    return {"workload": what, "grid": list(n), "box": [4.0, 4.0, 4.0], "precision": "fp32",
+            "initial": init,
             "l2": f"inputs larger than L2: {step_bytes / 1e9:.1f} GB moved per step",
             "parallelism": "replicas" if world > 1 else "single GPU"}
 
@@ -394,18 +431,18 @@ def run_reference(args):
     # choose the sample grid from a timed probe step
     pick = 32
     for n in (32, 48, 64, 96, 128):
-        cfg, ins = workloads.config_model_insect(n)
+        cfg, ins, u0 = oracle_workload(args.workload, n)
         sim = oracle.Simulation(cfg, ins)
-        sim.set_state(workloads.shear_waves(cfg["n"], cfg["L"], mean=cfg["u_inf"]))
+        sim.set_state(u0)
         t0 = time.perf_counter()
         sim.step(1)
         per = time.perf_counter() - t0
         if per * (args.steps + args.warmup) > 120.0:
             break
         pick = n
-    cfg, ins = workloads.config_model_insect(pick)
+    cfg, ins, u0 = oracle_workload(args.workload, pick)
     sim = oracle.Simulation(cfg, ins)
-    sim.set_state(workloads.shear_waves(cfg["n"], cfg["L"], mean=cfg["u_inf"]))
+    sim.set_state(u0)
     sim.step(args.warmup)
     t0 = time.perf_counter()
     sim.step(args.steps)
@@ -418,7 +455,7 @@ def run_reference(args):
            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "impl": "reference",
-           "config": workload_config((args.grid,) * 3, world),
+           "config": workload_config(workload_setup(args)[0]["n"], world, args.workload),
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                             "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

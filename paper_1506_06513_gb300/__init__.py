@@ -307,12 +307,29 @@ class Solver:
     def set_state(self, u):
         """u: numpy [3][nz][ny][nx] (float64 or float32) or a torch CUDA tensor
         in the solver's precision."""
+        nx, ny, nz = self.n
         if isinstance(u, np.ndarray):
+            if u.shape != (3, nz, ny, nx):
+                raise ValueError(f"u has shape {u.shape}, expected {(3, nz, ny, nx)}")
+            if u.dtype not in (np.float64, np.float32):
+                u = u.astype(np.float64)
             where = FLUSI_HOST_FP64 if u.dtype == np.float64 else FLUSI_HOST_FP32
             flusi_set_state(self.h, np.ascontiguousarray(u), where)
         else:
+            u = self._device_array(u)
             self.stream.wait_stream(self.torch.cuda.current_stream(self.device))
             flusi_set_state(self.h, u.data_ptr(), FLUSI_DEVICE)
+            self.stream.synchronize()   # u (possibly a converted copy) is read asynchronously
+
+    def _device_array(self, u):
+        """A contiguous CUDA tensor [3][nz][ny][nx] in the handle's precision on
+        the handle's device (the C call reads exactly that many values)."""
+        torch = self.torch
+        nx, ny, nz = self.n
+        if tuple(u.shape) != (3, nz, ny, nx):
+            raise ValueError(f"u has shape {tuple(u.shape)}, expected {(3, nz, ny, nx)}")
+        dt = torch.float64 if self.prec == FLUSI_FP64 else torch.float32
+        return u.to(device=self.device, dtype=dt).contiguous()
 
     def step(self, n=1):
         flusi_step(self.h, n)
@@ -330,6 +347,13 @@ class Solver:
         return out, t, step
 
     def get_state_device(self, out):
+        torch = self.torch
+        nx, ny, nz = self.n
+        dt = torch.float64 if self.prec == FLUSI_FP64 else torch.float32
+        if (tuple(out.shape) != (3, nz, ny, nx) or out.dtype != dt or not out.is_contiguous()
+                or out.device != self.device):
+            raise ValueError("out must be a contiguous [3][nz][ny][nx] tensor in the handle's "
+                             "precision on the handle's device")
         return flusi_get_state(self.h, out.data_ptr(), FLUSI_DEVICE)
 
     def get_spectrum(self):

@@ -222,6 +222,82 @@ def config_model_insect(n=512):
     return cfg, ins
 
 
+def turbulent_modes(L, seed=6513, kmin=2.0, kmax=8.0, urms=0.1):
+    """Modes of a seeded random-phase isotropic divergence-free field.
+
+    For every integer wave vector m in the half space (m_x > 0, or m_x = 0 and
+    m_y > 0, or m_x = m_y = 0 and m_z > 0) with kmin <= |k| <= kmax,
+    k = 2 pi m / L, in the order of the loops below: a complex Gaussian vector
+    from default_rng(seed), its component along k removed, scaled by
+    sqrt(E(|k|) / (4 pi |k|^2)) with E(k) = k^(-5/3).  The field is
+    u(x) = sum 2 Re(a e^{i k.x}); the amplitudes are rescaled so that
+    u_rms = sqrt(<|u|^2>/3) = urms, using <|u|^2> = sum 2 |a|^2.
+    Returns (m int array (M, 3), a complex array (M, 3))."""
+    rng = np.random.default_rng(seed)
+    mmax = [int(math.ceil(kmax * L[j] / (2 * math.pi))) for j in range(3)]
+    ms, amps = [], []
+    for mx in range(0, mmax[0] + 1):
+        for my in range(-mmax[1], mmax[1] + 1):
+            for mz in range(-mmax[2], mmax[2] + 1):
+                if mx == 0 and (my < 0 or (my == 0 and mz <= 0)):
+                    continue
+                k = np.array([2 * math.pi * mx / L[0], 2 * math.pi * my / L[1], 2 * math.pi * mz / L[2]])
+                kk = float(np.sqrt(k @ k))
+                if kk < kmin or kk > kmax:
+                    continue
+                a = rng.standard_normal(3) + 1j * rng.standard_normal(3)
+                a = a - k * (k @ a) / (kk * kk)
+                a = a * math.sqrt(kk ** (-5.0 / 3.0) / (4 * math.pi * kk * kk))
+                ms.append((mx, my, mz))
+                amps.append(a)
+    m = np.array(ms, dtype=np.int64)
+    a = np.array(amps)
+    scale = urms * math.sqrt(3.0) / math.sqrt(float(np.sum(2 * np.abs(a) ** 2)))
+    return m, a * scale
+
+
+def turbulent_field(n, L, mean=(0.0, 0.0, 0.0), seed=6513, kmin=2.0, kmax=8.0, urms=0.1,
+                    device=None, zchunk=32):
+    """turbulent_modes evaluated on the grid plus a uniform mean,
+    [3][nz][ny][nx].  Modes are grouped by (m_y, m_z); each z plane is a
+    (ny x P) by (P x nx) complex product of separable exponentials.  With
+    `device` (a torch CUDA device) the field is built there as a float32 torch
+    tensor; otherwise as a float64 numpy array."""
+    nx, ny, nz = n
+    m, a = turbulent_modes(L, seed, kmin, kmax, urms)
+    pairs = sorted(set((int(r[1]), int(r[2])) for r in m))
+    index = {p: i for i, p in enumerate(pairs)}
+    P = len(pairs)
+    x = np.arange(nx) * L[0] / nx
+    F = np.zeros((3, P, nx), complex)
+    for (mx, my, mz), amp in zip(m, a):
+        e = np.exp(1j * 2 * math.pi * mx / L[0] * x)
+        F[:, index[(int(my), int(mz))], :] += 2 * amp[:, None] * e[None, :]
+    y = np.arange(ny) * L[1] / ny
+    z = np.arange(nz) * L[2] / nz
+    Ey = np.exp(1j * 2 * math.pi * np.outer([p[0] for p in pairs], y) / L[1])     # (P, ny)
+    Ez = np.exp(1j * 2 * math.pi * np.outer([p[1] for p in pairs], z) / L[2])     # (P, nz)
+    if device is None:
+        u = np.empty((3, nz, ny, nx))
+        for z0 in range(0, nz, zchunk):
+            z1 = min(nz, z0 + zchunk)
+            G = Ez[:, z0:z1].T[:, None, :] * Ey.T[None, :, :]                     # (zc, ny, P)
+            for c in range(3):
+                u[c, z0:z1] = (G @ F[c]).real + mean[c]
+        return u
+    import torch
+    u = torch.empty((3, nz, ny, nx), dtype=torch.float32, device=device)
+    Ft = torch.as_tensor(F, dtype=torch.complex64, device=device)
+    Eyt = torch.as_tensor(Ey.T, dtype=torch.complex64, device=device)
+    Ezt = torch.as_tensor(Ez.T, dtype=torch.complex64, device=device)
+    for z0 in range(0, nz, zchunk):
+        z1 = min(nz, z0 + zchunk)
+        G = Ezt[z0:z1, None, :] * Eyt[None, :, :]
+        for c in range(3):
+            u[c, z0:z1] = torch.matmul(G, Ft[c]).real + mean[c]
+    return u
+
+
 ENSEMBLE_GRIDS = ((64, 64, 64), (96, 96, 96), (128, 128, 128), (96, 96, 192))
 
 
@@ -248,6 +324,19 @@ def config_ensemble(count=40, seed=1506):
     return out
 
 
+def config_turbulent_insect(n=1024):
+    """The model insect in turbulent inflow: mean (0.25, 0, 0) plus the
+    isotropic field of turbulent_field (seed 6513, 2 <= |k| <= 8, u_rms 0.1);
+    Re = 1000 on the chord and mean tip speed, C_eta = 5e-4, 4^3 box."""
+    L = (4.0, 4.0, 4.0)
+    U = mean_tip_speed(60 * DEG)
+    cfg = {"name": f"turbulent_insect_{n}", "n": (n, n, n), "L": L,
+           "nu": nu_from_re(1000.0, U, 0.3), "eta": 5e-4, "cfl": 0.1, "mean_mode": "fixed",
+           "u_inf": (0.25, 0.0, 0.0)}
+    cfg["init"] = ("turbulent", 6513)
+    return cfg, model_insect(L, cfg["n"])
+
+
 def initial_field(cfg, dtype=np.float64):
     """The configuration's initial velocity on the grid, [3][nz][ny][nx]."""
     kind = cfg["init"][0]
@@ -261,6 +350,8 @@ def initial_field(cfg, dtype=np.float64):
         return u
     elif kind == "random_smooth":
         u = random_smooth_field(cfg["n"], cfg["init"][1], mean=cfg.get("u_inf", (0, 0, 0)))
+    elif kind == "turbulent":
+        u = turbulent_field(cfg["n"], cfg["L"], mean=cfg.get("u_inf", (0, 0, 0)), seed=cfg["init"][1])
     else:
         raise ValueError(kind)
     return u.astype(dtype, copy=False)
