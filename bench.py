@@ -220,6 +220,33 @@ def oracle_sample(workload, n_sample=128, steps=3):
                       f"{steps} steps, FP64 single-threaded C, {el:.1f} s"}
 
 
+class Ranks:
+    """Replicas, one process per GPU: a barrier and the maximum over ranks of
+    a host number.  No data moves between ranks; `dist` is torch.distributed
+    (NCCL between GPUs, gloo in the CPU tests) or None for one process."""
+
+    def __init__(self, dist, device):
+        self.dist, self.device = dist, device
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def max(self, x):
+        if self.dist is None:
+            return x
+        import torch
+        t = torch.tensor([float(x)], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+
+def whole_job_rate(points, steps, world, ms_max):
+    """Grid-point steps/s of all replicas: every rank runs `steps` steps of a
+    `points`-point grid; the job takes the slowest rank's time."""
+    return points * steps * world / (ms_max * 1e-3)
+
+
 # ------------------------------------------------------------------ own arm
 
 def run_flusi(args):
@@ -232,17 +259,8 @@ def run_flusi(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
-    def allmax(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    ranks = Ranks(dist, torch.device("cuda", local))
+    barrier, allmax = ranks.barrier, ranks.max
 
     cfg, ins = workload_setup(args)
     N = int(np.prod(cfg["n"]))
@@ -277,7 +295,7 @@ def run_flusi(args):
     clk = clocks.stop()
     sim.sync()
     ms_max = allmax(ms)
-    value = N * args.steps * world / (ms_max * 1e-3)
+    value = whole_job_rate(N, args.steps, world, ms_max)
     ms_per_step = ms_max / args.steps
     kps = fl.flusi_kernels_per_step(sim.h)
 
@@ -324,7 +342,7 @@ def run_flusi(args):
     assert rows_total == e2e_steps and np.isfinite(host_out[:, ::64, ::64, ::64]).all()
     e2e_s = allmax(e2e_s)
     state_bytes = host_in.nbytes
-    e2e = {"value": N * e2e_steps * world / e2e_s, "unit": UNIT, "steps": e2e_steps,
+    e2e = {"value": whole_job_rate(N, e2e_steps, world, e2e_s * 1e3), "unit": UNIT, "steps": e2e_steps,
            "h2d_bytes_per_step": (state_bytes + e2e_steps * 1536) / e2e_steps,
            "d2h_bytes_per_step": (state_bytes + e2e_steps * 22 * 8) / e2e_steps,
            "what": "set_state from pinned host FP32, per step set_kinematics (H2D) + step + "
@@ -349,7 +367,7 @@ def run_flusi(args):
         sim64.sync()
         prof64 = sim64.profile(2)
         sim64.close()
-        v64 = N * args.fp64_steps * world / (ms64 * 1e-3)
+        v64 = whole_job_rate(N, args.fp64_steps, world, ms64)
         fp64 = {"value": v64, "unit": UNIT, "ms_per_step": ms64 / args.fp64_steps,
                 "steps": args.fp64_steps, "fp32_speedup": value / v64,
                 "kernels_ms": {k: round(v, 3) for k, v in prof64.items()}}
