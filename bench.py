@@ -100,7 +100,8 @@ def kernel_bytes(n, s):
         "yinv": 6 * A + 6 * B,
         "xpass_phys": 6 * B + 3 * B,
         "yfwd": 3 * B + 3 * A,
-        "zfwd_update": 3 * A + 2 * 3 * S + 2 * 3 * S,
+        "zfwd": 3 * A + 3 * S,
+        "update": 3 * S + 2 * 3 * S + 2 * 3 * S,
         "kinematics": 0,
         "scalars": 0,
     }

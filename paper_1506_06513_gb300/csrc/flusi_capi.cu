@@ -228,8 +228,26 @@ double box_margin(flusi_t h)
 }
 
 const char* kKernelNames[] = {"kinematics", "zinv_curl", "yinv", "xpass_phys", "scalars", "yfwd",
-                              "zfwd_update"};
-constexpr int kStepKernels = 7;
+                              "zfwd", "update"};
+constexpr int kStepKernels = 8;
+
+// The transformed nonlinear term N^ [3][Mz][My][Mxp] lives in W's vorticity
+// fields (3..5), which are free once the x pass has run.
+void* nhat(flusi_t h)
+{
+    const size_t cs = h->prec == FLUSI_FP64 ? 16 : 8;
+    return h->ws + h->oW + (size_t)3 * h->g.nz * h->g.ny * h->g.Mxp * cs;
+}
+
+ZfwdExtra zextra(flusi_t h)
+{
+    ZfwdExtra ze{};
+    ze.coef = at<StepCoef>(h, h->ocoef);
+    ze.etab = at<double>(h, h->oetab);
+    for (int i = 0; i < 3; ++i) ze.u_inf[i] = h->opt.u_inf[i];
+    ze.mean_free = h->opt.mean_mode;
+    return ze;
+}
 
 // Enqueue one step; with `ev` (kStepKernels + 1 events) records an event
 // before each kernel and after the last.
@@ -286,13 +304,10 @@ cudaError_t enqueue_step(flusi_t h, cudaStream_t s, cudaEvent_t* ev)
     mark();
     if ((e = launch_ypass(fp64, false, W, g, h->py, ty, at<int>(h, h->opy), 3, st, s))) return e;
     mark();
+    if ((e = launch_zfwd(fp64, W, nhat(h), g, h->pz, tz, at<int>(h, h->opz), st, s))) return e;
+    mark();
     if (branch && (e = cudaStreamWaitEvent(s, h->ev_sc, 0))) return e;
-    ZfwdExtra ze{};
-    ze.coef = at<StepCoef>(h, h->ocoef);
-    ze.etab = at<double>(h, h->oetab);
-    for (int i = 0; i < 3; ++i) ze.u_inf[i] = h->opt.u_inf[i];
-    ze.mean_free = h->opt.mean_mode;
-    if ((e = launch_zfwd(fp64, 0, W, h->ws + h->oU, h->ws + h->oH, g, h->pz, tz, at<int>(h, h->opz), ze, st, s))) return e;
+    if ((e = launch_zupdate(fp64, 0, nhat(h), h->ws + h->oU, h->ws + h->oH, g, zextra(h), st, s))) return e;
     mark();
     return cudaSuccess;
 }
@@ -505,11 +520,12 @@ int flusi_set_state(flusi_t h, const void* u, int where)
         }
     }
     CK(launch_ypass(fp64, false, W, g, h->py, at<double2>(h, h->oty), at<int>(h, h->opy), 3, nullptr, s), "y forward");
-    ZfwdExtra ze{};
-    for (int i = 0; i < 3; ++i) ze.u_inf[i] = h->opt.u_inf[i];
-    ze.mean_free = h->opt.mean_mode;
-    CK(launch_zfwd(fp64, 1, W, h->ws + h->oU, h->ws + h->oH, g, h->pz, at<double2>(h, h->otz),
-                   at<int>(h, h->opz), ze, nullptr, s), "z forward");
+    CK(launch_zfwd(fp64, W, nhat(h), g, h->pz, at<double2>(h, h->otz), at<int>(h, h->opz), nullptr, s),
+       "z forward");
+    ZfwdExtra ze = zextra(h);
+    ze.coef = nullptr;
+    ze.etab = nullptr;
+    CK(launch_zupdate(fp64, 1, nhat(h), h->ws + h->oU, h->ws + h->oH, g, ze, nullptr, s), "spectral set");
     CK(cudaStreamSynchronize(s), "set_state");
     h->has_state = 1;
     h->poisoned = 0;

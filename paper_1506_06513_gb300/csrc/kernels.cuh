@@ -41,9 +41,12 @@ struct ZfwdExtra {
     double u_inf[3];
     int mean_free;
 };
-cudaError_t launch_zfwd(int fp64, int mode, const void* W, void* U, void* H, const Geom& g,
-                        const FftPlan& plan, const double2* tw, const int* pos, const ZfwdExtra& ex,
-                        const StepState* st, cudaStream_t s);
+// forward z transform of W[0..2] (A form) into Nh [3][Mz][My][Mxp] (kept modes)
+cudaError_t launch_zfwd(int fp64, const void* W, void* Nh, const Geom& g, const FftPlan& plan,
+                        const double2* tw, const int* pos, const StepState* st, cudaStream_t s);
+// 1/N, projection and (mode 0) IF-AB2 update of U, H or (mode 1) U = N, H = 0
+cudaError_t launch_zupdate(int fp64, int mode, const void* Nh, void* U, void* H, const Geom& g,
+                           const ZfwdExtra& ex, const StepState* st, cudaStream_t s);
 
 // x pass (xpass.cu)
 enum XMode { XP_PHYS = 0, XP_R2C = 1, XP_C2R = 2, XP_DUMP = 3 };

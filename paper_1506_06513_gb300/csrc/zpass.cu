@@ -10,8 +10,10 @@
 //   omega_hat = i k x u_hat on the fly (Sec. 2.4: grad -> i k), fills the
 //   dropped z-modes with zeros and transforms back to z grid points:
 //   W[f] = iFFT_z(field f), f < 3 velocity, f = 3..5 vorticity.
-// zfwd (Algorithm 1 steps d, e): transforms W[0..2] (the nonlinear term
-//   after its x and y transforms) along z keeping only the 2/3-rule modes,
+// zfwd (Algorithm 1 step c, second half): transforms W[0..2] (the nonlinear
+//   term after its x and y transforms) along z and keeps only the 2/3-rule
+//   modes, in the state layout, in the free vorticity part of W.
+// zupdate (Algorithm 1 steps d, e), a streaming pass over the kept modes:
 //   scales by 1/N, applies the Leray projection N <- N - k (k.N)/|k|^2
 //   (Eq. PNST_UP_pressure_poisson_eqn in Fourier space) and
 //   mode 0: the integrating-factor AB2 update
@@ -20,6 +22,8 @@
 //     separable factors E1 = e^{-nu |k|^2 dt}, E2 = e^{-nu |k|^2 (dt + dt_prev)};
 //   mode 1: u_hat = N (initial condition), history cleared.
 //   The k = 0 mode is held at u_inf (N(0) = 0) unless the mean is free.
+#include <algorithm>
+
 #include "fft.cuh"
 #include "kernels.cuh"
 
@@ -28,10 +32,9 @@ namespace flusi {
 namespace {
 
 constexpr int kThreadsInv = 256;
-constexpr int kThreadsFwd = 384;
-// complex elements per tile: 64 KiB (inverse) and 96 KiB (forward, 3 components)
+// complex elements per column tile (64 KiB)
 template <typename T> constexpr int cap_zi() { return sizeof(T) == 4 ? 8192 : 4096; }
-template <typename T> constexpr int cap_zf() { return sizeof(T) == 4 ? 12288 : 6144; }
+inline size_t ceil_div_sz(size_t a, size_t b) { return (a + b - 1) / b; }
 
 template <typename T>
 __global__ void __launch_bounds__(kThreadsInv)
@@ -115,36 +118,38 @@ k_zinv(const cplx<T>* __restrict__ U, cplx<T>* __restrict__ W, Geom g, FftPlan p
     }
 }
 
-template <typename T, int MODE>
-__global__ void __launch_bounds__(kThreadsFwd, 2)
-k_zfwd(const cplx<T>* __restrict__ W, cplx<T>* __restrict__ U, cplx<T>* __restrict__ H, Geom g,
-       FftPlan plan, const double2* __restrict__ tw, const int* __restrict__ pos, int lgTX,
-       ZfwdExtra ex, const StepState* __restrict__ st)
+// Forward z transform of one component of a column tile: TX consecutive
+// columns q of W[c] (A form, all nz rows) in by 16-byte asynchronous copies,
+// the kept modes jz (2/3 rule) out to Nh[c] in the state layout [Mz][My][Mxp].
+template <typename T>
+__global__ void __launch_bounds__(kThreadsInv)
+k_zfwd(const cplx<T>* __restrict__ W, cplx<T>* __restrict__ Nh, Geom g, FftPlan plan,
+       const double2* __restrict__ tw, const int* __restrict__ pos, int lgTX,
+       const StepState* __restrict__ st)
 {
     if (st && st->status != 0) return;
-    if (MODE == 0 && ex.coef->skip) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int TX = 1 << lgTX, C = 3 * TX;
+    const int TX = 1 << lgTX;
     cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
-    cplx<T>* tws = buf + g.nz * C;
-    int* spos = reinterpret_cast<int*>(tws + g.nz);
-    const int Q = g.My * g.Mxp;
-    const int q0 = blockIdx.x * TX;
+    cplx<T>* tws = buf + (g.nz << lgTX);
+    int* sinv = reinterpret_cast<int*>(tws + g.nz);
+    const int Q = g.My * g.Mxp, nz = g.nz, Kz = g.Kz, Mz = g.Mz;
+    const int nqb = ceil_div(Q, TX);
+    const int c = blockIdx.x / nqb, q0 = (blockIdx.x - c * nqb) * TX;
     const size_t Wplane = (size_t)g.ny * g.Mxp;
-    const size_t Ustride = (size_t)g.Mz * Q;
-    const int nz = g.nz;
-    load_tables<T>(tws, spos, tw, pos, nz, nz);
-    __syncthreads();
+    load_tables<T>(tws, nullptr, tw, nullptr, nz, 0);
+    load_inverse_pos(sinv, pos, nz);
     {
         constexpr int VEC = 16 / sizeof(cplx<T>);
-        const int lpr = C / VEC;               // lanes per row of the tile
-        const int rstep = kThreadsFwd / lpr;
-        const int col = (threadIdx.x % lpr) * VEC;
-        const int c = col >> lgTX, q = q0 + (col & (TX - 1));
+        const int lpr = TX / VEC;              // lanes per row of the tile
+        const int rstep = kThreadsInv / lpr;
+        const int txv = (threadIdx.x % lpr) * VEC;
+        const int qv = q0 + txv;               // Q is a multiple of VEC
+        const cplx<T>* src = W + (size_t)c * nz * Wplane + qv;
         for (int z = threadIdx.x / lpr; z < nz; z += rstep) {
-            cplx<T>* dst = buf + z * C + col;
-            if (q < Q) {
-                cp_async_16(dst, W + ((size_t)c * nz + z) * Wplane + q);
+            cplx<T>* dst = buf + (z << lgTX) + txv;
+            if (qv < Q) {
+                cp_async_16(dst, src + (size_t)z * Wplane);
             } else {
 #pragma unroll
                 for (int v = 0; v < VEC; ++v) dst[v] = mkc<T>(0, 0);
@@ -153,8 +158,33 @@ k_zfwd(const cplx<T>* __restrict__ W, cplx<T>* __restrict__ U, cplx<T>* __restri
     }
     cp_async_wait_all();
     __syncthreads();
-    fft_dif<T, false>(buf, C, C, plan, tws);
+    const int q = q0 + (threadIdx.x & (TX - 1));
+    const bool qok = q < Q;
+    cplx<T>* out = Nh + (size_t)c * Mz * Q + (qok ? q : 0);
+    auto store = [&](int f, cplx<T> v) {   // keep modes |m| <= Kz only
+        const int jz = f <= Kz ? f : (f >= nz - Kz ? f - nz + Mz : -1);
+        if (qok && jz >= 0) out[(size_t)jz * Q] = v;
+    };
+    fft_dif_out<T, false>(buf, TX, TX, plan, tws, sinv, store);
+}
 
+// Pointwise spectral update over the kept modes, VEC adjacent columns per
+// thread: N = Nh / N_points, Leray projection N <- N - k (k.N)/|k|^2, then
+//   mode 0: IF-AB2  u^{n+1} = E1 (u^n + c_now N) - c_old E2 N^{n-1},  N^{n-1} <- N
+//   mode 1: u_hat = N (the initial condition), history cleared.
+// The mean (k = 0) is held at u_inf unless it is free.  Row padding x >= Mx
+// is never written (it is zero from the workspace reset on).
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256)
+k_zupdate(const cplx<T>* __restrict__ Nh, cplx<T>* __restrict__ U, cplx<T>* __restrict__ H, Geom g,
+          ZfwdExtra ex, const StepState* __restrict__ st)
+{
+    if (st && st->status != 0) return;
+    if (MODE == 0 && ex.coef->skip) return;
+    constexpr int VEC = 16 / sizeof(cplx<T>);
+    const int Q = g.My * g.Mxp;
+    const size_t S = (size_t)g.Mz * Q;     // values per component
+    const size_t groups = S / VEC;         // Mxp is a multiple of 4
     const T two_pi = T(6.283185307179586476925286766559);
     const T inv_n = T(1.0 / ((double)g.nx * g.ny * g.nz));
     double c_now = 0, c_old = 0;
@@ -171,57 +201,42 @@ k_zfwd(const cplx<T>* __restrict__ W, cplx<T>* __restrict__ U, cplx<T>* __restri
     const double* E2x = E1z + g.Mz;
     const double* E2y = E2x + g.Mx;
     const double* E2z = E2y + g.My;
-
-    // two modes per batch: the twelve global loads of U and H are issued before
-    // any of the arithmetic that needs them
-    constexpr int kB = 2;
-    const int total = g.Mz << lgTX;
-    for (int e0 = threadIdx.x; e0 < total; e0 += kB * kThreadsFwd) {
-        cplx<T> uo[kB][3], ho[kB][3];
-        int jzs[kB], qs[kB];
+    for (size_t gi = (size_t)blockIdx.x * blockDim.x + threadIdx.x; gi < groups;
+         gi += (size_t)gridDim.x * blockDim.x) {
+        const size_t o = gi * VEC;
+        const int jz = (int)(o / Q), q = (int)(o - (size_t)jz * Q);
+        const int jy = q / g.Mxp, x0 = q - jy * g.Mxp;
+        if (x0 >= g.Mx) continue;
+        cplx<T> n[3][VEC], u[3][VEC], h[3][VEC];
 #pragma unroll
-        for (int bb = 0; bb < kB; ++bb) {
-            const int e = e0 + bb * kThreadsFwd;
-            const int jz = e >> lgTX, q = q0 + (e & (TX - 1));
-            jzs[bb] = jz;
-            qs[bb] = (e < total && q < Q) ? q : -1;
-            const size_t o = (size_t)jz * Q + q;
+        for (int c = 0; c < 3; ++c) {
+            const size_t oc = c * S + o;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                uo[bb][c] = mkc<T>(0, 0);
-                ho[bb][c] = mkc<T>(0, 0);
-                if (qs[bb] >= 0) {
-                    if (MODE == 0) uo[bb][c] = U[c * Ustride + o];
-                    if (MODE == 0 && !first) ho[bb][c] = H[c * Ustride + o];
-                }
+            for (int v = 0; v < VEC; ++v) {
+                n[c][v] = Nh[oc + v];
+                u[c][v] = mkc<T>(0, 0);
+                h[c][v] = mkc<T>(0, 0);
+                if (MODE == 0) u[c][v] = U[oc + v];
+                if (MODE == 0 && !first) h[c][v] = H[oc + v];
             }
         }
+        const T ky = two_pi * T(mode_of(jy, g.Ky)) / T(g.Ly);
+        const T kz = two_pi * T(mode_of(jz, g.Kz)) / T(g.Lz);
 #pragma unroll
-        for (int bb = 0; bb < kB; ++bb) {
-            if (qs[bb] < 0) continue;
-            const int jz = jzs[bb], q = qs[bb], tx = q - q0;
-            const int jy = q / g.Mxp, x = q - jy * g.Mxp;
-            const size_t o = (size_t)jz * Q + q;
-            if (x >= g.Mx) {   // row padding stays zero
-                for (int c = 0; c < 3; ++c) {
-                    U[c * Ustride + o] = mkc<T>(0, 0);
-                    H[c * Ustride + o] = mkc<T>(0, 0);
-                }
-                continue;
-            }
-            const int s = spos[slot_of(jz, g.Kz, nz)];
+        for (int v = 0; v < VEC; ++v) {
+            const int x = x0 + v;
+            if (x >= g.Mx) break;
             cplx<T> N[3];
-            for (int c = 0; c < 3; ++c) N[c] = cscale(buf[s * C + c * TX + tx], inv_n);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) N[c] = cscale(n[c][v], inv_n);
             const T kx = two_pi * T(x) / T(g.Lx);
-            const T ky = two_pi * T(mode_of(jy, g.Ky)) / T(g.Ly);
-            const T kz = two_pi * T(mode_of(jz, g.Kz)) / T(g.Lz);
-            const T k2 = kx * kx + ky * ky + kz * kz;
             const bool zero_mode = (x == 0 && jy == 0 && jz == 0);
             if (!zero_mode) {
-                const T inv_k2 = T(1) / k2;
+                const T inv_k2 = T(1) / (kx * kx + ky * ky + kz * kz);
                 const T kNr = (kx * N[0].x + ky * N[1].x + kz * N[2].x) * inv_k2;
                 const T kNi = (kx * N[0].y + ky * N[1].y + kz * N[2].y) * inv_k2;
                 const T kk[3] = {kx, ky, kz};
+#pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     N[c].x -= kk[c] * kNr;
                     N[c].y -= kk[c] * kNi;
@@ -229,24 +244,26 @@ k_zfwd(const cplx<T>* __restrict__ W, cplx<T>* __restrict__ U, cplx<T>* __restri
             } else if (!ex.mean_free) {
                 N[0] = N[1] = N[2] = mkc<T>(0, 0);
             }
+            const size_t ov = o + v;
             if (MODE == 0) {
                 // products of the per-axis factors in the state precision
                 const T e1 = T(E1x[x]) * T(E1y[jy]) * T(E1z[jz]);
                 const T e2 = first ? T(0) : T(E2x[x]) * T(E2y[jy]) * T(E2z[jz]);
+#pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    const cplx<T> u = uo[bb][c], h = ho[bb][c];
                     cplx<T> r;
-                    r.x = e1 * (u.x + cn * N[c].x) - co * e2 * h.x;
-                    r.y = e1 * (u.y + cn * N[c].y) - co * e2 * h.y;
-                    U[c * Ustride + o] = r;
-                    H[c * Ustride + o] = N[c];
+                    r.x = e1 * (u[c][v].x + cn * N[c].x) - co * e2 * h[c][v].x;
+                    r.y = e1 * (u[c][v].y + cn * N[c].y) - co * e2 * h[c][v].y;
+                    U[c * S + ov] = r;
+                    H[c * S + ov] = N[c];
                 }
             } else {
+#pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    cplx<T> u = N[c];
-                    if (zero_mode && !ex.mean_free) u = mkc<T>(T(ex.u_inf[c]), 0);
-                    U[c * Ustride + o] = u;
-                    H[c * Ustride + o] = mkc<T>(0, 0);
+                    cplx<T> r = N[c];
+                    if (zero_mode && !ex.mean_free) r = mkc<T>(T(ex.u_inf[c]), 0);
+                    U[c * S + ov] = r;
+                    H[c * S + ov] = mkc<T>(0, 0);
                 }
             }
         }
@@ -258,14 +275,6 @@ template <typename T> int zinv_tx(const Geom& g)
     int TX = sizeof(T) == 4 ? 16 : 8;
     while (TX > 1 && g.nz * TX > cap_zi<T>()) TX >>= 1;
     while (2 * TX * g.nz <= cap_zi<T>() && 2 * TX <= 64) TX *= 2;
-    return TX;
-}
-
-template <typename T> int zfwd_tx(const Geom& g)
-{
-    int TX = sizeof(T) == 4 ? 8 : 4;
-    while (TX > 1 && g.nz * 3 * TX > cap_zf<T>()) TX >>= 1;
-    while (2 * TX * 3 * g.nz <= cap_zf<T>() && 2 * TX <= 32) TX *= 2;
     return TX;
 }
 
@@ -283,20 +292,29 @@ cudaError_t launch_zi(const void* U, void* W, const Geom& g, const FftPlan& plan
 }
 
 template <typename T>
-cudaError_t launch_zf(int mode, const void* W, void* U, void* H, const Geom& g, const FftPlan& plan,
-                      const double2* tw, const int* pos, const ZfwdExtra& ex, const StepState* st,
-                      cudaStream_t s)
+cudaError_t launch_zf(const void* W, void* Nh, const Geom& g, const FftPlan& plan, const double2* tw,
+                      const int* pos, const StepState* st, cudaStream_t s)
 {
-    const int TX = zfwd_tx<T>(g);
-    if (g.nz * 3 * TX > cap_zf<T>() || kThreadsFwd % (3 * TX) != 0) return cudaErrorInvalidValue;
-    const int blocks = ceil_div(g.My * g.Mxp, TX);
-    const size_t smem = sizeof(cplx<T>) * ((size_t)g.nz + (size_t)g.nz * 3 * TX) + sizeof(int) * g.nz;
+    const int TX = zinv_tx<T>(g);
+    if (g.nz * TX > cap_zi<T>() || kThreadsInv % TX != 0) return cudaErrorInvalidValue;
+    const int blocks = 3 * ceil_div(g.My * g.Mxp, TX);
+    const size_t smem = sizeof(cplx<T>) * ((size_t)g.nz + (size_t)g.nz * TX) + sizeof(int) * g.nz;
+    k_zfwd<T><<<blocks, kThreadsInv, smem, s>>>((const cplx<T>*)W, (cplx<T>*)Nh, g, plan, tw, pos,
+                                                __builtin_ctz(TX), st);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_zu(int mode, const void* Nh, void* U, void* H, const Geom& g, const ZfwdExtra& ex,
+                      const StepState* st, cudaStream_t s)
+{
+    constexpr int VEC = 16 / sizeof(cplx<T>);
+    const size_t groups = (size_t)g.Mz * g.My * g.Mxp / VEC;
+    const int blocks = (int)std::min<size_t>(ceil_div_sz(groups, 256), (size_t)152 * 64);
     if (mode == 0)
-        k_zfwd<T, 0><<<blocks, kThreadsFwd, smem, s>>>((const cplx<T>*)W, (cplx<T>*)U, (cplx<T>*)H, g,
-                                                       plan, tw, pos, __builtin_ctz(TX), ex, st);
+        k_zupdate<T, 0><<<blocks, 256, 0, s>>>((const cplx<T>*)Nh, (cplx<T>*)U, (cplx<T>*)H, g, ex, st);
     else
-        k_zfwd<T, 1><<<blocks, kThreadsFwd, smem, s>>>((const cplx<T>*)W, (cplx<T>*)U, (cplx<T>*)H, g,
-                                                       plan, tw, pos, __builtin_ctz(TX), ex, st);
+        k_zupdate<T, 1><<<blocks, 256, 0, s>>>((const cplx<T>*)Nh, (cplx<T>*)U, (cplx<T>*)H, g, ex, st);
     return cudaGetLastError();
 }
 
@@ -310,12 +328,18 @@ cudaError_t launch_zinv(int fp64, const void* U, void* W, const Geom& g, const F
                 : launch_zi<float>(U, W, g, plan, tw, pos, nf, st, s);
 }
 
-cudaError_t launch_zfwd(int fp64, int mode, const void* W, void* U, void* H, const Geom& g,
-                        const FftPlan& plan, const double2* tw, const int* pos, const ZfwdExtra& ex,
-                        const StepState* st, cudaStream_t s)
+cudaError_t launch_zfwd(int fp64, const void* W, void* Nh, const Geom& g, const FftPlan& plan,
+                        const double2* tw, const int* pos, const StepState* st, cudaStream_t s)
 {
-    return fp64 ? launch_zf<double>(mode, W, U, H, g, plan, tw, pos, ex, st, s)
-                : launch_zf<float>(mode, W, U, H, g, plan, tw, pos, ex, st, s);
+    return fp64 ? launch_zf<double>(W, Nh, g, plan, tw, pos, st, s)
+                : launch_zf<float>(W, Nh, g, plan, tw, pos, st, s);
+}
+
+cudaError_t launch_zupdate(int fp64, int mode, const void* Nh, void* U, void* H, const Geom& g,
+                           const ZfwdExtra& ex, const StepState* st, cudaStream_t s)
+{
+    return fp64 ? launch_zu<double>(mode, Nh, U, H, g, ex, st, s)
+                : launch_zu<float>(mode, Nh, U, H, g, ex, st, s);
 }
 
 cudaError_t configure_zpass()
@@ -326,10 +350,8 @@ cudaError_t configure_zpass()
     if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
     FLUSI_SMEM(k_zinv<float>)
     FLUSI_SMEM(k_zinv<double>)
-    FLUSI_SMEM((k_zfwd<float, 0>))
-    FLUSI_SMEM((k_zfwd<float, 1>))
-    FLUSI_SMEM((k_zfwd<double, 0>))
-    FLUSI_SMEM((k_zfwd<double, 1>))
+    FLUSI_SMEM(k_zfwd<float>)
+    FLUSI_SMEM(k_zfwd<double>)
 #undef FLUSI_SMEM
     return cudaSuccess;
 }

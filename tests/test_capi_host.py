@@ -120,5 +120,5 @@ def test_struct_layouts_match_header(fl):
 
 def test_kernels_per_step(fl):
     h = fl.flusi_create((16, 16, 16), (1.0, 1.0, 1.0), 0.1, 1e-2, fl.FLUSI_FP64)
-    assert fl.flusi_kernels_per_step(h) == 7
+    assert fl.flusi_kernels_per_step(h) == 8
     fl.flusi_destroy(h)
