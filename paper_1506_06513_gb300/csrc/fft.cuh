@@ -147,46 +147,100 @@ __device__ __forceinline__ void twiddle_table(cplx<T>* v, const cplx<T>* tw, int
     }
 }
 
-template <typename T, int R, bool INV, bool DIF>
+// V adjacent complex values of one tile row (16-byte accesses for V = 2 in FP32).
+template <typename T, int V>
+__device__ __forceinline__ void ld_row(const cplx<T>* p, cplx<T>* o)
+{
+    if constexpr (V == 2 && sizeof(T) == 4) {
+        const float4 q = *reinterpret_cast<const float4*>(p);
+        o[0] = mkc<T>(q.x, q.y);
+        o[1] = mkc<T>(q.z, q.w);
+    } else {
+#pragma unroll
+        for (int c = 0; c < V; ++c) o[c] = p[c];
+    }
+}
+
+template <typename T, int V>
+__device__ __forceinline__ void st_row(cplx<T>* p, const cplx<T>* o)
+{
+    if constexpr (V == 2 && sizeof(T) == 4) {
+        *reinterpret_cast<float4*>(p) = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
+    } else {
+#pragma unroll
+        for (int c = 0; c < V; ++c) p[c] = o[c];
+    }
+}
+
+// One stage on V adjacent columns per thread (they share the butterfly's
+// addresses and twiddles).  Butterfly j of the stage: rows b*ls + k + t*m.
+template <typename T, int R, bool INV, bool DIF, int V>
 __device__ __forceinline__ void fft_stage(cplx<T>* buf, int ld, int col, int jt, int P, int nbf,
                                           int m, int msh, int ls, int tstep, const cplx<T>* tw)
 {
-#pragma unroll 2
+    constexpr int kUnroll = V == 1 ? 2 : 1;
+#pragma unroll kUnroll
     for (int j = jt; j < nbf; j += P) {
         const int b = msh >= 0 ? (j >> msh) : (j / m);
         const int k = j - b * m;
         cplx<T>* p = buf + (b * ls + k) * ld + col;
         const int step = m * ld;
-        cplx<T> v[R];
+        cplx<T> v[V][R];
 #pragma unroll
-        for (int t = 0; t < R; ++t) v[t] = p[t * step];
-        if (DIF) Dft<T, R, INV>::run(v);
-        if (k != 0) twiddle_table<T, R, INV>(v, tw, k * tstep);
-        if (!DIF) Dft<T, R, INV>::run(v);
+        for (int t = 0; t < R; ++t) {
+            cplx<T> r[V];
+            ld_row<T, V>(p + t * step, r);
 #pragma unroll
-        for (int t = 0; t < R; ++t) p[t * step] = v[t];
+            for (int c = 0; c < V; ++c) v[c][t] = r[c];
+        }
+        if (DIF) {
+#pragma unroll
+            for (int c = 0; c < V; ++c) Dft<T, R, INV>::run(v[c]);
+        }
+        if (k != 0) {
+#pragma unroll
+            for (int t = 1; t < R; ++t) {
+                cplx<T> w = tw[k * tstep * t];
+                if (INV) w.y = -w.y;
+#pragma unroll
+                for (int c = 0; c < V; ++c) v[c][t] = cmul(v[c][t], w);
+            }
+        }
+        if (!DIF) {
+#pragma unroll
+            for (int c = 0; c < V; ++c) Dft<T, R, INV>::run(v[c]);
+        }
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            cplx<T> r[V];
+#pragma unroll
+            for (int c = 0; c < V; ++c) r[c] = v[c][t];
+            st_row<T, V>(p + t * step, r);
+        }
     }
     __syncthreads();
 }
 
-// Stages s in [s0, s1): ascending for DIF, descending for DIT.
-template <typename T, bool INV, bool DIF>
+// Stages s in [s0, s1): ascending for DIF, descending for DIT.  Thread map:
+// column group (threadIdx.x % (C/V)) * V, butterflies jt, jt + P, ...
+template <typename T, bool INV, bool DIF, int V = 1>
 __device__ __forceinline__ void fft_run(cplx<T>* buf, int C, int ld, const FftPlan& plan,
                                         const cplx<T>* tw, int s0, int s1)
 {
-    const int P = blockDim.x / C;
-    const int col = threadIdx.x % C;
-    const int jt = threadIdx.x / C;
+    const int G = C / V;
+    const int P = blockDim.x / G;
+    const int col = (threadIdx.x % G) * V;
+    const int jt = threadIdx.x / G;
     for (int i = s0; i < s1; ++i) {
         const int s = DIF ? i : s0 + s1 - 1 - i;
         const int R = plan.radix[s];
         const int nbf = plan.n / R;
         const int m = plan.m[s], msh = plan.mshift[s], ls = plan.ls[s], ts = plan.tstep[s];
         switch (R) {
-        case 8: fft_stage<T, 8, INV, DIF>(buf, ld, col, jt, P, nbf, m, msh, ls, ts, tw); break;
-        case 4: fft_stage<T, 4, INV, DIF>(buf, ld, col, jt, P, nbf, m, msh, ls, ts, tw); break;
-        case 3: fft_stage<T, 3, INV, DIF>(buf, ld, col, jt, P, nbf, m, msh, ls, ts, tw); break;
-        default: fft_stage<T, 2, INV, DIF>(buf, ld, col, jt, P, nbf, m, msh, ls, ts, tw); break;
+        case 8: fft_stage<T, 8, INV, DIF, V>(buf, ld, col, jt, P, nbf, m, msh, ls, ts, tw); break;
+        case 4: fft_stage<T, 4, INV, DIF, V>(buf, ld, col, jt, P, nbf, m, msh, ls, ts, tw); break;
+        case 3: fft_stage<T, 3, INV, DIF, V>(buf, ld, col, jt, P, nbf, m, msh, ls, ts, tw); break;
+        default: fft_stage<T, 2, INV, DIF, V>(buf, ld, col, jt, P, nbf, m, msh, ls, ts, tw); break;
         }
     }
 }
@@ -211,95 +265,132 @@ __device__ void fft_dit(cplx<T>* buf, int C, int ld, const FftPlan& plan, const 
 // ---------------------------------------------------------------------------
 // Column transforms with their first stage fed from registers loaded by a
 // functor and (optionally) their last stage handing results to a functor, so
-// the tile goes through shared memory only between stages.
-//   load(row) -> cplx<T>   input row `row` (natural order) of this thread's column
-//   store(f, v)            output frequency f of this thread's column
-// The thread-to-column map is fft_run's: column threadIdx.x % C.
+// the tile goes through shared memory only between stages.  V adjacent
+// columns per thread (the map of fft_run):
+//   load(row, out[V])   input row `row` (natural order) of this thread's columns
+//   store(f, in[V])     output frequency f of this thread's columns
 
 // DIF stage 0: butterfly j takes rows j + m t (m = n / R) and, after the
 // twiddles w^{j t}, leaves them where fft_stage would.
-template <typename T, int R, bool INV, class Load>
+template <typename T, int R, bool INV, int V, class Load>
 __device__ __forceinline__ void fft_stage_first(cplx<T>* buf, int ld, int col, int jt, int P, int m,
                                                 int tstep, const cplx<T>* tw, Load& load)
 {
-#pragma unroll 2
+    constexpr int kUnroll = V == 1 ? 2 : 1;
+#pragma unroll kUnroll
     for (int j = jt; j < m; j += P) {
-        cplx<T> v[R];
+        cplx<T> v[V][R];
 #pragma unroll
-        for (int t = 0; t < R; ++t) v[t] = load(j + t * m);
-        Dft<T, R, INV>::run(v);
-        if (j != 0) twiddle_table<T, R, INV>(v, tw, j * tstep);
+        for (int t = 0; t < R; ++t) {
+            cplx<T> r[V];
+            load(j + t * m, r);
+#pragma unroll
+            for (int c = 0; c < V; ++c) v[c][t] = r[c];
+        }
+#pragma unroll
+        for (int c = 0; c < V; ++c) Dft<T, R, INV>::run(v[c]);
+        if (j != 0) {
+#pragma unroll
+            for (int t = 1; t < R; ++t) {
+                cplx<T> w = tw[j * tstep * t];
+                if (INV) w.y = -w.y;
+#pragma unroll
+                for (int c = 0; c < V; ++c) v[c][t] = cmul(v[c][t], w);
+            }
+        }
         cplx<T>* p = buf + j * ld + col;
 #pragma unroll
-        for (int t = 0; t < R; ++t) p[t * m * ld] = v[t];
+        for (int t = 0; t < R; ++t) {
+            cplx<T> r[V];
+#pragma unroll
+            for (int c = 0; c < V; ++c) r[c] = v[c][t];
+            st_row<T, V>(p + t * m * ld, r);
+        }
     }
     __syncthreads();
 }
 
 // DIF last stage (span 1, no twiddles): butterfly j holds rows j R + t, which
 // are frequencies f0 + t fstep with f0 the frequency of row j R and fstep = n / R.
-template <typename T, int R, bool INV, class Store>
+template <typename T, int R, bool INV, int V, class Store>
 __device__ __forceinline__ void fft_stage_last(const cplx<T>* buf, int ld, int col, int jt, int P,
                                                int nbf, int fstep, const int* sinv, Store& store)
 {
-#pragma unroll 2
+    constexpr int kUnroll = V == 1 ? 2 : 1;
+#pragma unroll kUnroll
     for (int j = jt; j < nbf; j += P) {
-        cplx<T> v[R];
+        cplx<T> v[V][R];
         const cplx<T>* p = buf + j * R * ld + col;
 #pragma unroll
-        for (int t = 0; t < R; ++t) v[t] = p[t * ld];
-        Dft<T, R, INV>::run(v);
+        for (int t = 0; t < R; ++t) {
+            cplx<T> r[V];
+            ld_row<T, V>(p + t * ld, r);
+#pragma unroll
+            for (int c = 0; c < V; ++c) v[c][t] = r[c];
+        }
+#pragma unroll
+        for (int c = 0; c < V; ++c) Dft<T, R, INV>::run(v[c]);
         const int f0 = sinv[j * R];
 #pragma unroll
-        for (int t = 0; t < R; ++t) store(f0 + t * fstep, v[t]);
+        for (int t = 0; t < R; ++t) {
+            cplx<T> r[V];
+#pragma unroll
+            for (int c = 0; c < V; ++c) r[c] = v[c][t];
+            store(f0 + t * fstep, r);
+        }
+    }
+}
+
+template <typename T, bool INV, int V, class Store>
+__device__ __forceinline__ void fft_last_to(const cplx<T>* buf, int ld, int col, int jt, int P,
+                                            const FftPlan& plan, const int* sinv, Store& store)
+{
+    const int last = plan.nst - 1;
+    const int R = plan.radix[last], nbf = plan.n / R, fstep = plan.n / R;
+    switch (R) {
+    case 8: fft_stage_last<T, 8, INV, V>(buf, ld, col, jt, P, nbf, fstep, sinv, store); break;
+    case 4: fft_stage_last<T, 4, INV, V>(buf, ld, col, jt, P, nbf, fstep, sinv, store); break;
+    case 3: fft_stage_last<T, 3, INV, V>(buf, ld, col, jt, P, nbf, fstep, sinv, store); break;
+    default: fft_stage_last<T, 2, INV, V>(buf, ld, col, jt, P, nbf, fstep, sinv, store); break;
     }
 }
 
 // Stage 0 from `load`, the middle stages in shared memory, the last stage to
 // `store` (sinv[row] = frequency held by that row).  All threads must call.
-template <typename T, bool INV, class Load, class Store>
+template <typename T, bool INV, int V, class Load, class Store>
 __device__ void fft_dif_io(cplx<T>* buf, int C, int ld, const FftPlan& plan, const cplx<T>* tw,
                            const int* sinv, Load load, Store store)
 {
-    const int P = blockDim.x / C, col = threadIdx.x % C, jt = threadIdx.x / C;
+    const int G = C / V, P = blockDim.x / G, col = (threadIdx.x % G) * V, jt = threadIdx.x / G;
     const int m = plan.m[0], ts = plan.tstep[0];
     switch (plan.radix[0]) {
-    case 8: fft_stage_first<T, 8, INV>(buf, ld, col, jt, P, m, ts, tw, load); break;
-    case 4: fft_stage_first<T, 4, INV>(buf, ld, col, jt, P, m, ts, tw, load); break;
-    case 3: fft_stage_first<T, 3, INV>(buf, ld, col, jt, P, m, ts, tw, load); break;
-    default: fft_stage_first<T, 2, INV>(buf, ld, col, jt, P, m, ts, tw, load); break;
+    case 8: fft_stage_first<T, 8, INV, V>(buf, ld, col, jt, P, m, ts, tw, load); break;
+    case 4: fft_stage_first<T, 4, INV, V>(buf, ld, col, jt, P, m, ts, tw, load); break;
+    case 3: fft_stage_first<T, 3, INV, V>(buf, ld, col, jt, P, m, ts, tw, load); break;
+    default: fft_stage_first<T, 2, INV, V>(buf, ld, col, jt, P, m, ts, tw, load); break;
     }
     const int last = plan.nst - 1;
     if (last == 0) {   // a one-stage transform is in natural order already
-        for (int f = jt; f < plan.n; f += P) store(f, buf[f * ld + col]);
+        for (int f = jt; f < plan.n; f += P) {
+            cplx<T> r[V];
+            ld_row<T, V>(buf + f * ld + col, r);
+            store(f, r);
+        }
         return;
     }
-    fft_run<T, INV, true>(buf, C, ld, plan, tw, 1, last);
-    const int R = plan.radix[last], nbf = plan.n / R, fstep = plan.n / R;
-    switch (R) {
-    case 8: fft_stage_last<T, 8, INV>(buf, ld, col, jt, P, nbf, fstep, sinv, store); break;
-    case 4: fft_stage_last<T, 4, INV>(buf, ld, col, jt, P, nbf, fstep, sinv, store); break;
-    case 3: fft_stage_last<T, 3, INV>(buf, ld, col, jt, P, nbf, fstep, sinv, store); break;
-    default: fft_stage_last<T, 2, INV>(buf, ld, col, jt, P, nbf, fstep, sinv, store); break;
-    }
+    fft_run<T, INV, true, V>(buf, C, ld, plan, tw, 1, last);
+    fft_last_to<T, INV, V>(buf, ld, col, jt, P, plan, sinv, store);
 }
 
 // All stages but the last in shared memory (input tile in natural order), the
 // last stage to `store`.  All threads must call.
-template <typename T, bool INV, class Store>
+template <typename T, bool INV, int V, class Store>
 __device__ void fft_dif_out(cplx<T>* buf, int C, int ld, const FftPlan& plan, const cplx<T>* tw,
                             const int* sinv, Store store)
 {
-    const int P = blockDim.x / C, col = threadIdx.x % C, jt = threadIdx.x / C;
-    const int last = plan.nst - 1;
-    fft_run<T, INV, true>(buf, C, ld, plan, tw, 0, last);
-    const int R = plan.radix[last], nbf = plan.n / R, fstep = plan.n / R;
-    switch (R) {
-    case 8: fft_stage_last<T, 8, INV>(buf, ld, col, jt, P, nbf, fstep, sinv, store); break;
-    case 4: fft_stage_last<T, 4, INV>(buf, ld, col, jt, P, nbf, fstep, sinv, store); break;
-    case 3: fft_stage_last<T, 3, INV>(buf, ld, col, jt, P, nbf, fstep, sinv, store); break;
-    default: fft_stage_last<T, 2, INV>(buf, ld, col, jt, P, nbf, fstep, sinv, store); break;
-    }
+    const int G = C / V, P = blockDim.x / G, col = (threadIdx.x % G) * V, jt = threadIdx.x / G;
+    fft_run<T, INV, true, V>(buf, C, ld, plan, tw, 0, plan.nst - 1);
+    fft_last_to<T, INV, V>(buf, ld, col, jt, P, plan, sinv, store);
 }
 
 // Inverse digit-reversal table in shared memory: sinv[pos[f]] = f.

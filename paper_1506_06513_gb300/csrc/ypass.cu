@@ -45,10 +45,12 @@ k_ypass(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict
     load_inverse_pos(sinv, pos, g.ny);
     const int ny = g.ny, My = g.My, Ky = g.Ky;
     const int ld = g.Mxp;   // row stride; a plane holds fewer than 2^31 values
-    // this thread's column for the transform stages (fft_run's map)
-    const int col = threadIdx.x % C;
+    // this thread's two adjacent columns in the transform stages (fft_run's
+    // map with V = 2; TX is even, so both lie in one plane)
+    constexpr int V = 2;
+    const int col = (threadIdx.x % (C / V)) * V;
     const int z = z0 + (col >> lgTX), x = x0 + (col & (TX - 1));
-    const bool colok = z < g.nz && x < g.Mxp;
+    const bool colok = z < g.nz && x < g.Mxp;   // Mxp is a multiple of 4
     cplx<T>* gcol = base + (size_t)(colok ? z : 0) * plane + (colok ? x : 0);
     {
         // 16-byte asynchronous copies: each lane moves VEC adjacent columns
@@ -74,16 +76,16 @@ k_ypass(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict
     }
     __syncthreads();
     if (INV) {
-        auto store = [&](int f, cplx<T> v) {
-            if (colok) gcol[f * ld] = v;
+        auto store = [&](int f, const cplx<T>* v) {
+            if (colok) st_row<T, V>(gcol + f * ld, v);
         };
-        fft_dif_out<T, true>(buf, C, C, plan, tws, sinv, store);
+        fft_dif_out<T, true, V>(buf, C, C, plan, tws, sinv, store);
     } else {
-        auto store = [&](int f, cplx<T> v) {   // keep modes |m| <= Ky only
+        auto store = [&](int f, const cplx<T>* v) {   // keep modes |m| <= Ky only
             const int r = f <= Ky ? f : (f >= ny - Ky ? f - ny + My : -1);
-            if (colok && r >= 0) gcol[r * ld] = v;
+            if (colok && r >= 0) st_row<T, V>(gcol + r * ld, v);
         };
-        fft_dif_out<T, false>(buf, C, C, plan, tws, sinv, store);
+        fft_dif_out<T, false, V>(buf, C, C, plan, tws, sinv, store);
     }
 }
 

@@ -55,23 +55,24 @@ k_zinv(const cplx<T>* __restrict__ U, cplx<T>* __restrict__ W, Geom g, FftPlan p
     load_tables<T>(tws, nullptr, tw, nullptr, g.nz, 0);
     load_inverse_pos(sinv, pos, g.nz);
 
-    // this thread's column is fixed across the strided loops (TX divides blockDim)
-    const int tx = threadIdx.x & (TX - 1);
+    // this thread's two adjacent columns in the transform stages (fft_run's map
+    // with V = 2); Mxp is a multiple of 4, so both lie in one row jy
+    constexpr int V = 2;
+    const int tx = (threadIdx.x % (TX / V)) * V;
     const int q = q0 + tx;
     const bool qok = q < Q;
     const int jy = qok ? q / g.Mxp : 0;
     const int x = qok ? q - jy * g.Mxp : 0;
-    const bool kept = qok && x < g.Mx;
     const T two_pi = T(6.283185307179586476925286766559);
-    const T kx = two_pi * T(x) / T(g.Lx);
+    const T kxv[V] = {two_pi * T(x) / T(g.Lx), two_pi * T(x + 1) / T(g.Lx)};
     const T ky = two_pi * T(mode_of(jy, g.Ky)) / T(g.Ly);
     const int nz = g.nz, Kz = g.Kz, Mz = g.Mz;
     __syncthreads();
 
     for (int f = 0; f < nf; ++f) {
         cplx<T>* out = W + (size_t)f * nz * Wplane + (qok ? q : 0);
-        auto store = [&](int z, cplx<T> v) {
-            if (qok) out[(size_t)z * Wplane] = v;
+        auto store = [&](int z, const cplx<T>* v) {
+            if (qok) st_row<T, V>(out + (size_t)z * Wplane, v);
         };
         if (f < 3) {
             // U's row padding (x >= Mx) is zero
@@ -93,26 +94,34 @@ k_zinv(const cplx<T>* __restrict__ U, cplx<T>* __restrict__ W, Geom g, FftPlan p
             }
             cp_async_wait_all();
             __syncthreads();
-            fft_dif_out<T, true>(buf, TX, TX, plan, tws, sinv, store);
+            fft_dif_out<T, true, V>(buf, TX, TX, plan, tws, sinv, store);
         } else {
             // omega = i (k x u) from two velocity components
             const int cA = f == 3 ? 2 : f == 4 ? 0 : 1;
             const int cB = f == 3 ? 1 : f == 4 ? 2 : 0;
-            const T kb = f == 3 ? T(0) : f == 4 ? kx : ky;   // kz enters per mode
-            const T ka = f == 3 ? ky : f == 4 ? T(0) : kx;
             const cplx<T>* srcA = U + cA * Ustride + (qok ? q : 0);
             const cplx<T>* srcB = U + cB * Ustride + (qok ? q : 0);
-            auto load = [&](int s) -> cplx<T> {
+            // U's row padding (x >= Mx) is zero, so its vorticity is too
+            auto load = [&](int s, cplx<T>* r) {
                 const int jz = s <= Kz ? s : (s >= nz - Kz ? s - nz + Mz : -1);
-                if (!kept || jz < 0) return mkc<T>(0, 0);
-                const cplx<T> a = srcA[(size_t)jz * Q], b = srcB[(size_t)jz * Q];
+                if (!qok || jz < 0) {
+#pragma unroll
+                    for (int c = 0; c < V; ++c) r[c] = mkc<T>(0, 0);
+                    return;
+                }
+                cplx<T> a[V], b[V];
+                ld_row<T, V>(srcA + (size_t)jz * Q, a);
+                ld_row<T, V>(srcB + (size_t)jz * Q, b);
                 const T kz = two_pi * T(mode_of(jz, Kz)) / T(g.Lz);
-                // f=3: ky uz - kz uy; f=4: kz ux - kx uz; f=5: kx uy - ky ux
-                const T k1 = f == 4 ? kz : ka;
-                const T k2 = f == 3 ? kz : kb;
-                return cmuli(mkc<T>(k1 * a.x - k2 * b.x, k1 * a.y - k2 * b.y));
+#pragma unroll
+                for (int c = 0; c < V; ++c) {
+                    // f=3: ky uz - kz uy; f=4: kz ux - kx uz; f=5: kx uy - ky ux
+                    const T k1 = f == 3 ? ky : f == 4 ? kz : kxv[c];
+                    const T k2 = f == 3 ? kz : f == 4 ? kxv[c] : ky;
+                    r[c] = cmuli(mkc<T>(k1 * a[c].x - k2 * b[c].x, k1 * a[c].y - k2 * b[c].y));
+                }
             };
-            fft_dif_io<T, true>(buf, TX, TX, plan, tws, sinv, load, store);
+            fft_dif_io<T, true, V>(buf, TX, TX, plan, tws, sinv, load, store);
         }
         __syncthreads();
     }
@@ -158,14 +167,15 @@ k_zfwd(const cplx<T>* __restrict__ W, cplx<T>* __restrict__ Nh, Geom g, FftPlan 
     }
     cp_async_wait_all();
     __syncthreads();
-    const int q = q0 + (threadIdx.x & (TX - 1));
-    const bool qok = q < Q;
+    constexpr int V = 2;                       // adjacent columns per thread
+    const int q = q0 + (threadIdx.x % (TX / V)) * V;
+    const bool qok = q < Q;                    // Q is a multiple of 4
     cplx<T>* out = Nh + (size_t)c * Mz * Q + (qok ? q : 0);
-    auto store = [&](int f, cplx<T> v) {   // keep modes |m| <= Kz only
+    auto store = [&](int f, const cplx<T>* v) {   // keep modes |m| <= Kz only
         const int jz = f <= Kz ? f : (f >= nz - Kz ? f - nz + Mz : -1);
-        if (qok && jz >= 0) out[(size_t)jz * Q] = v;
+        if (qok && jz >= 0) st_row<T, V>(out + (size_t)jz * Q, v);
     };
-    fft_dif_out<T, false>(buf, TX, TX, plan, tws, sinv, store);
+    fft_dif_out<T, false, V>(buf, TX, TX, plan, tws, sinv, store);
 }
 
 // Pointwise spectral update over the kept modes, VEC adjacent columns per
