@@ -151,10 +151,13 @@ __device__ __forceinline__ void twiddle_table(cplx<T>* v, const cplx<T>* tw, int
 template <typename T, int V>
 __device__ __forceinline__ void ld_row(const cplx<T>* p, cplx<T>* o)
 {
-    if constexpr (V == 2 && sizeof(T) == 4) {
-        const float4 q = *reinterpret_cast<const float4*>(p);
-        o[0] = mkc<T>(q.x, q.y);
-        o[1] = mkc<T>(q.z, q.w);
+    if constexpr (V % 2 == 0 && sizeof(T) == 4) {
+#pragma unroll
+        for (int c = 0; c < V; c += 2) {
+            const float4 q = *reinterpret_cast<const float4*>(p + c);
+            o[c] = mkc<T>(q.x, q.y);
+            o[c + 1] = mkc<T>(q.z, q.w);
+        }
     } else {
 #pragma unroll
         for (int c = 0; c < V; ++c) o[c] = p[c];
@@ -164,8 +167,10 @@ __device__ __forceinline__ void ld_row(const cplx<T>* p, cplx<T>* o)
 template <typename T, int V>
 __device__ __forceinline__ void st_row(cplx<T>* p, const cplx<T>* o)
 {
-    if constexpr (V == 2 && sizeof(T) == 4) {
-        *reinterpret_cast<float4*>(p) = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
+    if constexpr (V % 2 == 0 && sizeof(T) == 4) {
+#pragma unroll
+        for (int c = 0; c < V; c += 2)
+            *reinterpret_cast<float4*>(p + c) = make_float4(o[c].x, o[c].y, o[c + 1].x, o[c + 1].y);
     } else {
 #pragma unroll
         for (int c = 0; c < V; ++c) p[c] = o[c];
