@@ -144,6 +144,13 @@ __device__ __forceinline__ void cp_async_16(void* smem_dst, const void* gmem_src
 
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// Bulk prefetch of `bytes` (a multiple of 16) from a 16-byte aligned global
+// address into L2; no completion to wait for.
+__device__ __forceinline__ void prefetch_l2_bulk(const void* gmem_src, unsigned bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(gmem_src), "r"(bytes) : "memory");
+}
+
 // Signed mode of a stored spectral index j in [0, M) with M = 2K + 1.
 __host__ __device__ __forceinline__ int mode_of(int j, int K) { return j <= K ? j : j - (2 * K + 1); }
 // FFT frequency slot of a stored index j for a length-n transform.

@@ -694,6 +694,15 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int row0 = tile * RB;
         cplx<T> v[R];
+        // the six input lines of this block's next tile on their way into L2
+        if (tid < 6) {
+            const int next0 = (tile + gridDim.x) * RB;
+            if (next0 < nrows) {
+                const int nr = min(RB, nrows - next0);
+                prefetch_l2_bulk(W + ((size_t)tid * nrows + next0) * Mxp,
+                                 (unsigned)(nr * Mxp * sizeof(cplx<T>)));
+            }
+        }
         if (tid < RB) {
             const int r = row0 + tid;
             int mask = 0;
