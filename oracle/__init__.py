@@ -46,7 +46,9 @@ class Params(C.Structure):
                 ("nu", C.c_double), ("eta", C.c_double), ("cfl", C.c_double),
                 ("dt_fixed", C.c_double), ("dt_max", C.c_double),
                 ("mean_mode", C.c_int), ("pad_", C.c_int),
-                ("u_inf", C.c_double * 3)]
+                ("u_inf", C.c_double * 3),
+                ("sponge_c", C.c_double), ("sponge_width", C.c_double * 3),
+                ("layer_width", C.c_double * 3)]
 
 
 _F = C.c_double * MAX_FOURIER
@@ -114,6 +116,11 @@ def lib():
         L.orc_inverse.argtypes = [C.POINTER(Params), _cp, _dp, C.c_int]
         L.orc_set_state.argtypes = [C.POINTER(Params), _dp, _cp, _cp, C.POINTER(Scalars)]
         L.orc_get_state.argtypes = [C.POINTER(Params), _cp, _dp]
+        L.orc_sponge_term.argtypes = [C.POINTER(Params), _cp, _cp]
+        L.orc_sponge_mask.argtypes = [C.POINTER(Params), _dp]
+        L.orc_sponge_mask.restype = C.c_double
+        L.orc_layer_mask.argtypes = [C.POINTER(Params), _dp]
+        L.orc_layer_mask.restype = C.c_double
         L.orc_rhs.argtypes = [C.POINTER(Params), C.POINTER(Insect), C.c_double, _cp, _cp, _dp]
         L.orc_rhs.restype = C.c_int
         L.orc_physical_fields.argtypes = [C.POINTER(Params), C.POINTER(Insect), C.c_double, _cp,
@@ -140,6 +147,9 @@ def make_params(cfg: dict) -> Params:
     p.dealias_strict = int(cfg.get("dealias_strict", 0))
     p.mean_mode = 1 if cfg.get("mean_mode", "fixed") == "free" else 0
     p.u_inf[:] = cfg.get("u_inf", (0.0, 0.0, 0.0))
+    p.sponge_c = cfg.get("sponge_c", 0.0)
+    p.sponge_width[:] = cfg.get("sponge_width", (0.0, 0.0, 0.0))
+    p.layer_width[:] = cfg.get("layer_width", (0.0, 0.0, 0.0))
     return p
 
 
@@ -305,6 +315,18 @@ class Spectral:
         ins = make_insect(insect)
         lib().orc_rhs(C.byref(self.p), _ins_ptr(ins), t, np.ascontiguousarray(uh), nh, sums)
         return nh, sums
+
+    def sponge_term(self, vh):
+        """-(i k x vh) / (C_sp |k|^2), zero at k = 0 (no truncation, no projection)."""
+        sh = np.zeros_like(vh)
+        lib().orc_sponge_term(C.byref(self.p), np.ascontiguousarray(vh), sh)
+        return sh
+
+    def sponge_mask(self, X):
+        return lib().orc_sponge_mask(C.byref(self.p), np.ascontiguousarray(X, dtype=np.float64))
+
+    def layer_mask(self, X):
+        return lib().orc_layer_mask(C.byref(self.p), np.ascontiguousarray(X, dtype=np.float64))
 
     def physical_fields(self, uh, t=0.0, insect=None):
         """[14][nz][ny][nx]: u, omega, chi, colour, u_s, u x omega - chi/C_eta (u - u_s)."""

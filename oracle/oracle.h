@@ -39,6 +39,13 @@ typedef struct {
     int mean_mode;       /* 0: k = 0 mode held at u_inf; 1: evolves       */
     int pad_;
     double u_inf[3];
+    /* Wake removal (Sec. 2.3).  Vorticity sponge: constant C_sp (0: off) and
+     * the sponge region, the union over axes i of x_i >= L_i - sponge_width[i]
+     * (width 0: none on that axis).  Dirichlet layer: u = u_inf penalized with
+     * C_eta in x_i >= L_i - layer_width[i] (width 0: none).                 */
+    double sponge_c;
+    double sponge_width[3];
+    double layer_width[3];
 } orc_params;
 
 typedef struct {
@@ -98,6 +105,9 @@ void orc_mask_grid(const orc_params *p, const orc_insect *ins, double t,
 
 /* ---- spectral operators (Sec. 2.4) ---- */
 void orc_dealias(const orc_params *p, double complex *fh, int ncomp);
+double orc_sponge_mask(const orc_params *p, const double *X);
+double orc_layer_mask(const orc_params *p, const double *X);
+void orc_sponge_term(const orc_params *p, const double complex *vh, double complex *sh);
 void orc_project(const orc_params *p, double complex *fh);
 void orc_curl(const orc_params *p, const double complex *uh, double complex *wh);
 void orc_forward(const orc_params *p, const double *u, double complex *uh, int ncomp);

@@ -66,6 +66,55 @@ void orc_dealias(const orc_params *p, double complex *fh, int ncomp)
                 }
 }
 
+/* Wake-removal regions (Sec. 2.3), a reading: the paper places a sponge and a
+ * thinner Dirichlet layer at the domain borders without formulas; here each
+ * is the union over axes of the end slab x_i >= L_i - width_i, mask 1 inside
+ * (a grid-aligned layer, no smoothing). */
+static double end_slab(const orc_params *p, const double *w, const double *X)
+{
+    const double L[3] = {p->Lx, p->Ly, p->Lz};
+    for (int i = 0; i < 3; ++i)
+        if (w[i] > 0 && X[i] >= L[i] - w[i]) return 1.0;
+    return 0.0;
+}
+
+double orc_sponge_mask(const orc_params *p, const double *X) { return end_slab(p, p->sponge_width, X); }
+
+double orc_layer_mask(const orc_params *p, const double *X) { return end_slab(p, p->layer_width, X); }
+
+/* Vorticity sponge (Sec. 2.3, Eq. PNST_org_momentum): -(1/C_sp) curl of the
+ * Biot-Savart-type inverse of chi_sp omega.  In Fourier space, with
+ * vh = FFT(chi_sp omega)/N, the reading that makes the term damp the vorticity
+ * (the printed 1/nabla^2 taken as division by |k|^2, i.e. the inverse of
+ * -nabla^2) is  S_hat = -(i k x vh) / (C_sp |k|^2),  S_hat(0) = 0.  Then
+ * curl S = -(1/C_sp) times the solenoidal part of chi_sp omega, the term is
+ * divergence-free and leaves the mean unchanged. */
+void orc_sponge_term(const orc_params *p, const double complex *vh, double complex *sh)
+{
+    int hx = p->nx / 2 + 1;
+    long nh = n_half(p);
+    for (int iz = 0; iz < p->nz; ++iz)
+        for (int iy = 0; iy < p->ny; ++iy)
+            for (int ix = 0; ix < hx; ++ix) {
+                long i = ((long)iz * p->ny + iy) * hx + ix;
+                double k[3];
+                wavevector(p, ix, iy, iz, k);
+                double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+                if (k2 == 0.0) {
+                    for (int c = 0; c < 3; ++c) sh[c * nh + i] = 0;
+                    continue;
+                }
+                double complex v0 = vh[i], v1 = vh[nh + i], v2 = vh[2 * nh + i];
+                double complex cx = I * (k[1] * v2 - k[2] * v1);
+                double complex cy = I * (k[2] * v0 - k[0] * v2);
+                double complex cz = I * (k[0] * v1 - k[1] * v0);
+                double f = -1.0 / (p->sponge_c * k2);
+                sh[i] = f * cx;
+                sh[nh + i] = f * cy;
+                sh[2 * nh + i] = f * cz;
+            }
+}
+
 /* Leray projection, Algorithm 1 step (d): F <- F - k (k.F)/|k|^2, k != 0.
  * This is the Fourier-space solution of Eq. PNST_UP_pressure_poisson_eqn. */
 void orc_project(const orc_params *p, double complex *fh)
@@ -154,7 +203,8 @@ static double grid_h(const orc_params *p, const orc_insect *ins)
  * Returns 1 if a non-finite value was met, else 0.
  */
 static int physical_terms(const orc_params *p, const orc_insect *ins, double t,
-                          const double complex *uh, double *nl, double *sums, double *fields)
+                          const double complex *uh, double *nl, double *sums, double *fields,
+                          double *vsp)
 {
     long N = n_phys(p), nhs = n_half(p);
     double complex *wh = malloc(sizeof(double complex) * (size_t)(3 * nhs));
@@ -187,10 +237,17 @@ static int physical_terms(const orc_params *p, const orc_insect *ins, double t,
                 double lamb[3] = {uu[1] * ww[2] - uu[2] * ww[1],
                                   uu[2] * ww[0] - uu[0] * ww[2],
                                   uu[0] * ww[1] - uu[1] * ww[0]};
+                /* Dirichlet layer u = u_inf (Sec. 2.3), a penalization of its own */
+                double chi_d = orc_layer_mask(p, X);
                 for (int c = 0; c < 3; ++c) {
                     double v = lamb[c] - chi / p->eta * (uu[c] - us[c]);
+                    if (chi_d > 0) v -= chi_d / p->eta * (uu[c] - p->u_inf[c]);
                     nl[c * N + i] = v;
                     if (!isfinite(v) || !isfinite(uu[c])) bad = 1;
+                }
+                if (vsp) {
+                    double chi_sp = orc_sponge_mask(p, X);
+                    for (int c = 0; c < 3; ++c) vsp[c * N + i] = chi_sp * ww[c];
                 }
                 if (fields) {
                     for (int c = 0; c < 3; ++c) {
@@ -241,7 +298,7 @@ void orc_physical_fields(const orc_params *p, const orc_insect *ins, double t,
     long N = n_phys(p);
     double *nl = malloc(sizeof(double) * (size_t)(3 * N));
     double sums[ORC_NSUMS];
-    physical_terms(p, ins, t, uh, nl, sums, fields);
+    physical_terms(p, ins, t, uh, nl, sums, fields, NULL);
     free(nl);
 }
 
@@ -255,9 +312,21 @@ int orc_rhs(const orc_params *p, const orc_insect *ins, double t,
 {
     long N = n_phys(p), nhs = n_half(p);
     double *nl = malloc(sizeof(double) * (size_t)(3 * N));
-    int bad = physical_terms(p, ins, t, uh, nl, sums, NULL);
+    double *vsp = p->sponge_c > 0 ? malloc(sizeof(double) * (size_t)(3 * N)) : NULL;
+    int bad = physical_terms(p, ins, t, uh, nl, sums, NULL, vsp);
 
     orc_forward(p, nl, nh, 3);
+    if (vsp) {
+        /* Algorithm 1 step (c): the sponge term joins the sources */
+        double complex *vh = malloc(sizeof(double complex) * (size_t)(3 * nhs));
+        double complex *sh = malloc(sizeof(double complex) * (size_t)(3 * nhs));
+        orc_forward(p, vsp, vh, 3);
+        orc_sponge_term(p, vh, sh);
+        for (long i = 0; i < 3 * nhs; ++i) nh[i] += sh[i];
+        free(vh);
+        free(sh);
+        free(vsp);
+    }
     orc_dealias(p, nh, 3);
     orc_project(p, nh);
     if (p->mean_mode == 0)
@@ -303,7 +372,7 @@ void orc_ab2_update(const orc_params *p, double complex *uh,
             }
 }
 
-/* One step of Algorithm 1 (without sponge, free flight and output). */
+/* One step of Algorithm 1 (without free flight and output). */
 int orc_step(const orc_params *p, const orc_insect *ins, double complex *uh,
              double complex *nh_prev, orc_scalars *s, double *row)
 {
