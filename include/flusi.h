@@ -74,6 +74,14 @@ typedef struct flusi_options {
     int dealias_strict;    /* 0: keep |m| <= floor(n/3); 1: keep |m| < n/3              */
     int force_ring;        /* device rows kept between flusi_forces calls (default 4096)*/
     int use_graph;         /* 1: replay a captured CUDA graph per step (default 1)      */
+    /* Wake removal (Sec. 2.3).  Vorticity sponge -(1/C_sp) curl (chi_sp omega)/nabla^2
+     * with C_sp = sponge_c (0: off, the default) over the region where some
+     * x_i >= L_i - sponge_width[i] (width 0: no slab on that axis).  Dirichlet
+     * layer: u = u_inf penalized with C_eta where some x_i >= L_i - layer_width[i].
+     * Both masks are 1 inside their slabs and 0 elsewhere.                      */
+    double sponge_c;
+    double sponge_width[3];
+    double layer_width[3];
 } flusi_options;
 
 /* Insect geometry and kinematics (Sec. 3).  Angles in radians.  Kinematic

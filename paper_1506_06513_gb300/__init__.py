@@ -32,7 +32,9 @@ class FlusiError(RuntimeError):
 class Options(C.Structure):
     _fields_ = [("cfl", C.c_double), ("dt_fixed", C.c_double), ("dt_max", C.c_double),
                 ("u_inf", C.c_double * 3), ("mean_mode", C.c_int), ("dealias_strict", C.c_int),
-                ("force_ring", C.c_int), ("use_graph", C.c_int)]
+                ("force_ring", C.c_int), ("use_graph", C.c_int),
+                ("sponge_c", C.c_double), ("sponge_width", C.c_double * 3),
+                ("layer_width", C.c_double * 3)]
 
 
 _F = C.c_double * MAX_FOURIER
@@ -278,6 +280,9 @@ def make_options(cfg: dict) -> Options:
     o.dealias_strict = int(cfg.get("dealias_strict", 0))
     o.force_ring = int(cfg.get("force_ring", 4096))
     o.use_graph = int(cfg.get("use_graph", 1))
+    o.sponge_c = cfg.get("sponge_c", 0.0)
+    o.sponge_width[:] = cfg.get("sponge_width", (0.0, 0.0, 0.0))
+    o.layer_width[:] = cfg.get("layer_width", (0.0, 0.0, 0.0))
     return o
 
 

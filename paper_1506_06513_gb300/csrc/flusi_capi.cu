@@ -227,17 +227,14 @@ double box_margin(flusi_t h)
     return s.profile == 1 ? 1e300 : s.h;
 }
 
-const char* kKernelNames[] = {"kinematics", "zinv_curl", "yinv", "xpass_phys", "scalars", "yfwd",
-                              "zfwd", "update"};
-constexpr int kStepKernels = 8;
+const char* kKernelNames[] = {"kinematics", "zinv_curl", "yinv", "xpass_phys", "scalars", "sponge_x",
+                              "yfwd", "zfwd", "update"};
+constexpr int kMaxStepKernels = 9;
+constexpr int kSpongeSlot = 5;
 
-// The transformed nonlinear term N^ [3][Mz][My][Mxp] lives in W's vorticity
-// fields (3..5), which are free once the x pass has run.
-void* nhat(flusi_t h)
-{
-    const size_t cs = h->prec == FLUSI_FP64 ? 16 : 8;
-    return h->ws + h->oW + (size_t)3 * h->g.nz * h->g.ny * h->g.Mxp * cs;
-}
+bool has_sponge(flusi_t h) { return h->opt.sponge_c > 0; }
+
+int step_kernels(flusi_t h) { return has_sponge(h) ? kMaxStepKernels : kMaxStepKernels - 1; }
 
 ZfwdExtra zextra(flusi_t h)
 {
@@ -246,10 +243,33 @@ ZfwdExtra zextra(flusi_t h)
     ze.etab = at<double>(h, h->oetab);
     for (int i = 0; i < 3; ++i) ze.u_inf[i] = h->opt.u_inf[i];
     ze.mean_free = h->opt.mean_mode;
+    ze.sponge_c = h->opt.sponge_c;
     return ze;
 }
 
-// Enqueue one step; with `ev` (kStepKernels + 1 events) records an event
+// First grid index of the end slab x_i >= L_i - w (i * L_i/n_i compared in
+// FP64 as the oracle does); n when w = 0.
+int slab_start(int n, double L, double w)
+{
+    if (!(w > 0)) return n;
+    const double d = L / n;
+    for (int i = 0; i < n; ++i)
+        if (i * d >= L - w) return i;
+    return n;
+}
+
+// Wake-removal fields of an x-pass descriptor (Sec. 2.3).
+void set_wake(flusi_t h, XExtra& xe)
+{
+    const int n[3] = {h->nx, h->ny, h->nz};
+    for (int i = 0; i < 3; ++i) {
+        xe.layer0[i] = slab_start(n[i], h->L[i], h->opt.layer_width[i]);
+        xe.sponge0[i] = slab_start(n[i], h->L[i], h->opt.sponge_width[i]);
+        xe.u_inf[i] = h->opt.u_inf[i];
+    }
+}
+
+// Enqueue one step; with `ev` (step_kernels + 1 events) records an event
 // before each kernel and after the last.
 cudaError_t enqueue_step(flusi_t h, cudaStream_t s, cudaEvent_t* ev)
 {
@@ -290,6 +310,7 @@ cudaError_t enqueue_step(flusi_t h, cudaStream_t s, cudaEvent_t* ev)
     xe.shape = make_shape(h);
     xe.part = at<double>(h, h->opart);
     xe.comp0 = 0;
+    set_wake(h, xe);
     if ((e = launch_xpass(fp64, XP_PHYS, W, g, h->px, tx, at<int>(h, h->opx), xe, st, s))) return e;
     mark();
     if (branch) {
@@ -302,12 +323,22 @@ cudaError_t enqueue_step(flusi_t h, cudaStream_t s, cudaEvent_t* ev)
     if ((e = cudaGetLastError())) return e;
     if (branch && (e = cudaEventRecord(h->ev_sc, sk))) return e;
     mark();
-    if ((e = launch_ypass(fp64, false, W, g, h->py, ty, at<int>(h, h->opy), 3, st, s))) return e;
+    const int nfwd = has_sponge(h) ? 6 : 3;
+    if (has_sponge(h)) {
+        // chi_sp omega of the vorticity still in W[3..5] (x transformed back in place)
+        XExtra xs{};
+        xs.ncomp = 3;
+        xs.comp0 = 3;
+        set_wake(h, xs);
+        if ((e = launch_xpass(fp64, XP_SPONGE, W, g, h->px, tx, at<int>(h, h->opx), xs, st, s))) return e;
+        mark();
+    }
+    if ((e = launch_ypass(fp64, false, W, g, h->py, ty, at<int>(h, h->opy), nfwd, st, s))) return e;
     mark();
-    if ((e = launch_zfwd(fp64, W, nhat(h), g, h->pz, tz, at<int>(h, h->opz), st, s))) return e;
+    if ((e = launch_zfwd(fp64, W, nfwd, g, h->pz, tz, at<int>(h, h->opz), st, s))) return e;
     mark();
     if (branch && (e = cudaStreamWaitEvent(s, h->ev_sc, 0))) return e;
-    if ((e = launch_zupdate(fp64, 0, nhat(h), h->ws + h->oU, h->ws + h->oH, g, zextra(h), st, s))) return e;
+    if ((e = launch_zupdate(fp64, 0, W, h->ws + h->oU, h->ws + h->oH, g, zextra(h), st, s))) return e;
     mark();
     return cudaSuccess;
 }
@@ -401,6 +432,12 @@ int flusi_set_options(flusi_t h, const flusi_options* o)
     if (!(o->cfl > 0) || o->dt_fixed < 0 || o->dt_max < 0 || o->force_ring < 1 ||
         (o->mean_mode != 0 && o->mean_mode != 1) || (o->dealias_strict != 0 && o->dealias_strict != 1))
         return fail(h, FLUSI_EINVAL, "bad option value");
+    if (!(o->sponge_c >= 0) || !std::isfinite(o->sponge_c))
+        return fail(h, FLUSI_EINVAL, "sponge_c must be >= 0 (0: no sponge)");
+    for (int i = 0; i < 3; ++i)
+        if (!(o->sponge_width[i] >= 0 && o->sponge_width[i] <= h->L[i]) ||
+            !(o->layer_width[i] >= 0 && o->layer_width[i] <= h->L[i]))
+            return fail(h, FLUSI_EINVAL, "sponge and layer widths must lie in [0, L]");
     if (h->bound && (o->force_ring != h->opt.force_ring || o->dealias_strict != h->opt.dealias_strict))
         return fail(h, FLUSI_EINVAL, "force_ring and dealias_strict cannot change after flusi_bind");
     h->opt = *o;
@@ -520,12 +557,13 @@ int flusi_set_state(flusi_t h, const void* u, int where)
         }
     }
     CK(launch_ypass(fp64, false, W, g, h->py, at<double2>(h, h->oty), at<int>(h, h->opy), 3, nullptr, s), "y forward");
-    CK(launch_zfwd(fp64, W, nhat(h), g, h->pz, at<double2>(h, h->otz), at<int>(h, h->opz), nullptr, s),
+    CK(launch_zfwd(fp64, W, 3, g, h->pz, at<double2>(h, h->otz), at<int>(h, h->opz), nullptr, s),
        "z forward");
     ZfwdExtra ze = zextra(h);
     ze.coef = nullptr;
     ze.etab = nullptr;
-    CK(launch_zupdate(fp64, 1, nhat(h), h->ws + h->oU, h->ws + h->oH, g, ze, nullptr, s), "spectral set");
+    ze.sponge_c = 0;
+    CK(launch_zupdate(fp64, 1, W, h->ws + h->oU, h->ws + h->oH, g, ze, nullptr, s), "spectral set");
     CK(cudaStreamSynchronize(s), "set_state");
     h->has_state = 1;
     h->poisoned = 0;
@@ -697,6 +735,7 @@ int flusi_debug_fields(flusi_t h, void* out_dev)
     xe.shape = make_shape(h);
     xe.rout = out_dev;
     xe.comp0 = 0;
+    set_wake(h, xe);
     CK(launch_xpass(fp64, XP_DUMP, W, g, h->px, at<double2>(h, h->otx), at<int>(h, h->opx), xe, nullptr, s), "x dump");
     return FLUSI_OK;
 }
@@ -707,31 +746,33 @@ int flusi_profile_step(flusi_t h, int n, double* ms, const char** names, int* nk
     if (rc) return rc;
     if (n < 1 || !ms || !nk) return fail(h, FLUSI_EINVAL, "bad argument");
     if (h->poisoned) return fail(h, FLUSI_ESTATE, "handle poisoned");
-    cudaEvent_t ev[kStepKernels + 1];
+    const int nk_step = step_kernels(h);
+    cudaEvent_t ev[kMaxStepKernels + 1];
     for (auto& e : ev) CK(cudaEventCreate(&e), "event");
-    std::vector<double> acc(kStepKernels, 0.0);
+    std::vector<double> acc(nk_step, 0.0);
     for (int i = 0; i < n; ++i) {
         CK(enqueue_step(h, h->stream, ev), "enqueue step");
-        CK(cudaEventSynchronize(ev[kStepKernels]), "event sync");
-        for (int k = 0; k < kStepKernels; ++k) {
+        CK(cudaEventSynchronize(ev[nk_step]), "event sync");
+        for (int k = 0; k < nk_step; ++k) {
             float t = 0;
             CK(cudaEventElapsedTime(&t, ev[k], ev[k + 1]), "elapsed");
             acc[k] += t;
         }
     }
     for (auto& e : ev) cudaEventDestroy(e);
-    for (int k = 0; k < kStepKernels; ++k) {
+    for (int k = 0, slot = 0; k < nk_step; ++k, ++slot) {
+        if (slot == kSpongeSlot && !has_sponge(h)) ++slot;
         ms[k] = acc[k] / n;
-        if (names) names[k] = kKernelNames[k];
+        if (names) names[k] = kKernelNames[slot];
     }
-    *nk = kStepKernels;
+    *nk = nk_step;
     return read_status(h, nullptr);
 }
 
 int flusi_kernels_per_step(flusi_t h, int* count)
 {
     if (!h || !count) return FLUSI_EINVAL;
-    *count = kStepKernels;
+    *count = step_kernels(h);
     return FLUSI_OK;
 }
 

@@ -40,16 +40,20 @@ struct ZfwdExtra {
     const double* etab;       // mode 0: [E1x Mx][E1y My][E1z Mz][E2x][E2y][E2z]
     double u_inf[3];
     int mean_free;
+    double sponge_c;          // mode 0: > 0 adds the vorticity sponge of W[3..5]
 };
-// forward z transform of W[0..2] (A form) into Nh [3][Mz][My][Mxp] (kept modes)
-cudaError_t launch_zfwd(int fp64, const void* W, void* Nh, const Geom& g, const FftPlan& plan,
+// forward z transform of W[0..nf-1] (A form), in place: the kept modes jz < Mz
+// end in rows jz of each field's A-form layout
+cudaError_t launch_zfwd(int fp64, void* W, int nf, const Geom& g, const FftPlan& plan,
                         const double2* tw, const int* pos, const StepState* st, cudaStream_t s);
-// 1/N, projection and (mode 0) IF-AB2 update of U, H or (mode 1) U = N, H = 0
-cudaError_t launch_zupdate(int fp64, int mode, const void* Nh, void* U, void* H, const Geom& g,
+// 1/N, sponge, projection and (mode 0) IF-AB2 update of U, H or (mode 1) U = N, H = 0,
+// reading the kept modes that launch_zfwd left in W
+cudaError_t launch_zupdate(int fp64, int mode, const void* W, void* U, void* H, const Geom& g,
                            const ZfwdExtra& ex, const StepState* st, cudaStream_t s);
 
 // x pass (xpass.cu)
-enum XMode { XP_PHYS = 0, XP_R2C = 1, XP_C2R = 2, XP_DUMP = 3 };
+// XP_SPONGE: c2r of W[comp0 .. comp0+2], times the sponge mask, r2c back in place
+enum XMode { XP_PHYS = 0, XP_R2C = 1, XP_C2R = 2, XP_DUMP = 3, XP_SPONGE = 4 };
 struct XExtra {
     const Frame* frame;
     Shape shape;
@@ -60,6 +64,11 @@ struct XExtra {
     int ncomp;               // XP_R2C / XP_C2R: components
     int comp0;               // first W component written (R2C) or read (C2R)
     long long cstride;       // elements between components of rin / rout
+    // Sec. 2.3 wake removal: first grid index of each axis' end slab (the
+    // axis length when there is none)
+    int layer0[3];           // XP_PHYS / XP_DUMP: Dirichlet layer u = u_inf
+    int sponge0[3];          // XP_SPONGE: vorticity sponge region
+    double u_inf[3];
 };
 int xpass_grid(int fp64, const Geom& g);   // CTAs of the persistent physical pass
 cudaError_t launch_xpass(int fp64, int mode, void* W, const Geom& g, const FftPlan& plan,

@@ -394,6 +394,21 @@ k_xpass(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict
             fft_dif<T, true>(buf, C, ld, plan, tws, 1, plan.nst);
         }
 
+        if (MODE == XP_SPONGE) {
+            // chi_sp omega (Sec. 2.3): keep the points of the sponge slabs
+            for (int i = tid; i < C * nh; i += kThreadsX) {
+                const int row = i / C, col = i - row * C;
+                const int r = row0 + (col & (RB - 1));
+                const int p = ipos[row];
+                const int z = r / g.ny, y = r - z * g.ny;
+                const bool in_row = y >= ex.sponge0[1] || z >= ex.sponge0[2];
+                cplx<T>& b = buf[row * ld + col];
+                b.x = (in_row || 2 * p >= ex.sponge0[0]) ? b.x : T(0);
+                b.y = (in_row || 2 * p + 1 >= ex.sponge0[0]) ? b.y : T(0);
+            }
+            __syncthreads();
+        }
+
 
         if (MODE == XP_C2R) {
             for (int i = tid; i < C * nh; i += kThreadsX) {
@@ -456,9 +471,12 @@ k_xpass(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict
                         T lamb[3];
                         cross3(u[h], om[h], lamb);
                         const T pen = chi2[h] * F.inv_eta;
+                        // Dirichlet layer u = u_inf (Sec. 2.3), penalized with C_eta
+                        const bool lay = y >= ex.layer0[1] || z >= ex.layer0[2] || 2 * p + h >= ex.layer0[0];
                         T uu = T(0);
                         for (int c = 0; c < 3; ++c) {
                             nl[h][c] = lamb[c] - pen * (u[h][c] - us2[h][c]);
+                            if (lay) nl[h][c] -= F.inv_eta * (u[h][c] - T(ex.u_inf[c]));
                             uu += u[h][c] * u[h][c];
                             if (!isfinite(nl[h][c]) || !isfinite(u[h][c])) bad = 1;
                         }
@@ -616,7 +634,7 @@ __device__ __forceinline__ void sq_exchange_pre(cplx<T>* x, int j, int width, co
     }
 }
 
-template <typename T, int R>
+template <typename T, int R, bool LAYER>
 __global__ void __launch_bounds__(192, sizeof(T) == 4 ? 3 : 1)
 k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExtra ex,
            const StepState* __restrict__ st)
@@ -690,6 +708,8 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
     const T dxT = T(g.dx), dyT = T(g.dy), dzT = T(g.dz);
     const FrameT<T>& F = *Fs;
     constexpr int NG = 192 / R;            // lane groups; group c owns lines c and c + NG
+    constexpr bool has_layer = LAYER;   // a Dirichlet layer is set
+    const T uinf[3] = {T(ex.u_inf[0]), T(ex.u_inf[1]), T(ex.u_inf[2])};
 
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int row0 = tile * RB;
@@ -772,6 +792,14 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
                             om[q] = h ? wv[q].y : wv[q].x;
                         }
                         cross3(u, om, nl[h]);
+                        if (has_layer) {   // Dirichlet layer u = u_inf (Sec. 2.3)
+                            const int r = row0 + rr, z = r / g.ny, y = r - z * g.ny;
+                            const int pp = lrow / R + R * (lrow % R);
+                            if (y >= ex.layer0[1] || z >= ex.layer0[2] || 2 * pp + h >= ex.layer0[0]) {
+#pragma unroll
+                                for (int q = 0; q < 3; ++q) nl[h][q] -= F.inv_eta * (u[q] - uinf[q]);
+                            }
+                        }
                         const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
                         e_tile += uu;
                         m_acc = fmax(m_acc, uu);
@@ -981,10 +1009,10 @@ template <typename T> int x_grid(const Geom& g)
     const int R = sq_radix<T>(g);
     if (R == 16) {
         ntiles = ceil_div(g.nz * g.ny, sq_rows<16>());
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_xpass_sq<T, 16>, 192, sq_smem<T, 16>(g));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_xpass_sq<T, 16, false>, 192, sq_smem<T, 16>(g));
     } else if (R == 8) {
         ntiles = ceil_div(g.nz * g.ny, sq_rows<8>());
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_xpass_sq<T, 8>, 192, sq_smem<T, 8>(g));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_xpass_sq<T, 8, false>, 192, sq_smem<T, 8>(g));
     } else {
         const int lg = x_lgrb<T>(g);
         ntiles = ceil_div(g.nz * g.ny, 1 << lg);
@@ -1008,12 +1036,17 @@ cudaError_t launch_x(int mode, void* W, const Geom& g, const FftPlan& plan, cons
     if (kThreadsX % (NF * RB) != 0) return cudaErrorInvalidValue;
     const size_t smem = x_smem<T>(g, lg, NF);
     cplx<T>* w = (cplx<T>*)W;
+    const bool layer = ex.layer0[0] < g.nx || ex.layer0[1] < g.ny || ex.layer0[2] < g.nz;
     switch (mode) {
     case XP_PHYS:
-        if (sq_radix<T>(g) == 16)
-            k_xpass_sq<T, 16><<<x_grid<T>(g), 192, sq_smem<T, 16>(g), s>>>(w, g, tw, ex, st);
+        if (sq_radix<T>(g) == 16 && layer)
+            k_xpass_sq<T, 16, true><<<x_grid<T>(g), 192, sq_smem<T, 16>(g), s>>>(w, g, tw, ex, st);
+        else if (sq_radix<T>(g) == 16)
+            k_xpass_sq<T, 16, false><<<x_grid<T>(g), 192, sq_smem<T, 16>(g), s>>>(w, g, tw, ex, st);
+        else if (sq_radix<T>(g) == 8 && layer)
+            k_xpass_sq<T, 8, true><<<x_grid<T>(g), 192, sq_smem<T, 8>(g), s>>>(w, g, tw, ex, st);
         else if (sq_radix<T>(g) == 8)
-            k_xpass_sq<T, 8><<<x_grid<T>(g), 192, sq_smem<T, 8>(g), s>>>(w, g, tw, ex, st);
+            k_xpass_sq<T, 8, false><<<x_grid<T>(g), 192, sq_smem<T, 8>(g), s>>>(w, g, tw, ex, st);
         else
             k_xpass<T, XP_PHYS><<<x_grid<T>(g), kThreadsX, smem, s>>>(w, g, plan, tw, pos, ex, lg, st);
         break;
@@ -1022,6 +1055,9 @@ cudaError_t launch_x(int mode, void* W, const Geom& g, const FftPlan& plan, cons
         break;
     case XP_C2R:
         k_xpass<T, XP_C2R><<<ntiles, kThreadsX, smem, s>>>(w, g, plan, tw, pos, ex, lg, st);
+        break;
+    case XP_SPONGE:
+        k_xpass<T, XP_SPONGE><<<ntiles, kThreadsX, smem, s>>>(w, g, plan, tw, pos, ex, lg, st);
         break;
     default:
         k_xpass<T, XP_DUMP><<<ntiles, kThreadsX, smem, s>>>(w, g, plan, tw, pos, ex, lg, st);
@@ -1052,14 +1088,20 @@ cudaError_t configure_xpass()
     FLUSI_SMEM((k_xpass<float, XP_R2C>))
     FLUSI_SMEM((k_xpass<float, XP_C2R>))
     FLUSI_SMEM((k_xpass<float, XP_DUMP>))
+    FLUSI_SMEM((k_xpass<float, XP_SPONGE>))
+    FLUSI_SMEM((k_xpass<double, XP_SPONGE>))
     FLUSI_SMEM((k_xpass<double, XP_PHYS>))
     FLUSI_SMEM((k_xpass<double, XP_R2C>))
     FLUSI_SMEM((k_xpass<double, XP_C2R>))
     FLUSI_SMEM((k_xpass<double, XP_DUMP>))
-    FLUSI_SMEM((k_xpass_sq<float, 16>))
-    FLUSI_SMEM((k_xpass_sq<float, 8>))
-    FLUSI_SMEM((k_xpass_sq<double, 16>))
-    FLUSI_SMEM((k_xpass_sq<double, 8>))
+    FLUSI_SMEM((k_xpass_sq<float, 16, false>))
+    FLUSI_SMEM((k_xpass_sq<float, 8, false>))
+    FLUSI_SMEM((k_xpass_sq<double, 16, false>))
+    FLUSI_SMEM((k_xpass_sq<double, 8, false>))
+    FLUSI_SMEM((k_xpass_sq<float, 16, true>))
+    FLUSI_SMEM((k_xpass_sq<float, 8, true>))
+    FLUSI_SMEM((k_xpass_sq<double, 16, true>))
+    FLUSI_SMEM((k_xpass_sq<double, 8, true>))
 #undef FLUSI_SMEM
     return cudaSuccess;
 }

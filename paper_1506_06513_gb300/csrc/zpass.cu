@@ -129,12 +129,12 @@ k_zinv(const cplx<T>* __restrict__ U, cplx<T>* __restrict__ W, Geom g, FftPlan p
 
 // Forward z transform of one component of a column tile: TX consecutive
 // columns q of W[c] (A form, all nz rows) in by 16-byte asynchronous copies,
-// the kept modes jz (2/3 rule) out to Nh[c] in the state layout [Mz][My][Mxp].
+// the kept modes jz (2/3 rule) back into rows jz < Mz of the same columns
+// (in place: a tile reads all of its rows before its first barrier).
 template <typename T>
 __global__ void __launch_bounds__(kThreadsInv)
-k_zfwd(const cplx<T>* __restrict__ W, cplx<T>* __restrict__ Nh, Geom g, FftPlan plan,
-       const double2* __restrict__ tw, const int* __restrict__ pos, int lgTX,
-       const StepState* __restrict__ st)
+k_zfwd(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict__ tw,
+       const int* __restrict__ pos, int lgTX, const StepState* __restrict__ st)
 {
     if (st && st->status != 0) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -170,23 +170,26 @@ k_zfwd(const cplx<T>* __restrict__ W, cplx<T>* __restrict__ Nh, Geom g, FftPlan 
     constexpr int V = 2;                       // adjacent columns per thread
     const int q = q0 + (threadIdx.x % (TX / V)) * V;
     const bool qok = q < Q;                    // Q is a multiple of 4
-    cplx<T>* out = Nh + (size_t)c * Mz * Q + (qok ? q : 0);
+    cplx<T>* out = W + (size_t)c * nz * Wplane + (qok ? q : 0);
     auto store = [&](int f, const cplx<T>* v) {   // keep modes |m| <= Kz only
         const int jz = f <= Kz ? f : (f >= nz - Kz ? f - nz + Mz : -1);
-        if (qok && jz >= 0) st_row<T, V>(out + (size_t)jz * Q, v);
+        if (qok && jz >= 0) st_row<T, V>(out + (size_t)jz * Wplane, v);
     };
     fft_dif_out<T, false, V>(buf, TX, TX, plan, tws, sinv, store);
 }
 
 // Pointwise spectral update over the kept modes, VEC adjacent columns per
-// thread: N = Nh / N_points, Leray projection N <- N - k (k.N)/|k|^2, then
+// thread: N = N^ / N_points (the kept modes that k_zfwd left in rows jz of
+// W[0..2]); with a sponge, N += -(i k x V^)/(C_sp |k|^2) with V^ the kept
+// modes of chi_sp omega in W[3..5] (Sec. 2.3, read as a damping of the
+// vorticity, zero at k = 0); Leray projection N <- N - k (k.N)/|k|^2, then
 //   mode 0: IF-AB2  u^{n+1} = E1 (u^n + c_now N) - c_old E2 N^{n-1},  N^{n-1} <- N
 //   mode 1: u_hat = N (the initial condition), history cleared.
 // The mean (k = 0) is held at u_inf unless it is free.  Row padding x >= Mx
 // is never written (it is zero from the workspace reset on).
-template <typename T, int MODE>
+template <typename T, int MODE, bool SPONGE>
 __global__ void __launch_bounds__(256)
-k_zupdate(const cplx<T>* __restrict__ Nh, cplx<T>* __restrict__ U, cplx<T>* __restrict__ H, Geom g,
+k_zupdate(const cplx<T>* __restrict__ Wn, cplx<T>* __restrict__ U, cplx<T>* __restrict__ H, Geom g,
           ZfwdExtra ex, const StepState* __restrict__ st)
 {
     if (st && st->status != 0) return;
@@ -195,6 +198,8 @@ k_zupdate(const cplx<T>* __restrict__ Nh, cplx<T>* __restrict__ U, cplx<T>* __re
     const int Q = g.My * g.Mxp;
     const size_t S = (size_t)g.Mz * Q;     // values per component
     const size_t groups = S / VEC;         // Mxp is a multiple of 4
+    const size_t Wplane = (size_t)g.ny * g.Mxp, Wfield = (size_t)g.nz * Wplane;
+    constexpr bool sponge = MODE == 0 && SPONGE;
     const T two_pi = T(6.283185307179586476925286766559);
     const T inv_n = T(1.0 / ((double)g.nx * g.ny * g.nz));
     double c_now = 0, c_old = 0;
@@ -217,13 +222,15 @@ k_zupdate(const cplx<T>* __restrict__ Nh, cplx<T>* __restrict__ U, cplx<T>* __re
         const int jz = (int)(o / Q), q = (int)(o - (size_t)jz * Q);
         const int jy = q / g.Mxp, x0 = q - jy * g.Mxp;
         if (x0 >= g.Mx) continue;
-        cplx<T> n[3][VEC], u[3][VEC], h[3][VEC];
+        cplx<T> n[3][VEC], u[3][VEC], h[3][VEC], sv[3][VEC];
+        const size_t on = (size_t)jz * Wplane + q;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const size_t oc = c * S + o;
 #pragma unroll
             for (int v = 0; v < VEC; ++v) {
-                n[c][v] = Nh[oc + v];
+                n[c][v] = Wn[c * Wfield + on + v];
+                sv[c][v] = sponge ? Wn[(3 + c) * Wfield + on + v] : mkc<T>(0, 0);
                 u[c][v] = mkc<T>(0, 0);
                 h[c][v] = mkc<T>(0, 0);
                 if (MODE == 0) u[c][v] = U[oc + v];
@@ -241,6 +248,21 @@ k_zupdate(const cplx<T>* __restrict__ Nh, cplx<T>* __restrict__ U, cplx<T>* __re
             for (int c = 0; c < 3; ++c) N[c] = cscale(n[c][v], inv_n);
             const T kx = two_pi * T(x) / T(g.Lx);
             const bool zero_mode = (x == 0 && jy == 0 && jz == 0);
+            if (sponge && !zero_mode) {
+                // -(i k x V)/(C_sp |k|^2): real part Im(k x V)/(C k^2), imaginary -Re(k x V)/(C k^2)
+                cplx<T> Vs[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) Vs[c] = cscale(sv[c][v], inv_n);
+                const T f = T(1) / (T(ex.sponge_c) * (kx * kx + ky * ky + kz * kz));
+                const cplx<T> cr[3] = {csub(cscale(Vs[2], ky), cscale(Vs[1], kz)),
+                                       csub(cscale(Vs[0], kz), cscale(Vs[2], kx)),
+                                       csub(cscale(Vs[1], kx), cscale(Vs[0], ky))};
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    N[c].x += f * cr[c].y;
+                    N[c].y -= f * cr[c].x;
+                }
+            }
             if (!zero_mode) {
                 const T inv_k2 = T(1) / (kx * kx + ky * ky + kz * kz);
                 const T kNr = (kx * N[0].x + ky * N[1].x + kz * N[2].x) * inv_k2;
@@ -302,15 +324,14 @@ cudaError_t launch_zi(const void* U, void* W, const Geom& g, const FftPlan& plan
 }
 
 template <typename T>
-cudaError_t launch_zf(const void* W, void* Nh, const Geom& g, const FftPlan& plan, const double2* tw,
+cudaError_t launch_zf(void* W, int nf, const Geom& g, const FftPlan& plan, const double2* tw,
                       const int* pos, const StepState* st, cudaStream_t s)
 {
     const int TX = zinv_tx<T>(g);
-    if (g.nz * TX > cap_zi<T>() || kThreadsInv % TX != 0) return cudaErrorInvalidValue;
-    const int blocks = 3 * ceil_div(g.My * g.Mxp, TX);
+    if (g.nz * TX > cap_zi<T>() || kThreadsInv % TX != 0 || nf < 1 || nf > 6) return cudaErrorInvalidValue;
+    const int blocks = nf * ceil_div(g.My * g.Mxp, TX);
     const size_t smem = sizeof(cplx<T>) * ((size_t)g.nz + (size_t)g.nz * TX) + sizeof(int) * g.nz;
-    k_zfwd<T><<<blocks, kThreadsInv, smem, s>>>((const cplx<T>*)W, (cplx<T>*)Nh, g, plan, tw, pos,
-                                                __builtin_ctz(TX), st);
+    k_zfwd<T><<<blocks, kThreadsInv, smem, s>>>((cplx<T>*)W, g, plan, tw, pos, __builtin_ctz(TX), st);
     return cudaGetLastError();
 }
 
@@ -321,10 +342,13 @@ cudaError_t launch_zu(int mode, const void* Nh, void* U, void* H, const Geom& g,
     constexpr int VEC = 16 / sizeof(cplx<T>);
     const size_t groups = (size_t)g.Mz * g.My * g.Mxp / VEC;
     const int blocks = (int)std::min<size_t>(ceil_div_sz(groups, 256), (size_t)152 * 64);
-    if (mode == 0)
-        k_zupdate<T, 0><<<blocks, 256, 0, s>>>((const cplx<T>*)Nh, (cplx<T>*)U, (cplx<T>*)H, g, ex, st);
+    const cplx<T>* n = (const cplx<T>*)Nh;
+    if (mode == 0 && ex.sponge_c > 0)
+        k_zupdate<T, 0, true><<<blocks, 256, 0, s>>>(n, (cplx<T>*)U, (cplx<T>*)H, g, ex, st);
+    else if (mode == 0)
+        k_zupdate<T, 0, false><<<blocks, 256, 0, s>>>(n, (cplx<T>*)U, (cplx<T>*)H, g, ex, st);
     else
-        k_zupdate<T, 1><<<blocks, 256, 0, s>>>((const cplx<T>*)Nh, (cplx<T>*)U, (cplx<T>*)H, g, ex, st);
+        k_zupdate<T, 1, false><<<blocks, 256, 0, s>>>(n, (cplx<T>*)U, (cplx<T>*)H, g, ex, st);
     return cudaGetLastError();
 }
 
@@ -338,18 +362,18 @@ cudaError_t launch_zinv(int fp64, const void* U, void* W, const Geom& g, const F
                 : launch_zi<float>(U, W, g, plan, tw, pos, nf, st, s);
 }
 
-cudaError_t launch_zfwd(int fp64, const void* W, void* Nh, const Geom& g, const FftPlan& plan,
+cudaError_t launch_zfwd(int fp64, void* W, int nf, const Geom& g, const FftPlan& plan,
                         const double2* tw, const int* pos, const StepState* st, cudaStream_t s)
 {
-    return fp64 ? launch_zf<double>(W, Nh, g, plan, tw, pos, st, s)
-                : launch_zf<float>(W, Nh, g, plan, tw, pos, st, s);
+    return fp64 ? launch_zf<double>(W, nf, g, plan, tw, pos, st, s)
+                : launch_zf<float>(W, nf, g, plan, tw, pos, st, s);
 }
 
-cudaError_t launch_zupdate(int fp64, int mode, const void* Nh, void* U, void* H, const Geom& g,
+cudaError_t launch_zupdate(int fp64, int mode, const void* W, void* U, void* H, const Geom& g,
                            const ZfwdExtra& ex, const StepState* st, cudaStream_t s)
 {
-    return fp64 ? launch_zu<double>(mode, Nh, U, H, g, ex, st, s)
-                : launch_zu<float>(mode, Nh, U, H, g, ex, st, s);
+    return fp64 ? launch_zu<double>(mode, W, U, H, g, ex, st, s)
+                : launch_zu<float>(mode, W, U, H, g, ex, st, s);
 }
 
 cudaError_t configure_zpass()

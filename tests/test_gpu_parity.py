@@ -355,3 +355,39 @@ def test_square_half_length_x_pass(fl, name, prec):
     tol_u, tol_f = (1e-11, 1e-9) if prec == "fp64" else (2e-5, 1e-4)
     assert rel_l2(u, ref.get_state()) <= tol_u
     assert rows_err(rows, ref_rows) <= tol_f
+
+
+WAKE = {"generic_48x36x24": ((48, 36, 24), (4.0, 3.0, 2.0)),
+        "square_512x16x12": ((512, 16, 12), (8.0, 1.0, 0.75)),
+        "square_128x24x16": ((128, 24, 16), (4.0, 0.75, 0.5))}
+
+
+@pytest.mark.parametrize("name", sorted(WAKE))
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_sponge_and_dirichlet_layer(fl, name, prec):
+    """Vorticity sponge and Dirichlet inflow layer (Sec. 2.3) with a sphere and
+    a mean flow: physical fields at t = 0 and 5 full steps against the oracle,
+    on the generic x pass and on both square ones."""
+    n, L = WAKE[name]
+    cfg = {"n": n, "L": L, "nu": 0.01, "eta": 1e-2, "cfl": 0.1, "mean_mode": "fixed",
+           "u_inf": (0.3, 0.0, 0.0), "sponge_c": 0.1,
+           "sponge_width": (L[0] / 6, L[1] / 8, 0.0), "layer_width": (L[0] / 16, 0.0, L[2] / 8)}
+    ins = workloads.sphere((L[0] / 2, L[1] / 2, L[2] / 2), 0.3 * min(L[1], L[2]), profile="cos")
+    u0 = workloads.random_smooth_field(n, 9, mean=(0.3, 0.0, 0.0))
+    sim = fl.Solver(cfg, ins, precision=prec)
+    sim.set_state(u0)
+    ref = oracle.Simulation(cfg, ins)
+    ref.set_state(u0)
+    got = sim.debug_fields().double().cpu().numpy()
+    exp = oracle.Spectral(cfg).physical_fields(ref.uh, 0.0, ins)
+    tol_f = 1e-11 if prec == "fp64" else 2e-5
+    assert rel_l2(got[11:14], exp[11:14]) <= tol_f
+    assert fl.flusi_kernels_per_step(sim.h) == 9
+    sim.step(5)
+    rows, _ = sim.forces()
+    u = sim.get_state()[0]
+    sim.close()
+    ref_rows = ref.step(5)
+    tol_u, tol_r = (1e-11, 1e-9) if prec == "fp64" else (3e-5, 1e-4)
+    assert rel_l2(u, ref.get_state()) <= tol_u
+    assert rows_err(rows, ref_rows) <= tol_r
