@@ -47,6 +47,9 @@ def parse():
                     help="model insect in uniform inflow plus waves (512^3 by default), or the "
                          "model insect in seeded isotropic turbulent inflow (1024^3 by default)")
     ap.add_argument("--grid", type=int, default=None)
+    ap.add_argument("--wake", action="store_true",
+                    help="add the wake-removal terms: a vorticity sponge (C_sp 0.1) 32 grid "
+                         "points deep at the x and y ends and a Dirichlet layer 4 points deep at the x end")
     ap.add_argument("--shape", default=None,
                     help="nx,ny,nz: a reduced grid of the same box and insect (profiling)")
     ap.add_argument("--fp64-steps", type=int, default=10)
@@ -85,26 +88,32 @@ def spectral_sizes(n):
     return Mx, My, Mz
 
 
-def kernel_bytes(n, s):
+def kernel_bytes(n, s, wake=False):
     """Algorithmic bytes per launch of each kernel: every input it must read
     and every output it must write once, complex values of 2s bytes over the
-    kept modes (x: Mx of nx/2+1; y: My of ny; z: Mz of nz)."""
+    kept modes (x: Mx of nx/2+1; y: My of ny; z: Mz of nz).  With the wake
+    terms the vorticity makes a second x round trip and three more fields
+    go through the forward y and z passes and the update."""
     nx, ny, nz = n
     Mx, My, Mz = spectral_sizes(n)
     c = 2 * s
     A = nz * My * Mx * c          # one field after the z transform
     B = nz * ny * Mx * c          # one field after the y transform
     S = Mz * My * Mx * c          # one state field
-    return {
+    f = 6 if wake else 3          # fields of the forward y and z passes
+    out = {
         "zinv_curl": 3 * S + 6 * A,
         "yinv": 6 * A + 6 * B,
         "xpass_phys": 6 * B + 3 * B,
-        "yfwd": 3 * B + 3 * A,
-        "zfwd": 3 * A + 3 * S,
-        "update": 3 * S + 2 * 3 * S + 2 * 3 * S,
+        "yfwd": f * B + f * A,
+        "zfwd": f * A + f * S,
+        "update": f * S + 2 * 3 * S + 2 * 3 * S,
         "kinematics": 0,
         "scalars": 0,
     }
+    if wake:
+        out["sponge_x"] = 3 * B + 3 * B
+    return out
 
 
 def stage_model_bytes(n, s):
@@ -126,6 +135,10 @@ def workload_setup(args):
         shape = tuple(int(v) for v in args.shape.split(","))
         cfg = dict(cfg, n=shape)
         ins = workloads.model_insect(cfg["L"], shape)
+    if args.wake:
+        d = [cfg["L"][i] / cfg["n"][i] for i in range(3)]
+        cfg = dict(cfg, sponge_c=0.1, sponge_width=(32 * d[0], 32 * d[1], 0.0),
+                   layer_width=(4 * d[0], 0.0, 0.0))
     return cfg, ins
 
 
@@ -302,7 +315,7 @@ def run_flusi(args):
 
     # ---- per-kernel durations (CUDA events on the solver stream)
     prof = sim.profile(10)
-    kb = kernel_bytes(cfg["n"], 4)
+    kb = kernel_bytes(cfg["n"], 4, wake=args.wake)
     dom = max(prof, key=prof.get)
     ach = kb[dom] / (prof[dom] * 1e-3) / 1e9
     traffic = None
@@ -387,7 +400,7 @@ def run_flusi(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": workload_config(cfg["n"], world, args.workload),
+        "config": workload_config(cfg["n"], world, args.workload, args.wake),
         "roofline": roofline,
         "stage_model": {"bytes_per_step": stage, "frac_of_peak": round(stage / (ms_per_step * 1e-3) / 1e9 / hbm, 4),
                         "frac_of_nominal_8TBs": round(stage / (ms_per_step * 1e-3) / 8e12, 4),
@@ -417,9 +430,9 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
-def workload_config(n, world, workload="model_insect"):
+def workload_config(n, world, workload="model_insect", wake=False):
     """The `config` object of both arms: the workload as the GPU arm runs it."""
-    step_bytes = sum(kernel_bytes(n, 4).values())
+    step_bytes = sum(kernel_bytes(n, 4, wake).values())
     insect = ("ellipsoid body (0.5, 0.12) + 2 flapping plates (c 0.3, R 1, 4dx thick, "
               "phi 60deg sin, alpha 45deg cos)")
     if workload == "turbulent_insect":
@@ -431,6 +444,9 @@ def workload_config(n, world, workload="model_insect"):
         what = (f"model insect {'x'.join(map(str, n))} FP32: {insect}, Re 300, u_inf (0.25,0,0), "
                 "C_eta 1e-3, CFL 0.1 adaptive dt")
         init = "inflow + band-limited divergence-free waves"
+    if wake:
+        what += ("; vorticity sponge C_sp 0.1, 32 points deep at the x and y ends, Dirichlet layer "
+                 "4 points deep at the x end")
     return {"workload": what, "grid": list(n), "box": [4.0, 4.0, 4.0], "precision": "fp32",
             "initial": init,
             "l2": f"inputs larger than L2: {step_bytes / 1e9:.1f} GB moved per step",
@@ -474,7 +490,7 @@ def run_reference(args):
            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "impl": "reference",
-           "config": workload_config(workload_setup(args)[0]["n"], world, args.workload),
+           "config": workload_config(workload_setup(args)[0]["n"], world, args.workload, args.wake),
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                             "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

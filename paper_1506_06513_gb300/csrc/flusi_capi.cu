@@ -234,7 +234,11 @@ constexpr int kSpongeSlot = 5;
 
 bool has_sponge(flusi_t h) { return h->opt.sponge_c > 0; }
 
-int step_kernels(flusi_t h) { return has_sponge(h) ? kMaxStepKernels : kMaxStepKernels - 1; }
+// The square x pass forms chi_sp omega itself; other grids take a separate
+// x round trip of the vorticity.
+bool sponge_kernel(flusi_t h) { return has_sponge(h) && !xpass_fuses_sponge(h->prec == FLUSI_FP64, h->g); }
+
+int step_kernels(flusi_t h) { return sponge_kernel(h) ? kMaxStepKernels : kMaxStepKernels - 1; }
 
 ZfwdExtra zextra(flusi_t h)
 {
@@ -311,6 +315,7 @@ cudaError_t enqueue_step(flusi_t h, cudaStream_t s, cudaEvent_t* ev)
     xe.part = at<double>(h, h->opart);
     xe.comp0 = 0;
     set_wake(h, xe);
+    xe.sponge_fused = has_sponge(h) && !sponge_kernel(h);
     if ((e = launch_xpass(fp64, XP_PHYS, W, g, h->px, tx, at<int>(h, h->opx), xe, st, s))) return e;
     mark();
     if (branch) {
@@ -324,7 +329,7 @@ cudaError_t enqueue_step(flusi_t h, cudaStream_t s, cudaEvent_t* ev)
     if (branch && (e = cudaEventRecord(h->ev_sc, sk))) return e;
     mark();
     const int nfwd = has_sponge(h) ? 6 : 3;
-    if (has_sponge(h)) {
+    if (sponge_kernel(h)) {
         // chi_sp omega of the vorticity still in W[3..5] (x transformed back in place)
         XExtra xs{};
         xs.ncomp = 3;
@@ -761,7 +766,7 @@ int flusi_profile_step(flusi_t h, int n, double* ms, const char** names, int* nk
     }
     for (auto& e : ev) cudaEventDestroy(e);
     for (int k = 0, slot = 0; k < nk_step; ++k, ++slot) {
-        if (slot == kSpongeSlot && !has_sponge(h)) ++slot;
+        if (slot == kSpongeSlot && !sponge_kernel(h)) ++slot;
         ms[k] = acc[k] / n;
         if (names) names[k] = kKernelNames[slot];
     }

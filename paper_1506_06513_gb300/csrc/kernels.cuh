@@ -67,9 +67,11 @@ struct XExtra {
     // Sec. 2.3 wake removal: first grid index of each axis' end slab (the
     // axis length when there is none)
     int layer0[3];           // XP_PHYS / XP_DUMP: Dirichlet layer u = u_inf
-    int sponge0[3];          // XP_SPONGE: vorticity sponge region
+    int sponge0[3];          // XP_SPONGE, or XP_PHYS with sponge_fused: sponge region
+    int sponge_fused;        // XP_PHYS: also form chi_sp omega and x-transform it into W[3..5]
     double u_inf[3];
 };
+int xpass_fuses_sponge(int fp64, const Geom& g);
 int xpass_grid(int fp64, const Geom& g);   // CTAs of the persistent physical pass
 cudaError_t launch_xpass(int fp64, int mode, void* W, const Geom& g, const FftPlan& plan,
                          const double2* tw, const int* pos, const XExtra& ex, const StepState* st,

@@ -634,7 +634,7 @@ __device__ __forceinline__ void sq_exchange_pre(cplx<T>* x, int j, int width, co
     }
 }
 
-template <typename T, int R, bool LAYER>
+template <typename T, int R, bool LAYER, bool SPONGE>
 __global__ void __launch_bounds__(192, sizeof(T) == 4 ? 3 : 1)
 k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExtra ex,
            const StepState* __restrict__ st)
@@ -782,6 +782,16 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
                         uv[q] = buf[(q * RB + rr) * CS + slot];
                         wv[q] = buf[((3 + q) * RB + rr) * CS + slot];
                     }
+                    if (SPONGE) {   // chi_sp omega (Sec. 2.3) into the sponge lines
+                        const int r = row0 + rr, z = r / g.ny, y = r - z * g.ny;
+                        const int pp = lrow / R + R * (lrow % R);
+                        const bool in_row = y >= ex.sponge0[1] || z >= ex.sponge0[2];
+                        const T s0 = (in_row || 2 * pp >= ex.sponge0[0]) ? T(1) : T(0);
+                        const T s1 = (in_row || 2 * pp + 1 >= ex.sponge0[0]) ? T(1) : T(0);
+#pragma unroll
+                        for (int q = 0; q < 3; ++q)
+                            buf[((6 + q) * RB + rr) * CS + slot] = mkc<T>(s0 * wv[q].x, s1 * wv[q].y);
+                    }
                     T nl[2][3];
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
@@ -888,11 +898,13 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
         }
         __syncthreads();
 
-        // ---- forward on the three NL lines of each row (one per lane group):
+        // ---- forward on the three NL lines of each row (one per lane group) and,
+        //      with the sponge, the three chi_sp omega lines (a second one):
         //      DIT stage 1, stage 0, r2c post-processing and store
-        {
-            cplx<T>* line = buf + (3 * RB + c) * CS;
-            const int fld = c / RB, lrr = c % RB;
+#pragma unroll 1
+        for (int li = 0; li < (SPONGE ? 2 : 1); ++li) {
+            cplx<T>* line = buf + (3 * RB + c + li * NG) * CS;
+            const int fld = 3 * li + c / RB, lrr = c % RB;
 #pragma unroll
             for (int i = 0; i < R; ++i) v[i] = line[R * j + i + j];
             Dft<T, R, false>::run(v);
@@ -962,12 +974,27 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
     }
 }
 
-template <typename T, int R> size_t sq_smem(const Geom& g)
+template <typename T, int R> size_t sq_smem(const Geom& g, bool sponge = false)
 {
     const int RB = sq_rows<R>(), NH = R * R;
     size_t s = sizeof(double) * kWarpsX * 36 + ((sizeof(FrameT<T>) + 15) / 16) * 16;
-    s += sizeof(cplx<T>) * ((size_t)g.nx + NH + (size_t)6 * RB * (NH + R));
+    s += sizeof(cplx<T>) * ((size_t)g.nx + NH + (size_t)(sponge ? 9 : 6) * RB * (NH + R));
     return s;
+}
+
+template <typename T, int R>
+void launch_sq(bool layer, bool sponge, cplx<T>* w, const Geom& g, const double2* tw, const XExtra& ex,
+               const StepState* st, cudaStream_t s, int grid)
+{
+    const size_t smem = sq_smem<T, R>(g, sponge);
+    if (layer && sponge)
+        k_xpass_sq<T, R, true, true><<<grid, 192, smem, s>>>(w, g, tw, ex, st);
+    else if (layer)
+        k_xpass_sq<T, R, true, false><<<grid, 192, smem, s>>>(w, g, tw, ex, st);
+    else if (sponge)
+        k_xpass_sq<T, R, false, true><<<grid, 192, smem, s>>>(w, g, tw, ex, st);
+    else
+        k_xpass_sq<T, R, false, false><<<grid, 192, smem, s>>>(w, g, tw, ex, st);
 }
 
 // radix of the square half-length kernel for this grid, or 0 for the generic one
@@ -1009,10 +1036,10 @@ template <typename T> int x_grid(const Geom& g)
     const int R = sq_radix<T>(g);
     if (R == 16) {
         ntiles = ceil_div(g.nz * g.ny, sq_rows<16>());
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_xpass_sq<T, 16, false>, 192, sq_smem<T, 16>(g));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_xpass_sq<T, 16, false, false>, 192, sq_smem<T, 16>(g));
     } else if (R == 8) {
         ntiles = ceil_div(g.nz * g.ny, sq_rows<8>());
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_xpass_sq<T, 8, false>, 192, sq_smem<T, 8>(g));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_xpass_sq<T, 8, false, false>, 192, sq_smem<T, 8>(g));
     } else {
         const int lg = x_lgrb<T>(g);
         ntiles = ceil_div(g.nz * g.ny, 1 << lg);
@@ -1037,16 +1064,13 @@ cudaError_t launch_x(int mode, void* W, const Geom& g, const FftPlan& plan, cons
     const size_t smem = x_smem<T>(g, lg, NF);
     cplx<T>* w = (cplx<T>*)W;
     const bool layer = ex.layer0[0] < g.nx || ex.layer0[1] < g.ny || ex.layer0[2] < g.nz;
+    const bool sponge = ex.sponge_fused != 0;
     switch (mode) {
     case XP_PHYS:
-        if (sq_radix<T>(g) == 16 && layer)
-            k_xpass_sq<T, 16, true><<<x_grid<T>(g), 192, sq_smem<T, 16>(g), s>>>(w, g, tw, ex, st);
-        else if (sq_radix<T>(g) == 16)
-            k_xpass_sq<T, 16, false><<<x_grid<T>(g), 192, sq_smem<T, 16>(g), s>>>(w, g, tw, ex, st);
-        else if (sq_radix<T>(g) == 8 && layer)
-            k_xpass_sq<T, 8, true><<<x_grid<T>(g), 192, sq_smem<T, 8>(g), s>>>(w, g, tw, ex, st);
+        if (sq_radix<T>(g) == 16)
+            launch_sq<T, 16>(layer, sponge, w, g, tw, ex, st, s, x_grid<T>(g));
         else if (sq_radix<T>(g) == 8)
-            k_xpass_sq<T, 8, false><<<x_grid<T>(g), 192, sq_smem<T, 8>(g), s>>>(w, g, tw, ex, st);
+            launch_sq<T, 8>(layer, sponge, w, g, tw, ex, st, s, x_grid<T>(g));
         else
             k_xpass<T, XP_PHYS><<<x_grid<T>(g), kThreadsX, smem, s>>>(w, g, plan, tw, pos, ex, lg, st);
         break;
@@ -1069,6 +1093,12 @@ cudaError_t launch_x(int mode, void* W, const Geom& g, const FftPlan& plan, cons
 }  // namespace
 
 int xpass_grid(int fp64, const Geom& g) { return fp64 ? x_grid<double>(g) : x_grid<float>(g); }
+
+// 1 when the physical x pass (square kernel) forms and transforms chi_sp omega itself
+int xpass_fuses_sponge(int fp64, const Geom& g)
+{
+    return fp64 ? sq_radix<double>(g) != 0 : sq_radix<float>(g) != 0;
+}
 
 cudaError_t launch_xpass(int fp64, int mode, void* W, const Geom& g, const FftPlan& plan,
                          const double2* tw, const int* pos, const XExtra& ex, const StepState* st,
@@ -1094,14 +1124,16 @@ cudaError_t configure_xpass()
     FLUSI_SMEM((k_xpass<double, XP_R2C>))
     FLUSI_SMEM((k_xpass<double, XP_C2R>))
     FLUSI_SMEM((k_xpass<double, XP_DUMP>))
-    FLUSI_SMEM((k_xpass_sq<float, 16, false>))
-    FLUSI_SMEM((k_xpass_sq<float, 8, false>))
-    FLUSI_SMEM((k_xpass_sq<double, 16, false>))
-    FLUSI_SMEM((k_xpass_sq<double, 8, false>))
-    FLUSI_SMEM((k_xpass_sq<float, 16, true>))
-    FLUSI_SMEM((k_xpass_sq<float, 8, true>))
-    FLUSI_SMEM((k_xpass_sq<double, 16, true>))
-    FLUSI_SMEM((k_xpass_sq<double, 8, true>))
+#define FLUSI_SMEM_SQ(T, R)                              \
+    FLUSI_SMEM((k_xpass_sq<T, R, false, false>))         \
+    FLUSI_SMEM((k_xpass_sq<T, R, true, false>))          \
+    FLUSI_SMEM((k_xpass_sq<T, R, false, true>))          \
+    FLUSI_SMEM((k_xpass_sq<T, R, true, true>))
+    FLUSI_SMEM_SQ(float, 16)
+    FLUSI_SMEM_SQ(float, 8)
+    FLUSI_SMEM_SQ(double, 16)
+    FLUSI_SMEM_SQ(double, 8)
+#undef FLUSI_SMEM_SQ
 #undef FLUSI_SMEM
     return cudaSuccess;
 }

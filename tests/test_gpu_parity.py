@@ -382,7 +382,7 @@ def test_sponge_and_dirichlet_layer(fl, name, prec):
     exp = oracle.Spectral(cfg).physical_fields(ref.uh, 0.0, ins)
     tol_f = 1e-11 if prec == "fp64" else 2e-5
     assert rel_l2(got[11:14], exp[11:14]) <= tol_f
-    assert fl.flusi_kernels_per_step(sim.h) == 9
+    assert fl.flusi_kernels_per_step(sim.h) == (8 if n[0] in (128, 512) else 9)
     sim.step(5)
     rows, _ = sim.forces()
     u = sim.get_state()[0]
