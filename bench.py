@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-yardstick", action="store_true",
+                    help="skip timing cuFFT on the step's nine 3-D transforms")
     ap.add_argument("--no-ensemble", action="store_true",
                     help="skip the 40-run uneven ensemble, batched against one by one")
     return ap.parse_args()
@@ -387,6 +389,14 @@ def run_flusi(args):
                 "kernels_ms": {k: round(v, 3) for k, v in prof64.items()}}
     del u0
 
+    yardstick = None
+    if not args.no_yardstick:
+        from paper_1506_06513_gb300.yardstick import run as run_yardstick
+        yardstick = run_yardstick(cfg["n"][0]) if len(set(cfg["n"])) == 1 else None
+        if yardstick:
+            yardstick["step_ms_over_cufft_ms"] = ms_per_step / yardstick["ms"]
+        torch.cuda.empty_cache()
+
     ensemble = None
     if not args.no_ensemble:
         from paper_1506_06513_gb300.ensemble import run as run_ensemble
@@ -409,6 +419,7 @@ def run_flusi(args):
         "kernels_ms": kernels,
         "fp64": fp64,
         "ensemble": ensemble,
+        "cufft_yardstick": yardstick,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": kps * args.steps,
