@@ -222,6 +222,27 @@ int flusi_penalization_sums_noalloc(int nx, int ny, int nz, const double L[3], d
                                     const flusi_insect *insect, double t, const double *u_dev,
                                     double *sums_out, void *cuda_stream);
 
+/* ---- Checkpoint and exact restart.  The paper writes flow fields to disk but
+ * describes no restart; an AB2 step depends on u_hat, the history N_hat^{n-1},
+ * t, dt_{n-1}, the step count and the previous solid integrals of the
+ * unsteady force correction (Eq. force_with_unst_corrections), and a
+ * checkpoint holds exactly those, in the handle's precision and internal
+ * layout (kept modes only), so a run restarted from it continues bit for bit.
+ * Options and kinematics are not stored: set them as they were.
+ *
+ * flusi_checkpoint_bytes: size of a checkpoint of this handle (no device work).
+ * flusi_save: write one into the caller's host buffer of `bytes` (at least that
+ *   size, else FLUSI_EINVAL); FLUSI_ESTATE without a state or on a poisoned
+ *   handle.  Synchronizes.
+ * flusi_load: restore one into a bound handle of the same grid, box, nu, eta,
+ *   precision and 2/3 rule (else FLUSI_EINVAL, checked before anything else);
+ *   replaces the state as flusi_set_state does.  Force rows from before the
+ *   save are not restored; the next drained row is the next step's.
+ *   Synchronizes. */
+int flusi_checkpoint_bytes(flusi_t h, size_t *bytes);
+int flusi_save(flusi_t h, void *host_buf, size_t bytes);
+int flusi_load(flusi_t h, const void *host_buf, size_t bytes);
+
 /* ---- Ensembles of independent runs (uneven grids, kinematics, Reynolds
  * numbers).  The paper runs one simulation at a time; this batches many small
  * ones into one CUDA graph per ensemble step so that their kernels fill the

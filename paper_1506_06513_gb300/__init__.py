@@ -80,6 +80,9 @@ def _load():
         "flusi_kernels_per_step": ([h, C.POINTER(C.c_int)], ip),
         "flusi_penalization_sums_noalloc": ([ip, ip, ip, dp, C.c_double, C.POINTER(Insect), C.c_double,
                                              vp, dp, vp], ip),
+        "flusi_checkpoint_bytes": ([h, C.POINTER(C.c_size_t)], ip),
+        "flusi_save": ([h, vp, C.c_size_t], ip),
+        "flusi_load": ([h, vp, C.c_size_t], ip),
         "flusi_ensemble_create": ([C.POINTER(h), ip, vp, C.POINTER(h)], ip),
         "flusi_ensemble_step": ([h, ip], ip),
         "flusi_ensemble_destroy": ([h], ip),
@@ -211,6 +214,24 @@ def flusi_penalization_sums_noalloc(n, L, eta, insect: Insect | None, t, u_dev: 
                                              C.c_void_p(stream))
     _check(None, rc)
     return out
+
+
+def flusi_checkpoint_bytes(h):
+    b = C.c_size_t()
+    _check(h, lib.flusi_checkpoint_bytes(h, C.byref(b)))
+    return b.value
+
+
+def flusi_save(h):
+    """The handle's checkpoint as a numpy uint8 array (see flusi.h)."""
+    buf = np.empty(flusi_checkpoint_bytes(h), np.uint8)
+    _check(h, lib.flusi_save(h, C.c_void_p(buf.ctypes.data), buf.nbytes))
+    return buf
+
+
+def flusi_load(h, buf: np.ndarray):
+    buf = np.ascontiguousarray(buf, np.uint8)
+    return _check(h, lib.flusi_load(h, C.c_void_p(buf.ctypes.data), buf.nbytes))
 
 
 def flusi_ensemble_create(handles, stream: int):
@@ -376,6 +397,13 @@ class Solver:
 
     def profile(self, n=3):
         return flusi_profile_step(self.h, n)
+
+    def save(self):
+        """Checkpoint for an exact restart (flusi_save)."""
+        return flusi_save(self.h)
+
+    def load(self, buf):
+        flusi_load(self.h, buf)
 
     def close(self):
         if self.h:

@@ -781,6 +781,106 @@ int flusi_kernels_per_step(flusi_t h, int* count)
     return FLUSI_OK;
 }
 
+// ---------------------------------------------------------------- checkpoints
+
+namespace {
+
+struct CkptHeader {
+    char magic[8];               // "FLUSICK1"
+    int prec, nx, ny, nz, Mx, My, Mz, Mxp;
+    int dealias_strict;
+    double L[3], nu, eta;
+    unsigned long long spec_bytes;  // one of U, H
+};
+
+size_t spec_bytes(flusi_t h)
+{
+    const size_t cs = h->prec == FLUSI_FP64 ? 16 : 8;
+    return (size_t)3 * h->g.Mz * h->g.My * h->g.Mxp * cs;
+}
+
+CkptHeader make_header(flusi_t h)
+{
+    CkptHeader c{};
+    std::memcpy(c.magic, "FLUSICK1", 8);
+    c.prec = h->prec;
+    c.nx = h->nx;
+    c.ny = h->ny;
+    c.nz = h->nz;
+    c.Mx = h->g.Mx;
+    c.My = h->g.My;
+    c.Mz = h->g.Mz;
+    c.Mxp = h->g.Mxp;
+    c.dealias_strict = h->opt.dealias_strict;
+    for (int i = 0; i < 3; ++i) c.L[i] = h->L[i];
+    c.nu = h->nu;
+    c.eta = h->eta;
+    c.spec_bytes = spec_bytes(h);
+    return c;
+}
+
+}  // namespace
+
+int flusi_checkpoint_bytes(flusi_t h, size_t* bytes)
+{
+    if (!h || !bytes) return fail(h, FLUSI_EINVAL, "NULL argument");
+    *bytes = sizeof(CkptHeader) + sizeof(StepState) + 2 * spec_bytes(h);
+    return FLUSI_OK;
+}
+
+int flusi_save(flusi_t h, void* host_buf, size_t bytes)
+{
+    size_t need = 0;
+    if (!h || !host_buf) return fail(h, FLUSI_EINVAL, "NULL argument");
+    flusi_checkpoint_bytes(h, &need);
+    if (bytes < need) return fail(h, FLUSI_EINVAL, "checkpoint buffer too small");
+    int rc = check_ready(h, true);
+    if (rc) return rc;
+    if (h->poisoned) return fail(h, FLUSI_ESTATE, "a device error poisoned the handle");
+    StepState st;
+    rc = read_status(h, &st);       // synchronizes; fails on a device error
+    if (rc) return rc;
+    char* p = static_cast<char*>(host_buf);
+    const CkptHeader hd = make_header(h);
+    std::memcpy(p, &hd, sizeof hd);
+    std::memcpy(p + sizeof hd, &st, sizeof st);
+    char* q = p + sizeof hd + sizeof st;
+    CK(cudaMemcpy(q, h->ws + h->oU, hd.spec_bytes, cudaMemcpyDeviceToHost), "save u_hat");
+    CK(cudaMemcpy(q + hd.spec_bytes, h->ws + h->oH, hd.spec_bytes, cudaMemcpyDeviceToHost), "save history");
+    return FLUSI_OK;
+}
+
+int flusi_load(flusi_t h, const void* host_buf, size_t bytes)
+{
+    size_t need = 0;
+    if (!h || !host_buf) return fail(h, FLUSI_EINVAL, "NULL argument");
+    flusi_checkpoint_bytes(h, &need);
+    if (bytes < need) return fail(h, FLUSI_EINVAL, "checkpoint buffer too small");
+    const char* p = static_cast<const char*>(host_buf);
+    CkptHeader hd, mine = make_header(h);
+    std::memcpy(&hd, p, sizeof hd);
+    if (std::memcmp(hd.magic, mine.magic, 8) != 0) return fail(h, FLUSI_EINVAL, "not a flusi checkpoint");
+    if (hd.prec != mine.prec || hd.nx != mine.nx || hd.ny != mine.ny || hd.nz != mine.nz ||
+        hd.Mx != mine.Mx || hd.My != mine.My || hd.Mz != mine.Mz || hd.Mxp != mine.Mxp ||
+        hd.dealias_strict != mine.dealias_strict || hd.nu != mine.nu || hd.eta != mine.eta ||
+        hd.L[0] != mine.L[0] || hd.L[1] != mine.L[1] || hd.L[2] != mine.L[2])
+        return fail(h, FLUSI_EINVAL, "checkpoint of another grid, box, nu, eta, precision or 2/3 rule");
+    int rc = check_ready(h, false);
+    if (rc) return rc;
+    StepState st;
+    std::memcpy(&st, p + sizeof hd, sizeof st);
+    if (st.status != 0 || st.n < 0) return fail(h, FLUSI_EINVAL, "checkpoint holds a failed or invalid state");
+    const char* q = p + sizeof hd + sizeof st;
+    CK(cudaStreamSynchronize(h->stream), "sync before load");
+    CK(cudaMemcpy(h->ws + h->ostate, &st, sizeof st, cudaMemcpyHostToDevice), "load step state");
+    CK(cudaMemcpy(h->ws + h->oU, q, hd.spec_bytes, cudaMemcpyHostToDevice), "load u_hat");
+    CK(cudaMemcpy(h->ws + h->oH, q + hd.spec_bytes, hd.spec_bytes, cudaMemcpyHostToDevice), "load history");
+    h->has_state = 1;
+    h->poisoned = 0;
+    h->rows_read = st.n;
+    return FLUSI_OK;
+}
+
 // ---------------------------------------------------------------- ensembles
 
 struct flusi_ensemble_s {
