@@ -48,7 +48,8 @@ class Params(C.Structure):
                 ("mean_mode", C.c_int), ("pad_", C.c_int),
                 ("u_inf", C.c_double * 3),
                 ("sponge_c", C.c_double), ("sponge_width", C.c_double * 3),
-                ("layer_width", C.c_double * 3)]
+                ("layer_width", C.c_double * 3),
+                ("time_scheme", C.c_int), ("pad2_", C.c_int)]
 
 
 _F = C.c_double * MAX_FOURIER
@@ -150,6 +151,7 @@ def make_params(cfg: dict) -> Params:
     p.sponge_c = cfg.get("sponge_c", 0.0)
     p.sponge_width[:] = cfg.get("sponge_width", (0.0, 0.0, 0.0))
     p.layer_width[:] = cfg.get("layer_width", (0.0, 0.0, 0.0))
+    p.time_scheme = {"ab2": 0, "rk4": 1}[cfg.get("time_scheme", "ab2")]
     return p
 
 

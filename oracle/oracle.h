@@ -46,6 +46,8 @@ typedef struct {
     double sponge_c;
     double sponge_width[3];
     double layer_width[3];
+    int time_scheme;     /* 0: integrating-factor AB2; 1: RK4, explicit diffusion */
+    int pad2_;
 } orc_params;
 
 typedef struct {
@@ -123,6 +125,9 @@ int orc_rhs(const orc_params *p, const orc_insect *ins, double t,
  * u x omega - chi/C_eta (u - u_s) (3) */
 void orc_physical_fields(const orc_params *p, const orc_insect *ins, double t,
                          const double complex *uh, double *fields);
+void orc_rk4_combine(const orc_params *p, double complex *uh, const double complex *k1,
+                     const double complex *k2, const double complex *k3,
+                     const double complex *k4, double dt);
 void orc_ab2_update(const orc_params *p, double complex *uh,
                     const double complex *nh, const double complex *nh_prev,
                     double dt, double dt_prev, int64_t n);

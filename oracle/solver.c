@@ -372,6 +372,46 @@ void orc_ab2_update(const orc_params *p, double complex *uh,
             }
 }
 
+/* RK4 with explicit diffusion (Sec. 2.4 names it as the alternative to
+ * IF-AB2): the classical four-stage combination
+ * u^{n+1} = u^n + dt/6 (k1 + 2 k2 + 2 k3 + k4). */
+void orc_rk4_combine(const orc_params *p, double complex *uh, const double complex *k1,
+                     const double complex *k2, const double complex *k3,
+                     const double complex *k4, double dt)
+{
+    long n = 3 * n_half(p);
+    for (long i = 0; i < n; ++i) uh[i] += dt / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
+}
+
+/* k = N_hat - nu |k|^2 u_hat: the right-hand side with the viscous term explicit. */
+static void add_viscous(const orc_params *p, const double complex *uh, double complex *k)
+{
+    int hx = p->nx / 2 + 1;
+    long nhs = n_half(p);
+    for (int iz = 0; iz < p->nz; ++iz)
+        for (int iy = 0; iy < p->ny; ++iy)
+            for (int ix = 0; ix < hx; ++ix) {
+                double kv[3];
+                wavevector(p, ix, iy, iz, kv);
+                double k2 = kv[0] * kv[0] + kv[1] * kv[1] + kv[2] * kv[2];
+                long i = ((long)iz * p->ny + iy) * hx + ix;
+                for (int c = 0; c < 3; ++c) k[c * nhs + i] -= p->nu * k2 * uh[c * nhs + i];
+            }
+}
+
+/* Largest |k|^2 over the retained modes (the explicit-diffusion limit of RK4). */
+static double k2_max(const orc_params *p)
+{
+    int K[3] = {cutoff(p->nx, p->dealias_strict), cutoff(p->ny, p->dealias_strict),
+                cutoff(p->nz, p->dealias_strict)};
+    double L[3] = {p->Lx, p->Ly, p->Lz}, k2 = 0;
+    for (int i = 0; i < 3; ++i) {
+        double k = 6.283185307179586476925286766559 * K[i] / L[i];
+        k2 += k * k;
+    }
+    return k2;
+}
+
 /* One step of Algorithm 1 (without free flight and output). */
 int orc_step(const orc_params *p, const orc_insect *ins, double complex *uh,
              double complex *nh_prev, orc_scalars *s, double *row)
@@ -385,7 +425,9 @@ int orc_step(const orc_params *p, const orc_insect *ins, double complex *uh,
         return 1;
     }
 
-    /* Algorithm 1 step (b): the time step */
+    /* Algorithm 1 step (b): the time step.  RK4 adds the explicit-diffusion
+     * limit dt <= 2.5 / (nu |k|^2_max) (a reading: inside the real-axis
+     * stability interval of RK4, about [-2.78, 0]). */
     double dt;
     if (p->dt_fixed > 0) {
         dt = p->dt_fixed;
@@ -397,9 +439,37 @@ int orc_step(const orc_params *p, const orc_insect *ins, double complex *uh,
         double umax = sums[ORC_SUM_UMAX];
         if (umax > 0 && p->cfl * dmin / umax < dt) dt = p->cfl * dmin / umax;
         if (p->dt_max > 0 && p->dt_max < dt) dt = p->dt_max;
+        if (p->time_scheme == 1 && p->nu > 0) {
+            double lim = 2.5 / (p->nu * k2_max(p));
+            if (lim < dt) dt = lim;
+        }
     }
 
-    orc_ab2_update(p, uh, nh, nh_prev, dt, s->dt_prev, s->n);
+    if (p->time_scheme == 1) {
+        /* stages at t, t + dt/2, t + dt/2, t + dt; the mask moves with them */
+        long n3 = 3 * nhs;
+        size_t bytes = sizeof(double complex) * (size_t)n3;
+        double complex *k[4], *us = malloc(bytes);
+        double stage_sums[ORC_NSUMS];
+        for (int q = 0; q < 4; ++q) k[q] = malloc(bytes);
+        memcpy(k[0], nh, bytes);
+        add_viscous(p, uh, k[0]);
+        const double frac[4] = {0.0, 0.5, 0.5, 1.0};
+        for (int q = 1; q < 4 && !bad; ++q) {
+            for (long i = 0; i < n3; ++i) us[i] = uh[i] + frac[q] * dt * k[q - 1][i];
+            bad = orc_rhs(p, ins, s->t + frac[q] * dt, us, k[q], stage_sums);
+            add_viscous(p, us, k[q]);
+        }
+        if (!bad) orc_rk4_combine(p, uh, k[0], k[1], k[2], k[3], dt);
+        for (int q = 0; q < 4; ++q) free(k[q]);
+        free(us);
+        if (bad) {
+            free(nh);
+            return 1;
+        }
+    } else {
+        orc_ab2_update(p, uh, nh, nh_prev, dt, s->dt_prev, s->n);
+    }
 
     row[0] = s->t;
     row[1] = dt;
