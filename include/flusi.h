@@ -82,6 +82,13 @@ typedef struct flusi_options {
     double sponge_c;
     double sponge_width[3];
     double layer_width[3];
+    /* Time scheme (Sec. 2.4): 0 = integrating-factor AB2 (default); 1 = RK4
+     * with explicit diffusion, four right-hand sides per step at t, t + dt/2,
+     * t + dt/2, t + dt, the mask moved to each, and the step further limited
+     * to dt <= 2.5/(nu |k|^2_max).  RK4 needs one more state-sized buffer, so
+     * it is fixed at flusi_bind.                                             */
+    int time_scheme;
+    int pad_;
 } flusi_options;
 
 /* Insect geometry and kinematics (Sec. 3).  Angles in radians.  Kinematic
@@ -180,8 +187,10 @@ int flusi_debug_fields(flusi_t h, void *out_dev);
 
 /* Diagnostic: time each kernel of one step with CUDA events on the bound
  * stream over n un-captured steps (which advance the state).  ms[i] gets the
- * mean duration of kernel i, names[i] its name; *nk the number of kernels
- * (at most 16).  Synchronizes. */
+ * mean duration of kernel i, names[i] its name (RK4 stages 2..4 carry a ".2",
+ * ".3", ".4" suffix); *nk the number of kernels (at most FLUSI_PROFILE_MAX;
+ * ms and names must hold that many).  Synchronizes. */
+#define FLUSI_PROFILE_MAX 40
 int flusi_profile_step(flusi_t h, int n, double *ms, const char **names, int *nk);
 
 /* Kernels launched per step (for launch accounting). */

@@ -20,6 +20,7 @@ FLUSI_FP64, FLUSI_FP32 = 0, 1
 FLUSI_HOST_FP64, FLUSI_HOST_FP32, FLUSI_DEVICE = 0, 1, 2
 MAX_FOURIER = 8
 FORCE_COLS = 22
+PROFILE_MAX = 40
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENONFINITE", "ETIMEOUT", "ESTATE"]
 
 
@@ -34,7 +35,8 @@ class Options(C.Structure):
                 ("u_inf", C.c_double * 3), ("mean_mode", C.c_int), ("dealias_strict", C.c_int),
                 ("force_ring", C.c_int), ("use_graph", C.c_int),
                 ("sponge_c", C.c_double), ("sponge_width", C.c_double * 3),
-                ("layer_width", C.c_double * 3)]
+                ("layer_width", C.c_double * 3),
+                ("time_scheme", C.c_int), ("pad_", C.c_int)]
 
 
 _F = C.c_double * MAX_FOURIER
@@ -185,8 +187,8 @@ def flusi_debug_fields(h, dev_ptr: int):
 
 
 def flusi_profile_step(h, n):
-    ms = (C.c_double * 16)()
-    names = (C.c_char_p * 16)()
+    ms = (C.c_double * PROFILE_MAX)()
+    names = (C.c_char_p * PROFILE_MAX)()
     nk = C.c_int()
     _check(h, lib.flusi_profile_step(h, int(n), ms, names, C.byref(nk)))
     return {names[i].decode(): ms[i] for i in range(nk.value)}
@@ -304,6 +306,7 @@ def make_options(cfg: dict) -> Options:
     o.sponge_c = cfg.get("sponge_c", 0.0)
     o.sponge_width[:] = cfg.get("sponge_width", (0.0, 0.0, 0.0))
     o.layer_width[:] = cfg.get("layer_width", (0.0, 0.0, 0.0))
+    o.time_scheme = {"ab2": 0, "rk4": 1}[cfg.get("time_scheme", "ab2")]
     return o
 
 

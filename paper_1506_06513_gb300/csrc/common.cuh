@@ -119,6 +119,7 @@ struct StepCoef {
     long long n;
     int first;
     int skip;                // 1 when the step is abandoned (status set)
+    double t0;               // time at the start of the step (RK stages)
 };
 
 __host__ __device__ inline int ceil_div(int a, int b) { return (a + b - 1) / b; }

@@ -30,7 +30,7 @@ struct flusi_s {
     size_t ws_bytes = 0;
     cudaStream_t stream = nullptr;
     int bound = 0;
-    size_t oU = 0, oH = 0, oW = 0, otx = 0, oty = 0, otz = 0, opx = 0, opy = 0, opz = 0,
+    size_t oU = 0, oH = 0, oUt = 0, oW = 0, otx = 0, oty = 0, otz = 0, opx = 0, opy = 0, opz = 0,
            oframe = 0, oins = 0, ostate = 0, ocoef = 0, oetab = 0, opart = 0, orows = 0, total = 0;
     int part_cap = 0, xgrid = 0;
     // run state
@@ -178,6 +178,7 @@ void layout(flusi_t h)
     size_t o = 0;
     h->oU = o; o = align256(o + spec);
     h->oH = o; o = align256(o + spec);
+    h->oUt = o; o = align256(o + (h->opt.time_scheme == 1 ? spec : 0));   // RK4 stage state
     h->oW = o; o = align256(o + work);
     h->otx = o; o = align256(o + sizeof(double2) * g.nx);
     h->oty = o; o = align256(o + sizeof(double2) * g.ny);
@@ -227,18 +228,40 @@ double box_margin(flusi_t h)
     return s.profile == 1 ? 1e300 : s.h;
 }
 
-const char* kKernelNames[] = {"kinematics", "zinv_curl", "yinv", "xpass_phys", "scalars", "sponge_x",
-                              "yfwd", "zfwd", "update"};
-constexpr int kMaxStepKernels = 9;
-constexpr int kSpongeSlot = 5;
+// Names of the kernels of a step, in launch order; RK4 stages 2..4 repeat the
+// right-hand-side kernels with a stage suffix.
+const char* kStageNames[4][8] = {
+    {"kinematics", "zinv_curl", "yinv", "xpass_phys", "sponge_x", "yfwd", "zfwd", "update"},
+    {"kinematics.2", "zinv_curl.2", "yinv.2", "xpass_phys.2", "sponge_x.2", "yfwd.2", "zfwd.2", "update.2"},
+    {"kinematics.3", "zinv_curl.3", "yinv.3", "xpass_phys.3", "sponge_x.3", "yfwd.3", "zfwd.3", "update.3"},
+    {"kinematics.4", "zinv_curl.4", "yinv.4", "xpass_phys.4", "sponge_x.4", "yfwd.4", "zfwd.4", "update.4"}};
+constexpr int kMaxStepKernels = 4 * 8 + 1;
 
 bool has_sponge(flusi_t h) { return h->opt.sponge_c > 0; }
+
+bool is_rk4(flusi_t h) { return h->opt.time_scheme == 1; }
 
 // The square x pass forms chi_sp omega itself; other grids take a separate
 // x round trip of the vorticity.
 bool sponge_kernel(flusi_t h) { return has_sponge(h) && !xpass_fuses_sponge(h->prec == FLUSI_FP64, h->g); }
 
-int step_kernels(flusi_t h) { return sponge_kernel(h) ? kMaxStepKernels : kMaxStepKernels - 1; }
+// Kernels per step: per right-hand side kinematics, z inverse, y inverse, x
+// pass, (sponge x pass), y forward, z forward, update; the scalar kernel once.
+int step_kernels(flusi_t h) { return (is_rk4(h) ? 4 : 1) * (7 + (sponge_kernel(h) ? 1 : 0)) + 1; }
+
+// Explicit-diffusion cap of the RK4 step: 2.5 / (nu |k|^2_max) over the kept modes.
+double rk4_dt_diff(flusi_t h)
+{
+    if (!is_rk4(h) || !(h->nu > 0)) return 0.0;
+    const double two_pi = 6.283185307179586476925286766559;
+    const int K[3] = {h->g.Kx, h->g.Ky, h->g.Kz};
+    double k2 = 0;
+    for (int i = 0; i < 3; ++i) {
+        const double k = two_pi * K[i] / h->L[i];
+        k2 += k * k;
+    }
+    return 2.5 / (h->nu * k2);
+}
 
 ZfwdExtra zextra(flusi_t h)
 {
@@ -273,78 +296,96 @@ void set_wake(flusi_t h, XExtra& xe)
     }
 }
 
-// Enqueue one step; with `ev` (step_kernels + 1 events) records an event
-// before each kernel and after the last.
-cudaError_t enqueue_step(flusi_t h, cudaStream_t s, cudaEvent_t* ev)
+// Enqueue one step.  With `ev` (step_kernels + 1 events) it records an event
+// before each kernel and after the last, and names[i] the kernel after event i.
+cudaError_t enqueue_step(flusi_t h, cudaStream_t s, cudaEvent_t* ev, const char** names = nullptr)
 {
     const Geom& g = h->g;
     const int fp64 = h->prec == FLUSI_FP64;
     StepState* st = at<StepState>(h, h->ostate);
+    StepCoef* coef = at<StepCoef>(h, h->ocoef);
     void* W = h->ws + h->oW;
     const double2* tx = at<double2>(h, h->otx);
     const double2* ty = at<double2>(h, h->oty);
     const double2* tz = at<double2>(h, h->otz);
     cudaError_t e;
     int k = 0;
-    auto mark = [&]() {
+    auto mark = [&](const char* next) {
         if (ev) cudaEventRecord(ev[k], s);
+        if (names) names[k] = next;
         ++k;
     };
-    // Without per-kernel events the two single-block kernels run on the side
-    // stream: the kinematics only have to finish before the x pass, the
-    // scalars (dt, IF-AB2 coefficients, force row) only before the z update.
+    // Without per-kernel events the two single-block kernels of the first
+    // right-hand side run on the side stream: the kinematics only have to
+    // finish before the x pass, the scalars (dt, coefficients, force row) only
+    // before the update.
     const bool branch = ev == nullptr;
     cudaStream_t sk = branch ? h->side : s;
-    mark();
-    if (branch) {
-        if ((e = cudaEventRecord(h->ev_fork, s))) return e;
-        if ((e = cudaStreamWaitEvent(sk, h->ev_fork, 0))) return e;
-    }
-    k_kinematics<<<1, 32, 0, sk>>>(at<flusi_insect>(h, h->oins), st, at<Frame>(h, h->oframe), box_margin(h));
-    if ((e = cudaGetLastError())) return e;
-    if (branch && (e = cudaEventRecord(h->ev_kin, sk))) return e;
-    mark();
-    if ((e = launch_zinv(fp64, h->ws + h->oU, W, g, h->pz, tz, at<int>(h, h->opz), 6, st, s))) return e;
-    mark();
-    if ((e = launch_ypass(fp64, true, W, g, h->py, ty, at<int>(h, h->opy), 6, st, s))) return e;
-    mark();
-    if (branch && (e = cudaStreamWaitEvent(s, h->ev_kin, 0))) return e;
-    XExtra xe{};
-    xe.frame = at<Frame>(h, h->oframe);
-    xe.shape = make_shape(h);
-    xe.part = at<double>(h, h->opart);
-    xe.comp0 = 0;
-    set_wake(h, xe);
-    xe.sponge_fused = has_sponge(h) && !sponge_kernel(h);
-    if ((e = launch_xpass(fp64, XP_PHYS, W, g, h->px, tx, at<int>(h, h->opx), xe, st, s))) return e;
-    mark();
-    if (branch) {
-        if ((e = cudaEventRecord(h->ev_x, s))) return e;
-        if ((e = cudaStreamWaitEvent(sk, h->ev_x, 0))) return e;
-    }
-    double3 opts = make_double3(h->opt.cfl, h->opt.dt_fixed, h->opt.dt_max);
-    k_scalars<<<1, 256, 0, sk>>>(g, at<double>(h, h->opart), h->xgrid, st, at<StepCoef>(h, h->ocoef),
-                                 at<double>(h, h->orows), h->opt.force_ring, at<double>(h, h->oetab), opts);
-    if ((e = cudaGetLastError())) return e;
-    if (branch && (e = cudaEventRecord(h->ev_sc, sk))) return e;
-    mark();
     const int nfwd = has_sponge(h) ? 6 : 3;
-    if (sponge_kernel(h)) {
-        // chi_sp omega of the vorticity still in W[3..5] (x transformed back in place)
-        XExtra xs{};
-        xs.ncomp = 3;
-        xs.comp0 = 3;
-        set_wake(h, xs);
-        if ((e = launch_xpass(fp64, XP_SPONGE, W, g, h->px, tx, at<int>(h, h->opx), xs, st, s))) return e;
-        mark();
+    const int stages = is_rk4(h) ? 4 : 1;
+    const double frac[4] = {0.0, 0.5, 0.5, 1.0};
+    for (int q = 0; q < stages; ++q) {
+        const char* const* nm = kStageNames[q];
+        // the right-hand side at the stage state: u^n first, then the RK4 stage buffer
+        void* ustage = q == 0 ? h->ws + h->oU : h->ws + h->oUt;
+        cudaStream_t skq = q == 0 ? sk : s;
+        const bool br = branch && q == 0;
+        mark(nm[0]);
+        if (br) {
+            if ((e = cudaEventRecord(h->ev_fork, s))) return e;
+            if ((e = cudaStreamWaitEvent(sk, h->ev_fork, 0))) return e;
+        }
+        k_kinematics<<<1, 32, 0, skq>>>(at<flusi_insect>(h, h->oins), st, coef, at<Frame>(h, h->oframe),
+                                        box_margin(h), frac[q]);
+        if ((e = cudaGetLastError())) return e;
+        if (br && (e = cudaEventRecord(h->ev_kin, sk))) return e;
+        mark(nm[1]);
+        if ((e = launch_zinv(fp64, ustage, W, g, h->pz, tz, at<int>(h, h->opz), 6, st, s))) return e;
+        mark(nm[2]);
+        if ((e = launch_ypass(fp64, true, W, g, h->py, ty, at<int>(h, h->opy), 6, st, s))) return e;
+        mark(nm[3]);
+        if (br && (e = cudaStreamWaitEvent(s, h->ev_kin, 0))) return e;
+        XExtra xe{};
+        xe.frame = at<Frame>(h, h->oframe);
+        xe.shape = make_shape(h);
+        xe.part = at<double>(h, h->opart);
+        xe.comp0 = 0;
+        set_wake(h, xe);
+        xe.sponge_fused = has_sponge(h) && !sponge_kernel(h);
+        if ((e = launch_xpass(fp64, XP_PHYS, W, g, h->px, tx, at<int>(h, h->opx), xe, st, s))) return e;
+        if (q == 0) {
+            mark("scalars");
+            if (branch) {
+                if ((e = cudaEventRecord(h->ev_x, s))) return e;
+                if ((e = cudaStreamWaitEvent(sk, h->ev_x, 0))) return e;
+            }
+            double3 opts = make_double3(h->opt.cfl, h->opt.dt_fixed, h->opt.dt_max);
+            k_scalars<<<1, 256, 0, sk>>>(g, at<double>(h, h->opart), h->xgrid, st, coef, at<double>(h, h->orows),
+                                         h->opt.force_ring, at<double>(h, h->oetab), opts, rk4_dt_diff(h));
+            if ((e = cudaGetLastError())) return e;
+            if (branch && (e = cudaEventRecord(h->ev_sc, sk))) return e;
+        }
+        if (sponge_kernel(h)) {
+            mark(nm[4]);
+            // chi_sp omega of the vorticity still in W[3..5] (x transformed back in place)
+            XExtra xs{};
+            xs.ncomp = 3;
+            xs.comp0 = 3;
+            set_wake(h, xs);
+            if ((e = launch_xpass(fp64, XP_SPONGE, W, g, h->px, tx, at<int>(h, h->opx), xs, st, s))) return e;
+        }
+        mark(nm[5]);
+        if ((e = launch_ypass(fp64, false, W, g, h->py, ty, at<int>(h, h->opy), nfwd, st, s))) return e;
+        mark(nm[6]);
+        if ((e = launch_zfwd(fp64, W, nfwd, g, h->pz, tz, at<int>(h, h->opz), st, s))) return e;
+        mark(nm[7]);
+        if (q == 0 && branch && (e = cudaStreamWaitEvent(s, h->ev_sc, 0))) return e;
+        ZfwdExtra ze = zextra(h);
+        ze.stage = h->ws + h->oUt;
+        if ((e = launch_zupdate(fp64, is_rk4(h) ? 2 + q : 0, W, h->ws + h->oU, h->ws + h->oH, g, ze, st, s)))
+            return e;
     }
-    if ((e = launch_ypass(fp64, false, W, g, h->py, ty, at<int>(h, h->opy), nfwd, st, s))) return e;
-    mark();
-    if ((e = launch_zfwd(fp64, W, nfwd, g, h->pz, tz, at<int>(h, h->opz), st, s))) return e;
-    mark();
-    if (branch && (e = cudaStreamWaitEvent(s, h->ev_sc, 0))) return e;
-    if ((e = launch_zupdate(fp64, 0, W, h->ws + h->oU, h->ws + h->oH, g, zextra(h), st, s))) return e;
-    mark();
+    mark(nullptr);
     return cudaSuccess;
 }
 
@@ -439,6 +480,9 @@ int flusi_set_options(flusi_t h, const flusi_options* o)
         return fail(h, FLUSI_EINVAL, "bad option value");
     if (!(o->sponge_c >= 0) || !std::isfinite(o->sponge_c))
         return fail(h, FLUSI_EINVAL, "sponge_c must be >= 0 (0: no sponge)");
+    if (o->time_scheme != 0 && o->time_scheme != 1) return fail(h, FLUSI_EINVAL, "time_scheme must be 0 or 1");
+    if (h->bound && o->time_scheme != h->opt.time_scheme)
+        return fail(h, FLUSI_EINVAL, "time_scheme cannot change after flusi_bind");
     for (int i = 0; i < 3; ++i)
         if (!(o->sponge_width[i] >= 0 && o->sponge_width[i] <= h->L[i]) ||
             !(o->layer_width[i] >= 0 && o->layer_width[i] <= h->L[i]))
@@ -731,7 +775,8 @@ int flusi_debug_fields(flusi_t h, void* out_dev)
     cudaStream_t s = h->stream;
     void* W = h->ws + h->oW;
     StepState* st = at<StepState>(h, h->ostate);
-    k_kinematics<<<1, 32, 0, s>>>(at<flusi_insect>(h, h->oins), st, at<Frame>(h, h->oframe), box_margin(h));
+    k_kinematics<<<1, 32, 0, s>>>(at<flusi_insect>(h, h->oins), st, at<StepCoef>(h, h->ocoef),
+                                  at<Frame>(h, h->oframe), box_margin(h), 0.0);
     CK(cudaGetLastError(), "kinematics");
     CK(launch_zinv(fp64, h->ws + h->oU, W, g, h->pz, at<double2>(h, h->otz), at<int>(h, h->opz), 6, nullptr, s), "z inverse");
     CK(launch_ypass(fp64, true, W, g, h->py, at<double2>(h, h->oty), at<int>(h, h->opy), 6, nullptr, s), "y inverse");
@@ -752,11 +797,13 @@ int flusi_profile_step(flusi_t h, int n, double* ms, const char** names, int* nk
     if (n < 1 || !ms || !nk) return fail(h, FLUSI_EINVAL, "bad argument");
     if (h->poisoned) return fail(h, FLUSI_ESTATE, "handle poisoned");
     const int nk_step = step_kernels(h);
+    if (nk_step > FLUSI_PROFILE_MAX) return fail(h, FLUSI_EINVAL, "too many kernels per step to profile");
     cudaEvent_t ev[kMaxStepKernels + 1];
+    const char* nm[kMaxStepKernels + 1];
     for (auto& e : ev) CK(cudaEventCreate(&e), "event");
     std::vector<double> acc(nk_step, 0.0);
     for (int i = 0; i < n; ++i) {
-        CK(enqueue_step(h, h->stream, ev), "enqueue step");
+        CK(enqueue_step(h, h->stream, ev, nm), "enqueue step");
         CK(cudaEventSynchronize(ev[nk_step]), "event sync");
         for (int k = 0; k < nk_step; ++k) {
             float t = 0;
@@ -765,10 +812,9 @@ int flusi_profile_step(flusi_t h, int n, double* ms, const char** names, int* nk
         }
     }
     for (auto& e : ev) cudaEventDestroy(e);
-    for (int k = 0, slot = 0; k < nk_step; ++k, ++slot) {
-        if (slot == kSpongeSlot && !sponge_kernel(h)) ++slot;
+    for (int k = 0; k < nk_step; ++k) {
         ms[k] = acc[k] / n;
-        if (names) names[k] = kKernelNames[slot];
+        if (names) names[k] = nm[k];
     }
     *nk = nk_step;
     return read_status(h, nullptr);

@@ -17,10 +17,11 @@
 namespace flusi {
 
 // kinematics / scalars (scalars.cu)
-__global__ void k_kinematics(const flusi_insect* ins, const StepState* st, Frame* fr, double h);
+__global__ void k_kinematics(const flusi_insect* ins, const StepState* st, const StepCoef* coef, Frame* fr,
+                             double h, double frac);
 __global__ void k_reset_state(StepState* st, StepCoef* coef);
 __global__ void k_scalars(Geom g, const double* part, int nparts, StepState* st, StepCoef* coef,
-                          double* rows, int ring, double* etab, double3 opts);
+                          double* rows, int ring, double* etab, double3 opts, double dt_diff);
 
 // y transform (ypass.cu): W[c] for c < ncomp, between A and B form.
 // tw: twiddle table of the axis; pos: digit-reversal table of its plan.
@@ -40,14 +41,16 @@ struct ZfwdExtra {
     const double* etab;       // mode 0: [E1x Mx][E1y My][E1z Mz][E2x][E2y][E2z]
     double u_inf[3];
     int mean_free;
-    double sponge_c;          // mode 0: > 0 adds the vorticity sponge of W[3..5]
+    double sponge_c;          // modes 0, 2..5: > 0 adds the vorticity sponge of W[3..5]
+    void* stage;              // modes 2..5: the RK4 stage state (state layout)
 };
 // forward z transform of W[0..nf-1] (A form), in place: the kept modes jz < Mz
 // end in rows jz of each field's A-form layout
 cudaError_t launch_zfwd(int fp64, void* W, int nf, const Geom& g, const FftPlan& plan,
                         const double2* tw, const int* pos, const StepState* st, cudaStream_t s);
-// 1/N, sponge, projection and (mode 0) IF-AB2 update of U, H or (mode 1) U = N, H = 0,
-// reading the kept modes that launch_zfwd left in W
+// 1/N, sponge, projection and (mode 0) IF-AB2 update of U, H, (mode 1) U = N,
+// H = 0, or (modes 2..5) RK4 stage 1..4, reading the kept modes that
+// launch_zfwd left in W
 cudaError_t launch_zupdate(int fp64, int mode, const void* W, void* U, void* H, const Geom& g,
                            const ZfwdExtra& ex, const StepState* st, cudaStream_t s);
 

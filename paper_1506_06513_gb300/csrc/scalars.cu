@@ -77,10 +77,13 @@ __device__ void box_grow(double* box, const double* p)
 
 }  // namespace
 
-__global__ void k_kinematics(const flusi_insect* ins, const StepState* st, Frame* fr, double h)
+// frac = 0: at the state's time; frac > 0: at t0 + frac dt of the current
+// step (the later RK4 stages, after k_scalars has written t0 and dt).
+__global__ void k_kinematics(const flusi_insect* ins, const StepState* st, const StepCoef* coef, Frame* fr,
+                             double h, double frac)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    const double t = st->t;
+    const double t = frac > 0.0 ? coef->t0 + frac * coef->dt : st->t;
     Frame F;
     F.t = t;
     for (int i = 0; i < 3; ++i) {
@@ -183,9 +186,10 @@ __global__ void k_reset_state(StepState* st, StepCoef* coef)
 }
 
 // One block.  Reduces part[nparts][kNumSums] in a fixed order, then forms the
-// step's scalars.  `opts` = {cfl, dt_fixed, dt_max}.
+// step's scalars.  `opts` = {cfl, dt_fixed, dt_max}; dt_diff > 0 caps the
+// adaptive step (the explicit-diffusion limit of RK4).
 __global__ void k_scalars(Geom g, const double* part, int nparts, StepState* st, StepCoef* coef,
-                          double* rows, int ring, double* etab, double3 opts)
+                          double* rows, int ring, double* etab, double3 opts, double dt_diff)
 {
     __shared__ double red[kNumSums][33];
     __shared__ double tot[kNumSums];
@@ -242,6 +246,7 @@ __global__ void k_scalars(Geom g, const double* part, int nparts, StepState* st,
         dt = g.eta;
         if (umax > 0.0) dt = fmin(dt, opts.x * dmin / umax);
         if (opts.z > 0.0) dt = fmin(dt, opts.z);
+        if (dt_diff > 0.0) dt = fmin(dt, dt_diff);
     }
     const int first = (n == 0);
 
@@ -264,6 +269,7 @@ __global__ void k_scalars(Geom g, const double* part, int nparts, StepState* st,
         c.dt = dt;
         c.n = n;
         c.first = first;
+        c.t0 = st->t;
         c.skip = 0;
         if (first) {
             c.c_now = dt;

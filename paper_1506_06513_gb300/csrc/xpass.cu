@@ -1418,7 +1418,7 @@ extern "C" int flusi_penalization_sums_noalloc(int nx, int ny, int nz, const dou
     const long long want = (N + kNoallocThreads - 1) / kNoallocThreads;
     const int grid = (int)(want < kNoallocMaxCtas ? want : kNoallocMaxCtas);
     k_noalloc_header<<<1, 1, 0, s>>>(ins, t, d_ins, d_st);
-    k_kinematics<<<1, 32, 0, s>>>(d_ins, d_st, d_fr, margin);
+    k_kinematics<<<1, 32, 0, s>>>(d_ins, d_st, nullptr, d_fr, margin, 0.0);
     k_noalloc_sums<<<grid, kNoallocThreads, 0, s>>>(u_dev, nx, ny, nz, dx, dy, dz, d_fr, sh, part);
     k_noalloc_reduce<<<1, 64, 0, s>>>(part, grid, dx * dy * dz, eta, sums);
     cudaError_t e = cudaGetLastError();

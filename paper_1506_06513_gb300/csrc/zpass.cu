@@ -185,6 +185,10 @@ k_zfwd(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict_
 // vorticity, zero at k = 0); Leray projection N <- N - k (k.N)/|k|^2, then
 //   mode 0: IF-AB2  u^{n+1} = E1 (u^n + c_now N) - c_old E2 N^{n-1},  N^{n-1} <- N
 //   mode 1: u_hat = N (the initial condition), history cleared.
+//   modes 2..5: RK4 stage 1..4 with R = N - nu |k|^2 u_s, u_s the stage state
+//     (U for stage 1, the stage buffer Ut after), H the accumulator:
+//     1: H = R, Ut = U + dt/2 R;  2: H += 2R, Ut = U + dt/2 R;
+//     3: H += 2R, Ut = U + dt R;  4: U += dt/6 (H + R).
 // The mean (k = 0) is held at u_inf unless it is free.  Row padding x >= Mx
 // is never written (it is zero from the workspace reset on).
 template <typename T, int MODE, bool SPONGE>
@@ -193,13 +197,17 @@ k_zupdate(const cplx<T>* __restrict__ Wn, cplx<T>* __restrict__ U, cplx<T>* __re
           ZfwdExtra ex, const StepState* __restrict__ st)
 {
     if (st && st->status != 0) return;
-    if (MODE == 0 && ex.coef->skip) return;
+    constexpr bool RK = MODE >= 2;
+    constexpr int STAGE = MODE - 1;        // RK4 stage 1..4
+    if ((MODE == 0 || RK) && ex.coef->skip) return;
     constexpr int VEC = 16 / sizeof(cplx<T>);
+    cplx<T>* __restrict__ Ut = (cplx<T>*)ex.stage;
     const int Q = g.My * g.Mxp;
     const size_t S = (size_t)g.Mz * Q;     // values per component
     const size_t groups = S / VEC;         // Mxp is a multiple of 4
     const size_t Wplane = (size_t)g.ny * g.Mxp, Wfield = (size_t)g.nz * Wplane;
-    constexpr bool sponge = MODE == 0 && SPONGE;
+    constexpr bool sponge = (MODE == 0 || RK) && SPONGE;
+    const T dt = RK ? T(ex.coef->dt) : T(0), nu = T(g.nu);
     const T two_pi = T(6.283185307179586476925286766559);
     const T inv_n = T(1.0 / ((double)g.nx * g.ny * g.nz));
     double c_now = 0, c_old = 0;
@@ -222,7 +230,7 @@ k_zupdate(const cplx<T>* __restrict__ Wn, cplx<T>* __restrict__ U, cplx<T>* __re
         const int jz = (int)(o / Q), q = (int)(o - (size_t)jz * Q);
         const int jy = q / g.Mxp, x0 = q - jy * g.Mxp;
         if (x0 >= g.Mx) continue;
-        cplx<T> n[3][VEC], u[3][VEC], h[3][VEC], sv[3][VEC];
+        cplx<T> n[3][VEC], u[3][VEC], h[3][VEC], sv[3][VEC], us[3][VEC];
         const size_t on = (size_t)jz * Wplane + q;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -233,8 +241,10 @@ k_zupdate(const cplx<T>* __restrict__ Wn, cplx<T>* __restrict__ U, cplx<T>* __re
                 sv[c][v] = sponge ? Wn[(3 + c) * Wfield + on + v] : mkc<T>(0, 0);
                 u[c][v] = mkc<T>(0, 0);
                 h[c][v] = mkc<T>(0, 0);
-                if (MODE == 0) u[c][v] = U[oc + v];
-                if (MODE == 0 && !first) h[c][v] = H[oc + v];
+                us[c][v] = mkc<T>(0, 0);
+                if (MODE == 0 || RK) u[c][v] = U[oc + v];
+                if ((MODE == 0 && !first) || (RK && STAGE > 1)) h[c][v] = H[oc + v];
+                if (RK && STAGE > 1) us[c][v] = Ut[oc + v];
             }
         }
         const T ky = two_pi * T(mode_of(jy, g.Ky)) / T(g.Ly);
@@ -288,6 +298,22 @@ k_zupdate(const cplx<T>* __restrict__ Wn, cplx<T>* __restrict__ U, cplx<T>* __re
                     r.y = e1 * (u[c][v].y + cn * N[c].y) - co * e2 * h[c][v].y;
                     U[c * S + ov] = r;
                     H[c * S + ov] = N[c];
+                }
+            } else if (RK) {
+                const T k2 = kx * kx + ky * ky + kz * kz;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const cplx<T> ust = STAGE == 1 ? u[c][v] : us[c][v];
+                    const cplx<T> R = csub(N[c], cscale(ust, nu * k2));
+                    if (STAGE == 1) {
+                        H[c * S + ov] = R;
+                        Ut[c * S + ov] = cadd(u[c][v], cscale(R, T(0.5) * dt));
+                    } else if (STAGE == 2 || STAGE == 3) {
+                        H[c * S + ov] = cadd(h[c][v], cscale(R, T(2)));
+                        Ut[c * S + ov] = cadd(u[c][v], cscale(R, STAGE == 2 ? T(0.5) * dt : dt));
+                    } else {
+                        U[c * S + ov] = cadd(u[c][v], cscale(cadd(h[c][v], R), dt / T(6)));
+                    }
                 }
             } else {
 #pragma unroll
@@ -343,12 +369,24 @@ cudaError_t launch_zu(int mode, const void* Nh, void* U, void* H, const Geom& g,
     const size_t groups = (size_t)g.Mz * g.My * g.Mxp / VEC;
     const int blocks = (int)std::min<size_t>(ceil_div_sz(groups, 256), (size_t)152 * 64);
     const cplx<T>* n = (const cplx<T>*)Nh;
-    if (mode == 0 && ex.sponge_c > 0)
-        k_zupdate<T, 0, true><<<blocks, 256, 0, s>>>(n, (cplx<T>*)U, (cplx<T>*)H, g, ex, st);
-    else if (mode == 0)
-        k_zupdate<T, 0, false><<<blocks, 256, 0, s>>>(n, (cplx<T>*)U, (cplx<T>*)H, g, ex, st);
-    else
-        k_zupdate<T, 1, false><<<blocks, 256, 0, s>>>(n, (cplx<T>*)U, (cplx<T>*)H, g, ex, st);
+    cplx<T>* u = (cplx<T>*)U;
+    cplx<T>* hh = (cplx<T>*)H;
+    const bool sp = ex.sponge_c > 0 && mode != 1;
+#define FLUSI_ZU(M)                                                           \
+    if (sp)                                                                   \
+        k_zupdate<T, M, true><<<blocks, 256, 0, s>>>(n, u, hh, g, ex, st);    \
+    else                                                                      \
+        k_zupdate<T, M, false><<<blocks, 256, 0, s>>>(n, u, hh, g, ex, st);
+    switch (mode) {
+    case 0: FLUSI_ZU(0) break;
+    case 1: k_zupdate<T, 1, false><<<blocks, 256, 0, s>>>(n, u, hh, g, ex, st); break;
+    case 2: FLUSI_ZU(2) break;
+    case 3: FLUSI_ZU(3) break;
+    case 4: FLUSI_ZU(4) break;
+    case 5: FLUSI_ZU(5) break;
+    default: return cudaErrorInvalidValue;
+    }
+#undef FLUSI_ZU
     return cudaGetLastError();
 }
 

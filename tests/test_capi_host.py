@@ -114,11 +114,21 @@ def test_insect_descriptor_validation(fl):
 
 def test_struct_layouts_match_header(fl):
     """The ctypes mirrors have the sizes the C compiler gives the structs."""
-    assert C.sizeof(fl.Options) == 3 * 8 + 3 * 8 + 4 * 4 + 7 * 8
+    assert C.sizeof(fl.Options) == 3 * 8 + 3 * 8 + 4 * 4 + 7 * 8 + 2 * 4
     assert C.sizeof(fl.Insect) == 4 * 4 + 8 * (1 + 3 + 3 + 6 + 2 + 3 + 3 + 1 + 4 + 1 + 3 * 17)
 
 
 def test_kernels_per_step(fl):
     h = fl.flusi_create((16, 16, 16), (1.0, 1.0, 1.0), 0.1, 1e-2, fl.FLUSI_FP64)
     assert fl.flusi_kernels_per_step(h) == 8
+    before = fl.flusi_workspace_bytes(h)
+    fl.flusi_set_options(h, fl.make_options({"time_scheme": "rk4"}))
+    # four right-hand sides of seven kernels, one scalar kernel; one more state buffer
+    assert fl.flusi_kernels_per_step(h) == 4 * 7 + 1
+    spec = 3 * 11 * 11 * 8 * 16
+    assert fl.flusi_workspace_bytes(h) - before == (spec + 255) // 256 * 256
+    bad = fl.make_options({})
+    bad.time_scheme = 2
+    with pytest.raises(fl.FlusiError):
+        fl.flusi_set_options(h, bad)
     fl.flusi_destroy(h)
