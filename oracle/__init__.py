@@ -20,6 +20,7 @@ _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _SOURCES = ["fft.c", "insect.c", "solver.c"]
 
 MAX_FOURIER = 8
+MAX_CONTOUR = 32
 ROW_COLS = 22
 NSUMS = 39
 SUM_EKIN, SUM_UMAX, SUM_NONFINITE = 36, 37, 38
@@ -68,7 +69,13 @@ class Insect(C.Structure):
                 ("wing_R", C.c_double), ("wing_h", C.c_double), ("freq", C.c_double),
                 ("phi_a0", C.c_double), ("phi_a", _F), ("phi_b", _F),
                 ("alpha_a0", C.c_double), ("alpha_a", _F), ("alpha_b", _F),
-                ("theta_a0", C.c_double), ("theta_a", _F), ("theta_b", _F)]
+                ("theta_a0", C.c_double), ("theta_a", _F), ("theta_b", _F),
+                ("head_x0", C.c_double * 3), ("head_r", C.c_double),
+                ("eye_x0", C.c_double * 3), ("eye_r", C.c_double),
+                ("wing_shape", C.c_int), ("ncontour", C.c_int),
+                ("contour_xc", C.c_double), ("contour_yc", C.c_double),
+                ("contour_a0", C.c_double), ("contour_a", C.c_double * MAX_CONTOUR),
+                ("contour_b", C.c_double * MAX_CONTOUR)]
 
 
 class Scalars(C.Structure):
@@ -122,6 +129,10 @@ def lib():
         L.orc_sponge_mask.restype = C.c_double
         L.orc_layer_mask.argtypes = [C.POINTER(Params), _dp]
         L.orc_layer_mask.restype = C.c_double
+        L.orc_body_distance.argtypes = [C.POINTER(Insect), _dp]
+        L.orc_body_distance.restype = C.c_double
+        L.orc_wing_distance.argtypes = [C.POINTER(Insect), _dp]
+        L.orc_wing_distance.restype = C.c_double
         L.orc_rhs.argtypes = [C.POINTER(Params), C.POINTER(Insect), C.c_double, _cp, _cp, _dp]
         L.orc_rhs.restype = C.c_int
         L.orc_physical_fields.argtypes = [C.POINTER(Params), C.POINTER(Insect), C.c_double, _cp,
@@ -185,6 +196,20 @@ def make_insect(d: dict | None) -> Insect | None:
             arr_b[i] = v
         nf = max(nf, len(a), len(b))
     s.nfourier = nf
+    if "head" in d:
+        s.head_x0[:], s.head_r = d["head"]
+    if "eyes" in d:
+        s.eye_x0[:], s.eye_r = d["eyes"]
+    if "contour" in d:
+        c = d["contour"]
+        s.wing_shape = 1
+        s.contour_xc, s.contour_yc = c["center"]
+        s.contour_a0 = c["a0"]
+        for i, v in enumerate(c.get("a", [])):
+            s.contour_a[i] = v
+        for i, v in enumerate(c.get("b", [])):
+            s.contour_b[i] = v
+        s.ncontour = max(len(c.get("a", [])), len(c.get("b", [])))
     return s
 
 
@@ -386,3 +411,13 @@ class Simulation:
     @property
     def nstep(self):
         return self.s.n
+
+
+def body_distance(insect: dict, xb):
+    """Signed distance of the body at a body-frame point (Sec. 3.2)."""
+    return lib().orc_body_distance(C.byref(make_insect(insect)), np.ascontiguousarray(xb, np.float64))
+
+
+def wing_distance(insect: dict, xw):
+    """Signed distance of a wing at a wing-frame point (Sec. 3.3)."""
+    return lib().orc_wing_distance(C.byref(make_insect(insect)), np.ascontiguousarray(xw, np.float64))

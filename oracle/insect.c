@@ -187,20 +187,57 @@ double orc_mask_profile(int profile, double delta, double h)
     return 0.5 * (1.0 + cos(PI * (delta + h) / (2.0 * h)));
 }
 
-static double body_distance(const orc_insect *ins, const double *xb)
+/* Signed distance of the body in its frame (Sec. 3.2).  The thorax is the
+ * ellipsoid rotationally symmetric about x^(b); head and eyes are spheres
+ * |x - x0| - r (the printed forms omit the radius).  The parts are joined
+ * by the minimum of their distances, the union of negative-inside sets (the
+ * printed max would be their intersection). */
+double orc_body_distance(const orc_insect *ins, const double *xb)
 {
     if (ins->body_type == 1)
         return sqrt(xb[0] * xb[0] + xb[1] * xb[1] + xb[2] * xb[2]) - ins->body_a;
-    /* thorax ellipsoid, rotationally symmetric about x^(b) (Sec. 3.2) */
     double a = ins->body_a, b = ins->body_b;
     double rr = sqrt(xb[1] * xb[1] + xb[2] * xb[2]);
     double ax = fabs(xb[0]);
-    if (ax <= a) return rr - sqrt(b * b * (1.0 - (xb[0] / a) * (xb[0] / a)));
-    return sqrt(rr * rr + (ax - a) * (ax - a));
+    double d;
+    if (ax <= a) d = rr - sqrt(b * b * (1.0 - (xb[0] / a) * (xb[0] / a)));
+    else d = sqrt(rr * rr + (ax - a) * (ax - a));
+    if (ins->head_r > 0) {
+        double e[3] = {xb[0] - ins->head_x0[0], xb[1] - ins->head_x0[1], xb[2] - ins->head_x0[2]};
+        double dh = sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]) - ins->head_r;
+        if (dh < d) d = dh;
+    }
+    if (ins->eye_r > 0) {
+        for (int s = 0; s < 2; ++s) {
+            double y0 = s == 0 ? ins->eye_x0[1] : -ins->eye_x0[1];
+            double e[3] = {xb[0] - ins->eye_x0[0], xb[1] - y0, xb[2] - ins->eye_x0[2]};
+            double de = sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]) - ins->eye_r;
+            if (de < d) d = de;
+        }
+    }
+    return d;
 }
 
-static double wing_distance(const orc_insect *ins, const double *xw)
+/* Contour radius R(theta), Eq. Fourier_radious_wing with the angle in
+ * radians (the printed argument 2 pi i theta takes theta in turns). */
+static double contour_radius(const orc_insect *ins, double th)
 {
+    double R = 0.5 * ins->contour_a0;
+    for (int i = 1; i <= ins->ncontour; ++i)
+        R += ins->contour_a[i - 1] * cos(i * th) + ins->contour_b[i - 1] * sin(i * th);
+    return R;
+}
+
+/* Signed distance of a wing in its frame (Sec. 3.3). */
+double orc_wing_distance(const orc_insect *ins, const double *xw)
+{
+    double dz = fabs(xw[2]) - 0.5 * ins->wing_h;
+    if (ins->wing_shape == 1) {
+        double dx = xw[0] - ins->contour_xc, dy = xw[1] - ins->contour_yc;
+        double r = sqrt(dx * dx + dy * dy);
+        double d = r - contour_radius(ins, atan2(dy, dx));
+        return dz > d ? dz : d;
+    }
     double d = xw[0] - ins->wing_c_le;
     double e;
     e = -xw[0] - ins->wing_c_te;
@@ -209,8 +246,7 @@ static double wing_distance(const orc_insect *ins, const double *xw)
     if (e > d) d = e;
     e = -xw[1];
     if (e > d) d = e;
-    e = fabs(xw[2]) - 0.5 * ins->wing_h;
-    if (e > d) d = e;
+    if (dz > d) d = dz;
     return d;
 }
 
@@ -232,7 +268,7 @@ void orc_solid_at(const orc_insect *ins, const orc_frames *fr, double h,
     us[0] = us[1] = us[2] = 0.0;
 
     if (ins->body_type != 0) {
-        double c = orc_mask_profile(ins->profile, body_distance(ins, xb), h);
+        double c = orc_mask_profile(ins->profile, orc_body_distance(ins, xb), h);
         if (c > *chi) {
             *chi = c;
             *colour = 1;
@@ -245,7 +281,7 @@ void orc_solid_at(const orc_insect *ins, const orc_frames *fr, double h,
         for (int i = 0; i < 3; ++i) xs[i] = xb[i] - pb[i];
         mat_vec(fr->M_stroke[s], xs, xs);
         mat_vec(fr->M_wing[s], xs, xw);
-        double c = orc_mask_profile(ins->profile, wing_distance(ins, xw), h);
+        double c = orc_mask_profile(ins->profile, orc_wing_distance(ins, xw), h);
         if (c > *chi) {
             /* Eq. wing_velocity_field, then u_s = u_w + u_b */
             double uw[3];

@@ -24,6 +24,7 @@
 #include <stdint.h>
 
 #define ORC_MAX_FOURIER 8
+#define ORC_MAX_CONTOUR 32   /* harmonics of a wing contour R(theta)     */
 #define ORC_NCOLOURS 3   /* 1 = body, 2 = left wing, 3 = right wing */
 #define ORC_ROW_COLS 22  /* t, dt, {F[3], M[3]} x 3 colours, E_kin, u_max */
 
@@ -67,6 +68,18 @@ typedef struct {
     double phi_a0, phi_a[ORC_MAX_FOURIER], phi_b[ORC_MAX_FOURIER];
     double alpha_a0, alpha_a[ORC_MAX_FOURIER], alpha_b[ORC_MAX_FOURIER];
     double theta_a0, theta_a[ORC_MAX_FOURIER], theta_b[ORC_MAX_FOURIER];
+    /* Head and eye spheres joined to the thorax (Sec. 3.2), body frame;
+     * radius 0: absent.  The right eye mirrors the left one in y^(b). */
+    double head_x0[3], head_r;
+    double eye_x0[3], eye_r;
+    /* Wing outline (Sec. 3.3): 0 = rectangular plate (wing_c_le, wing_c_te,
+     * wing_R); 1 = contour R(theta) = a0/2 + sum a_i cos(i theta) + b_i sin(i theta)
+     * about (contour_xc, contour_yc) in the wing plane, theta measured from
+     * x^(w) towards y^(w). */
+    int wing_shape;
+    int ncontour;
+    double contour_xc, contour_yc;
+    double contour_a0, contour_a[ORC_MAX_CONTOUR], contour_b[ORC_MAX_CONTOUR];
 } orc_insect;
 
 /* Time-level data of the AB2 scheme besides the two spectral fields. */
@@ -100,6 +113,8 @@ void orc_rot_y(double xi, double *R);
 void orc_rot_z(double xi, double *R);
 void orc_frames_at(const orc_insect *ins, double t, orc_frames *fr);
 double orc_mask_profile(int profile, double delta, double h);
+double orc_body_distance(const orc_insect *ins, const double *xb);
+double orc_wing_distance(const orc_insect *ins, const double *xw);
 void orc_solid_at(const orc_insect *ins, const orc_frames *fr, double h,
                   const double x[3], double *chi, int *colour, double us[3]);
 void orc_mask_grid(const orc_params *p, const orc_insect *ins, double t,
