@@ -54,6 +54,7 @@ typedef enum { FLUSI_FP64 = 0, FLUSI_FP32 = 1 } flusi_precision;
 typedef enum { FLUSI_HOST_FP64 = 0, FLUSI_HOST_FP32 = 1, FLUSI_DEVICE = 2 } flusi_where;
 
 #define FLUSI_MAX_FOURIER 8
+#define FLUSI_MAX_CONTOUR 32
 #define FLUSI_FORCE_COLS 22
 
 /* Columns of one force row (Eqs. force_with_unst_corrections and
@@ -111,6 +112,21 @@ typedef struct flusi_insect {
     double phi_a0, phi_a[FLUSI_MAX_FOURIER], phi_b[FLUSI_MAX_FOURIER];
     double alpha_a0, alpha_a[FLUSI_MAX_FOURIER], alpha_b[FLUSI_MAX_FOURIER];
     double theta_a0, theta_a[FLUSI_MAX_FOURIER], theta_b[FLUSI_MAX_FOURIER];
+    /* Head and eye spheres joined to an ellipsoid thorax (Sec. 3.2, Eq.
+     * DELTA_body_jerry), body frame; radius 0: absent.  The right eye mirrors
+     * the left one in y^(b).  The parts are joined by the minimum of their
+     * signed distances (their union). */
+    double head_x0[3], head_r;
+    double eye_x0[3], eye_r;
+    /* Wing outline (Sec. 3.3): wing_shape 0 = the rectangular plate above;
+     * 1 = the contour R(theta) = a0/2 + sum_{i<=ncontour} a_i cos(i theta) +
+     * b_i sin(i theta) (Eq. Fourier_radious_wing, theta in radians from x^(w)
+     * towards y^(w)) about (contour_xc, contour_yc) in the wing plane, with
+     * thickness wing_h.  R is evaluated exactly (no lookup table). */
+    int wing_shape;
+    int ncontour;              /* <= FLUSI_MAX_CONTOUR */
+    double contour_xc, contour_yc;
+    double contour_a0, contour_a[FLUSI_MAX_CONTOUR], contour_b[FLUSI_MAX_CONTOUR];
 } flusi_insect;
 
 /* Create a solver for an nx x ny x nz periodic grid over the box L[3], with
@@ -219,7 +235,7 @@ int flusi_kernels_per_step(flusi_t h, int *count);
  * into its force rows; a step's row adds the unsteady correction (the change
  * of sum chi u_s dV over the previous step) to them.
  *
- * Scratch: a fixed array of about 330 KB in the library's own device memory
+ * Scratch: a fixed array of about 332 KB in the library's own device memory
  * (every GPU that loads the library holds it until the process exits).  The
  * first call on a device looks up that array's device address; make that
  * first call before any stream capture.  Every call shares the array and

@@ -19,6 +19,7 @@ FLUSI_OK, FLUSI_EINVAL, FLUSI_ENOMEM, FLUSI_ECUDA, FLUSI_ENONFINITE, FLUSI_ETIME
 FLUSI_FP64, FLUSI_FP32 = 0, 1
 FLUSI_HOST_FP64, FLUSI_HOST_FP32, FLUSI_DEVICE = 0, 1, 2
 MAX_FOURIER = 8
+MAX_CONTOUR = 32
 FORCE_COLS = 22
 PROFILE_MAX = 40
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENONFINITE", "ETIMEOUT", "ESTATE"]
@@ -55,7 +56,13 @@ class Insect(C.Structure):
                 ("wing_h", C.c_double), ("freq", C.c_double),
                 ("phi_a0", C.c_double), ("phi_a", _F), ("phi_b", _F),
                 ("alpha_a0", C.c_double), ("alpha_a", _F), ("alpha_b", _F),
-                ("theta_a0", C.c_double), ("theta_a", _F), ("theta_b", _F)]
+                ("theta_a0", C.c_double), ("theta_a", _F), ("theta_b", _F),
+                ("head_x0", C.c_double * 3), ("head_r", C.c_double),
+                ("eye_x0", C.c_double * 3), ("eye_r", C.c_double),
+                ("wing_shape", C.c_int), ("ncontour", C.c_int),
+                ("contour_xc", C.c_double), ("contour_yc", C.c_double),
+                ("contour_a0", C.c_double), ("contour_a", C.c_double * MAX_CONTOUR),
+                ("contour_b", C.c_double * MAX_CONTOUR)]
 
 
 def _load():
@@ -290,6 +297,20 @@ def make_insect(d: dict | None) -> Insect | None:
             getattr(s, name + "_b")[i] = v
         nf = max(nf, len(a), len(b))
     s.nfourier = nf
+    if "head" in d:
+        s.head_x0[:], s.head_r = d["head"]
+    if "eyes" in d:
+        s.eye_x0[:], s.eye_r = d["eyes"]
+    if "contour" in d:
+        c = d["contour"]
+        s.wing_shape = 1
+        s.contour_xc, s.contour_yc = c["center"]
+        s.contour_a0 = c["a0"]
+        for i, v in enumerate(c.get("a", [])):
+            s.contour_a[i] = v
+        for i, v in enumerate(c.get("b", [])):
+            s.contour_b[i] = v
+        s.ncontour = max(len(c.get("a", [])), len(c.get("b", [])))
     return s
 
 

@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/flusi.h"
+
 namespace flusi {
 
 template <typename T> struct cplx_of;
@@ -93,11 +95,47 @@ struct Shape {
     int body_type;           // 0 none, 1 sphere, 2 ellipsoid
     int nwings;
     int profile;             // 0 cosine layer, 1 tanh layer
-    int pad;
+    int wing_shape;          // 0 plate, 1 contour R(theta)
     double h;                // smoothing half-width
     double body_a, body_b;
     double c_le, c_te, R, ht;
+    double head_x0[3], head_r, eye_x0[3], eye_r;   // body frame; radius 0: absent
+    int ncontour, pad;
+    double contour_xc, contour_yc, contour_a0;
+    double contour_a[FLUSI_MAX_CONTOUR], contour_b[FLUSI_MAX_CONTOUR];
 };
+
+// Mask shape of an insect descriptor with smoothing half-width h.
+inline Shape shape_of(const flusi_insect& I, double h)
+{
+    Shape s{};
+    s.body_type = I.body_type;
+    s.nwings = I.nwings;
+    s.profile = I.profile;
+    s.wing_shape = I.wing_shape;
+    s.h = h;
+    s.body_a = I.body_a;
+    s.body_b = I.body_b;
+    s.c_le = I.wing_c_le;
+    s.c_te = I.wing_c_te;
+    s.R = I.wing_R;
+    s.ht = I.wing_h;
+    for (int i = 0; i < 3; ++i) {
+        s.head_x0[i] = I.head_x0[i];
+        s.eye_x0[i] = I.eye_x0[i];
+    }
+    s.head_r = I.head_r;
+    s.eye_r = I.eye_r;
+    s.ncontour = I.ncontour;
+    s.contour_xc = I.contour_xc;
+    s.contour_yc = I.contour_yc;
+    s.contour_a0 = I.contour_a0;
+    for (int i = 0; i < FLUSI_MAX_CONTOUR; ++i) {
+        s.contour_a[i] = i < I.ncontour ? I.contour_a[i] : 0.0;
+        s.contour_b[i] = i < I.ncontour ? I.contour_b[i] : 0.0;
+    }
+    return s;
+}
 
 // Device-resident step state (persists across steps).
 struct StepState {

@@ -203,21 +203,9 @@ template <typename P> P* at(flusi_t h, size_t off) { return reinterpret_cast<P*>
 
 Shape make_shape(flusi_t h)
 {
-    Shape s{};
-    if (!h->have_ins) return s;
-    const flusi_insect& I = h->ins;
-    s.body_type = I.body_type;
-    s.nwings = I.nwings;
-    s.profile = I.profile;
-    double d = std::max(h->g.dx, std::max(h->g.dy, h->g.dz));
-    s.h = I.c_smth * d;
-    s.body_a = I.body_a;
-    s.body_b = I.body_b;
-    s.c_le = I.wing_c_le;
-    s.c_te = I.wing_c_te;
-    s.R = I.wing_R;
-    s.ht = I.wing_h;
-    return s;
+    if (!h->have_ins) return Shape{};
+    const double d = std::max(h->g.dx, std::max(h->g.dy, h->g.dz));
+    return shape_of(h->ins, h->ins.c_smth * d);
 }
 
 // Half-width used to grow the bounding boxes: the cosine layer vanishes
@@ -420,12 +408,8 @@ int read_status(flusi_t h, StepState* out)
     return FLUSI_OK;
 }
 
-bool same_shape(const Shape& a, const Shape& b)
-{
-    return a.body_type == b.body_type && a.nwings == b.nwings && a.profile == b.profile &&
-           a.h == b.h && a.body_a == b.body_a && a.body_b == b.body_b && a.c_le == b.c_le &&
-           a.c_te == b.c_te && a.R == b.R && a.ht == b.ht;
-}
+// Shapes are value-initialized, padding included, so bytes compare fields.
+bool same_shape(const Shape& a, const Shape& b) { return std::memcmp(&a, &b, sizeof a) == 0; }
 
 size_t real_size(int where, int prec)
 {
@@ -552,7 +536,10 @@ int flusi_set_kinematics(flusi_t h, const flusi_insect* ins)
             ins->profile < 0 || ins->profile > 1 || ins->nfourier < 0 ||
             ins->nfourier > FLUSI_MAX_FOURIER || !(ins->c_smth > 0) ||
             (ins->body_type == 1 && !(ins->body_a > 0)) ||
-            (ins->body_type == 2 && !(ins->body_a > 0 && ins->body_b > 0)))
+            (ins->body_type == 2 && !(ins->body_a > 0 && ins->body_b > 0)) ||
+            !(ins->head_r >= 0) || !(ins->eye_r >= 0) || ins->wing_shape < 0 || ins->wing_shape > 1 ||
+            ins->ncontour < 0 || ins->ncontour > FLUSI_MAX_CONTOUR ||
+            (ins->wing_shape == 1 && !(ins->contour_a0 > 0)))
             return fail(h, FLUSI_EINVAL, "bad insect descriptor");
         h->ins = *ins;
         h->have_ins = 1;

@@ -143,19 +143,32 @@ __global__ void k_kinematics(const flusi_insect* ins, const StepState* st, const
         F.active[p] = 0;
     }
     if (ins->body_type != 0) {
-        double e[3];
-        if (ins->body_type == 1) {
-            e[0] = e[1] = e[2] = ins->body_a + h;
-        } else {
-            e[0] = ins->body_a + h;
-            e[1] = e[2] = ins->body_b + h;
-        }
-        for (int i = 0; i < 3; ++i) {
-            // half extent of the rotated box along global axis i
-            double r = fabs(Mb.a[0 * 3 + i]) * e[0] + fabs(Mb.a[1 * 3 + i]) * e[1] +
-                       fabs(Mb.a[2 * 3 + i]) * e[2];
-            F.box[0][2 * i] = F.xc[i] - r;
-            F.box[0][2 * i + 1] = F.xc[i] + r;
+        // body-frame box of thorax, head and eyes, grown by h; its corners in
+        // the global frame
+        double lo[3], hi[3];
+        const double ey = ins->body_type == 1 ? ins->body_a : ins->body_b;
+        lo[0] = -ins->body_a;
+        hi[0] = ins->body_a;
+        lo[1] = lo[2] = -ey;
+        hi[1] = hi[2] = ey;
+        if (ins->body_type == 2 && ins->head_r > 0)
+            for (int i = 0; i < 3; ++i) {
+                lo[i] = fmin(lo[i], ins->head_x0[i] - ins->head_r);
+                hi[i] = fmax(hi[i], ins->head_x0[i] + ins->head_r);
+            }
+        if (ins->body_type == 2 && ins->eye_r > 0)
+            for (int i = 0; i < 3; ++i) {
+                const double c = ins->eye_x0[i], m = i == 1 ? -c : c;   // both eyes
+                lo[i] = fmin(lo[i], fmin(c, m) - ins->eye_r);
+                hi[i] = fmax(hi[i], fmax(c, m) + ins->eye_r);
+            }
+        for (int c = 0; c < 8; ++c) {
+            double q[3] = {(c & 1 ? hi[0] : lo[0]) + (c & 1 ? h : -h),
+                           (c & 2 ? hi[1] : lo[1]) + (c & 2 ? h : -h),
+                           (c & 4 ? hi[2] : lo[2]) + (c & 4 ? h : -h)}, gq[3];
+            apply_t(Mb, q, gq);
+            for (int i = 0; i < 3; ++i) gq[i] += F.xc[i];
+            box_grow(F.box[0], gq);
         }
         F.active[0] = 1;
     }
@@ -165,6 +178,16 @@ __global__ void k_kinematics(const flusi_insect* ins, const StepState* st, const
         double xs[2] = {-ins->wing_c_te - h, ins->wing_c_le + h};
         double ys[2] = {-h, ins->wing_R + h};
         double zs[2] = {-0.5 * ins->wing_h - h, 0.5 * ins->wing_h + h};
+        if (ins->wing_shape == 1) {
+            // R(theta) <= a0/2 + sum sqrt(a_i^2 + b_i^2)
+            double rb = 0.5 * ins->contour_a0;
+            for (int i = 0; i < ins->ncontour; ++i)
+                rb += sqrt(ins->contour_a[i] * ins->contour_a[i] + ins->contour_b[i] * ins->contour_b[i]);
+            xs[0] = ins->contour_xc - rb - h;
+            xs[1] = ins->contour_xc + rb + h;
+            ys[0] = ins->contour_yc - rb - h;
+            ys[1] = ins->contour_yc + rb + h;
+        }
         for (int c = 0; c < 8; ++c) {
             double q[3] = {xs[c & 1], ys[(c >> 1) & 1], zs[(c >> 2) & 1]}, g[3];
             apply_t(Mg, q, g);

@@ -33,8 +33,112 @@ template <typename T> struct FrameT {
     T xc[3], uc[3], Ob[3], Mb[9], Mw[2][9], pv[2][3], Ow[2][3], box[3][6];
     int active[3];
     T h, a, b, c_le, c_te, R, ht, inv_eta;
-    int body_type, profile;
+    int body_type, profile, wing_shape, ncontour;
+    T head_x0[3], head_r, eye_x0[3], eye_r;
+    T cxc, cyc, ca0, ca[FLUSI_MAX_CONTOUR], cb[FLUSI_MAX_CONTOUR];
 };
+
+// The pass's copy of the frame (FP64 on the device) and mask shape in T.
+template <typename T>
+__device__ void setup_frame(FrameT<T>& f, const Frame& F, const Shape& S, double inv_eta)
+{
+    for (int i = 0; i < 3; ++i) {
+        f.xc[i] = T(F.xc[i]);
+        f.uc[i] = T(F.uc[i]);
+        f.Ob[i] = T(F.Ob[i]);
+        f.active[i] = F.active[i];
+        for (int s2 = 0; s2 < 2; ++s2) {
+            f.pv[s2][i] = T(F.pv[s2][i]);
+            f.Ow[s2][i] = T(F.Ow[s2][i]);
+        }
+        for (int k = 0; k < 6; ++k) f.box[i][k] = T(F.box[i][k]);
+        f.head_x0[i] = T(S.head_x0[i]);
+        f.eye_x0[i] = T(S.eye_x0[i]);
+    }
+    for (int i = 0; i < 9; ++i) {
+        f.Mb[i] = T(F.Mb[i]);
+        f.Mw[0][i] = T(F.Mw[0][i]);
+        f.Mw[1][i] = T(F.Mw[1][i]);
+    }
+    f.h = T(S.h);
+    f.a = T(S.body_a);
+    f.b = T(S.body_b);
+    f.c_le = T(S.c_le);
+    f.c_te = T(S.c_te);
+    f.R = T(S.R);
+    f.ht = T(S.ht);
+    f.inv_eta = T(inv_eta);
+    f.body_type = S.body_type;
+    f.profile = S.profile;
+    f.wing_shape = S.wing_shape;
+    f.ncontour = S.ncontour;
+    f.head_r = T(S.head_r);
+    f.eye_r = T(S.eye_r);
+    f.cxc = T(S.contour_xc);
+    f.cyc = T(S.contour_yc);
+    f.ca0 = T(S.contour_a0);
+    for (int i = 0; i < FLUSI_MAX_CONTOUR; ++i) {
+        f.ca[i] = T(S.contour_a[i]);
+        f.cb[i] = T(S.contour_b[i]);
+    }
+    if (S.body_type == 0) f.active[0] = 0;
+    if (S.nwings < 1) f.active[1] = 0;
+    if (S.nwings < 2) f.active[2] = 0;
+}
+
+// Signed distance of the body in its frame (Sec. 3.2): thorax (sphere or
+// ellipsoid), joined with the head and eye spheres by the minimum.
+template <typename T>
+__device__ __forceinline__ T body_delta(const FrameT<T>& F, const T* xb)
+{
+    T delta;
+    if (F.body_type == 1) {
+        delta = sqrt(xb[0] * xb[0] + xb[1] * xb[1] + xb[2] * xb[2]) - F.a;
+    } else {
+        T rr = sqrt(xb[1] * xb[1] + xb[2] * xb[2]), ax = fabs(xb[0]);
+        if (ax <= F.a) {
+            T q = xb[0] / F.a;
+            delta = rr - F.b * sqrt(fmax(T(0), T(1) - q * q));
+        } else {
+            delta = sqrt(rr * rr + (ax - F.a) * (ax - F.a));
+        }
+        if (F.head_r > T(0)) {
+            const T e0 = xb[0] - F.head_x0[0], e1 = xb[1] - F.head_x0[1], e2 = xb[2] - F.head_x0[2];
+            delta = fmin(delta, sqrt(e0 * e0 + e1 * e1 + e2 * e2) - F.head_r);
+        }
+        if (F.eye_r > T(0)) {
+            for (int s = 0; s < 2; ++s) {
+                const T y0 = s == 0 ? F.eye_x0[1] : -F.eye_x0[1];
+                const T e0 = xb[0] - F.eye_x0[0], e1 = xb[1] - y0, e2 = xb[2] - F.eye_x0[2];
+                delta = fmin(delta, sqrt(e0 * e0 + e1 * e1 + e2 * e2) - F.eye_r);
+            }
+        }
+    }
+    return delta;
+}
+
+// Signed distance of a wing in its frame (Sec. 3.3): the rectangular plate,
+// or the contour R(theta) = a0/2 + sum a_i cos(i theta) + b_i sin(i theta)
+// with cos, sin of i theta from the angle-addition recurrence.
+template <typename T>
+__device__ __forceinline__ T wing_delta(const FrameT<T>& F, const T* xw)
+{
+    const T dz = fabs(xw[2]) - T(0.5) * F.ht;
+    if (F.wing_shape == 1) {
+        const T dx = xw[0] - F.cxc, dy = xw[1] - F.cyc;
+        const T r = sqrt(dx * dx + dy * dy);
+        const T c1 = r > T(0) ? dx / r : T(1), s1 = r > T(0) ? dy / r : T(0);
+        T R = T(0.5) * F.ca0, ci = c1, si = s1;
+        for (int i = 0; i < F.ncontour; ++i) {
+            R += F.ca[i] * ci + F.cb[i] * si;
+            const T cn = ci * c1 - si * s1;
+            si = si * c1 + ci * s1;
+            ci = cn;
+        }
+        return fmax(dz, r - R);
+    }
+    return fmax(fmax(xw[0] - F.c_le, -xw[0] - F.c_te), fmax(fmax(xw[1] - F.R, -xw[1]), dz));
+}
 
 template <typename T> __device__ __forceinline__ T profile_chi(int profile, T d, T h)
 {
@@ -63,21 +167,9 @@ __device__ __forceinline__ void solid_at(const FrameT<T>& F, const T* X, const b
     if (!(inrow[0] | inrow[1] | inrow[2])) return;
     T d[3] = {X[0] - F.xc[0], X[1] - F.xc[1], X[2] - F.xc[2]};
     if (inrow[0] && X[0] >= F.box[0][0] && X[0] <= F.box[0][1]) {
-        T delta;
-        if (F.body_type == 1) {
-            delta = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) - F.a;
-        } else {
-            T xb0 = F.Mb[0] * d[0] + F.Mb[1] * d[1] + F.Mb[2] * d[2];
-            T xb1 = F.Mb[3] * d[0] + F.Mb[4] * d[1] + F.Mb[5] * d[2];
-            T xb2 = F.Mb[6] * d[0] + F.Mb[7] * d[1] + F.Mb[8] * d[2];
-            T rr = sqrt(xb1 * xb1 + xb2 * xb2), ax = fabs(xb0);
-            if (ax <= F.a) {
-                T q = xb0 / F.a;
-                delta = rr - F.b * sqrt(fmax(T(0), T(1) - q * q));
-            } else {
-                delta = sqrt(rr * rr + (ax - F.a) * (ax - F.a));
-            }
-        }
+        T xb[3];
+        for (int i = 0; i < 3; ++i) xb[i] = F.Mb[3 * i] * d[0] + F.Mb[3 * i + 1] * d[1] + F.Mb[3 * i + 2] * d[2];
+        const T delta = body_delta(F, xb);
         T c = profile_chi(F.profile, delta, F.h);
         if (c > chi) {
             chi = c;
@@ -92,11 +184,9 @@ __device__ __forceinline__ void solid_at(const FrameT<T>& F, const T* X, const b
         if (!(inrow[1 + s] && X[0] >= F.box[1 + s][0] && X[0] <= F.box[1 + s][1])) continue;
         const T* M = F.Mw[s];
         T e[3] = {X[0] - F.pv[s][0], X[1] - F.pv[s][1], X[2] - F.pv[s][2]};
-        T xw0 = M[0] * e[0] + M[1] * e[1] + M[2] * e[2];
-        T xw1 = M[3] * e[0] + M[4] * e[1] + M[5] * e[2];
-        T xw2 = M[6] * e[0] + M[7] * e[1] + M[8] * e[2];
-        T delta = fmax(fmax(xw0 - F.c_le, -xw0 - F.c_te), fmax(fmax(xw1 - F.R, -xw1),
-                                                               fabs(xw2) - T(0.5) * F.ht));
+        T xw[3];
+        for (int i = 0; i < 3; ++i) xw[i] = M[3 * i] * e[0] + M[3 * i + 1] * e[1] + M[3 * i + 2] * e[2];
+        const T delta = wing_delta(F, xw);
         T c = profile_chi(F.profile, delta, F.h);
         if (c > chi) {
             chi = c;
@@ -292,41 +382,7 @@ k_xpass(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict
     load_tables<T>(tws, spos, tw, pos, nx, nh);
     if (kPhys) {
         for (int i = tid; i < kWarpsX * 36; i += kThreadsX) wacc[i] = 0.0;
-        if (tid == 0) {
-            const Frame& F = *ex.frame;
-            FrameT<T> f;
-            for (int i = 0; i < 3; ++i) {
-                f.xc[i] = T(F.xc[i]);
-                f.uc[i] = T(F.uc[i]);
-                f.Ob[i] = T(F.Ob[i]);
-                f.active[i] = F.active[i];
-                for (int s = 0; s < 2; ++s) {
-                    f.pv[s][i] = T(F.pv[s][i]);
-                    f.Ow[s][i] = T(F.Ow[s][i]);
-                }
-                for (int j = 0; j < 6; ++j) f.box[i][j] = T(F.box[i][j]);
-            }
-            for (int i = 0; i < 9; ++i) {
-                f.Mb[i] = T(F.Mb[i]);
-                f.Mw[0][i] = T(F.Mw[0][i]);
-                f.Mw[1][i] = T(F.Mw[1][i]);
-            }
-            const Shape& S = ex.shape;
-            f.h = T(S.h);
-            f.a = T(S.body_a);
-            f.b = T(S.body_b);
-            f.c_le = T(S.c_le);
-            f.c_te = T(S.c_te);
-            f.R = T(S.R);
-            f.ht = T(S.ht);
-            f.inv_eta = T(1.0 / g.eta);
-            f.body_type = S.body_type;
-            f.profile = S.profile;
-            if (S.body_type == 0) f.active[0] = 0;
-            if (S.nwings < 1) f.active[1] = 0;
-            if (S.nwings < 2) f.active[2] = 0;
-            *Fs = f;
-        }
+        if (tid == 0) setup_frame<T>(*Fs, *ex.frame, ex.shape, 1.0 / g.eta);
     }
     __syncthreads();
     for (int p = tid; p < nh; p += kThreadsX) ipos[spos[p]] = p;
@@ -665,41 +721,7 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
         tw2[i] = mkc<T>(T(w.x), T(w.y));
     }
     for (int i = tid; i < kWarpsX * 36; i += blockDim.x) wacc[i] = 0.0;
-    if (tid == 0) {
-        const Frame& F = *ex.frame;
-        FrameT<T> f;
-        for (int i = 0; i < 3; ++i) {
-            f.xc[i] = T(F.xc[i]);
-            f.uc[i] = T(F.uc[i]);
-            f.Ob[i] = T(F.Ob[i]);
-            f.active[i] = F.active[i];
-            for (int s2 = 0; s2 < 2; ++s2) {
-                f.pv[s2][i] = T(F.pv[s2][i]);
-                f.Ow[s2][i] = T(F.Ow[s2][i]);
-            }
-            for (int k = 0; k < 6; ++k) f.box[i][k] = T(F.box[i][k]);
-        }
-        for (int i = 0; i < 9; ++i) {
-            f.Mb[i] = T(F.Mb[i]);
-            f.Mw[0][i] = T(F.Mw[0][i]);
-            f.Mw[1][i] = T(F.Mw[1][i]);
-        }
-        const Shape& S = ex.shape;
-        f.h = T(S.h);
-        f.a = T(S.body_a);
-        f.b = T(S.body_b);
-        f.c_le = T(S.c_le);
-        f.c_te = T(S.c_te);
-        f.R = T(S.R);
-        f.ht = T(S.ht);
-        f.inv_eta = T(1.0 / g.eta);
-        f.body_type = S.body_type;
-        f.profile = S.profile;
-        if (S.body_type == 0) f.active[0] = 0;
-        if (S.nwings < 1) f.active[1] = 0;
-        if (S.nwings < 2) f.active[2] = 0;
-        *Fs = f;
-    }
+    if (tid == 0) setup_frame<T>(*Fs, *ex.frame, ex.shape, 1.0 / g.eta);
     __syncthreads();
 
     double e_acc = 0.0;
@@ -1161,10 +1183,10 @@ constexpr int kNoallocThreads = 256;
 constexpr int kNoallocWarps = kNoallocThreads / 32;
 constexpr int kNoallocMaxCtas = 1024;                       // partial-sum rows
 constexpr long long kNoallocMaxPoints = 1024LL * 1024 * 1024;
-constexpr int kNoallocHeader = 256;                         // doubles: descriptor, time, frame
+constexpr int kNoallocHeader = 512;                         // doubles: descriptor, time, frame
 
 // Scratch of the allocation-free entry point: [header | partials | sums],
-// 8 * (256 + 1024 * 40 + 40) bytes (about 330 KB), held by every GPU that
+// 8 * (512 + 1024 * 40 + 40) bytes (about 332 KB), held by every GPU that
 // loads the library until the process exits.
 constexpr size_t kNoallocDoubles = kNoallocHeader + (size_t)kNoallocMaxCtas * kNumSums + kNumSums;
 static __device__ __align__(256) double g_noalloc_scratch[kNoallocDoubles];
@@ -1191,38 +1213,7 @@ k_noalloc_sums(const double* __restrict__ u, int nx, int ny, int nz, double dx, 
     __shared__ double red[kNoallocWarps][3];
     const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
     for (int i = tid; i < kNoallocWarps * 36; i += kNoallocThreads) wacc[i] = 0.0;
-    if (tid == 0) {
-        const Frame& G = *frame;
-        for (int i = 0; i < 3; ++i) {
-            F.xc[i] = G.xc[i];
-            F.uc[i] = G.uc[i];
-            F.Ob[i] = G.Ob[i];
-            F.active[i] = G.active[i];
-            for (int s = 0; s < 2; ++s) {
-                F.pv[s][i] = G.pv[s][i];
-                F.Ow[s][i] = G.Ow[s][i];
-            }
-            for (int j = 0; j < 6; ++j) F.box[i][j] = G.box[i][j];
-        }
-        for (int i = 0; i < 9; ++i) {
-            F.Mb[i] = G.Mb[i];
-            F.Mw[0][i] = G.Mw[0][i];
-            F.Mw[1][i] = G.Mw[1][i];
-        }
-        F.h = S.h;
-        F.a = S.body_a;
-        F.b = S.body_b;
-        F.c_le = S.c_le;
-        F.c_te = S.c_te;
-        F.R = S.R;
-        F.ht = S.ht;
-        F.inv_eta = 0.0;
-        F.body_type = S.body_type;
-        F.profile = S.profile;
-        if (S.body_type == 0) F.active[0] = 0;
-        if (S.nwings < 1) F.active[1] = 0;
-        if (S.nwings < 2) F.active[2] = 0;
-    }
+    if (tid == 0) setup_frame<double>(F, *frame, S, 0.0);
     __syncthreads();
 
     const long long N = (long long)nx * ny * nz;
@@ -1400,18 +1391,7 @@ extern "C" int flusi_penalization_sums_noalloc(int nx, int ny, int nz, const dou
     if (insect) ins = *insect;
     const double dx = L[0] / nx, dy = L[1] / ny, dz = L[2] / nz;
     Shape sh{};
-    if (insect) {
-        sh.body_type = ins.body_type;
-        sh.nwings = ins.nwings;
-        sh.profile = ins.profile;
-        sh.h = ins.c_smth * fmax(dx, fmax(dy, dz));
-        sh.body_a = ins.body_a;
-        sh.body_b = ins.body_b;
-        sh.c_le = ins.wing_c_le;
-        sh.c_te = ins.wing_c_te;
-        sh.R = ins.wing_R;
-        sh.ht = ins.wing_h;
-    }
+    if (insect) sh = shape_of(ins, ins.c_smth * fmax(dx, fmax(dy, dz)));
     const double margin = sh.profile == 1 ? 1e300 : sh.h;
     // every slot read below is written first in this call: nothing carried
     // over from an earlier call needs clearing

@@ -115,7 +115,8 @@ def test_insect_descriptor_validation(fl):
 def test_struct_layouts_match_header(fl):
     """The ctypes mirrors have the sizes the C compiler gives the structs."""
     assert C.sizeof(fl.Options) == 3 * 8 + 3 * 8 + 4 * 4 + 7 * 8 + 2 * 4
-    assert C.sizeof(fl.Insect) == 4 * 4 + 8 * (1 + 3 + 3 + 6 + 2 + 3 + 3 + 1 + 4 + 1 + 3 * 17)
+    assert C.sizeof(fl.Insect) == (4 * 4 + 8 * (1 + 3 + 3 + 6 + 2 + 3 + 3 + 1 + 4 + 1 + 3 * 17)
+                                   + 8 * (3 + 1 + 3 + 1) + 2 * 4 + 8 * (3 + 2 * 32))
 
 
 def test_kernels_per_step(fl):

@@ -187,6 +187,34 @@ def model_insect(L=(4.0, 4.0, 4.0), n=(512, 512, 512)):
             "kinematics": flapping_kinematics()}
 
 
+def contour_wing_outline(span=0.96, chord=0.3, harmonics=16):
+    """A synthetic wing outline for the contour parametrization of Sec. 3.3:
+    an ellipse of the given span and chord centred at mid-span on the y^(w)
+    axis, with a slight forward sweep of the tip, written as the truncated
+    Fourier series R(theta) = a0/2 + sum a_i cos(i theta) + b_i sin(i theta)
+    (coefficients from 256 samples of the outline; made-up geometry, not
+    measured wing data)."""
+    a, b, sweep = 0.5 * chord, 0.5 * span, 0.04
+    th = 2 * math.pi * np.arange(256) / 256
+    R = a * b / np.sqrt((b * np.cos(th)) ** 2 + (a * np.sin(th)) ** 2)
+    R = R * (1.0 + sweep * np.sin(th) * np.cos(th))
+    F = np.fft.rfft(R) / 256
+    return {"center": (0.0, 0.5 * span + 0.02),
+            "a0": float(2 * F[0].real),
+            "a": [float(2 * F[i].real) for i in range(1, harmonics + 1)],
+            "b": [float(-2 * F[i].imag) for i in range(1, harmonics + 1)]}
+
+
+def realistic_insect(L=(4.0, 4.0, 4.0), n=(512, 512, 512)):
+    """Ellipsoid thorax with a head and two eyes (Sec. 3.2) and two contour
+    wings (Sec. 3.3) with the flapping kinematics of the model insect."""
+    ins = model_insect(L, n)
+    ins["head"] = ((0.62, 0.0, 0.04), 0.13)
+    ins["eyes"] = ((0.66, 0.09, 0.08), 0.06)
+    ins["contour"] = contour_wing_outline()
+    return ins
+
+
 # ------------------------------------------------------------ configurations
 
 def config_tg_sphere(n=32):
