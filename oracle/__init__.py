@@ -21,7 +21,7 @@ _SOURCES = ["fft.c", "insect.c", "solver.c"]
 
 MAX_FOURIER = 8
 MAX_CONTOUR = 32
-ROW_COLS = 22
+ROW_COLS = 26
 NSUMS = 39
 SUM_EKIN, SUM_UMAX, SUM_NONFINITE = 36, 37, 38
 
@@ -75,21 +75,28 @@ class Insect(C.Structure):
                 ("wing_shape", C.c_int), ("ncontour", C.c_int),
                 ("contour_xc", C.c_double), ("contour_yc", C.c_double),
                 ("contour_a0", C.c_double), ("contour_a", C.c_double * MAX_CONTOUR),
-                ("contour_b", C.c_double * MAX_CONTOUR)]
+                ("contour_b", C.c_double * MAX_CONTOUR),
+                ("J_wing", C.c_double * 6),
+                ("free_flight", C.c_int), ("pad3_", C.c_int),
+                ("mass", C.c_double), ("gravity", C.c_double), ("J_body", C.c_double * 3),
+                ("dof", C.c_double * 6), ("quat", C.c_double * 4), ("Omega_body", C.c_double * 3)]
 
 
 class Scalars(C.Structure):
     _fields_ = [("t", C.c_double), ("dt_prev", C.c_double), ("n", C.c_int64),
-                ("Is_prev", (C.c_double * 3) * 3), ("Js_prev", (C.c_double * 3) * 3)]
+                ("Is_prev", (C.c_double * 3) * 3), ("Js_prev", (C.c_double * 3) * 3),
+                ("body_rhs_prev", C.c_double * 13)]
 
 
 class Frames(C.Structure):
     _fields_ = [("M_body", C.c_double * 9), ("Omega_b_g", C.c_double * 3),
                 ("M_stroke", (C.c_double * 9) * 2), ("M_wing", (C.c_double * 9) * 2),
                 ("Omega_w_b", (C.c_double * 3) * 2), ("Omega_w_w", (C.c_double * 3) * 2),
+                ("dOmega_w_w", (C.c_double * 3) * 2),
                 ("pivot_g", (C.c_double * 3) * 2),
                 ("phi", C.c_double), ("alpha", C.c_double), ("theta", C.c_double),
-                ("phi_dot", C.c_double), ("alpha_dot", C.c_double), ("theta_dot", C.c_double)]
+                ("phi_dot", C.c_double), ("alpha_dot", C.c_double), ("theta_dot", C.c_double),
+                ("phi_ddot", C.c_double), ("alpha_ddot", C.c_double), ("theta_ddot", C.c_double)]
 
 
 _lib = None
@@ -133,6 +140,9 @@ def lib():
         L.orc_body_distance.restype = C.c_double
         L.orc_wing_distance.argtypes = [C.POINTER(Insect), _dp]
         L.orc_wing_distance.restype = C.c_double
+        L.orc_quat_from_angles.argtypes = [C.c_double, C.c_double, C.c_double, C.POINTER(C.c_double)]
+        L.orc_body_rhs.argtypes = [C.POINTER(Insect), _dp, _dp, _dp]
+        L.orc_wing_power.argtypes = [C.POINTER(Insect), C.POINTER(Frames), _dp, _dp, _dp]
         L.orc_rhs.argtypes = [C.POINTER(Params), C.POINTER(Insect), C.c_double, _cp, _cp, _dp]
         L.orc_rhs.restype = C.c_int
         L.orc_physical_fields.argtypes = [C.POINTER(Params), C.POINTER(Insect), C.c_double, _cp,
@@ -200,6 +210,18 @@ def make_insect(d: dict | None) -> Insect | None:
         s.head_x0[:], s.head_r = d["head"]
     if "eyes" in d:
         s.eye_x0[:], s.eye_r = d["eyes"]
+    if "J_wing" in d:
+        s.J_wing[:] = d["J_wing"]
+    if "free_flight" in d:
+        ff = d["free_flight"]
+        s.free_flight = 1
+        s.mass, s.gravity = ff["mass"], ff.get("gravity", 0.0)
+        s.J_body[:] = ff["J_body"]
+        s.dof[:] = ff.get("dof", (1.0,) * 6)
+        s.Omega_body[:] = ff.get("Omega_body", (0.0, 0.0, 0.0))
+        eps = (C.c_double * 4)()
+        lib().orc_quat_from_angles(s.psi, s.beta, s.gamma, eps)
+        s.quat[:] = eps[:]
     if "contour" in d:
         c = d["contour"]
         s.wing_shape = 1
@@ -266,6 +288,7 @@ def frames(insect: dict, t: float) -> dict:
         "M_wing": [m(fr.M_wing[i]) for i in range(2)],
         "Omega_w_b": [np.array(fr.Omega_w_b[i][:]) for i in range(2)],
         "Omega_w_w": [np.array(fr.Omega_w_w[i][:]) for i in range(2)],
+        "dOmega_w_w": [np.array(fr.dOmega_w_w[i][:]) for i in range(2)],
         "pivot_g": [np.array(fr.pivot_g[i][:]) for i in range(2)],
         "angles": (fr.phi, fr.alpha, fr.theta),
         "rates": (fr.phi_dot, fr.alpha_dot, fr.theta_dot),
@@ -399,6 +422,8 @@ class Simulation:
             row = np.zeros(ROW_COLS)
             rc = lib().orc_step(C.byref(self.p), _ins_ptr(self.ins), self.uh, self.nh_prev,
                                 C.byref(self.s), row)
+            if rc == 2:
+                raise ValueError("oracle: free flight runs with the AB2 scheme only")
             if rc != 0:
                 raise FloatingPointError("oracle: non-finite value in the step")
             self.rows.append(row)
@@ -421,3 +446,35 @@ def body_distance(insect: dict, xb):
 def wing_distance(insect: dict, xw):
     """Signed distance of a wing at a wing-frame point (Sec. 3.3)."""
     return lib().orc_wing_distance(C.byref(make_insect(insect)), np.ascontiguousarray(xw, np.float64))
+
+
+def quat_from_angles(psi, beta, gamma):
+    """Initial free-flight quaternion of the yaw, pitch and roll angles (Sec. 3.5)."""
+    eps = (C.c_double * 4)()
+    lib().orc_quat_from_angles(psi, beta, gamma, eps)
+    return np.array(eps[:])
+
+
+def body_rhs(insect: dict, F, m_b, state=None):
+    """Right-hand side of the 13 free-flight equations for a descriptor whose
+    body state is `state` = (x, u, quat, Omega) or the descriptor's own."""
+    ins = make_insect(insect)
+    if state is not None:
+        x, u, q, w = state
+        ins.x_cntr[:], ins.u_cntr[:], ins.quat[:], ins.Omega_body[:] = x, u, q, w
+    f = np.zeros(13)
+    lib().orc_body_rhs(C.byref(ins), np.ascontiguousarray(F, np.float64),
+                       np.ascontiguousarray(m_b, np.float64), f)
+    return f
+
+
+def wing_power(insect: dict, t: float, row=None):
+    """(P_aero[2], P_inert[2]) of the wings at time t (Sec. 3.4) for a force row
+    (zeros if none: only the inertial power is then meaningful)."""
+    ins = make_insect(insect)
+    fr = Frames()
+    lib().orc_frames_at(C.byref(ins), t, C.byref(fr))
+    r = np.zeros(ROW_COLS) if row is None else np.ascontiguousarray(row, np.float64)
+    pa, pi = np.zeros(2), np.zeros(2)
+    lib().orc_wing_power(C.byref(ins), C.byref(fr), r, pa, pi)
+    return pa, pi

@@ -90,16 +90,100 @@ static void cross(const double *a, const double *b, double *c)
 }
 
 static void fourier_series(double a0, const double *a, const double *b, int nf,
-                           double f, double t, double *val, double *dval)
+                           double f, double t, double *val, double *dval, double *ddval)
 {
-    double v = 0.5 * a0, dv = 0;
+    double v = 0.5 * a0, dv = 0, ddv = 0;
     for (int i = 1; i <= nf; ++i) {
         double w = 2.0 * PI * i * f;
         v += a[i - 1] * cos(w * t) + b[i - 1] * sin(w * t);
         dv += w * (-a[i - 1] * sin(w * t) + b[i - 1] * cos(w * t));
+        ddv -= w * w * (a[i - 1] * cos(w * t) + b[i - 1] * sin(w * t));
     }
     *val = v;
     *dval = dv;
+    *ddval = ddv;
+}
+
+/* Derivatives of the passive rotations R_y, R_z with respect to the angle. */
+static void rot_y_d(double xi, double *R)
+{
+    double c = cos(xi), s = sin(xi);
+    double M[9] = {-s, 0, -c, 0, 0, 0, c, 0, -s};
+    memcpy(R, M, sizeof M);
+}
+
+static void rot_z_d(double xi, double *R)
+{
+    double c = cos(xi), s = sin(xi);
+    double M[9] = {-s, c, 0, -c, -s, 0, 0, 0, 0};
+    memcpy(R, M, sizeof M);
+}
+
+/* Free-flight orientation (Sec. 3.5): the printed quaternion matrix maps body
+ * to global coordinates, the transpose of M_body of Eq. M_body_yawpitchroll
+ * (with the printed initial quaternion of (psi, beta, gamma) the two agree). */
+static void quat_body_to_global(const double *e, double *R)
+{
+    double e0 = e[0], e1 = e[1], e2 = e[2], e3 = e[3];
+    double M[9] = {e0 * e0 + e1 * e1 - e2 * e2 - e3 * e3, 2 * (e1 * e2 - e3 * e0), 2 * (e1 * e3 + e2 * e0),
+                   2 * (e1 * e2 + e3 * e0), e0 * e0 - e1 * e1 + e2 * e2 - e3 * e3, 2 * (e2 * e3 - e1 * e0),
+                   2 * (e1 * e3 - e2 * e0), 2 * (e2 * e3 + e1 * e0), e0 * e0 - e1 * e1 - e2 * e2 + e3 * e3};
+    memcpy(R, M, sizeof M);
+}
+
+void orc_quat_from_angles(double psi, double beta, double gamma, double *eps)
+{
+    double cp = cos(0.5 * psi), sp = sin(0.5 * psi), cb = cos(0.5 * beta), sb = sin(0.5 * beta);
+    double cg = cos(0.5 * gamma), sg = sin(0.5 * gamma);
+    eps[0] = cp * cb * cg + sp * sb * sg;
+    eps[1] = sp * cb * cg - cp * sb * sg;
+    eps[2] = cp * sb * cg + sp * cb * sg;
+    eps[3] = cp * cb * sg - sp * sb * cg;
+}
+
+/* Right-hand side of the 13 free-flight equations (Eq. oh_my_god_look_a_vector)
+ * for the state in the descriptor: F the total aerodynamic force (global),
+ * m_b the total aerodynamic moment about x_cntr in the body frame.  The six
+ * dof flags multiply the accelerations. */
+void orc_body_rhs(const orc_insect *ins, const double *F, const double *m_b, double *f)
+{
+    const double *e = ins->quat, *W = ins->Omega_body, *J = ins->J_body;
+    for (int i = 0; i < 3; ++i) f[i] = ins->u_cntr[i];
+    f[3] = ins->dof[0] * F[0] / ins->mass;
+    f[4] = ins->dof[1] * F[1] / ins->mass;
+    f[5] = ins->dof[2] * (F[2] / ins->mass - ins->gravity);
+    f[6] = 0.5 * (-e[1] * W[0] - e[2] * W[1] - e[3] * W[2]);
+    f[7] = 0.5 * (e[0] * W[0] - e[3] * W[1] + e[2] * W[2]);
+    f[8] = 0.5 * (e[3] * W[0] + e[0] * W[1] - e[1] * W[2]);
+    f[9] = 0.5 * (-e[2] * W[0] + e[1] * W[1] + e[0] * W[2]);
+    f[10] = ins->dof[3] * ((J[1] - J[2]) * W[1] * W[2] + m_b[0]) / J[0];
+    f[11] = ins->dof[4] * ((J[2] - J[0]) * W[2] * W[0] + m_b[1]) / J[1];
+    f[12] = ins->dof[5] * ((J[0] - J[1]) * W[0] * W[1] + m_b[2]) / J[2];
+}
+
+/* Power of each wing (Sec. 3.4, Eq. insect_power): aerodynamic
+ * P = -m . (Omega_w - Omega_b) with the wing's moment about its pivot (force
+ * row) and its rotation rate relative to the body in the global frame;
+ * inertial P = Omega^(w) . (J Omega'^(w) + Omega^(w) x J Omega^(w)). */
+void orc_wing_power(const orc_insect *ins, const orc_frames *fr, const double *row, double *p_aero,
+                    double *p_inert)
+{
+    const double *J6 = ins->J_wing;
+    const double J[9] = {J6[0], J6[3], J6[4], J6[3], J6[1], J6[5], J6[4], J6[5], J6[2]};
+    for (int s = 0; s < 2; ++s) {
+        p_aero[s] = p_inert[s] = 0.0;
+        if (s >= ins->nwings) continue;
+        double wg[3];
+        mat_tvec(fr->M_body, fr->Omega_w_b[s], wg);
+        const double *m = row + 2 + (1 + s) * 6 + 3;
+        p_aero[s] = -(m[0] * wg[0] + m[1] * wg[1] + m[2] * wg[2]);
+        const double *w = fr->Omega_w_w[s], *dw = fr->dOmega_w_w[s];
+        double Jw[3], Jdw[3], c[3];
+        mat_vec(J, w, Jw);
+        mat_vec(J, dw, Jdw);
+        cross(w, Jw, c);
+        p_inert[s] = w[0] * (Jdw[0] + c[0]) + w[1] * (Jdw[1] + c[1]) + w[2] * (Jdw[2] + c[2]);
+    }
 }
 
 void orc_frames_at(const orc_insect *ins, double t, orc_frames *fr)
@@ -107,31 +191,40 @@ void orc_frames_at(const orc_insect *ins, double t, orc_frames *fr)
     double Rx[9], Ry[9], Rz[9], v[3];
     memset(fr, 0, sizeof *fr);
 
-    /* Body frame, Eq. M_body_yawpitchroll: yaw, then pitch, then roll. */
-    orc_rot_x(ins->psi, Rx);
-    orc_rot_y(ins->beta, Ry);
-    orc_rot_z(ins->gamma, Rz);
-    mat_mul(Rx, Ry, fr->M_body);
-    mat_mul(fr->M_body, Rz, fr->M_body);
+    if (ins->free_flight) {
+        /* Sec. 3.5: orientation from the quaternion, Omega^(b) from the state */
+        double Rq[9];
+        quat_body_to_global(ins->quat, Rq);
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) fr->M_body[3 * i + j] = Rq[3 * j + i];
+        mat_tvec(fr->M_body, ins->Omega_body, fr->Omega_b_g);
+    } else {
+        /* Body frame, Eq. M_body_yawpitchroll: yaw, then pitch, then roll. */
+        orc_rot_x(ins->psi, Rx);
+        orc_rot_y(ins->beta, Ry);
+        orc_rot_z(ins->gamma, Rz);
+        mat_mul(Rx, Ry, fr->M_body);
+        mat_mul(fr->M_body, Rz, fr->M_body);
 
-    /* Body angular velocity in the global frame (Sec. 3.1, nested form). */
-    double e_psi[3] = {ins->psi_dot, 0, 0};
-    double e_beta[3] = {0, ins->beta_dot, 0};
-    double e_gamma[3] = {0, 0, ins->gamma_dot};
-    mat_tvec(Rx, e_psi, v);
-    for (int i = 0; i < 3; ++i) v[i] += e_beta[i];
-    mat_tvec(Ry, v, v);
-    for (int i = 0; i < 3; ++i) v[i] += e_gamma[i];
-    mat_tvec(Rz, v, fr->Omega_b_g);
+        /* Body angular velocity in the global frame (Sec. 3.1, nested form). */
+        double e_psi[3] = {ins->psi_dot, 0, 0};
+        double e_beta[3] = {0, ins->beta_dot, 0};
+        double e_gamma[3] = {0, 0, ins->gamma_dot};
+        mat_tvec(Rx, e_psi, v);
+        for (int i = 0; i < 3; ++i) v[i] += e_beta[i];
+        mat_tvec(Ry, v, v);
+        for (int i = 0; i < 3; ++i) v[i] += e_gamma[i];
+        mat_tvec(Rz, v, fr->Omega_b_g);
+    }
 
     /* Wing angles from their Fourier coefficients (Sec. 3.3). */
     int nf = ins->nfourier;
     fourier_series(ins->phi_a0, ins->phi_a, ins->phi_b, nf, ins->freq, t,
-                   &fr->phi, &fr->phi_dot);
+                   &fr->phi, &fr->phi_dot, &fr->phi_ddot);
     fourier_series(ins->alpha_a0, ins->alpha_a, ins->alpha_b, nf, ins->freq, t,
-                   &fr->alpha, &fr->alpha_dot);
+                   &fr->alpha, &fr->alpha_dot, &fr->alpha_ddot);
     fourier_series(ins->theta_a0, ins->theta_a, ins->theta_b, nf, ins->freq, t,
-                   &fr->theta, &fr->theta_dot);
+                   &fr->theta, &fr->theta_dot, &fr->theta_ddot);
 
     for (int s = 0; s < 2; ++s) {
         double sg = s == 0 ? 1.0 : -1.0;
@@ -169,6 +262,35 @@ void orc_frames_at(const orc_insect *ins, double t, orc_frames *fr)
         /* Omega_w^(w) = M_wing M_stroke Omega_w^(b). */
         mat_vec(fr->M_stroke[s], fr->Omega_w_b[s], v);
         mat_vec(fr->M_wing[s], v, fr->Omega_w_w[s]);
+
+        /* its time derivative: Omega^(w) = e_alpha + Ra e_theta + Ra Rt e_phi, so
+         * d/dt = e_alpha' + Ra' e_theta + Ra e_theta' + (Ra' Rt + Ra Rt') e_phi
+         * + Ra Rt e_phi' with Ra' = alpha' dR_y, Rt' = -theta' dR_z */
+        {
+            double alphadd = sg * fr->alpha_ddot, phidd = sg * fr->phi_ddot, thetadd = fr->theta_ddot;
+            double dRa[9], dRt[9], A[9], B[9], t1[3], t2[3], t3[3];
+            rot_y_d(alpha, dRa);
+            rot_z_d(-theta, dRt);
+            for (int i = 0; i < 9; ++i) {
+                dRa[i] *= alphad;
+                dRt[i] *= -thetad;
+            }
+            double d_theta[3] = {0, 0, -thetadd}, d_phi[3] = {phidd, 0, 0};
+            double *out = fr->dOmega_w_w[s];
+            out[0] = 0;
+            out[1] = alphadd;
+            out[2] = 0;
+            mat_vec(dRa, e_theta, t1);
+            mat_vec(Ra, d_theta, t2);
+            mat_mul(dRa, Rt, A);
+            mat_mul(Ra, dRt, B);
+            for (int i = 0; i < 9; ++i) A[i] += B[i];
+            mat_vec(A, e_phi, t3);
+            for (int i = 0; i < 3; ++i) out[i] += t1[i] + t2[i] + t3[i];
+            mat_mul(Ra, Rt, A);
+            mat_vec(A, d_phi, t1);
+            for (int i = 0; i < 3; ++i) out[i] += t1[i];
+        }
 
         /* Pivot in the global frame: x_cntr + M_body^-1 x_pivot^(b). */
         const double *pb = s == 0 ? ins->pivot_l : ins->pivot_r;

@@ -26,7 +26,8 @@
 #define ORC_MAX_FOURIER 8
 #define ORC_MAX_CONTOUR 32   /* harmonics of a wing contour R(theta)     */
 #define ORC_NCOLOURS 3   /* 1 = body, 2 = left wing, 3 = right wing */
-#define ORC_ROW_COLS 22  /* t, dt, {F[3], M[3]} x 3 colours, E_kin, u_max */
+#define ORC_ROW_COLS 26  /* t, dt, {F[3], M[3]} x 3 colours, E_kin, u_max,
+                            P_aero (left, right wing), P_inert (left, right) */
 
 typedef struct {
     int nx, ny, nz;
@@ -80,6 +81,19 @@ typedef struct {
     int ncontour;
     double contour_xc, contour_yc;
     double contour_a0, contour_a[ORC_MAX_CONTOUR], contour_b[ORC_MAX_CONTOUR];
+    /* Wing tensor of inertia in the wing frame (xx, yy, zz, xy, xz, yz) for
+     * the inertial power (Sec. 3.4). */
+    double J_wing[6];
+    /* Free flight (Sec. 3.5): 0 = tethered (the body moves as the fields
+     * above prescribe); 1 = x_cntr, u_cntr, quat and Omega_body are the state
+     * of the Newton-Euler system, advanced by each step. */
+    int free_flight;
+    int pad3_;
+    double mass, gravity;       /* M and g (gravity along -z)                    */
+    double J_body[3];           /* principal moments of inertia, body axes        */
+    double dof[6];              /* 1/0 on du_x, du_y, du_z, dOmega_x, dOmega_y, dOmega_z */
+    double quat[4];             /* orientation epsilon_0..3 (free flight)         */
+    double Omega_body[3];       /* Omega^(b) (free flight)                        */
 } orc_insect;
 
 /* Time-level data of the AB2 scheme besides the two spectral fields. */
@@ -89,6 +103,7 @@ typedef struct {
     int64_t n;
     double Is_prev[ORC_NCOLOURS][3];   /* sum chi u_s dV per colour          */
     double Js_prev[ORC_NCOLOURS][3];   /* sum r x chi u_s dV per colour      */
+    double body_rhs_prev[13];          /* free flight: previous ODE right-hand side */
 } orc_scalars;
 
 /* Frames of Sec. 3 evaluated at one instant (for the pins). */
@@ -97,8 +112,10 @@ typedef struct {
     double Omega_b_g[3];
     double M_stroke[2][9], M_wing[2][9];
     double Omega_w_b[2][3], Omega_w_w[2][3];
+    double dOmega_w_w[2][3];           /* time derivative of Omega_w^(w)    */
     double pivot_g[2][3];
     double phi, alpha, theta, phi_dot, alpha_dot, theta_dot;
+    double phi_ddot, alpha_ddot, theta_ddot;
 } orc_frames;
 
 /* ---- FFT (own code; no library) ---- */
@@ -112,6 +129,10 @@ void orc_rot_x(double xi, double *R);
 void orc_rot_y(double xi, double *R);
 void orc_rot_z(double xi, double *R);
 void orc_frames_at(const orc_insect *ins, double t, orc_frames *fr);
+void orc_quat_from_angles(double psi, double beta, double gamma, double *eps);
+void orc_body_rhs(const orc_insect *ins, const double *F, const double *m_b, double *f);
+void orc_wing_power(const orc_insect *ins, const orc_frames *fr, const double *row, double *p_aero,
+                    double *p_inert);
 double orc_mask_profile(int profile, double delta, double h);
 double orc_body_distance(const orc_insect *ins, const double *xb);
 double orc_wing_distance(const orc_insect *ins, const double *xw);
@@ -146,7 +167,7 @@ void orc_rk4_combine(const orc_params *p, double complex *uh, const double compl
 void orc_ab2_update(const orc_params *p, double complex *uh,
                     const double complex *nh, const double complex *nh_prev,
                     double dt, double dt_prev, int64_t n);
-int orc_step(const orc_params *p, const orc_insect *ins, double complex *uh,
+int orc_step(const orc_params *p, orc_insect *ins, double complex *uh,
              double complex *nh_prev, orc_scalars *s, double *row);
 
 /* Layout of the sums written by orc_rhs (doubles). */

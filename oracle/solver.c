@@ -413,9 +413,10 @@ static double k2_max(const orc_params *p)
 }
 
 /* One step of Algorithm 1 (without free flight and output). */
-int orc_step(const orc_params *p, const orc_insect *ins, double complex *uh,
+int orc_step(const orc_params *p, orc_insect *ins, double complex *uh,
              double complex *nh_prev, orc_scalars *s, double *row)
 {
+    if (ins && ins->free_flight && p->time_scheme == 1) return 2;   /* free flight is AB2 only */
     long nhs = n_half(p);
     double complex *nh = malloc(sizeof(double complex) * (size_t)(3 * nhs));
     double sums[ORC_NSUMS];
@@ -488,6 +489,58 @@ int orc_step(const orc_params *p, const orc_insect *ins, double complex *uh,
         }
     row[20] = sums[ORC_SUM_EKIN];
     row[21] = sums[ORC_SUM_UMAX];
+
+    /* power of the wings at t^n (Sec. 3.4) */
+    orc_frames fr;
+    if (ins) orc_frames_at(ins, s->t, &fr);
+    row[22] = row[23] = row[24] = row[25] = 0.0;
+    if (ins) orc_wing_power(ins, &fr, row, row + 22, row + 24);
+
+    /* free flight (Sec. 3.5): the body state advances with the fluid's AB2
+     * (same dt and ratio, Euler on the first step); the quaternion is
+     * renormalized after each step (a reading).  Force: all colours; moment:
+     * about x_cntr, the wings' moments moved from their pivots. */
+    if (ins && ins->free_flight) {
+        double F[3] = {0, 0, 0}, m[3] = {0, 0, 0}, mb[3], f[13], y[13];
+        for (int c = 0; c < ORC_NCOLOURS; ++c)
+            for (int i = 0; i < 3; ++i) {
+                F[i] += row[2 + 6 * c + i];
+                m[i] += row[2 + 6 * c + 3 + i];
+            }
+        for (int w = 0; w < 2 && w < ins->nwings; ++w) {
+            const double *Fw = row + 2 + 6 * (1 + w);
+            double r[3] = {fr.pivot_g[w][0] - ins->x_cntr[0], fr.pivot_g[w][1] - ins->x_cntr[1],
+                           fr.pivot_g[w][2] - ins->x_cntr[2]};
+            m[0] += r[1] * Fw[2] - r[2] * Fw[1];
+            m[1] += r[2] * Fw[0] - r[0] * Fw[2];
+            m[2] += r[0] * Fw[1] - r[1] * Fw[0];
+        }
+        for (int i = 0; i < 3; ++i)
+            mb[i] = fr.M_body[3 * i] * m[0] + fr.M_body[3 * i + 1] * m[1] + fr.M_body[3 * i + 2] * m[2];
+        orc_body_rhs(ins, F, mb, f);
+        for (int i = 0; i < 3; ++i) {
+            y[i] = ins->x_cntr[i];
+            y[3 + i] = ins->u_cntr[i];
+            y[10 + i] = ins->Omega_body[i];
+        }
+        for (int i = 0; i < 4; ++i) y[6 + i] = ins->quat[i];
+        for (int i = 0; i < 13; ++i) {
+            if (s->n == 0) {
+                y[i] += dt * f[i];
+            } else {
+                double r = dt / s->dt_prev;
+                y[i] += dt * ((1.0 + 0.5 * r) * f[i] - 0.5 * r * s->body_rhs_prev[i]);
+            }
+            s->body_rhs_prev[i] = f[i];
+        }
+        double qn = sqrt(y[6] * y[6] + y[7] * y[7] + y[8] * y[8] + y[9] * y[9]);
+        for (int i = 0; i < 3; ++i) {
+            ins->x_cntr[i] = y[i];
+            ins->u_cntr[i] = y[3 + i];
+            ins->Omega_body[i] = y[10 + i];
+        }
+        for (int i = 0; i < 4; ++i) ins->quat[i] = y[6 + i] / qn;
+    }
 
     memcpy(nh_prev, nh, sizeof(double complex) * (size_t)(3 * nhs));
     s->t += dt;
