@@ -16,6 +16,7 @@ Under torchrun (N > 1) every rank runs an independent replica on its own GPU
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import math
 import os
@@ -52,6 +53,9 @@ def parse():
     ap.add_argument("--wake", action="store_true",
                     help="add the wake-removal terms: a vorticity sponge (C_sp 0.1) 32 grid "
                          "points deep at the x and y ends and a Dirichlet layer 4 points deep at the x end")
+    ap.add_argument("--flight", action="store_true",
+                    help="free flight (Sec. 3.5) with the power columns: the body state advances "
+                         "every step (mass 400, J_body (2, 5, 5), g 9.81, wing J set)")
     ap.add_argument("--shape", default=None,
                     help="nx,ny,nz: a reduced grid of the same box and insect (profiling)")
     ap.add_argument("--fp64-steps", type=int, default=10)
@@ -141,6 +145,10 @@ def workload_setup(args):
         ins = workloads.model_insect(cfg["L"], shape)
     if args.rk4:
         cfg = dict(cfg, time_scheme="rk4")
+    if args.flight:
+        if args.rk4:
+            raise SystemExit("free flight runs with the AB2 scheme only")
+        ins = in_free_flight(ins)
     if args.wake:
         d = [cfg["L"][i] / cfg["n"][i] for i in range(3)]
         cfg = dict(cfg, sponge_c=0.1, sponge_width=(32 * d[0], 32 * d[1], 0.0),
@@ -214,7 +222,15 @@ class Clocks:
 
 # --------------------------------------------------------------- CPU oracle
 
-def oracle_workload(workload, n):
+def in_free_flight(ins):
+    """The insect in free flight (Sec. 3.5) with a wing tensor of inertia for
+    the power columns; heavy enough that the impulsive start in the inflow
+    moves it by a fraction of its length over a few hundred steps."""
+    return dict(ins, J_wing=(2e-2, 1e-3, 2e-2, 1e-4, 0.0, 0.0),
+                free_flight={"mass": 400.0, "gravity": 9.81, "J_body": (2.0, 5.0, 5.0)})
+
+
+def oracle_workload(workload, n, flight=False):
     """The workload at a reduced grid n^3 for the oracle: (cfg, insect, u0 FP64)."""
     if workload == "turbulent_insect":
         cfg, ins = workloads.config_turbulent_insect(n)
@@ -222,14 +238,14 @@ def oracle_workload(workload, n):
     else:
         cfg, ins = workloads.config_model_insect(n)
         u0 = workloads.shear_waves(cfg["n"], cfg["L"], mean=cfg["u_inf"])
-    return cfg, ins, u0
+    return cfg, in_free_flight(ins) if flight else ins, u0
 
 
-def oracle_sample(workload, n_sample=128, steps=3):
+def oracle_sample(workload, n_sample=128, steps=3, flight=False):
     """The oracle (single-threaded C, FP64) on the same workload at a reduced
     grid, as it stands: grid-point steps/s."""
     import oracle
-    cfg, ins, u0 = oracle_workload(workload, n_sample)
+    cfg, ins, u0 = oracle_workload(workload, n_sample, flight)
     sim = oracle.Simulation(cfg, ins)
     sim.set_state(u0)
     t0 = time.perf_counter()
@@ -355,7 +371,8 @@ def run_flusi(args):
     t0 = time.perf_counter()
     fl.flusi_set_state(sim.h, host_in, fl.FLUSI_HOST_FP32)
     for _ in range(e2e_steps):
-        fl.flusi_set_kinematics(sim.h, sim.insect)
+        if not args.flight:      # in free flight the body state lives on the device
+            fl.flusi_set_kinematics(sim.h, sim.insect)
         fl.flusi_step(sim.h, 1)
         rows, _ = fl.flusi_forces(sim.h, 4)
         rows_total += rows.shape[0]
@@ -365,8 +382,9 @@ def run_flusi(args):
     e2e_s = allmax(e2e_s)
     state_bytes = host_in.nbytes
     e2e = {"value": whole_job_rate(N, e2e_steps, world, e2e_s * 1e3), "unit": UNIT, "steps": e2e_steps,
-           "h2d_bytes_per_step": (state_bytes + e2e_steps * 1536) / e2e_steps,
-           "d2h_bytes_per_step": (state_bytes + e2e_steps * 22 * 8) / e2e_steps,
+           "h2d_bytes_per_step": (state_bytes + (0 if args.flight else e2e_steps * ctypes.sizeof(fl.Insect)))
+                                 / e2e_steps,
+           "d2h_bytes_per_step": (state_bytes + e2e_steps * fl.FORCE_COLS * 8) / e2e_steps,
            "what": "set_state from pinned host FP32, per step set_kinematics (H2D) + step + "
                    "force-row drain (D2H), get_state to pinned host FP32"}
     sim.close()
@@ -410,13 +428,13 @@ def run_flusi(args):
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = oracle_sample(args.workload)
+        cpu = oracle_sample(args.workload, flight=args.flight)
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": workload_config(cfg["n"], world, args.workload, args.wake),
+        "config": workload_config(cfg["n"], world, args.workload, args.wake, args.flight),
         "roofline": roofline,
         "stage_model": {"bytes_per_step": stage, "frac_of_peak": round(stage / (ms_per_step * 1e-3) / 1e9 / hbm, 4),
                         "frac_of_nominal_8TBs": round(stage / (ms_per_step * 1e-3) / 8e12, 4),
@@ -447,7 +465,7 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
-def workload_config(n, world, workload="model_insect", wake=False):
+def workload_config(n, world, workload="model_insect", wake=False, flight=False):
     """The `config` object of both arms: the workload as the GPU arm runs it."""
     step_bytes = sum(kernel_bytes(n, 4, wake).values())
     insect = ("ellipsoid body (0.5, 0.12) + 2 flapping plates (c 0.3, R 1, 4dx thick, "
@@ -464,6 +482,8 @@ def workload_config(n, world, workload="model_insect", wake=False):
     if wake:
         what += ("; vorticity sponge C_sp 0.1, 32 points deep at the x and y ends, Dirichlet layer "
                  "4 points deep at the x end")
+    if flight:
+        what += "; free flight (mass 400, J_body (2, 5, 5), g 9.81) with wing power"
     return {"workload": what, "grid": list(n), "box": [4.0, 4.0, 4.0], "precision": "fp32",
             "initial": init,
             "l2": f"inputs larger than L2: {step_bytes / 1e9:.1f} GB moved per step",
@@ -483,7 +503,7 @@ def run_reference(args):
     # choose the sample grid from a timed probe step
     pick = 32
     for n in (32, 48, 64, 96, 128):
-        cfg, ins, u0 = oracle_workload(args.workload, n)
+        cfg, ins, u0 = oracle_workload(args.workload, n, args.flight)
         sim = oracle.Simulation(cfg, ins)
         sim.set_state(u0)
         t0 = time.perf_counter()
@@ -492,7 +512,7 @@ def run_reference(args):
         if per * (args.steps + args.warmup) > 120.0:
             break
         pick = n
-    cfg, ins, u0 = oracle_workload(args.workload, pick)
+    cfg, ins, u0 = oracle_workload(args.workload, pick, args.flight)
     sim = oracle.Simulation(cfg, ins)
     sim.set_state(u0)
     sim.step(args.warmup)
@@ -507,7 +527,8 @@ def run_reference(args):
            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "impl": "reference",
-           "config": workload_config(workload_setup(args)[0]["n"], world, args.workload, args.wake),
+           "config": workload_config(workload_setup(args)[0]["n"], world, args.workload, args.wake,
+                                     args.flight),
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                             "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

@@ -55,16 +55,22 @@ typedef enum { FLUSI_HOST_FP64 = 0, FLUSI_HOST_FP32 = 1, FLUSI_DEVICE = 2 } flus
 
 #define FLUSI_MAX_FOURIER 8
 #define FLUSI_MAX_CONTOUR 32
-#define FLUSI_FORCE_COLS 22
+#define FLUSI_FORCE_COLS 26
 
 /* Columns of one force row (Eqs. force_with_unst_corrections and
- * moment_of_love, one block per mask colour: 0 body, 1 left wing, 2 right). */
+ * moment_of_love, one block per mask colour: 0 body, 1 left wing, 2 right;
+ * the moment of the body about x_cntr, of a wing about its pivot), then the
+ * power of each wing (Sec. 3.4, Eq. insect_power): aerodynamic
+ * P = -M_wing . (Omega_wing - Omega_body), global frame, and inertial
+ * P = Omega^(w) . (J Omega'^(w) + Omega^(w) x J Omega^(w)), wing frame. */
 #define FLUSI_COL_T 0
 #define FLUSI_COL_DT 1
 #define FLUSI_COL_F(colour) (2 + 6 * (colour))
 #define FLUSI_COL_M(colour) (5 + 6 * (colour))
 #define FLUSI_COL_EKIN 20
 #define FLUSI_COL_UMAX 21
+#define FLUSI_COL_PAERO(wing) (22 + (wing))
+#define FLUSI_COL_PINERT(wing) (24 + (wing))
 
 typedef struct flusi_options {
     double cfl;            /* CFL number of the adaptive step (default 0.1)            */
@@ -127,6 +133,27 @@ typedef struct flusi_insect {
     int ncontour;              /* <= FLUSI_MAX_CONTOUR */
     double contour_xc, contour_yc;
     double contour_a0, contour_a[FLUSI_MAX_CONTOUR], contour_b[FLUSI_MAX_CONTOUR];
+    /* Tensor of inertia of one wing in its own frame (xx, yy, zz, xy, xz, yz),
+     * used only by the inertial power column (Sec. 3.4). */
+    double J_wing[6];
+    /* Free flight (Sec. 3.5, Eq. oh_my_god_look_a_vector).  0: the body moves
+     * as x_cntr, u_cntr and the angles above prescribe (tethered).  1: x_cntr,
+     * u_cntr, quat and Omega_body are the initial state of the 13 Newton-Euler
+     * equations, which every step advances on the device with the fluid's AB2
+     * weights (Euler on the first step), driven by the step's total force and
+     * its moment about x_cntr (the wings' moments moved from their pivots);
+     * the quaternion is renormalized after each step.  The orientation is
+     * then the quaternion's (the angles and their rates are not used), the
+     * printed quaternion matrix being the body-to-global map.  Free flight
+     * needs time_scheme 0.  flusi_get_body reads the state back. */
+    int free_flight;
+    int pad2_;
+    double mass, gravity;      /* M; g > 0 pulls along -z                         */
+    double J_body[3];          /* principal moments of inertia (body axes), > 0   */
+    double dof[6];             /* factors on du_x, du_y, du_z and dOmega_x, _y, _z:
+                                  1 free, 0 held                                 */
+    double quat[4];            /* epsilon_0..3; all zero: from (psi, beta, gamma)  */
+    double Omega_body[3];      /* Omega^(b), body frame                           */
 } flusi_insect;
 
 /* Create a solver for an nx x ny x nz periodic grid over the box L[3], with
@@ -167,8 +194,16 @@ int flusi_bind(flusi_t h, void *dev_workspace, size_t bytes, void *cuda_stream);
 int flusi_set_state(flusi_t h, const void *u, int where);
 
 /* Set the insect (Sec. 3): body, wings, kinematics.  Without a call (or with
- * NULL) there is no mask.  May be called between steps. */
+ * NULL) there is no mask.  May be called between steps; with free flight it
+ * replaces the body's state (the ODE's AB2 history is kept).  FLUSI_EINVAL
+ * for a bad descriptor, or free flight with time_scheme 1. */
 int flusi_set_kinematics(flusi_t h, const flusi_insect *insect);
+
+/* Free flight (Sec. 3.5): the body state after the steps enqueued so far,
+ * state[13] = x_cntr[3], u_cntr[3], quat[4], Omega_body[3] (host).  Without
+ * free flight it is the descriptor's (constant) values.  Synchronizes;
+ * FLUSI_ESTATE without an insect or when not bound. */
+int flusi_get_body(flusi_t h, double state[13]);
 
 /* Enqueue n time steps (Algorithm 1 steps a-e) on the bound stream and
  * return without waiting.  Only argument and call-order errors are reported
@@ -181,7 +216,7 @@ int flusi_sync(flusi_t h);
 /* Drain the force rows produced since the last call (in step order) into
  * rows[count][FLUSI_FORCE_COLS] (host, capacity `cap` rows).  Row columns:
  * t, dt, then per colour F[3], M[3], then E_kin = 1/2 sum |u|^2 dV and
- * max |u|.  Synchronizes.  Rows beyond force_ring since the last call are
+ * max |u|, then the aerodynamic and the inertial power of each wing.  Synchronizes.  Rows beyond force_ring since the last call are
  * lost; *lost (may be NULL) receives their number. */
 int flusi_forces(flusi_t h, double *rows, int cap, int *count, long long *lost);
 
@@ -253,7 +288,10 @@ int flusi_penalization_sums_noalloc(int nx, int ny, int nz, const double L[3], d
  * unsteady force correction (Eq. force_with_unst_corrections), and a
  * checkpoint holds exactly those, in the handle's precision and internal
  * layout (kept modes only), so a run restarted from it continues bit for bit.
- * Options and kinematics are not stored: set them as they were.
+ * In free flight it also holds the body state and the ODE's previous
+ * right-hand side; loading writes the body state into the current insect when
+ * that is in free flight.  Options and kinematics are not stored otherwise:
+ * set them as they were, before flusi_load.
  *
  * flusi_checkpoint_bytes: size of a checkpoint of this handle (no device work).
  * flusi_save: write one into the caller's host buffer of `bytes` (at least that

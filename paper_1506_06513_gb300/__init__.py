@@ -20,7 +20,7 @@ FLUSI_FP64, FLUSI_FP32 = 0, 1
 FLUSI_HOST_FP64, FLUSI_HOST_FP32, FLUSI_DEVICE = 0, 1, 2
 MAX_FOURIER = 8
 MAX_CONTOUR = 32
-FORCE_COLS = 22
+FORCE_COLS = 26
 PROFILE_MAX = 40
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENONFINITE", "ETIMEOUT", "ESTATE"]
 
@@ -62,7 +62,11 @@ class Insect(C.Structure):
                 ("wing_shape", C.c_int), ("ncontour", C.c_int),
                 ("contour_xc", C.c_double), ("contour_yc", C.c_double),
                 ("contour_a0", C.c_double), ("contour_a", C.c_double * MAX_CONTOUR),
-                ("contour_b", C.c_double * MAX_CONTOUR)]
+                ("contour_b", C.c_double * MAX_CONTOUR),
+                ("J_wing", C.c_double * 6),
+                ("free_flight", C.c_int), ("pad2_", C.c_int),
+                ("mass", C.c_double), ("gravity", C.c_double), ("J_body", C.c_double * 3),
+                ("dof", C.c_double * 6), ("quat", C.c_double * 4), ("Omega_body", C.c_double * 3)]
 
 
 def _load():
@@ -79,6 +83,7 @@ def _load():
         "flusi_bind": ([h, vp, C.c_size_t, vp], ip),
         "flusi_set_state": ([h, vp, ip], ip),
         "flusi_set_kinematics": ([h, C.POINTER(Insect)], ip),
+        "flusi_get_body": ([h, dp], ip),
         "flusi_step": ([h, ip], ip),
         "flusi_sync": ([h], ip),
         "flusi_forces": ([h, dp, ip, C.POINTER(C.c_int), C.POINTER(C.c_longlong)], ip),
@@ -157,6 +162,13 @@ def flusi_set_state(h, u, where):
 
 def flusi_set_kinematics(h, insect: Insect | None):
     return _check(h, lib.flusi_set_kinematics(h, C.byref(insect) if insect is not None else None))
+
+
+def flusi_get_body(h):
+    """Body state (x_cntr, u_cntr, quat, Omega_body) as a dict of arrays."""
+    y = np.zeros(13)
+    _check(h, lib.flusi_get_body(h, _dptr(y)))
+    return {"x_cntr": y[0:3], "u_cntr": y[3:6], "quat": y[6:10], "Omega_body": y[10:13]}
 
 
 def flusi_step(h, n):
@@ -301,6 +313,16 @@ def make_insect(d: dict | None) -> Insect | None:
         s.head_x0[:], s.head_r = d["head"]
     if "eyes" in d:
         s.eye_x0[:], s.eye_r = d["eyes"]
+    if "J_wing" in d:
+        s.J_wing[:] = d["J_wing"]
+    if "free_flight" in d:
+        ff = d["free_flight"]
+        s.free_flight = 1
+        s.mass, s.gravity = ff["mass"], ff.get("gravity", 0.0)
+        s.J_body[:] = ff["J_body"]
+        s.dof[:] = ff.get("dof", (1.0,) * 6)
+        s.Omega_body[:] = ff.get("Omega_body", (0.0, 0.0, 0.0))
+        s.quat[:] = ff.get("quat", (0.0, 0.0, 0.0, 0.0))   # zero: from the body angles
     if "contour" in d:
         c = d["contour"]
         s.wing_shape = 1
@@ -389,6 +411,10 @@ class Solver:
 
     def forces(self, cap=4096):
         return flusi_forces(self.h, cap)
+
+    def body(self):
+        """Free flight: the body state after the enqueued steps (synchronizes)."""
+        return flusi_get_body(self.h)
 
     def get_state(self, dtype=np.float64):
         nx, ny, nz = self.n

@@ -42,7 +42,7 @@ template <typename C> __device__ __forceinline__ C cmul(C a, C b)
 constexpr int kMaxN = 1024;
 constexpr int kMaxStages = 10;
 constexpr int kNumSums = 40;     // per-CTA partial sums of the physical pass
-constexpr int kRowCols = 22;     // one force row
+constexpr int kRowCols = 26;     // one force row
 
 // Partial-sum slots: per colour c (0 body, 1 left, 2 right) 12 doubles:
 // [0..2] sum chi (u - u_s), [3..5] sum r x chi (u - u_s),
@@ -85,6 +85,8 @@ struct Frame {
     double Mw[2][9];         // global -> wing frame, per wing
     double pv[2][3];         // wing pivots (global)
     double Ow[2][3];         // wing angular velocity relative to the body (global frame)
+    double Oww[2][3];        // the same in the wing's own frame
+    double dOww[2][3];       // its time derivative (inertial power)
     double box[3][6];        // bounding box per part: xmin xmax ymin ymax zmin zmax
     int active[3];           // part present
     int pad;
@@ -146,6 +148,8 @@ struct StepState {
     int pad;
     double Is_prev[3][3];
     double Js_prev[3][3];
+    double body_rhs_prev[13];   // free flight: the ODE right-hand side of the previous step
+    double pad2;
 };
 
 // Coefficients of the current step, written by the scalar kernel and read by

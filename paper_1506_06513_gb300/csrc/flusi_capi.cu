@@ -5,6 +5,7 @@
 // in the kernels.
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <initializer_list>
@@ -349,7 +350,8 @@ cudaError_t enqueue_step(flusi_t h, cudaStream_t s, cudaEvent_t* ev, const char*
             }
             double3 opts = make_double3(h->opt.cfl, h->opt.dt_fixed, h->opt.dt_max);
             k_scalars<<<1, 256, 0, sk>>>(g, at<double>(h, h->opart), h->xgrid, st, coef, at<double>(h, h->orows),
-                                         h->opt.force_ring, at<double>(h, h->oetab), opts, rk4_dt_diff(h));
+                                         h->opt.force_ring, at<double>(h, h->oetab), opts, rk4_dt_diff(h),
+                                         at<Frame>(h, h->oframe), at<flusi_insect>(h, h->oins));
             if ((e = cudaGetLastError())) return e;
             if (branch && (e = cudaEventRecord(h->ev_sc, sk))) return e;
         }
@@ -406,6 +408,28 @@ int read_status(flusi_t h, StepState* out)
                                       : "device-side failure");
     }
     return FLUSI_OK;
+}
+
+// Quaternion of the yaw-pitch-roll orientation (psi, beta, gamma) of Eq.
+// M_body_yawpitchroll.  M_body = R_x(psi) R_y(beta) R_z(gamma) maps global to
+// body coordinates, so the body-to-global map is the active rotation by gamma
+// about z after beta about y after psi about x: eps = q_z (x) q_y (x) q_x, with
+// q_n(a) = (cos a/2, sin a/2 n) and (x) the quaternion product.
+void quat_of_angles(double psi, double beta, double gamma, double* eps)
+{
+    auto mulq = [](const double* a, const double* b, double* c) {
+        double r[4] = {a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3],
+                       a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2],
+                       a[0] * b[2] + a[2] * b[0] + a[3] * b[1] - a[1] * b[3],
+                       a[0] * b[3] + a[3] * b[0] + a[1] * b[2] - a[2] * b[1]};
+        std::memcpy(c, r, sizeof r);
+    };
+    const double qx[4] = {std::cos(0.5 * psi), std::sin(0.5 * psi), 0, 0};
+    const double qy[4] = {std::cos(0.5 * beta), 0, std::sin(0.5 * beta), 0};
+    const double qz[4] = {std::cos(0.5 * gamma), 0, 0, std::sin(0.5 * gamma)};
+    double t[4];
+    mulq(qz, qy, t);
+    mulq(t, qx, eps);
 }
 
 // Shapes are value-initialized, padding included, so bytes compare fields.
@@ -467,6 +491,8 @@ int flusi_set_options(flusi_t h, const flusi_options* o)
     if (o->time_scheme != 0 && o->time_scheme != 1) return fail(h, FLUSI_EINVAL, "time_scheme must be 0 or 1");
     if (h->bound && o->time_scheme != h->opt.time_scheme)
         return fail(h, FLUSI_EINVAL, "time_scheme cannot change after flusi_bind");
+    if (o->time_scheme != 0 && h->have_ins && h->ins.free_flight)
+        return fail(h, FLUSI_EINVAL, "free flight needs time_scheme 0");
     for (int i = 0; i < 3; ++i)
         if (!(o->sponge_width[i] >= 0 && o->sponge_width[i] <= h->L[i]) ||
             !(o->layer_width[i] >= 0 && o->layer_width[i] <= h->L[i]))
@@ -541,8 +567,26 @@ int flusi_set_kinematics(flusi_t h, const flusi_insect* ins)
             ins->ncontour < 0 || ins->ncontour > FLUSI_MAX_CONTOUR ||
             (ins->wing_shape == 1 && !(ins->contour_a0 > 0)))
             return fail(h, FLUSI_EINVAL, "bad insect descriptor");
+        if (ins->free_flight != 0 && ins->free_flight != 1) return fail(h, FLUSI_EINVAL, "free_flight must be 0 or 1");
+        if (ins->free_flight) {
+            bool ok = ins->mass > 0 && std::isfinite(ins->gravity) && h->opt.time_scheme == 0;
+            for (int i = 0; i < 3; ++i) ok = ok && ins->J_body[i] > 0 && std::isfinite(ins->Omega_body[i]);
+            for (int i = 0; i < 6; ++i) ok = ok && std::isfinite(ins->dof[i]);
+            if (!ok)
+                return fail(h, FLUSI_EINVAL, "free flight needs mass > 0, J_body > 0, finite gravity, dof and "
+                                             "Omega_body, and time_scheme 0");
+        }
         h->ins = *ins;
         h->have_ins = 1;
+        double qn = 0.0;
+        for (int i = 0; i < 4; ++i) qn += ins->quat[i] * ins->quat[i];
+        if (qn == 0.0) {
+            quat_of_angles(ins->psi, ins->beta, ins->gamma, h->ins.quat);
+        } else {
+            if (!std::isfinite(qn)) return fail(h, FLUSI_EINVAL, "bad quaternion");
+            if (qn != 1.0)
+                for (int i = 0; i < 4; ++i) h->ins.quat[i] = ins->quat[i] / std::sqrt(qn);
+        }
     } else {
         std::memset(&h->ins, 0, sizeof h->ins);
         h->have_ins = 0;
@@ -555,6 +599,40 @@ int flusi_set_kinematics(flusi_t h, const flusi_insect* ins)
     return FLUSI_OK;
 }
 
+namespace {
+
+// The 13 body-state values inside a device descriptor: x_cntr and u_cntr
+// are adjacent, so are quat and Omega_body.
+constexpr size_t kBodyA = offsetof(flusi_insect, x_cntr), kBodyB = offsetof(flusi_insect, quat);
+static_assert(offsetof(flusi_insect, u_cntr) == kBodyA + 3 * sizeof(double), "x_cntr, u_cntr adjacent");
+static_assert(offsetof(flusi_insect, Omega_body) == kBodyB + 4 * sizeof(double), "quat, Omega_body adjacent");
+
+cudaError_t read_body(flusi_t h, double* y)
+{
+    cudaError_t e = cudaMemcpy(y, h->ws + h->oins + kBodyA, 6 * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e) return e;
+    return cudaMemcpy(y + 6, h->ws + h->oins + kBodyB, 7 * sizeof(double), cudaMemcpyDeviceToHost);
+}
+
+cudaError_t write_body(flusi_t h, const double* y)
+{
+    cudaError_t e = cudaMemcpy(h->ws + h->oins + kBodyA, y, 6 * sizeof(double), cudaMemcpyHostToDevice);
+    if (e) return e;
+    return cudaMemcpy(h->ws + h->oins + kBodyB, y + 6, 7 * sizeof(double), cudaMemcpyHostToDevice);
+}
+
+}  // namespace
+
+int flusi_get_body(flusi_t h, double* state)
+{
+    if (!h || !state) return fail(h, FLUSI_EINVAL, "NULL argument");
+    int rc = check_ready(h, false);
+    if (rc) return rc;
+    if (!h->have_ins) return fail(h, FLUSI_ESTATE, "no insect set");
+    CK(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    CK(read_body(h, state), "read body state");
+    return FLUSI_OK;
+}
 
 int flusi_set_state(flusi_t h, const void* u, int where)
 {
@@ -819,12 +897,15 @@ int flusi_kernels_per_step(flusi_t h, int* count)
 namespace {
 
 struct CkptHeader {
-    char magic[8];               // "FLUSICK1"
+    char magic[8];               // "FLUSICK2"
     int prec, nx, ny, nz, Mx, My, Mz, Mxp;
     int dealias_strict;
     double L[3], nu, eta;
     unsigned long long spec_bytes;  // one of U, H
 };
+
+// after the step state: the free-flight body state (13 doubles, padded)
+constexpr size_t kCkptBody = 16 * sizeof(double);
 
 size_t spec_bytes(flusi_t h)
 {
@@ -835,7 +916,7 @@ size_t spec_bytes(flusi_t h)
 CkptHeader make_header(flusi_t h)
 {
     CkptHeader c{};
-    std::memcpy(c.magic, "FLUSICK1", 8);
+    std::memcpy(c.magic, "FLUSICK2", 8);
     c.prec = h->prec;
     c.nx = h->nx;
     c.ny = h->ny;
@@ -857,7 +938,7 @@ CkptHeader make_header(flusi_t h)
 int flusi_checkpoint_bytes(flusi_t h, size_t* bytes)
 {
     if (!h || !bytes) return fail(h, FLUSI_EINVAL, "NULL argument");
-    *bytes = sizeof(CkptHeader) + sizeof(StepState) + 2 * spec_bytes(h);
+    *bytes = sizeof(CkptHeader) + sizeof(StepState) + kCkptBody + 2 * spec_bytes(h);
     return FLUSI_OK;
 }
 
@@ -877,7 +958,10 @@ int flusi_save(flusi_t h, void* host_buf, size_t bytes)
     const CkptHeader hd = make_header(h);
     std::memcpy(p, &hd, sizeof hd);
     std::memcpy(p + sizeof hd, &st, sizeof st);
-    char* q = p + sizeof hd + sizeof st;
+    double body[16] = {};
+    if (h->have_ins) CK(read_body(h, body), "save body state");
+    std::memcpy(p + sizeof hd + sizeof st, body, kCkptBody);
+    char* q = p + sizeof hd + sizeof st + kCkptBody;
     CK(cudaMemcpy(q, h->ws + h->oU, hd.spec_bytes, cudaMemcpyDeviceToHost), "save u_hat");
     CK(cudaMemcpy(q + hd.spec_bytes, h->ws + h->oH, hd.spec_bytes, cudaMemcpyDeviceToHost), "save history");
     return FLUSI_OK;
@@ -903,9 +987,18 @@ int flusi_load(flusi_t h, const void* host_buf, size_t bytes)
     StepState st;
     std::memcpy(&st, p + sizeof hd, sizeof st);
     if (st.status != 0 || st.n < 0) return fail(h, FLUSI_EINVAL, "checkpoint holds a failed or invalid state");
-    const char* q = p + sizeof hd + sizeof st;
+    double body[16];
+    std::memcpy(body, p + sizeof hd + sizeof st, kCkptBody);
+    const char* q = p + sizeof hd + sizeof st + kCkptBody;
     CK(cudaStreamSynchronize(h->stream), "sync before load");
     CK(cudaMemcpy(h->ws + h->ostate, &st, sizeof st, cudaMemcpyHostToDevice), "load step state");
+    if (h->have_ins && h->ins.free_flight) {
+        CK(write_body(h, body), "load body state");
+        std::memcpy(h->ins.x_cntr, body, 3 * sizeof(double));
+        std::memcpy(h->ins.u_cntr, body + 3, 3 * sizeof(double));
+        std::memcpy(h->ins.quat, body + 6, 4 * sizeof(double));
+        std::memcpy(h->ins.Omega_body, body + 10, 3 * sizeof(double));
+    }
     CK(cudaMemcpy(h->ws + h->oU, q, hd.spec_bytes, cudaMemcpyHostToDevice), "load u_hat");
     CK(cudaMemcpy(h->ws + h->oH, q + hd.spec_bytes, hd.spec_bytes, cudaMemcpyHostToDevice), "load history");
     h->has_state = 1;

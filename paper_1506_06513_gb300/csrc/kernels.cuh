@@ -21,7 +21,8 @@ __global__ void k_kinematics(const flusi_insect* ins, const StepState* st, const
                              double h, double frac);
 __global__ void k_reset_state(StepState* st, StepCoef* coef);
 __global__ void k_scalars(Geom g, const double* part, int nparts, StepState* st, StepCoef* coef,
-                          double* rows, int ring, double* etab, double3 opts, double dt_diff);
+                          double* rows, int ring, double* etab, double3 opts, double dt_diff,
+                          const Frame* fr, flusi_insect* ins);
 
 // y transform (ypass.cu): W[c] for c < ncomp, between A and B form.
 // tw: twiddle table of the axis; pos: digit-reversal table of its plan.

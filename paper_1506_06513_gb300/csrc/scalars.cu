@@ -50,21 +50,52 @@ __device__ void apply_t(const M3& A, const double* x, double* y)
     y[0] = t0, y[1] = t1, y[2] = t2;
 }
 
-// a0/2 + sum a_i cos(2 pi i f t) + b_i sin(2 pi i f t) and its time derivative
+// A x
+__device__ void apply(const M3& A, const double* x, double* y)
+{
+    double t0 = A.a[0] * x[0] + A.a[1] * x[1] + A.a[2] * x[2];
+    double t1 = A.a[3] * x[0] + A.a[4] * x[1] + A.a[5] * x[2];
+    double t2 = A.a[6] * x[0] + A.a[7] * x[1] + A.a[8] * x[2];
+    y[0] = t0, y[1] = t1, y[2] = t2;
+}
+
+__device__ void cross3(const double* a, const double* b, double* c)
+{
+    double c0 = a[1] * b[2] - a[2] * b[1];
+    double c1 = a[2] * b[0] - a[0] * b[2];
+    double c2 = a[0] * b[1] - a[1] * b[0];
+    c[0] = c0, c[1] = c1, c[2] = c2;
+}
+
+// a0/2 + sum a_i cos(2 pi i f t) + b_i sin(2 pi i f t) and its first two time
+// derivatives
 __device__ void series(double a0, const double* a, const double* b, int nf, double f, double t,
-                       double* v, double* dv)
+                       double* v, double* dv, double* ddv)
 {
     const double two_pi = 6.283185307179586476925286766559;
-    double s = 0.5 * a0, d = 0.0;
+    double s = 0.5 * a0, d = 0.0, dd = 0.0;
     for (int i = 0; i < nf; ++i) {
         double w = two_pi * (i + 1) * f;
         double sn, cs;
         sincos(w * t, &sn, &cs);
-        s += a[i] * cs + b[i] * sn;
+        const double c = a[i] * cs + b[i] * sn;
+        s += c;
         d += w * (b[i] * cs - a[i] * sn);
+        dd -= w * w * c;
     }
     *v = s;
     *dv = d;
+    *ddv = dd;
+}
+
+// Body-to-global matrix of the quaternion (e0, e1, e2, e3) as printed in
+// Sec. 3.5; its transpose is the global-to-body matrix M_body.
+__device__ M3 quat_to_global(const double* e)
+{
+    const double a = e[0], b = e[1], c = e[2], d = e[3];
+    return {{a * a + b * b - c * c - d * d, 2 * (b * c - a * d), 2 * (b * d + a * c),
+             2 * (b * c + a * d), a * a - b * b + c * c - d * d, 2 * (c * d - a * b),
+             2 * (b * d - a * c), 2 * (c * d + a * b), a * a - b * b - c * c + d * d}};
 }
 
 __device__ void box_grow(double* box, const double* p)
@@ -73,6 +104,69 @@ __device__ void box_grow(double* box, const double* p)
         box[2 * i] = fmin(box[2 * i], p[i]);
         box[2 * i + 1] = fmax(box[2 * i + 1], p[i]);
     }
+}
+
+// Free flight (Sec. 3.5, Eq. oh_my_god_look_a_vector): one AB2 step of the
+// 13 body equations with the fluid step's dt and ratio r = dt/dt_prev (Euler
+// when `first`).  State y = (x_cntr, u_cntr, quat, Omega_body); forcing: the
+// row's total force and its total moment about x_cntr, taken into body axes.
+__device__ void advance_body(flusi_insect* ins, StepState* st, const Frame& F, const double* row,
+                             double dt, double r, int first)
+{
+    double Ft[3] = {0, 0, 0}, mg[3] = {0, 0, 0};
+    for (int p = 0; p < 3; ++p)
+        for (int i = 0; i < 3; ++i) {
+            Ft[i] += row[2 + 6 * p + i];
+            mg[i] += row[5 + 6 * p + i];
+        }
+    // a wing's moment is about its pivot: M_c = M_pivot + (pivot - x_cntr) x F
+    for (int s = 0; s < 2 && s < ins->nwings; ++s) {
+        const double arm[3] = {F.pv[s][0] - F.xc[0], F.pv[s][1] - F.xc[1], F.pv[s][2] - F.xc[2]};
+        double c[3];
+        cross3(arm, row + 2 + 6 * (1 + s), c);
+        for (int i = 0; i < 3; ++i) mg[i] += c[i];
+    }
+    M3 Mb;
+    for (int i = 0; i < 9; ++i) Mb.a[i] = F.Mb[i];
+    double mb[3];
+    apply(Mb, mg, mb);
+
+    double y[13], f[13];
+    const double* e = ins->quat;
+    const double* W = ins->Omega_body;
+    const double* J = ins->J_body;
+    const double* dof = ins->dof;
+    for (int i = 0; i < 3; ++i) {
+        y[i] = ins->x_cntr[i];
+        y[3 + i] = ins->u_cntr[i];
+        y[10 + i] = W[i];
+        f[i] = ins->u_cntr[i];
+        f[3 + i] = dof[i] * Ft[i] / ins->mass;
+    }
+    f[5] -= dof[2] * ins->gravity;
+    for (int i = 0; i < 4; ++i) y[6 + i] = e[i];
+    // quaternion rate: half the product eps (x) (0, Omega^(b))
+    f[6] = -0.5 * (e[1] * W[0] + e[2] * W[1] + e[3] * W[2]);
+    f[7] = 0.5 * (e[0] * W[0] + e[2] * W[2] - e[3] * W[1]);
+    f[8] = 0.5 * (e[0] * W[1] + e[3] * W[0] - e[1] * W[2]);
+    f[9] = 0.5 * (e[0] * W[2] + e[1] * W[1] - e[2] * W[0]);
+    // Euler's equations in principal body axes
+    for (int i = 0; i < 3; ++i) {
+        const int j = (i + 1) % 3, k = (i + 2) % 3;
+        f[10 + i] = dof[3 + i] * ((J[j] - J[k]) * W[j] * W[k] + mb[i]) / J[i];
+    }
+    for (int i = 0; i < 13; ++i) {
+        const double step = first ? f[i] : (1.0 + 0.5 * r) * f[i] - 0.5 * r * st->body_rhs_prev[i];
+        y[i] += dt * step;
+        st->body_rhs_prev[i] = f[i];
+    }
+    const double qn = sqrt(y[6] * y[6] + y[7] * y[7] + y[8] * y[8] + y[9] * y[9]);
+    for (int i = 0; i < 3; ++i) {
+        ins->x_cntr[i] = y[i];
+        ins->u_cntr[i] = y[3 + i];
+        ins->Omega_body[i] = y[10 + i];
+    }
+    for (int i = 0; i < 4; ++i) ins->quat[i] = y[6 + i] / qn;
 }
 
 }  // namespace
@@ -90,23 +184,32 @@ __global__ void k_kinematics(const flusi_insect* ins, const StepState* st, const
         F.xc[i] = ins->x_cntr[i];
         F.uc[i] = ins->u_cntr[i];
     }
-    // body frame: yaw, then pitch, then roll
-    M3 Rx = rot_x(ins->psi), Ry = rot_y(ins->beta), Rz = rot_z(ins->gamma);
-    M3 Mb = mul(mul(Rx, Ry), Rz);
+    M3 Mb;
+    if (ins->free_flight) {
+        // Sec. 3.5: the orientation is the quaternion's, Omega^(b) is state
+        const M3 Q = quat_to_global(ins->quat);
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) Mb.a[3 * i + j] = Q.a[3 * j + i];
+        apply(Q, ins->Omega_body, F.Ob);
+    } else {
+        // body frame: yaw, then pitch, then roll
+        M3 Rx = rot_x(ins->psi), Ry = rot_y(ins->beta), Rz = rot_z(ins->gamma);
+        Mb = mul(mul(Rx, Ry), Rz);
+        // body angular velocity in the global frame (nested form of Sec. 3.1)
+        double v[3] = {ins->psi_dot, 0, 0};
+        apply_t(Rx, v, v);
+        v[1] += ins->beta_dot;
+        apply_t(Ry, v, v);
+        v[2] += ins->gamma_dot;
+        apply_t(Rz, v, F.Ob);
+    }
     for (int i = 0; i < 9; ++i) F.Mb[i] = Mb.a[i];
-    // body angular velocity in the global frame (nested form of Sec. 3.1)
-    double v[3] = {ins->psi_dot, 0, 0};
-    apply_t(Rx, v, v);
-    v[1] += ins->beta_dot;
-    apply_t(Ry, v, v);
-    v[2] += ins->gamma_dot;
-    apply_t(Rz, v, F.Ob);
 
-    double phi, alpha, theta, dphi, dalpha, dtheta;
+    double phi, alpha, theta, dphi, dalpha, dtheta, ddphi, ddalpha, ddtheta;
     int nf = ins->nfourier;
-    series(ins->phi_a0, ins->phi_a, ins->phi_b, nf, ins->freq, t, &phi, &dphi);
-    series(ins->alpha_a0, ins->alpha_a, ins->alpha_b, nf, ins->freq, t, &alpha, &dalpha);
-    series(ins->theta_a0, ins->theta_a, ins->theta_b, nf, ins->freq, t, &theta, &dtheta);
+    series(ins->phi_a0, ins->phi_a, ins->phi_b, nf, ins->freq, t, &phi, &dphi, &ddphi);
+    series(ins->alpha_a0, ins->alpha_a, ins->alpha_b, nf, ins->freq, t, &alpha, &dalpha, &ddalpha);
+    series(ins->theta_a0, ins->theta_a, ins->theta_b, nf, ins->freq, t, &theta, &dtheta, &ddtheta);
 
     const double pi = 3.141592653589793238462643383279;
     for (int s = 0; s < 2; ++s) {
@@ -128,6 +231,26 @@ __global__ void k_kinematics(const flusi_insect* ins, const StepState* st, const
         apply_t(Rp, w, w);
         apply_t(Ms, w, w);
         apply_t(Mb, w, F.Ow[s]);
+        // In the wing frame Omega^(w) = e_a + Ra (e_t + Rt e_p) with
+        // e_a = (0, alpha', 0), e_t = (0, 0, -theta'), e_p = (phi', 0, 0).  Both
+        // factors are rotations about one fixed axis, so d/dt (Ra x) =
+        // Ra x' - e_a x (Ra x) and d/dt (Rt x) = Rt x' - e_t x (Rt x).
+        {
+            const double ea[3] = {0, sg * dalpha, 0}, et[3] = {0, 0, -dtheta}, ep[3] = {sg * dphi, 0, 0};
+            const double dea[3] = {0, sg * ddalpha, 0}, det[3] = {0, 0, -ddtheta};
+            const double dep[3] = {sg * ddphi, 0, 0};
+            double rp[3], in[3], v[3], dv[3], c[3], drp[3];
+            apply(Rt, ep, rp);                          // Rt e_p
+            for (int i = 0; i < 3; ++i) in[i] = et[i] + rp[i];
+            apply(Ra, in, v);                           // Ra (e_t + Rt e_p)
+            for (int i = 0; i < 3; ++i) F.Oww[s][i] = ea[i] + v[i];
+            apply(Rt, dep, drp);
+            cross3(et, rp, c);
+            for (int i = 0; i < 3; ++i) dv[i] = det[i] + drp[i] - c[i];
+            apply(Ra, dv, dv);
+            cross3(ea, v, c);
+            for (int i = 0; i < 3; ++i) F.dOww[s][i] = dea[i] + dv[i] - c[i];
+        }
         const double* pb = s == 0 ? ins->pivot_l : ins->pivot_r;
         double pg[3];
         apply_t(Mb, pb, pg);
@@ -212,7 +335,8 @@ __global__ void k_reset_state(StepState* st, StepCoef* coef)
 // step's scalars.  `opts` = {cfl, dt_fixed, dt_max}; dt_diff > 0 caps the
 // adaptive step (the explicit-diffusion limit of RK4).
 __global__ void k_scalars(Geom g, const double* part, int nparts, StepState* st, StepCoef* coef,
-                          double* rows, int ring, double* etab, double3 opts, double dt_diff)
+                          double* rows, int ring, double* etab, double3 opts, double dt_diff,
+                          const Frame* fr, flusi_insect* ins)
 {
     __shared__ double red[kNumSums][33];
     __shared__ double tot[kNumSums];
@@ -326,6 +450,28 @@ __global__ void k_scalars(Geom g, const double* part, int nparts, StepState* st,
         }
         row[20] = 0.5 * tot[kSumEkin] * dV;
         row[21] = umax;
+
+        // wing power at t^n (Sec. 3.4, Eq. insect_power)
+        const Frame& F = *fr;
+        for (int s = 0; s < 2; ++s) {
+            double pa = 0.0, pi = 0.0;
+            if (s < ins->nwings) {
+                const double* m = row + 5 + 6 * (1 + s);
+                pa = -(m[0] * F.Ow[s][0] + m[1] * F.Ow[s][1] + m[2] * F.Ow[s][2]);
+                const double* J = ins->J_wing;   // xx yy zz xy xz yz
+                const M3 Jm = {{J[0], J[3], J[4], J[3], J[1], J[5], J[4], J[5], J[2]}};
+                const double* w = F.Oww[s];
+                double Jw[3], Jdw[3], c[3];
+                apply(Jm, w, Jw);
+                apply(Jm, F.dOww[s], Jdw);
+                cross3(w, Jw, c);
+                pi = w[0] * (Jdw[0] + c[0]) + w[1] * (Jdw[1] + c[1]) + w[2] * (Jdw[2] + c[2]);
+            }
+            row[22 + s] = pa;
+            row[24 + s] = pi;
+        }
+
+        if (ins->free_flight) advance_body(ins, st, F, row, dt, first ? 0.0 : dt / dt_prev, first);
 
         st->t += dt;
         st->dt_prev = dt;

@@ -8,6 +8,8 @@ import re
 import numpy as np
 import pytest
 
+import workloads
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -116,7 +118,36 @@ def test_struct_layouts_match_header(fl):
     """The ctypes mirrors have the sizes the C compiler gives the structs."""
     assert C.sizeof(fl.Options) == 3 * 8 + 3 * 8 + 4 * 4 + 7 * 8 + 2 * 4
     assert C.sizeof(fl.Insect) == (4 * 4 + 8 * (1 + 3 + 3 + 6 + 2 + 3 + 3 + 1 + 4 + 1 + 3 * 17)
-                                   + 8 * (3 + 1 + 3 + 1) + 2 * 4 + 8 * (3 + 2 * 32))
+                                   + 8 * (3 + 1 + 3 + 1) + 2 * 4 + 8 * (3 + 2 * 32)
+                                   + 8 * 6 + 2 * 4 + 8 * (2 + 3 + 6 + 4 + 3))
+    assert fl.FORCE_COLS == 26
+
+
+def test_free_flight_descriptor_checks(fl):
+    """Free flight needs a positive mass and moments of inertia and the AB2
+    scheme, whichever of options and kinematics comes first."""
+    L, n = (4.0, 4.0, 4.0), (16, 16, 16)
+    ff = {"mass": 0.2, "gravity": 9.81, "J_body": (1e-3, 2e-3, 2e-3)}
+    h = fl.flusi_create(n, L, 0.1, 1e-2, fl.FLUSI_FP64)
+    fl.flusi_set_kinematics(h, fl.make_insect(dict(workloads.model_insect(L, n), free_flight=ff)))
+    with pytest.raises(fl.FlusiError):
+        fl.flusi_set_options(h, fl.make_options({"time_scheme": "rk4"}))
+    for bad in ({"mass": 0.0}, {"J_body": (1e-3, 0.0, 2e-3)}, {"gravity": float("nan")}):
+        with pytest.raises(fl.FlusiError):
+            fl.flusi_set_kinematics(h, fl.make_insect(dict(workloads.model_insect(L, n),
+                                                           free_flight=dict(ff, **bad))))
+    ins = fl.make_insect(dict(workloads.model_insect(L, n), free_flight=ff))
+    ins.free_flight = 2
+    with pytest.raises(fl.FlusiError):
+        fl.flusi_set_kinematics(h, ins)
+    fl.flusi_destroy(h)
+    h = fl.flusi_create(n, L, 0.1, 1e-2, fl.FLUSI_FP64)
+    fl.flusi_set_options(h, fl.make_options({"time_scheme": "rk4"}))
+    with pytest.raises(fl.FlusiError):
+        fl.flusi_set_kinematics(h, fl.make_insect(dict(workloads.model_insect(L, n), free_flight=ff)))
+    # tethered kinematics stay allowed with RK4
+    fl.flusi_set_kinematics(h, fl.make_insect(workloads.model_insect(L, n)))
+    fl.flusi_destroy(h)
 
 
 def test_kernels_per_step(fl):

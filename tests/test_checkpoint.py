@@ -18,11 +18,11 @@ def fl():
 def test_checkpoint_size_and_host_checks(fl):
     h = fl.flusi_create((16, 12, 8), (1.0, 1.0, 1.0), 0.1, 1e-2, fl.FLUSI_FP32)
     nbytes = fl.flusi_checkpoint_bytes(h)
-    # header + step state + u_hat and the history over the kept modes
+    # header + step state + body state + u_hat and the history over the kept modes
     Mx, My, Mz = 16 // 3 + 1, 2 * (12 // 3) + 1, 2 * (8 // 3) + 1
     Mxp = (Mx + 3) // 4 * 4
     spec = 3 * Mz * My * Mxp * 8
-    assert nbytes > 2 * spec and nbytes - 2 * spec < 512
+    assert nbytes > 2 * spec and nbytes - 2 * spec < 1024
     buf = np.zeros(nbytes, np.uint8)
     ptr = C.c_void_p(buf.ctypes.data)
     # no state yet

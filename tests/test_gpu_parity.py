@@ -147,7 +147,7 @@ def test_c0_full_step_fp64(fl):
     ref = oracle.Simulation(cfg, ins)
     ref.set_state(u0)
     ref_rows = ref.step(20)
-    assert step == 20 and lost == 0 and rows.shape == (20, 22)
+    assert step == 20 and lost == 0 and rows.shape == (20, 26)
     assert abs(t - ref.t) <= 1e-15
     assert rel_l2(u, ref.get_state()) <= 1e-11
     assert rows_err(rows, ref_rows) <= 1e-10
