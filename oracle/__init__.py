@@ -79,7 +79,8 @@ class Insect(C.Structure):
                 ("J_wing", C.c_double * 6),
                 ("free_flight", C.c_int), ("pad3_", C.c_int),
                 ("mass", C.c_double), ("gravity", C.c_double), ("J_body", C.c_double * 3),
-                ("dof", C.c_double * 6), ("quat", C.c_double * 4), ("Omega_body", C.c_double * 3)]
+                ("dof", C.c_double * 6), ("quat", C.c_double * 4), ("Omega_body", C.c_double * 3),
+                ("body_arc", C.c_double * 3)]
 
 
 class Scalars(C.Structure):
@@ -180,7 +181,9 @@ def make_insect(d: dict | None) -> Insect | None:
     if d is None:
         return None
     s = Insect()
-    s.body_type = {"none": 0, "sphere": 1, "ellipsoid": 2}[d.get("body", "none")]
+    s.body_type = {"none": 0, "sphere": 1, "ellipsoid": 2, "curved": 3}[d.get("body", "none")]
+    if "body_arc" in d:
+        s.body_arc[:] = d["body_arc"]     # (radius, x centre, z centre), body frame
     s.nwings = d.get("nwings", 0)
     s.profile = {"cos": 0, "tanh": 1}[d.get("profile", "cos")]
     s.c_smth = d.get("c_smth", 1.0)
@@ -444,12 +447,12 @@ def body_distance(insect: dict, xb):
 
 
 def wing_distance(insect: dict, xw):
-    """Signed distance of a wing at a wing-frame point (Sec. 3.3)."""
+    """Signed distance of a wing at a wing-frame point (Sec. 3.4)."""
     return lib().orc_wing_distance(C.byref(make_insect(insect)), np.ascontiguousarray(xw, np.float64))
 
 
 def quat_from_angles(psi, beta, gamma):
-    """Initial free-flight quaternion of the yaw, pitch and roll angles (Sec. 3.5)."""
+    """Initial free-flight quaternion of the yaw, pitch and roll angles (Sec. 3.6)."""
     eps = (C.c_double * 4)()
     lib().orc_quat_from_angles(psi, beta, gamma, eps)
     return np.array(eps[:])
@@ -469,7 +472,7 @@ def body_rhs(insect: dict, F, m_b, state=None):
 
 
 def wing_power(insect: dict, t: float, row=None):
-    """(P_aero[2], P_inert[2]) of the wings at time t (Sec. 3.4) for a force row
+    """(P_aero[2], P_inert[2]) of the wings at time t (Sec. 3.5) for a force row
     (zeros if none: only the inertial power is then meaningful)."""
     ins = make_insect(insect)
     fr = Frames()

@@ -119,7 +119,7 @@ static void rot_z_d(double xi, double *R)
     memcpy(R, M, sizeof M);
 }
 
-/* Free-flight orientation (Sec. 3.5): the printed quaternion matrix maps body
+/* Free-flight orientation (Sec. 3.6): the printed quaternion matrix maps body
  * to global coordinates, the transpose of M_body of Eq. M_body_yawpitchroll
  * (with the printed initial quaternion of (psi, beta, gamma) the two agree). */
 static void quat_body_to_global(const double *e, double *R)
@@ -161,7 +161,7 @@ void orc_body_rhs(const orc_insect *ins, const double *F, const double *m_b, dou
     f[12] = ins->dof[5] * ((J[0] - J[1]) * W[0] * W[1] + m_b[2]) / J[2];
 }
 
-/* Power of each wing (Sec. 3.4, Eq. insect_power): aerodynamic
+/* Power of each wing (Sec. 3.5, Eq. insect_power): aerodynamic
  * P = -m . (Omega_w - Omega_b) with the wing's moment about its pivot (force
  * row) and its rotation rate relative to the body in the global frame;
  * inertial P = Omega^(w) . (J Omega'^(w) + Omega^(w) x J Omega^(w)). */
@@ -192,7 +192,7 @@ void orc_frames_at(const orc_insect *ins, double t, orc_frames *fr)
     memset(fr, 0, sizeof *fr);
 
     if (ins->free_flight) {
-        /* Sec. 3.5: orientation from the quaternion, Omega^(b) from the state */
+        /* Sec. 3.6: orientation from the quaternion, Omega^(b) from the state */
         double Rq[9];
         quat_body_to_global(ins->quat, Rq);
         for (int i = 0; i < 3; ++i)
@@ -314,16 +314,48 @@ double orc_mask_profile(int profile, double delta, double h)
  * |x - x0| - r (the printed forms omit the radius).  The parts are joined
  * by the minimum of their distances, the union of negative-inside sets (the
  * printed max would be their intersection). */
+/* Thorax whose centre line is an arc of the circle of radius rc about
+ * (xc, 0, zc), with circular cross-sections centred on the arc (the
+ * fruit-fly body of Sec. 5.3 has this form).  Along the arc the
+ * thorax profile of the straight body applies with the arc length s, measured
+ * from the arc point in the direction of the body origin, in place of x^(b):
+ * radius b sqrt(1 - (s/a)^2) for |s| <= a, beyond it the distance to the arc's
+ * end point. */
+static double curved_thorax_distance(const orc_insect *ins, const double *xb)
+{
+    const double a = ins->body_a, b = ins->body_b;
+    const double rc = ins->body_arc[0], xc = ins->body_arc[1], zc = ins->body_arc[2];
+    /* angles about the circle's centre, from +z^(b) towards +x^(b) */
+    const double th0 = atan2(-xc, -zc);
+    const double vx = xb[0] - xc, vz = xb[2] - zc;
+    double dth = atan2(vx, vz) - th0;
+    while (dth > PI) dth -= 2.0 * PI;
+    while (dth <= -PI) dth += 2.0 * PI;
+    const double s = rc * dth;
+    const double rp = sqrt(vx * vx + vz * vz);
+    if (fabs(s) <= a) {
+        const double dc = sqrt((rp - rc) * (rp - rc) + xb[1] * xb[1]);
+        return dc - b * sqrt(1.0 - (s / a) * (s / a));
+    }
+    const double te = th0 + (s > 0 ? a : -a) / rc;
+    const double ex = xc + rc * sin(te), ez = zc + rc * cos(te);
+    return sqrt((xb[0] - ex) * (xb[0] - ex) + xb[1] * xb[1] + (xb[2] - ez) * (xb[2] - ez));
+}
+
 double orc_body_distance(const orc_insect *ins, const double *xb)
 {
     if (ins->body_type == 1)
         return sqrt(xb[0] * xb[0] + xb[1] * xb[1] + xb[2] * xb[2]) - ins->body_a;
-    double a = ins->body_a, b = ins->body_b;
-    double rr = sqrt(xb[1] * xb[1] + xb[2] * xb[2]);
-    double ax = fabs(xb[0]);
     double d;
-    if (ax <= a) d = rr - sqrt(b * b * (1.0 - (xb[0] / a) * (xb[0] / a)));
-    else d = sqrt(rr * rr + (ax - a) * (ax - a));
+    if (ins->body_type == 3) {
+        d = curved_thorax_distance(ins, xb);
+    } else {
+        double a = ins->body_a, b = ins->body_b;
+        double rr = sqrt(xb[1] * xb[1] + xb[2] * xb[2]);
+        double ax = fabs(xb[0]);
+        if (ax <= a) d = rr - sqrt(b * b * (1.0 - (xb[0] / a) * (xb[0] / a)));
+        else d = sqrt(rr * rr + (ax - a) * (ax - a));
+    }
     if (ins->head_r > 0) {
         double e[3] = {xb[0] - ins->head_x0[0], xb[1] - ins->head_x0[1], xb[2] - ins->head_x0[2]};
         double dh = sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]) - ins->head_r;
@@ -350,7 +382,7 @@ static double contour_radius(const orc_insect *ins, double th)
     return R;
 }
 
-/* Signed distance of a wing in its frame (Sec. 3.3). */
+/* Signed distance of a wing in its frame (Sec. 3.4). */
 double orc_wing_distance(const orc_insect *ins, const double *xw)
 {
     double dz = fabs(xw[2]) - 0.5 * ins->wing_h;

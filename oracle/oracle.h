@@ -53,7 +53,7 @@ typedef struct {
 } orc_params;
 
 typedef struct {
-    int body_type;       /* 0 none, 1 sphere, 2 ellipsoid (thorax)        */
+    int body_type;       /* 0 none, 1 sphere, 2 ellipsoid (thorax), 3 thorax on a circular centre line */
     int nwings;          /* 0, 1 (left only) or 2                         */
     int profile;         /* 0: cosine layer of Sec. 2.2, 1: tanh layer    */
     int nfourier;        /* harmonics used in the kinematics series       */
@@ -73,7 +73,7 @@ typedef struct {
      * radius 0: absent.  The right eye mirrors the left one in y^(b). */
     double head_x0[3], head_r;
     double eye_x0[3], eye_r;
-    /* Wing outline (Sec. 3.3): 0 = rectangular plate (wing_c_le, wing_c_te,
+    /* Wing outline (Sec. 3.4): 0 = rectangular plate (wing_c_le, wing_c_te,
      * wing_R); 1 = contour R(theta) = a0/2 + sum a_i cos(i theta) + b_i sin(i theta)
      * about (contour_xc, contour_yc) in the wing plane, theta measured from
      * x^(w) towards y^(w). */
@@ -82,9 +82,9 @@ typedef struct {
     double contour_xc, contour_yc;
     double contour_a0, contour_a[ORC_MAX_CONTOUR], contour_b[ORC_MAX_CONTOUR];
     /* Wing tensor of inertia in the wing frame (xx, yy, zz, xy, xz, yz) for
-     * the inertial power (Sec. 3.4). */
+     * the inertial power (Sec. 3.5). */
     double J_wing[6];
-    /* Free flight (Sec. 3.5): 0 = tethered (the body moves as the fields
+    /* Free flight (Sec. 3.6): 0 = tethered (the body moves as the fields
      * above prescribe); 1 = x_cntr, u_cntr, quat and Omega_body are the state
      * of the Newton-Euler system, advanced by each step. */
     int free_flight;
@@ -94,6 +94,9 @@ typedef struct {
     double dof[6];              /* 1/0 on du_x, du_y, du_z, dOmega_x, dOmega_y, dOmega_z */
     double quat[4];             /* orientation epsilon_0..3 (free flight)         */
     double Omega_body[3];       /* Omega^(b) (free flight)                        */
+    /* body_type 3: centre-line circle of radius body_arc[0] about
+     * (body_arc[1], 0, body_arc[2]) in the x^(b)-z^(b) plane (Sec. 5.3). */
+    double body_arc[3];
 } orc_insect;
 
 /* Time-level data of the AB2 scheme besides the two spectral fields. */

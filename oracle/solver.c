@@ -490,13 +490,13 @@ int orc_step(const orc_params *p, orc_insect *ins, double complex *uh,
     row[20] = sums[ORC_SUM_EKIN];
     row[21] = sums[ORC_SUM_UMAX];
 
-    /* power of the wings at t^n (Sec. 3.4) */
+    /* power of the wings at t^n (Sec. 3.5) */
     orc_frames fr;
     if (ins) orc_frames_at(ins, s->t, &fr);
     row[22] = row[23] = row[24] = row[25] = 0.0;
     if (ins) orc_wing_power(ins, &fr, row, row + 22, row + 24);
 
-    /* free flight (Sec. 3.5): the body state advances with the fluid's AB2
+    /* free flight (Sec. 3.6): the body state advances with the fluid's AB2
      * (same dt and ratio, Euler on the first step); the quaternion is
      * renormalized after each step (a reading).  Force: all colours; moment:
      * about x_cntr, the wings' moments moved from their pivots. */
