@@ -54,7 +54,7 @@ def parse():
                     help="add the wake-removal terms: a vorticity sponge (C_sp 0.1) 32 grid "
                          "points deep at the x and y ends and a Dirichlet layer 4 points deep at the x end")
     ap.add_argument("--flight", action="store_true",
-                    help="free flight (Sec. 3.5) with the power columns: the body state advances "
+                    help="free flight (Sec. 3.6) with the power columns: the body state advances "
                          "every step (mass 400, J_body (2, 5, 5), g 9.81, wing J set)")
     ap.add_argument("--shape", default=None,
                     help="nx,ny,nz: a reduced grid of the same box and insect (profiling)")
@@ -223,7 +223,7 @@ class Clocks:
 # --------------------------------------------------------------- CPU oracle
 
 def in_free_flight(ins):
-    """The insect in free flight (Sec. 3.5) with a wing tensor of inertia for
+    """The insect in free flight (Sec. 3.6) with a wing tensor of inertia for
     the power columns; heavy enough that the impulsive start in the inflow
     moves it by a fraction of its length over a few hundred steps."""
     return dict(ins, J_wing=(2e-2, 1e-3, 2e-2, 1e-4, 0.0, 0.0),

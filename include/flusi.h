@@ -60,7 +60,7 @@ typedef enum { FLUSI_HOST_FP64 = 0, FLUSI_HOST_FP32 = 1, FLUSI_DEVICE = 2 } flus
 /* Columns of one force row (Eqs. force_with_unst_corrections and
  * moment_of_love, one block per mask colour: 0 body, 1 left wing, 2 right;
  * the moment of the body about x_cntr, of a wing about its pivot), then the
- * power of each wing (Sec. 3.4, Eq. insect_power): aerodynamic
+ * power of each wing (Sec. 3.5, Eq. insect_power): aerodynamic
  * P = -M_wing . (Omega_wing - Omega_body), global frame, and inertial
  * P = Omega^(w) . (J Omega'^(w) + Omega^(w) x J Omega^(w)), wing frame. */
 #define FLUSI_COL_T 0
@@ -102,7 +102,8 @@ typedef struct flusi_options {
  * angles are Fourier series a0/2 + sum_i a[i] cos(2 pi (i+1) f t)
  * + b[i] sin(2 pi (i+1) f t), i < nfourier. */
 typedef struct flusi_insect {
-    int body_type;             /* 0 none, 1 sphere (radius body_a), 2 ellipsoid thorax */
+    int body_type;             /* 0 none, 1 sphere (radius body_a), 2 ellipsoid thorax,
+                                  3 thorax on a circular centre line (body_arc)        */
     int nwings;                /* 0, 1 (left wing only) or 2                            */
     int profile;               /* 0: cosine layer (Sec. 2.2); 1: 1/2 (1 - tanh(delta/h)) */
     int nfourier;              /* harmonics used, <= FLUSI_MAX_FOURIER                  */
@@ -124,7 +125,7 @@ typedef struct flusi_insect {
      * signed distances (their union). */
     double head_x0[3], head_r;
     double eye_x0[3], eye_r;
-    /* Wing outline (Sec. 3.3): wing_shape 0 = the rectangular plate above;
+    /* Wing outline (Sec. 3.4): wing_shape 0 = the rectangular plate above;
      * 1 = the contour R(theta) = a0/2 + sum_{i<=ncontour} a_i cos(i theta) +
      * b_i sin(i theta) (Eq. Fourier_radious_wing, theta in radians from x^(w)
      * towards y^(w)) about (contour_xc, contour_yc) in the wing plane, with
@@ -134,9 +135,9 @@ typedef struct flusi_insect {
     double contour_xc, contour_yc;
     double contour_a0, contour_a[FLUSI_MAX_CONTOUR], contour_b[FLUSI_MAX_CONTOUR];
     /* Tensor of inertia of one wing in its own frame (xx, yy, zz, xy, xz, yz),
-     * used only by the inertial power column (Sec. 3.4). */
+     * used only by the inertial power column (Sec. 3.5). */
     double J_wing[6];
-    /* Free flight (Sec. 3.5, Eq. oh_my_god_look_a_vector).  0: the body moves
+    /* Free flight (Sec. 3.6, Eq. oh_my_god_look_a_vector).  0: the body moves
      * as x_cntr, u_cntr and the angles above prescribe (tethered).  1: x_cntr,
      * u_cntr, quat and Omega_body are the initial state of the 13 Newton-Euler
      * equations, which every step advances on the device with the fluid's AB2
@@ -154,6 +155,15 @@ typedef struct flusi_insect {
                                   1 free, 0 held                                 */
     double quat[4];            /* epsilon_0..3; all zero: from (psi, beta, gamma)  */
     double Omega_body[3];      /* Omega^(b), body frame                           */
+    /* body_type 3 (the fruit-fly body of Sec. 5.3): the thorax (body_a, body_b)
+     * bent along an arc of the circle of radius body_arc[0] about
+     * (body_arc[1], 0, body_arc[2]) in the x^(b)-z^(b) plane, with circular
+     * cross-sections of radius body_b sqrt(1 - (s/body_a)^2) centred on the
+     * arc, s the arc length from the arc point towards the body origin; beyond
+     * |s| = body_a the distance is that to the arc's end point.  Needs
+     * body_b < body_arc[0], body_a < pi body_arc[0], and the circle's centre
+     * away from the body origin.  Head and eyes join it as for type 2. */
+    double body_arc[3];
 } flusi_insect;
 
 /* Create a solver for an nx x ny x nz periodic grid over the box L[3], with
@@ -199,7 +209,7 @@ int flusi_set_state(flusi_t h, const void *u, int where);
  * for a bad descriptor, or free flight with time_scheme 1. */
 int flusi_set_kinematics(flusi_t h, const flusi_insect *insect);
 
-/* Free flight (Sec. 3.5): the body state after the steps enqueued so far,
+/* Free flight (Sec. 3.6): the body state after the steps enqueued so far,
  * state[13] = x_cntr[3], u_cntr[3], quat[4], Omega_body[3] (host).  Without
  * free flight it is the descriptor's (constant) values.  Synchronizes;
  * FLUSI_ESTATE without an insect or when not bound. */

@@ -66,7 +66,8 @@ class Insect(C.Structure):
                 ("J_wing", C.c_double * 6),
                 ("free_flight", C.c_int), ("pad2_", C.c_int),
                 ("mass", C.c_double), ("gravity", C.c_double), ("J_body", C.c_double * 3),
-                ("dof", C.c_double * 6), ("quat", C.c_double * 4), ("Omega_body", C.c_double * 3)]
+                ("dof", C.c_double * 6), ("quat", C.c_double * 4), ("Omega_body", C.c_double * 3),
+                ("body_arc", C.c_double * 3)]
 
 
 def _load():
@@ -285,7 +286,9 @@ def make_insect(d: dict | None) -> Insect | None:
     if d is None:
         return None
     s = Insect()
-    s.body_type = {"none": 0, "sphere": 1, "ellipsoid": 2}[d.get("body", "none")]
+    s.body_type = {"none": 0, "sphere": 1, "ellipsoid": 2, "curved": 3}[d.get("body", "none")]
+    if "body_arc" in d:
+        s.body_arc[:] = d["body_arc"]     # (radius, x centre, z centre), body frame
     s.nwings = d.get("nwings", 0)
     s.profile = {"cos": 0, "tanh": 1}[d.get("profile", "cos")]
     s.c_smth = d.get("c_smth", 1.0)

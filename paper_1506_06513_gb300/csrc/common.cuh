@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+
 #include "../../include/flusi.h"
 
 namespace flusi {
@@ -105,7 +107,33 @@ struct Shape {
     int ncontour, pad;
     double contour_xc, contour_yc, contour_a0;
     double contour_a[FLUSI_MAX_CONTOUR], contour_b[FLUSI_MAX_CONTOUR];
+    // body_type 3: centre-line circle (radius, centre x, z), the unit vector
+    // from its centre towards the body origin, and the arc's end points (x, z)
+    double arc_r, arc_x, arc_z, arc_ux, arc_uz;
+    double arc_end[2][2];
 };
+
+// Why a descriptor cannot be used, or nullptr (checks shared by every entry
+// point that takes one; the free-flight fields are checked where they apply).
+inline const char* insect_error(const flusi_insect& I)
+{
+    if (I.body_type < 0 || I.body_type > 3 || I.nwings < 0 || I.nwings > 2 || I.profile < 0 ||
+        I.profile > 1 || I.nfourier < 0 || I.nfourier > FLUSI_MAX_FOURIER || !(I.c_smth > 0))
+        return "bad insect descriptor (body_type, nwings, profile, nfourier or c_smth)";
+    if ((I.body_type == 1 && !(I.body_a > 0)) || (I.body_type >= 2 && !(I.body_a > 0 && I.body_b > 0)))
+        return "bad insect descriptor (body axes)";
+    if (I.body_type == 3) {
+        const double pi = 3.141592653589793238462643383279;
+        const double d = std::sqrt(I.body_arc[1] * I.body_arc[1] + I.body_arc[2] * I.body_arc[2]);
+        if (!(I.body_arc[0] > I.body_b) || !(I.body_a < pi * I.body_arc[0]) || !(d > 0) || !std::isfinite(d))
+            return "bad insect descriptor (body_arc: need body_b < radius, body_a < pi radius, "
+                   "centre away from the body origin)";
+    }
+    if (!(I.head_r >= 0) || !(I.eye_r >= 0) || I.wing_shape < 0 || I.wing_shape > 1 || I.ncontour < 0 ||
+        I.ncontour > FLUSI_MAX_CONTOUR || (I.wing_shape == 1 && !(I.contour_a0 > 0)))
+        return "bad insect descriptor (head, eyes or wing outline)";
+    return nullptr;
+}
 
 // Mask shape of an insect descriptor with smoothing half-width h.
 inline Shape shape_of(const flusi_insect& I, double h)
@@ -135,6 +163,24 @@ inline Shape shape_of(const flusi_insect& I, double h)
     for (int i = 0; i < FLUSI_MAX_CONTOUR; ++i) {
         s.contour_a[i] = i < I.ncontour ? I.contour_a[i] : 0.0;
         s.contour_b[i] = i < I.ncontour ? I.contour_b[i] : 0.0;
+    }
+    if (I.body_type == 3) {
+        s.arc_r = I.body_arc[0];
+        s.arc_x = I.body_arc[1];
+        s.arc_z = I.body_arc[2];
+        const double d = std::sqrt(s.arc_x * s.arc_x + s.arc_z * s.arc_z);
+        s.arc_ux = -s.arc_x / d;
+        s.arc_uz = -s.arc_z / d;
+        // end points at the angles theta_0 -+ a / r_c about the centre
+        // (angles from +z^(b) towards +x^(b))
+        for (int e = 0; e < 2; ++e) {
+            const double dth = (e == 0 ? -1.0 : 1.0) * I.body_a / s.arc_r;
+            const double c = std::cos(dth), sn = std::sin(dth);
+            // rotate (ux, uz) = (sin theta_0, cos theta_0) by dth
+            const double ux = s.arc_ux * c + s.arc_uz * sn, uz = s.arc_uz * c - s.arc_ux * sn;
+            s.arc_end[e][0] = s.arc_x + s.arc_r * ux;
+            s.arc_end[e][1] = s.arc_z + s.arc_r * uz;
+        }
     }
     return s;
 }

@@ -558,15 +558,7 @@ int flusi_set_kinematics(flusi_t h, const flusi_insect* ins)
     if (!h) return FLUSI_EINVAL;
     const Shape before = make_shape(h);
     if (ins) {
-        if (ins->body_type < 0 || ins->body_type > 2 || ins->nwings < 0 || ins->nwings > 2 ||
-            ins->profile < 0 || ins->profile > 1 || ins->nfourier < 0 ||
-            ins->nfourier > FLUSI_MAX_FOURIER || !(ins->c_smth > 0) ||
-            (ins->body_type == 1 && !(ins->body_a > 0)) ||
-            (ins->body_type == 2 && !(ins->body_a > 0 && ins->body_b > 0)) ||
-            !(ins->head_r >= 0) || !(ins->eye_r >= 0) || ins->wing_shape < 0 || ins->wing_shape > 1 ||
-            ins->ncontour < 0 || ins->ncontour > FLUSI_MAX_CONTOUR ||
-            (ins->wing_shape == 1 && !(ins->contour_a0 > 0)))
-            return fail(h, FLUSI_EINVAL, "bad insect descriptor");
+        if (const char* why = insect_error(*ins)) return fail(h, FLUSI_EINVAL, why);
         if (ins->free_flight != 0 && ins->free_flight != 1) return fail(h, FLUSI_EINVAL, "free_flight must be 0 or 1");
         if (ins->free_flight) {
             bool ok = ins->mass > 0 && std::isfinite(ins->gravity) && h->opt.time_scheme == 0;

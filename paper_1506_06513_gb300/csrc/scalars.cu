@@ -89,7 +89,7 @@ __device__ void series(double a0, const double* a, const double* b, int nf, doub
 }
 
 // Body-to-global matrix of the quaternion (e0, e1, e2, e3) as printed in
-// Sec. 3.5; its transpose is the global-to-body matrix M_body.
+// Sec. 3.6; its transpose is the global-to-body matrix M_body.
 __device__ M3 quat_to_global(const double* e)
 {
     const double a = e[0], b = e[1], c = e[2], d = e[3];
@@ -106,7 +106,7 @@ __device__ void box_grow(double* box, const double* p)
     }
 }
 
-// Free flight (Sec. 3.5, Eq. oh_my_god_look_a_vector): one AB2 step of the
+// Free flight (Sec. 3.6, Eq. oh_my_god_look_a_vector): one AB2 step of the
 // 13 body equations with the fluid step's dt and ratio r = dt/dt_prev (Euler
 // when `first`).  State y = (x_cntr, u_cntr, quat, Omega_body); forcing: the
 // row's total force and its total moment about x_cntr, taken into body axes.
@@ -186,7 +186,7 @@ __global__ void k_kinematics(const flusi_insect* ins, const StepState* st, const
     }
     M3 Mb;
     if (ins->free_flight) {
-        // Sec. 3.5: the orientation is the quaternion's, Omega^(b) is state
+        // Sec. 3.6: the orientation is the quaternion's, Omega^(b) is state
         const M3 Q = quat_to_global(ins->quat);
         for (int i = 0; i < 3; ++i)
             for (int j = 0; j < 3; ++j) Mb.a[3 * i + j] = Q.a[3 * j + i];
@@ -274,12 +274,30 @@ __global__ void k_kinematics(const flusi_insect* ins, const StepState* st, const
         hi[0] = ins->body_a;
         lo[1] = lo[2] = -ey;
         hi[1] = hi[2] = ey;
-        if (ins->body_type == 2 && ins->head_r > 0)
+        if (ins->body_type == 3) {
+            // the arc x = x_c + r_c sin th, z = z_c + r_c cos th over
+            // th0 -+ a/r_c: its ends and the quarter angles inside, grown by b
+            const double rc = ins->body_arc[0], xc = ins->body_arc[1], zc = ins->body_arc[2];
+            const double th0 = atan2(-xc, -zc), t1 = th0 - ins->body_a / rc, t2 = th0 + ins->body_a / rc;
+            const double half_pi = 1.5707963267948966192313216916398;
+            lo[0] = lo[2] = 1e300;
+            hi[0] = hi[2] = -1e300;
+            const int k1 = (int)ceil(t1 / half_pi), k2 = (int)floor(t2 / half_pi);
+            for (int k = k1 - 1; k <= k2 + 1; ++k) {
+                const double th = k < k1 ? t1 : k > k2 ? t2 : k * half_pi;
+                const double px = xc + rc * sin(th), pz = zc + rc * cos(th);
+                lo[0] = fmin(lo[0], px - ins->body_b);
+                hi[0] = fmax(hi[0], px + ins->body_b);
+                lo[2] = fmin(lo[2], pz - ins->body_b);
+                hi[2] = fmax(hi[2], pz + ins->body_b);
+            }
+        }
+        if (ins->body_type >= 2 && ins->head_r > 0)
             for (int i = 0; i < 3; ++i) {
                 lo[i] = fmin(lo[i], ins->head_x0[i] - ins->head_r);
                 hi[i] = fmax(hi[i], ins->head_x0[i] + ins->head_r);
             }
-        if (ins->body_type == 2 && ins->eye_r > 0)
+        if (ins->body_type >= 2 && ins->eye_r > 0)
             for (int i = 0; i < 3; ++i) {
                 const double c = ins->eye_x0[i], m = i == 1 ? -c : c;   // both eyes
                 lo[i] = fmin(lo[i], fmin(c, m) - ins->eye_r);
@@ -451,7 +469,7 @@ __global__ void k_scalars(Geom g, const double* part, int nparts, StepState* st,
         row[20] = 0.5 * tot[kSumEkin] * dV;
         row[21] = umax;
 
-        // wing power at t^n (Sec. 3.4, Eq. insect_power)
+        // wing power at t^n (Sec. 3.5, Eq. insect_power)
         const Frame& F = *fr;
         for (int s = 0; s < 2; ++s) {
             double pa = 0.0, pi = 0.0;

@@ -36,6 +36,7 @@ template <typename T> struct FrameT {
     int body_type, profile, wing_shape, ncontour;
     T head_x0[3], head_r, eye_x0[3], eye_r;
     T cxc, cyc, ca0, ca[FLUSI_MAX_CONTOUR], cb[FLUSI_MAX_CONTOUR];
+    T arc_r, arc_x, arc_z, arc_ux, arc_uz, arc_end[2][2];
 };
 
 // The pass's copy of the frame (FP64 on the device) and mask shape in T.
@@ -81,13 +82,23 @@ __device__ void setup_frame(FrameT<T>& f, const Frame& F, const Shape& S, double
         f.ca[i] = T(S.contour_a[i]);
         f.cb[i] = T(S.contour_b[i]);
     }
+    f.arc_r = T(S.arc_r);
+    f.arc_x = T(S.arc_x);
+    f.arc_z = T(S.arc_z);
+    f.arc_ux = T(S.arc_ux);
+    f.arc_uz = T(S.arc_uz);
+    for (int e = 0; e < 2; ++e) {
+        f.arc_end[e][0] = T(S.arc_end[e][0]);
+        f.arc_end[e][1] = T(S.arc_end[e][1]);
+    }
     if (S.body_type == 0) f.active[0] = 0;
     if (S.nwings < 1) f.active[1] = 0;
     if (S.nwings < 2) f.active[2] = 0;
 }
 
-// Signed distance of the body in its frame (Sec. 3.2): thorax (sphere or
-// ellipsoid), joined with the head and eye spheres by the minimum.
+// Signed distance of the body in its frame (Sec. 3.2): thorax (sphere,
+// ellipsoid, or the ellipsoid bent along a circular arc as for the fruit fly
+// of Sec. 5.3), joined with the head and eye spheres by the minimum.
 template <typename T>
 __device__ __forceinline__ T body_delta(const FrameT<T>& F, const T* xb)
 {
@@ -95,12 +106,28 @@ __device__ __forceinline__ T body_delta(const FrameT<T>& F, const T* xb)
     if (F.body_type == 1) {
         delta = sqrt(xb[0] * xb[0] + xb[1] * xb[1] + xb[2] * xb[2]) - F.a;
     } else {
-        T rr = sqrt(xb[1] * xb[1] + xb[2] * xb[2]), ax = fabs(xb[0]);
-        if (ax <= F.a) {
-            T q = xb[0] / F.a;
-            delta = rr - F.b * sqrt(fmax(T(0), T(1) - q * q));
+        if (F.body_type == 3) {
+            // arc length s of the point's angle about the circle's centre,
+            // from the direction u towards the body origin; the offset from
+            // the centre line in the circle's plane is r - r_c, across it y
+            const T vx = xb[0] - F.arc_x, vz = xb[2] - F.arc_z;
+            const T s = F.arc_r * atan2(vx * F.arc_uz - vz * F.arc_ux, vx * F.arc_ux + vz * F.arc_uz);
+            if (fabs(s) <= F.a) {
+                const T dr = sqrt(vx * vx + vz * vz) - F.arc_r, q = s / F.a;
+                delta = sqrt(dr * dr + xb[1] * xb[1]) - F.b * sqrt(fmax(T(0), T(1) - q * q));
+            } else {
+                const T* e = F.arc_end[s > T(0) ? 1 : 0];
+                const T ex = xb[0] - e[0], ez = xb[2] - e[1];
+                delta = sqrt(ex * ex + xb[1] * xb[1] + ez * ez);
+            }
         } else {
-            delta = sqrt(rr * rr + (ax - F.a) * (ax - F.a));
+            T rr = sqrt(xb[1] * xb[1] + xb[2] * xb[2]), ax = fabs(xb[0]);
+            if (ax <= F.a) {
+                T q = xb[0] / F.a;
+                delta = rr - F.b * sqrt(fmax(T(0), T(1) - q * q));
+            } else {
+                delta = sqrt(rr * rr + (ax - F.a) * (ax - F.a));
+            }
         }
         if (F.head_r > T(0)) {
             const T e0 = xb[0] - F.head_x0[0], e1 = xb[1] - F.head_x0[1], e2 = xb[2] - F.head_x0[2];
@@ -117,7 +144,7 @@ __device__ __forceinline__ T body_delta(const FrameT<T>& F, const T* xb)
     return delta;
 }
 
-// Signed distance of a wing in its frame (Sec. 3.3): the rectangular plate,
+// Signed distance of a wing in its frame (Sec. 3.4): the rectangular plate,
 // or the contour R(theta) = a0/2 + sum a_i cos(i theta) + b_i sin(i theta)
 // with cos, sin of i theta from the angle-addition recurrence.
 template <typename T>
@@ -1352,10 +1379,7 @@ extern "C" int flusi_penalization_sums_noalloc(int nx, int ny, int nz, const dou
                          "FLUSI_NOALLOC_MAX_POINTS (2^30) points");
         return FLUSI_EINVAL;
     }
-    if (insect && (insect->body_type < 0 || insect->body_type > 2 || insect->nwings < 0 ||
-                   insect->nwings > 2 || insect->profile < 0 || insect->profile > 1 ||
-                   insect->nfourier < 0 || insect->nfourier > FLUSI_MAX_FOURIER ||
-                   !(insect->c_smth > 0))) {
+    if (insect && insect_error(*insect)) {
         set_global_error("flusi_penalization_sums_noalloc: bad insect descriptor");
         return FLUSI_EINVAL;
     }

@@ -106,11 +106,18 @@ def test_insect_descriptor_validation(fl):
     good = fl.make_insect(workloads.model_insect((4.0, 4.0, 4.0), (16, 16, 16)))
     fl.flusi_set_kinematics(h, good)
     fl.flusi_set_kinematics(h, None)
-    for field, bad in (("nwings", 3), ("body_type", 5), ("c_smth", 0.0), ("nfourier", 9)):
+    for field, bad in (("nwings", 3), ("body_type", 5), ("c_smth", 0.0), ("nfourier", 9),
+                       ("body_type", 3)):   # a curved thorax without its arc
         ins = fl.make_insect(workloads.model_insect((4.0, 4.0, 4.0), (16, 16, 16)))
         setattr(ins, field, bad)
         with pytest.raises(fl.FlusiError):
             fl.flusi_set_kinematics(h, ins)
+    curved = fl.make_insect(workloads.curved_insect((4.0, 4.0, 4.0), (16, 16, 16)))
+    fl.flusi_set_kinematics(h, curved)
+    for arc in ((0.1, 0.0, -1.0), (1.0, 0.0, 0.0), (0.1, 0.0, -0.05)):
+        bad = fl.make_insect(dict(workloads.curved_insect((4.0, 4.0, 4.0), (16, 16, 16)), body_arc=arc))
+        with pytest.raises(fl.FlusiError):
+            fl.flusi_set_kinematics(h, bad)
     fl.flusi_destroy(h)
 
 
@@ -119,7 +126,7 @@ def test_struct_layouts_match_header(fl):
     assert C.sizeof(fl.Options) == 3 * 8 + 3 * 8 + 4 * 4 + 7 * 8 + 2 * 4
     assert C.sizeof(fl.Insect) == (4 * 4 + 8 * (1 + 3 + 3 + 6 + 2 + 3 + 3 + 1 + 4 + 1 + 3 * 17)
                                    + 8 * (3 + 1 + 3 + 1) + 2 * 4 + 8 * (3 + 2 * 32)
-                                   + 8 * 6 + 2 * 4 + 8 * (2 + 3 + 6 + 4 + 3))
+                                   + 8 * 6 + 2 * 4 + 8 * (2 + 3 + 6 + 4 + 3) + 8 * 3)
     assert fl.FORCE_COLS == 26
 
 

@@ -1,4 +1,4 @@
-"""Wing power (Sec. 3.4) and free flight (Sec. 3.5) on the GPU against the
+"""Wing power (Sec. 3.5) and free flight (Sec. 3.6) on the GPU against the
 oracle: the power columns of the force rows, the free-fall closed form, a
 free-flying model insect step by step, a body held by its dof mask, and an
 exact restart of a free flight."""

@@ -92,6 +92,8 @@ CASES = {
                           workloads.model_insect((4.0, 4.0, 4.0), (32, 32, 32))),
     "realistic_48x32x32": lambda: (dict(workloads.config_model_insect(32)[0], n=(48, 32, 32)),
                                    workloads.realistic_insect((4.0, 4.0, 4.0), (48, 32, 32))),
+    "curved_48x32x32": lambda: (dict(workloads.config_model_insect(32)[0], n=(48, 32, 32)),
+                                workloads.curved_insect((4.0, 4.0, 4.0), (48, 32, 32))),
     "wing_48x36x24": lambda: ({"n": (48, 36, 24), "L": (4.0, 3.0, 2.0), "nu": 0.0125664,
                                "eta": 2.5e-3, "cfl": 0.1, "mean_mode": "fixed",
                                "init": ("random_smooth", 5)},
@@ -153,7 +155,7 @@ def test_c0_full_step_fp64(fl):
     assert rows_err(rows, ref_rows) <= 1e-10
 
 
-@pytest.mark.parametrize("case", ["insect_32", "realistic_48x32x32", "wing_48x36x24"])
+@pytest.mark.parametrize("case", ["insect_32", "realistic_48x32x32", "curved_48x32x32", "wing_48x36x24"])
 def test_flapping_steps_fp64(fl, case):
     """Moving wings, adaptive dt (CFL and dt <= C_eta), unsteady corrections."""
     cfg, ins = CASES[case]()

@@ -1,5 +1,5 @@
-"""Pins of the oracle's power (Sec. 3.4, Eq. insect_power) and free flight
-(Sec. 3.5, Eq. oh_my_god_look_a_vector): quaternion and yaw-pitch-roll
+"""Pins of the oracle's power (Sec. 3.5, Eq. insect_power) and free flight
+(Sec. 3.6, Eq. oh_my_god_look_a_vector): quaternion and yaw-pitch-roll
 frames agree, rigid rotation at a constant body rate, free fall with the AB2
 start-up error in closed form, a body held by its dof mask is the tethered
 run, the wing's angular acceleration is the derivative of its rate, and the

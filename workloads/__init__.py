@@ -188,7 +188,7 @@ def model_insect(L=(4.0, 4.0, 4.0), n=(512, 512, 512)):
 
 
 def contour_wing_outline(span=0.96, chord=0.3, harmonics=16):
-    """A synthetic wing outline for the contour parametrization of Sec. 3.3:
+    """A synthetic wing outline for the contour parametrization of Sec. 3.4:
     an ellipse of the given span and chord centred at mid-span on the y^(w)
     axis, with a slight forward sweep of the tip, written as the truncated
     Fourier series R(theta) = a0/2 + sum a_i cos(i theta) + b_i sin(i theta)
@@ -207,11 +207,25 @@ def contour_wing_outline(span=0.96, chord=0.3, harmonics=16):
 
 def realistic_insect(L=(4.0, 4.0, 4.0), n=(512, 512, 512)):
     """Ellipsoid thorax with a head and two eyes (Sec. 3.2) and two contour
-    wings (Sec. 3.3) with the flapping kinematics of the model insect."""
+    wings (Sec. 3.4) with the flapping kinematics of the model insect."""
     ins = model_insect(L, n)
     ins["head"] = ((0.62, 0.0, 0.04), 0.13)
     ins["eyes"] = ((0.66, 0.09, 0.08), 0.06)
     ins["contour"] = contour_wing_outline()
+    return ins
+
+
+def curved_insect(L=(4.0, 4.0, 4.0), n=(512, 512, 512)):
+    """The realistic insect with its thorax bent along a circular centre line
+    (the body form of the fruit fly of Sec. 5.3): centre-line circle of
+    radius 1 below the body origin, head and eyes moved to its front end,
+    pitched body.  Made-up geometry, no paper values."""
+    ins = realistic_insect(L, n)
+    ins["body"] = "curved"
+    ins["body_arc"] = (1.0, 0.0, -1.0)
+    ins["head"] = ((0.56, 0.0, -0.16), 0.13)
+    ins["eyes"] = ((0.6, 0.09, -0.1), 0.06)
+    ins["body_angles"] = (0.0, -0.3, 0.0)
     return ins
 
 
