@@ -317,13 +317,25 @@ __device__ __forceinline__ void fft_stage_first(cplx<T>* buf, int ld, int col, i
 
 // DIF last stage (span 1, no twiddles): butterfly j holds rows j R + t, which
 // are frequencies f0 + t fstep with f0 the frequency of row j R and fstep = n / R.
-template <typename T, int R, bool INV, int V, class Store>
+// With AUX the store is an object that also takes one side-input row per
+// output (store.aux(f, a) reads it, store.put(f, v, a) writes); the side rows
+// of the first half of a butterfly's outputs are read before its DFT, so
+// their latency overlaps it, those of the second half after the first puts
+// (half the registers of holding all R).
+template <typename T, int R, bool INV, int V, bool AUX, class Store>
 __device__ __forceinline__ void fft_stage_last(const cplx<T>* buf, int ld, int col, int jt, int P,
                                                int nbf, int fstep, const int* sinv, Store& store)
 {
     constexpr int kUnroll = V == 1 ? 2 : 1;
+    constexpr int H = AUX ? (R + 1) / 2 : 1;
 #pragma unroll kUnroll
     for (int j = jt; j < nbf; j += P) {
+        const int f0 = sinv[j * R];
+        cplx<T> a[H][V];
+        if constexpr (AUX) {
+#pragma unroll
+            for (int t = 0; t < H; ++t) store.aux(f0 + t * fstep, a[t]);
+        }
         cplx<T> v[V][R];
         const cplx<T>* p = buf + j * R * ld + col;
 #pragma unroll
@@ -335,34 +347,41 @@ __device__ __forceinline__ void fft_stage_last(const cplx<T>* buf, int ld, int c
         }
 #pragma unroll
         for (int c = 0; c < V; ++c) Dft<T, R, INV>::run(v[c]);
-        const int f0 = sinv[j * R];
 #pragma unroll
         for (int t = 0; t < R; ++t) {
             cplx<T> r[V];
 #pragma unroll
             for (int c = 0; c < V; ++c) r[c] = v[c][t];
-            store(f0 + t * fstep, r);
+            if constexpr (AUX) {
+                if (t == H) {
+#pragma unroll
+                    for (int u = 0; u < H && H + u < R; ++u) store.aux(f0 + (H + u) * fstep, a[u]);
+                }
+                store.put(f0 + t * fstep, r, a[t % H]);
+            } else {
+                store(f0 + t * fstep, r);
+            }
         }
     }
 }
 
-template <typename T, bool INV, int V, class Store>
+template <typename T, bool INV, int V, bool AUX = false, class Store>
 __device__ __forceinline__ void fft_last_to(const cplx<T>* buf, int ld, int col, int jt, int P,
                                             const FftPlan& plan, const int* sinv, Store& store)
 {
     const int last = plan.nst - 1;
     const int R = plan.radix[last], nbf = plan.n / R, fstep = plan.n / R;
     switch (R) {
-    case 8: fft_stage_last<T, 8, INV, V>(buf, ld, col, jt, P, nbf, fstep, sinv, store); break;
-    case 4: fft_stage_last<T, 4, INV, V>(buf, ld, col, jt, P, nbf, fstep, sinv, store); break;
-    case 3: fft_stage_last<T, 3, INV, V>(buf, ld, col, jt, P, nbf, fstep, sinv, store); break;
-    default: fft_stage_last<T, 2, INV, V>(buf, ld, col, jt, P, nbf, fstep, sinv, store); break;
+    case 8: fft_stage_last<T, 8, INV, V, AUX>(buf, ld, col, jt, P, nbf, fstep, sinv, store); break;
+    case 4: fft_stage_last<T, 4, INV, V, AUX>(buf, ld, col, jt, P, nbf, fstep, sinv, store); break;
+    case 3: fft_stage_last<T, 3, INV, V, AUX>(buf, ld, col, jt, P, nbf, fstep, sinv, store); break;
+    default: fft_stage_last<T, 2, INV, V, AUX>(buf, ld, col, jt, P, nbf, fstep, sinv, store); break;
     }
 }
 
 // Stage 0 from `load`, the middle stages in shared memory, the last stage to
 // `store` (sinv[row] = frequency held by that row).  All threads must call.
-template <typename T, bool INV, int V, class Load, class Store>
+template <typename T, bool INV, int V, bool AUX = false, class Load, class Store>
 __device__ void fft_dif_io(cplx<T>* buf, int C, int ld, const FftPlan& plan, const cplx<T>* tw,
                            const int* sinv, Load load, Store store)
 {
@@ -379,23 +398,29 @@ __device__ void fft_dif_io(cplx<T>* buf, int C, int ld, const FftPlan& plan, con
         for (int f = jt; f < plan.n; f += P) {
             cplx<T> r[V];
             ld_row<T, V>(buf + f * ld + col, r);
-            store(f, r);
+            if constexpr (AUX) {
+                cplx<T> a[V];
+                store.aux(f, a);
+                store.put(f, r, a);
+            } else {
+                store(f, r);
+            }
         }
         return;
     }
     fft_run<T, INV, true, V>(buf, C, ld, plan, tw, 1, last);
-    fft_last_to<T, INV, V>(buf, ld, col, jt, P, plan, sinv, store);
+    fft_last_to<T, INV, V, AUX>(buf, ld, col, jt, P, plan, sinv, store);
 }
 
 // All stages but the last in shared memory (input tile in natural order), the
 // last stage to `store`.  All threads must call.
-template <typename T, bool INV, int V, class Store>
+template <typename T, bool INV, int V, bool AUX = false, class Store>
 __device__ void fft_dif_out(cplx<T>* buf, int C, int ld, const FftPlan& plan, const cplx<T>* tw,
                             const int* sinv, Store store)
 {
     const int G = C / V, P = blockDim.x / G, col = (threadIdx.x % G) * V, jt = threadIdx.x / G;
     fft_run<T, INV, true, V>(buf, C, ld, plan, tw, 0, plan.nst - 1);
-    fft_last_to<T, INV, V>(buf, ld, col, jt, P, plan, sinv, store);
+    fft_last_to<T, INV, V, AUX>(buf, ld, col, jt, P, plan, sinv, store);
 }
 
 // Inverse digit-reversal table in shared memory: sinv[pos[f]] = f.

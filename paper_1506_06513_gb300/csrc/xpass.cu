@@ -670,8 +670,9 @@ k_xpass(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict
 // each: the length-nh transforms are two register-resident radix-R passes
 // (DIF stage 0 then stage 1 for the inverse, their transposes in reverse for
 // the forward transform) exchanging through the line's own shared-memory
-// slice, so they need __syncwarp only.  A line's slice stores logical row r at
-// r + r/R (one pad slot per R rows) so both passes are free of bank conflicts.
+// slice, so they need __syncwarp only.  A line's slice stores logical row
+// R q + j at R q + (j ^ q), so both passes are free of bank conflicts without
+// padding (sq_slot).
 // The c2r mirror values X[nh - k] and the r2c mirror values Z[nh - k] are
 // exchanged between lanes j and R - j with warp shuffles; inputs are loaded
 // from global memory straight into registers and outputs are stored from
@@ -717,15 +718,23 @@ __device__ __forceinline__ void sq_exchange_pre(cplx<T>* x, int j, int width, co
     }
 }
 
+// Shared-memory slot of logical row R q + j of a line slice: the column
+// index is XOR-ed with the row, so both the column-wise (pass 1) and the
+// row-wise (pass 2) accesses of R lanes meet R distinct banks.
+template <int R> __device__ __forceinline__ int sq_slot(int lrow)
+{
+    return (lrow & ~(R - 1)) | ((lrow ^ (lrow / R)) & (R - 1));
+}
+
 template <typename T, int R, bool LAYER, bool SPONGE>
-__global__ void __launch_bounds__(192, sizeof(T) == 4 ? 3 : 1)
+__global__ void __launch_bounds__(192, sizeof(T) == 4 ? 4 : 1)
 k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExtra ex,
            const StepState* __restrict__ st)
 {
     if (st && st->status != 0) return;
     constexpr int RB = sq_rows<R>();
     constexpr int NH = R * R;
-    constexpr int CS = NH + R;             // padded line slice
+    constexpr int CS = NH;                 // line slice; logical row R q + j at R q + (j ^ q)
     const int nx = g.nx, Mx = g.Mx, Mxp = g.Mxp;
     const int nrows = g.nz * g.ny;
     const int ntiles = ceil_div(nrows, RB);
@@ -735,13 +744,14 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
     FrameT<T>* Fs = reinterpret_cast<FrameT<T>*>(wacc + kWarpsX * 36);
     cplx<T>* twx = reinterpret_cast<cplx<T>*>(
         reinterpret_cast<unsigned char*>(Fs) + ((sizeof(FrameT<T>) + 15) / 16) * 16);
-    cplx<T>* tw2 = twx + nx;               // tw2[q R + j] = w_nh^{j q}
+    cplx<T>* tw2 = twx + NH;               // tw2[q R + j] = w_nh^{j q}
     cplx<T>* buf = tw2 + NH;               // C line slices of CS values
     __shared__ int rowmask[RB];
 
     const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
     const int c = tid / R, j = tid % R;    // this lane's line and index within it
-    for (int i = tid; i < nx; i += blockDim.x) twx[i] = mkc<T>(T(tw[i].x), T(tw[i].y));
+    // w_nx^k for k < nh: the c2r/r2c mirror steps use no higher power
+    for (int i = tid; i < NH; i += blockDim.x) twx[i] = mkc<T>(T(tw[i].x), T(tw[i].y));
     for (int i = tid; i < NH; i += blockDim.x) {
         const int q = i / R, jj = i % R;
         const double2 w = tw[(2 * jj * q) % nx];
@@ -805,13 +815,13 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
 #pragma unroll
             for (int q = 1; q < R; ++q) v[q] = cmul(v[q], cconj(tw2[q * R + j]));
 #pragma unroll
-            for (int q = 0; q < R; ++q) line[j + R * q + q] = v[q];
+            for (int q = 0; q < R; ++q) line[R * q + (j ^ q)] = v[q];
             __syncwarp();
 #pragma unroll
-            for (int i = 0; i < R; ++i) v[i] = line[R * j + i + j];
+            for (int i = 0; i < R; ++i) v[i] = line[R * j + (i ^ j)];
             Dft<T, R, true>::run(v);
 #pragma unroll
-            for (int d = 0; d < R; ++d) line[R * j + d + j] = v[d];
+            for (int d = 0; d < R; ++d) line[R * j + (d ^ j)] = v[d];
         }
         __syncthreads();
 
@@ -824,7 +834,7 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
                 const int i = tid + it * 192;
                 const int rr = i / NH, lrow = i % NH;
                 if (i < items && row0 + rr < nrows) {
-                    const int slot = lrow + lrow / R;
+                    const int slot = sq_slot<R>(lrow);
                     cplx<T> uv[3], wv[3];
 #pragma unroll
                     for (int q = 0; q < 3; ++q) {
@@ -900,7 +910,7 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
                         // point xi is half h of pair p, held at logical row R (p % R) + p / R
                         const int pp = xi >> 1, h = xi & 1;
                         const int lrow = R * (pp % R) + pp / R;
-                        const int slot = lrow + lrow / R;
+                        const int slot = sq_slot<R>(lrow);
                         const T pen = chi * F.inv_eta;
 #pragma unroll
                         for (int q = 0; q < 3; ++q) {
@@ -955,13 +965,13 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
             cplx<T>* line = buf + (3 * RB + c + li * NG) * CS;
             const int fld = 3 * li + c / RB, lrr = c % RB;
 #pragma unroll
-            for (int i = 0; i < R; ++i) v[i] = line[R * j + i + j];
+            for (int i = 0; i < R; ++i) v[i] = line[R * j + (i ^ j)];
             Dft<T, R, false>::run(v);
 #pragma unroll
-            for (int d = 0; d < R; ++d) line[R * j + d + j] = v[d];
+            for (int d = 0; d < R; ++d) line[R * j + (d ^ j)] = v[d];
             __syncwarp();
 #pragma unroll
-            for (int t = 0; t < R; ++t) v[t] = line[j + R * t + t];
+            for (int t = 0; t < R; ++t) v[t] = line[R * t + (j ^ t)];
 #pragma unroll
             for (int t = 1; t < R; ++t) v[t] = cmul(v[t], tw2[t * R + j]);
             Dft<T, R, false>::run(v);      // v[q] = Z[j + R q]
@@ -1027,7 +1037,7 @@ template <typename T, int R> size_t sq_smem(const Geom& g, bool sponge = false)
 {
     const int RB = sq_rows<R>(), NH = R * R;
     size_t s = sizeof(double) * kWarpsX * 36 + ((sizeof(FrameT<T>) + 15) / 16) * 16;
-    s += sizeof(cplx<T>) * ((size_t)g.nx + NH + (size_t)(sponge ? 9 : 6) * RB * (NH + R));
+    s += sizeof(cplx<T>) * ((size_t)2 * NH + (size_t)(sponge ? 9 : 6) * RB * NH);
     return s;
 }
 

@@ -6,10 +6,11 @@
 // in registers as the first FFT stage loads it.  The inverse pass stores its
 // last stage's results from registers.
 //
-// zinv (Algorithm 1 step c, first half): loads the state u_hat, forms
-//   omega_hat = i k x u_hat on the fly (Sec. 2.4: grad -> i k), fills the
+// zinv (Algorithm 1 step c, first half): loads the state u_hat, fills the
 //   dropped z-modes with zeros and transforms back to z grid points:
-//   W[f] = iFFT_z(field f), f < 3 velocity, f = 3..5 vorticity.
+//   W[f] = iFFT_z(field f), f < 3 velocity, f = 3..5 the vorticity
+//   omega_hat = i k x u_hat (Sec. 2.4: grad -> i k), of which only the kz
+//   terms take transforms of their own (five transforms for six fields).
 // zfwd (Algorithm 1 step c, second half): transforms W[0..2] (the nonlinear
 //   term after its x and y transforms) along z and keeps only the 2/3-rule
 //   modes, in the state layout, in the free vorticity part of W.
@@ -36,8 +37,87 @@ constexpr int kThreadsInv = 256;
 template <typename T> constexpr int cap_zi() { return sizeof(T) == 4 ? 8192 : 4096; }
 inline size_t ceil_div_sz(size_t a, size_t b) { return (a + b - 1) / b; }
 
+// Stores of k_zinv.  Plain: the transformed column to `out`.
+template <typename T, int V> struct ZStore {
+    cplx<T>* out;
+    size_t plane;
+    bool ok;
+    __device__ __forceinline__ void operator()(int z, const cplx<T>* v) const
+    {
+        if (ok) st_row<T, V>(out + (size_t)z * plane, v);
+    }
+};
+
+// A vorticity component from a transform v and a side row a of an already
+// transformed velocity component: out_c = i (cv v + ca a) per column, and v
+// itself to out_v when that is set.  The side rows were written earlier in
+// the same kernel by this block, so they are read through L2 (ld.cg).
+template <typename T, int V> struct ZCurlStore {
+    cplx<T>* out_v;
+    cplx<T>* out_c;
+    const cplx<T>* side;
+    size_t plane;
+    T cv[V], ca[V];
+    bool ok;
+    __device__ __forceinline__ void aux(int z, cplx<T>* a) const
+    {
+        if (!ok) {
+#pragma unroll
+            for (int c = 0; c < V; ++c) a[c] = mkc<T>(0, 0);
+            return;
+        }
+        const cplx<T>* p = side + (size_t)z * plane;
+        if constexpr (sizeof(T) == 4 && V % 2 == 0) {
+#pragma unroll
+            for (int c = 0; c < V; c += 2) {
+                const float4 q = __ldcg(reinterpret_cast<const float4*>(p + c));
+                a[c] = mkc<T>(q.x, q.y);
+                a[c + 1] = mkc<T>(q.z, q.w);
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < V; ++c) {
+                const double2 q = __ldcg(reinterpret_cast<const double2*>(p + c));
+                a[c] = mkc<T>(T(q.x), T(q.y));
+            }
+        }
+    }
+    __device__ __forceinline__ void put(int z, const cplx<T>* v, const cplx<T>* a) const
+    {
+        if (!ok) return;
+        if (out_v) st_row<T, V>(out_v + (size_t)z * plane, v);
+        cplx<T> r[V];
+#pragma unroll
+        for (int c = 0; c < V; ++c)
+            r[c] = cmuli(mkc<T>(cv[c] * v[c].x + ca[c] * a[c].x, cv[c] * v[c].y + ca[c] * a[c].y));
+        st_row<T, V>(out_c + (size_t)z * plane, r);
+    }
+};
+
+// First-stage loads of kz times the staged tile (in place: the first stage
+// reads and writes the same rows of each butterfly).
+template <typename T, int V> struct ZLoadKz {
+    const cplx<T>* buf;
+    int ld, col, nz, Kz;
+    T kunit;                                   // 2 pi / Lz
+    __device__ __forceinline__ void operator()(int s, cplx<T>* r) const
+    {
+        ld_row<T, V>(buf + s * ld + col, r);
+        const T kz = kunit * T(s <= Kz ? s : s - nz);   // rows of dropped modes are zero
+#pragma unroll
+        for (int c = 0; c < V; ++c) r[c] = cscale(r[c], kz);
+    }
+};
+
+// The z transform is linear and kx, ky are constant along a column, so of
+// omega = i k x u only the kz terms need transforms of their own:
+//   W2 = Fz u_z;  W4 = i (Fz(kz u_x) - kx W2);  W0 = Fz u_x;
+//   W3 = i (ky W2 - Fz(kz u_y));  W1 = Fz u_y, W5 = i (kx W1 - ky W0)
+// five transforms, each velocity component read from DRAM once (its second
+// read follows the first), the side rows read back from L2.  nf = 3: the
+// velocity alone.
 template <typename T>
-__global__ void __launch_bounds__(kThreadsInv)
+__global__ void __launch_bounds__(kThreadsInv, sizeof(T) == 4 ? 3 : 1)
 k_zinv(const cplx<T>* __restrict__ U, cplx<T>* __restrict__ W, Geom g, FftPlan plan,
        const double2* __restrict__ tw, const int* __restrict__ pos, int nf, int lgTX,
        const StepState* __restrict__ st)
@@ -52,6 +132,7 @@ k_zinv(const cplx<T>* __restrict__ U, cplx<T>* __restrict__ W, Geom g, FftPlan p
     const int q0 = blockIdx.x * TX;
     const size_t Ustride = (size_t)g.Mz * Q;           // between components of U
     const size_t Wplane = (size_t)g.ny * g.Mxp;        // between z planes of W
+    const size_t Wfield = (size_t)g.nz * Wplane;       // between fields of W
     load_tables<T>(tws, nullptr, tw, nullptr, g.nz, 0);
     load_inverse_pos(sinv, pos, g.nz);
 
@@ -67,63 +148,60 @@ k_zinv(const cplx<T>* __restrict__ U, cplx<T>* __restrict__ W, Geom g, FftPlan p
     const T kxv[V] = {two_pi * T(x) / T(g.Lx), two_pi * T(x + 1) / T(g.Lx)};
     const T ky = two_pi * T(mode_of(jy, g.Ky)) / T(g.Ly);
     const int nz = g.nz, Kz = g.Kz, Mz = g.Mz;
+    cplx<T>* Wq = W + (qok ? q : 0);
     __syncthreads();
 
-    for (int f = 0; f < nf; ++f) {
-        cplx<T>* out = W + (size_t)f * nz * Wplane + (qok ? q : 0);
-        auto store = [&](int z, const cplx<T>* v) {
-            if (qok) st_row<T, V>(out + (size_t)z * Wplane, v);
-        };
-        if (f < 3) {
-            // U's row padding (x >= Mx) is zero
-            // 16-byte asynchronous copies of VEC adjacent columns
-            constexpr int VEC = 16 / sizeof(cplx<T>);
-            const int lpr = TX / VEC;                  // lanes per row of the tile
-            const int rstep = kThreadsInv / lpr;
-            const int txv = (threadIdx.x % lpr) * VEC;
-            const int qv = q0 + txv;                   // Q is a multiple of VEC
-            for (int s = threadIdx.x / lpr; s < nz; s += rstep) {
-                const int jz = s <= Kz ? s : (s >= nz - Kz ? s - nz + Mz : -1);
-                cplx<T>* dst = buf + (s << lgTX) + txv;
-                if (qv < Q && jz >= 0) {
-                    cp_async_16(dst, U + f * Ustride + (size_t)jz * Q + qv);
-                } else {
+    // component `comp` of the tile into buf: kept modes at their z rows, zeros
+    // elsewhere (U's row padding x >= Mx is zero), by 16-byte asynchronous copies
+    auto stage_in = [&](int comp) {
+        constexpr int VEC = 16 / sizeof(cplx<T>);
+        const int lpr = TX / VEC;                  // lanes per row of the tile
+        const int rstep = kThreadsInv / lpr;
+        const int txv = (threadIdx.x % lpr) * VEC;
+        const int qv = q0 + txv;                   // Q is a multiple of VEC
+        for (int s = threadIdx.x / lpr; s < nz; s += rstep) {
+            const int jz = s <= Kz ? s : (s >= nz - Kz ? s - nz + Mz : -1);
+            cplx<T>* dst = buf + (s << lgTX) + txv;
+            if (qv < Q && jz >= 0) {
+                cp_async_16(dst, U + comp * Ustride + (size_t)jz * Q + qv);
+            } else {
 #pragma unroll
-                    for (int v = 0; v < VEC; ++v) dst[v] = mkc<T>(0, 0);
-                }
+                for (int v = 0; v < VEC; ++v) dst[v] = mkc<T>(0, 0);
             }
-            cp_async_wait_all();
-            __syncthreads();
-            fft_dif_out<T, true, V>(buf, TX, TX, plan, tws, sinv, store);
-        } else {
-            // omega = i (k x u) from two velocity components
-            const int cA = f == 3 ? 2 : f == 4 ? 0 : 1;
-            const int cB = f == 3 ? 1 : f == 4 ? 2 : 0;
-            const cplx<T>* srcA = U + cA * Ustride + (qok ? q : 0);
-            const cplx<T>* srcB = U + cB * Ustride + (qok ? q : 0);
-            // U's row padding (x >= Mx) is zero, so its vorticity is too
-            auto load = [&](int s, cplx<T>* r) {
-                const int jz = s <= Kz ? s : (s >= nz - Kz ? s - nz + Mz : -1);
-                if (!qok || jz < 0) {
-#pragma unroll
-                    for (int c = 0; c < V; ++c) r[c] = mkc<T>(0, 0);
-                    return;
-                }
-                cplx<T> a[V], b[V];
-                ld_row<T, V>(srcA + (size_t)jz * Q, a);
-                ld_row<T, V>(srcB + (size_t)jz * Q, b);
-                const T kz = two_pi * T(mode_of(jz, Kz)) / T(g.Lz);
-#pragma unroll
-                for (int c = 0; c < V; ++c) {
-                    // f=3: ky uz - kz uy; f=4: kz ux - kx uz; f=5: kx uy - ky ux
-                    const T k1 = f == 3 ? ky : f == 4 ? kz : kxv[c];
-                    const T k2 = f == 3 ? kz : f == 4 ? kxv[c] : ky;
-                    r[c] = cmuli(mkc<T>(k1 * a[c].x - k2 * b[c].x, k1 * a[c].y - k2 * b[c].y));
-                }
-            };
-            fft_dif_io<T, true, V>(buf, TX, TX, plan, tws, sinv, load, store);
         }
+        cp_async_wait_all();
         __syncthreads();
+    };
+    auto velocity = [&](int comp) {
+        stage_in(comp);
+        fft_dif_out<T, true, V>(buf, TX, TX, plan, tws, sinv, ZStore<T, V>{Wq + comp * Wfield, Wplane, qok});
+        __syncthreads();
+    };
+    const ZLoadKz<T, V> kz_load{buf, TX, tx, nz, Kz, two_pi / T(g.Lz)};
+
+    if (nf < 6) {
+        for (int f = 0; f < nf; ++f) velocity(f);
+        return;
+    }
+    velocity(2);
+    {   // W4 = i (Fz(kz u_x) - kx W2)
+        stage_in(0);
+        ZCurlStore<T, V> w4{nullptr, Wq + 4 * Wfield, Wq + 2 * Wfield, Wplane, {T(1), T(1)},
+                            {-kxv[0], -kxv[1]}, qok};
+        fft_dif_io<T, true, V, true>(buf, TX, TX, plan, tws, sinv, kz_load, w4);
+        __syncthreads();
+    }
+    velocity(0);
+    {   // W3 = i (ky W2 - Fz(kz u_y))
+        stage_in(1);
+        ZCurlStore<T, V> w3{nullptr, Wq + 3 * Wfield, Wq + 2 * Wfield, Wplane, {T(-1), T(-1)}, {ky, ky}, qok};
+        fft_dif_io<T, true, V, true>(buf, TX, TX, plan, tws, sinv, kz_load, w3);
+        __syncthreads();
+    }
+    {   // W1 = Fz u_y and W5 = i (kx W1 - ky W0)
+        stage_in(1);
+        ZCurlStore<T, V> w5{Wq + 1 * Wfield, Wq + 5 * Wfield, Wq, Wplane, {kxv[0], kxv[1]}, {-ky, -ky}, qok};
+        fft_dif_out<T, true, V, true>(buf, TX, TX, plan, tws, sinv, w5);
     }
 }
 
