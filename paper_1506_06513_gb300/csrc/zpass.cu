@@ -37,6 +37,21 @@ constexpr int kThreadsInv = 256;
 template <typename T> constexpr int cap_zi() { return sizeof(T) == 4 ? 8192 : 4096; }
 inline size_t ceil_div_sz(size_t a, size_t b) { return (a + b - 1) / b; }
 
+// A row store marked streaming (st.global.cs: likely read once, so evicted
+// from L2 first), for outputs the kernel does not read back.
+template <typename T, int V>
+__device__ __forceinline__ void st_row_cs(cplx<T>* p, const cplx<T>* o)
+{
+    if constexpr (V % 2 == 0 && sizeof(T) == 4) {
+#pragma unroll
+        for (int c = 0; c < V; c += 2)
+            __stcs(reinterpret_cast<float4*>(p + c), make_float4(o[c].x, o[c].y, o[c + 1].x, o[c + 1].y));
+    } else {
+#pragma unroll
+        for (int c = 0; c < V; ++c) __stcs(reinterpret_cast<double2*>(p + c), make_double2(o[c].x, o[c].y));
+    }
+}
+
 // Stores of k_zinv.  Plain: the transformed column to `out`.
 template <typename T, int V> struct ZStore {
     cplx<T>* out;
@@ -50,8 +65,9 @@ template <typename T, int V> struct ZStore {
 
 // A vorticity component from a transform v and a side row a of an already
 // transformed velocity component: out_c = i (cv v + ca a) per column, and v
-// itself to out_v when that is set.  The side rows were written earlier in
-// the same kernel by this block, so they are read through L2 (ld.cg).
+// itself to out_v when that is set (both streaming stores: nothing reads
+// them back here).  The side rows were written earlier in the same kernel by
+// this block, so they are read through L2 (ld.cg).
 template <typename T, int V> struct ZCurlStore {
     cplx<T>* out_v;
     cplx<T>* out_c;
@@ -85,12 +101,12 @@ template <typename T, int V> struct ZCurlStore {
     __device__ __forceinline__ void put(int z, const cplx<T>* v, const cplx<T>* a) const
     {
         if (!ok) return;
-        if (out_v) st_row<T, V>(out_v + (size_t)z * plane, v);
+        if (out_v) st_row_cs<T, V>(out_v + (size_t)z * plane, v);
         cplx<T> r[V];
 #pragma unroll
         for (int c = 0; c < V; ++c)
             r[c] = cmuli(mkc<T>(cv[c] * v[c].x + ca[c] * a[c].x, cv[c] * v[c].y + ca[c] * a[c].y));
-        st_row<T, V>(out_c + (size_t)z * plane, r);
+        st_row_cs<T, V>(out_c + (size_t)z * plane, r);
     }
 };
 
