@@ -345,7 +345,7 @@ def run_flusi(args):
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             tr = json.load(f)
         ent = tr.get(f"{dom}@{'x'.join(map(str, cfg['n']))}/fp32")
-        if ent and ent.get("source_hash") == source_hash():
+        if ent and ent.get("source_hash") == source_hash(ent.get("sources")):
             traffic = ent["bytes_per_launch"]
     except (OSError, ValueError):
         pass
@@ -455,11 +455,14 @@ def run_flusi(args):
         dist.destroy_process_group()
 
 
-def source_hash():
+def source_hash(sources=None):
+    """Hash of the CUDA sources a kernel's counters were taken from (all of
+    csrc/ when no list is given): a counter whose sources changed since is
+    not reported."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1506_06513_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
+    for name in sorted(sources or os.listdir(csrc)):
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
