@@ -665,39 +665,55 @@ k_xpass(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict
 }
 
 // ---------------------------------------------------------------------------
-// x pass for nh = nx/2 = R*R (R = 16: nx = 512; R = 8: nx = 128).  Each line
-// (one field of one row) belongs to R consecutive lanes, which hold R values
-// each: the length-nh transforms are two register-resident radix-R passes
-// (DIF stage 0 then stage 1 for the inverse, their transposes in reverse for
-// the forward transform) exchanging through the line's own shared-memory
-// slice, so they need __syncwarp only.  A line's slice stores logical row
-// R q + j at R q + (j ^ q), so both passes are free of bank conflicts without
-// padding (sq_slot).
-// The c2r mirror values X[nh - k] and the r2c mirror values Z[nh - k] are
-// exchanged between lanes j and R - j with warp shuffles; inputs are loaded
-// from global memory straight into registers and outputs are stored from
-// registers.  After the inverse passes logical row R q + d holds the point
-// pair p = q + R d.
+// x pass for nh = nx/2 = S R^2 (S = 1: nx = 512 with R = 16, 128 with R = 8;
+// S = 2: nx = 1024, 256).  Each line (one field of one row) belongs to
+// L = S R consecutive lanes, which hold R values each, lane j the points
+// j + L t.  The inverse transform of length nh is a register-resident
+// radix-R pass over t, the twiddles w_nh^{j k1}, then for S = 1 a radix-R
+// pass over j and for S = 2 a radix-R pass over j' (j = 2 j' + p, lane pair
+// p = 0, 1 for each k1) and a radix-2 step between the pair (lanes k1 and
+// k1 + R) with the twiddles w_2R^{k'}; the forward transform runs the same
+// steps transposed, in reverse.  The passes exchange through the line's own
+// shared-memory slice, so they need __syncwarp only; XOR swizzles keep both
+// sides of each exchange free of bank conflicts without padding.  The c2r
+// mirror values X[nh - k] and the r2c mirror values Z[nh - k] are exchanged
+// between lanes j and L - j with warp shuffles; inputs are loaded from global
+// memory straight into registers and outputs are stored from registers.
+// After the inverse, logical row l R + d of a line holds the point pair
+// (l % R) + R d + R^2 (l / R) (SqMap).
 // ---------------------------------------------------------------------------
-// rows per tile: each group of R lanes inverse-transforms two lines (u and
+// rows per tile: each group of L lanes inverse-transforms two lines (u and
 // omega fields) and forward-transforms one (the three NL fields)
-template <int R> constexpr int sq_rows() { return 384 / (6 * R); }
+template <int L> constexpr int sq_rows() { return 384 / (6 * L); }
 
-template <typename T, int R>
-__device__ __forceinline__ void sq_exchange_pre(cplx<T>* x, int j, int width, const cplx<T>* twx)
+template <int R, int S> struct SqMap {
+    // point pair held by logical row lrow after the inverse, and its inverse map
+    __device__ __forceinline__ static int point(int lrow)
+    {
+        const int l = lrow / R, d = lrow % R;
+        return (l % R) + R * d + R * R * (l / R);
+    }
+    __device__ __forceinline__ static int lrow(int pp)
+    {
+        return (pp % R + R * (pp / (R * R))) * R + (pp / R) % R;
+    }
+};
+
+template <typename T, int R, int L>
+__device__ __forceinline__ void sq_exchange_pre(cplx<T>* x, int j, const cplx<T>* twx)
 {
-    // x[t] holds X[j + R t]; on return x[t] = Z[j + R t] (c2r pre-processing)
+    // x[t] holds X[j + L t]; on return x[t] = Z[j + L t] (c2r pre-processing)
 #pragma unroll
     for (int s = 0; s < R / 2; ++s) {
         cplx<T> a, b;   // partner's X[s] and X[R-1-s]
-        a.x = __shfl_sync(0xffffffffu, x[s].x, (R - j) & (R - 1), width);
-        a.y = __shfl_sync(0xffffffffu, x[s].y, (R - j) & (R - 1), width);
-        b.x = __shfl_sync(0xffffffffu, x[R - 1 - s].x, (R - j) & (R - 1), width);
-        b.y = __shfl_sync(0xffffffffu, x[R - 1 - s].y, (R - j) & (R - 1), width);
+        a.x = __shfl_sync(0xffffffffu, x[s].x, (L - j) & (L - 1), L);
+        a.y = __shfl_sync(0xffffffffu, x[s].y, (L - j) & (L - 1), L);
+        b.x = __shfl_sync(0xffffffffu, x[R - 1 - s].x, (L - j) & (L - 1), L);
+        b.y = __shfl_sync(0xffffffffu, x[R - 1 - s].y, (L - j) & (L - 1), L);
         if (j != 0) {
             // mirror of element t is the partner's element R-1-t
-            const cplx<T> zs = c2r_pre<T>(x[s], b, twx[j + R * s]);
-            const cplx<T> zt = c2r_pre<T>(x[R - 1 - s], a, twx[j + R * (R - 1 - s)]);
+            const cplx<T> zs = c2r_pre<T>(x[s], b, twx[j + L * s]);
+            const cplx<T> zt = c2r_pre<T>(x[R - 1 - s], a, twx[j + L * (R - 1 - s)]);
             x[s] = zs;
             x[R - 1 - s] = zt;
         }
@@ -705,11 +721,11 @@ __device__ __forceinline__ void sq_exchange_pre(cplx<T>* x, int j, int width, co
     if (j == 0) {
         // mirror of element t is own element R - t (element 0 mirrors X[nh] = 0)
         const cplx<T> z0 = c2r_pre<T>(x[0], mkc<T>(0, 0), twx[0]);
-        const cplx<T> zh = c2r_pre<T>(x[R / 2], x[R / 2], twx[R * (R / 2)]);
+        const cplx<T> zh = c2r_pre<T>(x[R / 2], x[R / 2], twx[L * (R / 2)]);
 #pragma unroll
         for (int t = 1; t < R / 2; ++t) {
-            const cplx<T> za = c2r_pre<T>(x[t], x[R - t], twx[R * t]);
-            const cplx<T> zb = c2r_pre<T>(x[R - t], x[t], twx[R * (R - t)]);
+            const cplx<T> za = c2r_pre<T>(x[t], x[R - t], twx[L * t]);
+            const cplx<T> zb = c2r_pre<T>(x[R - t], x[t], twx[L * (R - t)]);
             x[t] = za;
             x[R - t] = zb;
         }
@@ -726,14 +742,16 @@ template <int R> __device__ __forceinline__ int sq_slot(int lrow)
     return (lrow & ~(R - 1)) | ((lrow ^ (lrow / R)) & (R - 1));
 }
 
-template <typename T, int R, bool LAYER, bool SPONGE>
-__global__ void __launch_bounds__(192, sizeof(T) == 4 ? 4 : 1)
+template <typename T, int R, int S, bool LAYER, bool SPONGE>
+__global__ void __launch_bounds__(192, sizeof(T) == 4 ? (S == 1 ? 4 : 3) : 1)
 k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExtra ex,
            const StepState* __restrict__ st)
 {
     if (st && st->status != 0) return;
-    constexpr int RB = sq_rows<R>();
-    constexpr int NH = R * R;
+    constexpr int L = S * R;               // lanes per line
+    constexpr int RB = sq_rows<L>();
+    constexpr int NH = S * R * R;
+    using Map = SqMap<R, S>;
     constexpr int CS = NH;                 // line slice; logical row R q + j at R q + (j ^ q)
     const int nx = g.nx, Mx = g.Mx, Mxp = g.Mxp;
     const int nrows = g.nz * g.ny;
@@ -744,16 +762,16 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
     FrameT<T>* Fs = reinterpret_cast<FrameT<T>*>(wacc + kWarpsX * 36);
     cplx<T>* twx = reinterpret_cast<cplx<T>*>(
         reinterpret_cast<unsigned char*>(Fs) + ((sizeof(FrameT<T>) + 15) / 16) * 16);
-    cplx<T>* tw2 = twx + NH;               // tw2[q R + j] = w_nh^{j q}
+    cplx<T>* tw2 = twx + NH;               // tw2[q L + j] = w_nh^{j q}
     cplx<T>* buf = tw2 + NH;               // C line slices of CS values
     __shared__ int rowmask[RB];
 
     const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
-    const int c = tid / R, j = tid % R;    // this lane's line and index within it
+    const int c = tid / L, j = tid % L;    // this lane's line and index within it
     // w_nx^k for k < nh: the c2r/r2c mirror steps use no higher power
     for (int i = tid; i < NH; i += blockDim.x) twx[i] = mkc<T>(T(tw[i].x), T(tw[i].y));
     for (int i = tid; i < NH; i += blockDim.x) {
-        const int q = i / R, jj = i % R;
+        const int q = i / L, jj = i % L;
         const double2 w = tw[(2 * jj * q) % nx];
         tw2[i] = mkc<T>(T(w.x), T(w.y));
     }
@@ -766,7 +784,7 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
     int bad = 0;
     const T dxT = T(g.dx), dyT = T(g.dy), dzT = T(g.dz);
     const FrameT<T>& F = *Fs;
-    constexpr int NG = 192 / R;            // lane groups; group c owns lines c and c + NG
+    constexpr int NG = 192 / L;            // lane groups; group c owns lines c and c + NG
     constexpr bool has_layer = LAYER;   // a Dirichlet layer is set
     const T uinf[3] = {T(ex.u_inf[0]), T(ex.u_inf[1]), T(ex.u_inf[2])};
 
@@ -805,23 +823,50 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
             const cplx<T>* src = W + ((size_t)fld * nrows + (r < nrows ? r : 0)) * Mxp;
 #pragma unroll
             for (int t = 0; t < R; ++t) {
-                const int k = j + R * t;
+                const int k = j + L * t;
                 v[t] = (r < nrows && k < Mx) ? src[k] : mkc<T>(0, 0);
             }
             if (j == 0) v[0].y = T(0);     // a real line has a real mean
-            // ---- inverse: c2r pre-processing, DIF stage 0 (radix R + twiddles), stage 1
-            sq_exchange_pre<T, R>(v, j, R, twx);
+            // ---- inverse: c2r pre-processing, radix R over t and the twiddles
+            //      w_nh^{j k1}, then the second pass(es)
+            sq_exchange_pre<T, R, L>(v, j, twx);
             Dft<T, R, true>::run(v);
 #pragma unroll
-            for (int q = 1; q < R; ++q) v[q] = cmul(v[q], cconj(tw2[q * R + j]));
+            for (int q = 1; q < R; ++q) v[q] = cmul(v[q], cconj(tw2[q * L + j]));
+            if constexpr (S == 1) {
 #pragma unroll
-            for (int q = 0; q < R; ++q) line[R * q + (j ^ q)] = v[q];
-            __syncwarp();
+                for (int q = 0; q < R; ++q) line[R * q + (j ^ q)] = v[q];
+                __syncwarp();
 #pragma unroll
-            for (int i = 0; i < R; ++i) v[i] = line[R * j + (i ^ j)];
-            Dft<T, R, true>::run(v);
+                for (int i = 0; i < R; ++i) v[i] = line[R * j + (i ^ j)];
+                Dft<T, R, true>::run(v);
 #pragma unroll
-            for (int d = 0; d < R; ++d) line[R * j + (d ^ j)] = v[d];
+                for (int d = 0; d < R; ++d) line[R * j + (d ^ j)] = v[d];
+            } else {
+                // Y[j][k1] at L k1 + (j ^ k1); lane j turns into (k1, p) = (j % R, j / R)
+#pragma unroll
+                for (int q = 0; q < R; ++q) line[L * q + (j ^ q)] = v[q];
+                __syncwarp();
+                const int k1 = j % R, p = j / R;
+#pragma unroll
+                for (int i = 0; i < R; ++i) v[i] = line[L * k1 + ((2 * i + p) ^ k1)];
+                Dft<T, R, true>::run(v);   // over j' -> k'
+                if (p) {
+#pragma unroll
+                    for (int d = 1; d < R; ++d) v[d] = cmul(v[d], cconj(twx[2 * R * d]));   // w_2R^{k'}
+                }
+                // radix 2 between the lane pair: outputs k1 + R k' + R^2 p
+#pragma unroll
+                for (int d = 0; d < R; ++d) {
+                    cplx<T> o;
+                    o.x = __shfl_xor_sync(0xffffffffu, v[d].x, R);
+                    o.y = __shfl_xor_sync(0xffffffffu, v[d].y, R);
+                    v[d] = p ? csub(o, v[d]) : cadd(v[d], o);
+                }
+                __syncwarp();
+#pragma unroll
+                for (int d = 0; d < R; ++d) line[sq_slot<R>(R * j + d)] = v[d];
+            }
         }
         __syncthreads();
 
@@ -843,7 +888,7 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
                     }
                     if (SPONGE) {   // chi_sp omega (Sec. 2.3) into the sponge lines
                         const int r = row0 + rr, z = r / g.ny, y = r - z * g.ny;
-                        const int pp = lrow / R + R * (lrow % R);
+                        const int pp = Map::point(lrow);
                         const bool in_row = y >= ex.sponge0[1] || z >= ex.sponge0[2];
                         const T s0 = (in_row || 2 * pp >= ex.sponge0[0]) ? T(1) : T(0);
                         const T s1 = (in_row || 2 * pp + 1 >= ex.sponge0[0]) ? T(1) : T(0);
@@ -863,7 +908,7 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
                         cross3(u, om, nl[h]);
                         if (has_layer) {   // Dirichlet layer u = u_inf (Sec. 2.3)
                             const int r = row0 + rr, z = r / g.ny, y = r - z * g.ny;
-                            const int pp = lrow / R + R * (lrow % R);
+                            const int pp = Map::point(lrow);
                             if (y >= ex.layer0[1] || z >= ex.layer0[2] || 2 * pp + h >= ex.layer0[0]) {
 #pragma unroll
                                 for (int q = 0; q < 3; ++q) nl[h][q] -= F.inv_eta * (u[q] - uinf[q]);
@@ -907,9 +952,9 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
                     const bool inrow[3] = {(mask & 1) != 0, (mask & 2) != 0, (mask & 4) != 0};
                     solid_at(F, X, inrow, chi, colr, us);
                     if (chi > T(0)) {
-                        // point xi is half h of pair p, held at logical row R (p % R) + p / R
+                        // point xi is half h of pair pp, held at logical row Map::lrow(pp)
                         const int pp = xi >> 1, h = xi & 1;
-                        const int lrow = R * (pp % R) + pp / R;
+                        const int lrow = Map::lrow(pp);
                         const int slot = sq_slot<R>(lrow);
                         const T pen = chi * F.inv_eta;
 #pragma unroll
@@ -964,30 +1009,55 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
         for (int li = 0; li < (SPONGE ? 2 : 1); ++li) {
             cplx<T>* line = buf + (3 * RB + c + li * NG) * CS;
             const int fld = 3 * li + c / RB, lrr = c % RB;
+            if constexpr (S == 1) {
 #pragma unroll
-            for (int i = 0; i < R; ++i) v[i] = line[R * j + (i ^ j)];
-            Dft<T, R, false>::run(v);
+                for (int i = 0; i < R; ++i) v[i] = line[R * j + (i ^ j)];
+                Dft<T, R, false>::run(v);
 #pragma unroll
-            for (int d = 0; d < R; ++d) line[R * j + (d ^ j)] = v[d];
-            __syncwarp();
+                for (int d = 0; d < R; ++d) line[R * j + (d ^ j)] = v[d];
+                __syncwarp();
 #pragma unroll
-            for (int t = 0; t < R; ++t) v[t] = line[R * t + (j ^ t)];
+                for (int t = 0; t < R; ++t) v[t] = line[R * t + (j ^ t)];
 #pragma unroll
-            for (int t = 1; t < R; ++t) v[t] = cmul(v[t], tw2[t * R + j]);
-            Dft<T, R, false>::run(v);      // v[q] = Z[j + R q]
+                for (int t = 1; t < R; ++t) v[t] = cmul(v[t], tw2[t * R + j]);
+            } else {
+                // lane j = (k1, p): radix 2 over the two halves h of its points
+                // k1 + R k' + R^2 h, the twiddles w_2R^{p k'}, radix R over k',
+                // then w_nh^{k1 (2 j' + p)}
+                const int k1 = j % R, p = j / R;
+#pragma unroll
+                for (int d = 0; d < R; ++d) {
+                    const cplx<T> a = line[sq_slot<R>(R * j + d)];
+                    const cplx<T> b = line[sq_slot<R>(R * (j ^ R) + d)];
+                    v[d] = p ? csub(b, a) : cadd(a, b);
+                }
+                if (p) {
+#pragma unroll
+                    for (int d = 1; d < R; ++d) v[d] = cmul(v[d], twx[2 * R * d]);
+                }
+                Dft<T, R, false>::run(v);   // over k' -> j'
+#pragma unroll
+                for (int i = 0; i < R; ++i) v[i] = cmul(v[i], tw2[k1 * L + 2 * i + p]);
+                __syncwarp();
+#pragma unroll
+                for (int i = 0; i < R; ++i) line[L * k1 + ((2 * i + p) ^ k1)] = v[i];
+                __syncwarp();
+#pragma unroll
+                for (int q = 0; q < R; ++q) v[q] = line[L * q + (j ^ q)];
+            }
+            Dft<T, R, false>::run(v);      // v[q] = Z[j + L q]
             const int r = row0 + lrr;
             cplx<T>* out = W + ((size_t)fld * nrows + (r < nrows ? r : 0)) * Mxp;
-            const int width = R;
 #pragma unroll
             for (int s2 = 0; s2 < R / 2; ++s2) {
                 cplx<T> a, b;   // partner's Z[s2] and Z[R-1-s2]
-                a.x = __shfl_sync(0xffffffffu, v[s2].x, (R - j) & (R - 1), width);
-                a.y = __shfl_sync(0xffffffffu, v[s2].y, (R - j) & (R - 1), width);
-                b.x = __shfl_sync(0xffffffffu, v[R - 1 - s2].x, (R - j) & (R - 1), width);
-                b.y = __shfl_sync(0xffffffffu, v[R - 1 - s2].y, (R - j) & (R - 1), width);
+                a.x = __shfl_sync(0xffffffffu, v[s2].x, (L - j) & (L - 1), L);
+                a.y = __shfl_sync(0xffffffffu, v[s2].y, (L - j) & (L - 1), L);
+                b.x = __shfl_sync(0xffffffffu, v[R - 1 - s2].x, (L - j) & (L - 1), L);
+                b.y = __shfl_sync(0xffffffffu, v[R - 1 - s2].y, (L - j) & (L - 1), L);
                 if (r < nrows) {
                     const int q1 = s2, q2 = R - 1 - s2;
-                    const int k1 = j + R * q1, k2 = j + R * q2;
+                    const int k1 = j + L * q1, k2 = j + L * q2;
                     cplx<T> m1, m2;
                     if (j != 0) {
                         m1 = b;    // Z[nh - k1] = partner's Z[R-1-q1]
@@ -1033,35 +1103,40 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
     }
 }
 
-template <typename T, int R> size_t sq_smem(const Geom& g, bool sponge = false)
+template <typename T, int R, int S> size_t sq_smem(const Geom& g, bool sponge = false)
 {
-    const int RB = sq_rows<R>(), NH = R * R;
+    const int RB = sq_rows<S * R>(), NH = S * R * R;
     size_t s = sizeof(double) * kWarpsX * 36 + ((sizeof(FrameT<T>) + 15) / 16) * 16;
     s += sizeof(cplx<T>) * ((size_t)2 * NH + (size_t)(sponge ? 9 : 6) * RB * NH);
     return s;
 }
 
-template <typename T, int R>
+template <typename T, int R, int S>
 void launch_sq(bool layer, bool sponge, cplx<T>* w, const Geom& g, const double2* tw, const XExtra& ex,
                const StepState* st, cudaStream_t s, int grid)
 {
-    const size_t smem = sq_smem<T, R>(g, sponge);
+    const size_t smem = sq_smem<T, R, S>(g, sponge);
     if (layer && sponge)
-        k_xpass_sq<T, R, true, true><<<grid, 192, smem, s>>>(w, g, tw, ex, st);
+        k_xpass_sq<T, R, S, true, true><<<grid, 192, smem, s>>>(w, g, tw, ex, st);
     else if (layer)
-        k_xpass_sq<T, R, true, false><<<grid, 192, smem, s>>>(w, g, tw, ex, st);
+        k_xpass_sq<T, R, S, true, false><<<grid, 192, smem, s>>>(w, g, tw, ex, st);
     else if (sponge)
-        k_xpass_sq<T, R, false, true><<<grid, 192, smem, s>>>(w, g, tw, ex, st);
+        k_xpass_sq<T, R, S, false, true><<<grid, 192, smem, s>>>(w, g, tw, ex, st);
     else
-        k_xpass_sq<T, R, false, false><<<grid, 192, smem, s>>>(w, g, tw, ex, st);
+        k_xpass_sq<T, R, S, false, false><<<grid, 192, smem, s>>>(w, g, tw, ex, st);
 }
 
-// radix of the square half-length kernel for this grid, or 0 for the generic one
-template <typename T> int sq_radix(const Geom& g)
+// the register-resident kernel for this grid: 10 R + S (R = 16 or 8, S = 1
+// or 2), or 0 for the generic one
+template <typename T> int sq_kind(const Geom& g)
 {
-    if (g.nx == 512) return 16;
-    if (g.nx == 128) return 8;
-    return 0;
+    switch (g.nx) {
+    case 512: return 161;
+    case 128: return 81;
+    case 1024: return 162;
+    case 256: return 82;
+    default: return 0;
+    }
 }
 
 template <typename T> int x_lgrb(const Geom& g)
@@ -1092,19 +1167,26 @@ template <typename T> int x_grid(const Geom& g)
         if (g_sm_count <= 0) g_sm_count = 1;
     }
     int per_sm = 0, ntiles = 0;
-    const int R = sq_radix<T>(g);
-    if (R == 16) {
-        ntiles = ceil_div(g.nz * g.ny, sq_rows<16>());
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_xpass_sq<T, 16, false, false>, 192, sq_smem<T, 16>(g));
-    } else if (R == 8) {
-        ntiles = ceil_div(g.nz * g.ny, sq_rows<8>());
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_xpass_sq<T, 8, false, false>, 192, sq_smem<T, 8>(g));
+    const int kind = sq_kind<T>(g);
+#define FLUSI_SQ_OCC(R, S)                                                                          \
+    ntiles = ceil_div(g.nz * g.ny, sq_rows<S * R>());                                               \
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_xpass_sq<T, R, S, false, false>, 192, \
+                                                  sq_smem<T, R, S>(g));
+    if (kind == 161) {
+        FLUSI_SQ_OCC(16, 1)
+    } else if (kind == 81) {
+        FLUSI_SQ_OCC(8, 1)
+    } else if (kind == 162) {
+        FLUSI_SQ_OCC(16, 2)
+    } else if (kind == 82) {
+        FLUSI_SQ_OCC(8, 2)
     } else {
         const int lg = x_lgrb<T>(g);
         ntiles = ceil_div(g.nz * g.ny, 1 << lg);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_xpass<T, XP_PHYS>, kThreadsX,
                                                       x_smem<T>(g, lg, 6));
     }
+#undef FLUSI_SQ_OCC
     if (per_sm <= 0) per_sm = 1;
     int grid = g_sm_count * per_sm;
     return grid < ntiles ? grid : ntiles;
@@ -1126,12 +1208,14 @@ cudaError_t launch_x(int mode, void* W, const Geom& g, const FftPlan& plan, cons
     const bool sponge = ex.sponge_fused != 0;
     switch (mode) {
     case XP_PHYS:
-        if (sq_radix<T>(g) == 16)
-            launch_sq<T, 16>(layer, sponge, w, g, tw, ex, st, s, x_grid<T>(g));
-        else if (sq_radix<T>(g) == 8)
-            launch_sq<T, 8>(layer, sponge, w, g, tw, ex, st, s, x_grid<T>(g));
-        else
+        switch (sq_kind<T>(g)) {
+        case 161: launch_sq<T, 16, 1>(layer, sponge, w, g, tw, ex, st, s, x_grid<T>(g)); break;
+        case 81: launch_sq<T, 8, 1>(layer, sponge, w, g, tw, ex, st, s, x_grid<T>(g)); break;
+        case 162: launch_sq<T, 16, 2>(layer, sponge, w, g, tw, ex, st, s, x_grid<T>(g)); break;
+        case 82: launch_sq<T, 8, 2>(layer, sponge, w, g, tw, ex, st, s, x_grid<T>(g)); break;
+        default:
             k_xpass<T, XP_PHYS><<<x_grid<T>(g), kThreadsX, smem, s>>>(w, g, plan, tw, pos, ex, lg, st);
+        }
         break;
     case XP_R2C:
         k_xpass<T, XP_R2C><<<ntiles, kThreadsX, smem, s>>>(w, g, plan, tw, pos, ex, lg, st);
@@ -1156,7 +1240,7 @@ int xpass_grid(int fp64, const Geom& g) { return fp64 ? x_grid<double>(g) : x_gr
 // 1 when the physical x pass (square kernel) forms and transforms chi_sp omega itself
 int xpass_fuses_sponge(int fp64, const Geom& g)
 {
-    return fp64 ? sq_radix<double>(g) != 0 : sq_radix<float>(g) != 0;
+    return fp64 ? sq_kind<double>(g) != 0 : sq_kind<float>(g) != 0;
 }
 
 cudaError_t launch_xpass(int fp64, int mode, void* W, const Geom& g, const FftPlan& plan,
@@ -1183,15 +1267,19 @@ cudaError_t configure_xpass()
     FLUSI_SMEM((k_xpass<double, XP_R2C>))
     FLUSI_SMEM((k_xpass<double, XP_C2R>))
     FLUSI_SMEM((k_xpass<double, XP_DUMP>))
-#define FLUSI_SMEM_SQ(T, R)                              \
-    FLUSI_SMEM((k_xpass_sq<T, R, false, false>))         \
-    FLUSI_SMEM((k_xpass_sq<T, R, true, false>))          \
-    FLUSI_SMEM((k_xpass_sq<T, R, false, true>))          \
-    FLUSI_SMEM((k_xpass_sq<T, R, true, true>))
-    FLUSI_SMEM_SQ(float, 16)
-    FLUSI_SMEM_SQ(float, 8)
-    FLUSI_SMEM_SQ(double, 16)
-    FLUSI_SMEM_SQ(double, 8)
+#define FLUSI_SMEM_SQ(T, R, S)                              \
+    FLUSI_SMEM((k_xpass_sq<T, R, S, false, false>))         \
+    FLUSI_SMEM((k_xpass_sq<T, R, S, true, false>))          \
+    FLUSI_SMEM((k_xpass_sq<T, R, S, false, true>))          \
+    FLUSI_SMEM((k_xpass_sq<T, R, S, true, true>))
+    FLUSI_SMEM_SQ(float, 16, 1)
+    FLUSI_SMEM_SQ(float, 8, 1)
+    FLUSI_SMEM_SQ(float, 16, 2)
+    FLUSI_SMEM_SQ(float, 8, 2)
+    FLUSI_SMEM_SQ(double, 16, 1)
+    FLUSI_SMEM_SQ(double, 8, 1)
+    FLUSI_SMEM_SQ(double, 16, 2)
+    FLUSI_SMEM_SQ(double, 8, 2)
 #undef FLUSI_SMEM_SQ
 #undef FLUSI_SMEM
     return cudaSuccess;

@@ -333,15 +333,19 @@ def test_bench_configuration_sampled(fl):
     sim.close()
 
 
-WIDE = {"x512": ((512, 16, 12), (8.0, 1.0, 0.75)), "x128": ((128, 24, 16), (4.0, 0.75, 0.5))}
+WIDE = {"x512": ((512, 16, 12), (8.0, 1.0, 0.75)), "x128": ((128, 24, 16), (4.0, 0.75, 0.5)),
+        "x1024": ((1024, 12, 8), (16.0, 1.0, 0.75)), "x256": ((256, 18, 16), (8.0, 0.75, 0.75))}
+# nx of the register-resident x pass (nh = R^2 or 2 R^2 with R = 16 or 8)
+SQUARE_NX = (128, 256, 512, 1024)
 
 
 @pytest.mark.parametrize("name", sorted(WIDE))
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_square_half_length_x_pass(fl, name, prec):
-    """Grids with nx = 512 and nx = 128 take the x pass whose half-length
-    transform is two register-resident radix-16 (radix-8) passes; full steps
-    with a sphere, adaptive dt and a mean flow against the oracle."""
+    """Grids with nx = 512 and 128 take the x pass whose half-length transform
+    is two register-resident radix-16 (radix-8) passes, nx = 1024 and 256 the
+    one with a radix-2 step between lane pairs after them; full steps with a
+    sphere, adaptive dt and a mean flow against the oracle."""
     n, L = WIDE[name]
     cfg = {"n": n, "L": L, "nu": 0.01, "eta": 1e-2, "cfl": 0.1, "mean_mode": "fixed",
            "u_inf": (0.3, 0.0, 0.0)}
@@ -363,7 +367,9 @@ def test_square_half_length_x_pass(fl, name, prec):
 
 WAKE = {"generic_48x36x24": ((48, 36, 24), (4.0, 3.0, 2.0)),
         "square_512x16x12": ((512, 16, 12), (8.0, 1.0, 0.75)),
-        "square_128x24x16": ((128, 24, 16), (4.0, 0.75, 0.5))}
+        "square_128x24x16": ((128, 24, 16), (4.0, 0.75, 0.5)),
+        "square_1024x12x8": ((1024, 12, 8), (16.0, 1.0, 0.75)),
+        "square_256x18x16": ((256, 18, 16), (8.0, 0.75, 0.75))}
 
 
 @pytest.mark.parametrize("name", sorted(WAKE))
@@ -386,7 +392,7 @@ def test_sponge_and_dirichlet_layer(fl, name, prec):
     exp = oracle.Spectral(cfg).physical_fields(ref.uh, 0.0, ins)
     tol_f = 1e-11 if prec == "fp64" else 2e-5
     assert rel_l2(got[11:14], exp[11:14]) <= tol_f
-    assert fl.flusi_kernels_per_step(sim.h) == (8 if n[0] in (128, 512) else 9)
+    assert fl.flusi_kernels_per_step(sim.h) == (8 if n[0] in SQUARE_NX else 9)
     sim.step(5)
     rows, _ = sim.forces()
     u = sim.get_state()[0]
