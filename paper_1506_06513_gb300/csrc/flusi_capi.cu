@@ -26,6 +26,7 @@ struct flusi_s {
     int have_ins = 0;
     Geom g{};
     FftPlan px{}, py{}, pz{};
+    YMaps ymaps{};                 // TMA descriptors of W for the y passes (built at bind)
     // workspace
     char* ws = nullptr;
     size_t ws_bytes = 0;
@@ -230,6 +231,9 @@ bool has_sponge(flusi_t h) { return h->opt.sponge_c > 0; }
 
 bool is_rk4(flusi_t h) { return h->opt.time_scheme == 1; }
 
+// device status word of the handle (where a device-side wait that gives up reports)
+int* status_word(flusi_t h) { return &reinterpret_cast<StepState*>(h->ws + h->ostate)->status; }
+
 // The square x pass forms chi_sp omega itself; other grids take a separate
 // x round trip of the vorticity.
 bool sponge_kernel(flusi_t h) { return has_sponge(h) && !xpass_fuses_sponge(h->prec == FLUSI_FP64, h->g); }
@@ -331,7 +335,7 @@ cudaError_t enqueue_step(flusi_t h, cudaStream_t s, cudaEvent_t* ev, const char*
         mark(nm[1]);
         if ((e = launch_zinv(fp64, ustage, W, g, h->pz, tz, at<int>(h, h->opz), 6, st, s))) return e;
         mark(nm[2]);
-        if ((e = launch_ypass(fp64, true, W, g, h->py, ty, at<int>(h, h->opy), 6, st, s))) return e;
+        if ((e = launch_ypass(fp64, true, W, g, h->py, ty, at<int>(h, h->opy), 6, st, &h->ymaps, &st->status, s))) return e;
         mark(nm[3]);
         if (br && (e = cudaStreamWaitEvent(s, h->ev_kin, 0))) return e;
         XExtra xe{};
@@ -365,7 +369,7 @@ cudaError_t enqueue_step(flusi_t h, cudaStream_t s, cudaEvent_t* ev, const char*
             if ((e = launch_xpass(fp64, XP_SPONGE, W, g, h->px, tx, at<int>(h, h->opx), xs, st, s))) return e;
         }
         mark(nm[5]);
-        if ((e = launch_ypass(fp64, false, W, g, h->py, ty, at<int>(h, h->opy), nfwd, st, s))) return e;
+        if ((e = launch_ypass(fp64, false, W, g, h->py, ty, at<int>(h, h->opy), nfwd, st, &h->ymaps, &st->status, s))) return e;
         mark(nm[6]);
         if ((e = launch_zfwd(fp64, W, nfwd, g, h->pz, tz, at<int>(h, h->opz), st, s))) return e;
         mark(nm[7]);
@@ -529,6 +533,7 @@ int flusi_bind(flusi_t h, void* ws, size_t bytes, void* stream)
     h->ws_bytes = bytes;
     h->stream = static_cast<cudaStream_t>(stream);
     h->xgrid = xpass_grid(h->prec == FLUSI_FP64, h->g);
+    CK(prepare_ymaps(h->prec == FLUSI_FP64, h->ws + h->oW, h->g, &h->ymaps), "y tensor maps");
     if (h->xgrid > h->part_cap) h->xgrid = h->part_cap;
     CK(cudaMemsetAsync(h->ws, 0, h->total, h->stream), "clear workspace");
     auto tx = twiddles(h->nx), ty = twiddles(h->ny), tz = twiddles(h->nz);
@@ -662,7 +667,8 @@ int flusi_set_state(flusi_t h, const void* u, int where)
             CK(launch_xpass(fp64, XP_R2C, W, g, h->px, tx, at<int>(h, h->opx), xe, nullptr, s), "x r2c");
         }
     }
-    CK(launch_ypass(fp64, false, W, g, h->py, at<double2>(h, h->oty), at<int>(h, h->opy), 3, nullptr, s), "y forward");
+    CK(launch_ypass(fp64, false, W, g, h->py, at<double2>(h, h->oty), at<int>(h, h->opy), 3, nullptr,
+                    &h->ymaps, status_word(h), s), "y forward");
     CK(launch_zfwd(fp64, W, 3, g, h->pz, at<double2>(h, h->otz), at<int>(h, h->opz), nullptr, s),
        "z forward");
     ZfwdExtra ze = zextra(h);
@@ -759,7 +765,8 @@ int flusi_get_state(flusi_t h, void* u_out, int where, double* t, long long* ste
     void* W = h->ws + h->oW;
     cudaStream_t s = h->stream;
     CK(launch_zinv(fp64, h->ws + h->oU, W, g, h->pz, at<double2>(h, h->otz), at<int>(h, h->opz), 3, nullptr, s), "z inverse");
-    CK(launch_ypass(fp64, true, W, g, h->py, at<double2>(h, h->oty), at<int>(h, h->opy), 3, nullptr, s), "y inverse");
+    CK(launch_ypass(fp64, true, W, g, h->py, at<double2>(h, h->oty), at<int>(h, h->opy), 3, nullptr,
+                    &h->ymaps, status_word(h), s), "y inverse");
     XExtra xe{};
     xe.cstride = (long long)N;
     if (where == FLUSI_DEVICE) {
@@ -836,7 +843,8 @@ int flusi_debug_fields(flusi_t h, void* out_dev)
                                   at<Frame>(h, h->oframe), box_margin(h), 0.0);
     CK(cudaGetLastError(), "kinematics");
     CK(launch_zinv(fp64, h->ws + h->oU, W, g, h->pz, at<double2>(h, h->otz), at<int>(h, h->opz), 6, nullptr, s), "z inverse");
-    CK(launch_ypass(fp64, true, W, g, h->py, at<double2>(h, h->oty), at<int>(h, h->opy), 6, nullptr, s), "y inverse");
+    CK(launch_ypass(fp64, true, W, g, h->py, at<double2>(h, h->oty), at<int>(h, h->opy), 6, nullptr,
+                    &h->ymaps, status_word(h), s), "y inverse");
     XExtra xe{};
     xe.frame = at<Frame>(h, h->oframe);
     xe.shape = make_shape(h);

@@ -11,6 +11,8 @@
 //           -> scalars -> yfwd -> zfwd (projection, IF-AB2).
 #pragma once
 
+#include <cuda.h>   // CUtensorMap (descriptor type only; the encoder is fetched at run time)
+
 #include "../../include/flusi.h"
 #include "common.cuh"
 
@@ -26,9 +28,17 @@ __global__ void k_scalars(Geom g, const double* part, int nparts, StepState* st,
 
 // y transform (ypass.cu): W[c] for c < ncomp, between A and B form.
 // tw: twiddle table of the axis; pos: digit-reversal table of its plan.
+// With maps (tensor descriptors of W built by prepare_ymaps for this handle's
+// W) a tile arrives by TMA boxes, else by 16-byte asynchronous copies; a TMA
+// wait that gives up sets *err = FLUSI_ETIMEOUT.
+struct YMaps {
+    CUtensorMap inv, fwd;
+    int inv_bh = 0, fwd_bh = 0;   // box heights (rows); 0: that direction copies by 16 bytes
+};
+cudaError_t prepare_ymaps(int fp64, void* W, const Geom& g, YMaps* maps);
 cudaError_t launch_ypass(int fp64, bool inverse, void* W, const Geom& g, const FftPlan& plan,
                          const double2* tw, const int* pos, int ncomp, const StepState* st,
-                         cudaStream_t s);
+                         const YMaps* maps, int* err, cudaStream_t s);
 
 // z transforms (zpass.cu)
 //   zinv: U -> W[0..nf) in A form; nf = 3 (u) or 6 (u and omega = i k x u).

@@ -2,10 +2,14 @@
 //
 // A tile is TX consecutive x-mode columns of NP consecutive z planes of one
 // component: every global access is a run of TX complex values (128 bytes).
-// Rows arrive by 16-byte asynchronous copies, all FFT stages but the last run
-// in shared memory and the last one stores its results to global memory from
-// registers; the pass works in place (a tile reads all of its rows before its
-// first barrier and writes after its last).
+// Rows arrive by TMA: one thread issues the tile's boxes of a 3-D tensor map
+// of W (dims: x reals, planes of all components, y rows, so a box lands in
+// shared memory row-major as the transform wants it) against an mbarrier;
+// where no map fits (box heights over 256 rows) by 16-byte asynchronous
+// copies.  All FFT stages but the last run in shared memory and the last one
+// stores its results to global memory from registers; the pass works in place
+// (a tile reads all of its rows before its first barrier and writes after its
+// last).
 //   inverse: rows j < My hold the kept y-modes 0..Ky, -Ky..-1 -> ny grid rows
 //   forward: ny grid rows -> the My kept y-modes (2/3 rule, pruned output)
 #include "fft.cuh"
@@ -19,15 +23,19 @@ constexpr int kThreads = 256;
 // complex elements per tile (64 KiB of shared memory)
 template <typename T> constexpr int tile_elems() { return sizeof(T) == 4 ? 8192 : 4096; }
 
-template <typename T, bool INV>
+template <typename T, bool INV, bool TMA>
 __global__ void __launch_bounds__(kThreads)
 k_ypass(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict__ tw,
-        const int* __restrict__ pos, int ncomp, int lgTX, int lgNP, const StepState* __restrict__ st)
+        const int* __restrict__ pos, int ncomp, int lgTX, int lgNP, const StepState* __restrict__ st,
+        const __grid_constant__ CUtensorMap tmap, int bh, int* err)
 {
     if (st && st->status != 0) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    // after a TMA wait gave up, the remaining blocks leave at once
+    if (TMA && *(volatile int*)err != 0) return;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     const int TX = 1 << lgTX, lgC = lgTX + lgNP, C = 1 << lgC;
-    cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
+    // the tile at a 128-byte boundary of shared memory (TMA destinations)
+    cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127));
     cplx<T>* tws = buf + (g.ny << lgC);
     int* sinv = reinterpret_cast<int*>(tws + g.ny);
     const int nxb = ceil_div(g.Mxp, TX), nzb = ceil_div(g.nz, 1 << lgNP);
@@ -52,7 +60,40 @@ k_ypass(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict
     const int z = z0 + (col >> lgTX), x = x0 + (col & (TX - 1));
     const bool colok = z < g.nz && x < g.Mxp;   // Mxp is a multiple of 4
     cplx<T>* gcol = base + (size_t)(colok ? z : 0) * plane + (colok ? x : 0);
-    {
+    if constexpr (TMA) {
+        __shared__ unsigned long long bar;
+        if (threadIdx.x == 0) mbar_init(&bar, 1);
+        __syncthreads();
+        // coordinates: x in reals (2 x0 sizeof(T) is a multiple of 128 bytes),
+        // plane c nz + z0, row; a box is bh rows of NP planes of TX columns
+        const int xr = 2 * x0, pl = c * g.nz + z0;
+        const unsigned box = (unsigned)(((size_t)bh << lgC) * sizeof(cplx<T>));
+        if (threadIdx.x == 0) {
+            if (INV) {
+                // modes 0..Ky to rows 0..Ky; modes Ky..2Ky to rows ny-Ky-1..ny-1
+                // (bh = Ky + 1; row ny-Ky-1 is cleared below)
+                mbar_expect_tx(&bar, 2 * box);
+                tma_load_3d(buf, &tmap, xr, pl, 0, &bar);
+                tma_load_3d(buf + ((size_t)(ny - Ky - 1) << lgC), &tmap, xr, pl, Ky, &bar);
+            } else {
+                const int nb = ny / bh;
+                mbar_expect_tx(&bar, nb * box);
+                for (int q = 0; q < nb; ++q) tma_load_3d(buf + ((size_t)(q * bh) << lgC), &tmap, xr, pl, q * bh, &bar);
+            }
+        }
+        const bool ok = mbar_wait(&bar, 0);
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) atomicCAS(err, 0, (int)FLUSI_ETIMEOUT);
+            mbar_wait(&bar, 0);   // let the copies in flight land before the block leaves
+            return;
+        }
+        if (INV) {
+            // grid slots of the dropped modes are zero
+            const int nzero = (ny - My) << lgC;
+            cplx<T>* gap = buf + ((size_t)(Ky + 1) << lgC);
+            for (int i = threadIdx.x; i < nzero; i += kThreads) gap[i] = mkc<T>(0, 0);
+        }
+    } else {
         // 16-byte asynchronous copies: each lane moves VEC adjacent columns
         constexpr int VEC = 16 / sizeof(cplx<T>);
         const int lanes_per_row = C / VEC;
@@ -105,43 +146,117 @@ template <typename T> YTile y_tile(const Geom& g, int ncomp)
     t.lgTX = __builtin_ctz(TX);
     t.lgNP = __builtin_ctz(NP);
     t.blocks = ceil_div(g.Mxp, TX) * ceil_div(g.nz, NP) * ncomp;
-    t.smem = sizeof(cplx<T>) * ((size_t)g.ny + (size_t)g.ny * TX * NP) + sizeof(int) * g.ny;
+    t.smem = sizeof(cplx<T>) * ((size_t)g.ny + (size_t)g.ny * TX * NP) + sizeof(int) * g.ny + 128;
     return t;
 }
 
 template <typename T>
 cudaError_t launch_y(bool inverse, void* W, const Geom& g, const FftPlan& plan, const double2* tw,
-                     const int* pos, int ncomp, const StepState* st, cudaStream_t s)
+                     const int* pos, int ncomp, const StepState* st, const YMaps* maps, int* err,
+                     cudaStream_t s)
 {
     YTile t = y_tile<T>(g, ncomp);
     if ((size_t)g.ny << (t.lgTX + t.lgNP) > (size_t)tile_elems<T>()) return cudaErrorInvalidValue;
-    if (inverse)
-        k_ypass<T, true><<<t.blocks, kThreads, t.smem, s>>>((cplx<T>*)W, g, plan, tw, pos, ncomp,
-                                                              t.lgTX, t.lgNP, st);
-    else
-        k_ypass<T, false><<<t.blocks, kThreads, t.smem, s>>>((cplx<T>*)W, g, plan, tw, pos, ncomp,
-                                                               t.lgTX, t.lgNP, st);
+    const int bh = maps ? (inverse ? maps->inv_bh : maps->fwd_bh) : 0;
+    cplx<T>* w = (cplx<T>*)W;
+    if (bh > 0 && err) {
+        const CUtensorMap& m = inverse ? maps->inv : maps->fwd;
+        if (inverse)
+            k_ypass<T, true, true><<<t.blocks, kThreads, t.smem, s>>>(w, g, plan, tw, pos, ncomp, t.lgTX, t.lgNP,
+                                                                       st, m, bh, err);
+        else
+            k_ypass<T, false, true><<<t.blocks, kThreads, t.smem, s>>>(w, g, plan, tw, pos, ncomp, t.lgTX, t.lgNP,
+                                                                        st, m, bh, err);
+    } else {
+        CUtensorMap none{};
+        if (inverse)
+            k_ypass<T, true, false><<<t.blocks, kThreads, t.smem, s>>>(w, g, plan, tw, pos, ncomp, t.lgTX,
+                                                                        t.lgNP, st, none, 0, err);
+        else
+            k_ypass<T, false, false><<<t.blocks, kThreads, t.smem, s>>>(w, g, plan, tw, pos, ncomp, t.lgTX,
+                                                                         t.lgNP, st, none, 0, err);
+    }
     return cudaGetLastError();
+}
+
+typedef CUresult (*EncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// Tensor maps of W for the y tiles: dims (2 Mxp reals, 6 nz planes, ny rows)
+// with strides (plane ny Mxp, row Mxp complex); boxes (2 TX, NP, bh).  A box
+// height over 256 (the hardware's limit) leaves that direction to 16-byte
+// copies, as does a failed encoding.
+template <typename T> cudaError_t prepare_y(void* W, const Geom& g, YMaps* m)
+{
+    m->inv_bh = m->fwd_bh = 0;
+    static EncodeTiled encode = nullptr;
+    if (!encode) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn) {
+            cudaGetLastError();
+            return cudaSuccess;   // no encoder: 16-byte copies
+        }
+        encode = reinterpret_cast<EncodeTiled>(fn);
+    }
+    if (reinterpret_cast<uintptr_t>(W) % 16 != 0) return cudaSuccess;
+    const YTile t = y_tile<T>(g, 1);
+    const cuuint64_t dims[3] = {(cuuint64_t)2 * g.Mxp, (cuuint64_t)6 * g.nz, (cuuint64_t)g.ny};
+    const cuuint64_t strides[2] = {(cuuint64_t)g.ny * g.Mxp * sizeof(cplx<T>), (cuuint64_t)g.Mxp * sizeof(cplx<T>)};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUtensorMapDataType dt = sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    auto make = [&](CUtensorMap* map, int bh) {
+        if (bh <= 0 || bh > 256) return 0;
+        const cuuint32_t box[3] = {(cuuint32_t)(2 << t.lgTX), (cuuint32_t)(1 << t.lgNP), (cuuint32_t)bh};
+        const CUresult r = encode(map, dt, 3, W, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        return r == CUDA_SUCCESS ? bh : 0;
+    };
+    // every box destination (row offsets of the tile) on a 128-byte boundary
+    const size_t row_bytes = sizeof(cplx<T>) << (t.lgTX + t.lgNP);
+    const int ibh = ((size_t)(g.ny - g.Ky - 1) * row_bytes) % 128 == 0 ? g.Ky + 1 : 0;
+    m->inv_bh = make(&m->inv, ibh);
+    int fbh = g.ny <= 256 ? g.ny : (g.ny % 256 == 0 ? 256 : 0);
+    if (((size_t)fbh * row_bytes) % 128 != 0) fbh = 0;
+    m->fwd_bh = make(&m->fwd, fbh);
+    return cudaSuccess;
 }
 
 }  // namespace
 
+cudaError_t prepare_ymaps(int fp64, void* W, const Geom& g, YMaps* maps)
+{
+    return fp64 ? prepare_y<double>(W, g, maps) : prepare_y<float>(W, g, maps);
+}
+
 cudaError_t launch_ypass(int fp64, bool inverse, void* W, const Geom& g, const FftPlan& plan,
                          const double2* tw, const int* pos, int ncomp, const StepState* st,
-                         cudaStream_t s)
+                         const YMaps* maps, int* err, cudaStream_t s)
 {
-    return fp64 ? launch_y<double>(inverse, W, g, plan, tw, pos, ncomp, st, s)
-                : launch_y<float>(inverse, W, g, plan, tw, pos, ncomp, st, s);
+    return fp64 ? launch_y<double>(inverse, W, g, plan, tw, pos, ncomp, st, maps, err, s)
+                : launch_y<float>(inverse, W, g, plan, tw, pos, ncomp, st, maps, err, s);
 }
 
 cudaError_t configure_ypass()
 {
     const int big = 100 * 1024;
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_ypass<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
-    if ((e = cudaFuncSetAttribute(k_ypass<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
-    if ((e = cudaFuncSetAttribute(k_ypass<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
-    return cudaFuncSetAttribute(k_ypass<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+#define FLUSI_SMEM(fn) \
+    if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    FLUSI_SMEM((k_ypass<float, true, false>))
+    FLUSI_SMEM((k_ypass<float, false, false>))
+    FLUSI_SMEM((k_ypass<double, true, false>))
+    FLUSI_SMEM((k_ypass<double, false, false>))
+    FLUSI_SMEM((k_ypass<float, true, true>))
+    FLUSI_SMEM((k_ypass<float, false, true>))
+    FLUSI_SMEM((k_ypass<double, true, true>))
+    FLUSI_SMEM((k_ypass<double, false, true>))
+#undef FLUSI_SMEM
+    return cudaSuccess;
 }
 
 }  // namespace flusi

@@ -331,6 +331,41 @@ def test_bench_configuration_sampled(fl):
     assert abs(rows[0, 20] - ek) <= 1e-5 * ek
     assert rows[0, 1] == pytest.approx(min(0.1 * dx / rows[0, 21], cfg["eta"]), rel=1e-12)
     sim.close()
+    _check_first_force_row(cfg, ins, rows[0])
+
+
+def _check_first_force_row(cfg, ins, row):
+    """Force and moment of every part in the first row of the 512^3 step (the
+    square x pass the benchmark times), against the oracle's mask over a
+    sub-box that holds the whole insect and the closed-form initial field:
+    F = sum chi (u - u_s) dV / C_eta, M = sum r x chi (u - u_s) dV / C_eta
+    (no unsteady correction on the first step)."""
+    n, L = cfg["n"], cfg["L"]
+    dx = L[0] / n[0]
+    lo, hi = (176, 92, 220), (336, 420, 292)        # grid indices, x y z
+    nsub = tuple(h - l for l, h in zip(lo, hi))
+    off = np.array(lo) * dx
+    sub = {"n": nsub, "L": tuple(m * dx for m in nsub), "nu": cfg["nu"], "eta": cfg["eta"]}
+    shifted = dict(ins, x_cntr=tuple(np.asarray(ins["x_cntr"]) - off))
+    chi, col, us = oracle.mask_grid(sub, shifted, 0.0)
+    # the sub-box holds the whole insect: nothing on its faces
+    for face in (chi[0], chi[-1], chi[:, 0], chi[:, -1], chi[:, :, 0], chi[:, :, -1]):
+        assert face.max() == 0.0
+    z, y, x = np.meshgrid(*(np.arange(lo[a], hi[a]) for a in (2, 1, 0)), indexing="ij")
+    pts = np.column_stack([x.ravel(), y.ravel(), z.ravel()])
+    u = workloads.shear_waves(n, L, mean=cfg["u_inf"], points=pts)
+    X = pts.T * dx
+    pen = chi.ravel() * (u - us.reshape(3, -1)) * dx ** 3 / cfg["eta"]
+    fr = oracle.frames(ins, 0.0)
+    refs = [np.asarray(ins["x_cntr"]), fr["pivot_g"][0], fr["pivot_g"][1]]
+    for c in range(3):
+        sel = col.ravel() == c + 1
+        F = pen[:, sel].sum(axis=1)
+        M = np.cross((X[:, sel] - refs[c][:, None]).T, pen[:, sel].T).sum(axis=0)
+        got_F, got_M = row[2 + 6 * c: 5 + 6 * c], row[5 + 6 * c: 8 + 6 * c]
+        assert np.abs(got_F - F).max() <= 2e-4 * np.abs(F).max(), c
+        assert np.abs(got_M - M).max() <= 2e-4 * np.abs(M).max(), c
+        assert np.abs(F).max() > 1.0
 
 
 WIDE = {"x512": ((512, 16, 12), (8.0, 1.0, 0.75)), "x128": ((128, 24, 16), (4.0, 0.75, 0.5)),
