@@ -250,6 +250,13 @@ __device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned coun
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
 }
 
+// order this thread's earlier generic-proxy shared-memory accesses before the
+// asynchronous proxy's (a TMA write into a buffer the block used before)
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+
 __device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes)
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)

@@ -27,6 +27,7 @@ struct flusi_s {
     Geom g{};
     FftPlan px{}, py{}, pz{};
     YMaps ymaps{};                 // TMA descriptors of W for the y passes (built at bind)
+    ZMaps zmaps{};                 // TMA descriptors of U, the RK4 stage state and W for the z passes
     // workspace
     char* ws = nullptr;
     size_t ws_bytes = 0;
@@ -333,7 +334,10 @@ cudaError_t enqueue_step(flusi_t h, cudaStream_t s, cudaEvent_t* ev, const char*
         if ((e = cudaGetLastError())) return e;
         if (br && (e = cudaEventRecord(h->ev_kin, sk))) return e;
         mark(nm[1]);
-        if ((e = launch_zinv(fp64, ustage, W, g, h->pz, tz, at<int>(h, h->opz), 6, st, s))) return e;
+        const CUtensorMap* umap = q == 0 ? &h->zmaps.u : &h->zmaps.ut;
+        const int ubh = q == 0 ? h->zmaps.u_bh : h->zmaps.ut_bh;
+        if ((e = launch_zinv(fp64, ustage, W, g, h->pz, tz, at<int>(h, h->opz), 6, st, umap, ubh, &st->status, s)))
+            return e;
         mark(nm[2]);
         if ((e = launch_ypass(fp64, true, W, g, h->py, ty, at<int>(h, h->opy), 6, st, &h->ymaps, &st->status, s))) return e;
         mark(nm[3]);
@@ -371,7 +375,9 @@ cudaError_t enqueue_step(flusi_t h, cudaStream_t s, cudaEvent_t* ev, const char*
         mark(nm[5]);
         if ((e = launch_ypass(fp64, false, W, g, h->py, ty, at<int>(h, h->opy), nfwd, st, &h->ymaps, &st->status, s))) return e;
         mark(nm[6]);
-        if ((e = launch_zfwd(fp64, W, nfwd, g, h->pz, tz, at<int>(h, h->opz), st, s))) return e;
+        if ((e = launch_zfwd(fp64, W, nfwd, g, h->pz, tz, at<int>(h, h->opz), st, &h->zmaps.w, h->zmaps.w_bh,
+                             &st->status, s)))
+            return e;
         mark(nm[7]);
         if (q == 0 && branch && (e = cudaStreamWaitEvent(s, h->ev_sc, 0))) return e;
         ZfwdExtra ze = zextra(h);
@@ -534,6 +540,9 @@ int flusi_bind(flusi_t h, void* ws, size_t bytes, void* stream)
     h->stream = static_cast<cudaStream_t>(stream);
     h->xgrid = xpass_grid(h->prec == FLUSI_FP64, h->g);
     CK(prepare_ymaps(h->prec == FLUSI_FP64, h->ws + h->oW, h->g, &h->ymaps), "y tensor maps");
+    CK(prepare_zmaps(h->prec == FLUSI_FP64, h->ws + h->oU, is_rk4(h) ? h->ws + h->oUt : nullptr, h->ws + h->oW,
+                     h->g, &h->zmaps),
+       "z tensor maps");
     if (h->xgrid > h->part_cap) h->xgrid = h->part_cap;
     CK(cudaMemsetAsync(h->ws, 0, h->total, h->stream), "clear workspace");
     auto tx = twiddles(h->nx), ty = twiddles(h->ny), tz = twiddles(h->nz);
@@ -669,7 +678,8 @@ int flusi_set_state(flusi_t h, const void* u, int where)
     }
     CK(launch_ypass(fp64, false, W, g, h->py, at<double2>(h, h->oty), at<int>(h, h->opy), 3, nullptr,
                     &h->ymaps, status_word(h), s), "y forward");
-    CK(launch_zfwd(fp64, W, 3, g, h->pz, at<double2>(h, h->otz), at<int>(h, h->opz), nullptr, s),
+    CK(launch_zfwd(fp64, W, 3, g, h->pz, at<double2>(h, h->otz), at<int>(h, h->opz), nullptr, &h->zmaps.w,
+                   h->zmaps.w_bh, status_word(h), s),
        "z forward");
     ZfwdExtra ze = zextra(h);
     ze.coef = nullptr;
@@ -764,7 +774,9 @@ int flusi_get_state(flusi_t h, void* u_out, int where, double* t, long long* ste
     const size_t N = (size_t)g.nx * g.ny * g.nz;
     void* W = h->ws + h->oW;
     cudaStream_t s = h->stream;
-    CK(launch_zinv(fp64, h->ws + h->oU, W, g, h->pz, at<double2>(h, h->otz), at<int>(h, h->opz), 3, nullptr, s), "z inverse");
+    CK(launch_zinv(fp64, h->ws + h->oU, W, g, h->pz, at<double2>(h, h->otz), at<int>(h, h->opz), 3, nullptr,
+                   &h->zmaps.u, h->zmaps.u_bh, status_word(h), s),
+       "z inverse");
     CK(launch_ypass(fp64, true, W, g, h->py, at<double2>(h, h->oty), at<int>(h, h->opy), 3, nullptr,
                     &h->ymaps, status_word(h), s), "y inverse");
     XExtra xe{};
@@ -842,7 +854,9 @@ int flusi_debug_fields(flusi_t h, void* out_dev)
     k_kinematics<<<1, 32, 0, s>>>(at<flusi_insect>(h, h->oins), st, at<StepCoef>(h, h->ocoef),
                                   at<Frame>(h, h->oframe), box_margin(h), 0.0);
     CK(cudaGetLastError(), "kinematics");
-    CK(launch_zinv(fp64, h->ws + h->oU, W, g, h->pz, at<double2>(h, h->otz), at<int>(h, h->opz), 6, nullptr, s), "z inverse");
+    CK(launch_zinv(fp64, h->ws + h->oU, W, g, h->pz, at<double2>(h, h->otz), at<int>(h, h->opz), 6, nullptr,
+                   &h->zmaps.u, h->zmaps.u_bh, status_word(h), s),
+       "z inverse");
     CK(launch_ypass(fp64, true, W, g, h->py, at<double2>(h, h->oty), at<int>(h, h->opy), 6, nullptr,
                     &h->ymaps, status_word(h), s), "y inverse");
     XExtra xe{};

@@ -42,9 +42,17 @@ cudaError_t launch_ypass(int fp64, bool inverse, void* W, const Geom& g, const F
 
 // z transforms (zpass.cu)
 //   zinv: U -> W[0..nf) in A form; nf = 3 (u) or 6 (u and omega = i k x u).
+// TMA descriptors of the z passes' sources: the state U, the RK4 stage state
+// and W, each as (2 Q reals, rows, components) with Q = My Mxp columns; box
+// height 0: that source copies by 16 bytes.
+struct ZMaps {
+    CUtensorMap u, ut, w;
+    int u_bh = 0, ut_bh = 0, w_bh = 0;
+};
+cudaError_t prepare_zmaps(int fp64, void* U, void* Ut, void* W, const Geom& g, ZMaps* maps);
 cudaError_t launch_zinv(int fp64, const void* U, void* W, const Geom& g, const FftPlan& plan,
                         const double2* tw, const int* pos, int nf, const StepState* st,
-                        cudaStream_t s);
+                        const CUtensorMap* map, int bh, int* err, cudaStream_t s);
 //   zfwd: W[0..3) in A form -> FFT -> projection ->
 //   mode 0: IF-AB2 update of U with history H;  mode 1: U = result, H = 0.
 struct ZfwdExtra {
@@ -58,7 +66,8 @@ struct ZfwdExtra {
 // forward z transform of W[0..nf-1] (A form), in place: the kept modes jz < Mz
 // end in rows jz of each field's A-form layout
 cudaError_t launch_zfwd(int fp64, void* W, int nf, const Geom& g, const FftPlan& plan,
-                        const double2* tw, const int* pos, const StepState* st, cudaStream_t s);
+                        const double2* tw, const int* pos, const StepState* st,
+                        const CUtensorMap* map, int bh, int* err, cudaStream_t s);
 // 1/N, sponge, projection and (mode 0) IF-AB2 update of U, H, (mode 1) U = N,
 // H = 0, or (modes 2..5) RK4 stage 1..4, reading the kept modes that
 // launch_zfwd left in W

@@ -132,16 +132,18 @@ template <typename T, int V> struct ZLoadKz {
 // five transforms, each velocity component read from DRAM once (its second
 // read follows the first), the side rows read back from L2.  nf = 3: the
 // velocity alone.
-template <typename T>
+template <typename T, bool TMA>
 __global__ void __launch_bounds__(kThreadsInv, sizeof(T) == 4 ? 3 : 1)
 k_zinv(const cplx<T>* __restrict__ U, cplx<T>* __restrict__ W, Geom g, FftPlan plan,
        const double2* __restrict__ tw, const int* __restrict__ pos, int nf, int lgTX,
-       const StepState* __restrict__ st)
+       const StepState* __restrict__ st, const __grid_constant__ CUtensorMap umap, int bh, int* err)
 {
     if (st && st->status != 0) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (TMA && *(volatile int*)err != 0) return;   // a TMA wait gave up earlier
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     const int TX = 1 << lgTX;
-    cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
+    // the tile at a 128-byte boundary of shared memory (TMA destinations)
+    cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127));
     cplx<T>* tws = buf + (g.nz << lgTX);
     int* sinv = reinterpret_cast<int*>(tws + g.nz);
     const int Q = g.My * g.Mxp;
@@ -167,9 +169,40 @@ k_zinv(const cplx<T>* __restrict__ U, cplx<T>* __restrict__ W, Geom g, FftPlan p
     cplx<T>* Wq = W + (qok ? q : 0);
     __syncthreads();
 
+    __shared__ unsigned long long bar;
+    unsigned phase = 0;
+    if (TMA) {
+        if (threadIdx.x == 0) mbar_init(&bar, 1);
+        __syncthreads();
+    }
     // component `comp` of the tile into buf: kept modes at their z rows, zeros
-    // elsewhere (U's row padding x >= Mx is zero), by 16-byte asynchronous copies
-    auto stage_in = [&](int comp) {
+    // elsewhere (U's row padding x >= Mx is zero); by two TMA boxes (modes
+    // 0..Kz to rows 0..Kz, Kz..2Kz to rows nz-Kz-1..nz-1, the duplicate row
+    // cleared with the dropped modes) or by 16-byte asynchronous copies.
+    // false: a TMA wait gave up (status set; the block must leave).
+    auto stage_in = [&](int comp) -> bool {
+        if constexpr (TMA) {
+            if (threadIdx.x == 0) {
+                // earlier generic writes to buf before the asynchronous proxy's
+                fence_proxy_async();
+                const unsigned box = (unsigned)(((size_t)bh << lgTX) * sizeof(cplx<T>));
+                mbar_expect_tx(&bar, 2 * box);
+                tma_load_3d(buf, &umap, 2 * q0, 0, comp, &bar);
+                tma_load_3d(buf + ((size_t)(nz - Kz - 1) << lgTX), &umap, 2 * q0, Kz, comp, &bar);
+            }
+            const bool ok = mbar_wait(&bar, phase);
+            if (__syncthreads_or(!ok)) {
+                if (threadIdx.x == 0) atomicCAS(err, 0, (int)FLUSI_ETIMEOUT);
+                mbar_wait(&bar, phase);   // let the copies in flight land
+                return false;
+            }
+            phase ^= 1;
+            const int nzero = (nz - Mz) << lgTX;
+            cplx<T>* gap = buf + ((size_t)(Kz + 1) << lgTX);
+            for (int i = threadIdx.x; i < nzero; i += kThreadsInv) gap[i] = mkc<T>(0, 0);
+            __syncthreads();
+            return true;
+        }
         constexpr int VEC = 16 / sizeof(cplx<T>);
         const int lpr = TX / VEC;                  // lanes per row of the tile
         const int rstep = kThreadsInv / lpr;
@@ -187,35 +220,38 @@ k_zinv(const cplx<T>* __restrict__ U, cplx<T>* __restrict__ W, Geom g, FftPlan p
         }
         cp_async_wait_all();
         __syncthreads();
+        return true;
     };
-    auto velocity = [&](int comp) {
-        stage_in(comp);
+    auto velocity = [&](int comp) -> bool {
+        if (!stage_in(comp)) return false;
         fft_dif_out<T, true, V>(buf, TX, TX, plan, tws, sinv, ZStore<T, V>{Wq + comp * Wfield, Wplane, qok});
         __syncthreads();
+        return true;
     };
     const ZLoadKz<T, V> kz_load{buf, TX, tx, nz, Kz, two_pi / T(g.Lz)};
 
     if (nf < 6) {
-        for (int f = 0; f < nf; ++f) velocity(f);
+        for (int f = 0; f < nf; ++f)
+            if (!velocity(f)) return;
         return;
     }
-    velocity(2);
+    if (!velocity(2)) return;
     {   // W4 = i (Fz(kz u_x) - kx W2)
-        stage_in(0);
+        if (!stage_in(0)) return;
         ZCurlStore<T, V> w4{nullptr, Wq + 4 * Wfield, Wq + 2 * Wfield, Wplane, {T(1), T(1)},
                             {-kxv[0], -kxv[1]}, qok};
         fft_dif_io<T, true, V, true>(buf, TX, TX, plan, tws, sinv, kz_load, w4);
         __syncthreads();
     }
-    velocity(0);
+    if (!velocity(0)) return;
     {   // W3 = i (ky W2 - Fz(kz u_y))
-        stage_in(1);
+        if (!stage_in(1)) return;
         ZCurlStore<T, V> w3{nullptr, Wq + 3 * Wfield, Wq + 2 * Wfield, Wplane, {T(-1), T(-1)}, {ky, ky}, qok};
         fft_dif_io<T, true, V, true>(buf, TX, TX, plan, tws, sinv, kz_load, w3);
         __syncthreads();
     }
     {   // W1 = Fz u_y and W5 = i (kx W1 - ky W0)
-        stage_in(1);
+        if (!stage_in(1)) return;
         ZCurlStore<T, V> w5{Wq + 1 * Wfield, Wq + 5 * Wfield, Wq, Wplane, {kxv[0], kxv[1]}, {-ky, -ky}, qok};
         fft_dif_out<T, true, V, true>(buf, TX, TX, plan, tws, sinv, w5);
     }
@@ -225,15 +261,17 @@ k_zinv(const cplx<T>* __restrict__ U, cplx<T>* __restrict__ W, Geom g, FftPlan p
 // columns q of W[c] (A form, all nz rows) in by 16-byte asynchronous copies,
 // the kept modes jz (2/3 rule) back into rows jz < Mz of the same columns
 // (in place: a tile reads all of its rows before its first barrier).
-template <typename T>
+template <typename T, bool TMA>
 __global__ void __launch_bounds__(kThreadsInv)
 k_zfwd(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict__ tw,
-       const int* __restrict__ pos, int lgTX, const StepState* __restrict__ st)
+       const int* __restrict__ pos, int lgTX, const StepState* __restrict__ st,
+       const __grid_constant__ CUtensorMap wmap, int bh, int* err)
 {
     if (st && st->status != 0) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (TMA && *(volatile int*)err != 0) return;   // a TMA wait gave up earlier
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     const int TX = 1 << lgTX;
-    cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
+    cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127));
     cplx<T>* tws = buf + (g.nz << lgTX);
     int* sinv = reinterpret_cast<int*>(tws + g.nz);
     const int Q = g.My * g.Mxp, nz = g.nz, Kz = g.Kz, Mz = g.Mz;
@@ -242,7 +280,24 @@ k_zfwd(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict_
     const size_t Wplane = (size_t)g.ny * g.Mxp;
     load_tables<T>(tws, nullptr, tw, nullptr, nz, 0);
     load_inverse_pos(sinv, pos, nz);
-    {
+    if constexpr (TMA) {
+        // nz / bh boxes of bh rows of TX columns
+        __shared__ unsigned long long bar;
+        if (threadIdx.x == 0) mbar_init(&bar, 1);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const unsigned box = (unsigned)(((size_t)bh << lgTX) * sizeof(cplx<T>));
+            const int nb = nz / bh;
+            mbar_expect_tx(&bar, nb * box);
+            for (int b = 0; b < nb; ++b) tma_load_3d(buf + ((size_t)(b * bh) << lgTX), &wmap, 2 * q0, b * bh, c, &bar);
+        }
+        const bool ok = mbar_wait(&bar, 0);
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) atomicCAS(err, 0, (int)FLUSI_ETIMEOUT);
+            mbar_wait(&bar, 0);
+            return;
+        }
+    } else {
         constexpr int VEC = 16 / sizeof(cplx<T>);
         const int lpr = TX / VEC;              // lanes per row of the tile
         const int rstep = kThreadsInv / lpr;
@@ -258,8 +313,8 @@ k_zfwd(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict_
                 for (int v = 0; v < VEC; ++v) dst[v] = mkc<T>(0, 0);
             }
         }
+        cp_async_wait_all();
     }
-    cp_async_wait_all();
     __syncthreads();
     constexpr int V = 2;                       // adjacent columns per thread
     const int q = q0 + (threadIdx.x % (TX / V)) * V;
@@ -432,27 +487,92 @@ template <typename T> int zinv_tx(const Geom& g)
 
 template <typename T>
 cudaError_t launch_zi(const void* U, void* W, const Geom& g, const FftPlan& plan, const double2* tw,
-                      const int* pos, int nf, const StepState* st, cudaStream_t s)
+                      const int* pos, int nf, const StepState* st, const CUtensorMap* map, int bh, int* err,
+                      cudaStream_t s)
 {
     const int TX = zinv_tx<T>(g);
     if (g.nz * TX > cap_zi<T>() || kThreadsInv % TX != 0) return cudaErrorInvalidValue;
     const int blocks = ceil_div(g.My * g.Mxp, TX);
-    const size_t smem = sizeof(cplx<T>) * ((size_t)g.nz + (size_t)g.nz * TX) + sizeof(int) * g.nz;
-    k_zinv<T><<<blocks, kThreadsInv, smem, s>>>((const cplx<T>*)U, (cplx<T>*)W, g, plan, tw, pos, nf,
-                                                __builtin_ctz(TX), st);
+    const size_t smem = sizeof(cplx<T>) * ((size_t)g.nz + (size_t)g.nz * TX) + sizeof(int) * g.nz + 128;
+    const cplx<T>* u = (const cplx<T>*)U;
+    cplx<T>* w = (cplx<T>*)W;
+    if (map && bh > 0 && err) {
+        k_zinv<T, true><<<blocks, kThreadsInv, smem, s>>>(u, w, g, plan, tw, pos, nf, __builtin_ctz(TX), st, *map,
+                                                          bh, err);
+    } else {
+        CUtensorMap none{};
+        k_zinv<T, false><<<blocks, kThreadsInv, smem, s>>>(u, w, g, plan, tw, pos, nf, __builtin_ctz(TX), st, none,
+                                                           0, err);
+    }
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_zf(void* W, int nf, const Geom& g, const FftPlan& plan, const double2* tw,
-                      const int* pos, const StepState* st, cudaStream_t s)
+                      const int* pos, const StepState* st, const CUtensorMap* map, int bh, int* err,
+                      cudaStream_t s)
 {
     const int TX = zinv_tx<T>(g);
     if (g.nz * TX > cap_zi<T>() || kThreadsInv % TX != 0 || nf < 1 || nf > 6) return cudaErrorInvalidValue;
     const int blocks = nf * ceil_div(g.My * g.Mxp, TX);
-    const size_t smem = sizeof(cplx<T>) * ((size_t)g.nz + (size_t)g.nz * TX) + sizeof(int) * g.nz;
-    k_zfwd<T><<<blocks, kThreadsInv, smem, s>>>((cplx<T>*)W, g, plan, tw, pos, __builtin_ctz(TX), st);
+    const size_t smem = sizeof(cplx<T>) * ((size_t)g.nz + (size_t)g.nz * TX) + sizeof(int) * g.nz + 128;
+    cplx<T>* w = (cplx<T>*)W;
+    if (map && bh > 0 && err) {
+        k_zfwd<T, true><<<blocks, kThreadsInv, smem, s>>>(w, g, plan, tw, pos, __builtin_ctz(TX), st, *map, bh, err);
+    } else {
+        CUtensorMap none{};
+        k_zfwd<T, false><<<blocks, kThreadsInv, smem, s>>>(w, g, plan, tw, pos, __builtin_ctz(TX), st, none, 0, err);
+    }
     return cudaGetLastError();
+}
+
+typedef CUresult (*EncodeTiledZ)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// Tensor maps of the z sources: (2 Q reals, rows, components) with row stride
+// rs and component stride cs (complex values); box (2 TX, bh, 1).  The
+// inverse reads the kept rows of U (bh = Kz + 1, two boxes), the forward all
+// nz rows of W (bh = nz or 256).  Boxes over 256 rows, destinations off a
+// 128-byte boundary or a failed encoding leave that source to 16-byte copies.
+template <typename T> cudaError_t prepare_z(void* U, void* Ut, void* W, const Geom& g, ZMaps* m)
+{
+    m->u_bh = m->ut_bh = m->w_bh = 0;
+    static EncodeTiledZ encode = nullptr;
+    if (!encode) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn) {
+            cudaGetLastError();
+            return cudaSuccess;
+        }
+        encode = reinterpret_cast<EncodeTiledZ>(fn);
+    }
+    const int TX = zinv_tx<T>(g);
+    const size_t row_bytes = (size_t)TX * sizeof(cplx<T>);
+    const size_t Q = (size_t)g.My * g.Mxp;
+    const CUtensorMapDataType dt = sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    auto make = [&](CUtensorMap* map, void* base, size_t rows, size_t ncomp, size_t rs, size_t cs, int bh) {
+        if (!base || bh <= 0 || bh > 256 || reinterpret_cast<uintptr_t>(base) % 16 != 0) return 0;
+        const cuuint64_t dims[3] = {(cuuint64_t)(2 * Q), (cuuint64_t)rows, (cuuint64_t)ncomp};
+        const cuuint64_t strides[2] = {(cuuint64_t)(rs * sizeof(cplx<T>)), (cuuint64_t)(cs * sizeof(cplx<T>))};
+        const cuuint32_t box[3] = {(cuuint32_t)(2 * TX), (cuuint32_t)bh, 1};
+        const cuuint32_t estr[3] = {1, 1, 1};
+        const CUresult r = encode(map, dt, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        return r == CUDA_SUCCESS ? bh : 0;
+    };
+    const int ibh = ((size_t)(g.nz - g.Kz - 1) * row_bytes) % 128 == 0 ? g.Kz + 1 : 0;
+    m->u_bh = make(&m->u, U, g.Mz, 3, Q, (size_t)g.Mz * Q, ibh);
+    m->ut_bh = make(&m->ut, Ut, g.Mz, 3, Q, (size_t)g.Mz * Q, ibh);
+    int fbh = g.nz <= 256 ? g.nz : (g.nz % 256 == 0 ? 256 : 0);
+    if (((size_t)fbh * row_bytes) % 128 != 0) fbh = 0;
+    const size_t Wplane = (size_t)g.ny * g.Mxp;
+    m->w_bh = make(&m->w, W, g.nz, 6, Wplane, (size_t)g.nz * Wplane, fbh);
+    return cudaSuccess;
 }
 
 template <typename T>
@@ -486,19 +606,25 @@ cudaError_t launch_zu(int mode, const void* Nh, void* U, void* H, const Geom& g,
 
 }  // namespace
 
+cudaError_t prepare_zmaps(int fp64, void* U, void* Ut, void* W, const Geom& g, ZMaps* maps)
+{
+    return fp64 ? prepare_z<double>(U, Ut, W, g, maps) : prepare_z<float>(U, Ut, W, g, maps);
+}
+
 cudaError_t launch_zinv(int fp64, const void* U, void* W, const Geom& g, const FftPlan& plan,
                         const double2* tw, const int* pos, int nf, const StepState* st,
-                        cudaStream_t s)
+                        const CUtensorMap* map, int bh, int* err, cudaStream_t s)
 {
-    return fp64 ? launch_zi<double>(U, W, g, plan, tw, pos, nf, st, s)
-                : launch_zi<float>(U, W, g, plan, tw, pos, nf, st, s);
+    return fp64 ? launch_zi<double>(U, W, g, plan, tw, pos, nf, st, map, bh, err, s)
+                : launch_zi<float>(U, W, g, plan, tw, pos, nf, st, map, bh, err, s);
 }
 
 cudaError_t launch_zfwd(int fp64, void* W, int nf, const Geom& g, const FftPlan& plan,
-                        const double2* tw, const int* pos, const StepState* st, cudaStream_t s)
+                        const double2* tw, const int* pos, const StepState* st,
+                        const CUtensorMap* map, int bh, int* err, cudaStream_t s)
 {
-    return fp64 ? launch_zf<double>(W, nf, g, plan, tw, pos, st, s)
-                : launch_zf<float>(W, nf, g, plan, tw, pos, st, s);
+    return fp64 ? launch_zf<double>(W, nf, g, plan, tw, pos, st, map, bh, err, s)
+                : launch_zf<float>(W, nf, g, plan, tw, pos, st, map, bh, err, s);
 }
 
 cudaError_t launch_zupdate(int fp64, int mode, const void* W, void* U, void* H, const Geom& g,
@@ -514,10 +640,14 @@ cudaError_t configure_zpass()
     cudaError_t e;
 #define FLUSI_SMEM(fn) \
     if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
-    FLUSI_SMEM(k_zinv<float>)
-    FLUSI_SMEM(k_zinv<double>)
-    FLUSI_SMEM(k_zfwd<float>)
-    FLUSI_SMEM(k_zfwd<double>)
+    FLUSI_SMEM((k_zinv<float, false>))
+    FLUSI_SMEM((k_zinv<double, false>))
+    FLUSI_SMEM((k_zinv<float, true>))
+    FLUSI_SMEM((k_zinv<double, true>))
+    FLUSI_SMEM((k_zfwd<float, true>))
+    FLUSI_SMEM((k_zfwd<double, true>))
+    FLUSI_SMEM((k_zfwd<float, false>))
+    FLUSI_SMEM((k_zfwd<double, false>))
 #undef FLUSI_SMEM
     return cudaSuccess;
 }
