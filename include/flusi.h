@@ -254,6 +254,15 @@ int flusi_debug_fields(flusi_t h, void *out_dev);
 #define FLUSI_PROFILE_MAX 40
 int flusi_profile_step(flusi_t h, int n, double *ms, const char **names, int *nk);
 
+/* Diagnostic of the device-side failure path (no passage of the paper): one
+ * block waits, bounded by about `milliseconds` of SM clock, on an mbarrier
+ * that nothing completes -- the same bounded wait the tile loads of the y and
+ * z passes use -- and, when it gives up, sets FLUSI_ETIMEOUT in the device
+ * status word exactly as they do.  The next synchronizing call reports it
+ * and the handle answers FLUSI_ESTATE until flusi_set_state; the context
+ * stays usable.  0 < milliseconds <= 1000, else FLUSI_EINVAL. */
+int flusi_debug_wait_timeout(flusi_t h, double milliseconds);
+
 /* Kernels launched per step (for launch accounting). */
 int flusi_kernels_per_step(flusi_t h, int *count);
 

@@ -85,6 +85,7 @@ def _load():
         "flusi_set_state": ([h, vp, ip], ip),
         "flusi_set_kinematics": ([h, C.POINTER(Insect)], ip),
         "flusi_get_body": ([h, dp], ip),
+        "flusi_debug_wait_timeout": ([h, C.c_double], ip),
         "flusi_step": ([h, ip], ip),
         "flusi_sync": ([h], ip),
         "flusi_forces": ([h, dp, ip, C.POINTER(C.c_int), C.POINTER(C.c_longlong)], ip),

@@ -288,11 +288,12 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
 // Bounded wait for phase `parity` of the barrier: false when it gave up after
 // about 0.2 s of SM clock (each try_wait itself blocks for a short,
 // hardware-bounded time).
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity)
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity,
+                                          long long max_cycles = 400000000LL)
 {
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > 400000000LL) return false;
+        if (clock64() - t0 > max_cycles) return false;
     return true;
 }
 

@@ -841,6 +841,21 @@ int flusi_get_spectrum(flusi_t h, double* uh_out)
     return FLUSI_OK;
 }
 
+int flusi_debug_wait_timeout(flusi_t h, double milliseconds)
+{
+    int rc = check_ready(h, false);
+    if (rc) return rc;
+    if (!(milliseconds > 0 && milliseconds <= 1000)) return fail(h, FLUSI_EINVAL, "milliseconds must be in (0, 1000]");
+    int dev = 0, khz = 0;
+    CK(cudaGetDevice(&dev), "cudaGetDevice");
+    CK(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev), "clock rate");
+    if (khz <= 0) khz = 2000000;
+    const long long cycles = (long long)(milliseconds * khz);
+    k_wait_probe<<<1, 32, 0, h->stream>>>(status_word(h), cycles);
+    CK(cudaGetLastError(), "wait probe");
+    return FLUSI_OK;
+}
+
 int flusi_debug_fields(flusi_t h, void* out_dev)
 {
     int rc = check_ready(h, true);

@@ -22,6 +22,7 @@ namespace flusi {
 __global__ void k_kinematics(const flusi_insect* ins, const StepState* st, const StepCoef* coef, Frame* fr,
                              double h, double frac);
 __global__ void k_reset_state(StepState* st, StepCoef* coef);
+__global__ void k_wait_probe(int* err, long long max_cycles);
 __global__ void k_scalars(Geom g, const double* part, int nparts, StepState* st, StepCoef* coef,
                           double* rows, int ring, double* etab, double3 opts, double dt_diff,
                           const Frame* fr, flusi_insect* ins);

@@ -340,6 +340,21 @@ __global__ void k_kinematics(const flusi_insect* ins, const StepState* st, const
     *fr = F;
 }
 
+// A bounded wait on a barrier that nothing completes (the arrival count is 2
+// and one thread arrives once): gives up after max_cycles and reports as the
+// tile loads do.
+__global__ void k_wait_probe(int* err, long long max_cycles)
+{
+    __shared__ unsigned long long bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 2);
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(&bar)) : "memory");
+    }
+    __syncthreads();
+    const bool ok = mbar_wait(&bar, 0, max_cycles);
+    if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicCAS(err, 0, (int)FLUSI_ETIMEOUT);
+}
+
 __global__ void k_reset_state(StepState* st, StepCoef* coef)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;

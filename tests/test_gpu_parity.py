@@ -245,6 +245,35 @@ def test_nonfinite_state_is_reported(fl):
     sim.close()
 
 
+def test_bounded_wait_reports_a_timeout(fl):
+    """A device-side wait that runs out (an mbarrier nothing completes, the
+    bounded wait of the TMA tile loads) sets FLUSI_ETIMEOUT in the status word:
+    the next synchronizing call reports it within the bound, the handle refuses
+    steps until a new state is set, and the context stays usable."""
+    import time
+    cfg, ins = CASES["insect_32"]()
+    u0 = _initial(cfg)
+    sim = fl.Solver(cfg, ins, precision="fp32")
+    sim.set_state(u0)
+    sim.step(2)
+    sim.sync()
+    assert fl.lib.flusi_debug_wait_timeout(sim.h, 0.0) == fl.FLUSI_EINVAL
+    t0 = time.perf_counter()
+    assert fl.lib.flusi_debug_wait_timeout(sim.h, 20.0) == fl.FLUSI_OK
+    with pytest.raises(fl.FlusiError) as e:
+        sim.sync()
+    assert e.value.code == fl.FLUSI_ETIMEOUT
+    assert time.perf_counter() - t0 < 5.0
+    with pytest.raises(fl.FlusiError) as e:
+        sim.step(1)
+    assert e.value.code == fl.FLUSI_ESTATE
+    sim.set_state(u0)
+    sim.step(3)
+    rows, _ = sim.forces()
+    assert rows.shape[0] == 3 and np.isfinite(rows).all()
+    sim.close()
+
+
 def test_force_ring_drain(fl):
     cfg, ins = CASES["insect_32"]()
     cfg = dict(cfg, force_ring=4)
