@@ -54,7 +54,7 @@ constexpr int kSumEkin = 36;     // sum |u|^2
 constexpr int kSumUmax2 = 37;    // max |u|^2
 constexpr int kSumBad = 38;      // 1 if a non-finite value was met
 
-// Radix plan of one 1-D transform (mixed radix 2, 3, 4, 8; in-place
+// Radix plan of one 1-D transform (mixed radix 2, 3, 4, 8, 16; in-place
 // decimation in frequency / time, see fft.cuh).
 struct FftPlan {
     int n;                   // transform length
@@ -211,6 +211,13 @@ struct StepCoef {
 };
 
 __host__ __device__ inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+inline bool plan_has_radix16(const FftPlan& p)
+{
+    for (int s = 0; s < p.nst; ++s)
+        if (p.radix[s] == 16) return true;
+    return false;
+}
 
 // Asynchronous global -> shared copies of one complex value (8 or 16 bytes):
 // a tile's loads are all issued back to back, then waited for at once.

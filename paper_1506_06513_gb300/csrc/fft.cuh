@@ -228,7 +228,9 @@ __device__ __forceinline__ void fft_stage(cplx<T>* buf, int ld, int col, int jt,
 
 // Stages s in [s0, s1): ascending for DIF, descending for DIT.  Thread map:
 // column group (threadIdx.x % (C/V)) * V, butterflies jt, jt + P, ...
-template <typename T, bool INV, bool DIF, int V = 1>
+// R16: the plan may hold radix-16 stages (a separate instantiation, so the
+// kernels without them keep their register budget).
+template <typename T, bool INV, bool DIF, int V = 1, bool R16 = false>
 __device__ __forceinline__ void fft_run(cplx<T>* buf, int C, int ld, const FftPlan& plan,
                                         const cplx<T>* tw, int s0, int s1)
 {
@@ -241,6 +243,12 @@ __device__ __forceinline__ void fft_run(cplx<T>* buf, int C, int ld, const FftPl
         const int R = plan.radix[s];
         const int nbf = plan.n / R;
         const int m = plan.m[s], msh = plan.mshift[s], ls = plan.ls[s], ts = plan.tstep[s];
+        if constexpr (R16) {
+            if (R == 16) {
+                fft_stage<T, 16, INV, DIF, V>(buf, ld, col, jt, P, nbf, m, msh, ls, ts, tw);
+                continue;
+            }
+        }
         switch (R) {
         case 8: fft_stage<T, 8, INV, DIF, V>(buf, ld, col, jt, P, nbf, m, msh, ls, ts, tw); break;
         case 4: fft_stage<T, 4, INV, DIF, V>(buf, ld, col, jt, P, nbf, m, msh, ls, ts, tw); break;
@@ -365,12 +373,18 @@ __device__ __forceinline__ void fft_stage_last(const cplx<T>* buf, int ld, int c
     }
 }
 
-template <typename T, bool INV, int V, bool AUX = false, class Store>
+template <typename T, bool INV, int V, bool AUX = false, bool R16 = false, class Store>
 __device__ __forceinline__ void fft_last_to(const cplx<T>* buf, int ld, int col, int jt, int P,
                                             const FftPlan& plan, const int* sinv, Store& store)
 {
     const int last = plan.nst - 1;
     const int R = plan.radix[last], nbf = plan.n / R, fstep = plan.n / R;
+    if constexpr (R16) {
+        if (R == 16) {
+            fft_stage_last<T, 16, INV, V, AUX>(buf, ld, col, jt, P, nbf, fstep, sinv, store);
+            return;
+        }
+    }
     switch (R) {
     case 8: fft_stage_last<T, 8, INV, V, AUX>(buf, ld, col, jt, P, nbf, fstep, sinv, store); break;
     case 4: fft_stage_last<T, 4, INV, V, AUX>(buf, ld, col, jt, P, nbf, fstep, sinv, store); break;
@@ -381,12 +395,15 @@ __device__ __forceinline__ void fft_last_to(const cplx<T>* buf, int ld, int col,
 
 // Stage 0 from `load`, the middle stages in shared memory, the last stage to
 // `store` (sinv[row] = frequency held by that row).  All threads must call.
-template <typename T, bool INV, int V, bool AUX = false, class Load, class Store>
+template <typename T, bool INV, int V, bool AUX = false, bool R16 = false, class Load, class Store>
 __device__ void fft_dif_io(cplx<T>* buf, int C, int ld, const FftPlan& plan, const cplx<T>* tw,
                            const int* sinv, Load load, Store store)
 {
     const int G = C / V, P = blockDim.x / G, col = (threadIdx.x % G) * V, jt = threadIdx.x / G;
     const int m = plan.m[0], ts = plan.tstep[0];
+    if (R16 && plan.radix[0] == 16) {
+        if constexpr (R16) fft_stage_first<T, 16, INV, V>(buf, ld, col, jt, P, m, ts, tw, load);
+    } else
     switch (plan.radix[0]) {
     case 8: fft_stage_first<T, 8, INV, V>(buf, ld, col, jt, P, m, ts, tw, load); break;
     case 4: fft_stage_first<T, 4, INV, V>(buf, ld, col, jt, P, m, ts, tw, load); break;
@@ -408,19 +425,19 @@ __device__ void fft_dif_io(cplx<T>* buf, int C, int ld, const FftPlan& plan, con
         }
         return;
     }
-    fft_run<T, INV, true, V>(buf, C, ld, plan, tw, 1, last);
-    fft_last_to<T, INV, V, AUX>(buf, ld, col, jt, P, plan, sinv, store);
+    fft_run<T, INV, true, V, R16>(buf, C, ld, plan, tw, 1, last);
+    fft_last_to<T, INV, V, AUX, R16>(buf, ld, col, jt, P, plan, sinv, store);
 }
 
 // All stages but the last in shared memory (input tile in natural order), the
 // last stage to `store`.  All threads must call.
-template <typename T, bool INV, int V, bool AUX = false, class Store>
+template <typename T, bool INV, int V, bool AUX = false, bool R16 = false, class Store>
 __device__ void fft_dif_out(cplx<T>* buf, int C, int ld, const FftPlan& plan, const cplx<T>* tw,
                             const int* sinv, Store store)
 {
     const int G = C / V, P = blockDim.x / G, col = (threadIdx.x % G) * V, jt = threadIdx.x / G;
-    fft_run<T, INV, true, V>(buf, C, ld, plan, tw, 0, plan.nst - 1);
-    fft_last_to<T, INV, V, AUX>(buf, ld, col, jt, P, plan, sinv, store);
+    fft_run<T, INV, true, V, R16>(buf, C, ld, plan, tw, 0, plan.nst - 1);
+    fft_last_to<T, INV, V, AUX, R16>(buf, ld, col, jt, P, plan, sinv, store);
 }
 
 // Inverse digit-reversal table in shared memory: sinv[pos[f]] = f.

@@ -25,7 +25,7 @@ struct flusi_s {
     flusi_insect ins{};
     int have_ins = 0;
     Geom g{};
-    FftPlan px{}, py{}, pz{};
+    FftPlan px{}, py{}, pz{}, pzi{};   // pzi: the inverse z pass's plan (no radix-16 stage)
     YMaps ymaps{};                 // TMA descriptors of W for the y passes (built at bind)
     ZMaps zmaps{};                 // TMA descriptors of U, the RK4 stage state and W for the z passes
     // workspace
@@ -33,7 +33,7 @@ struct flusi_s {
     size_t ws_bytes = 0;
     cudaStream_t stream = nullptr;
     int bound = 0;
-    size_t oU = 0, oH = 0, oUt = 0, oW = 0, otx = 0, oty = 0, otz = 0, opx = 0, opy = 0, opz = 0,
+    size_t oU = 0, oH = 0, oUt = 0, oW = 0, otx = 0, oty = 0, otz = 0, opx = 0, opy = 0, opz = 0, opzi = 0,
            oframe = 0, oins = 0, ostate = 0, ocoef = 0, oetab = 0, opart = 0, orows = 0, total = 0;
     int part_cap = 0, xgrid = 0;
     // run state
@@ -89,7 +89,10 @@ bool smooth_size(int n)
 // Radix order: 3s first (their stages divide), then 8s, then a 4 or 4*4 or 2.
 // `tws` is the stride of the twiddle table the transform reads (its table has
 // n*tws entries), folded into the per-stage twiddle steps.
-FftPlan make_plan(int n, int tws)
+// radix16: 2^a with a = 3q + 1 (q >= 1) takes one radix-16 stage in place of
+// 8 x 2 (e.g. 1024 = 16 8 8 instead of 8 8 4 4): one pass through shared
+// memory fewer, for the y and z passes whose kernels have radix-16 variants.
+FftPlan make_plan(int n, int tws, bool radix16 = false)
 {
     FftPlan p{};
     p.n = n;
@@ -99,7 +102,8 @@ FftPlan make_plan(int n, int tws)
     int a = 0;
     while (m % 2 == 0) { ++a; m /= 2; }
     int q = a / 3, rem = a % 3;
-    if (rem == 1 && q >= 1) { q -= 1; rem = 4; }
+    if (rem == 1 && q >= 1) { q -= 1; rem = radix16 ? 16 : 4; }
+    if (rem == 16) r.push_back(16);
     for (int i = 0; i < q; ++i) r.push_back(8);
     if (rem == 2) r.push_back(4);
     if (rem == 1) r.push_back(2);
@@ -189,6 +193,7 @@ void layout(flusi_t h)
     h->opx = o; o = align256(o + sizeof(int) * (g.nx / 2));
     h->opy = o; o = align256(o + sizeof(int) * g.ny);
     h->opz = o; o = align256(o + sizeof(int) * g.nz);
+    h->opzi = o; o = align256(o + sizeof(int) * g.nz);
     h->oframe = o; o = align256(o + sizeof(Frame));
     h->oins = o; o = align256(o + sizeof(flusi_insect));
     h->ostate = o; o = align256(o + sizeof(StepState));
@@ -198,8 +203,11 @@ void layout(flusi_t h)
     h->orows = o; o = align256(o + sizeof(double) * kRowCols * h->opt.force_ring);
     h->total = o;
     h->px = make_plan(h->nx / 2, 2);
-    h->py = make_plan(h->ny, 1);
-    h->pz = make_plan(h->nz, 1);
+    h->py = make_plan(h->ny, 1, true);
+    h->pz = make_plan(h->nz, 1, true);
+    // the inverse z pass holds more live values per thread (the curl's side
+    // rows); a radix-16 stage there costs it a block per SM, more than it saves
+    h->pzi = make_plan(h->nz, 1, false);
 }
 
 template <typename P> P* at(flusi_t h, size_t off) { return reinterpret_cast<P*>(h->ws + off); }
@@ -336,7 +344,7 @@ cudaError_t enqueue_step(flusi_t h, cudaStream_t s, cudaEvent_t* ev, const char*
         mark(nm[1]);
         const CUtensorMap* umap = q == 0 ? &h->zmaps.u : &h->zmaps.ut;
         const int ubh = q == 0 ? h->zmaps.u_bh : h->zmaps.ut_bh;
-        if ((e = launch_zinv(fp64, ustage, W, g, h->pz, tz, at<int>(h, h->opz), 6, st, umap, ubh, &st->status, s)))
+        if ((e = launch_zinv(fp64, ustage, W, g, h->pzi, tz, at<int>(h, h->opzi), 6, st, umap, ubh, &st->status, s)))
             return e;
         mark(nm[2]);
         if ((e = launch_ypass(fp64, true, W, g, h->py, ty, at<int>(h, h->opy), 6, st, &h->ymaps, &st->status, s))) return e;
@@ -547,12 +555,15 @@ int flusi_bind(flusi_t h, void* ws, size_t bytes, void* stream)
     CK(cudaMemsetAsync(h->ws, 0, h->total, h->stream), "clear workspace");
     auto tx = twiddles(h->nx), ty = twiddles(h->ny), tz = twiddles(h->nz);
     auto px = digit_reversal(h->px), py = digit_reversal(h->py), pz = digit_reversal(h->pz);
+    auto pzi = digit_reversal(h->pzi);
     CK(cudaMemcpyAsync(h->ws + h->otx, tx.data(), sizeof(double2) * tx.size(), cudaMemcpyHostToDevice, h->stream), "twiddles");
     CK(cudaMemcpyAsync(h->ws + h->oty, ty.data(), sizeof(double2) * ty.size(), cudaMemcpyHostToDevice, h->stream), "twiddles");
     CK(cudaMemcpyAsync(h->ws + h->otz, tz.data(), sizeof(double2) * tz.size(), cudaMemcpyHostToDevice, h->stream), "twiddles");
     CK(cudaMemcpyAsync(h->ws + h->opx, px.data(), sizeof(int) * px.size(), cudaMemcpyHostToDevice, h->stream), "digit reversal");
     CK(cudaMemcpyAsync(h->ws + h->opy, py.data(), sizeof(int) * py.size(), cudaMemcpyHostToDevice, h->stream), "digit reversal");
     CK(cudaMemcpyAsync(h->ws + h->opz, pz.data(), sizeof(int) * pz.size(), cudaMemcpyHostToDevice, h->stream), "digit reversal");
+    CK(cudaMemcpyAsync(h->ws + h->opzi, pzi.data(), sizeof(int) * pzi.size(), cudaMemcpyHostToDevice, h->stream),
+       "digit reversal");
     // the host tables must outlive the asynchronous copies
     CK(cudaStreamSynchronize(h->stream), "bind tables");
     if (h->have_ins)
@@ -774,7 +785,7 @@ int flusi_get_state(flusi_t h, void* u_out, int where, double* t, long long* ste
     const size_t N = (size_t)g.nx * g.ny * g.nz;
     void* W = h->ws + h->oW;
     cudaStream_t s = h->stream;
-    CK(launch_zinv(fp64, h->ws + h->oU, W, g, h->pz, at<double2>(h, h->otz), at<int>(h, h->opz), 3, nullptr,
+    CK(launch_zinv(fp64, h->ws + h->oU, W, g, h->pzi, at<double2>(h, h->otz), at<int>(h, h->opzi), 3, nullptr,
                    &h->zmaps.u, h->zmaps.u_bh, status_word(h), s),
        "z inverse");
     CK(launch_ypass(fp64, true, W, g, h->py, at<double2>(h, h->oty), at<int>(h, h->opy), 3, nullptr,
@@ -869,7 +880,7 @@ int flusi_debug_fields(flusi_t h, void* out_dev)
     k_kinematics<<<1, 32, 0, s>>>(at<flusi_insect>(h, h->oins), st, at<StepCoef>(h, h->ocoef),
                                   at<Frame>(h, h->oframe), box_margin(h), 0.0);
     CK(cudaGetLastError(), "kinematics");
-    CK(launch_zinv(fp64, h->ws + h->oU, W, g, h->pz, at<double2>(h, h->otz), at<int>(h, h->opz), 6, nullptr,
+    CK(launch_zinv(fp64, h->ws + h->oU, W, g, h->pzi, at<double2>(h, h->otz), at<int>(h, h->opzi), 6, nullptr,
                    &h->zmaps.u, h->zmaps.u_bh, status_word(h), s),
        "z inverse");
     CK(launch_ypass(fp64, true, W, g, h->py, at<double2>(h, h->oty), at<int>(h, h->opy), 6, nullptr,

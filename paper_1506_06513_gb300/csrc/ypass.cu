@@ -23,7 +23,7 @@ constexpr int kThreads = 256;
 // complex elements per tile (64 KiB of shared memory)
 template <typename T> constexpr int tile_elems() { return sizeof(T) == 4 ? 8192 : 4096; }
 
-template <typename T, bool INV, bool TMA>
+template <typename T, bool INV, bool TMA, bool R16>
 __global__ void __launch_bounds__(kThreads)
 k_ypass(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict__ tw,
         const int* __restrict__ pos, int ncomp, int lgTX, int lgNP, const StepState* __restrict__ st,
@@ -120,13 +120,13 @@ k_ypass(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict
         auto store = [&](int f, const cplx<T>* v) {
             if (colok) st_row<T, V>(gcol + f * ld, v);
         };
-        fft_dif_out<T, true, V>(buf, C, C, plan, tws, sinv, store);
+        fft_dif_out<T, true, V, false, R16>(buf, C, C, plan, tws, sinv, store);
     } else {
         auto store = [&](int f, const cplx<T>* v) {   // keep modes |m| <= Ky only
             const int r = f <= Ky ? f : (f >= ny - Ky ? f - ny + My : -1);
             if (colok && r >= 0) st_row<T, V>(gcol + r * ld, v);
         };
-        fft_dif_out<T, false, V>(buf, C, C, plan, tws, sinv, store);
+        fft_dif_out<T, false, V, false, R16>(buf, C, C, plan, tws, sinv, store);
     }
 }
 
@@ -150,6 +150,32 @@ template <typename T> YTile y_tile(const Geom& g, int ncomp)
     return t;
 }
 
+template <typename T, bool R16>
+cudaError_t launch_y2(bool inverse, cplx<T>* w, const Geom& g, const FftPlan& plan, const double2* tw,
+                      const int* pos, int ncomp, const StepState* st, const YMaps* maps, int* err,
+                      const YTile& t, cudaStream_t s)
+{
+    const int bh = maps ? (inverse ? maps->inv_bh : maps->fwd_bh) : 0;
+    if (bh > 0 && err) {
+        const CUtensorMap& m = inverse ? maps->inv : maps->fwd;
+        if (inverse)
+            k_ypass<T, true, true, R16><<<t.blocks, kThreads, t.smem, s>>>(w, g, plan, tw, pos, ncomp, t.lgTX,
+                                                                            t.lgNP, st, m, bh, err);
+        else
+            k_ypass<T, false, true, R16><<<t.blocks, kThreads, t.smem, s>>>(w, g, plan, tw, pos, ncomp, t.lgTX,
+                                                                             t.lgNP, st, m, bh, err);
+    } else {
+        CUtensorMap none{};
+        if (inverse)
+            k_ypass<T, true, false, R16><<<t.blocks, kThreads, t.smem, s>>>(w, g, plan, tw, pos, ncomp, t.lgTX,
+                                                                             t.lgNP, st, none, 0, err);
+        else
+            k_ypass<T, false, false, R16><<<t.blocks, kThreads, t.smem, s>>>(w, g, plan, tw, pos, ncomp, t.lgTX,
+                                                                              t.lgNP, st, none, 0, err);
+    }
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_y(bool inverse, void* W, const Geom& g, const FftPlan& plan, const double2* tw,
                      const int* pos, int ncomp, const StepState* st, const YMaps* maps, int* err,
@@ -157,26 +183,9 @@ cudaError_t launch_y(bool inverse, void* W, const Geom& g, const FftPlan& plan, 
 {
     YTile t = y_tile<T>(g, ncomp);
     if ((size_t)g.ny << (t.lgTX + t.lgNP) > (size_t)tile_elems<T>()) return cudaErrorInvalidValue;
-    const int bh = maps ? (inverse ? maps->inv_bh : maps->fwd_bh) : 0;
     cplx<T>* w = (cplx<T>*)W;
-    if (bh > 0 && err) {
-        const CUtensorMap& m = inverse ? maps->inv : maps->fwd;
-        if (inverse)
-            k_ypass<T, true, true><<<t.blocks, kThreads, t.smem, s>>>(w, g, plan, tw, pos, ncomp, t.lgTX, t.lgNP,
-                                                                       st, m, bh, err);
-        else
-            k_ypass<T, false, true><<<t.blocks, kThreads, t.smem, s>>>(w, g, plan, tw, pos, ncomp, t.lgTX, t.lgNP,
-                                                                        st, m, bh, err);
-    } else {
-        CUtensorMap none{};
-        if (inverse)
-            k_ypass<T, true, false><<<t.blocks, kThreads, t.smem, s>>>(w, g, plan, tw, pos, ncomp, t.lgTX,
-                                                                        t.lgNP, st, none, 0, err);
-        else
-            k_ypass<T, false, false><<<t.blocks, kThreads, t.smem, s>>>(w, g, plan, tw, pos, ncomp, t.lgTX,
-                                                                         t.lgNP, st, none, 0, err);
-    }
-    return cudaGetLastError();
+    return plan_has_radix16(plan) ? launch_y2<T, true>(inverse, w, g, plan, tw, pos, ncomp, st, maps, err, t, s)
+                                  : launch_y2<T, false>(inverse, w, g, plan, tw, pos, ncomp, st, maps, err, t, s);
 }
 
 typedef CUresult (*EncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -247,14 +256,16 @@ cudaError_t configure_ypass()
     cudaError_t e;
 #define FLUSI_SMEM(fn) \
     if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
-    FLUSI_SMEM((k_ypass<float, true, false>))
-    FLUSI_SMEM((k_ypass<float, false, false>))
-    FLUSI_SMEM((k_ypass<double, true, false>))
-    FLUSI_SMEM((k_ypass<double, false, false>))
-    FLUSI_SMEM((k_ypass<float, true, true>))
-    FLUSI_SMEM((k_ypass<float, false, true>))
-    FLUSI_SMEM((k_ypass<double, true, true>))
-    FLUSI_SMEM((k_ypass<double, false, true>))
+#define FLUSI_SMEM_Y(T, R16)                         \
+    FLUSI_SMEM((k_ypass<T, true, false, R16>))       \
+    FLUSI_SMEM((k_ypass<T, false, false, R16>))      \
+    FLUSI_SMEM((k_ypass<T, true, true, R16>))        \
+    FLUSI_SMEM((k_ypass<T, false, true, R16>))
+    FLUSI_SMEM_Y(float, false)
+    FLUSI_SMEM_Y(double, false)
+    FLUSI_SMEM_Y(float, true)
+    FLUSI_SMEM_Y(double, true)
+#undef FLUSI_SMEM_Y
 #undef FLUSI_SMEM
     return cudaSuccess;
 }

@@ -132,8 +132,8 @@ template <typename T, int V> struct ZLoadKz {
 // five transforms, each velocity component read from DRAM once (its second
 // read follows the first), the side rows read back from L2.  nf = 3: the
 // velocity alone.
-template <typename T, bool TMA>
-__global__ void __launch_bounds__(kThreadsInv, sizeof(T) == 4 ? 3 : 1)
+template <typename T, bool TMA, bool R16>
+__global__ void __launch_bounds__(kThreadsInv, sizeof(T) == 4 ? (R16 ? 2 : 3) : 1)
 k_zinv(const cplx<T>* __restrict__ U, cplx<T>* __restrict__ W, Geom g, FftPlan plan,
        const double2* __restrict__ tw, const int* __restrict__ pos, int nf, int lgTX,
        const StepState* __restrict__ st, const __grid_constant__ CUtensorMap umap, int bh, int* err)
@@ -224,7 +224,7 @@ k_zinv(const cplx<T>* __restrict__ U, cplx<T>* __restrict__ W, Geom g, FftPlan p
     };
     auto velocity = [&](int comp) -> bool {
         if (!stage_in(comp)) return false;
-        fft_dif_out<T, true, V>(buf, TX, TX, plan, tws, sinv, ZStore<T, V>{Wq + comp * Wfield, Wplane, qok});
+        fft_dif_out<T, true, V, false, R16>(buf, TX, TX, plan, tws, sinv, ZStore<T, V>{Wq + comp * Wfield, Wplane, qok});
         __syncthreads();
         return true;
     };
@@ -240,20 +240,20 @@ k_zinv(const cplx<T>* __restrict__ U, cplx<T>* __restrict__ W, Geom g, FftPlan p
         if (!stage_in(0)) return;
         ZCurlStore<T, V> w4{nullptr, Wq + 4 * Wfield, Wq + 2 * Wfield, Wplane, {T(1), T(1)},
                             {-kxv[0], -kxv[1]}, qok};
-        fft_dif_io<T, true, V, true>(buf, TX, TX, plan, tws, sinv, kz_load, w4);
+        fft_dif_io<T, true, V, true, R16>(buf, TX, TX, plan, tws, sinv, kz_load, w4);
         __syncthreads();
     }
     if (!velocity(0)) return;
     {   // W3 = i (ky W2 - Fz(kz u_y))
         if (!stage_in(1)) return;
         ZCurlStore<T, V> w3{nullptr, Wq + 3 * Wfield, Wq + 2 * Wfield, Wplane, {T(-1), T(-1)}, {ky, ky}, qok};
-        fft_dif_io<T, true, V, true>(buf, TX, TX, plan, tws, sinv, kz_load, w3);
+        fft_dif_io<T, true, V, true, R16>(buf, TX, TX, plan, tws, sinv, kz_load, w3);
         __syncthreads();
     }
     {   // W1 = Fz u_y and W5 = i (kx W1 - ky W0)
         if (!stage_in(1)) return;
         ZCurlStore<T, V> w5{Wq + 1 * Wfield, Wq + 5 * Wfield, Wq, Wplane, {kxv[0], kxv[1]}, {-ky, -ky}, qok};
-        fft_dif_out<T, true, V, true>(buf, TX, TX, plan, tws, sinv, w5);
+        fft_dif_out<T, true, V, true, R16>(buf, TX, TX, plan, tws, sinv, w5);
     }
 }
 
@@ -261,7 +261,7 @@ k_zinv(const cplx<T>* __restrict__ U, cplx<T>* __restrict__ W, Geom g, FftPlan p
 // columns q of W[c] (A form, all nz rows) in by 16-byte asynchronous copies,
 // the kept modes jz (2/3 rule) back into rows jz < Mz of the same columns
 // (in place: a tile reads all of its rows before its first barrier).
-template <typename T, bool TMA>
+template <typename T, bool TMA, bool R16>
 __global__ void __launch_bounds__(kThreadsInv)
 k_zfwd(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict__ tw,
        const int* __restrict__ pos, int lgTX, const StepState* __restrict__ st,
@@ -324,7 +324,7 @@ k_zfwd(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict_
         const int jz = f <= Kz ? f : (f >= nz - Kz ? f - nz + Mz : -1);
         if (qok && jz >= 0) st_row<T, V>(out + (size_t)jz * Wplane, v);
     };
-    fft_dif_out<T, false, V>(buf, TX, TX, plan, tws, sinv, store);
+    fft_dif_out<T, false, V, false, R16>(buf, TX, TX, plan, tws, sinv, store);
 }
 
 // Pointwise spectral update over the kept modes, VEC adjacent columns per
@@ -496,13 +496,16 @@ cudaError_t launch_zi(const void* U, void* W, const Geom& g, const FftPlan& plan
     const size_t smem = sizeof(cplx<T>) * ((size_t)g.nz + (size_t)g.nz * TX) + sizeof(int) * g.nz + 128;
     const cplx<T>* u = (const cplx<T>*)U;
     cplx<T>* w = (cplx<T>*)W;
-    if (map && bh > 0 && err) {
-        k_zinv<T, true><<<blocks, kThreadsInv, smem, s>>>(u, w, g, plan, tw, pos, nf, __builtin_ctz(TX), st, *map,
-                                                          bh, err);
+    const bool tma = map && bh > 0 && err;
+    CUtensorMap none{};
+    const CUtensorMap& m = tma ? *map : none;
+    const int lg = __builtin_ctz(TX);
+    if (plan_has_radix16(plan)) {
+        if (tma) k_zinv<T, true, true><<<blocks, kThreadsInv, smem, s>>>(u, w, g, plan, tw, pos, nf, lg, st, m, bh, err);
+        else k_zinv<T, false, true><<<blocks, kThreadsInv, smem, s>>>(u, w, g, plan, tw, pos, nf, lg, st, m, 0, err);
     } else {
-        CUtensorMap none{};
-        k_zinv<T, false><<<blocks, kThreadsInv, smem, s>>>(u, w, g, plan, tw, pos, nf, __builtin_ctz(TX), st, none,
-                                                           0, err);
+        if (tma) k_zinv<T, true, false><<<blocks, kThreadsInv, smem, s>>>(u, w, g, plan, tw, pos, nf, lg, st, m, bh, err);
+        else k_zinv<T, false, false><<<blocks, kThreadsInv, smem, s>>>(u, w, g, plan, tw, pos, nf, lg, st, m, 0, err);
     }
     return cudaGetLastError();
 }
@@ -517,11 +520,16 @@ cudaError_t launch_zf(void* W, int nf, const Geom& g, const FftPlan& plan, const
     const int blocks = nf * ceil_div(g.My * g.Mxp, TX);
     const size_t smem = sizeof(cplx<T>) * ((size_t)g.nz + (size_t)g.nz * TX) + sizeof(int) * g.nz + 128;
     cplx<T>* w = (cplx<T>*)W;
-    if (map && bh > 0 && err) {
-        k_zfwd<T, true><<<blocks, kThreadsInv, smem, s>>>(w, g, plan, tw, pos, __builtin_ctz(TX), st, *map, bh, err);
+    const bool tma = map && bh > 0 && err;
+    CUtensorMap none{};
+    const CUtensorMap& m = tma ? *map : none;
+    const int lg = __builtin_ctz(TX);
+    if (plan_has_radix16(plan)) {
+        if (tma) k_zfwd<T, true, true><<<blocks, kThreadsInv, smem, s>>>(w, g, plan, tw, pos, lg, st, m, bh, err);
+        else k_zfwd<T, false, true><<<blocks, kThreadsInv, smem, s>>>(w, g, plan, tw, pos, lg, st, m, 0, err);
     } else {
-        CUtensorMap none{};
-        k_zfwd<T, false><<<blocks, kThreadsInv, smem, s>>>(w, g, plan, tw, pos, __builtin_ctz(TX), st, none, 0, err);
+        if (tma) k_zfwd<T, true, false><<<blocks, kThreadsInv, smem, s>>>(w, g, plan, tw, pos, lg, st, m, bh, err);
+        else k_zfwd<T, false, false><<<blocks, kThreadsInv, smem, s>>>(w, g, plan, tw, pos, lg, st, m, 0, err);
     }
     return cudaGetLastError();
 }
@@ -640,14 +648,16 @@ cudaError_t configure_zpass()
     cudaError_t e;
 #define FLUSI_SMEM(fn) \
     if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
-    FLUSI_SMEM((k_zinv<float, false>))
-    FLUSI_SMEM((k_zinv<double, false>))
-    FLUSI_SMEM((k_zinv<float, true>))
-    FLUSI_SMEM((k_zinv<double, true>))
-    FLUSI_SMEM((k_zfwd<float, true>))
-    FLUSI_SMEM((k_zfwd<double, true>))
-    FLUSI_SMEM((k_zfwd<float, false>))
-    FLUSI_SMEM((k_zfwd<double, false>))
+#define FLUSI_SMEM_Z(T, R16)                  \
+    FLUSI_SMEM((k_zinv<T, false, R16>))       \
+    FLUSI_SMEM((k_zinv<T, true, R16>))        \
+    FLUSI_SMEM((k_zfwd<T, false, R16>))       \
+    FLUSI_SMEM((k_zfwd<T, true, R16>))
+    FLUSI_SMEM_Z(float, false)
+    FLUSI_SMEM_Z(double, false)
+    FLUSI_SMEM_Z(float, true)
+    FLUSI_SMEM_Z(double, true)
+#undef FLUSI_SMEM_Z
 #undef FLUSI_SMEM
     return cudaSuccess;
 }
