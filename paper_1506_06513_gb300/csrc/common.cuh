@@ -212,6 +212,24 @@ struct StepCoef {
 
 __host__ __device__ inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
 
+// Rows per TMA box for an inverse tile of length n that keeps modes 0..K and
+// -K..-1 (rows 0..K and K..2K of the source, two parts of K + 1 rows): the
+// part split into the fewest equal boxes of at most 256 rows whose
+// destinations (row offsets times row_bytes) start on 128-byte boundaries;
+// 0 if there is none (the pass then copies by 16 bytes).
+inline int inverse_box_rows(int n, int K, size_t row_bytes)
+{
+    if (((size_t)(n - K - 1) * row_bytes) % 128 != 0) return 0;
+    for (int k = 1; k <= 8; ++k) {
+        if ((K + 1) % k != 0) continue;
+        const int bh = (K + 1) / k;
+        if (bh > 256) continue;
+        if (k > 1 && ((size_t)bh * row_bytes) % 128 != 0) continue;
+        return bh;
+    }
+    return 0;
+}
+
 inline bool plan_has_radix16(const FftPlan& p)
 {
     for (int s = 0; s < p.nst; ++s)

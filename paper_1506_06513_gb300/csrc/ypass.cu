@@ -71,10 +71,14 @@ k_ypass(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict
         if (threadIdx.x == 0) {
             if (INV) {
                 // modes 0..Ky to rows 0..Ky; modes Ky..2Ky to rows ny-Ky-1..ny-1
-                // (bh = Ky + 1; row ny-Ky-1 is cleared below)
-                mbar_expect_tx(&bar, 2 * box);
-                tma_load_3d(buf, &tmap, xr, pl, 0, &bar);
-                tma_load_3d(buf + ((size_t)(ny - Ky - 1) << lgC), &tmap, xr, pl, Ky, &bar);
+                // (kb boxes of bh = (Ky + 1)/kb rows each; row ny-Ky-1 is
+                // cleared below)
+                const int kb = (Ky + 1) / bh;
+                mbar_expect_tx(&bar, 2 * kb * box);
+                for (int q = 0; q < kb; ++q) {
+                    tma_load_3d(buf + ((size_t)(q * bh) << lgC), &tmap, xr, pl, q * bh, &bar);
+                    tma_load_3d(buf + ((size_t)(ny - Ky - 1 + q * bh) << lgC), &tmap, xr, pl, Ky + q * bh, &bar);
+                }
             } else {
                 const int nb = ny / bh;
                 mbar_expect_tx(&bar, nb * box);
@@ -227,8 +231,7 @@ template <typename T> cudaError_t prepare_y(void* W, const Geom& g, YMaps* m)
     };
     // every box destination (row offsets of the tile) on a 128-byte boundary
     const size_t row_bytes = sizeof(cplx<T>) << (t.lgTX + t.lgNP);
-    const int ibh = ((size_t)(g.ny - g.Ky - 1) * row_bytes) % 128 == 0 ? g.Ky + 1 : 0;
-    m->inv_bh = make(&m->inv, ibh);
+    m->inv_bh = make(&m->inv, inverse_box_rows(g.ny, g.Ky, row_bytes));
     int fbh = g.ny <= 256 ? g.ny : (g.ny % 256 == 0 ? 256 : 0);
     if (((size_t)fbh * row_bytes) % 128 != 0) fbh = 0;
     m->fwd_bh = make(&m->fwd, fbh);

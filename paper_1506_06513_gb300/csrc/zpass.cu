@@ -186,9 +186,13 @@ k_zinv(const cplx<T>* __restrict__ U, cplx<T>* __restrict__ W, Geom g, FftPlan p
                 // earlier generic writes to buf before the asynchronous proxy's
                 fence_proxy_async();
                 const unsigned box = (unsigned)(((size_t)bh << lgTX) * sizeof(cplx<T>));
-                mbar_expect_tx(&bar, 2 * box);
-                tma_load_3d(buf, &umap, 2 * q0, 0, comp, &bar);
-                tma_load_3d(buf + ((size_t)(nz - Kz - 1) << lgTX), &umap, 2 * q0, Kz, comp, &bar);
+                const int kb = (Kz + 1) / bh;   // boxes per part
+                mbar_expect_tx(&bar, 2 * kb * box);
+                for (int b = 0; b < kb; ++b) {
+                    tma_load_3d(buf + ((size_t)(b * bh) << lgTX), &umap, 2 * q0, b * bh, comp, &bar);
+                    tma_load_3d(buf + ((size_t)(nz - Kz - 1 + b * bh) << lgTX), &umap, 2 * q0, Kz + b * bh, comp,
+                                &bar);
+                }
             }
             const bool ok = mbar_wait(&bar, phase);
             if (__syncthreads_or(!ok)) {
@@ -573,7 +577,7 @@ template <typename T> cudaError_t prepare_z(void* U, void* Ut, void* W, const Ge
                                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         return r == CUDA_SUCCESS ? bh : 0;
     };
-    const int ibh = ((size_t)(g.nz - g.Kz - 1) * row_bytes) % 128 == 0 ? g.Kz + 1 : 0;
+    const int ibh = inverse_box_rows(g.nz, g.Kz, row_bytes);
     m->u_bh = make(&m->u, U, g.Mz, 3, Q, (size_t)g.Mz * Q, ibh);
     m->ut_bh = make(&m->ut, Ut, g.Mz, 3, Q, (size_t)g.Mz * Q, ibh);
     int fbh = g.nz <= 256 ? g.nz : (g.nz % 256 == 0 ? 256 : 0);
