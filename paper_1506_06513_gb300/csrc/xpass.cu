@@ -762,7 +762,9 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
     FrameT<T>* Fs = reinterpret_cast<FrameT<T>*>(wacc + kWarpsX * 36);
     cplx<T>* twx = reinterpret_cast<cplx<T>*>(
         reinterpret_cast<unsigned char*>(Fs) + ((sizeof(FrameT<T>) + 15) / 16) * 16);
-    cplx<T>* tw2 = twx + NH;               // tw2[q L + j] = w_nh^{j q}
+    // w_nh^{j q} (q < R, j < L) at q L + (j ^ q): conflict-free both for a
+    // fixed q across lanes j and for a fixed j across lanes q
+    cplx<T>* tw2 = twx + NH;
     cplx<T>* buf = tw2 + NH;               // C line slices of CS values
     __shared__ int rowmask[RB];
 
@@ -773,7 +775,7 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
     for (int i = tid; i < NH; i += blockDim.x) {
         const int q = i / L, jj = i % L;
         const double2 w = tw[(2 * jj * q) % nx];
-        tw2[i] = mkc<T>(T(w.x), T(w.y));
+        tw2[q * L + (jj ^ q)] = mkc<T>(T(w.x), T(w.y));
     }
     for (int i = tid; i < kWarpsX * 36; i += blockDim.x) wacc[i] = 0.0;
     if (tid == 0) setup_frame<T>(*Fs, *ex.frame, ex.shape, 1.0 / g.eta);
@@ -832,7 +834,7 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
             sq_exchange_pre<T, R, L>(v, j, twx);
             Dft<T, R, true>::run(v);
 #pragma unroll
-            for (int q = 1; q < R; ++q) v[q] = cmul(v[q], cconj(tw2[q * L + j]));
+            for (int q = 1; q < R; ++q) v[q] = cmul(v[q], cconj(tw2[q * L + (j ^ q)]));
             if constexpr (S == 1) {
 #pragma unroll
                 for (int q = 0; q < R; ++q) line[R * q + (j ^ q)] = v[q];
@@ -1019,7 +1021,7 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
 #pragma unroll
                 for (int t = 0; t < R; ++t) v[t] = line[R * t + (j ^ t)];
 #pragma unroll
-                for (int t = 1; t < R; ++t) v[t] = cmul(v[t], tw2[t * R + j]);
+                for (int t = 1; t < R; ++t) v[t] = cmul(v[t], tw2[t * R + (j ^ t)]);
             } else {
                 // lane j = (k1, p): radix 2 over the two halves h of its points
                 // k1 + R k' + R^2 h, the twiddles w_2R^{p k'}, radix R over k',
@@ -1037,7 +1039,7 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
                 }
                 Dft<T, R, false>::run(v);   // over k' -> j'
 #pragma unroll
-                for (int i = 0; i < R; ++i) v[i] = cmul(v[i], tw2[k1 * L + 2 * i + p]);
+                for (int i = 0; i < R; ++i) v[i] = cmul(v[i], tw2[k1 * L + ((2 * i + p) ^ k1)]);
                 __syncwarp();
 #pragma unroll
                 for (int i = 0; i < R; ++i) line[L * k1 + ((2 * i + p) ^ k1)] = v[i];
