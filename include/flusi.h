@@ -5,9 +5,11 @@
  *
  * Method: Engels, Kolomenskiy, Schneider, Sesterhenn, "FluSI: a novel
  * parallel simulation tool for flapping insect flight using a Fourier method
- * with volume penalization" (arXiv 1506.06513): Eq. PNST_org_momentum without
- * the sponge term, Sec. 2.4 (discretization, 2/3 rule, AB2 with integrating
- * factor), Sec. 3 (insect geometry and kinematics), Algorithm 1 (one step).
+ * with volume penalization" (arXiv 1506.06513): Eq. PNST_org_momentum (the
+ * vorticity sponge and the Dirichlet inflow layer of Sec. 2.3 as options),
+ * Sec. 2.4 (discretization, 2/3 rule, AB2 with integrating factor, or RK4),
+ * Sec. 3 (insect geometry, kinematics, power and free flight), Algorithm 1
+ * (one step).
  *
  * Conventions shared by every entry point
  *  - Grid x_i = i*Lx/nx (same for y, z); physical fields are [3][nz][ny][nx],

@@ -7,8 +7,8 @@
 //          y-modes ("A" form, after the z transform) or all ny rows hold grid
 //          y values ("B" form, after the y transform); each row carries the
 //          Mx kept x-modes padded with zeros to Mxp.
-// One step: kinematics -> zinv (u, curl) -> yinv -> xpass (c2r, physics, r2c)
-//           -> scalars -> yfwd -> zfwd (projection, IF-AB2).
+// One step: kinematics -> zinv (u, omega) -> yinv -> xpass (c2r, physics, r2c)
+//           -> scalars -> yfwd -> zfwd -> zupdate (projection, IF-AB2).
 #pragma once
 
 #include <cuda.h>   // CUtensorMap (descriptor type only; the encoder is fetched at run time)
@@ -54,8 +54,7 @@ cudaError_t prepare_zmaps(int fp64, void* U, void* Ut, void* W, const Geom& g, Z
 cudaError_t launch_zinv(int fp64, const void* U, void* W, const Geom& g, const FftPlan& plan,
                         const double2* tw, const int* pos, int nf, const StepState* st,
                         const CUtensorMap* map, int bh, int* err, cudaStream_t s);
-//   zfwd: W[0..3) in A form -> FFT -> projection ->
-//   mode 0: IF-AB2 update of U with history H;  mode 1: U = result, H = 0.
+// Extra arguments of the spectral update (launch_zupdate).
 struct ZfwdExtra {
     const StepCoef* coef;     // mode 0
     const double* etab;       // mode 0: [E1x Mx][E1y My][E1z Mz][E2x][E2y][E2z]
