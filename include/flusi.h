@@ -97,7 +97,10 @@ typedef struct flusi_options {
      * to dt <= 2.5/(nu |k|^2_max).  RK4 needs one more state-sized buffer, so
      * it is fixed at flusi_bind.                                             */
     int time_scheme;
-    int pad_;
+    /* 1 (default): the y and z passes receive their tiles by TMA boxes
+     * (cp.async.bulk.tensor) where a box fits; 0: by 16-byte asynchronous
+     * copies everywhere.  Both give identical results. */
+    int use_tma;
 } flusi_options;
 
 /* Insect geometry and kinematics (Sec. 3).  Angles in radians.  Kinematic

@@ -37,7 +37,7 @@ class Options(C.Structure):
                 ("force_ring", C.c_int), ("use_graph", C.c_int),
                 ("sponge_c", C.c_double), ("sponge_width", C.c_double * 3),
                 ("layer_width", C.c_double * 3),
-                ("time_scheme", C.c_int), ("pad_", C.c_int)]
+                ("time_scheme", C.c_int), ("use_tma", C.c_int)]
 
 
 _F = C.c_double * MAX_FOURIER
@@ -354,6 +354,7 @@ def make_options(cfg: dict) -> Options:
     o.sponge_width[:] = cfg.get("sponge_width", (0.0, 0.0, 0.0))
     o.layer_width[:] = cfg.get("layer_width", (0.0, 0.0, 0.0))
     o.time_scheme = {"ab2": 0, "rk4": 1}[cfg.get("time_scheme", "ab2")]
+    o.use_tma = int(cfg.get("use_tma", 1))
     return o
 
 

@@ -450,6 +450,19 @@ void quat_of_angles(double psi, double beta, double gamma, double* eps)
     mulq(t, qx, eps);
 }
 
+// TMA descriptors of the bound workspace (none with use_tma = 0).
+int prepare_maps(flusi_t h)
+{
+    h->ymaps = YMaps{};
+    h->zmaps = ZMaps{};
+    if (!h->opt.use_tma) return FLUSI_OK;
+    CK(prepare_ymaps(h->prec == FLUSI_FP64, h->ws + h->oW, h->g, &h->ymaps), "y tensor maps");
+    CK(prepare_zmaps(h->prec == FLUSI_FP64, h->ws + h->oU, is_rk4(h) ? h->ws + h->oUt : nullptr, h->ws + h->oW,
+                     h->g, &h->zmaps),
+       "z tensor maps");
+    return FLUSI_OK;
+}
+
 // Shapes are value-initialized, padding included, so bytes compare fields.
 bool same_shape(const Shape& a, const Shape& b) { return std::memcmp(&a, &b, sizeof a) == 0; }
 
@@ -471,6 +484,7 @@ void flusi_default_options(flusi_options* o)
     o->cfl = 0.1;
     o->force_ring = 4096;
     o->use_graph = 1;
+    o->use_tma = 1;
 }
 
 int flusi_create(int nx, int ny, int nz, const double L[3], double nu, double eta, int precision,
@@ -507,6 +521,7 @@ int flusi_set_options(flusi_t h, const flusi_options* o)
     if (!(o->sponge_c >= 0) || !std::isfinite(o->sponge_c))
         return fail(h, FLUSI_EINVAL, "sponge_c must be >= 0 (0: no sponge)");
     if (o->time_scheme != 0 && o->time_scheme != 1) return fail(h, FLUSI_EINVAL, "time_scheme must be 0 or 1");
+    if (o->use_tma != 0 && o->use_tma != 1) return fail(h, FLUSI_EINVAL, "use_tma must be 0 or 1");
     if (h->bound && o->time_scheme != h->opt.time_scheme)
         return fail(h, FLUSI_EINVAL, "time_scheme cannot change after flusi_bind");
     if (o->time_scheme != 0 && h->have_ins && h->ins.free_flight)
@@ -520,6 +535,10 @@ int flusi_set_options(flusi_t h, const flusi_options* o)
     h->opt = *o;
     layout(h);
     drop_graph(h);
+    if (h->bound) {
+        int rc = prepare_maps(h);
+        if (rc) return rc;
+    }
     return FLUSI_OK;
 }
 
@@ -547,10 +566,8 @@ int flusi_bind(flusi_t h, void* ws, size_t bytes, void* stream)
     h->ws_bytes = bytes;
     h->stream = static_cast<cudaStream_t>(stream);
     h->xgrid = xpass_grid(h->prec == FLUSI_FP64, h->g);
-    CK(prepare_ymaps(h->prec == FLUSI_FP64, h->ws + h->oW, h->g, &h->ymaps), "y tensor maps");
-    CK(prepare_zmaps(h->prec == FLUSI_FP64, h->ws + h->oU, is_rk4(h) ? h->ws + h->oUt : nullptr, h->ws + h->oW,
-                     h->g, &h->zmaps),
-       "z tensor maps");
+    int rc = prepare_maps(h);
+    if (rc) return rc;
     if (h->xgrid > h->part_cap) h->xgrid = h->part_cap;
     CK(cudaMemsetAsync(h->ws, 0, h->total, h->stream), "clear workspace");
     auto tx = twiddles(h->nx), ty = twiddles(h->ny), tz = twiddles(h->nz);
