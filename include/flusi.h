@@ -368,7 +368,9 @@ int flusi_ensemble_destroy(flusi_ensemble_t e);
 /* Release the handle (not the caller's workspace).  NULL is a no-op. */
 int flusi_destroy(flusi_t h);
 
-/* Message of the last failed call on h (or of flusi_create when h is NULL). */
+/* Message of the last failed call on h; with h NULL, of the calling thread's
+ * last failed call that had no handle (flusi_create, the allocation-free
+ * entry point).  Valid until the next failing call of the same kind. */
 const char *flusi_last_error(flusi_t h);
 
 #ifdef __cplusplus

@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <initializer_list>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -52,7 +53,9 @@ struct flusi_s {
 
 namespace {
 
-std::string g_create_err;
+// errors without a handle (creation, the allocation-free entry point), per
+// calling thread
+thread_local std::string g_create_err;
 
 }  // namespace
 
@@ -554,12 +557,19 @@ int flusi_bind(flusi_t h, void* ws, size_t bytes, void* stream)
     if (!h || !ws) return fail(h, FLUSI_EINVAL, "NULL argument");
     if ((reinterpret_cast<uintptr_t>(ws) & 255) != 0) return fail(h, FLUSI_EINVAL, "workspace not 256-byte aligned");
     if (bytes < h->total) return fail(h, FLUSI_ENOMEM, "workspace smaller than flusi_workspace_bytes");
-    static int configured = 0;
-    if (!configured) {
-        CK(configure_ypass(), "configure y pass");
-        CK(configure_zpass(), "configure z pass");
-        CK(configure_xpass(), "configure x pass");
-        configured = 1;
+    {
+        // kernel attributes (shared-memory limits), once per device
+        static std::mutex mu;
+        static std::vector<int> done;
+        int dev = 0;
+        CK(cudaGetDevice(&dev), "cudaGetDevice");
+        std::lock_guard<std::mutex> lock(mu);
+        if (std::find(done.begin(), done.end(), dev) == done.end()) {
+            CK(configure_ypass(), "configure y pass");
+            CK(configure_zpass(), "configure z pass");
+            CK(configure_xpass(), "configure x pass");
+            done.push_back(dev);
+        }
     }
     drop_graph(h);
     h->ws = static_cast<char*>(ws);

@@ -32,6 +32,13 @@ __global__ void k_scalars(Geom g, const double* part, int nparts, StepState* st,
 // With maps (tensor descriptors of W built by prepare_ymaps for this handle's
 // W) a tile arrives by TMA boxes, else by 16-byte asynchronous copies; a TMA
 // wait that gives up sets *err = FLUSI_ETIMEOUT.
+// cuTensorMapEncodeTiled through the runtime's driver entry point (fetched
+// once, thread-safely), or nullptr when the driver does not offer it.
+typedef CUresult (*TensorMapEncoder)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                     const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
+                                     CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                     CUtensorMapFloatOOBfill);
+TensorMapEncoder tensor_map_encoder();
 struct YMaps {
     CUtensorMap inv, fwd;
     int inv_bh = 0, fwd_bh = 0;   // box heights (rows); 0: that direction copies by 16 bytes

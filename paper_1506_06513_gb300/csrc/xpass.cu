@@ -17,6 +17,8 @@
 //   r x chi u_s per colour, |u|^2, max |u|^2 and a non-finite flag.
 // The grid is persistent (a multiple of the SM count); each CTA writes one
 // row of partial sums, reduced in a fixed order by the scalar kernel.
+#include <atomic>
+
 #include "fft.cuh"
 #include "kernels.cuh"
 
@@ -1158,16 +1160,12 @@ template <typename T> size_t x_smem(const Geom& g, int lgRB, int NF)
     return s;
 }
 
-int g_sm_count = 0;
-
 template <typename T> int x_grid(const Geom& g)
 {
-    if (g_sm_count == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev);
-        if (g_sm_count <= 0) g_sm_count = 1;
-    }
+    int dev = 0, sm_count = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (sm_count <= 0) sm_count = 1;
     int per_sm = 0, ntiles = 0;
     const int kind = sq_kind<T>(g);
 #define FLUSI_SQ_OCC(R, S)                                                                          \
@@ -1190,7 +1188,7 @@ template <typename T> int x_grid(const Geom& g)
     }
 #undef FLUSI_SQ_OCC
     if (per_sm <= 0) per_sm = 1;
-    int grid = g_sm_count * per_sm;
+    int grid = sm_count * per_sm;
     return grid < ntiles ? grid : ntiles;
 }
 
@@ -1456,7 +1454,7 @@ __global__ void k_noalloc_reduce(const double* __restrict__ part, int nparts, do
 
 // Device address of the scratch array, looked up once per device.
 constexpr int kNoallocMaxDevices = 64;
-double* g_noalloc_ptr[kNoallocMaxDevices] = {};
+std::atomic<double*> g_noalloc_ptr[kNoallocMaxDevices] = {};
 
 }  // namespace
 
@@ -1490,16 +1488,17 @@ extern "C" int flusi_penalization_sums_noalloc(int nx, int ny, int nz, const dou
         set_global_error("flusi_penalization_sums_noalloc: no usable current device");
         return FLUSI_ECUDA;
     }
-    if (!g_noalloc_ptr[dev]) {
+    double* scratch = g_noalloc_ptr[dev].load(std::memory_order_acquire);
+    if (!scratch) {
         void* p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) {
             set_global_error("flusi_penalization_sums_noalloc: cudaGetSymbolAddress failed");
             return FLUSI_ECUDA;
         }
-        g_noalloc_ptr[dev] = static_cast<double*>(p);
+        scratch = static_cast<double*>(p);
+        g_noalloc_ptr[dev].store(scratch, std::memory_order_release);   // the same address from any thread
     }
-    double* scratch = g_noalloc_ptr[dev];
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
 
     // header: descriptor, step state (only t is read), frame block

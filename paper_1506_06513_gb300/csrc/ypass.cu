@@ -192,10 +192,6 @@ cudaError_t launch_y(bool inverse, void* W, const Geom& g, const FftPlan& plan, 
                                   : launch_y2<T, false>(inverse, w, g, plan, tw, pos, ncomp, st, maps, err, t, s);
 }
 
-typedef CUresult (*EncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
 // Tensor maps of W for the y tiles: dims (2 Mxp reals, 6 nz planes, ny rows)
 // with strides (plane ny Mxp, row Mxp complex); boxes (2 TX, NP, bh).  A box
 // height over 256 (the hardware's limit) leaves that direction to 16-byte
@@ -203,18 +199,8 @@ typedef CUresult (*EncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, v
 template <typename T> cudaError_t prepare_y(void* W, const Geom& g, YMaps* m)
 {
     m->inv_bh = m->fwd_bh = 0;
-    static EncodeTiled encode = nullptr;
-    if (!encode) {
-        void* fn = nullptr;
-        cudaDriverEntryPointQueryResult q{};
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
-                cudaSuccess ||
-            q != cudaDriverEntryPointSuccess || !fn) {
-            cudaGetLastError();
-            return cudaSuccess;   // no encoder: 16-byte copies
-        }
-        encode = reinterpret_cast<EncodeTiled>(fn);
-    }
+    const TensorMapEncoder encode = tensor_map_encoder();
+    if (!encode) return cudaSuccess;   // no encoder: 16-byte copies
     if (reinterpret_cast<uintptr_t>(W) % 16 != 0) return cudaSuccess;
     const YTile t = y_tile<T>(g, 1);
     const cuuint64_t dims[3] = {(cuuint64_t)2 * g.Mxp, (cuuint64_t)6 * g.nz, (cuuint64_t)g.ny};
@@ -239,6 +225,22 @@ template <typename T> cudaError_t prepare_y(void* W, const Geom& g, YMaps* m)
 }
 
 }  // namespace
+
+TensorMapEncoder tensor_map_encoder()
+{
+    static const TensorMapEncoder enc = [] {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn) {
+            cudaGetLastError();
+            return TensorMapEncoder(nullptr);
+        }
+        return reinterpret_cast<TensorMapEncoder>(fn);
+    }();
+    return enc;
+}
 
 cudaError_t prepare_ymaps(int fp64, void* W, const Geom& g, YMaps* maps)
 {

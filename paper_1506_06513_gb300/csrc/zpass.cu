@@ -538,10 +538,6 @@ cudaError_t launch_zf(void* W, int nf, const Geom& g, const FftPlan& plan, const
     return cudaGetLastError();
 }
 
-typedef CUresult (*EncodeTiledZ)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
 // Tensor maps of the z sources: (2 Q reals, rows, components) with row stride
 // rs and component stride cs (complex values); box (2 TX, bh, 1).  The
 // inverse reads the kept rows of U (bh = Kz + 1, two boxes), the forward all
@@ -550,18 +546,8 @@ typedef CUresult (*EncodeTiledZ)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, 
 template <typename T> cudaError_t prepare_z(void* U, void* Ut, void* W, const Geom& g, ZMaps* m)
 {
     m->u_bh = m->ut_bh = m->w_bh = 0;
-    static EncodeTiledZ encode = nullptr;
-    if (!encode) {
-        void* fn = nullptr;
-        cudaDriverEntryPointQueryResult q{};
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
-                cudaSuccess ||
-            q != cudaDriverEntryPointSuccess || !fn) {
-            cudaGetLastError();
-            return cudaSuccess;
-        }
-        encode = reinterpret_cast<EncodeTiledZ>(fn);
-    }
+    const TensorMapEncoder encode = tensor_map_encoder();
+    if (!encode) return cudaSuccess;   // no encoder: 16-byte copies
     const int TX = zinv_tx<T>(g);
     const size_t row_bytes = (size_t)TX * sizeof(cplx<T>);
     const size_t Q = (size_t)g.My * g.Mxp;
