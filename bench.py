@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--wake", action="store_true",
                     help="add the wake-removal terms: a vorticity sponge (C_sp 0.1) 32 grid "
                          "points deep at the x and y ends and a Dirichlet layer 4 points deep at the x end")
+    ap.add_argument("--insect", default="model", choices=["model", "realistic", "curved"],
+                    help="model: ellipsoid thorax and plate wings; realistic: thorax, head, eyes and "
+                         "16-harmonic contour wings; curved: the realistic insect on a curved thorax")
     ap.add_argument("--flight", action="store_true",
                     help="free flight (Sec. 3.6) with the power columns: the body state advances "
                          "every step (mass 400, J_body (2, 5, 5), g 9.81, wing J set)")
@@ -143,6 +146,9 @@ def workload_setup(args):
         shape = tuple(int(v) for v in args.shape.split(","))
         cfg = dict(cfg, n=shape)
         ins = workloads.model_insect(cfg["L"], shape)
+    if args.insect != "model":
+        make = workloads.realistic_insect if args.insect == "realistic" else workloads.curved_insect
+        ins = dict(make(cfg["L"], cfg["n"]), kinematics=ins["kinematics"])
     if args.rk4:
         cfg = dict(cfg, time_scheme="rk4")
     if args.flight:
@@ -230,7 +236,7 @@ def in_free_flight(ins):
                 free_flight={"mass": 400.0, "gravity": 9.81, "J_body": (2.0, 5.0, 5.0)})
 
 
-def oracle_workload(workload, n, flight=False):
+def oracle_workload(workload, n, flight=False, insect="model"):
     """The workload at a reduced grid n^3 for the oracle: (cfg, insect, u0 FP64)."""
     if workload == "turbulent_insect":
         cfg, ins = workloads.config_turbulent_insect(n)
@@ -238,14 +244,17 @@ def oracle_workload(workload, n, flight=False):
     else:
         cfg, ins = workloads.config_model_insect(n)
         u0 = workloads.shear_waves(cfg["n"], cfg["L"], mean=cfg["u_inf"])
+    if insect != "model":
+        make = workloads.realistic_insect if insect == "realistic" else workloads.curved_insect
+        ins = dict(make(cfg["L"], cfg["n"]), kinematics=ins["kinematics"])
     return cfg, in_free_flight(ins) if flight else ins, u0
 
 
-def oracle_sample(workload, n_sample=128, steps=3, flight=False):
+def oracle_sample(workload, n_sample=128, steps=3, flight=False, insect="model"):
     """The oracle (single-threaded C, FP64) on the same workload at a reduced
     grid, as it stands: grid-point steps/s."""
     import oracle
-    cfg, ins, u0 = oracle_workload(workload, n_sample, flight)
+    cfg, ins, u0 = oracle_workload(workload, n_sample, flight, insect)
     sim = oracle.Simulation(cfg, ins)
     sim.set_state(u0)
     t0 = time.perf_counter()
@@ -428,13 +437,13 @@ def run_flusi(args):
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = oracle_sample(args.workload, flight=args.flight)
+        cpu = oracle_sample(args.workload, flight=args.flight, insect=args.insect)
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": workload_config(cfg["n"], world, args.workload, args.wake, args.flight),
+        "config": workload_config(cfg["n"], world, args.workload, args.wake, args.flight, args.insect),
         "roofline": roofline,
         "stage_model": {"bytes_per_step": stage, "frac_of_peak": round(stage / (ms_per_step * 1e-3) / 1e9 / hbm, 4),
                         "frac_of_nominal_8TBs": round(stage / (ms_per_step * 1e-3) / 8e12, 4),
@@ -468,7 +477,7 @@ def source_hash(sources=None):
     return h.hexdigest()[:16]
 
 
-def workload_config(n, world, workload="model_insect", wake=False, flight=False):
+def workload_config(n, world, workload="model_insect", wake=False, flight=False, insect="model"):
     """The `config` object of both arms: the workload as the GPU arm runs it."""
     step_bytes = sum(kernel_bytes(n, 4, wake).values())
     insect = ("ellipsoid body (0.5, 0.12) + 2 flapping plates (c 0.3, R 1, 4dx thick, "
@@ -487,6 +496,9 @@ def workload_config(n, world, workload="model_insect", wake=False, flight=False)
                  "4 points deep at the x end")
     if flight:
         what += "; free flight (mass 400, J_body (2, 5, 5), g 9.81) with wing power"
+    if insect != "model":
+        what += ("; insect: thorax with head and eyes, 16-harmonic contour wings"
+                 + (", thorax on a centre-line circle of radius 1" if insect == "curved" else ""))
     return {"workload": what, "grid": list(n), "box": [4.0, 4.0, 4.0], "precision": "fp32",
             "initial": init,
             "l2": f"inputs larger than L2: {step_bytes / 1e9:.1f} GB moved per step",
@@ -506,7 +518,7 @@ def run_reference(args):
     # choose the sample grid from a timed probe step
     pick = 32
     for n in (32, 48, 64, 96, 128):
-        cfg, ins, u0 = oracle_workload(args.workload, n, args.flight)
+        cfg, ins, u0 = oracle_workload(args.workload, n, args.flight, args.insect)
         sim = oracle.Simulation(cfg, ins)
         sim.set_state(u0)
         t0 = time.perf_counter()
@@ -515,7 +527,7 @@ def run_reference(args):
         if per * (args.steps + args.warmup) > 120.0:
             break
         pick = n
-    cfg, ins, u0 = oracle_workload(args.workload, pick, args.flight)
+    cfg, ins, u0 = oracle_workload(args.workload, pick, args.flight, args.insect)
     sim = oracle.Simulation(cfg, ins)
     sim.set_state(u0)
     sim.step(args.warmup)
@@ -531,7 +543,7 @@ def run_reference(args):
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "impl": "reference",
            "config": workload_config(workload_setup(args)[0]["n"], world, args.workload, args.wake,
-                                     args.flight),
+                                     args.flight, args.insect),
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                             "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
