@@ -386,6 +386,47 @@ def test_bench_configuration_sampled(fl):
     _check_first_force_row(cfg, ins, rows[0])
 
 
+def test_turbulent_configuration_at_the_largest_size(fl):
+    """The 1024^3 FP32 turbulent-inflow workload (the largest grid, the nh = 2R^2
+    x pass, split TMA boxes, radix-16 y stages) in the benchmark's launch
+    shape: the state after set_state at sampled points against the sum of its
+    modes, the first force row's kinetic energy against its closed form, the
+    adaptive step against the CFL rule, and a finite state after three steps."""
+    import torch
+    cfg, ins = workloads.config_turbulent_insect(1024)
+    n, L = cfg["n"], cfg["L"]
+    u0 = workloads.turbulent_field(n, L, mean=cfg["u_inf"], seed=cfg["init"][1], device="cuda")
+    sim = fl.Solver(cfg, ins, precision="fp32")
+    sim.set_state(u0)
+    del u0
+    torch.cuda.empty_cache()
+    rng = np.random.default_rng(1024)
+    pts = np.column_stack([rng.integers(0, 1024, 3000) for _ in range(3)])
+    out = torch.empty((3, 1024, 1024, 1024), dtype=torch.float32, device="cuda")
+    sim.get_state_device(out)
+    idx = [torch.as_tensor(pts[:, a], device="cuda") for a in (2, 1, 0)]
+    vals = out[:, idx[0], idx[1], idx[2]].double().cpu().numpy()
+    del out, idx
+    torch.cuda.empty_cache()
+    m, a = workloads.turbulent_modes(L, seed=cfg["init"][1])
+    X = pts * (L[0] / n[0])
+    k = 2 * np.pi * m / np.asarray(L)
+    phase = np.exp(1j * (X @ k.T))                       # (points, modes)
+    exact = np.asarray(cfg["u_inf"])[:, None] + 2 * np.real(a.T @ phase.T)
+    assert np.abs(vals - exact).max() <= 2e-6
+    sim.step(1)
+    rows, _ = sim.forces()
+    vol = L[0] * L[1] * L[2]
+    ek = 0.5 * vol * (sum(c * c for c in cfg["u_inf"]) + 2 * np.sum(np.abs(a) ** 2))
+    assert abs(rows[0, 20] - ek) <= 1e-5 * ek
+    dx = L[0] / n[0]
+    assert rows[0, 1] == pytest.approx(min(0.1 * dx / rows[0, 21], cfg["eta"]), rel=1e-12)
+    sim.step(2)
+    rows2, _ = sim.forces()
+    assert rows2.shape[0] == 2 and np.isfinite(rows2).all()
+    sim.close()
+
+
 def _check_first_force_row(cfg, ins, row):
     """Force and moment of every part in the first row of the 512^3 step (the
     square x pass the benchmark times), against the oracle's mask over a
