@@ -383,7 +383,27 @@ def test_bench_configuration_sampled(fl):
     assert abs(rows[0, 20] - ek) <= 1e-5 * ek
     assert rows[0, 1] == pytest.approx(min(0.1 * dx / rows[0, 21], cfg["eta"]), rel=1e-12)
     sim.close()
-    _check_first_force_row(cfg, ins, rows[0])
+    _check_first_force_row(cfg, ins, rows[0], (176, 92, 220), (336, 420, 292),
+                           lambda pts: workloads.shear_waves(n, L, mean=cfg["u_inf"], points=pts))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_single_wing_first_row_at_256(fl, prec):
+    """The 256^3 single-wing configuration (C1: nx = 256, the nh = 2R^2 x pass
+    with R = 8) from rest: its first force row is minus the penalized solid
+    velocity, sum -chi u_s dV / C_eta and its moment about the pivot, against
+    the oracle's mask over a sub-box that holds the whole wing."""
+    cfg, ins = workloads.config_single_wing(256)
+    n = cfg["n"]
+    sim = fl.Solver(cfg, ins, precision=prec)
+    sim.set_state(np.zeros((3,) + tuple(reversed(n)), np.float32 if prec == "fp32" else np.float64))
+    sim.step(1)
+    rows, _ = sim.forces()
+    sim.close()
+    assert rows[0, 20] == 0.0
+    _check_first_force_row(cfg, ins, rows[0], (104, 116, 104), (152, 212, 152),
+                           lambda pts: np.zeros((3, len(pts))), parts=(1,),
+                           tol=1e-10 if prec == "fp64" else 2e-4)
 
 
 def test_turbulent_configuration_at_the_largest_size(fl):
@@ -427,15 +447,15 @@ def test_turbulent_configuration_at_the_largest_size(fl):
     sim.close()
 
 
-def _check_first_force_row(cfg, ins, row):
-    """Force and moment of every part in the first row of the 512^3 step (the
-    square x pass the benchmark times), against the oracle's mask over a
-    sub-box that holds the whole insect and the closed-form initial field:
+def _check_first_force_row(cfg, ins, row, lo, hi, u_at, parts=(0, 1, 2), tol=2e-4):
+    """Force and moment of the given parts in the first row of a full-size step
+    (the register-resident x pass the benchmark times), against the oracle's
+    mask over the sub-box [lo, hi) of grid indices (x, y, z) that holds the
+    whole insect and the closed-form initial field u_at(points):
     F = sum chi (u - u_s) dV / C_eta, M = sum r x chi (u - u_s) dV / C_eta
     (no unsteady correction on the first step)."""
     n, L = cfg["n"], cfg["L"]
     dx = L[0] / n[0]
-    lo, hi = (176, 92, 220), (336, 420, 292)        # grid indices, x y z
     nsub = tuple(h - l for l, h in zip(lo, hi))
     off = np.array(lo) * dx
     sub = {"n": nsub, "L": tuple(m * dx for m in nsub), "nu": cfg["nu"], "eta": cfg["eta"]}
@@ -446,19 +466,19 @@ def _check_first_force_row(cfg, ins, row):
         assert face.max() == 0.0
     z, y, x = np.meshgrid(*(np.arange(lo[a], hi[a]) for a in (2, 1, 0)), indexing="ij")
     pts = np.column_stack([x.ravel(), y.ravel(), z.ravel()])
-    u = workloads.shear_waves(n, L, mean=cfg["u_inf"], points=pts)
+    u = u_at(pts)
     X = pts.T * dx
     pen = chi.ravel() * (u - us.reshape(3, -1)) * dx ** 3 / cfg["eta"]
     fr = oracle.frames(ins, 0.0)
     refs = [np.asarray(ins["x_cntr"]), fr["pivot_g"][0], fr["pivot_g"][1]]
-    for c in range(3):
+    for c in parts:
         sel = col.ravel() == c + 1
         F = pen[:, sel].sum(axis=1)
         M = np.cross((X[:, sel] - refs[c][:, None]).T, pen[:, sel].T).sum(axis=0)
         got_F, got_M = row[2 + 6 * c: 5 + 6 * c], row[5 + 6 * c: 8 + 6 * c]
-        assert np.abs(got_F - F).max() <= 2e-4 * np.abs(F).max(), c
-        assert np.abs(got_M - M).max() <= 2e-4 * np.abs(M).max(), c
-        assert np.abs(F).max() > 1.0
+        assert np.abs(got_F - F).max() <= tol * np.abs(F).max(), c
+        assert np.abs(got_M - M).max() <= tol * np.abs(M).max(), c
+        assert np.abs(F).max() > 1e-3
 
 
 WIDE = {"x512": ((512, 16, 12), (8.0, 1.0, 0.75)), "x128": ((128, 24, 16), (4.0, 0.75, 0.5)),
