@@ -382,6 +382,25 @@ def test_bench_configuration_sampled(fl):
     ek = workloads.shear_waves_energy(L, mean=cfg["u_inf"])
     assert abs(rows[0, 20] - ek) <= 1e-5 * ek
     assert rows[0, 1] == pytest.approx(min(0.1 * dx / rows[0, 21], cfg["eta"]), rel=1e-12)
+    # properties of the stepped state at full size: solenoidal, 2/3-rule
+    # truncated, the mean held at u_inf
+    uh = sim.get_spectrum()
+    mx = np.arange(n[0] // 2 + 1)
+    my = np.fft.fftfreq(n[1], 1.0 / n[1])
+    mz = np.fft.fftfreq(n[2], 1.0 / n[2])
+    div = np.zeros(uh.shape[1:], complex)
+    for c, (m, ax) in enumerate(((mx, 2), (my, 1), (mz, 0))):
+        shape = [1, 1, 1]
+        shape[ax] = -1
+        div += (2 * np.pi / L[c]) * m.reshape(shape) * uh[c]
+    kmax = 2 * np.pi * (n[0] // 3) / L[0] * np.sqrt(3)
+    assert np.abs(div).max() <= 1e-6 * kmax * np.abs(uh).max()
+    del div
+    drop = (np.abs(mz)[:, None, None] > n[2] // 3) | (np.abs(my)[None, :, None] > n[1] // 3) | \
+           (mx[None, None, :] > n[0] // 3)
+    assert np.abs(uh[:, drop]).max() == 0.0
+    assert np.allclose(uh[:, 0, 0, 0], cfg["u_inf"], rtol=0, atol=1e-7)
+    del uh, drop
     sim.close()
     _check_first_force_row(cfg, ins, rows[0], (176, 92, 220), (336, 420, 292),
                            lambda pts: workloads.shear_waves(n, L, mean=cfg["u_inf"], points=pts))
