@@ -133,7 +133,7 @@ template <typename T, int V> struct ZLoadKz {
 // read follows the first), the side rows read back from L2.  nf = 3: the
 // velocity alone.
 template <typename T, bool TMA, bool R16>
-__global__ void __launch_bounds__(kThreadsInv, sizeof(T) == 4 ? (R16 ? 2 : 3) : 1)
+__global__ void __launch_bounds__(kThreadsInv, sizeof(T) == 4 ? 3 : 1)
 k_zinv(const cplx<T>* __restrict__ U, cplx<T>* __restrict__ W, Geom g, FftPlan plan,
        const double2* __restrict__ tw, const int* __restrict__ pos, int nf, int lgTX,
        const StepState* __restrict__ st, const __grid_constant__ CUtensorMap umap, int bh, int* err)
@@ -504,13 +504,10 @@ cudaError_t launch_zi(const void* U, void* W, const Geom& g, const FftPlan& plan
     CUtensorMap none{};
     const CUtensorMap& m = tma ? *map : none;
     const int lg = __builtin_ctz(TX);
-    if (plan_has_radix16(plan)) {
-        if (tma) k_zinv<T, true, true><<<blocks, kThreadsInv, smem, s>>>(u, w, g, plan, tw, pos, nf, lg, st, m, bh, err);
-        else k_zinv<T, false, true><<<blocks, kThreadsInv, smem, s>>>(u, w, g, plan, tw, pos, nf, lg, st, m, 0, err);
-    } else {
-        if (tma) k_zinv<T, true, false><<<blocks, kThreadsInv, smem, s>>>(u, w, g, plan, tw, pos, nf, lg, st, m, bh, err);
-        else k_zinv<T, false, false><<<blocks, kThreadsInv, smem, s>>>(u, w, g, plan, tw, pos, nf, lg, st, m, 0, err);
-    }
+    // the inverse z pass is built without radix-16 stages (its plan has none)
+    if (plan_has_radix16(plan)) return cudaErrorInvalidValue;
+    if (tma) k_zinv<T, true, false><<<blocks, kThreadsInv, smem, s>>>(u, w, g, plan, tw, pos, nf, lg, st, m, bh, err);
+    else k_zinv<T, false, false><<<blocks, kThreadsInv, smem, s>>>(u, w, g, plan, tw, pos, nf, lg, st, m, 0, err);
     return cudaGetLastError();
 }
 
@@ -639,8 +636,6 @@ cudaError_t configure_zpass()
 #define FLUSI_SMEM(fn) \
     if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
 #define FLUSI_SMEM_Z(T, R16)                  \
-    FLUSI_SMEM((k_zinv<T, false, R16>))       \
-    FLUSI_SMEM((k_zinv<T, true, R16>))        \
     FLUSI_SMEM((k_zfwd<T, false, R16>))       \
     FLUSI_SMEM((k_zfwd<T, true, R16>))
     FLUSI_SMEM_Z(float, false)
@@ -648,6 +643,10 @@ cudaError_t configure_zpass()
     FLUSI_SMEM_Z(float, true)
     FLUSI_SMEM_Z(double, true)
 #undef FLUSI_SMEM_Z
+    FLUSI_SMEM((k_zinv<float, false, false>))
+    FLUSI_SMEM((k_zinv<float, true, false>))
+    FLUSI_SMEM((k_zinv<double, false, false>))
+    FLUSI_SMEM((k_zinv<double, true, false>))
 #undef FLUSI_SMEM
     return cudaSuccess;
 }
