@@ -268,6 +268,39 @@ def test_tma_tiles_equal_copied_tiles(fl, n, prec):
     assert np.array_equal(ra, rb) and np.array_equal(ua, ub) and np.array_equal(sa, sb)
 
 
+@pytest.mark.parametrize("n", [(48, 36, 24), (96, 24, 12)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_strict_dealiasing(fl, n, prec):
+    """dealias_strict keeps |m| < n/3 (one mode fewer per axis where 3 divides
+    n): five steps with a sphere in a mean flow against the oracle with the
+    same option, and the dropped modes zero in the spectrum."""
+    L = tuple(0.125 * m for m in n)
+    cfg = {"n": n, "L": L, "nu": 0.01, "eta": 1e-2, "cfl": 0.1, "mean_mode": "fixed",
+           "u_inf": (0.3, 0.0, 0.0), "dealias_strict": 1}
+    ins = workloads.sphere(tuple(0.5 * x for x in L), 0.3 * min(L), profile="cos")
+    u0 = workloads.random_smooth_field(n, 7, mean=(0.3, 0.0, 0.0))
+    sim = fl.Solver(cfg, ins, precision=prec)
+    sim.set_state(u0)
+    sim.step(5)
+    rows, _ = sim.forces()
+    u = sim.get_state()[0]
+    uh = sim.get_spectrum()
+    sim.close()
+    ref = oracle.Simulation(cfg, ins)
+    ref.set_state(u0)
+    ref_rows = ref.step(5)
+    tol_u, tol_r = (1e-11, 1e-9) if prec == "fp64" else (2e-5, 1e-4)
+    assert rel_l2(u, ref.get_state()) <= tol_u
+    assert rows_err(rows, ref_rows) <= tol_r
+    for ax, m in ((2, np.arange(n[0] // 2 + 1)), (1, np.fft.fftfreq(n[1], 1.0 / n[1])),
+                  (0, np.fft.fftfreq(n[2], 1.0 / n[2]))):
+        nn = n[2 - ax]
+        drop = np.abs(m) >= nn / 3
+        sl = [slice(None)] * 4
+        sl[1 + ax] = drop
+        assert np.abs(uh[tuple(sl)]).max(initial=0.0) == 0.0
+
+
 def test_bounded_wait_reports_a_timeout(fl):
     """A device-side wait that runs out (an mbarrier nothing completes, the
     bounded wait of the TMA tile loads) sets FLUSI_ETIMEOUT in the status word:
