@@ -63,6 +63,8 @@ def parse():
                     help="nx,ny,nz: a reduced grid of the same box and insect (profiling)")
     ap.add_argument("--fp64-steps", type=int, default=10)
     ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default FFT plans and tiles instead of flusi_autotune's choice")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-yardstick", action="store_true",
@@ -316,6 +318,8 @@ def run_flusi(args):
     # ---- FP32, device-resident timed region
     sim = fl.Solver(cfg, ins, precision="fp32", device=local)
     sim.set_state(u0)
+    # plans and tile shapes timed on this GPU; the state is left as it was
+    tuning = sim.tuning() if args.no_autotune else sim.autotune(steps=3)
     sim.step(args.warmup)
     sim.sync()
     uuid = None
@@ -404,6 +408,7 @@ def run_flusi(args):
     if not args.no_fp64:
         sim64 = fl.Solver(cfg, ins, precision="fp64", device=local)
         sim64.set_state(u0)
+        tuning64 = sim64.tuning() if args.no_autotune else sim64.autotune(steps=1)
         sim64.step(2)
         sim64.sync()
         barrier()
@@ -419,7 +424,7 @@ def run_flusi(args):
         v64 = whole_job_rate(N, args.fp64_steps, world, ms64)
         fp64 = {"value": v64, "unit": UNIT, "ms_per_step": ms64 / args.fp64_steps,
                 "steps": args.fp64_steps, "fp32_speedup": value / v64,
-                "kernels_ms": {k: round(v, 3) for k, v in prof64.items()}}
+                "kernels_ms": {k: round(v, 3) for k, v in prof64.items()}, "tuning": tuning64}
     del u0
 
     yardstick = None
@@ -450,6 +455,7 @@ def run_flusi(args):
                         "kernel_bytes_per_step": step_bytes,
                         "kernel_bytes_frac_of_peak": round(step_bytes / (ms_per_step * 1e-3) / 1e9 / hbm, 4)},
         "kernels_ms": kernels,
+        "tuning": dict(tuning, autotuned=not args.no_autotune),
         "fp64": fp64,
         "ensemble": ensemble,
         "cufft_yardstick": yardstick,

@@ -271,6 +271,63 @@ int flusi_debug_wait_timeout(flusi_t h, double milliseconds);
 /* Kernels launched per step (for launch accounting). */
 int flusi_kernels_per_step(flusi_t h, int *count);
 
+/* ---- FFT plans and tile shapes, and their autotuner.  The paper takes its
+ * 1-D transforms from a library (Sec. 4, P3DFFT over FFTW); here each axis
+ * pass is the project's own kernel, and how a length is factored into radix
+ * stages and how many columns a y or z tile holds are choices whose best
+ * value depends on the grid and the GPU.  Every setting computes the same
+ * transforms; results differ only by rounding.
+ *
+ * Plans (y_plan, zf_plan): 0 radix 8 first, then one 4 or 2 (and 3 for each
+ * factor 3; 16 = 4 4); 1 (default) as 0, but 2^(3q+1) takes one radix-16
+ * stage in place of 4 4 or 8 2 (1024 = 16 8 8, 128 = 16 8, 16 = 16);
+ * 2 fewest stages: as 1, and 2^(3q+2) with q >= 2 takes 16 16 in place of
+ * 8 8 4 (256 = 16 16).  The inverse z pass always takes plan 0 (its kernel
+ * has no radix-16 variant).
+ * Tile columns (y_cols, z_cols): 0 (default) the widest tile that fits a
+ * block's 64 KB, else a cap on the tile's columns (x columns times z planes
+ * for y; columns of the flattened (y, x) plane for z), a power of two of at
+ * least 32 bytes of complex values (4 in FP32, 2 in FP64) and at most 256.
+ * x_kernel: 0 (default) the register-resident line kernel where one exists
+ * (nx = 128, 256, 512, 1024), 1 the shared-memory kernel of every length.
+ *
+ * flusi_get_tuning fills every field, including the read-only ones: the
+ * radices each pass takes (0-terminated), the columns a tile takes, and
+ * whether the x pass runs the register-resident kernel.
+ * flusi_set_tuning takes the five settings (the rest is ignored); any
+ * other value is FLUSI_EINVAL with nothing changed.  On a bound handle it
+ * waits for the handle's stream, uploads the new digit-reversal tables and
+ * rebuilds the TMA descriptors; the state is kept.  No device work on an
+ * unbound handle.
+ *
+ * flusi_autotune: on a bound handle with a state, coordinate descent over
+ * the settings (y_plan, y_cols, zf_plan, z_cols, x_kernel, in that order):
+ * each candidate runs one untimed step and `steps` (1..1000) timed steps,
+ * and is scored by the CUDA-event time of the kernels it changes
+ * (flusi_profile_step's per-kernel times); the best is kept.  The state,
+ * time, step count and free-flight body state are saved before and restored
+ * after, as by flusi_save/flusi_load, so the run continues where it was;
+ * undrained force rows are dropped, as by flusi_load.  cache_path (NULL: no
+ * cache) names a text file of lines "key y_plan zf_plan y_cols z_cols
+ * x_kernel", key = GPU name (spaces as '_'), SM count, grid, precision,
+ * time scheme and wake terms: a line with this handle's key is applied
+ * without timing; otherwise the result is appended (a file that cannot be
+ * written is FLUSI_EINVAL after the tuning is applied).  *out (may be
+ * NULL) receives the chosen settings as flusi_get_tuning does.
+ * Synchronizes. */
+#define FLUSI_MAX_STAGES 8
+typedef struct flusi_tuning {
+    int y_plan, zf_plan;       /* 0, 1 (default) or 2                      */
+    int y_cols, z_cols;        /* 0 (default) or a power of two cap        */
+    int x_kernel;              /* 0 (default) or 1                         */
+    /* read-only, filled by flusi_get_tuning */
+    int y_radix[FLUSI_MAX_STAGES], zf_radix[FLUSI_MAX_STAGES], zi_radix[FLUSI_MAX_STAGES];
+    int y_tile_cols, z_tile_cols, x_line_kernel;
+} flusi_tuning;
+int flusi_get_tuning(flusi_t h, flusi_tuning *out);
+int flusi_set_tuning(flusi_t h, const flusi_tuning *tuning);
+int flusi_autotune(flusi_t h, int steps, const char *cache_path, flusi_tuning *out);
+
 /* Largest grid (points) and output length of flusi_penalization_sums_noalloc. */
 #define FLUSI_NOALLOC_MAX_POINTS (1024LL * 1024LL * 1024LL)
 #define FLUSI_NOALLOC_SUMS 38

@@ -40,6 +40,26 @@ class Options(C.Structure):
                 ("time_scheme", C.c_int), ("use_tma", C.c_int)]
 
 
+MAX_STAGES = 8
+TUNING_SETTINGS = ("y_plan", "zf_plan", "y_cols", "z_cols", "x_kernel")
+
+
+class Tuning(C.Structure):
+    _fields_ = [("y_plan", C.c_int), ("zf_plan", C.c_int), ("y_cols", C.c_int), ("z_cols", C.c_int),
+                ("x_kernel", C.c_int),
+                ("y_radix", C.c_int * MAX_STAGES), ("zf_radix", C.c_int * MAX_STAGES),
+                ("zi_radix", C.c_int * MAX_STAGES),
+                ("y_tile_cols", C.c_int), ("z_tile_cols", C.c_int), ("x_line_kernel", C.c_int)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k in TUNING_SETTINGS}
+        for k in ("y_radix", "zf_radix", "zi_radix"):
+            d[k] = [r for r in getattr(self, k) if r]
+        for k in ("y_tile_cols", "z_tile_cols", "x_line_kernel"):
+            d[k] = getattr(self, k)
+        return d
+
+
 _F = C.c_double * MAX_FOURIER
 
 
@@ -94,6 +114,9 @@ def _load():
         "flusi_debug_fields": ([h, vp], ip),
         "flusi_profile_step": ([h, ip, dp, C.POINTER(C.c_char_p), C.POINTER(C.c_int)], ip),
         "flusi_kernels_per_step": ([h, C.POINTER(C.c_int)], ip),
+        "flusi_get_tuning": ([h, C.POINTER(Tuning)], ip),
+        "flusi_set_tuning": ([h, C.POINTER(Tuning)], ip),
+        "flusi_autotune": ([h, ip, C.c_char_p, C.POINTER(Tuning)], ip),
         "flusi_penalization_sums_noalloc": ([ip, ip, ip, dp, C.c_double, C.POINTER(Insect), C.c_double,
                                              vp, dp, vp], ip),
         "flusi_checkpoint_bytes": ([h, C.POINTER(C.c_size_t)], ip),
@@ -219,6 +242,32 @@ def flusi_kernels_per_step(h):
     c = C.c_int()
     _check(h, lib.flusi_kernels_per_step(h, C.byref(c)))
     return c.value
+
+
+def flusi_get_tuning(h):
+    """Plans, tile caps and x kernel of the handle, with what the passes take."""
+    t = Tuning()
+    _check(h, lib.flusi_get_tuning(h, C.byref(t)))
+    return t.as_dict()
+
+
+def flusi_set_tuning(h, **settings):
+    """Change some of y_plan, zf_plan, y_cols, z_cols, x_kernel; the others keep
+    their current values."""
+    t = Tuning()
+    _check(h, lib.flusi_get_tuning(h, C.byref(t)))
+    for k, v in settings.items():
+        if k not in TUNING_SETTINGS:
+            raise ValueError(f"unknown tuning setting {k!r}")
+        setattr(t, k, int(v))
+    return _check(h, lib.flusi_set_tuning(h, C.byref(t)))
+
+
+def flusi_autotune(h, steps=5, cache_path=None):
+    t = Tuning()
+    path = os.fsencode(cache_path) if cache_path is not None else None
+    _check(h, lib.flusi_autotune(h, int(steps), path, C.byref(t)))
+    return t.as_dict()
 
 
 NOALLOC_SUMS = 38
@@ -452,6 +501,17 @@ class Solver:
 
     def profile(self, n=3):
         return flusi_profile_step(self.h, n)
+
+    def tuning(self):
+        return flusi_get_tuning(self.h)
+
+    def set_tuning(self, **settings):
+        flusi_set_tuning(self.h, **settings)
+
+    def autotune(self, steps=5, cache_path=None):
+        """Time the plan, tile and x-kernel choices and keep the fastest
+        (flusi_autotune); the state is left as it was."""
+        return flusi_autotune(self.h, steps, cache_path)
 
     def save(self):
         """Checkpoint for an exact restart (flusi_save)."""

@@ -75,6 +75,9 @@ struct Geom {
     double Lx, Ly, Lz;
     double dx, dy, dz;
     double nu, eta;
+    // tile and kernel choices (0: defaults): caps on the columns of a y and a
+    // z tile, and the shared-memory x kernel in place of the line kernel
+    int ycols, zcols, xgeneric;
 };
 
 // Per-step geometry of the insect, written by the kinematics kernel (FP64).

@@ -8,9 +8,11 @@
 #include <cstddef>
 #include <cstdio>
 #include <cstring>
+#include <fstream>
 #include <initializer_list>
 #include <mutex>
 #include <new>
+#include <sstream>
 #include <string>
 #include <vector>
 
@@ -23,6 +25,7 @@ struct flusi_s {
     int nx = 0, ny = 0, nz = 0, prec = 0;
     double L[3] = {0, 0, 0}, nu = 0, eta = 0;
     flusi_options opt{};
+    flusi_tuning tune{};           // plans, tile caps and x kernel (flusi_set_tuning)
     flusi_insect ins{};
     int have_ins = 0;
     Geom g{};
@@ -92,10 +95,16 @@ bool smooth_size(int n)
 // Radix order: 3s first (their stages divide), then 8s, then a 4 or 4*4 or 2.
 // `tws` is the stride of the twiddle table the transform reads (its table has
 // n*tws entries), folded into the per-stage twiddle steps.
-// radix16: 2^a with a = 3q + 1 (q >= 1) takes one radix-16 stage in place of
-// 8 x 2 (e.g. 1024 = 16 8 8 instead of 8 8 4 4): one pass through shared
-// memory fewer, for the y and z passes whose kernels have radix-16 variants.
-FftPlan make_plan(int n, int tws, bool radix16 = false)
+// Radix stages of a length n = 2^a 3^b: the factors 3 first, then (a = 3q + r)
+// mode 0: 8^q and one 4 (r = 2) or 2 (r = 1), except that 2^(3q+1) with
+//   q >= 1 ends in 4 4 (16 = 4 4, 128 = 8 4 4, 1024 = 8 8 4 4);
+// mode 1: as 0, but 2^(3q+1) with q >= 1 takes one radix-16 stage in place of
+//   that 4 4 (16, 16 8, 16 8 8): one pass through shared memory fewer;
+// mode 2: as 1, and 2^(3q+2) with q >= 2 takes 16 16 in place of 8 8 4
+//   (256 = 16 16).
+// Modes 1 and 2 are for the y and forward z passes, whose kernels have
+// radix-16 variants.
+FftPlan make_plan(int n, int tws, int mode = 0)
 {
     FftPlan p{};
     p.n = n;
@@ -104,9 +113,16 @@ FftPlan make_plan(int n, int tws, bool radix16 = false)
     while (m % 3 == 0) { r.push_back(3); m /= 3; }
     int a = 0;
     while (m % 2 == 0) { ++a; m /= 2; }
-    int q = a / 3, rem = a % 3;
-    if (rem == 1 && q >= 1) { q -= 1; rem = radix16 ? 16 : 4; }
-    if (rem == 16) r.push_back(16);
+    int q = a / 3, rem = a % 3, n16 = 0;
+    if (rem == 1 && q >= 1) {
+        q -= 1;
+        if (mode >= 1) { n16 = 1; rem = 0; } else rem = 4;
+    } else if (rem == 2 && q >= 2 && mode == 2) {
+        q -= 2;
+        n16 = 2;
+        rem = 0;
+    }
+    for (int i = 0; i < n16; ++i) r.push_back(16);
     for (int i = 0; i < q; ++i) r.push_back(8);
     if (rem == 2) r.push_back(4);
     if (rem == 1) r.push_back(2);
@@ -206,11 +222,14 @@ void layout(flusi_t h)
     h->orows = o; o = align256(o + sizeof(double) * kRowCols * h->opt.force_ring);
     h->total = o;
     h->px = make_plan(h->nx / 2, 2);
-    h->py = make_plan(h->ny, 1, true);
-    h->pz = make_plan(h->nz, 1, true);
+    h->py = make_plan(h->ny, 1, h->tune.y_plan);
+    h->pz = make_plan(h->nz, 1, h->tune.zf_plan);
     // the inverse z pass holds more live values per thread (the curl's side
     // rows); a radix-16 stage there costs it a block per SM, more than it saves
-    h->pzi = make_plan(h->nz, 1, false);
+    h->pzi = make_plan(h->nz, 1, 0);
+    g.ycols = h->tune.y_cols;
+    g.zcols = h->tune.z_cols;
+    g.xgeneric = h->tune.x_kernel;
 }
 
 template <typename P> P* at(flusi_t h, size_t off) { return reinterpret_cast<P*>(h->ws + off); }
@@ -510,6 +529,7 @@ int flusi_create(int nx, int ny, int nz, const double L[3], double nu, double et
     h->nu = nu;
     h->eta = eta;
     flusi_default_options(&h->opt);
+    h->tune.y_plan = h->tune.zf_plan = 1;
     layout(h);
     *out = h;
     return FLUSI_OK;
@@ -956,6 +976,222 @@ int flusi_kernels_per_step(flusi_t h, int* count)
 {
     if (!h || !count) return FLUSI_EINVAL;
     *count = step_kernels(h);
+    return FLUSI_OK;
+}
+
+// ---------------------------------------------------------------- tuning
+
+namespace {
+
+int tuning_error(flusi_t h, const flusi_tuning& t)
+{
+    const int cmin = h->prec == FLUSI_FP64 ? 2 : 4;   // 32 bytes of complex values
+    auto cols_ok = [&](int c) { return c == 0 || (c >= cmin && c <= 256 && (c & (c - 1)) == 0); };
+    if (t.y_plan < 0 || t.y_plan > 2 || t.zf_plan < 0 || t.zf_plan > 2)
+        return fail(h, FLUSI_EINVAL, "y_plan and zf_plan must be 0, 1 or 2");
+    if (!cols_ok(t.y_cols) || !cols_ok(t.z_cols))
+        return fail(h, FLUSI_EINVAL, "y_cols and z_cols must be 0 or a power of two in [32 bytes, 256]");
+    if (t.x_kernel != 0 && t.x_kernel != 1) return fail(h, FLUSI_EINVAL, "x_kernel must be 0 or 1");
+    return FLUSI_OK;
+}
+
+void radices(const FftPlan& p, int* out)
+{
+    for (int s = 0; s < FLUSI_MAX_STAGES; ++s) out[s] = s < p.nst ? p.radix[s] : 0;
+}
+
+// Sum of the mean per-kernel times (ms) of the kernels whose names, stage
+// suffix removed, are in `names`, over `steps` un-captured steps after one
+// untimed step.
+int time_kernels(flusi_t h, int steps, const char* const names[2], double* ms_out)
+{
+    double ms[FLUSI_PROFILE_MAX];
+    const char* nm[FLUSI_PROFILE_MAX];
+    int nk = 0;
+    int rc = flusi_profile_step(h, 1, ms, nm, &nk);
+    if (rc) return rc;
+    rc = flusi_profile_step(h, steps, ms, nm, &nk);
+    if (rc) return rc;
+    double sum = 0;
+    for (int k = 0; k < nk; ++k) {
+        const std::string base = std::string(nm[k]).substr(0, std::string(nm[k]).find('.'));
+        for (int i = 0; i < 2; ++i)
+            if (names[i] && base == names[i]) sum += ms[k];
+    }
+    *ms_out = sum;
+    return FLUSI_OK;
+}
+
+std::string tuning_key(flusi_t h)
+{
+    int dev = 0;
+    cudaDeviceProp prop{};
+    cudaGetDevice(&dev);
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) cudaGetLastError();
+    std::string name = prop.name;
+    for (char& c : name)
+        if (c == ' ' || c == '\t') c = '_';
+    const bool wake = h->opt.sponge_c > 0 || h->opt.layer_width[0] > 0 || h->opt.layer_width[1] > 0 ||
+                      h->opt.layer_width[2] > 0;
+    char buf[256];
+    std::snprintf(buf, sizeof buf, "%s|%d|%dx%dx%d|%s|%s|%s|d%d", name.empty() ? "gpu" : name.c_str(),
+                  prop.multiProcessorCount, h->nx, h->ny, h->nz, h->prec == FLUSI_FP64 ? "fp64" : "fp32",
+                  is_rk4(h) ? "rk4" : "ab2", wake ? "wake" : "nowake", h->opt.dealias_strict);
+    return buf;
+}
+
+// the last line of the cache with this key, if any
+bool cache_lookup(const char* path, const std::string& key, flusi_tuning* t)
+{
+    std::ifstream f(path);
+    if (!f) return false;
+    std::string line;
+    bool found = false;
+    while (std::getline(f, line)) {
+        std::istringstream in(line);
+        std::string k;
+        flusi_tuning c{};
+        if (!(in >> k >> c.y_plan >> c.zf_plan >> c.y_cols >> c.z_cols >> c.x_kernel)) continue;
+        if (k == key) {
+            *t = c;
+            found = true;
+        }
+    }
+    return found;
+}
+
+}  // namespace
+
+int flusi_get_tuning(flusi_t h, flusi_tuning* out)
+{
+    if (!h || !out) return fail(h, FLUSI_EINVAL, "NULL argument");
+    *out = h->tune;
+    radices(h->py, out->y_radix);
+    radices(h->pz, out->zf_radix);
+    radices(h->pzi, out->zi_radix);
+    const int fp64 = h->prec == FLUSI_FP64;
+    out->y_tile_cols = ypass_tile_cols(fp64, h->g);
+    out->z_tile_cols = zpass_tile_cols(fp64, h->g);
+    out->x_line_kernel = xpass_fuses_sponge(fp64, h->g);
+    return FLUSI_OK;
+}
+
+int flusi_set_tuning(flusi_t h, const flusi_tuning* t)
+{
+    if (!h || !t) return fail(h, FLUSI_EINVAL, "NULL argument");
+    int rc = tuning_error(h, *t);
+    if (rc) return rc;
+    if (h->bound) CK(cudaStreamSynchronize(h->stream), "wait before retuning");
+    h->tune = flusi_tuning{};
+    h->tune.y_plan = t->y_plan;
+    h->tune.zf_plan = t->zf_plan;
+    h->tune.y_cols = t->y_cols;
+    h->tune.z_cols = t->z_cols;
+    h->tune.x_kernel = t->x_kernel;
+    layout(h);
+    drop_graph(h);
+    if (!h->bound) return FLUSI_OK;
+    const auto py = digit_reversal(h->py), pz = digit_reversal(h->pz);
+    CK(cudaMemcpyAsync(h->ws + h->opy, py.data(), sizeof(int) * py.size(), cudaMemcpyHostToDevice, h->stream),
+       "digit reversal");
+    CK(cudaMemcpyAsync(h->ws + h->opz, pz.data(), sizeof(int) * pz.size(), cudaMemcpyHostToDevice, h->stream),
+       "digit reversal");
+    CK(cudaStreamSynchronize(h->stream), "retune tables");
+    h->xgrid = std::min(xpass_grid(h->prec == FLUSI_FP64, h->g), h->part_cap);
+    return prepare_maps(h);
+}
+
+int flusi_autotune(flusi_t h, int steps, const char* cache_path, flusi_tuning* out)
+{
+    int rc = check_ready(h, true);
+    if (rc) return rc;
+    if (steps < 1 || steps > 1000) return fail(h, FLUSI_EINVAL, "steps must lie in [1, 1000]");
+    if (h->poisoned) return fail(h, FLUSI_ESTATE, "a device error poisoned the handle");
+    const std::string key = tuning_key(h);
+    flusi_tuning best{};
+    if (cache_path && cache_lookup(cache_path, key, &best)) {
+        rc = flusi_set_tuning(h, &best);
+        if (rc) return rc;
+        return out ? flusi_get_tuning(h, out) : FLUSI_OK;
+    }
+    size_t bytes = 0;
+    flusi_checkpoint_bytes(h, &bytes);
+    std::vector<char> saved(bytes);
+    rc = flusi_save(h, saved.data(), bytes);
+    if (rc) return rc;
+    flusi_get_tuning(h, &best);
+    struct Knob {
+        int flusi_tuning::*field;
+        const char* kernels[2];
+    };
+    const Knob knobs[] = {{&flusi_tuning::y_plan, {"yinv", "yfwd"}},
+                          {&flusi_tuning::y_cols, {"yinv", "yfwd"}},
+                          {&flusi_tuning::zf_plan, {"zfwd", nullptr}},
+                          {&flusi_tuning::z_cols, {"zinv_curl", "zfwd"}},
+                          {&flusi_tuning::x_kernel, {"xpass_phys", "sponge_x"}}};
+    for (const Knob& kb : knobs) {
+        // candidate values: the plans, or the default tile and two halvings
+        std::vector<int> vals;
+        if (kb.field == &flusi_tuning::y_plan || kb.field == &flusi_tuning::zf_plan) vals = {1, 0, 2};
+        else if (kb.field == &flusi_tuning::x_kernel) vals = {0, 1};
+        else {
+            flusi_tuning d = best;
+            d.*kb.field = 0;
+            rc = flusi_set_tuning(h, &d);
+            if (rc) break;
+            flusi_tuning got{};
+            flusi_get_tuning(h, &got);
+            const int c0 = kb.field == &flusi_tuning::y_cols ? got.y_tile_cols : got.z_tile_cols;
+            vals = {0};
+            const int cmin = h->prec == FLUSI_FP64 ? 2 : 4;
+            for (int c = c0 / 2; c >= cmin && c >= c0 / 4; c /= 2) vals.push_back(c);
+        }
+        std::vector<std::string> seen;
+        double best_ms = 0;
+        int best_v = best.*kb.field, timed = 0;
+        for (int v : vals) {
+            flusi_tuning t = best;
+            t.*kb.field = v;
+            rc = flusi_set_tuning(h, &t);
+            if (rc) break;
+            // settings that give the same plans, tiles and kernels are timed once
+            flusi_tuning got{};
+            flusi_get_tuning(h, &got);
+            std::string sig;
+            for (int i = 0; i < FLUSI_MAX_STAGES; ++i)
+                sig += std::to_string(got.y_radix[i]) + "," + std::to_string(got.zf_radix[i]) + ",";
+            sig += std::to_string(got.y_tile_cols) + "," + std::to_string(got.z_tile_cols) + "," +
+                   std::to_string(got.x_line_kernel);
+            if (std::find(seen.begin(), seen.end(), sig) != seen.end()) continue;
+            seen.push_back(sig);
+            double ms = 0;
+            rc = time_kernels(h, steps, kb.kernels, &ms);
+            if (rc) break;
+            if (!timed || ms < best_ms) {
+                best_ms = ms;
+                best_v = v;
+            }
+            timed = 1;
+        }
+        if (rc) break;
+        best.*kb.field = best_v;
+    }
+    if (rc) {   // restore the state; the error stays the result
+        const std::string msg = h->err;
+        if (flusi_load(h, saved.data(), bytes) == FLUSI_OK) h->err = msg;
+        return rc;
+    }
+    rc = flusi_set_tuning(h, &best);
+    if (rc) return rc;
+    rc = flusi_load(h, saved.data(), bytes);
+    if (rc) return rc;
+    if (out) flusi_get_tuning(h, out);
+    if (cache_path) {
+        std::ofstream f(cache_path, std::ios::app);
+        f << key << ' ' << best.y_plan << ' ' << best.zf_plan << ' ' << best.y_cols << ' ' << best.z_cols << ' '
+          << best.x_kernel << '\n';
+        if (!f) return fail(h, FLUSI_EINVAL, "cannot append to the tuning cache");
+    }
     return FLUSI_OK;
 }
 

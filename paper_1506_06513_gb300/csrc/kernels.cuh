@@ -58,6 +58,9 @@ struct ZMaps {
     int u_bh = 0, ut_bh = 0, w_bh = 0;
 };
 cudaError_t prepare_zmaps(int fp64, void* U, void* Ut, void* W, const Geom& g, ZMaps* maps);
+// columns of a y tile and of a z tile for this grid and its tile caps
+int ypass_tile_cols(int fp64, const Geom& g);
+int zpass_tile_cols(int fp64, const Geom& g);
 cudaError_t launch_zinv(int fp64, const void* U, void* W, const Geom& g, const FftPlan& plan,
                         const double2* tw, const int* pos, int nf, const StepState* st,
                         const CUtensorMap* map, int bh, int* err, cudaStream_t s);

@@ -1134,6 +1134,7 @@ void launch_sq(bool layer, bool sponge, cplx<T>* w, const Geom& g, const double2
 // or 2), or 0 for the generic one
 template <typename T> int sq_kind(const Geom& g)
 {
+    if (g.xgeneric) return 0;
     switch (g.nx) {
     case 512: return 161;
     case 128: return 81;

@@ -12,6 +12,8 @@
 // last).
 //   inverse: rows j < My hold the kept y-modes 0..Ky, -Ky..-1 -> ny grid rows
 //   forward: ny grid rows -> the My kept y-modes (2/3 rule, pruned output)
+#include <algorithm>
+
 #include "fft.cuh"
 #include "kernels.cuh"
 
@@ -143,10 +145,11 @@ template <typename T> YTile y_tile(const Geom& g, int ncomp)
 {
     YTile t;
     const int cap = tile_elems<T>();
-    int TX = sizeof(T) == 4 ? 16 : 8;               // 128-byte runs
-    while (TX > 1 && g.ny * TX > cap) TX >>= 1;
+    const int cmax = g.ycols > 0 ? g.ycols : kThreads;   // columns per tile
+    int TX = sizeof(T) == 4 ? 16 : 8;                     // 128-byte runs
+    while (TX > 1 && (g.ny * TX > cap || TX > cmax)) TX >>= 1;
     int NP = 1;
-    while (2 * NP * TX * g.ny <= cap && 2 * NP * TX <= kThreads && 2 * NP <= g.nz) NP *= 2;
+    while (2 * NP * TX * g.ny <= cap && 2 * NP * TX <= std::min(kThreads, cmax) && 2 * NP <= g.nz) NP *= 2;
     t.lgTX = __builtin_ctz(TX);
     t.lgNP = __builtin_ctz(NP);
     t.blocks = ceil_div(g.Mxp, TX) * ceil_div(g.nz, NP) * ncomp;
@@ -240,6 +243,12 @@ TensorMapEncoder tensor_map_encoder()
         return reinterpret_cast<TensorMapEncoder>(fn);
     }();
     return enc;
+}
+
+int ypass_tile_cols(int fp64, const Geom& g)
+{
+    const YTile t = fp64 ? y_tile<double>(g, 1) : y_tile<float>(g, 1);
+    return 1 << (t.lgTX + t.lgNP);
 }
 
 cudaError_t prepare_ymaps(int fp64, void* W, const Geom& g, YMaps* maps)

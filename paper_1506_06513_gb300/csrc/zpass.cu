@@ -483,9 +483,10 @@ k_zupdate(const cplx<T>* __restrict__ Wn, cplx<T>* __restrict__ U, cplx<T>* __re
 
 template <typename T> int zinv_tx(const Geom& g)
 {
+    const int cmax = g.zcols > 0 ? g.zcols : 64;   // columns per tile
     int TX = sizeof(T) == 4 ? 16 : 8;
-    while (TX > 1 && g.nz * TX > cap_zi<T>()) TX >>= 1;
-    while (2 * TX * g.nz <= cap_zi<T>() && 2 * TX <= 64) TX *= 2;
+    while (TX > 1 && (g.nz * TX > cap_zi<T>() || TX > cmax)) TX >>= 1;
+    while (2 * TX * g.nz <= cap_zi<T>() && 2 * TX <= cmax) TX *= 2;
     return TX;
 }
 
@@ -600,6 +601,8 @@ cudaError_t launch_zu(int mode, const void* Nh, void* U, void* H, const Geom& g,
 }
 
 }  // namespace
+
+int zpass_tile_cols(int fp64, const Geom& g) { return fp64 ? zinv_tx<double>(g) : zinv_tx<float>(g); }
 
 cudaError_t prepare_zmaps(int fp64, void* U, void* Ut, void* W, const Geom& g, ZMaps* maps)
 {

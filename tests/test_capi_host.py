@@ -171,3 +171,90 @@ def test_kernels_per_step(fl):
     with pytest.raises(fl.FlusiError):
         fl.flusi_set_options(h, bad)
     fl.flusi_destroy(h)
+
+
+def _prod(rs):
+    p = 1
+    for r in rs:
+        p *= r
+    return p
+
+
+@pytest.mark.parametrize("n", [16, 48, 96, 128, 192, 256, 384, 512, 768, 1024])
+def test_radix_plans(fl, n):
+    """The three plan modes of the y and forward z passes: every plan
+    factors n; mode 1 differs from mode 0 only for 2^(3q+1) (one 16 for 4 4),
+    mode 2 from mode 1 only for 2^(3q+2) with q >= 2 (16 16 for 8 8 4); the
+    inverse z pass keeps mode 0."""
+    h = fl.flusi_create((16, n, n), (1.0, 1.0, 1.0), 0.1, 1e-2, fl.FLUSI_FP32)
+    plans = {}
+    for mode in (0, 1, 2):
+        fl.flusi_set_tuning(h, y_plan=mode, zf_plan=mode)
+        t = fl.flusi_get_tuning(h)
+        assert t["y_radix"] == t["zf_radix"]
+        assert _prod(t["y_radix"]) == n and _prod(t["zi_radix"]) == n
+        plans[mode] = t["y_radix"]
+        zi = t["zi_radix"]
+    fl.flusi_destroy(h)
+    b = 0
+    while n % 3 ** (b + 1) == 0:
+        b += 1
+    a = (n // 3 ** b).bit_length() - 1          # n = 2^a 3^b
+    assert zi == plans[0] and 16 not in plans[0]
+    assert all(r in (2, 3, 4, 8) for r in plans[0])
+    if a % 3 == 1 and a >= 4:
+        assert plans[1].count(16) == 1 and len(plans[1]) == len(plans[0]) - 1
+    else:
+        assert plans[1] == plans[0]
+    if a % 3 == 2 and a >= 8:
+        assert plans[2].count(16) == 2 and len(plans[2]) == len(plans[0]) - 1
+    else:
+        assert plans[2] == plans[1]
+    for p in plans.values():                      # the factors 3 come first
+        assert p[:b] == [3] * b and 3 not in p[b:]
+
+
+def test_named_plans(fl):
+    h = fl.flusi_create((16, 256, 1024), (1.0, 1.0, 1.0), 0.1, 1e-2, fl.FLUSI_FP64)
+    t = fl.flusi_get_tuning(h)
+    assert (t["y_radix"], t["zf_radix"], t["zi_radix"]) == ([8, 8, 4], [16, 8, 8], [8, 8, 4, 4])
+    fl.flusi_set_tuning(h, y_plan=2, zf_plan=0)
+    t = fl.flusi_get_tuning(h)
+    assert (t["y_radix"], t["zf_radix"]) == ([16, 16], [8, 8, 4, 4])
+    fl.flusi_destroy(h)
+
+
+def test_tuning_is_validated(fl):
+    """Bad settings are FLUSI_EINVAL and leave the handle's tuning unchanged;
+    tile caps bound the tiles the passes take."""
+    h = fl.flusi_create((512, 64, 64), (1.0, 1.0, 1.0), 0.1, 1e-2, fl.FLUSI_FP32)
+    before = fl.flusi_get_tuning(h)
+    assert before["y_plan"] == 1 and before["zf_plan"] == 1 and before["x_line_kernel"] == 1
+    for bad in ({"y_plan": 3}, {"zf_plan": -1}, {"y_cols": 3}, {"y_cols": 2}, {"z_cols": 512},
+                {"z_cols": -4}, {"x_kernel": 2}):
+        with pytest.raises(fl.FlusiError) as e:
+            fl.flusi_set_tuning(h, **bad)
+        assert e.value.code == fl.FLUSI_EINVAL
+        assert fl.flusi_get_tuning(h) == before
+    with pytest.raises(ValueError):
+        fl.flusi_set_tuning(h, y_radix=4)
+    for cap in (4, 8, 16):
+        fl.flusi_set_tuning(h, y_cols=cap, z_cols=cap)
+        t = fl.flusi_get_tuning(h)
+        assert t["y_tile_cols"] <= cap and t["z_tile_cols"] <= cap
+    fl.flusi_set_tuning(h, x_kernel=1)
+    assert fl.flusi_get_tuning(h)["x_line_kernel"] == 0
+    fl.flusi_destroy(h)
+    h = fl.flusi_create((64, 64, 64), (1.0, 1.0, 1.0), 0.1, 1e-2, fl.FLUSI_FP64)
+    fl.flusi_set_tuning(h, y_cols=2, z_cols=2)   # 32 bytes of FP64 complex values
+    t = fl.flusi_get_tuning(h)
+    assert t["y_tile_cols"] == 2 and t["z_tile_cols"] == 2 and t["x_line_kernel"] == 0
+    fl.flusi_destroy(h)
+
+
+def test_autotune_needs_a_bound_handle(fl):
+    h = fl.flusi_create((32, 32, 32), (1.0, 1.0, 1.0), 0.1, 1e-2, fl.FLUSI_FP32)
+    with pytest.raises(fl.FlusiError) as e:
+        fl.flusi_autotune(h, 2)
+    assert e.value.code == fl.FLUSI_ESTATE
+    fl.flusi_destroy(h)
