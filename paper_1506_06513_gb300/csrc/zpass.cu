@@ -52,14 +52,68 @@ __device__ __forceinline__ void st_row_cs(cplx<T>* p, const cplx<T>* o)
     }
 }
 
+// L2 eviction policies of the inverse pass: a velocity component is read
+// twice by the same block with one transform between, and the transformed
+// u_z and u_x are read back as side rows a phase or two after they are
+// written, so those lines are kept (evict_last) until their last use, which
+// marks them evict_first.
+constexpr int kZinvHints = 2;   // 0 none, 1 the velocity loads, 2 also the side rows
+
+__device__ __forceinline__ unsigned long long l2_evict_last()
+{
+    unsigned long long p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ unsigned long long l2_evict_first()
+{
+    unsigned long long p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+// tma_load_3d with an L2 eviction policy for the lines it reads
+__device__ __forceinline__ void tma_load_3d_hint(void* dst, const void* map, int c0, int c1, int c2,
+                                                 unsigned long long* bar, unsigned long long policy)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%2, %3, %4}], [%5], %6;\n" ::"r"(smem_u32(dst)),
+        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar)), "l"(policy)
+        : "memory");
+}
+
+template <typename T, int V>
+__device__ __forceinline__ void st_row_hint(cplx<T>* p, const cplx<T>* o, unsigned long long pol)
+{
+    if constexpr (V % 2 == 0 && sizeof(T) == 4) {
+#pragma unroll
+        for (int c = 0; c < V; c += 2)
+            asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p + c), "f"(o[c].x),
+                         "f"(o[c].y), "f"(o[c + 1].x), "f"(o[c + 1].y), "l"(pol)
+                         : "memory");
+    } else {
+#pragma unroll
+        for (int c = 0; c < V; ++c)
+            asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1, %2}, %3;" ::"l"(p + c), "d"(double(o[c].x)),
+                         "d"(double(o[c].y)), "l"(pol)
+                         : "memory");
+    }
+}
+
 // Stores of k_zinv.  Plain: the transformed column to `out`.
 template <typename T, int V> struct ZStore {
     cplx<T>* out;
     size_t plane;
     bool ok;
+    bool keep = false;                 // the lines are read back later (evict_last)
+    unsigned long long pol = 0;
     __device__ __forceinline__ void operator()(int z, const cplx<T>* v) const
     {
-        if (ok) st_row<T, V>(out + (size_t)z * plane, v);
+        if (!ok) return;
+        if (keep) st_row_hint<T, V>(out + (size_t)z * plane, v, pol);
+        else st_row<T, V>(out + (size_t)z * plane, v);
     }
 };
 
@@ -75,6 +129,8 @@ template <typename T, int V> struct ZCurlStore {
     size_t plane;
     T cv[V], ca[V];
     bool ok;
+    bool last = false;                 // the side rows' last use (evict_first)
+    unsigned long long pol = 0;
     __device__ __forceinline__ void aux(int z, cplx<T>* a) const
     {
         if (!ok) {
@@ -83,6 +139,29 @@ template <typename T, int V> struct ZCurlStore {
             return;
         }
         const cplx<T>* p = side + (size_t)z * plane;
+        if (last) {
+            if constexpr (sizeof(T) == 4 && V % 2 == 0) {
+#pragma unroll
+                for (int c = 0; c < V; c += 2) {
+                    float4 q;
+                    asm volatile("ld.global.cg.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                                 : "=f"(q.x), "=f"(q.y), "=f"(q.z), "=f"(q.w)
+                                 : "l"(p + c), "l"(pol));
+                    a[c] = mkc<T>(q.x, q.y);
+                    a[c + 1] = mkc<T>(q.z, q.w);
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < V; ++c) {
+                    double qx, qy;
+                    asm volatile("ld.global.cg.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;"
+                                 : "=d"(qx), "=d"(qy)
+                                 : "l"(p + c), "l"(pol));
+                    a[c] = mkc<T>(T(qx), T(qy));
+                }
+            }
+            return;
+        }
         if constexpr (sizeof(T) == 4 && V % 2 == 0) {
 #pragma unroll
             for (int c = 0; c < V; c += 2) {
@@ -180,7 +259,8 @@ k_zinv(const cplx<T>* __restrict__ U, cplx<T>* __restrict__ W, Geom g, FftPlan p
     // 0..Kz to rows 0..Kz, Kz..2Kz to rows nz-Kz-1..nz-1, the duplicate row
     // cleared with the dropped modes) or by 16-byte asynchronous copies.
     // false: a TMA wait gave up (status set; the block must leave).
-    auto stage_in = [&](int comp) -> bool {
+    // hint: 0 none, 1 keep the lines for a second read, 2 their last read
+    auto stage_in = [&](int comp, int hint) -> bool {
         if constexpr (TMA) {
             if (threadIdx.x == 0) {
                 // earlier generic writes to buf before the asynchronous proxy's
@@ -188,10 +268,19 @@ k_zinv(const cplx<T>* __restrict__ U, cplx<T>* __restrict__ W, Geom g, FftPlan p
                 const unsigned box = (unsigned)(((size_t)bh << lgTX) * sizeof(cplx<T>));
                 const int kb = (Kz + 1) / bh;   // boxes per part
                 mbar_expect_tx(&bar, 2 * kb * box);
-                for (int b = 0; b < kb; ++b) {
-                    tma_load_3d(buf + ((size_t)(b * bh) << lgTX), &umap, 2 * q0, b * bh, comp, &bar);
-                    tma_load_3d(buf + ((size_t)(nz - Kz - 1 + b * bh) << lgTX), &umap, 2 * q0, Kz + b * bh, comp,
-                                &bar);
+                if (kZinvHints >= 1 && hint) {
+                    const unsigned long long pol = hint == 1 ? l2_evict_last() : l2_evict_first();
+                    for (int b = 0; b < kb; ++b) {
+                        tma_load_3d_hint(buf + ((size_t)(b * bh) << lgTX), &umap, 2 * q0, b * bh, comp, &bar, pol);
+                        tma_load_3d_hint(buf + ((size_t)(nz - Kz - 1 + b * bh) << lgTX), &umap, 2 * q0,
+                                         Kz + b * bh, comp, &bar, pol);
+                    }
+                } else {
+                    for (int b = 0; b < kb; ++b) {
+                        tma_load_3d(buf + ((size_t)(b * bh) << lgTX), &umap, 2 * q0, b * bh, comp, &bar);
+                        tma_load_3d(buf + ((size_t)(nz - Kz - 1 + b * bh) << lgTX), &umap, 2 * q0, Kz + b * bh,
+                                    comp, &bar);
+                    }
                 }
             }
             const bool ok = mbar_wait(&bar, phase);
@@ -226,9 +315,15 @@ k_zinv(const cplx<T>* __restrict__ U, cplx<T>* __restrict__ W, Geom g, FftPlan p
         __syncthreads();
         return true;
     };
-    auto velocity = [&](int comp) -> bool {
-        if (!stage_in(comp)) return false;
-        fft_dif_out<T, true, V, false, R16>(buf, TX, TX, plan, tws, sinv, ZStore<T, V>{Wq + comp * Wfield, Wplane, qok});
+    // keep: the transformed component is read back as side rows (evict_last)
+    auto velocity = [&](int comp, int hint, bool keep) -> bool {
+        if (!stage_in(comp, hint)) return false;
+        ZStore<T, V> out{Wq + comp * Wfield, Wplane, qok};
+        if (kZinvHints >= 2 && keep) {
+            out.keep = true;
+            out.pol = l2_evict_last();
+        }
+        fft_dif_out<T, true, V, false, R16>(buf, TX, TX, plan, tws, sinv, out);
         __syncthreads();
         return true;
     };
@@ -236,27 +331,35 @@ k_zinv(const cplx<T>* __restrict__ U, cplx<T>* __restrict__ W, Geom g, FftPlan p
 
     if (nf < 6) {
         for (int f = 0; f < nf; ++f)
-            if (!velocity(f)) return;
+            if (!velocity(f, 0, false)) return;
         return;
     }
-    if (!velocity(2)) return;
+    if (!velocity(2, 2, true)) return;
     {   // W4 = i (Fz(kz u_x) - kx W2)
-        if (!stage_in(0)) return;
+        if (!stage_in(0, 1)) return;
         ZCurlStore<T, V> w4{nullptr, Wq + 4 * Wfield, Wq + 2 * Wfield, Wplane, {T(1), T(1)},
                             {-kxv[0], -kxv[1]}, qok};
         fft_dif_io<T, true, V, true, R16>(buf, TX, TX, plan, tws, sinv, kz_load, w4);
         __syncthreads();
     }
-    if (!velocity(0)) return;
+    if (!velocity(0, 2, true)) return;
     {   // W3 = i (ky W2 - Fz(kz u_y))
-        if (!stage_in(1)) return;
+        if (!stage_in(1, 1)) return;
         ZCurlStore<T, V> w3{nullptr, Wq + 3 * Wfield, Wq + 2 * Wfield, Wplane, {T(-1), T(-1)}, {ky, ky}, qok};
+        if (kZinvHints >= 2) {
+            w3.last = true;
+            w3.pol = l2_evict_first();
+        }
         fft_dif_io<T, true, V, true, R16>(buf, TX, TX, plan, tws, sinv, kz_load, w3);
         __syncthreads();
     }
     {   // W1 = Fz u_y and W5 = i (kx W1 - ky W0)
-        if (!stage_in(1)) return;
+        if (!stage_in(1, 2)) return;
         ZCurlStore<T, V> w5{Wq + 1 * Wfield, Wq + 5 * Wfield, Wq, Wplane, {kxv[0], kxv[1]}, {-ky, -ky}, qok};
+        if (kZinvHints >= 2) {
+            w5.last = true;
+            w5.pol = l2_evict_first();
+        }
         fft_dif_out<T, true, V, true, R16>(buf, TX, TX, plan, tws, sinv, w5);
     }
 }
