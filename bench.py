@@ -486,15 +486,21 @@ def source_hash(sources=None):
 def workload_config(n, world, workload="model_insect", wake=False, flight=False, insect="model"):
     """The `config` object of both arms: the workload as the GPU arm runs it."""
     step_bytes = sum(kernel_bytes(n, 4, wake).values())
-    insect = ("ellipsoid body (0.5, 0.12) + 2 flapping plates (c 0.3, R 1, 4dx thick, "
-              "phi 60deg sin, alpha 45deg cos)")
+    if insect == "model":
+        parts = ("ellipsoid body (0.5, 0.12) + 2 flapping plates (c 0.3, R 1, 4dx thick, "
+                 "phi 60deg sin, alpha 45deg cos)")
+    else:
+        parts = ("ellipsoid thorax (0.5, 0.12)" + (" bent on a centre-line circle of radius 1"
+                                                   if insect == "curved" else "")
+                 + " with head and eyes + 2 flapping 16-harmonic contour wings (R 1, 4dx thick, "
+                   "phi 60deg sin, alpha 45deg cos)")
     if workload == "turbulent_insect":
-        what = (f"model insect {'x'.join(map(str, n))} FP32 in turbulent inflow: {insect}, Re 1000, "
+        what = (f"model insect {'x'.join(map(str, n))} FP32 in turbulent inflow: {parts}, Re 1000, "
                 "u_inf (0.25,0,0), C_eta 5e-4, CFL 0.1 adaptive dt")
         init = ("inflow + seeded isotropic divergence-free field, E(k) ~ k^-5/3 on 2 <= |k| <= 8, "
                 "u_rms 0.1 (seed 6513)")
     else:
-        what = (f"model insect {'x'.join(map(str, n))} FP32: {insect}, Re 300, u_inf (0.25,0,0), "
+        what = (f"model insect {'x'.join(map(str, n))} FP32: {parts}, Re 300, u_inf (0.25,0,0), "
                 "C_eta 1e-3, CFL 0.1 adaptive dt")
         init = "inflow + band-limited divergence-free waves"
     if wake:
@@ -502,9 +508,6 @@ def workload_config(n, world, workload="model_insect", wake=False, flight=False,
                  "4 points deep at the x end")
     if flight:
         what += "; free flight (mass 400, J_body (2, 5, 5), g 9.81) with wing power"
-    if insect != "model":
-        what += ("; insect: thorax with head and eyes, 16-harmonic contour wings"
-                 + (", thorax on a centre-line circle of radius 1" if insect == "curved" else ""))
     return {"workload": what, "grid": list(n), "box": [4.0, 4.0, 4.0], "precision": "fp32",
             "initial": init,
             "l2": f"inputs larger than L2: {step_bytes / 1e9:.1f} GB moved per step",

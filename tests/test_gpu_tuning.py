@@ -157,3 +157,45 @@ def test_autotune_rejects_bad_arguments(fl):
             sim.autotune(steps=steps)
         assert e.value.code == fl.FLUSI_EINVAL
     sim.close()
+
+
+@pytest.mark.parametrize("kind", ["rk4_wake", "free_flight"])
+def test_autotune_restores_every_kind_of_state(fl, kind):
+    """RK4 with the wake terms (stage-suffixed kernel names, the separate
+    sponge pass of the shared-memory x kernel) and free flight (the body state
+    lives on the device): after flusi_autotune the spectrum, time, step count
+    and body state are those before it, and the run continues exactly as a
+    handle given the same settings from a checkpoint would."""
+    import test_gpu_flight as tf
+    n, L = (128, 64, 32), (4.0, 2.0, 1.0)
+    cfg = {"n": n, "L": L, "nu": 0.01, "eta": 1e-2, "cfl": 0.1, "mean_mode": "fixed",
+           "u_inf": (0.3, 0.0, 0.0)}
+    if kind == "rk4_wake":
+        cfg.update(time_scheme="rk4", sponge_c=0.1, sponge_width=(L[0] / 8, 0.0, 0.0),
+                   layer_width=(L[0] / 16, 0.0, 0.0))
+        ins = workloads.sphere((2.0, 1.0, 0.5), 0.3, profile="cos")
+    else:
+        ins = tf.flying_insect(n, L)
+        ins["x_cntr"] = (2.0, 1.0, 0.5)
+    u0 = workloads.random_smooth_field(n, 5, mean=(0.3, 0.0, 0.0))
+    sim = fl.Solver(cfg, ins, precision="fp32")
+    sim.set_state(u0)
+    sim.step(3)
+    ck = sim.save()
+    spec, (t0, s0) = sim.get_spectrum(), sim.get_state()[1:]
+    body = sim.body() if kind == "free_flight" else None
+    chosen = sim.autotune(steps=1)
+    assert np.array_equal(sim.get_spectrum(), spec) and sim.get_state()[1:] == (t0, s0)
+    if body is not None:
+        after = sim.body()
+        for k in body:
+            assert np.array_equal(after[k], body[k]), k
+    sim.step(2)
+    u_a = sim.get_state()[0]
+    sim.close()
+    other = fl.Solver(cfg, ins, precision="fp32")
+    other.set_tuning(**{k: chosen[k] for k in fl.TUNING_SETTINGS})
+    other.load(ck)
+    other.step(2)
+    assert np.array_equal(other.get_state()[0], u_a)
+    other.close()
