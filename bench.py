@@ -62,7 +62,8 @@ def parse():
     ap.add_argument("--shape", default=None,
                     help="nx,ny,nz: a reduced grid of the same box and insect (profiling)")
     ap.add_argument("--fp64-steps", type=int, default=10)
-    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--e2e-steps", type=int, default=None,
+                    help="steps of the end-to-end job (default: --steps, the device-timed job's length)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default FFT plans and tiles instead of flusi_autotune's choice")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -373,12 +374,13 @@ def run_flusi(args):
     step_bytes = sum(kb[k.split(".")[0]] for k in prof)   # every launch of the step
 
     # ---- end to end through the C-ABI with pinned host buffers
-    e2e_steps = args.e2e_steps
+    e2e_steps = args.e2e_steps if args.e2e_steps else args.steps
     if isinstance(u0, np.ndarray):
         host_in = torch.from_numpy(u0).pin_memory().numpy()
     else:
         host_in = u0.cpu().pin_memory().numpy()
     host_out = torch.empty(tuple(u0.shape), dtype=torch.float32).pin_memory().numpy()
+    host_rows = torch.zeros((e2e_steps, fl.FORCE_COLS), dtype=torch.float64).pin_memory().numpy()
     rows_total = 0
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -387,11 +389,12 @@ def run_flusi(args):
         if not args.flight:      # in free flight the body state lives on the device
             fl.flusi_set_kinematics(sim.h, sim.insect)
         fl.flusi_step(sim.h, 1)
-        rows, _ = fl.flusi_forces(sim.h, 4)
-        rows_total += rows.shape[0]
-    fl.flusi_get_state(sim.h, host_out, fl.FLUSI_HOST_FP32)
+        cnt, _ = fl.flusi_forces_async(sim.h, host_rows, rows_total)
+        rows_total += cnt
+    fl.flusi_get_state(sim.h, host_out, fl.FLUSI_HOST_FP32)   # waits for the steps and the row copies
     e2e_s = time.perf_counter() - t0
     assert rows_total == e2e_steps and np.isfinite(host_out[:, ::64, ::64, ::64]).all()
+    assert np.isfinite(host_rows).all() and (host_rows[:, 1] > 0).all() and np.all(np.diff(host_rows[:, 0]) > 0)
     e2e_s = allmax(e2e_s)
     state_bytes = host_in.nbytes
     e2e = {"value": whole_job_rate(N, e2e_steps, world, e2e_s * 1e3), "unit": UNIT, "steps": e2e_steps,
@@ -399,7 +402,8 @@ def run_flusi(args):
                                  / e2e_steps,
            "d2h_bytes_per_step": (state_bytes + e2e_steps * fl.FORCE_COLS * 8) / e2e_steps,
            "what": "set_state from pinned host FP32, per step set_kinematics (H2D) + step + "
-                   "force-row drain (D2H), get_state to pinned host FP32"}
+                   "force-row drain (D2H into pinned rows, flusi_forces_async: no per-step wait), "
+                   "get_state to pinned host FP32"}
     sim.close()
     del host_in, host_out
 

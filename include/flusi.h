@@ -211,7 +211,11 @@ int flusi_set_state(flusi_t h, const void *u, int where);
 /* Set the insect (Sec. 3): body, wings, kinematics.  Without a call (or with
  * NULL) there is no mask.  May be called between steps; with free flight it
  * replaces the body's state (the ODE's AB2 history is kept).  FLUSI_EINVAL
- * for a bad descriptor, or free flight with time_scheme 1. */
+ * for a bad descriptor, or free flight with time_scheme 1.  On a bound
+ * handle the descriptor is copied into one of 8 page-locked slots of the
+ * handle and uploaded in stream order without waiting for the enqueued
+ * steps; the call waits only when the slot it reuses still has its copy
+ * pending (the host is 8 calls ahead of the GPU). */
 int flusi_set_kinematics(flusi_t h, const flusi_insect *insect);
 
 /* Free flight (Sec. 3.6): the body state after the steps enqueued so far,
@@ -234,6 +238,18 @@ int flusi_sync(flusi_t h);
  * max |u|, then the aerodynamic and the inertial power of each wing.  Synchronizes.  Rows beyond force_ring since the last call are
  * lost; *lost (may be NULL) receives their number. */
 int flusi_forces(flusi_t h, double *rows, int cap, int *count, long long *lost);
+
+/* The same drain without waiting: enqueues on the bound stream the copy of the
+ * rows of every step enqueued since the last drain (at most `cap`, the oldest
+ * first; rows beyond force_ring are lost as above) into rows[count][...] and
+ * returns.  The rows are there once the stream has run the copy (after the
+ * next synchronizing call, or an event or synchronization of the stream).
+ * `rows` should be page-locked host memory (cudaHostAlloc, or a pinned
+ * torch tensor): from pageable memory the copy, and so the call, waits for
+ * the enqueued steps.  A step that failed on the device writes no row; the
+ * failure surfaces at the next synchronizing call, and the rows counted
+ * for the steps after it are undefined. */
+int flusi_forces_async(flusi_t h, double *rows, int cap, int *count, long long *lost);
 
 /* Copy the velocity u [3][nz][ny][nx] to host FP64 (where = FLUSI_HOST_FP64),
  * host FP32, or a caller device array in the handle's precision, with the

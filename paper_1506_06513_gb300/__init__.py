@@ -114,6 +114,7 @@ def _load():
         "flusi_debug_fields": ([h, vp], ip),
         "flusi_profile_step": ([h, ip, dp, C.POINTER(C.c_char_p), C.POINTER(C.c_int)], ip),
         "flusi_kernels_per_step": ([h, C.POINTER(C.c_int)], ip),
+        "flusi_forces_async": ([h, dp, ip, C.POINTER(C.c_int), C.POINTER(C.c_longlong)], ip),
         "flusi_get_tuning": ([h, C.POINTER(Tuning)], ip),
         "flusi_set_tuning": ([h, C.POINTER(Tuning)], ip),
         "flusi_autotune": ([h, ip, C.c_char_p, C.POINTER(Tuning)], ip),
@@ -209,6 +210,20 @@ def flusi_forces(h, cap=4096):
     count, lost = C.c_int(), C.c_longlong()
     _check(h, lib.flusi_forces(h, _dptr(rows), cap, C.byref(count), C.byref(lost)))
     return rows[: count.value].copy(), lost.value
+
+
+def flusi_forces_async(h, rows: np.ndarray, start: int = 0):
+    """Enqueue the copy of the undrained rows into rows[start:] (a C-contiguous
+    float64 array [cap][FORCE_COLS], best page-locked) without waiting; returns
+    (count, lost).  The rows are valid after the next synchronizing call."""
+    if rows.dtype != np.float64 or rows.ndim != 2 or rows.shape[1] != FORCE_COLS or not rows.flags.c_contiguous:
+        raise ValueError("rows must be a C-contiguous float64 array [cap][FORCE_COLS]")
+    if not 0 <= start <= rows.shape[0]:
+        raise ValueError("start outside rows")
+    count, lost = C.c_int(), C.c_longlong()
+    ptr = C.cast(C.c_void_p(rows.ctypes.data + start * FORCE_COLS * 8), C.POINTER(C.c_double))
+    _check(h, lib.flusi_forces_async(h, ptr, rows.shape[0] - start, C.byref(count), C.byref(lost)))
+    return count.value, lost.value
 
 
 def flusi_get_state(h, out, where):

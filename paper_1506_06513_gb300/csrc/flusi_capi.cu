@@ -21,6 +21,8 @@
 
 using namespace flusi;
 
+constexpr int kStageSlots = 8;   // pinned insect-descriptor slots per handle
+
 struct flusi_s {
     int nx = 0, ny = 0, nz = 0, prec = 0;
     double L[3] = {0, 0, 0}, nu = 0, eta = 0;
@@ -43,6 +45,12 @@ struct flusi_s {
     // run state
     int has_state = 0, poisoned = 0;
     long long rows_read = 0;
+    long long n_enq = 0;          // the device step count once the enqueued steps complete
+    // page-locked staging slots of the insect descriptor: its upload is
+    // asynchronous; a slot is reused once the copy out of it has run
+    flusi_insect* ins_stage = nullptr;
+    cudaEvent_t stage_ev[8] = {};
+    int stage_next = 0;
     cudaStream_t cap_stream = nullptr;
     // side branch of the step: the kinematics run beside the inverse z and y
     // passes, the scalar kernel beside the forward y pass
@@ -657,8 +665,21 @@ int flusi_set_kinematics(flusi_t h, const flusi_insect* ins)
     }
     // the step kernels read the descriptor from device memory in stream order;
     // only the mask shape is baked into the captured kernel arguments
-    if (h->bound)
-        CK(cudaMemcpyAsync(h->ws + h->oins, &h->ins, sizeof h->ins, cudaMemcpyHostToDevice, h->stream), "insect");
+    if (h->bound) {
+        if (!h->ins_stage) {
+            CK(cudaHostAlloc(reinterpret_cast<void**>(&h->ins_stage), sizeof(flusi_insect) * kStageSlots,
+                             cudaHostAllocDefault),
+               "pinned descriptor slots");
+            for (cudaEvent_t& ev : h->stage_ev) CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "slot event");
+        }
+        const int k = h->stage_next;
+        h->stage_next = (k + 1) % kStageSlots;
+        CK(cudaEventSynchronize(h->stage_ev[k]), "descriptor slot");   // its previous copy has run
+        h->ins_stage[k] = h->ins;
+        CK(cudaMemcpyAsync(h->ws + h->oins, &h->ins_stage[k], sizeof h->ins, cudaMemcpyHostToDevice, h->stream),
+           "insect");
+        CK(cudaEventRecord(h->stage_ev[k], h->stream), "descriptor slot");
+    }
     if (!same_shape(before, make_shape(h))) drop_graph(h);
     return FLUSI_OK;
 }
@@ -748,6 +769,7 @@ int flusi_set_state(flusi_t h, const void* u, int where)
     h->has_state = 1;
     h->poisoned = 0;
     h->rows_read = 0;
+    h->n_enq = 0;
     return FLUSI_OK;
 }
 
@@ -759,7 +781,10 @@ int flusi_step(flusi_t h, int n)
     if (h->poisoned) return fail(h, FLUSI_ESTATE, "a device error poisoned the handle; set a new state");
     if (n == 0) return FLUSI_OK;
     if (!h->opt.use_graph) {
-        for (int i = 0; i < n; ++i) CK(enqueue_step(h, h->stream, nullptr), "enqueue step");
+        for (int i = 0; i < n; ++i) {
+            CK(enqueue_step(h, h->stream, nullptr), "enqueue step");
+            ++h->n_enq;
+        }
         return FLUSI_OK;
     }
     if (!h->graph_ok) {
@@ -777,7 +802,10 @@ int flusi_step(flusi_t h, int n)
         CK(e, "instantiate graph");
         h->graph_ok = 1;
     }
-    for (int i = 0; i < n; ++i) CK(cudaGraphLaunch(h->gexec, h->stream), "graph launch");
+    for (int i = 0; i < n; ++i) {
+        CK(cudaGraphLaunch(h->gexec, h->stream), "graph launch");
+        ++h->n_enq;
+    }
     return FLUSI_OK;
 }
 
@@ -810,6 +838,35 @@ int flusi_forces(flusi_t h, double* rows, int cap, int* count, long long* lost)
         long long chunk = std::min(take - done, ring - idx);
         CK(cudaMemcpy(rows + done * kRowCols, dev + idx * kRowCols, sizeof(double) * kRowCols * chunk,
                       cudaMemcpyDeviceToHost), "read force rows");
+        done += chunk;
+    }
+    h->rows_read = first + take;
+    *count = (int)take;
+    if (lost) *lost = dropped;
+    return FLUSI_OK;
+}
+
+int flusi_forces_async(flusi_t h, double* rows, int cap, int* count, long long* lost)
+{
+    int rc = check_ready(h, true);
+    if (rc) return rc;
+    if (!rows || !count || cap < 0) return fail(h, FLUSI_EINVAL, "bad argument");
+    if (h->poisoned) return fail(h, FLUSI_ESTATE, "a device error poisoned the handle");
+    *count = 0;
+    if (lost) *lost = 0;
+    const long long ring = h->opt.force_ring;
+    const long long avail = h->n_enq - h->rows_read;
+    const long long dropped = avail > ring ? avail - ring : 0;
+    const long long first = h->rows_read + dropped;
+    const long long take = std::min<long long>(avail - dropped, cap);
+    const double* dev = at<double>(h, h->orows);
+    long long done = 0;
+    while (done < take) {
+        const long long idx = (first + done) % ring;
+        const long long chunk = std::min(take - done, ring - idx);
+        CK(cudaMemcpyAsync(rows + done * kRowCols, dev + idx * kRowCols, sizeof(double) * kRowCols * chunk,
+                           cudaMemcpyDeviceToHost, h->stream),
+           "enqueue force rows");
         done += chunk;
     }
     h->rows_read = first + take;
@@ -956,6 +1013,7 @@ int flusi_profile_step(flusi_t h, int n, double* ms, const char** names, int* nk
     std::vector<double> acc(nk_step, 0.0);
     for (int i = 0; i < n; ++i) {
         CK(enqueue_step(h, h->stream, ev, nm), "enqueue step");
+        ++h->n_enq;
         CK(cudaEventSynchronize(ev[nk_step]), "event sync");
         for (int k = 0; k < nk_step; ++k) {
             float t = 0;
@@ -1307,6 +1365,7 @@ int flusi_load(flusi_t h, const void* host_buf, size_t bytes)
     h->has_state = 1;
     h->poisoned = 0;
     h->rows_read = st.n;
+    h->n_enq = st.n;
     return FLUSI_OK;
 }
 
@@ -1441,6 +1500,7 @@ int flusi_ensemble_step(flusi_ensemble_t e, int n)
         CKE(cudaStreamWaitEvent(e->stream, e->pre[i], 0), "ensemble: order after members");
     }
     for (int k = 0; k < n; ++k) CKE(cudaGraphLaunch(e->gexec, e->stream), "ensemble: graph launch");
+    for (flusi_t h : e->m) h->n_enq += n;
     CKE(cudaEventRecord(e->done, e->stream), "ensemble: order members after");
     for (flusi_t h : e->m) CKE(cudaStreamWaitEvent(h->stream, e->done, 0), "ensemble: order members after");
     return FLUSI_OK;
@@ -1461,6 +1521,9 @@ int flusi_destroy(flusi_t h)
     if (h->side) cudaStreamDestroy(h->side);
     for (cudaEvent_t ev : {h->ev_fork, h->ev_kin, h->ev_x, h->ev_sc})
         if (ev) cudaEventDestroy(ev);
+    for (cudaEvent_t ev : h->stage_ev)
+        if (ev) cudaEventDestroy(ev);
+    if (h->ins_stage) cudaFreeHost(h->ins_stage);
     delete h;
     return FLUSI_OK;
 }
