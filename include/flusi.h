@@ -306,18 +306,23 @@ int flusi_kernels_per_step(flusi_t h, int *count);
  * least 32 bytes of complex values (4 in FP32, 2 in FP64) and at most 256.
  * x_kernel: 0 (default) the register-resident line kernel where one exists
  * (nx = 128, 256, 512, 1024), 1 the shared-memory kernel of every length.
+ * y_pair: 1 the y passes' paired kernel, a cluster of two CTAs per tile,
+ * each holding the grid rows of one parity and transforming them at half the
+ * length, joined by a radix-2 step through distributed shared memory, so
+ * that tiles keep 128-byte rows at twice the length (ny even); 0 (default)
+ * one CTA per tile.  With it, y_cols caps the paired tile.
  *
  * flusi_get_tuning fills every field, including the read-only ones: the
  * radices each pass takes (0-terminated), the columns a tile takes, and
  * whether the x pass runs the register-resident kernel.
- * flusi_set_tuning takes the five settings (the rest is ignored); any
+ * flusi_set_tuning takes the six settings (the rest is ignored); any
  * other value is FLUSI_EINVAL with nothing changed.  On a bound handle it
  * waits for the handle's stream, uploads the new digit-reversal tables and
  * rebuilds the TMA descriptors; the state is kept.  No device work on an
  * unbound handle.
  *
  * flusi_autotune: on a bound handle with a state, coordinate descent over
- * the settings (y_plan, y_cols, zf_plan, z_cols, x_kernel, in that order):
+ * the settings (y_plan, y_pair, y_cols, zf_plan, z_cols, x_kernel, in that order):
  * each candidate runs one untimed step and `steps` (1..1000) timed steps,
  * and is scored by the CUDA-event time of the kernels it changes
  * (flusi_profile_step's per-kernel times); the best is kept.  The state,
@@ -325,7 +330,7 @@ int flusi_kernels_per_step(flusi_t h, int *count);
  * after, as by flusi_save/flusi_load, so the run continues where it was;
  * undrained force rows are dropped, as by flusi_load.  cache_path (NULL: no
  * cache) names a text file of lines "key y_plan zf_plan y_cols z_cols
- * x_kernel", key = GPU name (spaces as '_'), SM count, grid, precision,
+ * x_kernel y_pair", key = GPU name (spaces as '_'), SM count, grid, precision,
  * time scheme and wake terms: a line with this handle's key is applied
  * without timing; otherwise the result is appended (a file that cannot be
  * written is FLUSI_EINVAL after the tuning is applied).  *out (may be
@@ -336,9 +341,11 @@ typedef struct flusi_tuning {
     int y_plan, zf_plan;       /* 0, 1 (default) or 2                      */
     int y_cols, z_cols;        /* 0 (default) or a power of two cap        */
     int x_kernel;              /* 0 (default) or 1                         */
-    /* read-only, filled by flusi_get_tuning */
+    int y_pair;                /* 0 (default) or 1                         */
+    /* read-only, filled by flusi_get_tuning (y_radix: the paired kernel's
+     * half-length plan when y_paired is 1) */
     int y_radix[FLUSI_MAX_STAGES], zf_radix[FLUSI_MAX_STAGES], zi_radix[FLUSI_MAX_STAGES];
-    int y_tile_cols, z_tile_cols, x_line_kernel;
+    int y_tile_cols, z_tile_cols, x_line_kernel, y_paired;
 } flusi_tuning;
 int flusi_get_tuning(flusi_t h, flusi_tuning *out);
 int flusi_set_tuning(flusi_t h, const flusi_tuning *tuning);

@@ -41,21 +41,22 @@ class Options(C.Structure):
 
 
 MAX_STAGES = 8
-TUNING_SETTINGS = ("y_plan", "zf_plan", "y_cols", "z_cols", "x_kernel")
+TUNING_SETTINGS = ("y_plan", "zf_plan", "y_cols", "z_cols", "x_kernel", "y_pair")
 
 
 class Tuning(C.Structure):
     _fields_ = [("y_plan", C.c_int), ("zf_plan", C.c_int), ("y_cols", C.c_int), ("z_cols", C.c_int),
-                ("x_kernel", C.c_int),
+                ("x_kernel", C.c_int), ("y_pair", C.c_int),
                 ("y_radix", C.c_int * MAX_STAGES), ("zf_radix", C.c_int * MAX_STAGES),
                 ("zi_radix", C.c_int * MAX_STAGES),
-                ("y_tile_cols", C.c_int), ("z_tile_cols", C.c_int), ("x_line_kernel", C.c_int)]
+                ("y_tile_cols", C.c_int), ("z_tile_cols", C.c_int), ("x_line_kernel", C.c_int),
+                ("y_paired", C.c_int)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k in TUNING_SETTINGS}
         for k in ("y_radix", "zf_radix", "zi_radix"):
             d[k] = [r for r in getattr(self, k) if r]
-        for k in ("y_tile_cols", "z_tile_cols", "x_line_kernel"):
+        for k in ("y_tile_cols", "z_tile_cols", "x_line_kernel", "y_paired"):
             d[k] = getattr(self, k)
         return d
 

@@ -76,8 +76,9 @@ struct Geom {
     double dx, dy, dz;
     double nu, eta;
     // tile and kernel choices (0: defaults): caps on the columns of a y and a
-    // z tile, and the shared-memory x kernel in place of the line kernel
-    int ycols, zcols, xgeneric;
+    // z tile, the shared-memory x kernel in place of the line kernel, and the
+    // paired (two-CTA) y kernel where ny is even
+    int ycols, zcols, xgeneric, ypair;
 };
 
 // Per-step geometry of the insect, written by the kinematics kernel (FP64).

@@ -32,6 +32,7 @@ struct flusi_s {
     int have_ins = 0;
     Geom g{};
     FftPlan px{}, py{}, pz{}, pzi{};   // pzi: the inverse z pass's plan (no radix-16 stage)
+    FftPlan pyh{};                 // half the y length, for the paired y kernel (ny even)
     YMaps ymaps{};                 // TMA descriptors of W for the y passes (built at bind)
     ZMaps zmaps{};                 // TMA descriptors of U, the RK4 stage state and W for the z passes
     // workspace
@@ -39,7 +40,7 @@ struct flusi_s {
     size_t ws_bytes = 0;
     cudaStream_t stream = nullptr;
     int bound = 0;
-    size_t oU = 0, oH = 0, oUt = 0, oW = 0, otx = 0, oty = 0, otz = 0, opx = 0, opy = 0, opz = 0, opzi = 0,
+    size_t oU = 0, oH = 0, oUt = 0, oW = 0, otx = 0, oty = 0, otz = 0, opx = 0, opy = 0, opz = 0, opzi = 0, opyh = 0,
            oframe = 0, oins = 0, ostate = 0, ocoef = 0, oetab = 0, opart = 0, orows = 0, total = 0;
     int part_cap = 0, xgrid = 0;
     // run state
@@ -221,6 +222,7 @@ void layout(flusi_t h)
     h->opy = o; o = align256(o + sizeof(int) * g.ny);
     h->opz = o; o = align256(o + sizeof(int) * g.nz);
     h->opzi = o; o = align256(o + sizeof(int) * g.nz);
+    h->opyh = o; o = align256(o + sizeof(int) * (g.ny / 2));
     h->oframe = o; o = align256(o + sizeof(Frame));
     h->oins = o; o = align256(o + sizeof(flusi_insect));
     h->ostate = o; o = align256(o + sizeof(StepState));
@@ -235,7 +237,9 @@ void layout(flusi_t h)
     // the inverse z pass holds more live values per thread (the curl's side
     // rows); a radix-16 stage there costs it a block per SM, more than it saves
     h->pzi = make_plan(h->nz, 1, 0);
+    h->pyh = h->ny % 2 == 0 ? make_plan(h->ny / 2, 1, h->tune.y_plan) : FftPlan{};
     g.ycols = h->tune.y_cols;
+    g.ypair = h->tune.y_pair;
     g.zcols = h->tune.z_cols;
     g.xgeneric = h->tune.x_kernel;
 }
@@ -377,7 +381,7 @@ cudaError_t enqueue_step(flusi_t h, cudaStream_t s, cudaEvent_t* ev, const char*
         if ((e = launch_zinv(fp64, ustage, W, g, h->pzi, tz, at<int>(h, h->opzi), 6, st, umap, ubh, &st->status, s)))
             return e;
         mark(nm[2]);
-        if ((e = launch_ypass(fp64, true, W, g, h->py, ty, at<int>(h, h->opy), 6, st, &h->ymaps, &st->status, s))) return e;
+        if ((e = launch_ypass(fp64, true, W, g, h->py, ty, at<int>(h, h->opy), 6, st, &h->ymaps, &st->status, s, &h->pyh, at<int>(h, h->opyh)))) return e;
         mark(nm[3]);
         if (br && (e = cudaStreamWaitEvent(s, h->ev_kin, 0))) return e;
         XExtra xe{};
@@ -411,7 +415,7 @@ cudaError_t enqueue_step(flusi_t h, cudaStream_t s, cudaEvent_t* ev, const char*
             if ((e = launch_xpass(fp64, XP_SPONGE, W, g, h->px, tx, at<int>(h, h->opx), xs, st, s))) return e;
         }
         mark(nm[5]);
-        if ((e = launch_ypass(fp64, false, W, g, h->py, ty, at<int>(h, h->opy), nfwd, st, &h->ymaps, &st->status, s))) return e;
+        if ((e = launch_ypass(fp64, false, W, g, h->py, ty, at<int>(h, h->opy), nfwd, st, &h->ymaps, &st->status, s, &h->pyh, at<int>(h, h->opyh)))) return e;
         mark(nm[6]);
         if ((e = launch_zfwd(fp64, W, nfwd, g, h->pz, tz, at<int>(h, h->opz), st, &h->zmaps.w, h->zmaps.w_bh,
                              &st->status, s)))
@@ -619,6 +623,13 @@ int flusi_bind(flusi_t h, void* ws, size_t bytes, void* stream)
     CK(cudaMemcpyAsync(h->ws + h->opz, pz.data(), sizeof(int) * pz.size(), cudaMemcpyHostToDevice, h->stream), "digit reversal");
     CK(cudaMemcpyAsync(h->ws + h->opzi, pzi.data(), sizeof(int) * pzi.size(), cudaMemcpyHostToDevice, h->stream),
        "digit reversal");
+    std::vector<int> pyh;
+    if (h->pyh.n > 0) {
+        pyh = digit_reversal(h->pyh);
+        CK(cudaMemcpyAsync(h->ws + h->opyh, pyh.data(), sizeof(int) * pyh.size(), cudaMemcpyHostToDevice,
+                           h->stream),
+           "digit reversal");
+    }
     // the host tables must outlive the asynchronous copies
     CK(cudaStreamSynchronize(h->stream), "bind tables");
     if (h->have_ins)
@@ -756,7 +767,7 @@ int flusi_set_state(flusi_t h, const void* u, int where)
         }
     }
     CK(launch_ypass(fp64, false, W, g, h->py, at<double2>(h, h->oty), at<int>(h, h->opy), 3, nullptr,
-                    &h->ymaps, status_word(h), s), "y forward");
+                    &h->ymaps, status_word(h), s, &h->pyh, at<int>(h, h->opyh)), "y forward");
     CK(launch_zfwd(fp64, W, 3, g, h->pz, at<double2>(h, h->otz), at<int>(h, h->opz), nullptr, &h->zmaps.w,
                    h->zmaps.w_bh, status_word(h), s),
        "z forward");
@@ -893,7 +904,7 @@ int flusi_get_state(flusi_t h, void* u_out, int where, double* t, long long* ste
                    &h->zmaps.u, h->zmaps.u_bh, status_word(h), s),
        "z inverse");
     CK(launch_ypass(fp64, true, W, g, h->py, at<double2>(h, h->oty), at<int>(h, h->opy), 3, nullptr,
-                    &h->ymaps, status_word(h), s), "y inverse");
+                    &h->ymaps, status_word(h), s, &h->pyh, at<int>(h, h->opyh)), "y inverse");
     XExtra xe{};
     xe.cstride = (long long)N;
     if (where == FLUSI_DEVICE) {
@@ -988,7 +999,7 @@ int flusi_debug_fields(flusi_t h, void* out_dev)
                    &h->zmaps.u, h->zmaps.u_bh, status_word(h), s),
        "z inverse");
     CK(launch_ypass(fp64, true, W, g, h->py, at<double2>(h, h->oty), at<int>(h, h->opy), 6, nullptr,
-                    &h->ymaps, status_word(h), s), "y inverse");
+                    &h->ymaps, status_word(h), s, &h->pyh, at<int>(h, h->opyh)), "y inverse");
     XExtra xe{};
     xe.frame = at<Frame>(h, h->oframe);
     xe.shape = make_shape(h);
@@ -1050,6 +1061,7 @@ int tuning_error(flusi_t h, const flusi_tuning& t)
     if (!cols_ok(t.y_cols) || !cols_ok(t.z_cols))
         return fail(h, FLUSI_EINVAL, "y_cols and z_cols must be 0 or a power of two in [32 bytes, 256]");
     if (t.x_kernel != 0 && t.x_kernel != 1) return fail(h, FLUSI_EINVAL, "x_kernel must be 0 or 1");
+    if (t.y_pair != 0 && t.y_pair != 1) return fail(h, FLUSI_EINVAL, "y_pair must be 0 or 1");
     return FLUSI_OK;
 }
 
@@ -1109,7 +1121,7 @@ bool cache_lookup(const char* path, const std::string& key, flusi_tuning* t)
         std::istringstream in(line);
         std::string k;
         flusi_tuning c{};
-        if (!(in >> k >> c.y_plan >> c.zf_plan >> c.y_cols >> c.z_cols >> c.x_kernel)) continue;
+        if (!(in >> k >> c.y_plan >> c.zf_plan >> c.y_cols >> c.z_cols >> c.x_kernel >> c.y_pair)) continue;
         if (k == key) {
             *t = c;
             found = true;
@@ -1124,10 +1136,11 @@ int flusi_get_tuning(flusi_t h, flusi_tuning* out)
 {
     if (!h || !out) return fail(h, FLUSI_EINVAL, "NULL argument");
     *out = h->tune;
-    radices(h->py, out->y_radix);
+    const int fp64 = h->prec == FLUSI_FP64;
+    out->y_paired = ypass_paired(fp64, h->g);
+    radices(out->y_paired ? h->pyh : h->py, out->y_radix);
     radices(h->pz, out->zf_radix);
     radices(h->pzi, out->zi_radix);
-    const int fp64 = h->prec == FLUSI_FP64;
     out->y_tile_cols = ypass_tile_cols(fp64, h->g);
     out->z_tile_cols = zpass_tile_cols(fp64, h->g);
     out->x_line_kernel = xpass_fuses_sponge(fp64, h->g);
@@ -1146,12 +1159,20 @@ int flusi_set_tuning(flusi_t h, const flusi_tuning* t)
     h->tune.y_cols = t->y_cols;
     h->tune.z_cols = t->z_cols;
     h->tune.x_kernel = t->x_kernel;
+    h->tune.y_pair = t->y_pair;
     layout(h);
     drop_graph(h);
     if (!h->bound) return FLUSI_OK;
     const auto py = digit_reversal(h->py), pz = digit_reversal(h->pz);
     CK(cudaMemcpyAsync(h->ws + h->opy, py.data(), sizeof(int) * py.size(), cudaMemcpyHostToDevice, h->stream),
        "digit reversal");
+    std::vector<int> pyh;
+    if (h->pyh.n > 0) {
+        pyh = digit_reversal(h->pyh);
+        CK(cudaMemcpyAsync(h->ws + h->opyh, pyh.data(), sizeof(int) * pyh.size(), cudaMemcpyHostToDevice,
+                           h->stream),
+           "digit reversal");
+    }
     CK(cudaMemcpyAsync(h->ws + h->opz, pz.data(), sizeof(int) * pz.size(), cudaMemcpyHostToDevice, h->stream),
        "digit reversal");
     CK(cudaStreamSynchronize(h->stream), "retune tables");
@@ -1183,6 +1204,7 @@ int flusi_autotune(flusi_t h, int steps, const char* cache_path, flusi_tuning* o
         const char* kernels[2];
     };
     const Knob knobs[] = {{&flusi_tuning::y_plan, {"yinv", "yfwd"}},
+                          {&flusi_tuning::y_pair, {"yinv", "yfwd"}},
                           {&flusi_tuning::y_cols, {"yinv", "yfwd"}},
                           {&flusi_tuning::zf_plan, {"zfwd", nullptr}},
                           {&flusi_tuning::z_cols, {"zinv_curl", "zfwd"}},
@@ -1191,6 +1213,7 @@ int flusi_autotune(flusi_t h, int steps, const char* cache_path, flusi_tuning* o
         // candidate values: the plans, or the default tile and two halvings
         std::vector<int> vals;
         if (kb.field == &flusi_tuning::y_plan || kb.field == &flusi_tuning::zf_plan) vals = {1, 0, 2};
+        else if (kb.field == &flusi_tuning::y_pair) vals = {0, 1};
         else if (kb.field == &flusi_tuning::x_kernel) vals = {0, 1};
         else {
             flusi_tuning d = best;
@@ -1219,7 +1242,7 @@ int flusi_autotune(flusi_t h, int steps, const char* cache_path, flusi_tuning* o
             for (int i = 0; i < FLUSI_MAX_STAGES; ++i)
                 sig += std::to_string(got.y_radix[i]) + "," + std::to_string(got.zf_radix[i]) + ",";
             sig += std::to_string(got.y_tile_cols) + "," + std::to_string(got.z_tile_cols) + "," +
-                   std::to_string(got.x_line_kernel);
+                   std::to_string(got.x_line_kernel) + "," + std::to_string(got.y_paired);
             if (std::find(seen.begin(), seen.end(), sig) != seen.end()) continue;
             seen.push_back(sig);
             double ms = 0;
@@ -1247,7 +1270,7 @@ int flusi_autotune(flusi_t h, int steps, const char* cache_path, flusi_tuning* o
     if (cache_path) {
         std::ofstream f(cache_path, std::ios::app);
         f << key << ' ' << best.y_plan << ' ' << best.zf_plan << ' ' << best.y_cols << ' ' << best.z_cols << ' '
-          << best.x_kernel << '\n';
+          << best.x_kernel << ' ' << best.y_pair << '\n';
         if (!f) return fail(h, FLUSI_EINVAL, "cannot append to the tuning cache");
     }
     return FLUSI_OK;

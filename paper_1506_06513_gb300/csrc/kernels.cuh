@@ -44,9 +44,15 @@ struct YMaps {
     int inv_bh = 0, fwd_bh = 0;   // box heights (rows); 0: that direction copies by 16 bytes
 };
 cudaError_t prepare_ymaps(int fp64, void* W, const Geom& g, YMaps* maps);
+// half, pos_half: the plan of length ny / 2 and its digit-reversal table, for
+// the paired kernel (a cluster of two CTAs per tile; see ypass_paired);
+// nullptr: one CTA per tile always
 cudaError_t launch_ypass(int fp64, bool inverse, void* W, const Geom& g, const FftPlan& plan,
                          const double2* tw, const int* pos, int ncomp, const StepState* st,
-                         const YMaps* maps, int* err, cudaStream_t s);
+                         const YMaps* maps, int* err, cudaStream_t s, const FftPlan* half = nullptr,
+                         const int* pos_half = nullptr);
+// 1 when the y passes of this grid take the paired kernel (Geom::ypair)
+int ypass_paired(int fp64, const Geom& g);
 
 // z transforms (zpass.cu)
 //   zinv: U -> W[0..nf) in A form; nf = 3 (u) or 6 (u and omega = i k x u).

@@ -14,6 +14,8 @@
 //   forward: ny grid rows -> the My kept y-modes (2/3 rule, pruned output)
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 #include "fft.cuh"
 #include "kernels.cuh"
 
@@ -136,6 +138,106 @@ k_ypass(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict
     }
 }
 
+// Paired variant (a cluster of two CTAs per tile), for lengths where a
+// one-CTA tile of 128-byte rows would not fit its shared memory.  With
+// n = 2 m, the CTA of cluster rank p holds the grid rows 2 s + p (s < m) of
+// the tile, and transforms them at length m, every stage in shared memory
+// (row pos_h[f] then holds frequency f).  The two halves are joined by one
+// radix-2 decimation-in-time step: X[f] = E[f] + w_n^f O[f] and
+// X[f + m] = E[f] - w_n^f O[f] (conjugate twiddles for the inverse), E from
+// rank 0, O from rank 1, read across the cluster through distributed shared
+// memory; rank p computes and stores the frequencies f + p m.  The loads are
+// 16-byte asynchronous copies.  Both CTAs take every cluster barrier on every
+// path (no early return), so neither can wait on a partner that has left.
+template <typename T, bool INV, bool R16>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads)
+k_ypass_pair(cplx<T>* __restrict__ W, Geom g, FftPlan plan_h, const double2* __restrict__ tw,
+             const int* __restrict__ pos_h, int ncomp, int lgTX, int lgNP)
+{
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int p = (int)cluster.block_rank();
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int TX = 1 << lgTX, lgC = lgTX + lgNP, C = 1 << lgC;
+    const int ny = g.ny, m = ny / 2, My = g.My, Ky = g.Ky;
+    cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127));
+    cplx<T>* tws = buf + ((size_t)m << lgC);     // w_m^j = w_n^(2j), j < m
+    int* spos = reinterpret_cast<int*>(tws + m);  // row of frequency f after the length-m transform
+    const int nxb = ceil_div(g.Mxp, TX), nzb = ceil_div(g.nz, 1 << lgNP);
+    int b = blockIdx.x / 2;
+    const int xb = b % nxb;
+    b /= nxb;
+    const int zb = b % nzb;
+    const int c = min(b / nzb, ncomp - 1);        // the grid holds whole clusters of real tiles
+    const int x0 = xb * TX, z0 = zb << lgNP;
+    const size_t plane = (size_t)ny * g.Mxp;
+    cplx<T>* base = W + (size_t)c * g.nz * plane;
+    const int ld = g.Mxp;
+
+    for (int i = threadIdx.x; i < m; i += kThreads) {
+        const double2 w = tw[2 * i];
+        tws[i] = mkc<T>(T(w.x), T(w.y));
+        spos[i] = pos_h[i];
+    }
+    // rows 2 s + p of the tile: VEC adjacent columns per lane
+    {
+        constexpr int VEC = 16 / sizeof(cplx<T>);
+        const int lanes_per_row = C / VEC;
+        const int rstep = kThreads / lanes_per_row;
+        const int cv = (threadIdx.x % lanes_per_row) * VEC;
+        const int zv = z0 + (cv >> lgTX), xv = x0 + (cv & (TX - 1));
+        const bool okv = zv < g.nz && xv < g.Mxp;   // Mxp and TX are multiples of VEC
+        const cplx<T>* gv = base + (size_t)(okv ? zv : 0) * plane + (okv ? xv : 0);
+        for (int sr = threadIdx.x / lanes_per_row; sr < m; sr += rstep) {
+            const int s2 = 2 * sr + p;
+            // inverse: grid slot s2 <- kept mode row j (modes 0..Ky, -Ky..-1 in rows j < My)
+            const int j = INV ? (s2 <= Ky ? s2 : (s2 >= ny - Ky ? s2 - ny + My : -1)) : s2;
+            cplx<T>* dst = buf + ((size_t)sr << lgC) + cv;
+            if (okv && j >= 0) {
+                cp_async_16(dst, gv + (size_t)j * ld);
+            } else {
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) dst[v] = mkc<T>(0, 0);
+            }
+        }
+        cp_async_wait_all();
+    }
+    __syncthreads();
+    fft_run<T, INV, true, 2, R16>(buf, C, C, plan_h, tws, 0, plan_h.nst);   // ends with a block barrier
+    cluster.sync();   // both halves transformed: the partner's buffer is readable
+
+    constexpr int V = 2;
+    const int G = C / V, P = kThreads / G, col = (threadIdx.x % G) * V, jt = threadIdx.x / G;
+    const int z = z0 + (col >> lgTX), x = x0 + (col & (TX - 1));
+    const bool colok = z < g.nz && x < g.Mxp && b / nzb < ncomp;
+    cplx<T>* gcol = base + (size_t)(colok ? z : 0) * plane + (colok ? x : 0);
+    const cplx<T>* other = cluster.map_shared_rank(buf, p ^ 1);
+    for (int f = jt; f < m; f += P) {
+        const int r = spos[f];
+        cplx<T> a[V], o[V];
+        ld_row<T, V>(buf + ((size_t)r << lgC) + col, a);
+        ld_row<T, V>(other + ((size_t)r << lgC) + col, o);
+        const double2 wd = tw[f];
+        const cplx<T> w = mkc<T>(T(wd.x), INV ? -T(wd.y) : T(wd.y));
+        cplx<T> out[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            // own half: E for rank 0, O for rank 1
+            const cplx<T> E = p ? o[v] : a[v], O = p ? a[v] : o[v];
+            const cplx<T> t = cmul(w, O);
+            out[v] = p ? csub(E, t) : cadd(E, t);
+        }
+        const int fr = f + p * m;   // the frequency this CTA stores
+        if (INV) {
+            if (colok) st_row<T, V>(gcol + (size_t)fr * ld, out);
+        } else {
+            const int r2 = fr <= Ky ? fr : (fr >= ny - Ky ? fr - ny + My : -1);
+            if (colok && r2 >= 0) st_row<T, V>(gcol + (size_t)r2 * ld, out);
+        }
+    }
+    cluster.sync();   // the partner has read this buffer
+}
+
 struct YTile {
     int lgTX, lgNP, blocks;
     size_t smem;
@@ -183,11 +285,48 @@ cudaError_t launch_y2(bool inverse, cplx<T>* w, const Geom& g, const FftPlan& pl
     return cudaGetLastError();
 }
 
+// The paired kernel's tile: a one-CTA tile for the half length m = ny / 2.
+template <typename T> YTile y_tile_pair(const Geom& g, int ncomp)
+{
+    Geom h = g;
+    h.ny = g.ny / 2;
+    YTile t = y_tile<T>(h, ncomp);
+    t.blocks *= 2;
+    t.smem = sizeof(cplx<T>) * ((size_t)h.ny << (t.lgTX + t.lgNP)) + (sizeof(cplx<T>) + sizeof(int)) * h.ny + 128;
+    return t;
+}
+
+// whether the y passes take the paired kernel: ypair 1 and ny even (at
+// least 16).  It keeps 128-byte rows at n = 1024, but measured slower than
+// one CTA per tile on 512^3 and 1024^3 (the second pass through shared
+// memory, the 16-byte copies in place of TMA boxes and the reads across the
+// cluster cost more than the narrower rows), so it is an autotuner candidate,
+// not a default.
+template <typename T> bool y_paired(const Geom& g) { return g.ypair == 1 && g.ny % 2 == 0 && g.ny >= 16; }
+
 template <typename T>
 cudaError_t launch_y(bool inverse, void* W, const Geom& g, const FftPlan& plan, const double2* tw,
                      const int* pos, int ncomp, const StepState* st, const YMaps* maps, int* err,
-                     cudaStream_t s)
+                     const FftPlan* half, const int* pos_half, cudaStream_t s)
 {
+    if (half && pos_half && y_paired<T>(g)) {
+        const YTile t = y_tile_pair<T>(g, ncomp);
+        if (((size_t)(g.ny / 2) << (t.lgTX + t.lgNP)) > (size_t)tile_elems<T>() || half->n != g.ny / 2)
+            return cudaErrorInvalidValue;
+        cplx<T>* w = (cplx<T>*)W;
+        const bool r16 = plan_has_radix16(*half);
+#define FLUSI_PAIR(I, R)                                                                                  \
+    k_ypass_pair<T, I, R><<<t.blocks, kThreads, t.smem, s>>>(w, g, *half, tw, pos_half, ncomp, t.lgTX, t.lgNP)
+        if (inverse) {
+            if (r16) FLUSI_PAIR(true, true);
+            else FLUSI_PAIR(true, false);
+        } else {
+            if (r16) FLUSI_PAIR(false, true);
+            else FLUSI_PAIR(false, false);
+        }
+#undef FLUSI_PAIR
+        return cudaGetLastError();
+    }
     YTile t = y_tile<T>(g, ncomp);
     if ((size_t)g.ny << (t.lgTX + t.lgNP) > (size_t)tile_elems<T>()) return cudaErrorInvalidValue;
     cplx<T>* w = (cplx<T>*)W;
@@ -247,7 +386,9 @@ TensorMapEncoder tensor_map_encoder()
 
 int ypass_tile_cols(int fp64, const Geom& g)
 {
-    const YTile t = fp64 ? y_tile<double>(g, 1) : y_tile<float>(g, 1);
+    YTile t;
+    if (fp64) t = y_paired<double>(g) ? y_tile_pair<double>(g, 1) : y_tile<double>(g, 1);
+    else t = y_paired<float>(g) ? y_tile_pair<float>(g, 1) : y_tile<float>(g, 1);
     return 1 << (t.lgTX + t.lgNP);
 }
 
@@ -258,11 +399,14 @@ cudaError_t prepare_ymaps(int fp64, void* W, const Geom& g, YMaps* maps)
 
 cudaError_t launch_ypass(int fp64, bool inverse, void* W, const Geom& g, const FftPlan& plan,
                          const double2* tw, const int* pos, int ncomp, const StepState* st,
-                         const YMaps* maps, int* err, cudaStream_t s)
+                         const YMaps* maps, int* err, cudaStream_t s, const FftPlan* half,
+                         const int* pos_half)
 {
-    return fp64 ? launch_y<double>(inverse, W, g, plan, tw, pos, ncomp, st, maps, err, s)
-                : launch_y<float>(inverse, W, g, plan, tw, pos, ncomp, st, maps, err, s);
+    return fp64 ? launch_y<double>(inverse, W, g, plan, tw, pos, ncomp, st, maps, err, half, pos_half, s)
+                : launch_y<float>(inverse, W, g, plan, tw, pos, ncomp, st, maps, err, half, pos_half, s);
 }
+
+int ypass_paired(int fp64, const Geom& g) { return fp64 ? y_paired<double>(g) : y_paired<float>(g); }
 
 cudaError_t configure_ypass()
 {
@@ -280,6 +424,14 @@ cudaError_t configure_ypass()
     FLUSI_SMEM_Y(float, true)
     FLUSI_SMEM_Y(double, true)
 #undef FLUSI_SMEM_Y
+#define FLUSI_SMEM_P(T, R16)                     \
+    FLUSI_SMEM((k_ypass_pair<T, true, R16>))     \
+    FLUSI_SMEM((k_ypass_pair<T, false, R16>))
+    FLUSI_SMEM_P(float, false)
+    FLUSI_SMEM_P(double, false)
+    FLUSI_SMEM_P(float, true)
+    FLUSI_SMEM_P(double, true)
+#undef FLUSI_SMEM_P
 #undef FLUSI_SMEM
     return cudaSuccess;
 }

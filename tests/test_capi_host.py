@@ -231,7 +231,7 @@ def test_tuning_is_validated(fl):
     before = fl.flusi_get_tuning(h)
     assert before["y_plan"] == 1 and before["zf_plan"] == 1 and before["x_line_kernel"] == 1
     for bad in ({"y_plan": 3}, {"zf_plan": -1}, {"y_cols": 3}, {"y_cols": 2}, {"z_cols": 512},
-                {"z_cols": -4}, {"x_kernel": 2}):
+                {"z_cols": -4}, {"x_kernel": 2}, {"y_pair": 2}, {"y_pair": -1}):
         with pytest.raises(fl.FlusiError) as e:
             fl.flusi_set_tuning(h, **bad)
         assert e.value.code == fl.FLUSI_EINVAL
@@ -258,3 +258,24 @@ def test_autotune_needs_a_bound_handle(fl):
         fl.flusi_autotune(h, 2)
     assert e.value.code == fl.FLUSI_ESTATE
     fl.flusi_destroy(h)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_paired_y_kernel_choice(fl, prec):
+    """y_pair 1 takes the paired y kernel wherever ny is even (at least 16),
+    with the half length's plan and a tile of 128-byte rows or wider; 0 (the
+    default) never."""
+    P = fl.FLUSI_FP32 if prec == "fp32" else fl.FLUSI_FP64
+    row = 128 // (8 if prec == "fp32" else 16)       # complex values in 128 bytes
+    for ny in (512, 768, 1024, 96, 16, 27):
+        h = fl.flusi_create((16, ny, 16), (1.0, 1.0, 1.0), 0.1, 1e-2, P)
+        t = fl.flusi_get_tuning(h)
+        assert t["y_pair"] == 0 and t["y_paired"] == 0 and _prod(t["y_radix"]) == ny
+        fl.flusi_set_tuning(h, y_pair=1)
+        t = fl.flusi_get_tuning(h)
+        assert t["y_paired"] == (ny % 2 == 0)
+        if ny % 2 == 0:
+            assert _prod(t["y_radix"]) == ny // 2 and t["y_tile_cols"] >= min(row, 8192 // 8)
+        else:
+            assert _prod(t["y_radix"]) == ny
+        fl.flusi_destroy(h)

@@ -25,7 +25,8 @@ SETTINGS = {
     "narrow_tiles": {"y_cols": 8, "z_cols": 8},
     "narrowest_tiles": {"y_cols": 4, "z_cols": 4},
     "shared_memory_x_kernel": {"x_kernel": 1},
-    "all_changed": {"y_plan": 2, "zf_plan": 0, "y_cols": 8, "z_cols": 16, "x_kernel": 1},
+    "paired_y": {"y_pair": 1},
+    "all_changed": {"y_plan": 2, "zf_plan": 0, "y_cols": 8, "z_cols": 16, "x_kernel": 1, "y_pair": 1},
 }
 
 
@@ -78,6 +79,38 @@ def test_every_setting_matches_the_oracle(fl, reference, name, prec):
     assert lost == 0 and rows.shape == rows_ref.shape
     tol_u, tol_f = (1e-11, 1e-10) if prec == "fp64" else (3e-5, 1e-4)
     assert rel_l2(u, u_ref) <= tol_u
+    assert rel_l2(rows[:, 2:20], rows_ref[:, 2:20]) <= tol_f
+
+
+PAIR_GRIDS = [((16, 1024, 12), (1.0, 8.0, 0.75)),    # half 512 = 8 8 8
+              ((24, 768, 8), (1.5, 6.0, 0.5)),       # half 384 = 3 16 8
+              ((8, 96, 18), (0.5, 0.75, 1.125)),     # half 48 = 3 16
+              ((16, 16, 16), (1.0, 1.0, 1.0))]       # half 8 = 8: one stage
+
+
+@pytest.mark.parametrize("n,L", PAIR_GRIDS)
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_paired_y_kernel_matches_the_oracle(fl, n, L, prec):
+    """The two-CTA y kernel (y_pair 1; rows split by parity, joined by a
+    radix-2 step through distributed shared memory) against the oracle, on
+    grids with half lengths of one to three stages and a factor 3."""
+    cfg = {"n": n, "L": L, "nu": 0.01, "eta": 1e-2, "dt_fixed": 1e-3, "mean_mode": "fixed",
+           "u_inf": (0.3, 0.0, 0.0)}
+    ins = workloads.sphere(tuple(0.5 * x for x in L), 0.3 * min(L), profile="cos")
+    u0 = workloads.random_smooth_field(n, 5, mean=(0.3, 0.0, 0.0))
+    ref = oracle.Simulation(cfg, ins)
+    ref.set_state(u0)
+    rows_ref = ref.step(2)
+    sim = fl.Solver(cfg, ins, precision=prec)
+    sim.set_tuning(y_pair=1)
+    assert sim.tuning()["y_paired"] == 1
+    sim.set_state(u0)
+    sim.step(2)
+    rows, _ = sim.forces()
+    u = sim.get_state()[0]
+    sim.close()
+    tol_u, tol_f = (1e-11, 1e-10) if prec == "fp64" else (3e-5, 1e-4)
+    assert rel_l2(u, ref.get_state()) <= tol_u
     assert rel_l2(rows[:, 2:20], rows_ref[:, 2:20]) <= tol_f
 
 
