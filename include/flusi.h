@@ -433,8 +433,9 @@ int flusi_load(flusi_t h, const void *host_buf, size_t bytes);
  * member see the ensemble's steps.  A member with a device error stops
  * stepping (its kernels return at entry) and reports it at its next
  * synchronizing call; the others are unaffected.  Options and kinematics of
- * the members are those at the first call; changing a member's options or the
- * shape of its insect afterwards needs a new ensemble (FLUSI_ESTATE).
+ * the members are those at the first call; changing a member's options, its
+ * tuning (flusi_set_tuning, flusi_autotune) or the shape of its insect
+ * afterwards needs a new ensemble (FLUSI_ESTATE).
  *
  * flusi_ensemble_destroy: release the ensemble (not the members).  NULL is a
  * no-op. */

@@ -1510,7 +1510,7 @@ int flusi_ensemble_step(flusi_ensemble_t e, int n)
             return ens_fail(FLUSI_ESTATE, "member " + std::to_string(i) + " is not bound or has no state");
         if (e->gexec && e->gen[i] != h->generation)
             return ens_fail(FLUSI_ESTATE, "member " + std::to_string(i) +
-                                              " changed options, workspace or insect shape; create a new ensemble");
+                                              " changed options, tuning, workspace or insect shape; create a new ensemble");
     }
     if (n == 0) return FLUSI_OK;
     if (!e->gexec) {

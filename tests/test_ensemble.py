@@ -95,5 +95,18 @@ def test_ensemble_equals_one_by_one(fl, prec):
         ens.step(1)
     assert e.value.code == fl.FLUSI_ESTATE
     ens.close()
+    # so does a member's new tuning; the asynchronous drain counts the
+    # ensemble's steps
+    ens = fl.Ensemble(solvers)
+    ens.step(2)
+    rows = torch.zeros((4, fl.FORCE_COLS), dtype=torch.float64).pin_memory().numpy()
+    assert fl.flusi_forces_async(solvers[0].h, rows) == (2, 0)
+    solvers[0].sync()
+    assert np.isfinite(rows[:2]).all() and rows[1, 0] > rows[0, 0] > 0
+    solvers[2].set_tuning(y_cols=8)
+    with pytest.raises(fl.FlusiError) as e:
+        ens.step(1)
+    assert e.value.code == fl.FLUSI_ESTATE
+    ens.close()
     for s in solvers:
         s.close()
