@@ -11,7 +11,9 @@ buffers, and the CPU oracle timed on a bounded sample.
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 
 Under torchrun (N > 1) every rank runs an independent replica on its own GPU
-(the step has no exchange) and rank 0 prints one JSON line.
+(one step has no exchange between replicas: each is a whole simulation) and
+rank 0 prints one JSON line.  The solver's FFT plans and tile shapes are
+autotuned first (flusi_autotune; --no-autotune keeps the defaults).
 """
 from __future__ import annotations
 
