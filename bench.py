@@ -132,6 +132,24 @@ def kernel_bytes(n, s, wake=False):
     return out
 
 
+# Nominal FP32 rate: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def xpass_flops(n, wake=False):
+    """Algorithmic FP32 flops of one physical x pass: per row, the 6 inverse
+    and 3 forward real transforms as half-length complex FFTs at the
+    conventional 5 m log2 m flops (m = nx/2), their mirror steps (one complex
+    multiply and three complex adds, 14 flops, per output), and per point the
+    Lamb vector, energy and max |u| (15 flops).  The penalization of masked
+    rows is left out (its share depends on the insect)."""
+    nx, ny, nz = n
+    m = nx // 2
+    lines = 9 + (6 if wake else 0)
+    per_row = lines * (5 * m * math.log2(m) + 14 * m) + 15 * nx
+    return ny * nz * per_row
+
+
 def stage_model_bytes(n, s):
     """Stage-model bytes per step: 6 inverse + 3 forward full FFTs read and
     written once, the physical pass and the spectral pass over the full half
@@ -368,6 +386,14 @@ def run_flusi(args):
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": hbm,
                 "unit": "GB/s", "frac": round(ach / hbm, 4), "traffic": traffic,
                 "algorithmic_bytes": kb[dom.split(".")[0]], "peak_source": f"{peak_src} (hbm_gbs, copy)"}
+    if dom.split(".")[0] == "xpass_phys":
+        # the same kernel against the FP32 arithmetic roofline (it is issue-bound
+        # between the two: see profiles/k_xpass_sq_512x192x192_fp32.md)
+        fl_x = xpass_flops(cfg["n"], args.wake)
+        tf = fl_x / (prof[dom] * 1e-3) / 1e12
+        roofline["alu"] = {"achieved": round(tf, 2), "peak": round(FP32_PEAK_TFLOPS, 1), "unit": "TFLOP/s",
+                           "frac": round(tf / FP32_PEAK_TFLOPS, 4), "flop_per_launch": fl_x,
+                           "peak_source": "nominal: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
     base = lambda k: k.split(".")[0]    # RK4 stages 2..4 carry a ".q" suffix
     kernels = {k: {"ms": round(v, 4),
                    "GB_s": round(kb[base(k)] / (v * 1e-3) / 1e9, 1) if kb[base(k)] else None}
