@@ -21,7 +21,8 @@
  *    across the ABI.  flusi_last_error() describes the last failure.
  *  - A handle is not thread-safe; use one host thread per handle.
  *  - Host arrays are owned by the caller and copied synchronously on the bound
- *    stream.  Device pointers passed in are owned by the caller.
+ *    stream, except by flusi_forces_async, which only enqueues its copy.
+ *    Device pointers passed in are owned by the caller.
  *  - Errors found on the device (a non-finite velocity or nonlinear term) land
  *    in a device status word; they surface at the next call that synchronizes
  *    (flusi_forces, flusi_get_state, flusi_get_spectrum, flusi_sync), after

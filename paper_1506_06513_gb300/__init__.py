@@ -482,6 +482,12 @@ class Solver:
     def forces(self, cap=4096):
         return flusi_forces(self.h, cap)
 
+    def forces_async(self, rows, start=0):
+        """Enqueue the copy of the undrained force rows into rows[start:]
+        (page-locked float64 [cap][FORCE_COLS]); returns (count, lost).  The
+        rows are there after the next synchronizing call."""
+        return flusi_forces_async(self.h, rows, start)
+
     def body(self):
         """Free flight: the body state after the enqueued steps (synchronizes)."""
         return flusi_get_body(self.h)
