@@ -69,6 +69,35 @@ def test_transform_round_trip(fl, n, L, prec):
     assert t == 0.0 and step == 0
 
 
+ODD = [((54, 27, 81), (2.0, 1.0, 3.0)),     # radix 3 only; odd y and z lengths
+       ((18, 9, 27), (2.0, 1.0, 3.0))]      # the smallest odd lengths (9 = 3 3)
+
+
+@pytest.mark.parametrize("n,L", ODD)
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_odd_lengths(fl, n, L, prec):
+    """Odd y and z lengths (radix-3 plans only, K = (n - 1)/3 ... kept modes
+    around an odd row count): the transform round trip, then three steps with
+    a sphere against the oracle."""
+    cfg = free_cfg(n, L, u_inf=(0.3, 0.0, 0.0))
+    u0 = workloads.random_smooth_field(n, 3, mean=(0.3, 0.0, 0.0))
+    ins = workloads.sphere(tuple(0.5 * x for x in L), 0.3 * min(L), profile="cos")
+    ref = oracle.Simulation(cfg, ins)
+    ref.set_state(u0)
+    sim = fl.Solver(cfg, ins, precision=prec)
+    sim.set_state(u0)
+    tol = 1e-13 if prec == "fp64" else 3e-6
+    assert rel_l2(sim.get_spectrum(), ref.uh) <= tol
+    rows_ref = ref.step(3)
+    sim.step(3)
+    rows, _ = sim.forces()
+    u = sim.get_state()[0]
+    sim.close()
+    tol_u, tol_f = (1e-11, 1e-10) if prec == "fp64" else (3e-5, 1e-4)
+    assert rel_l2(u, ref.get_state()) <= tol_u
+    assert rel_l2(rows[:, 2:20], rows_ref[:, 2:20]) <= tol_f
+
+
 def test_device_in_and_out(fl):
     """set_state / get_state with device arrays; the field's modes are all
     inside the 2/3-rule set of this grid, so it comes back unchanged."""
