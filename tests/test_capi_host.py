@@ -279,3 +279,15 @@ def test_paired_y_kernel_choice(fl, prec):
         else:
             assert _prod(t["y_radix"]) == ny
         fl.flusi_destroy(h)
+
+
+def test_async_drain_needs_a_state(fl):
+    """flusi_forces_async checks its handle before any device work."""
+    h = fl.flusi_create((16, 16, 16), (1.0, 1.0, 1.0), 0.1, 1e-2, fl.FLUSI_FP32)
+    rows = np.zeros((4, fl.FORCE_COLS))
+    with pytest.raises(fl.FlusiError) as e:
+        fl.flusi_forces_async(h, rows)
+    assert e.value.code == fl.FLUSI_ESTATE
+    with pytest.raises(ValueError):
+        fl.flusi_forces_async(h, rows, 5)
+    fl.flusi_destroy(h)
