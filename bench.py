@@ -387,8 +387,8 @@ def run_flusi(args):
                 "unit": "GB/s", "frac": round(ach / hbm, 4), "traffic": traffic,
                 "algorithmic_bytes": kb[dom.split(".")[0]], "peak_source": f"{peak_src} (hbm_gbs, copy)"}
     if dom.split(".")[0] == "xpass_phys":
-        # the same kernel against the FP32 arithmetic roofline (it is issue-bound
-        # between the two: see profiles/k_xpass_sq_512x192x192_fp32.md)
+        # the same kernel against the FP32 arithmetic roofline (it is bound by
+        # instruction issue, between the two)
         fl_x = xpass_flops(cfg["n"], args.wake)
         tf = fl_x / (prof[dom] * 1e-3) / 1e12
         roofline["alu"] = {"achieved": round(tf, 2), "peak": round(FP32_PEAK_TFLOPS, 1), "unit": "TFLOP/s",
