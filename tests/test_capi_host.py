@@ -291,3 +291,44 @@ def test_async_drain_needs_a_state(fl):
     with pytest.raises(ValueError):
         fl.flusi_forces_async(h, rows, 5)
     fl.flusi_destroy(h)
+
+
+def test_header_is_plain_c(fl, tmp_path):
+    """include/flusi.h compiles as C99 and a C program links against the
+    library and calls it (no device work: defaults, creation, sizes, tuning)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use.c"
+    src.write_text(r"""
+#include <stdio.h>
+#include "flusi.h"
+int main(void)
+{
+    flusi_options o;
+    flusi_default_options(&o);
+    double L[3] = {1.0, 1.0, 1.0};
+    flusi_t h = 0;
+    if (flusi_create(64, 48, 32, L, 0.01, 1e-2, FLUSI_FP32, &h) != FLUSI_OK) return 1;
+    size_t bytes = 0;
+    if (flusi_workspace_bytes(h, &bytes) != FLUSI_OK || bytes == 0) return 2;
+    flusi_tuning t;
+    if (flusi_get_tuning(h, &t) != FLUSI_OK || t.y_plan != 1) return 3;
+    t.y_cols = 3;
+    if (flusi_set_tuning(h, &t) != FLUSI_EINVAL) return 4;
+    if (flusi_step(h, 1) != FLUSI_ESTATE) return 5;
+    printf("%zu %d\n", bytes, t.y_tile_cols);
+    return flusi_destroy(h);
+}
+""")
+    exe = tmp_path / "use"
+    libdir = os.path.dirname(fl.LIB_PATH)
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
+                        "-o", str(exe), "-L", libdir, "-lflusi", f"-Wl,-rpath,{libdir}"],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
+    assert int(r.stdout.split()[0]) > 0
