@@ -648,6 +648,7 @@ int flusi_set_kinematics(flusi_t h, const flusi_insect* ins)
 {
     if (!h) return FLUSI_EINVAL;
     const Shape before = make_shape(h);
+    double qn = 0.0;
     if (ins) {
         if (const char* why = insect_error(*ins)) return fail(h, FLUSI_EINVAL, why);
         if (ins->free_flight != 0 && ins->free_flight != 1) return fail(h, FLUSI_EINVAL, "free_flight must be 0 or 1");
@@ -659,16 +660,23 @@ int flusi_set_kinematics(flusi_t h, const flusi_insect* ins)
                 return fail(h, FLUSI_EINVAL, "free flight needs mass > 0, J_body > 0, finite gravity, dof and "
                                              "Omega_body, and time_scheme 0");
         }
+        for (int i = 0; i < 4; ++i) qn += ins->quat[i] * ins->quat[i];
+        if (!std::isfinite(qn)) return fail(h, FLUSI_EINVAL, "bad quaternion");
+    }
+    // page-locked upload slots, before anything of the handle changes
+    if (h->bound && !h->ins_stage) {
+        CK(cudaHostAlloc(reinterpret_cast<void**>(&h->ins_stage), sizeof(flusi_insect) * kStageSlots,
+                         cudaHostAllocDefault),
+           "pinned descriptor slots");
+        for (cudaEvent_t& ev : h->stage_ev) CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "slot event");
+    }
+    if (ins) {
         h->ins = *ins;
         h->have_ins = 1;
-        double qn = 0.0;
-        for (int i = 0; i < 4; ++i) qn += ins->quat[i] * ins->quat[i];
         if (qn == 0.0) {
             quat_of_angles(ins->psi, ins->beta, ins->gamma, h->ins.quat);
-        } else {
-            if (!std::isfinite(qn)) return fail(h, FLUSI_EINVAL, "bad quaternion");
-            if (qn != 1.0)
-                for (int i = 0; i < 4; ++i) h->ins.quat[i] = ins->quat[i] / std::sqrt(qn);
+        } else if (qn != 1.0) {
+            for (int i = 0; i < 4; ++i) h->ins.quat[i] = ins->quat[i] / std::sqrt(qn);
         }
     } else {
         std::memset(&h->ins, 0, sizeof h->ins);
@@ -677,12 +685,6 @@ int flusi_set_kinematics(flusi_t h, const flusi_insect* ins)
     // the step kernels read the descriptor from device memory in stream order;
     // only the mask shape is baked into the captured kernel arguments
     if (h->bound) {
-        if (!h->ins_stage) {
-            CK(cudaHostAlloc(reinterpret_cast<void**>(&h->ins_stage), sizeof(flusi_insect) * kStageSlots,
-                             cudaHostAllocDefault),
-               "pinned descriptor slots");
-            for (cudaEvent_t& ev : h->stage_ev) CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "slot event");
-        }
         const int k = h->stage_next;
         h->stage_next = (k + 1) % kStageSlots;
         CK(cudaEventSynchronize(h->stage_ev[k]), "descriptor slot");   // its previous copy has run
