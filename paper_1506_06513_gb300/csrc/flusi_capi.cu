@@ -10,6 +10,7 @@
 #include <cstring>
 #include <fstream>
 #include <initializer_list>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <sstream>
@@ -1197,8 +1198,9 @@ int flusi_autotune(flusi_t h, int steps, const char* cache_path, flusi_tuning* o
     }
     size_t bytes = 0;
     flusi_checkpoint_bytes(h, &bytes);
-    std::vector<char> saved(bytes);
-    rc = flusi_save(h, saved.data(), bytes);
+    std::unique_ptr<char[]> saved(new (std::nothrow) char[bytes]);   // nothing throws across the ABI
+    if (!saved) return fail(h, FLUSI_ENOMEM, "no host memory for the state while tuning");
+    rc = flusi_save(h, saved.get(), bytes);
     if (rc) return rc;
     flusi_get_tuning(h, &best);
     struct Knob {
@@ -1261,12 +1263,12 @@ int flusi_autotune(flusi_t h, int steps, const char* cache_path, flusi_tuning* o
     }
     if (rc) {   // restore the state; the error stays the result
         const std::string msg = h->err;
-        if (flusi_load(h, saved.data(), bytes) == FLUSI_OK) h->err = msg;
+        if (flusi_load(h, saved.get(), bytes) == FLUSI_OK) h->err = msg;
         return rc;
     }
     rc = flusi_set_tuning(h, &best);
     if (rc) return rc;
-    rc = flusi_load(h, saved.data(), bytes);
+    rc = flusi_load(h, saved.get(), bytes);
     if (rc) return rc;
     if (out) flusi_get_tuning(h, out);
     if (cache_path) {
