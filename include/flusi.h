@@ -335,8 +335,11 @@ int flusi_kernels_per_step(flusi_t h, int *count);
  * time scheme and wake terms: a line with this handle's key is applied
  * without timing; otherwise the result is appended (a file that cannot be
  * written is FLUSI_EINVAL after the tuning is applied).  *out (may be
- * NULL) receives the chosen settings as flusi_get_tuning does.
- * Synchronizes. */
+ * NULL) receives the chosen settings as flusi_get_tuning does.  The saved
+ * state is held in host memory the call allocates and frees (two state-sized
+ * spectra; FLUSI_ENOMEM when it cannot); a failing candidate step restores
+ * the state and returns its error.  FLUSI_ESTATE without a bound workspace or
+ * a state, or on a poisoned handle.  Synchronizes. */
 #define FLUSI_MAX_STAGES 8
 typedef struct flusi_tuning {
     int y_plan, zf_plan;       /* 0, 1 (default) or 2                      */
