@@ -380,8 +380,11 @@ int flusi_autotune(flusi_t h, int steps, const char *cache_path, flusi_tuning *o
  *
  * Scratch: a fixed array of about 332 KB in the library's own device memory
  * (every GPU that loads the library holds it until the process exits).  The
- * first call on a device looks up that array's device address; make that
- * first call before any stream capture.  Every call shares the array and
+ * first call on a device looks up that array's device address, and looks it
+ * up again whenever the device's current CUDA context has changed since (after
+ * cudaDeviceReset the library's device memory is reloaded and can move); make
+ * that first call, and the first after a reset, before any stream capture.
+ * Every call shares the array and
  * leaves its contents behind, so calls that overlap on the GPU (two streams,
  * two host threads) race and corrupt each other's results.  The work is
  * enqueued on cuda_stream (NULL: legacy default stream) and the call waits for
@@ -457,6 +460,21 @@ int flusi_destroy(flusi_t h);
  * last failed call that had no handle (flusi_create, the allocation-free
  * entry point).  Valid until the next failing call of the same kind. */
 const char *flusi_last_error(flusi_t h);
+
+/* Measured arithmetic peak of the current device: the rate of independent
+ * dependent chains of fused multiply-adds in FP32 (fp64 = 0) or FP64
+ * (fp64 = 1), every SM full, in flop/s (2 per FMA) into *flops_per_s, the
+ * timed kernel's duration in ms into *ms (may be NULL).  The chain length is
+ * calibrated so that one launch takes about target_ms (0 < target_ms <= 1e4);
+ * the best of three launches counts.  A measuring aid with no counterpart in
+ * the paper: the arithmetic rooflines of the x pass and of the FP64 path are
+ * quoted against it.  Changes no clock or power setting; synchronizes. */
+int flusi_fma_peak(int fp64, double target_ms, double *flops_per_s, double *ms);
+
+/* Identity of the build: a digest of the library's sources, headers and
+ * compiler flags (the build script's source hash), or "unstamped" for a build
+ * made without it.  Lets a caller refuse a library built from other sources. */
+const char *flusi_build_id(void);
 
 #ifdef __cplusplus
 }

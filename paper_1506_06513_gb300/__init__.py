@@ -129,11 +129,18 @@ def _load():
         "flusi_ensemble_destroy": ([h], ip),
         "flusi_destroy": ([h], ip),
         "flusi_last_error": ([h], C.c_char_p),
+        "flusi_build_id": ([], C.c_char_p),
+        "flusi_fma_peak": ([ip, C.c_double, dp, dp], ip),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
         fn.argtypes = args
         fn.restype = res
+    from . import _build
+    built, want = lib.flusi_build_id().decode(), _build.source_hash()
+    if built != want:
+        raise ImportError(f"libflusi.so was built from other sources (build id {built}, sources {want}); "
+                          "rebuild it with __graft_entry__.build() or python -m paper_1506_06513_gb300._build")
     return lib
 
 
@@ -343,6 +350,17 @@ def flusi_destroy(h):
 
 def flusi_last_error(h):
     return lib.flusi_last_error(h).decode()
+
+
+def flusi_build_id():
+    return lib.flusi_build_id().decode()
+
+
+def flusi_fma_peak(fp64, target_ms=30.0):
+    """Measured FMA rate of the current device in flop/s, and the timed launch's ms."""
+    f, ms = C.c_double(), C.c_double()
+    _check(None, lib.flusi_fma_peak(int(fp64), float(target_ms), C.byref(f), C.byref(ms)))
+    return f.value, ms.value
 
 
 # ------------------------------------------------------------ descriptors

@@ -1,13 +1,16 @@
 """Build libflusi.so in-tree with nvcc for sm_103a (GB300).
 
 Each CUDA translation unit is compiled in parallel, then linked into one
-shared library next to this file.  Rebuilds only when a source is newer than
-the library.
+shared library next to this file.  The library carries the SHA-256 of the
+sources and flags it was built from (``flusi_build_id()``), and the build is
+redone whenever that differs from the sources present, so a library left over
+from other sources is never reused, whatever the file times say.
 """
 from __future__ import annotations
 
 import concurrent.futures as cf
 import glob
+import hashlib
 import os
 import shutil
 import subprocess
@@ -34,22 +37,41 @@ def sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
-        return True
-    deps = sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
-    return max(os.path.getmtime(p) for p in deps) > os.path.getmtime(LIB)
+def source_hash(extra=()) -> str:
+    """SHA-256 (hex, 32 digits) of every source, header and flag of the library."""
+    deps = sorted(sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h")))
+    h = hashlib.sha256()
+    for p in deps:
+        h.update(os.path.relpath(p, os.path.dirname(HERE)).encode())
+        with open(p, "rb") as f:
+            h.update(f.read())
+    h.update(" ".join([*ARCH, *FLAGS[:-1], *extra]).encode())
+    return h.hexdigest()[:32]
+
+
+def built_hash():
+    """The source hash a built library reports, or None."""
+    stamp = LIB + ".stamp"
+    if not (os.path.exists(LIB) and os.path.exists(stamp)):
+        return None
+    with open(stamp) as f:
+        return f.read().strip()
+
+
+def _stale(extra=()) -> bool:
+    return built_hash() != source_hash(extra)
 
 
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    if not force and not _stale():
+    if not force and not _stale(extra):
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
+    digest = source_hash(extra)
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        cmd = [cc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
+        cmd = [cc, *ARCH, *FLAGS, *extra, f'-DFLUSI_SOURCE_HASH="{digest}"', "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {os.path.basename(src)}:\n{r.stderr}")
@@ -65,6 +87,8 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(LIB + ".stamp", "w") as f:
+        f.write(digest + "\n")
     return LIB
 
 

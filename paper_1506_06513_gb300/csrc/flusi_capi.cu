@@ -664,12 +664,24 @@ int flusi_set_kinematics(flusi_t h, const flusi_insect* ins)
         for (int i = 0; i < 4; ++i) qn += ins->quat[i] * ins->quat[i];
         if (!std::isfinite(qn)) return fail(h, FLUSI_EINVAL, "bad quaternion");
     }
-    // page-locked upload slots, before anything of the handle changes
+    // page-locked upload slots, before anything of the handle changes: made
+    // into locals and handed to the handle only when every part exists, so a
+    // failure leaves the handle as it was (and the next call tries again)
     if (h->bound && !h->ins_stage) {
-        CK(cudaHostAlloc(reinterpret_cast<void**>(&h->ins_stage), sizeof(flusi_insect) * kStageSlots,
-                         cudaHostAllocDefault),
-           "pinned descriptor slots");
-        for (cudaEvent_t& ev : h->stage_ev) CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "slot event");
+        flusi_insect* stage = nullptr;
+        cudaEvent_t ev[kStageSlots] = {};
+        cudaError_t e = cudaHostAlloc(reinterpret_cast<void**>(&stage), sizeof(flusi_insect) * kStageSlots,
+                                      cudaHostAllocDefault);
+        for (int k = 0; k < kStageSlots && e == cudaSuccess; ++k)
+            e = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            for (cudaEvent_t x : ev)
+                if (x) cudaEventDestroy(x);
+            if (stage) cudaFreeHost(stage);
+            return fail(h, FLUSI_ECUDA, (std::string("pinned descriptor slots: ") + cudaGetErrorString(e)).c_str());
+        }
+        h->ins_stage = stage;
+        for (int k = 0; k < kStageSlots; ++k) h->stage_ev[k] = ev[k];
     }
     if (ins) {
         h->ins = *ins;
@@ -1559,5 +1571,10 @@ const char* flusi_last_error(flusi_t h)
 {
     return h ? h->err.c_str() : g_create_err.c_str();
 }
+
+#ifndef FLUSI_SOURCE_HASH
+#define FLUSI_SOURCE_HASH "unstamped"
+#endif
+const char* flusi_build_id(void) { return FLUSI_SOURCE_HASH; }
 
 }  // extern "C"

@@ -17,7 +17,8 @@
 //   r x chi u_s per colour, |u|^2, max |u|^2 and a non-finite flag.
 // The grid is persistent (a multiple of the SM count); each CTA writes one
 // row of partial sums, reduced in a fixed order by the scalar kernel.
-#include <atomic>
+#include <mutex>
+#include <utility>
 
 #include "fft.cuh"
 #include "kernels.cuh"
@@ -1453,9 +1454,48 @@ __global__ void k_noalloc_reduce(const double* __restrict__ part, int nparts, do
     }
 }
 
-// Device address of the scratch array, looked up once per device.
+// Device address of the scratch array, looked up once per device and CUDA
+// context.  A module's device globals live in one context: after
+// cudaDeviceReset (or any teardown of the primary context) the library's
+// module is loaded again into the new context and the array can move, so the
+// cached address is kept together with the unique id of the context it was
+// found in (cuCtxGetId) and looked up again when that id changes.
 constexpr int kNoallocMaxDevices = 64;
-std::atomic<double*> g_noalloc_ptr[kNoallocMaxDevices] = {};
+struct NoallocSlot {
+    std::mutex m;
+    unsigned long long ctx_id = 0;   // 0: nothing cached
+    double* ptr = nullptr;
+};
+NoallocSlot g_noalloc_slot[kNoallocMaxDevices];
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
+// Unique id of the calling thread's current context, or 0 when there is none
+// or the driver cannot tell (then nothing is cached).
+unsigned long long current_context_id()
+{
+    static const std::pair<CtxGetCurrentFn, CtxGetIdFn> fns = [] {
+        void* cur = nullptr;
+        void* id = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &cur, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            cur = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &id, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            id = nullptr;
+        cudaGetLastError();
+        return std::make_pair(reinterpret_cast<CtxGetCurrentFn>(cur), reinterpret_cast<CtxGetIdFn>(id));
+    }();
+    if (!fns.first || !fns.second) return 0;
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (fns.first(&ctx) != CUDA_SUCCESS || !ctx) return 0;
+    if (fns.second(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 }  // namespace
 
@@ -1483,22 +1523,32 @@ extern "C" int flusi_penalization_sums_noalloc(int nx, int ny, int nz, const dou
         return FLUSI_EINVAL;
     }
 
-    // set-up, once per device: the device address of the scratch array
+    // set-up, once per device and context: the device address of the
+    // scratch array (host code holds only a stand-in for the symbol)
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices) {
         set_global_error("flusi_penalization_sums_noalloc: no usable current device");
         return FLUSI_ECUDA;
     }
-    double* scratch = g_noalloc_ptr[dev].load(std::memory_order_acquire);
-    if (!scratch) {
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) {
-            set_global_error("flusi_penalization_sums_noalloc: cudaGetSymbolAddress failed");
-            return FLUSI_ECUDA;
+    double* scratch = nullptr;
+    {
+        NoallocSlot& slot = g_noalloc_slot[dev];
+        std::lock_guard<std::mutex> lock(slot.m);
+        const unsigned long long id = current_context_id();
+        if (slot.ptr && id != 0 && id == slot.ctx_id) {
+            scratch = slot.ptr;
+        } else {
+            void* p = nullptr;
+            const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess || !p) {
+                set_global_error("flusi_penalization_sums_noalloc: cudaGetSymbolAddress failed");
+                return FLUSI_ECUDA;
+            }
+            scratch = static_cast<double*>(p);
+            // the lookup made the device's primary context current if it was not
+            slot.ctx_id = current_context_id();
+            slot.ptr = slot.ctx_id != 0 ? scratch : nullptr;
         }
-        scratch = static_cast<double*>(p);
-        g_noalloc_ptr[dev].store(scratch, std::memory_order_release);   // the same address from any thread
     }
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
 

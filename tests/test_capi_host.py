@@ -332,3 +332,19 @@ int main(void)
     r = subprocess.run([str(exe)], capture_output=True, text=True)
     assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
     assert int(r.stdout.split()[0]) > 0
+
+
+def test_build_id_is_the_source_hash(fl):
+    """The loaded library was built from the sources present (the import
+    refuses any other); the hash changes with the flags."""
+    from paper_1506_06513_gb300 import _build
+    assert fl.flusi_build_id() == _build.source_hash() == _build.built_hash()
+    assert _build.source_hash(("-DX=1",)) != _build.source_hash()
+    assert len(fl.flusi_build_id()) == 32
+
+
+def test_fma_peak_validates_arguments(fl):
+    f = C.c_double()
+    for fp64, ms in ((2, 10.0), (0, 0.0), (1, -1.0), (0, 1e5)):
+        assert fl.lib.flusi_fma_peak(fp64, ms, C.byref(f), None) == fl.FLUSI_EINVAL
+    assert fl.lib.flusi_fma_peak(0, 10.0, None, None) == fl.FLUSI_EINVAL
