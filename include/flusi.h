@@ -50,8 +50,25 @@ typedef enum {
 } flusi_status;
 
 /* Arithmetic of the state, the FFTs and the pointwise products.  Force,
- * energy and CFL reductions and the kinematics are FP64 in both. */
-typedef enum { FLUSI_FP64 = 0, FLUSI_FP32 = 1 } flusi_precision;
+ * energy and CFL reductions and the kinematics are FP64 in all of them.
+ *  FLUSI_FP64, FLUSI_FP32: every transform and product in that precision.
+ *  FLUSI_FP32_SPLITBF16: FP32 state, y and z transforms and pointwise
+ *    products; the DFT stages of the physical x pass (the c2r transforms of
+ *    u and omega and the r2c transforms of the nonlinear term, Sec. 2.4) run
+ *    on the tensor cores as BF16 matrix products with FP32 accumulation, each
+ *    operand split into a hi + lo pair of BF16 values and the product taken
+ *    as hi*hi + hi*lo + lo*hi (relative error of a product about 2^-16).
+ *  FLUSI_FP32_SPLITBF16X3: the same with hi + mid + lo pieces and the six
+ *    products of order up to 2^-16 (error at the FP32 rounding level).
+ * The split forms need nx = 256 or 512 (else flusi_create fails with
+ * FLUSI_EINVAL); the vorticity sponge's extra x round trip, set_state and
+ * get_state transforms stay in FP32 arithmetic. */
+typedef enum {
+    FLUSI_FP64 = 0,
+    FLUSI_FP32 = 1,
+    FLUSI_FP32_SPLITBF16 = 2,
+    FLUSI_FP32_SPLITBF16X3 = 3
+} flusi_precision;
 
 /* Where an array passed to set_state / get_state lives. */
 typedef enum { FLUSI_HOST_FP64 = 0, FLUSI_HOST_FP32 = 1, FLUSI_DEVICE = 2 } flusi_where;

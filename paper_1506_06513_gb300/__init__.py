@@ -16,7 +16,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libflusi.so")
 
 FLUSI_OK, FLUSI_EINVAL, FLUSI_ENOMEM, FLUSI_ECUDA, FLUSI_ENONFINITE, FLUSI_ETIMEOUT, FLUSI_ESTATE = range(7)
-FLUSI_FP64, FLUSI_FP32 = 0, 1
+FLUSI_FP64, FLUSI_FP32, FLUSI_FP32_SPLITBF16, FLUSI_FP32_SPLITBF16X3 = 0, 1, 2, 3
+# Solver precision names and their flusi_precision values
+PRECISIONS = {"fp64": FLUSI_FP64, "fp32": FLUSI_FP32, "bf16x2": FLUSI_FP32_SPLITBF16,
+              "bf16x3": FLUSI_FP32_SPLITBF16X3}
 FLUSI_HOST_FP64, FLUSI_HOST_FP32, FLUSI_DEVICE = 0, 1, 2
 MAX_FOURIER = 8
 MAX_CONTOUR = 32
@@ -449,7 +452,9 @@ class Solver:
         import torch
         self.torch = torch
         self.cfg = cfg
-        self.prec = FLUSI_FP64 if precision == "fp64" else FLUSI_FP32
+        if precision not in PRECISIONS:
+            raise ValueError(f"precision must be one of {sorted(PRECISIONS)}")
+        self.prec = PRECISIONS[precision]
         self.n = tuple(cfg["n"])
         self.h = flusi_create(self.n, cfg["L"], cfg["nu"], cfg["eta"], self.prec)
         flusi_set_options(self.h, make_options(cfg))

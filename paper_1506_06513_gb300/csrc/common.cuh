@@ -79,6 +79,9 @@ struct Geom {
     // z tile, the shared-memory x kernel in place of the line kernel, and the
     // paired (two-CTA) y kernel where ny is even
     int ycols, zcols, xgeneric, ypair;
+    // physical x pass on the tensor cores with the operands split into xtc
+    // BF16 pieces (2 or 3); 0: FP32 (or FP64) arithmetic units
+    int xtc;
 };
 
 // Per-step geometry of the insect, written by the kinematics kernel (FP64).

@@ -243,6 +243,7 @@ void layout(flusi_t h)
     g.ypair = h->tune.y_pair;
     g.zcols = h->tune.z_cols;
     g.xgeneric = h->tune.x_kernel;
+    g.xtc = h->prec == FLUSI_FP32_SPLITBF16 ? 2 : h->prec == FLUSI_FP32_SPLITBF16X3 ? 3 : 0;
 }
 
 template <typename P> P* at(flusi_t h, size_t off) { return reinterpret_cast<P*>(h->ws + off); }
@@ -269,6 +270,8 @@ const char* kStageNames[4][8] = {
     {"kinematics.2", "zinv_curl.2", "yinv.2", "xpass_phys.2", "sponge_x.2", "yfwd.2", "zfwd.2", "update.2"},
     {"kinematics.3", "zinv_curl.3", "yinv.3", "xpass_phys.3", "sponge_x.3", "yfwd.3", "zfwd.3", "update.3"},
     {"kinematics.4", "zinv_curl.4", "yinv.4", "xpass_phys.4", "sponge_x.4", "yfwd.4", "zfwd.4", "update.4"}};
+// the physical x pass on the tensor cores (split-BF16 precisions)
+const char* kTcNames[4] = {"xpass_tc", "xpass_tc.2", "xpass_tc.3", "xpass_tc.4"};
 constexpr int kMaxStepKernels = 4 * 8 + 1;
 
 bool has_sponge(flusi_t h) { return h->opt.sponge_c > 0; }
@@ -383,7 +386,7 @@ cudaError_t enqueue_step(flusi_t h, cudaStream_t s, cudaEvent_t* ev, const char*
             return e;
         mark(nm[2]);
         if ((e = launch_ypass(fp64, true, W, g, h->py, ty, at<int>(h, h->opy), 6, st, &h->ymaps, &st->status, s, &h->pyh, at<int>(h, h->opyh)))) return e;
-        mark(nm[3]);
+        mark(g.xtc ? kTcNames[q] : nm[3]);
         if (br && (e = cudaStreamWaitEvent(s, h->ev_kin, 0))) return e;
         XExtra xe{};
         xe.frame = at<Frame>(h, h->oframe);
@@ -392,6 +395,7 @@ cudaError_t enqueue_step(flusi_t h, cudaStream_t s, cudaEvent_t* ev, const char*
         xe.comp0 = 0;
         set_wake(h, xe);
         xe.sponge_fused = has_sponge(h) && !sponge_kernel(h);
+        xe.err = &st->status;
         if ((e = launch_xpass(fp64, XP_PHYS, W, g, h->px, tx, at<int>(h, h->opx), xe, st, s))) return e;
         if (q == 0) {
             mark("scalars");
@@ -531,7 +535,9 @@ int flusi_create(int nx, int ny, int nz, const double L[3], double nu, double et
         return fail(nullptr, FLUSI_EINVAL, "each n must be 2^a 3^b in [8, 1024], nx even");
     if (!L || !(L[0] > 0) || !(L[1] > 0) || !(L[2] > 0)) return fail(nullptr, FLUSI_EINVAL, "box sides must be > 0");
     if (!(nu >= 0) || !(eta > 0)) return fail(nullptr, FLUSI_EINVAL, "need nu >= 0 and eta > 0");
-    if (precision != FLUSI_FP64 && precision != FLUSI_FP32) return fail(nullptr, FLUSI_EINVAL, "bad precision");
+    if (precision < FLUSI_FP64 || precision > FLUSI_FP32_SPLITBF16X3) return fail(nullptr, FLUSI_EINVAL, "bad precision");
+    if (precision >= FLUSI_FP32_SPLITBF16 && !xpass_tc_supported(nx))
+        return fail(nullptr, FLUSI_EINVAL, "split-BF16 tensor-core stages are built for nx = 256 and 512");
     flusi_t h = new (std::nothrow) flusi_s();
     if (!h) return fail(nullptr, FLUSI_ENOMEM, "host allocation failed");
     h->nx = nx;
@@ -601,6 +607,7 @@ int flusi_bind(flusi_t h, void* ws, size_t bytes, void* stream)
             CK(configure_ypass(), "configure y pass");
             CK(configure_zpass(), "configure z pass");
             CK(configure_xpass(), "configure x pass");
+            CK(configure_xpass_tc(), "configure tensor-core x pass");
             done.push_back(dev);
         }
     }
@@ -1120,7 +1127,8 @@ std::string tuning_key(flusi_t h)
                       h->opt.layer_width[2] > 0;
     char buf[256];
     std::snprintf(buf, sizeof buf, "%s|%d|%dx%dx%d|%s|%s|%s|d%d", name.empty() ? "gpu" : name.c_str(),
-                  prop.multiProcessorCount, h->nx, h->ny, h->nz, h->prec == FLUSI_FP64 ? "fp64" : "fp32",
+                  prop.multiProcessorCount, h->nx, h->ny, h->nz,
+                  h->prec == FLUSI_FP64 ? "fp64" : h->prec == FLUSI_FP32 ? "fp32" : h->prec == FLUSI_FP32_SPLITBF16 ? "bf16x2" : "bf16x3",
                   is_rk4(h) ? "rk4" : "ab2", wake ? "wake" : "nowake", h->opt.dealias_strict);
     return buf;
 }

@@ -109,12 +109,22 @@ struct XExtra {
     int sponge0[3];          // XP_SPONGE, or XP_PHYS with sponge_fused: sponge region
     int sponge_fused;        // XP_PHYS: also form chi_sp omega and x-transform it into W[3..5]
     double u_inf[3];
+    int* err;                // XP_PHYS on the tensor cores: status word for a wait that gives up
 };
 int xpass_fuses_sponge(int fp64, const Geom& g);
 int xpass_grid(int fp64, const Geom& g);   // CTAs of the persistent physical pass
 cudaError_t launch_xpass(int fp64, int mode, void* W, const Geom& g, const FftPlan& plan,
                          const double2* tw, const int* pos, const XExtra& ex, const StepState* st,
                          cudaStream_t s);
+
+// x pass on the tensor cores (xpass_tc.cu): the physical pass of an FP32
+// state with its DFT stages as split-BF16 tcgen05 products (g.xtc pieces),
+// for nx = 256 and 512 without the fused sponge.
+int xpass_tc_supported(int nx);
+int xpass_tc_grid(const Geom& g);
+cudaError_t launch_xpass_tc(void* W, const Geom& g, const double2* tw, const XExtra& ex, const StepState* st,
+                            cudaStream_t s);
+cudaError_t configure_xpass_tc();
 
 // Message returned by flusi_last_error(NULL).
 void set_global_error(const char* msg);

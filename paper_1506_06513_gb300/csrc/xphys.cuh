@@ -1,0 +1,283 @@
+// Physical-space pieces of the x pass shared by its kernels: the FP64 frame
+// block turned into the pass's precision, the signed distances of the
+// insect's parts and the smoothed mask (Sec. 3, Eq.
+// smoothing_mask_as_function_of_delta), the solid velocity (Eqs.
+// body_velocity_field, wing_velocity_field), and the pre- and
+// post-processing that turns a length-nx real transform into a length-nx/2
+// complex one.
+#pragma once
+
+#include "kernels.cuh"
+
+namespace flusi {
+namespace {
+
+template <typename T> struct FrameT {
+    T xc[3], uc[3], Ob[3], Mb[9], Mw[2][9], pv[2][3], Ow[2][3], box[3][6];
+    int active[3];
+    T h, a, b, c_le, c_te, R, ht, inv_eta;
+    int body_type, profile, wing_shape, ncontour;
+    T head_x0[3], head_r, eye_x0[3], eye_r;
+    T cxc, cyc, ca0, ca[FLUSI_MAX_CONTOUR], cb[FLUSI_MAX_CONTOUR];
+    T arc_r, arc_x, arc_z, arc_ux, arc_uz, arc_end[2][2];
+};
+
+// The pass's copy of the frame (FP64 on the device) and mask shape in T.
+template <typename T>
+__device__ void setup_frame(FrameT<T>& f, const Frame& F, const Shape& S, double inv_eta)
+{
+    for (int i = 0; i < 3; ++i) {
+        f.xc[i] = T(F.xc[i]);
+        f.uc[i] = T(F.uc[i]);
+        f.Ob[i] = T(F.Ob[i]);
+        f.active[i] = F.active[i];
+        for (int s2 = 0; s2 < 2; ++s2) {
+            f.pv[s2][i] = T(F.pv[s2][i]);
+            f.Ow[s2][i] = T(F.Ow[s2][i]);
+        }
+        for (int k = 0; k < 6; ++k) f.box[i][k] = T(F.box[i][k]);
+        f.head_x0[i] = T(S.head_x0[i]);
+        f.eye_x0[i] = T(S.eye_x0[i]);
+    }
+    for (int i = 0; i < 9; ++i) {
+        f.Mb[i] = T(F.Mb[i]);
+        f.Mw[0][i] = T(F.Mw[0][i]);
+        f.Mw[1][i] = T(F.Mw[1][i]);
+    }
+    f.h = T(S.h);
+    f.a = T(S.body_a);
+    f.b = T(S.body_b);
+    f.c_le = T(S.c_le);
+    f.c_te = T(S.c_te);
+    f.R = T(S.R);
+    f.ht = T(S.ht);
+    f.inv_eta = T(inv_eta);
+    f.body_type = S.body_type;
+    f.profile = S.profile;
+    f.wing_shape = S.wing_shape;
+    f.ncontour = S.ncontour;
+    f.head_r = T(S.head_r);
+    f.eye_r = T(S.eye_r);
+    f.cxc = T(S.contour_xc);
+    f.cyc = T(S.contour_yc);
+    f.ca0 = T(S.contour_a0);
+    for (int i = 0; i < FLUSI_MAX_CONTOUR; ++i) {
+        f.ca[i] = T(S.contour_a[i]);
+        f.cb[i] = T(S.contour_b[i]);
+    }
+    f.arc_r = T(S.arc_r);
+    f.arc_x = T(S.arc_x);
+    f.arc_z = T(S.arc_z);
+    f.arc_ux = T(S.arc_ux);
+    f.arc_uz = T(S.arc_uz);
+    for (int e = 0; e < 2; ++e) {
+        f.arc_end[e][0] = T(S.arc_end[e][0]);
+        f.arc_end[e][1] = T(S.arc_end[e][1]);
+    }
+    if (S.body_type == 0) f.active[0] = 0;
+    if (S.nwings < 1) f.active[1] = 0;
+    if (S.nwings < 2) f.active[2] = 0;
+}
+
+// Signed distance of the body in its frame (Sec. 3.2): thorax (sphere,
+// ellipsoid, or the ellipsoid bent along a circular arc as for the fruit fly
+// of Sec. 5.3), joined with the head and eye spheres by the minimum.
+template <typename T>
+__device__ __forceinline__ T body_delta(const FrameT<T>& F, const T* xb)
+{
+    T delta;
+    if (F.body_type == 1) {
+        delta = sqrt(xb[0] * xb[0] + xb[1] * xb[1] + xb[2] * xb[2]) - F.a;
+    } else {
+        if (F.body_type == 3) {
+            // arc length s of the point's angle about the circle's centre,
+            // from the direction u towards the body origin; the offset from
+            // the centre line in the circle's plane is r - r_c, across it y
+            const T vx = xb[0] - F.arc_x, vz = xb[2] - F.arc_z;
+            const T s = F.arc_r * atan2(vx * F.arc_uz - vz * F.arc_ux, vx * F.arc_ux + vz * F.arc_uz);
+            if (fabs(s) <= F.a) {
+                const T dr = sqrt(vx * vx + vz * vz) - F.arc_r, q = s / F.a;
+                delta = sqrt(dr * dr + xb[1] * xb[1]) - F.b * sqrt(fmax(T(0), T(1) - q * q));
+            } else {
+                const T* e = F.arc_end[s > T(0) ? 1 : 0];
+                const T ex = xb[0] - e[0], ez = xb[2] - e[1];
+                delta = sqrt(ex * ex + xb[1] * xb[1] + ez * ez);
+            }
+        } else {
+            T rr = sqrt(xb[1] * xb[1] + xb[2] * xb[2]), ax = fabs(xb[0]);
+            if (ax <= F.a) {
+                T q = xb[0] / F.a;
+                delta = rr - F.b * sqrt(fmax(T(0), T(1) - q * q));
+            } else {
+                delta = sqrt(rr * rr + (ax - F.a) * (ax - F.a));
+            }
+        }
+        if (F.head_r > T(0)) {
+            const T e0 = xb[0] - F.head_x0[0], e1 = xb[1] - F.head_x0[1], e2 = xb[2] - F.head_x0[2];
+            delta = fmin(delta, sqrt(e0 * e0 + e1 * e1 + e2 * e2) - F.head_r);
+        }
+        if (F.eye_r > T(0)) {
+            for (int s = 0; s < 2; ++s) {
+                const T y0 = s == 0 ? F.eye_x0[1] : -F.eye_x0[1];
+                const T e0 = xb[0] - F.eye_x0[0], e1 = xb[1] - y0, e2 = xb[2] - F.eye_x0[2];
+                delta = fmin(delta, sqrt(e0 * e0 + e1 * e1 + e2 * e2) - F.eye_r);
+            }
+        }
+    }
+    return delta;
+}
+
+// Signed distance of a wing in its frame (Sec. 3.4): the rectangular plate,
+// or the contour R(theta) = a0/2 + sum a_i cos(i theta) + b_i sin(i theta)
+// with cos, sin of i theta from the angle-addition recurrence.
+template <typename T>
+__device__ __forceinline__ T wing_delta(const FrameT<T>& F, const T* xw)
+{
+    const T dz = fabs(xw[2]) - T(0.5) * F.ht;
+    if (F.wing_shape == 1) {
+        const T dx = xw[0] - F.cxc, dy = xw[1] - F.cyc;
+        const T r = sqrt(dx * dx + dy * dy);
+        const T c1 = r > T(0) ? dx / r : T(1), s1 = r > T(0) ? dy / r : T(0);
+        T R = T(0.5) * F.ca0, ci = c1, si = s1;
+        for (int i = 0; i < F.ncontour; ++i) {
+            R += F.ca[i] * ci + F.cb[i] * si;
+            const T cn = ci * c1 - si * s1;
+            si = si * c1 + ci * s1;
+            ci = cn;
+        }
+        return fmax(dz, r - R);
+    }
+    return fmax(fmax(xw[0] - F.c_le, -xw[0] - F.c_te), fmax(fmax(xw[1] - F.R, -xw[1]), dz));
+}
+
+template <typename T> __device__ __forceinline__ T profile_chi(int profile, T d, T h)
+{
+    if (profile == 1) return T(0.5) * (T(1) - tanh(d / h));
+    if (d <= -h) return T(1);
+    if (d >= h) return T(0);
+    return T(0.5) * (T(1) + cospi((d + h) / (T(2) * h)));
+}
+
+template <typename T>
+__device__ __forceinline__ void cross3(const T* a, const T* b, T* c)
+{
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// Mask, colour (0 fluid, 1 body, 2/3 wings) and solid velocity at X.
+template <typename T>
+__device__ __forceinline__ void solid_at(const FrameT<T>& F, const T* X, const bool* inrow, T& chi,
+                                         int& col, T* us)
+{
+    chi = T(0);
+    col = 0;
+    us[0] = us[1] = us[2] = T(0);
+    if (!(inrow[0] | inrow[1] | inrow[2])) return;
+    T d[3] = {X[0] - F.xc[0], X[1] - F.xc[1], X[2] - F.xc[2]};
+    if (inrow[0] && X[0] >= F.box[0][0] && X[0] <= F.box[0][1]) {
+        T xb[3];
+        for (int i = 0; i < 3; ++i) xb[i] = F.Mb[3 * i] * d[0] + F.Mb[3 * i + 1] * d[1] + F.Mb[3 * i + 2] * d[2];
+        const T delta = body_delta(F, xb);
+        T c = profile_chi(F.profile, delta, F.h);
+        if (c > chi) {
+            chi = c;
+            col = 1;
+            T w[3];
+            cross3(F.Ob, d, w);
+            for (int i = 0; i < 3; ++i) us[i] = F.uc[i] + w[i];
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        if (!(inrow[1 + s] && X[0] >= F.box[1 + s][0] && X[0] <= F.box[1 + s][1])) continue;
+        const T* M = F.Mw[s];
+        T e[3] = {X[0] - F.pv[s][0], X[1] - F.pv[s][1], X[2] - F.pv[s][2]};
+        T xw[3];
+        for (int i = 0; i < 3; ++i) xw[i] = M[3 * i] * e[0] + M[3 * i + 1] * e[1] + M[3 * i + 2] * e[2];
+        const T delta = wing_delta(F, xw);
+        T c = profile_chi(F.profile, delta, F.h);
+        if (c > chi) {
+            chi = c;
+            col = 2 + s;
+            T w[3], v[3];
+            cross3(F.Ob, d, w);
+            cross3(F.Ow[s], e, v);
+            for (int i = 0; i < 3; ++i) us[i] = F.uc[i] + w[i] + v[i];
+        }
+    }
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum over the warp in the pass's own precision; the force and moment partials
+// of one warp's 64 points are added in T and only the warp totals in FP64
+// (FP64 adds are scarce on this part: a per-point FP64 accumulation cost as
+// much as the transforms of the rows that meet the insect).
+template <typename T> __device__ __forceinline__ T warp_sum_t(T v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// c2r pre-processing: Z[k] = (X[k] + X*[m]) + i (X[k] - X*[m]) w^{-k} with the
+// mirror value Xm = X[nh - k].
+template <typename T>
+__device__ __forceinline__ cplx<T> c2r_pre(cplx<T> Xk, cplx<T> Xm, cplx<T> wk)
+{
+    const cplx<T> s = cadd(Xk, cconj(Xm)), d = csub(Xk, cconj(Xm));
+    return cadd(s, cmuli(cmul(d, cconj(wk))));
+}
+
+// r2c post-processing: X[k] = E + w^k O, E = (Z[k] + Z*[m])/2, O = -i (Z[k] - Z*[m])/2.
+template <typename T>
+__device__ __forceinline__ cplx<T> r2c_post(cplx<T> Zk, cplx<T> Zm, cplx<T> wk)
+{
+    const cplx<T> zc = cconj(Zm);
+    const cplx<T> E = cscale(cadd(Zk, zc), T(0.5));
+    const cplx<T> O = cscale(cmulmi(csub(Zk, zc)), T(0.5));
+    return cadd(E, cmul(wk, O));
+}
+
+template <typename T, int R, int L>
+__device__ __forceinline__ void sq_exchange_pre(cplx<T>* x, int j, const cplx<T>* twx)
+{
+    // x[t] holds X[j + L t]; on return x[t] = Z[j + L t] (c2r pre-processing)
+#pragma unroll
+    for (int s = 0; s < R / 2; ++s) {
+        cplx<T> a, b;   // partner's X[s] and X[R-1-s]
+        a.x = __shfl_sync(0xffffffffu, x[s].x, (L - j) & (L - 1), L);
+        a.y = __shfl_sync(0xffffffffu, x[s].y, (L - j) & (L - 1), L);
+        b.x = __shfl_sync(0xffffffffu, x[R - 1 - s].x, (L - j) & (L - 1), L);
+        b.y = __shfl_sync(0xffffffffu, x[R - 1 - s].y, (L - j) & (L - 1), L);
+        if (j != 0) {
+            // mirror of element t is the partner's element R-1-t
+            const cplx<T> zs = c2r_pre<T>(x[s], b, twx[j + L * s]);
+            const cplx<T> zt = c2r_pre<T>(x[R - 1 - s], a, twx[j + L * (R - 1 - s)]);
+            x[s] = zs;
+            x[R - 1 - s] = zt;
+        }
+    }
+    if (j == 0) {
+        // mirror of element t is own element R - t (element 0 mirrors X[nh] = 0)
+        const cplx<T> z0 = c2r_pre<T>(x[0], mkc<T>(0, 0), twx[0]);
+        const cplx<T> zh = c2r_pre<T>(x[R / 2], x[R / 2], twx[L * (R / 2)]);
+#pragma unroll
+        for (int t = 1; t < R / 2; ++t) {
+            const cplx<T> za = c2r_pre<T>(x[t], x[R - t], twx[L * t]);
+            const cplx<T> zb = c2r_pre<T>(x[R - t], x[t], twx[L * (R - t)]);
+            x[t] = za;
+            x[R - t] = zb;
+        }
+        x[0] = z0;
+        x[R / 2] = zh;
+    }
+}
+
+}  // namespace
+}  // namespace flusi
