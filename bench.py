@@ -63,6 +63,12 @@ def parse():
                          "every step (mass 400, J_body (2, 5, 5), g 9.81, wing J set)")
     ap.add_argument("--shape", default=None,
                     help="nx,ny,nz: a reduced grid of the same box and insect (profiling)")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x2", "bf16x3"],
+                    help="the timed leg's form: FP32, or FP32 with the x pass's DFT stages as split-BF16 "
+                         "tensor-core products (two or three pieces)")
+    ap.add_argument("--no-split", action="store_true",
+                    help="skip the split-BF16 legs timed beside the FP32 one")
+    ap.add_argument("--split-steps", type=int, default=50)
     ap.add_argument("--fp64-steps", type=int, default=10)
     ap.add_argument("--e2e-steps", type=int, default=None,
                     help="steps of the end-to-end job (default: --steps, the device-timed job's length)")
@@ -121,6 +127,7 @@ def kernel_bytes(n, s, wake=False):
         "zinv_curl": 3 * S + 6 * A,
         "yinv": 6 * A + 6 * B,
         "xpass_phys": 6 * B + 3 * B,
+        "xpass_tc": 6 * B + 3 * B,
         "yfwd": f * B + f * A,
         "zfwd": f * A + f * S,
         "update": f * S + 2 * 3 * S + 2 * 3 * S,
@@ -148,6 +155,21 @@ def xpass_flops(n, wake=False):
     lines = 9 + (6 if wake else 0)
     per_row = lines * (5 * m * math.log2(m) + 14 * m) + 15 * nx
     return ny * nz * per_row
+
+
+def xpass_tc_flops(n, pieces):
+    """Tensor-core flops of one split-BF16 x pass (2 M N K per product of an
+    M x K and a K x N matrix): per tile of 128/Q rows (nx = 32 Q), the six
+    inverse and three forward line transforms take a 16-row stage of Q-point
+    DFTs (16/Q products of 128 x 2Q x 2Q) and a Q-row stage of 16-point DFTs
+    (one product of 128 x 32 x 32), each product taken P(P+1)/2 times over
+    the operand pieces."""
+    nx, ny, nz = n
+    Q = nx // 32
+    rows_per_tile = 128 // Q
+    tiles = -(-(ny * nz) // rows_per_tile)
+    per_line = (16 // Q) * 128 * (2 * Q) ** 2 + 128 * 32 * 32
+    return 2 * tiles * 9 * per_line * pieces * (pieces + 1) // 2
 
 
 def stage_model_bytes(n, s):
@@ -337,7 +359,7 @@ def run_flusi(args):
     hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
 
     # ---- FP32, device-resident timed region
-    sim = fl.Solver(cfg, ins, precision="fp32", device=local)
+    sim = fl.Solver(cfg, ins, precision=args.precision, device=local)
     sim.set_state(u0)
     # plans and tile shapes timed on this GPU; the state is left as it was
     tuning = sim.tuning() if args.no_autotune else sim.autotune(steps=3)
@@ -386,6 +408,14 @@ def run_flusi(args):
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": hbm,
                 "unit": "GB/s", "frac": round(ach / hbm, 4), "traffic": traffic,
                 "algorithmic_bytes": kb[dom.split(".")[0]], "peak_source": f"{peak_src} (hbm_gbs, copy)"}
+    if dom.split(".")[0] == "xpass_tc":
+        pieces = 2 if args.precision == "bf16x2" else 3
+        tfl = xpass_tc_flops(cfg["n"], pieces)
+        bf16 = float(peaks.get("bf16_tflops", 1900.0))
+        tf = tfl / (prof[dom] * 1e-3) / 1e12
+        roofline["tensor"] = {"achieved": round(tf, 2), "peak": bf16, "unit": "TFLOP/s",
+                              "frac": round(tf / bf16, 4), "flop_per_launch": tfl,
+                              "peak_source": f"{peak_src} (bf16_tflops, cuBLAS burst)"}
     if dom.split(".")[0] == "xpass_phys":
         # the same kernel against the FP32 arithmetic roofline (it is bound by
         # instruction issue, between the two)
@@ -435,6 +465,43 @@ def run_flusi(args):
     sim.close()
     del host_in, host_out
 
+    # ---- the split-BF16 forms beside it: same workload, the FP32 leg's tuning
+    split = None
+    if not args.no_split and args.precision == "fp32":
+        split = {}
+        bf16 = float(peaks.get("bf16_tflops", 1900.0))
+        for form, pieces in (("bf16x2", 2), ("bf16x3", 3)):
+            try:
+                s2 = fl.Solver(cfg, ins, precision=form, device=local)
+            except fl.FlusiError as exc:   # grids whose nx has no tensor-core x pass
+                split[form] = {"unavailable": str(exc)}
+                continue
+            s2.set_state(u0)
+            fl.flusi_set_tuning(s2.h, **{k: tuning[k] for k in fl.TUNING_SETTINGS})
+            s2.step(3)
+            s2.sync()
+            barrier()
+            torch.cuda.synchronize()
+            ev0.record(s2.stream)
+            s2.step(args.split_steps)
+            ev1.record(s2.stream)
+            torch.cuda.synchronize()
+            ms2 = allmax(ev0.elapsed_time(ev1)) / args.split_steps
+            prof2 = s2.profile(5)
+            s2.close()
+            tc_ms = prof2.get("xpass_tc")
+            tfl = xpass_tc_flops(cfg["n"], pieces)
+            split[form] = {"value": whole_job_rate(N, args.split_steps, world, ms2 * args.split_steps),
+                           "unit": UNIT, "ms_per_step": ms2, "steps": args.split_steps,
+                           "vs_fp32": ms_per_step / ms2,
+                           "kernels_ms": {k: round(v, 3) for k, v in prof2.items()},
+                           "xpass_tc": None if tc_ms is None else {
+                               "ms": round(tc_ms, 4),
+                               "GB_s": round(kb["xpass_phys"] / (tc_ms * 1e-3) / 1e9, 1),
+                               "tensor_TFLOP_s": round(tfl / (tc_ms * 1e-3) / 1e12, 2),
+                               "tensor_frac": round(tfl / (tc_ms * 1e-3) / 1e12 / bf16, 4),
+                               "flop_per_launch": tfl}}
+
     # ---- FP64 beside it
     fp64 = None
     if not args.no_fp64:
@@ -480,7 +547,8 @@ def run_flusi(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": workload_config(cfg["n"], world, args.workload, args.wake, args.flight, args.insect),
+        "config": dict(workload_config(cfg["n"], world, args.workload, args.wake, args.flight, args.insect),
+                       precision=args.precision),
         "roofline": roofline,
         "stage_model": {"bytes_per_step": stage, "frac_of_peak": round(stage / (ms_per_step * 1e-3) / 1e9 / hbm, 4),
                         "frac_of_nominal_8TBs": round(stage / (ms_per_step * 1e-3) / 8e12, 4),
@@ -489,6 +557,7 @@ def run_flusi(args):
         "kernels_ms": kernels,
         "tuning": dict(tuning, autotuned=not args.no_autotune),
         "fp64": fp64,
+        "split_bf16": split,
         "ensemble": ensemble,
         "cufft_yardstick": yardstick,
         "cpu_baseline": cpu,

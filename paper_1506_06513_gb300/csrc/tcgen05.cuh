@@ -136,6 +136,17 @@ __device__ __forceinline__ void ld4x2(unsigned taddr, unsigned off, float* re, f
     }
 }
 
+// Untiled bulk copy of `bytes` (a multiple of 16; both addresses 16-byte
+// aligned) from global into shared memory, completing on the mbarrier.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
 // Two FP32 values as a packed BF16 pair (first value in the low half, the
 // lower address), rounded to nearest even.
 __device__ __forceinline__ uint32_t pack_bf16(float lo_addr, float hi_addr)

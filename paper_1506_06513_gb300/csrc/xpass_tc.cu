@@ -51,15 +51,21 @@ template <int Q, int P> struct TcLayout {
     static constexpr unsigned kB16 = 2048;                     // 32 x 32 BF16: one piece of the 16-point matrix
     static constexpr unsigned kBQ = 8u * Q * Q;                // (2Q)^2 BF16: one piece of the Q-point matrix
     static constexpr unsigned oA = 0;                          // three operand buffers
+    static_assert(kBuf % 1024 == 0, "operand buffers stay 1 KB aligned");
     static constexpr unsigned oB16 = oA + 3 * kBuf;            // [forward, inverse][piece]
     static constexpr unsigned oBQ = oB16 + 2 * P * kB16;       // [forward, inverse][piece] when Q != 16
-    static constexpr unsigned oTwx = oBQ + (Q == 16 ? 0u : 2 * P * kBQ);
+    // input ring depth (fields in flight), as deep as two CTAs per SM allow
+    static constexpr int kSlots = P == 2 ? 3 : (Q == 16 ? 2 : 1);
+    static constexpr unsigned kMxpMax = (32u * Q / 3 + 4) / 4 * 4; // kept x-modes, padded to 4
+    static constexpr unsigned kSlot = RB * kMxpMax * 8;          // one field's rows of a tile
+    static constexpr unsigned oRing = oBQ + (Q == 16 ? 0u : 2 * P * kBQ);
+    static constexpr unsigned oTwx = oRing + kSlots * kSlot;
     static constexpr unsigned oTw2 = oTwx + 8 * NH;
     static constexpr unsigned oFrame = oTw2 + 8 * NH;
     static constexpr unsigned oWacc = (oFrame + (unsigned)sizeof(FrameT<float>) + 15) / 16 * 16;
     static constexpr unsigned oMask = oWacc + 4 * 36 * 8;
-    static constexpr unsigned oBar = (oMask + 4 * RB + 15) / 16 * 16;
-    static constexpr unsigned kBytes = oBar + 16;
+    static constexpr unsigned oBar = (oMask + 4 * RB + 15) / 16 * 16;   // kSlots + 2 mbarriers, TMEM slot
+    static constexpr unsigned kBytes = oBar + 8 * (kSlots + 2) + 16;
     static constexpr unsigned kSmem = kBytes > kTcMinSmem ? kBytes : kTcMinSmem;
 };
 
@@ -166,22 +172,27 @@ k_xpass_tc(float2* __restrict__ W, Geom g, const double2* __restrict__ tw, XExtr
     if (st && st->status != 0) return;
     using Lt = TcLayout<Q, P>;
     constexpr int NH = Lt::NH, RB = Lt::RB, G = 16 / Q;   // G: 8-line groups of the 16-row stages
+    constexpr int S = Lt::kSlots;
     constexpr unsigned SBO_Q = 32 * Q;                     // K = 2Q operands: 128 (K/8) bytes per 8 rows
+    constexpr unsigned kD1 = 192;                          // TMEM: two stage-1 accumulators of 32 columns
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     char* sm = reinterpret_cast<char*>(smem_raw);
-    char* abuf = sm + Lt::oA;
+    char* abuf = sm + Lt::oA;                              // [A1 even | A1 odd | A2]
     const char* b16f = sm + Lt::oB16;
     const char* b16i = sm + Lt::oB16 + P * Lt::kB16;
     const char* bqf = Q == 16 ? b16f : sm + Lt::oBQ;
     const char* bqi = Q == 16 ? b16i : sm + Lt::oBQ + P * Lt::kBQ;
     const unsigned bq_piece = Q == 16 ? Lt::kB16 : Lt::kBQ;
+    char* ring = sm + Lt::oRing;
     float2* twx = reinterpret_cast<float2*>(sm + Lt::oTwx);
     float2* tw2 = reinterpret_cast<float2*>(sm + Lt::oTw2);
     FrameT<float>* Fs = reinterpret_cast<FrameT<float>*>(sm + Lt::oFrame);
     double* wacc = reinterpret_cast<double*>(sm + Lt::oWacc);
     int* rowmask = reinterpret_cast<int*>(sm + Lt::oMask);
-    unsigned long long* bar = reinterpret_cast<unsigned long long*>(sm + Lt::oBar);
-    unsigned* tslot = reinterpret_cast<unsigned*>(sm + Lt::oBar + 8);
+    unsigned long long* full = reinterpret_cast<unsigned long long*>(sm + Lt::oBar);   // [S] ring slots
+    unsigned long long* bar1 = full + S;                                                // stage-1 products
+    unsigned long long* bar2 = full + S + 1;                                            // stage-2 products
+    unsigned* tslot = reinterpret_cast<unsigned*>(full + S + 2);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nx = g.nx, Mx = g.Mx, Mxp = g.Mxp;
@@ -201,36 +212,36 @@ k_xpass_tc(float2* __restrict__ W, Geom g, const double2* __restrict__ tw, XExtr
     }
     if (tid == 0) {
         setup_frame<float>(*Fs, *ex.frame, ex.shape, 1.0 / g.eta);
-        mbar_init(bar, 1);
+        for (int i = 0; i < S + 2; ++i) mbar_init(full + i, 1);
     }
     if (warp == 0) tc::tmem_alloc(tslot, kTcCols);
-    fence_proxy_async();   // the B matrices, written by this thread, before the tensor cores read them
+    fence_proxy_async();   // the B matrices, written by these threads, before the tensor cores read them
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const unsigned tb = *tslot;
     const unsigned tl = tb + ((unsigned)(warp * 32) << 16);   // this warp's quarter of the lanes
 
-    unsigned phase = 0;
+    // Input ring: load L is field L % 6 of this CTA's (L / 6)-th tile, the
+    // tile's RB rows of kept x-modes (contiguous in W) in one bulk copy.
+    int ring_hi = 0;   // thread 0: one past the last load issued
+    auto ring_issue = [&](int L) {
+        const int k = L / 6, f = L - 6 * k;
+        const int tile = blockIdx.x + k * gridDim.x;
+        if (tile >= ntiles) return;
+        ring_hi = L + 1;
+        const int r0 = tile * RB, nr = min(RB, nrows - r0);
+        const unsigned bytes = (unsigned)(nr * Mxp) * (unsigned)sizeof(float2);
+        unsigned long long* fb = full + (L % S);
+        mbar_expect_tx(fb, bytes);
+        tc::bulk_load(ring + (L % S) * Lt::kSlot, W + ((size_t)f * nrows + r0) * Mxp, bytes, fb);
+    };
+    if (tid == 0)
+        for (int L = 0; L < S; ++L) ring_issue(L);
+
+    unsigned ph1 = 0, ph2 = 0;   // completed phases of bar1, bar2
+    int ring_lo = 0;             // loads consumed
     bool timed_out = false;
-    // operands written by every thread -> one thread issues the products
-    auto issue = [&](auto products) {
-        fence_proxy_async();
-        tc::fence_before_sync();
-        __syncthreads();
-        if (tid == 0) {
-            tc::fence_after_sync();
-            products();
-            tc::commit(bar);
-        }
-    };
-    // wait for the last commit; false (for the whole CTA) when it gave up
-    auto wait_mma = [&]() -> bool {
-        const bool ok = mbar_wait(bar, phase & 1u);
-        ++phase;
-        tc::fence_after_sync();
-        return __syncthreads_or(!ok) == 0;
-    };
 
     double acc[3][12];
 #pragma unroll
@@ -248,7 +259,8 @@ k_xpass_tc(float2* __restrict__ W, Geom g, const double2* __restrict__ tw, XExtr
     constexpr uint32_t id_fwd1 = tc::idesc_bf16(128, 32, 0, 0);
     constexpr uint32_t id_fwd2 = tc::idesc_bf16(128, 2 * Q, 1, 0);
 
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    int k = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
         const int row0 = tile * RB;
         if (tid < RB) {
             const int r = row0 + tid;
@@ -264,79 +276,117 @@ k_xpass_tc(float2* __restrict__ W, Geom g, const double2* __restrict__ tw, XExtr
             rowmask[tid] = mask;
         }
 
-        // ---- inverse transforms of the six fields (u, omega): stage 2 of field
-        //      f lands in TMEM columns [32 f, 32 f + 32), stage 1 uses the next 32
+        // ---- inverse transforms of the six fields (u, omega), two deep:
+        //      iteration f forms the stage-1 operands of field f while the
+        //      tensor cores run field f-1's stage 1 and f-2's stage 2, then the
+        //      stage-2 operands of field f-1.  Stage 2 of field f lands in TMEM
+        //      columns [32 f, 32 f + 32); stage 1 alternates between [192, 224)
+        //      and [224, 256).
 #pragma unroll 1
-        for (int f = 0; f < 6; ++f) {
-            const unsigned d1 = 32u * (f + 1);
+        for (int f = 0; f <= 6; ++f) {
+            bool fail = false;
+            if (f < 6) {
+                const int L = 6 * k + f, s = L % S;
+                fail |= !mbar_wait(full + s, (unsigned)(L / S) & 1u);
+                ring_lo = L + 1;
+                const float2* rows = reinterpret_cast<const float2*>(ring + s * Lt::kSlot);
+                char* a1 = abuf + (f & 1) * Lt::kBuf;
 #pragma unroll
-            for (int gi = 0; gi < G; ++gi) {
-                const int line = 8 * gi + (tid >> 4), n1 = tid & 15;
-                const int r = row0 + line;
-                const float2* src = W + ((size_t)f * nrows + (r < nrows ? r : 0)) * Mxp;
-                float2 v[Q];
+                for (int gi = 0; gi < G; ++gi) {
+                    const int line = 8 * gi + (tid >> 4), n1 = tid & 15;
+                    const bool in = row0 + line < nrows;
+                    const float2* src = rows + line * Mxp;
+                    float2 v[Q];
 #pragma unroll
-                for (int t = 0; t < Q; ++t) {
-                    const int k = n1 + 16 * t;
-                    v[t] = (r < nrows && k < Mx) ? src[k] : make_float2(0.f, 0.f);
-                }
-                if (n1 == 0) v[0].y = 0.f;   // a real line has a real mean
-                sq_exchange_pre<float, Q, 16>(v, n1, twx);
-                // row (line, n1) of group gi: K = [Re v_t | Im v_t], t < Q
-                char* row = abuf + gi * (16 * SBO_Q) + (tid >> 3) * SBO_Q + (tid & 7) * 16;
-#pragma unroll
-                for (int kb = 0; kb < Q / 8; ++kb) {
-                    float re[8], im[8];
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        re[i] = v[8 * kb + i].x;
-                        im[i] = v[8 * kb + i].y;
+                    for (int t = 0; t < Q; ++t) {
+                        const int kx = n1 + 16 * t;
+                        v[t] = (in && kx < Mx) ? src[kx] : make_float2(0.f, 0.f);
                     }
-                    store8<P>(re, row + kb * 128, Lt::kPiece);
-                    store8<P>(im, row + (Q / 8 + kb) * 128, Lt::kPiece);
+                    if (n1 == 0) v[0].y = 0.f;   // a real line has a real mean
+                    sq_exchange_pre<float, Q, 16>(v, n1, twx);
+                    // row (line, n1) of group gi: K = [Re v_t | Im v_t], t < Q
+                    char* row = a1 + gi * (16 * SBO_Q) + (tid >> 3) * SBO_Q + (tid & 7) * 16;
+#pragma unroll
+                    for (int kb = 0; kb < Q / 8; ++kb) {
+                        float re[8], im[8];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            re[i] = v[8 * kb + i].x;
+                            im[i] = v[8 * kb + i].y;
+                        }
+                        store8<P>(re, row + kb * 128, Lt::kPiece);
+                        store8<P>(im, row + (Q / 8 + kb) * 128, Lt::kPiece);
+                    }
                 }
             }
-            issue([&] {
-                for (int gi = 0; gi < G; ++gi)
-                    mma_split<P>(tb + d1 + gi * 2 * Q, abuf + gi * (16 * SBO_Q), Lt::kPiece, SBO_Q, bqi, bq_piece,
-                                 SBO_Q, 2 * Q / 16, id_inv1);
-            });
-            if (!wait_mma()) {
+            if (f >= 1) {
+                // stage 1 of field f-1 done; stage 2 of f-2 done (its operand buffer is free)
+                fail |= !mbar_wait(bar1, ph1 & 1u);
+                ++ph1;
+                if (f >= 2) {
+                    fail |= !mbar_wait(bar2, ph2 & 1u);
+                    ++ph2;
+                }
+                tc::fence_after_sync();
+                const unsigned d1 = kD1 + 32u * ((f - 1) & 1);
+                // twiddle conj(W_NH^{n1 k1}); the row (line, n1) becomes
+                // K-row n1 of the transposed block (M = line Q + k1)
+#pragma unroll
+                for (int gi = 0; gi < G; ++gi) {
+                    const int line = 8 * gi + (tid >> 4), n1 = tid & 15;
+                    float y[2 * Q];
+                    if constexpr (Q == 16) tc::ld32(tl + d1 + gi * 2 * Q, y);
+                    else tc::ld16(tl + d1 + gi * 2 * Q, y);
+                    float re[Q], im[Q];
+#pragma unroll
+                    for (int k1 = 0; k1 < Q; ++k1) {
+                        const float2 w = tw2[n1 * k1];
+                        re[k1] = y[k1] * w.x + y[Q + k1] * w.y;
+                        im[k1] = y[Q + k1] * w.x - y[k1] * w.y;
+                    }
+#pragma unroll
+                    for (int c = 0; c < Q / 8; ++c) {
+                        const int M0 = line * Q + 8 * c;
+                        char* base = abuf + 2 * Lt::kBuf + (M0 / 8) * 512 + (n1 % 8) * 16;
+                        store8<P>(re + 8 * c, base + (n1 / 8) * 128, Lt::kPiece);
+                        store8<P>(im + 8 * c, base + ((16 + n1) / 8) * 128, Lt::kPiece);
+                    }
+                }
+            }
+            // hand the operands to the tensor cores
+            fence_proxy_async();
+            tc::fence_before_sync();
+            if (__syncthreads_or(fail)) {
                 timed_out = true;
                 break;
             }
-            // twiddle conj(W_NH^{n1 k1}); the row (line, n1) becomes K-row n1
-            // of the transposed block (M = line Q + k1)
-#pragma unroll
-            for (int gi = 0; gi < G; ++gi) {
-                const int line = 8 * gi + (tid >> 4), n1 = tid & 15;
-                float y[2 * Q];
-                if constexpr (Q == 16) tc::ld32(tl + d1 + gi * 2 * Q, y);
-                else tc::ld16(tl + d1 + gi * 2 * Q, y);
-                float re[Q], im[Q];
-#pragma unroll
-                for (int k1 = 0; k1 < Q; ++k1) {
-                    const float2 w = tw2[n1 * k1];
-                    re[k1] = y[k1] * w.x + y[Q + k1] * w.y;
-                    im[k1] = y[Q + k1] * w.x - y[k1] * w.y;
+            if (tid == 0) {
+                tc::fence_after_sync();
+                if (f < 6) ring_issue(6 * k + f + S);   // into the slot just read
+                if (f >= 1) {
+                    mma_split<P>(tb + 32u * (f - 1), abuf + 2 * Lt::kBuf, Lt::kPiece, 512, b16i, Lt::kB16, 512, 2,
+                                 id_inv2);
+                    tc::commit(bar2);
                 }
-#pragma unroll
-                for (int c = 0; c < Q / 8; ++c) {
-                    const int M0 = line * Q + 8 * c;
-                    char* base = abuf + Lt::kBuf + (M0 / 8) * 512 + (n1 % 8) * 16;
-                    store8<P>(re + 8 * c, base + (n1 / 8) * 128, Lt::kPiece);
-                    store8<P>(im + 8 * c, base + ((16 + n1) / 8) * 128, Lt::kPiece);
+                if (f < 6) {
+                    const unsigned d1 = kD1 + 32u * (f & 1);
+                    for (int gi = 0; gi < G; ++gi)
+                        mma_split<P>(tb + d1 + gi * 2 * Q, abuf + (f & 1) * Lt::kBuf + gi * (16 * SBO_Q),
+                                     Lt::kPiece, SBO_Q, bqi, bq_piece, SBO_Q, 2 * Q / 16, id_inv1);
+                    tc::commit(bar1);
                 }
             }
-            issue([&] {
-                mma_split<P>(tb + 32u * f, abuf + Lt::kBuf, Lt::kPiece, 512, b16i, Lt::kB16, 512, 2, id_inv2);
-            });
-            if (!wait_mma()) {
+        }
+        if (timed_out) break;
+        {
+            const bool ok = mbar_wait(bar2, ph2 & 1u);   // stage 2 of field 5
+            ++ph2;
+            tc::fence_after_sync();
+            if (__syncthreads_or(!ok)) {
                 timed_out = true;
                 break;
             }
         }
-        if (timed_out) break;
 
         // ---- physical space: lane (line, k1) holds the pairs k1 + Q k2 of
         //      every field; NL into the forward stage-1 operands (row = lane)
@@ -433,15 +483,20 @@ k_xpass_tc(float2* __restrict__ W, Geom g, const double2* __restrict__ tw, XExtr
         }
 
         // ---- forward transforms of the three NL fields: stage 1 into the
-        //      columns of u, stage 2 into those of omega
-        issue([&] {
+        //      columns of u, stage 2 into those of omega; the stage-2 operands
+        //      of a field are formed while the previous field's product runs
+        fence_proxy_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
             for (int q = 0; q < 3; ++q)
                 mma_split<P>(tb + 32u * q, abuf + q * Lt::kBuf, Lt::kPiece, 512, b16f, Lt::kB16, 512, 2, id_fwd1);
-        });
-        if (!wait_mma()) {
-            timed_out = true;
-            break;
+            tc::commit(bar1);
         }
+        bool fail = !mbar_wait(bar1, ph1 & 1u);
+        ++ph1;
+        tc::fence_after_sync();
         {
             const int line = tid / Q, n1 = tid % Q;
 #pragma unroll 1
@@ -450,12 +505,12 @@ k_xpass_tc(float2* __restrict__ W, Geom g, const double2* __restrict__ tw, XExtr
                 tc::ld32(tl + 32u * q, y);
                 float re[16], im[16];
 #pragma unroll
-                for (int k = 0; k < 16; ++k) {
-                    const float2 w = tw2[n1 * k];
-                    re[k] = y[k] * w.x - y[16 + k] * w.y;
-                    im[k] = y[k] * w.y + y[16 + k] * w.x;
+                for (int kk = 0; kk < 16; ++kk) {
+                    const float2 w = tw2[n1 * kk];
+                    re[kk] = y[kk] * w.x - y[16 + kk] * w.y;
+                    im[kk] = y[kk] * w.y + y[16 + kk] * w.x;
                 }
-                // transposed block of group line / 8: M = (line % 8) 16 + k, K = n1 (Re), Q + n1 (Im)
+                // transposed block of group line / 8: M = (line % 8) 16 + kk, K = n1 (Re), Q + n1 (Im)
                 char* base = abuf + q * Lt::kBuf + (line / 8) * (16 * SBO_Q) + (n1 % 8) * 16;
 #pragma unroll
                 for (int c = 0; c < 2; ++c) {
@@ -463,17 +518,30 @@ k_xpass_tc(float2* __restrict__ W, Geom g, const double2* __restrict__ tw, XExtr
                     store8<P>(re + 8 * c, base + (M0 / 8) * SBO_Q + (n1 / 8) * 128, Lt::kPiece);
                     store8<P>(im + 8 * c, base + (M0 / 8) * SBO_Q + ((Q + n1) / 8) * 128, Lt::kPiece);
                 }
+                fence_proxy_async();
+                tc::fence_before_sync();
+                if (__syncthreads_or(fail)) {
+                    timed_out = true;
+                    break;
+                }
+                if (tid == 0) {
+                    tc::fence_after_sync();
+                    for (int gi = 0; gi < G; ++gi)
+                        mma_split<P>(tb + 96u + 32u * q + gi * 2 * Q, abuf + q * Lt::kBuf + gi * (16 * SBO_Q),
+                                     Lt::kPiece, SBO_Q, bqf, bq_piece, SBO_Q, 2 * Q / 16, id_fwd2);
+                    if (q == 2) tc::commit(bar2);
+                }
             }
         }
-        issue([&] {
-            for (int q = 0; q < 3; ++q)
-                for (int gi = 0; gi < G; ++gi)
-                    mma_split<P>(tb + 96u + 32u * q + gi * 2 * Q, abuf + q * Lt::kBuf + gi * (16 * SBO_Q),
-                                 Lt::kPiece, SBO_Q, bqf, bq_piece, SBO_Q, 2 * Q / 16, id_fwd2);
-        });
-        if (!wait_mma()) {
-            timed_out = true;
-            break;
+        if (timed_out) break;
+        {
+            const bool ok = mbar_wait(bar2, ph2 & 1u);
+            ++ph2;
+            tc::fence_after_sync();
+            if (__syncthreads_or(!ok)) {
+                timed_out = true;
+                break;
+            }
         }
         // ---- r2c post-processing and the store of the kept x-modes: lane
         //      (line, j) holds Z[j + 16 k2], k2 < Q
@@ -517,11 +585,15 @@ k_xpass_tc(float2* __restrict__ W, Geom g, const double2* __restrict__ tw, XExtr
     }
 
     if (timed_out) {
-        // a product that never completed: report, wait once more (bounded)
-        // for what is in flight, give the tensor memory back and leave
+        // a product or a copy that never completed: report, wait once more
+        // (bounded) for what is in flight, give the tensor memory back, leave
         if (tid == 0) {
             atomicCAS(ex.err, 0, (int)FLUSI_ETIMEOUT);
-            mbar_wait(bar, (phase - 1) & 1u);
+            mbar_wait(bar1, ph1 & 1u);
+            mbar_wait(bar2, ph2 & 1u);
+            // input copies still on their way into this CTA's shared memory
+            for (int L = ring_lo - 1 < 0 ? 0 : ring_lo - 1; L < ring_hi; ++L)
+                mbar_wait(full + L % S, (unsigned)(L / S) & 1u);
         }
         tc::fence_before_sync();
         __syncthreads();
@@ -537,9 +609,9 @@ k_xpass_tc(float2* __restrict__ W, Geom g, const double2* __restrict__ tw, XExtr
 #pragma unroll
     for (int cc = 0; cc < 3; ++cc)
 #pragma unroll
-        for (int k = 0; k < 12; ++k) {
-            const double s = warp_sum(acc[cc][k]);
-            if (lane == 0) wacc[warp * 36 + cc * 12 + k] = s;
+        for (int kk = 0; kk < 12; ++kk) {
+            const double s2 = warp_sum(acc[cc][kk]);
+            if (lane == 0) wacc[warp * 36 + cc * 12 + kk] = s2;
         }
     e_acc = warp_sum(e_acc);
     double m_d = double(m_acc);
@@ -584,6 +656,26 @@ cudaError_t launch_tc_qp(bool layer, float2* W, const Geom& g, const double2* tw
     return cudaGetLastError();
 }
 
+// Resident CTAs per SM (at most two: two CTAs of 256 TMEM columns fill an
+// SM's 512), from the SM's shared memory and registers.
+template <int Q, int P> int tc_per_sm()
+{
+    int dev = 0, smem_sm = 0, reserved = 0, regs_sm = 0;
+    cudaFuncAttributes fa{};
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, k_xpass_tc<Q, P, false>) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    const size_t per_cta = TcLayout<Q, P>::kSmem + fa.sharedSizeBytes + (size_t)reserved;
+    const int warp_regs = (fa.numRegs * 32 + 255) / 256 * 256;   // allocation granularity
+    const bool two = 2 * per_cta <= (size_t)smem_sm && 2 * 4 * warp_regs <= regs_sm;
+    return two ? 2 : 1;
+}
+
 }  // namespace
 
 int xpass_tc_supported(int nx) { return nx == 512 || nx == 256; }
@@ -594,9 +686,12 @@ int xpass_tc_grid(const Geom& g)
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev);
     if (sm_count <= 0) sm_count = 1;
+    int per_sm = 1;
+    if (g.nx == 512) per_sm = g.xtc == 3 ? tc_per_sm<16, 3>() : tc_per_sm<16, 2>();
+    else per_sm = g.xtc == 3 ? tc_per_sm<8, 3>() : tc_per_sm<8, 2>();
     const int RB = 128 / (g.nx / 32);
     const int ntiles = ceil_div(g.nz * g.ny, RB);
-    const int grid = 2 * sm_count;   // two CTAs of 256 TMEM columns fill an SM's 512
+    const int grid = per_sm * sm_count;
     return grid < ntiles ? grid : ntiles;
 }
 
@@ -607,6 +702,12 @@ cudaError_t launch_xpass_tc(void* W, const Geom& g, const double2* tw, const XEx
     const bool layer = ex.layer0[0] < g.nx || ex.layer0[1] < g.ny || ex.layer0[2] < g.nz;
     const int grid = xpass_tc_grid(g);
     if (!ex.err || ex.sponge_fused) return cudaErrorInvalidValue;
+    // the input ring's bulk copies need 16-byte aligned rows that fit a slot
+    if ((reinterpret_cast<uintptr_t>(W) & 15) != 0 || (g.Mxp * sizeof(float2)) % 16 != 0)
+        return cudaErrorInvalidValue;
+    if ((g.nx == 512 && (unsigned)g.Mxp > TcLayout<16, 2>::kMxpMax) ||
+        (g.nx == 256 && (unsigned)g.Mxp > TcLayout<8, 2>::kMxpMax))
+        return cudaErrorInvalidValue;
     if (g.nx == 512 && g.xtc == 2) return launch_tc_qp<16, 2>(layer, w, g, tw, ex, st, s, grid);
     if (g.nx == 512 && g.xtc == 3) return launch_tc_qp<16, 3>(layer, w, g, tw, ex, st, s, grid);
     if (g.nx == 256 && g.xtc == 2) return launch_tc_qp<8, 2>(layer, w, g, tw, ex, st, s, grid);
@@ -617,12 +718,19 @@ cudaError_t launch_xpass_tc(void* W, const Geom& g, const double2* tw, const XEx
 cudaError_t configure_xpass_tc()
 {
     cudaError_t e;
+    // the largest shared-memory carveout, so that two CTAs fit an SM
 #define FLUSI_TC_SMEM(Q, P)                                                                                \
     if ((e = cudaFuncSetAttribute(k_xpass_tc<Q, P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
                                   TcLayout<Q, P>::kSmem)))                                                 \
         return e;                                                                                          \
     if ((e = cudaFuncSetAttribute(k_xpass_tc<Q, P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
                                   TcLayout<Q, P>::kSmem)))                                                 \
+        return e;                                                                                          \
+    if ((e = cudaFuncSetAttribute(k_xpass_tc<Q, P, false>, cudaFuncAttributePreferredSharedMemoryCarveout, \
+                                  (int)cudaSharedmemCarveoutMaxShared)))                                   \
+        return e;                                                                                          \
+    if ((e = cudaFuncSetAttribute(k_xpass_tc<Q, P, true>, cudaFuncAttributePreferredSharedMemoryCarveout,  \
+                                  (int)cudaSharedmemCarveoutMaxShared)))                                   \
         return e;
     FLUSI_TC_SMEM(16, 2)
     FLUSI_TC_SMEM(16, 3)

@@ -22,7 +22,9 @@ def test_xpass_bytes_512():
     A, B = 512 * 341 * row, 512 * 512 * row
     assert kb["yinv"] == 6 * A + 6 * B
     assert kb["zinv_curl"] == 3 * 341 * 341 * row + 6 * A
-    assert sum(kb.values()) == 14094707832
+    # the step runs one of the two x kernels (CUDA-core or tensor-core), same bytes
+    assert kb["xpass_tc"] == kb["xpass_phys"]
+    assert sum(v for k, v in kb.items() if k != "xpass_tc") == 14094707832
 
 
 def test_xpass_flops_512():
@@ -38,3 +40,15 @@ def test_xpass_flops_512():
 
 def test_fp32_peak():
     assert math.isclose(bench.FP32_PEAK_TFLOPS, 80.54784)
+
+
+def test_xpass_tc_flops():
+    """Tensor-core flops of the split-BF16 x pass, counted by hand at 512^3:
+    32 768 tiles of 8 rows, per line two products of 128 x 32 x 32 (the two
+    16-point stages), 2 flops per multiply-add, three piece products (hi+lo)
+    or six (hi+mid+lo)."""
+    per_line = 2 * 128 * 32 * 32
+    assert bench.xpass_tc_flops((512, 512, 512), 2) == 2 * 32768 * 9 * per_line * 3
+    assert bench.xpass_tc_flops((512, 512, 512), 3) == 2 * bench.xpass_tc_flops((512, 512, 512), 2)
+    # nx = 256: 16-row tiles, a stage of two 128 x 16 x 16 products and one of 128 x 32 x 32
+    assert bench.xpass_tc_flops((256, 16, 16), 2) == 2 * 16 * 9 * (2 * 128 * 16 * 16 + 128 * 32 * 32) * 3
