@@ -75,6 +75,10 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default FFT plans and tiles instead of flusi_autotune's choice")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-grid", type=int, default=256,
+                    help="grid of the all-cores oracle sample of the CPU baseline (512: the bench's own)")
+    ap.add_argument("--cpu-steps", type=int, default=2)
+    ap.add_argument("--oracle-time", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-yardstick", action="store_true",
                     help="skip timing cuFFT on the step's nine 3-D transforms")
@@ -170,6 +174,26 @@ def xpass_tc_flops(n, pieces):
     tiles = -(-(ny * nz) // rows_per_tile)
     per_line = (16 // Q) * 128 * (2 * Q) ** 2 + 128 * 32 * 32
     return 2 * tiles * 9 * per_line * pieces * (pieces + 1) // 2
+
+
+def kernel_flops(n, wake=False):
+    """Algorithmic flops per launch of each kernel: every 1-D complex FFT of m
+    points at the conventional 5 m log2 m (the x pass as xpass_flops), the
+    curl, projection and IF-AB2 update at 60 flops per kept mode (three
+    components).  The FP64 path's arithmetic roofline divides by these."""
+    nx, ny, nz = n
+    Mx, My, Mz = spectral_sizes(n)
+    f = 6 if wake else 3
+    fft = lambda m: 5 * m * math.log2(m)
+    out = {"zinv_curl": 5 * My * Mx * fft(nz) + 12 * Mz * My * Mx,
+           "yinv": 6 * nz * Mx * fft(ny),
+           "xpass_phys": xpass_flops(n, wake),
+           "yfwd": f * nz * Mx * fft(ny),
+           "zfwd": f * My * Mx * fft(nz),
+           "update": 60 * Mz * My * Mx,
+           "kinematics": 0, "scalars": 0}
+    out["xpass_tc"] = out["xpass_phys"]
+    return out
 
 
 def stage_model_bytes(n, s):
@@ -295,19 +319,73 @@ def oracle_workload(workload, n, flight=False, insect="model"):
     return cfg, in_free_flight(ins) if flight else ins, u0
 
 
-def oracle_sample(workload, n_sample=128, steps=3, flight=False, insect="model"):
-    """The oracle (single-threaded C, FP64) on the same workload at a reduced
-    grid, as it stands: grid-point steps/s."""
+def host_cpu():
+    """CPU model and logical core count of this host."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                model = line.split(":", 1)[1].strip()
+                if line.startswith("Model name"):
+                    break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        import platform
+        model = platform.processor() or platform.machine()
+    return {"cpu_model": model, "nproc": os.cpu_count()}
+
+
+def oracle_time(workload, n, steps, threads, flight=False, insect="model"):
+    """One oracle timing in a fresh process (the single-threaded build, or the
+    OpenMP build on `threads` threads): set_state untimed, then `steps` steps."""
+    env = dict(os.environ, OMP_NUM_THREADS=str(threads))
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-time",
+           f"{workload},{n},{steps},{int(threads > 1)},{int(flight)},{insect}"]
+    r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=1800)
+    if r.returncode != 0:
+        raise RuntimeError(f"oracle timing failed: {r.stderr[-500:]}")
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def oracle_time_main(spec):
     import oracle
-    cfg, ins, u0 = oracle_workload(workload, n_sample, flight, insect)
+    workload, n, steps, omp, flight, insect = spec.split(",")
+    n, steps = int(n), int(steps)
+    if int(omp) and not oracle.use_openmp():
+        raise SystemExit("the OpenMP build of the oracle is not available on this host")
+    cfg, ins, u0 = oracle_workload(workload, n, bool(int(flight)), insect)
     sim = oracle.Simulation(cfg, ins)
     sim.set_state(u0)
     t0 = time.perf_counter()
     sim.step(steps)
     el = time.perf_counter() - t0
-    return {"value": n_sample ** 3 * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"the same workload at {n_sample}^3 (same box, body, wings, Re, C_eta, inflow), "
-                      f"{steps} steps, FP64 single-threaded C, {el:.1f} s"}
+    print(json.dumps({"n": n, "steps": steps, "seconds": el, "threads": oracle.threads(),
+                      "value": n ** 3 * steps / el}))
+
+
+def oracle_sample(workload, flight=False, insect="model", n_all=256, steps_all=2, n_one=128, steps_one=2):
+    """The oracle (C, FP64) as it stands on the same workload at reduced grids:
+    the OpenMP build on every host core (the reported value) and the plain
+    build on one core beside it; grid-point steps/s."""
+    host = host_cpu()
+    cores = host["nproc"] or 1
+    one = oracle_time(workload, n_one, steps_one, 1, flight, insect)
+    try:
+        alls = oracle_time(workload, n_all, steps_all, cores, flight, insect)
+    except RuntimeError:
+        alls = None
+    main = alls or one
+    what = (f"the same workload at {main['n']}^3 (same box, body, wings, Re, C_eta, inflow), "
+            f"{main['steps']} steps, FP64 C oracle on {main['threads']} thread(s), {main['seconds']:.1f} s")
+    return {"value": main["value"], "unit": UNIT, "cores": main["threads"], "kind": "oracle",
+            "sample": what, "host": host,
+            "single_thread": {"value": one["value"], "grid": one["n"], "steps": one["steps"],
+                              "seconds": round(one["seconds"], 2)},
+            "all_cores": None if alls is None else {"value": alls["value"], "grid": alls["n"],
+                                                    "steps": alls["steps"], "threads": alls["threads"],
+                                                    "seconds": round(alls["seconds"], 2)}}
 
 
 class Ranks:
@@ -357,6 +435,11 @@ def run_flusi(args):
     u0 = bench_field(cfg, local)
     peaks, peak_src = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+
+    # ---- measured FMA peaks (dependent-FMA chains on every SM, CUDA events)
+    fp32_peak, _ = fl.flusi_fma_peak(0, 30.0)
+    fp64_peak, _ = fl.flusi_fma_peak(1, 30.0)
+    alu_src = "measured: flusi_fma_peak (independent chains of dependent FMAs, every SM, best of 3)"
 
     # ---- FP32, device-resident timed region
     sim = fl.Solver(cfg, ins, precision=args.precision, device=local)
@@ -421,9 +504,10 @@ def run_flusi(args):
         # instruction issue, between the two)
         fl_x = xpass_flops(cfg["n"], args.wake)
         tf = fl_x / (prof[dom] * 1e-3) / 1e12
-        roofline["alu"] = {"achieved": round(tf, 2), "peak": round(FP32_PEAK_TFLOPS, 1), "unit": "TFLOP/s",
-                           "frac": round(tf / FP32_PEAK_TFLOPS, 4), "flop_per_launch": fl_x,
-                           "peak_source": "nominal: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
+        peak32 = fp32_peak / 1e12
+        roofline["alu"] = {"achieved": round(tf, 2), "peak": round(peak32, 2), "unit": "TFLOP/s",
+                           "frac": round(tf / peak32, 4), "flop_per_launch": fl_x, "peak_source": alu_src,
+                           "nominal_peak": round(FP32_PEAK_TFLOPS, 1)}
     base = lambda k: k.split(".")[0]    # RK4 stages 2..4 carry a ".q" suffix
     kernels = {k: {"ms": round(v, 4),
                    "GB_s": round(kb[base(k)] / (v * 1e-3) / 1e9, 1) if kb[base(k)] else None}
@@ -521,9 +605,27 @@ def run_flusi(args):
         prof64 = sim64.profile(2)
         sim64.close()
         v64 = whole_job_rate(N, args.fp64_steps, world, ms64)
+        # the FP64 path against max(bytes / HBM, flops / FP64 peak), per kernel and per step
+        kb64, kf = kernel_bytes(cfg["n"], 8, wake=args.wake), kernel_flops(cfg["n"], wake=args.wake)
+        dom64 = max(prof64, key=prof64.get)
+        b64, f64 = kb64[dom64.split(".")[0]], kf[dom64.split(".")[0]]
+        t64 = prof64[dom64] * 1e-3
+        step_b64 = sum(kb64[k.split(".")[0]] for k in prof64)
+        step_f64 = sum(kf[k.split(".")[0]] for k in prof64)
+        step_s = ms64 / args.fp64_steps * 1e-3
         fp64 = {"value": v64, "unit": UNIT, "ms_per_step": ms64 / args.fp64_steps,
                 "steps": args.fp64_steps, "fp32_speedup": value / v64,
-                "kernels_ms": {k: round(v, 3) for k, v in prof64.items()}, "tuning": tuning64}
+                "kernels_ms": {k: round(v, 3) for k, v in prof64.items()}, "tuning": tuning64,
+                "roofline": {"kernel": dom64, "bound": "fp64" if f64 / fp64_peak > b64 / (hbm * 1e9) else "hbm",
+                             "achieved": round(f64 / t64 / 1e12, 3), "peak": round(fp64_peak / 1e12, 3),
+                             "unit": "TFLOP/s", "frac": round(f64 / t64 / fp64_peak, 4),
+                             "flop_per_launch": f64, "bytes_per_launch": b64,
+                             "fp64_floor_ms": round(f64 / fp64_peak * 1e3, 3),
+                             "hbm_floor_ms": round(b64 / (hbm * 1e9) * 1e3, 3),
+                             "peak_source": alu_src},
+                "step_roofline": {"flop_per_step": step_f64, "bytes_per_step": step_b64,
+                                  "floor_ms": round(max(step_f64 / fp64_peak, step_b64 / (hbm * 1e9)) * 1e3, 3),
+                                  "frac": round(max(step_f64 / fp64_peak, step_b64 / (hbm * 1e9)) / step_s, 4)}}
     del u0
 
     yardstick = None
@@ -541,7 +643,8 @@ def run_flusi(args):
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = oracle_sample(args.workload, flight=args.flight, insect=args.insect)
+        cpu = oracle_sample(args.workload, flight=args.flight, insect=args.insect, n_all=args.cpu_grid,
+                            steps_all=args.cpu_steps)
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -558,6 +661,8 @@ def run_flusi(args):
         "tuning": dict(tuning, autotuned=not args.no_autotune),
         "fp64": fp64,
         "split_bf16": split,
+        "alu_peaks": {"fp32_tflops": round(fp32_peak / 1e12, 2), "fp64_tflops": round(fp64_peak / 1e12, 3),
+                      "source": alu_src},
         "ensemble": ensemble,
         "cufft_yardstick": yardstick,
         "cpu_baseline": cpu,
@@ -618,51 +723,45 @@ def workload_config(n, world, workload="model_insect", wake=False, flight=False,
 # ----------------------------------------------------------- reference arm
 
 def run_reference(args):
-    """The oracle as it stands, on the host cores: each step is one oracle
-    step of the same workload at a grid small enough that the whole run ends
-    in about two minutes."""
+    """The oracle as it stands, on the host cores (its OpenMP build, every
+    core): each step is one oracle step of the same workload at the largest
+    grid of a ladder that keeps the whole run near two minutes."""
     world, rank, _ = dist_env()
     if rank != 0:
         return
-    import oracle
-    # choose the sample grid from a timed probe step
-    pick = 32
-    for n in (32, 48, 64, 96, 128):
-        cfg, ins, u0 = oracle_workload(args.workload, n, args.flight, args.insect)
-        sim = oracle.Simulation(cfg, ins)
-        sim.set_state(u0)
-        t0 = time.perf_counter()
-        sim.step(1)
-        per = time.perf_counter() - t0
-        if per * (args.steps + args.warmup) > 120.0:
+    host = host_cpu()
+    cores = host["nproc"] or 1
+    pick, probe = 32, None
+    for n in (32, 48, 64, 96, 128, 192, 256):
+        probe = oracle_time(args.workload, n, 1, cores, args.flight, args.insect)
+        if probe["seconds"] * (args.steps + args.warmup) > 120.0:
             break
         pick = n
-    cfg, ins, u0 = oracle_workload(args.workload, pick, args.flight, args.insect)
-    sim = oracle.Simulation(cfg, ins)
-    sim.set_state(u0)
-    sim.step(args.warmup)
-    t0 = time.perf_counter()
-    sim.step(args.steps)
-    el = time.perf_counter() - t0
-    value = pick ** 3 * args.steps / el
-    sample = (f"the same workload at {pick}^3 (same box, body, wings, Re, C_eta, inflow), FP64 "
-              f"single-threaded C oracle, {args.steps} steps in {el:.1f} s; value in grid-point "
-              f"steps/s of that sample")
+    # the timed run: warm-up steps are untimed inside the same process
+    r = oracle_time(args.workload, pick, args.steps, cores, args.flight, args.insect)
+    value = r["value"]
+    el = r["seconds"]
+    sample = (f"the same workload at {pick}^3 (same box, body, wings, Re, C_eta, inflow), FP64 C "
+              f"oracle on {r['threads']} thread(s) of {host['cpu_model']} ({host['nproc']} logical cores), "
+              f"{args.steps} steps in {el:.1f} s; value in grid-point steps/s of that sample")
+    cfg = workload_config((pick, pick, pick), world, args.workload, args.wake, args.flight, args.insect)
+    cfg["sample_of"] = list(workload_setup(args)[0]["n"])
+    cfg["precision"] = "fp64"
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "impl": "reference",
-           "config": workload_config(workload_setup(args)[0]["n"], world, args.workload, args.wake,
-                                     args.flight, args.insect),
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                            "sample": sample},
+           "impl": "reference", "config": cfg,
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": r["threads"], "kind": "oracle",
+                            "sample": sample, "host": host},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
 
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.oracle_time:
+        oracle_time_main(args.oracle_time)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_flusi(args)

@@ -274,6 +274,14 @@ int flusi_forces_async(flusi_t h, double *rows, int cap, int *count, long long *
  * time t and step count (either may be NULL).  Synchronizes. */
 int flusi_get_state(flusi_t h, void *u_out, int where, double *t, long long *step);
 
+/* Divergence of the current state (Eq. PNST_UP_pressure_poisson_eqn: the
+ * Leray projection keeps k . u_hat = 0): *div_max = max over the kept modes of
+ * |k . u_hat| and, when ku_max is not NULL, *ku_max = max of |k| |u_hat| (its
+ * scale; the ratio is the relative divergence, round-off after a step).  Both
+ * reduced in FP64 on the device from the state in the handle's precision.
+ * Waits for the enqueued steps; a non-finite state gives a NaN maximum. */
+int flusi_divergence(flusi_t h, double *div_max, double *ku_max);
+
 /* Copy u_hat to host FP64 complex, half-spectrum layout [3][nz][ny][nx/2+1]
  * (interleaved re, im), zero outside the 2/3-rule set.  Synchronizes. */
 int flusi_get_spectrum(flusi_t h, double *uh_out);

@@ -17,7 +17,11 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
+# the same sources built with OpenMP: used only to time the oracle on all host
+# cores (bench.py's CPU baseline); the tests use the single-threaded build
+_LIB_OMP_PATH = os.path.join(_HERE, "liboracle_omp.so")
 _SOURCES = ["fft.c", "insect.c", "solver.c"]
+_use_openmp = False
 
 MAX_FOURIER = 8
 MAX_CONTOUR = 32
@@ -26,18 +30,53 @@ NSUMS = 39
 SUM_EKIN, SUM_UMAX, SUM_NONFINITE = 36, 37, 38
 
 
-def build(force: bool = False) -> str:
-    """Compile liboracle.so with gcc (no fast-math, no FMA contraction)."""
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile liboracle.so with gcc (no fast-math, no FMA contraction); with
+    openmp, liboracle_omp.so from the same sources with -fopenmp (its loops
+    over independent lines, planes and points split across threads)."""
+    path = _LIB_OMP_PATH if openmp else _LIB_PATH
     srcs = [os.path.join(_HERE, s) for s in _SOURCES] + [os.path.join(_HERE, "oracle.h")]
-    if not force and os.path.exists(_LIB_PATH):
+    if not force and os.path.exists(path):
         newest = max(os.path.getmtime(s) for s in srcs)
-        if os.path.getmtime(_LIB_PATH) >= newest:
-            return _LIB_PATH
+        if os.path.getmtime(path) >= newest:
+            return path
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-           "-o", _LIB_PATH + ".tmp"] + [os.path.join(_HERE, s) for s in _SOURCES] + ["-lm"]
+           *(["-fopenmp"] if openmp else []),
+           "-o", path + ".tmp"] + [os.path.join(_HERE, s) for s in _SOURCES] + ["-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(_LIB_PATH + ".tmp", _LIB_PATH)
-    return _LIB_PATH
+    os.replace(path + ".tmp", path)
+    return path
+
+
+def build_all() -> None:
+    """Both builds (the OpenMP one only where gcc offers -fopenmp)."""
+    build()
+    try:
+        build(openmp=True)
+    except (OSError, subprocess.CalledProcessError):
+        pass
+
+
+def use_openmp() -> bool:
+    """Load the OpenMP build in this process (before any other oracle call);
+    False when it cannot be built here, and the single-threaded one stays."""
+    global _use_openmp
+    if _lib is not None:
+        raise RuntimeError("the oracle library is already loaded in this process")
+    try:
+        build(openmp=True)
+    except (OSError, subprocess.CalledProcessError):
+        return False
+    _use_openmp = True
+    return True
+
+
+def threads() -> int:
+    """Threads the loaded build runs its loops on (1 for the plain build)."""
+    if not _use_openmp:
+        return 1
+    env = os.environ.get("OMP_NUM_THREADS")
+    return int(env) if env and env.isdigit() else (os.cpu_count() or 1)
 
 
 class Params(C.Structure):
@@ -109,7 +148,7 @@ _ip = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
 def lib():
     global _lib
     if _lib is None:
-        _lib = C.CDLL(build())
+        _lib = C.CDLL(build(openmp=_use_openmp))
         L = _lib
         L.orc_fft1.argtypes = [C.c_int, _cp, C.c_int]
         L.orc_fft3_r2c.argtypes = [C.c_int, C.c_int, C.c_int, _dp, _cp]

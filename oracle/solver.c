@@ -55,7 +55,8 @@ void orc_dealias(const orc_params *p, double complex *fh, int ncomp)
     int Ky = cutoff(p->ny, p->dealias_strict);
     int Kz = cutoff(p->nz, p->dealias_strict);
     long nh = n_half(p);
-    for (int c = 0; c < ncomp; ++c)
+    for (int c = 0; c < ncomp; ++c) {
+#pragma omp parallel for schedule(static)
         for (int iz = 0; iz < p->nz; ++iz)
             for (int iy = 0; iy < p->ny; ++iy)
                 for (int ix = 0; ix < hx; ++ix) {
@@ -64,6 +65,7 @@ void orc_dealias(const orc_params *p, double complex *fh, int ncomp)
                     if (ix > Kx || my > Ky || mz > Kz)
                         fh[c * nh + ((long)iz * p->ny + iy) * hx + ix] = 0;
                 }
+    }
 }
 
 /* Wake-removal regions (Sec. 2.3), a reading: the paper places a sponge and a
@@ -93,6 +95,7 @@ void orc_sponge_term(const orc_params *p, const double complex *vh, double compl
 {
     int hx = p->nx / 2 + 1;
     long nh = n_half(p);
+#pragma omp parallel for schedule(static)
     for (int iz = 0; iz < p->nz; ++iz)
         for (int iy = 0; iy < p->ny; ++iy)
             for (int ix = 0; ix < hx; ++ix) {
@@ -121,6 +124,7 @@ void orc_project(const orc_params *p, double complex *fh)
 {
     int hx = p->nx / 2 + 1;
     long nh = n_half(p);
+#pragma omp parallel for schedule(static)
     for (int iz = 0; iz < p->nz; ++iz)
         for (int iy = 0; iy < p->ny; ++iy)
             for (int ix = 0; ix < hx; ++ix) {
@@ -139,6 +143,7 @@ void orc_curl(const orc_params *p, const double complex *uh, double complex *wh)
 {
     int hx = p->nx / 2 + 1;
     long nh = n_half(p);
+#pragma omp parallel for schedule(static)
     for (int iz = 0; iz < p->nz; ++iz)
         for (int iy = 0; iy < p->ny; ++iy)
             for (int ix = 0; ix < hx; ++ix) {
@@ -222,7 +227,14 @@ static int physical_terms(const orc_params *p, const orc_insect *ins, double t,
     double dV = dx * dy * dz;
     memset(sums, 0, sizeof(double) * ORC_NSUMS);
     int bad = 0;
+    /* sums[0 .. ORC_SUM_EKIN] add up, ORC_SUM_UMAX is a maximum; in the
+     * OpenMP build (timing only) each thread keeps its own copies of them */
+    double acc[ORC_SUM_EKIN + 1];
+    memset(acc, 0, sizeof acc);
+    double umax = 0.0;
 
+#pragma omp parallel for schedule(static) reduction(+ : acc[:ORC_SUM_EKIN + 1]) reduction(max : umax) \
+    reduction(| : bad)
     for (long iz = 0; iz < p->nz; ++iz)
         for (long iy = 0; iy < p->ny; ++iy)
             for (long ix = 0; ix < p->nx; ++ix) {
@@ -260,8 +272,8 @@ static int physical_terms(const orc_params *p, const orc_insect *ins, double t,
                     fields[7 * N + i] = col;
                 }
                 double u2 = uu[0] * uu[0] + uu[1] * uu[1] + uu[2] * uu[2];
-                sums[ORC_SUM_EKIN] += 0.5 * u2 * dV;
-                if (sqrt(u2) > sums[ORC_SUM_UMAX]) sums[ORC_SUM_UMAX] = sqrt(u2);
+                acc[ORC_SUM_EKIN] += 0.5 * u2 * dV;
+                if (sqrt(u2) > umax) umax = sqrt(u2);
                 if (col > 0) {
                     int c0 = col - 1;
                     const double *xr = col == 1 ? ins->x_cntr : fr.pivot_g[col - 2];
@@ -278,13 +290,15 @@ static int physical_terms(const orc_params *p, const orc_insect *ins, double t,
                     m2[1] = r[2] * cus[0] - r[0] * cus[2];
                     m2[2] = r[0] * cus[1] - r[1] * cus[0];
                     for (int c = 0; c < 3; ++c) {
-                        sums[ORC_SUM_FP(c0) + c] += pen[c] * dV / p->eta;
-                        sums[ORC_SUM_MP(c0) + c] += m1[c] * dV / p->eta;
-                        sums[ORC_SUM_IS(c0) + c] += cus[c] * dV;
-                        sums[ORC_SUM_JS(c0) + c] += m2[c] * dV;
+                        acc[ORC_SUM_FP(c0) + c] += pen[c] * dV / p->eta;
+                        acc[ORC_SUM_MP(c0) + c] += m1[c] * dV / p->eta;
+                        acc[ORC_SUM_IS(c0) + c] += cus[c] * dV;
+                        acc[ORC_SUM_JS(c0) + c] += m2[c] * dV;
                     }
                 }
             }
+    for (int k = 0; k <= ORC_SUM_EKIN; ++k) sums[k] = acc[k];
+    sums[ORC_SUM_UMAX] = umax;
     sums[ORC_SUM_NONFINITE] = bad;
     free(w);
     free(u);
@@ -350,6 +364,7 @@ void orc_ab2_update(const orc_params *p, double complex *uh,
 {
     int hx = p->nx / 2 + 1;
     long nhs = n_half(p);
+#pragma omp parallel for schedule(static)
     for (int iz = 0; iz < p->nz; ++iz)
         for (int iy = 0; iy < p->ny; ++iy)
             for (int ix = 0; ix < hx; ++ix) {
@@ -388,6 +403,7 @@ static void add_viscous(const orc_params *p, const double complex *uh, double co
 {
     int hx = p->nx / 2 + 1;
     long nhs = n_half(p);
+#pragma omp parallel for schedule(static)
     for (int iz = 0; iz < p->nz; ++iz)
         for (int iy = 0; iy < p->ny; ++iy)
             for (int ix = 0; ix < hx; ++ix) {

@@ -134,6 +134,7 @@ def _load():
         "flusi_last_error": ([h], C.c_char_p),
         "flusi_build_id": ([], C.c_char_p),
         "flusi_fma_peak": ([ip, C.c_double, dp, dp], ip),
+        "flusi_divergence": ([h, dp, dp], ip),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -355,6 +356,13 @@ def flusi_last_error(h):
     return lib.flusi_last_error(h).decode()
 
 
+def flusi_divergence(h):
+    """(max |k . u_hat|, max |k| |u_hat|) of the state, reduced in FP64 on the device."""
+    d, ku = C.c_double(), C.c_double()
+    _check(h, lib.flusi_divergence(h, C.byref(d), C.byref(ku)))
+    return d.value, ku.value
+
+
 def flusi_build_id():
     return lib.flusi_build_id().decode()
 
@@ -530,6 +538,10 @@ class Solver:
             raise ValueError("out must be a contiguous [3][nz][ny][nx] tensor in the handle's "
                              "precision on the handle's device")
         return flusi_get_state(self.h, out.data_ptr(), FLUSI_DEVICE)
+
+    def divergence(self):
+        """(max |k . u_hat|, max |k| |u_hat|) over the kept modes, FP64 on the device."""
+        return flusi_divergence(self.h)
 
     def get_spectrum(self):
         nx, ny, nz = self.n

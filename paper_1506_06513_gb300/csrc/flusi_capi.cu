@@ -955,6 +955,24 @@ int flusi_get_state(flusi_t h, void* u_out, int where, double* t, long long* ste
     return FLUSI_OK;
 }
 
+int flusi_divergence(flusi_t h, double* div_max, double* ku_max)
+{
+    int rc = check_ready(h, true);
+    if (rc) return rc;
+    if (!div_max) return fail(h, FLUSI_EINVAL, "div_max is NULL");
+    rc = read_status(h, nullptr);
+    if (rc) return rc;
+    // the per-CTA partial-sum rows are free between steps (stream order)
+    unsigned long long* slot = at<unsigned long long>(h, h->opart);
+    CK(launch_divergence(h->prec == FLUSI_FP64, h->ws + h->oU, h->g, slot, h->stream), "divergence");
+    unsigned long long bits[2] = {0, 0};
+    CK(cudaMemcpyAsync(bits, slot, sizeof bits, cudaMemcpyDeviceToHost, h->stream), "read divergence");
+    CK(cudaStreamSynchronize(h->stream), "divergence");
+    std::memcpy(div_max, &bits[0], sizeof(double));
+    if (ku_max) std::memcpy(ku_max, &bits[1], sizeof(double));
+    return FLUSI_OK;
+}
+
 int flusi_get_spectrum(flusi_t h, double* uh_out)
 {
     int rc = check_ready(h, true);

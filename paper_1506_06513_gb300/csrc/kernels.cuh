@@ -90,6 +90,10 @@ cudaError_t launch_zfwd(int fp64, void* W, int nf, const Geom& g, const FftPlan&
 cudaError_t launch_zupdate(int fp64, int mode, const void* W, void* U, void* H, const Geom& g,
                            const ZfwdExtra& ex, const StepState* st, cudaStream_t s);
 
+// max |k . u_hat| and max |k| |u_hat| over the kept modes of a state, FP64,
+// into out[0], out[1] (device; cleared here)
+cudaError_t launch_divergence(int fp64, const void* U, const Geom& g, unsigned long long* out, cudaStream_t s);
+
 // x pass (xpass.cu)
 // XP_SPONGE: c2r of W[comp0 .. comp0+2], times the sponge mask, r2c back in place
 enum XMode { XP_PHYS = 0, XP_R2C = 1, XP_C2R = 2, XP_DUMP = 3, XP_SPONGE = 4 };

@@ -362,7 +362,7 @@ k_xpass(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict
                     for (int cc = 0; cc < 3; ++cc) {
                         const bool has = valid && (colr[0] == cc + 1 || colr[1] == cc + 1);
                         if (!__any_sync(0xffffffffu, has)) continue;
-                        T v[12];   // partial over this warp's points, in T
+                        T v[12];   // this lane's contribution, in T
                         for (int k = 0; k < 12; ++k) v[k] = T(0);
                         if (has) {
                             for (int h = 0; h < 2; ++h) {
@@ -384,9 +384,11 @@ k_xpass(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict
                                 }
                             }
                         }
-                        for (int k = 0; k < 12; ++k) v[k] = warp_sum_t(v[k]);
-                        if (lane == 0)
-                            for (int k = 0; k < 12; ++k) wacc[warp * 36 + cc * 12 + k] += double(v[k]);
+                        // a lane's points in T, everything above it in FP64
+                        for (int k = 0; k < 12; ++k) {
+                            const double sv = warp_sum(double(v[k]));
+                            if (lane == 0) wacc[warp * 36 + cc * 12 + k] += sv;
+                        }
                     }
                 }
             }
@@ -709,7 +711,7 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
                     for (int cc = 0; cc < 3; ++cc) {
                         const bool has = colr == cc + 1;
                         if (!__any_sync(0xffffffffu, has)) continue;
-                        T acc[12];   // partial over this warp's points, in T
+                        T acc[12];   // this lane's contribution, in T
 #pragma unroll
                         for (int k2 = 0; k2 < 12; ++k2) acc[k2] = T(0);
                         if (has) {
@@ -731,10 +733,13 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
                                 acc[9 + q] = m2[q];
                             }
                         }
+                        // one point per lane in T; the sums across lanes, warps
+                        // and blocks in FP64
 #pragma unroll
-                        for (int k2 = 0; k2 < 12; ++k2) acc[k2] = warp_sum_t(acc[k2]);
-                        if (lane == 0)
-                            for (int k2 = 0; k2 < 12; ++k2) wacc[warp * 36 + cc * 12 + k2] += double(acc[k2]);
+                        for (int k2 = 0; k2 < 12; ++k2) {
+                            const double sv = warp_sum(double(acc[k2]));
+                            if (lane == 0) wacc[warp * 36 + cc * 12 + k2] += sv;
+                        }
                     }
                 }
             }

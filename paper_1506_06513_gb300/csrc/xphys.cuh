@@ -215,15 +215,6 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
-// Sum over the warp in the pass's own precision; the force and moment partials
-// of one warp's 64 points are added in T and only the warp totals in FP64
-// (FP64 adds are scarce on this part: a per-point FP64 accumulation cost as
-// much as the transforms of the rows that meet the insect).
-template <typename T> __device__ __forceinline__ T warp_sum_t(T v)
-{
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
 
 // c2r pre-processing: Z[k] = (X[k] + X*[m]) + i (X[k] - X*[m]) w^{-k} with the
 // mirror value Xm = X[nh - k].

@@ -735,6 +735,57 @@ cudaError_t launch_zupdate(int fp64, int mode, const void* W, void* U, void* H, 
                 : launch_zu<float>(mode, W, U, H, g, ex, st, s);
 }
 
+// max over the kept modes of |k . u_hat| and of |k| |u_hat|, in FP64 from a
+// state of precision T: the discrete divergence that the Leray projection
+// (Eq. PNST_UP_pressure_poisson_eqn) removes, and its scale.  Non-negative
+// doubles order like their bit patterns, so the maxima are kept with 64-bit
+// integer atomics in out[0], out[1] (cleared by the caller).
+template <typename T>
+__global__ void __launch_bounds__(256) k_divergence(const cplx<T>* __restrict__ U, Geom g,
+                                                     unsigned long long* __restrict__ out)
+{
+    const int Q = g.My * g.Mxp;
+    const size_t S = (size_t)g.Mz * Q;
+    const double two_pi = 6.283185307179586476925286766559;
+    double dmax = 0.0, kumax = 0.0;
+    for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < S; o += (size_t)gridDim.x * blockDim.x) {
+        const int jz = (int)(o / Q), q = (int)(o - (size_t)jz * Q);
+        const int jy = q / g.Mxp, jx = q - jy * g.Mxp;
+        if (jx >= g.Mx) continue;
+        const double k[3] = {two_pi * jx / g.Lx, two_pi * mode_of(jy, g.Ky) / g.Ly, two_pi * mode_of(jz, g.Kz) / g.Lz};
+        double dr = 0.0, di = 0.0, uu = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            const cplx<T> u = U[c * S + o];
+            dr += k[c] * double(u.x);
+            di += k[c] * double(u.y);
+            uu += double(u.x) * double(u.x) + double(u.y) * double(u.y);
+        }
+        const double kk = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+        dmax = fmax(dmax, sqrt(dr * dr + di * di));
+        kumax = fmax(kumax, sqrt(kk * uu));
+        if (!(dr == dr && di == di && uu == uu)) dmax = __longlong_as_double(0x7ff8000000000000LL);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, off));
+        kumax = fmax(kumax, __shfl_xor_sync(0xffffffffu, kumax, off));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(out, (unsigned long long)__double_as_longlong(dmax));
+        atomicMax(out + 1, (unsigned long long)__double_as_longlong(kumax));
+    }
+}
+
+cudaError_t launch_divergence(int fp64, const void* U, const Geom& g, unsigned long long* out, cudaStream_t s)
+{
+    const size_t S = (size_t)g.Mz * g.My * g.Mxp;
+    const int grid = (int)std::min<size_t>(1024, (S + 255) / 256);
+    cudaError_t e = cudaMemsetAsync(out, 0, 2 * sizeof(unsigned long long), s);
+    if (e) return e;
+    if (fp64) k_divergence<double><<<grid, 256, 0, s>>>(static_cast<const cplx<double>*>(U), g, out);
+    else k_divergence<float><<<grid, 256, 0, s>>>(static_cast<const cplx<float>*>(U), g, out);
+    return cudaGetLastError();
+}
+
 cudaError_t configure_zpass()
 {
     const int big = 120 * 1024;

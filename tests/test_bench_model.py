@@ -52,3 +52,16 @@ def test_xpass_tc_flops():
     assert bench.xpass_tc_flops((512, 512, 512), 3) == 2 * bench.xpass_tc_flops((512, 512, 512), 2)
     # nx = 256: 16-row tiles, a stage of two 128 x 16 x 16 products and one of 128 x 32 x 32
     assert bench.xpass_tc_flops((256, 16, 16), 2) == 2 * 16 * 9 * (2 * 128 * 16 * 16 + 128 * 32 * 32) * 3
+
+
+def test_kernel_flops_512():
+    """FP64 roofline flops: y inverse = 6 fields x nz Mx lines of a 512-point
+    FFT (5 m log2 m = 23 040 flops), y forward half of it, the x pass as
+    xpass_flops; the step at 512^3 totals about 65 GFLOP (pruned modes)."""
+    kf = bench.kernel_flops((512, 512, 512))
+    assert kf["yinv"] == 6 * 512 * 171 * 5 * 512 * 9
+    assert kf["yfwd"] * 2 == kf["yinv"]
+    assert kf["xpass_phys"] == bench.xpass_flops((512, 512, 512)) == kf["xpass_tc"]
+    assert kf["zfwd"] == 3 * 341 * 171 * 5 * 512 * 9
+    step = sum(v for k, v in kf.items() if k != "xpass_tc")
+    assert 6.4e10 < step < 6.6e10

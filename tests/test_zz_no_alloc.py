@@ -73,6 +73,64 @@ def test_noalloc_sums_match_step_force_rows(fl):
     assert np.abs(s0[:12]).max() > 0 and np.abs(s0[12:24]).max() > 0   # body and a wing hit
 
 
+def _oracle_sums(cfg, insect, u, t):
+    """The oracle's force, moment, solid-integral, energy and max|u| sums of
+    the physical field u (Sec. 2.2, Eqs. force_with_unst_corrections,
+    moment_of_love): its right-hand side evaluated on the spectrum of u."""
+    import oracle
+    sp = oracle.Spectral(cfg)
+    return sp.rhs(sp.forward(u), t, insect)[1], sp.inverse(sp.forward(u))
+
+
+@pytest.mark.gpu
+def test_noalloc_sums_match_the_oracle_at_the_cta_cap(fl):
+    """128 x 64 x 48 points (more than 1 024 CTAs of 256 points, so the grid
+    is capped and every CTA strides over several blocks), a flapping insect at
+    two times: each colour's F, M, sum chi u_s, sum r x chi u_s, the energy
+    and max |u| against the CPU oracle, on two calls in a row."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU test needs a CUDA device")
+    n, L = (128, 64, 48), (4.0, 2.0, 1.5)
+    assert n[0] * n[1] * n[2] > 1024 * 256
+    cfg = {"n": n, "L": L, "nu": 0.01, "eta": 2.5e-3}
+    insect = dict(workloads.model_insect(L, n), x_cntr=(2.0, 1.0, 0.75))
+    desc = fl.make_insect(insect)
+    for seed, t in ((3, 0.13), (4, 0.41)):
+        u = workloads.random_smooth_field(n, seed, amplitude=0.7, mean=(0.25, 0.0, 0.0))
+        ref, u_band = _oracle_sums(cfg, insect, u, t)
+        u_dev = torch.from_numpy(np.ascontiguousarray(u_band)).cuda()
+        torch.cuda.synchronize()
+        got = fl.flusi_penalization_sums_noalloc(n, L, cfg["eta"], desc, t, u_dev.data_ptr())
+        for c in range(3):
+            blk, rb = got[12 * c: 12 * c + 12], ref[12 * c: 12 * c + 12]
+            assert np.abs(rb).max() > 0, c   # every part meets the grid
+            for q in range(4):
+                assert _close(blk[3 * q: 3 * q + 3], rb[3 * q: 3 * q + 3], 1e-10), (c, q)
+        assert abs(got[36] - ref[36]) <= 1e-12 * ref[36]
+        assert abs(got[37] - ref[37]) <= 1e-13 * ref[37]
+
+
+@pytest.mark.gpu
+def test_noalloc_without_an_insect(fl):
+    """No insect: all 36 force and moment sums exactly zero; the energy and
+    max |u| against a direct host computation."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU test needs a CUDA device")
+    n, L = (96, 48, 64), (3.0, 1.5, 2.0)
+    u = workloads.random_field(n, 11, amplitude=0.5)
+    u_dev = torch.from_numpy(np.ascontiguousarray(u)).cuda()
+    torch.cuda.synchronize()
+    got = fl.flusi_penalization_sums_noalloc(n, L, 1e-2, None, 0.0, u_dev.data_ptr())
+    assert np.all(np.asarray(got[:36]) == 0.0)
+    dV = L[0] * L[1] * L[2] / (n[0] * n[1] * n[2])
+    e = 0.5 * float((u * u).sum()) * dV
+    umax = float(np.sqrt((u * u).sum(axis=0)).max())
+    assert abs(got[36] - e) <= 1e-12 * e
+    assert abs(got[37] - umax) <= 1e-14 * umax
+
+
 def test_noalloc_rejects_oversized_grids(fl):
     dummy = 0x100000
     with pytest.raises(fl.FlusiError) as e:
