@@ -467,10 +467,17 @@ def run_flusi(args):
     torch.cuda.synchronize()
     barrier()
     ms = ev0.elapsed_time(ev1)
-    # the step timed again: median of 5 repeats of at least 50 graph steps
+    # the last force row of the timed steps (t, dt, ..., E_kin, max|u| at its start)
+    rows_t, _ = sim.forces()
+    last_row = None
+    if len(rows_t):
+        lr = rows_t[-1]
+        last_row = {"rows": int(len(rows_t)), "t": float(lr[0]), "dt": float(lr[1]),
+                    "E_kin": float(lr[20]), "u_max": float(lr[21]), "finite": bool(np.isfinite(rows_t).all())}
+    # the step timed again: median of 5 repeats of 50 graph steps
     reps = []
     for _ in range(5):
-        k = max(50, args.steps)
+        k = 50
         torch.cuda.synchronize()
         ev0.record(sim.stream)
         sim.step(k)
@@ -482,7 +489,7 @@ def run_flusi(args):
     ms_max = allmax(ms)
     value = whole_job_rate(N, args.steps, world, ms_max)
     ms_per_step = ms_max / args.steps
-    repeats = {"ms_per_step": [round(r, 4) for r in reps], "steps_each": max(50, args.steps),
+    repeats = {"ms_per_step": [round(r, 4) for r in reps], "steps_each": 50,
                "median_ms_per_step": round(statistics.median(reps), 4),
                "median_value": N * 1e3 / statistics.median(reps) * world}
     kps = fl.flusi_kernels_per_step(sim.h)
@@ -667,6 +674,7 @@ def run_flusi(args):
                        precision=args.precision),
         "roofline": roofline,
         "repeats": repeats,
+        "last_row": last_row,
         "stage_model": {"bytes_per_step": stage, "frac_of_peak": round(stage / (ms_per_step * 1e-3) / 1e9 / hbm, 4),
                         "frac_of_nominal_8TBs": round(stage / (ms_per_step * 1e-3) / 8e12, 4),
                         "kernel_bytes_per_step": step_bytes,
