@@ -460,6 +460,13 @@ int flusi_load(flusi_t h, const void *host_buf, size_t bytes);
  * a-e, each member with its own adaptive dt) and return without waiting.  The
  * first call captures one graph holding one step of all members, forked from
  * and joined back into the ensemble stream; later calls launch it n times.
+ * Members with the same grid, box, C_eta, precision, options, tuning and mask
+ * shape, stepped with AB2, without the vorticity sponge, on the CUDA-core x
+ * pass (nu and the kinematics may differ) share their launches: one launch
+ * per kernel covers the whole group, each member's blocks reading its own
+ * buffers; the others step with launches of their own.  Every member's
+ * arithmetic is the same either way (its results equal a solo run's bit for
+ * bit).
  * Work already enqueued on a member's bound stream runs before, and work
  * enqueued there afterwards runs after, so flusi_forces / flusi_get_state on a
  * member see the ensemble's steps.  A member with a device error stops
@@ -477,6 +484,9 @@ int flusi_ensemble_create(const flusi_t *members, int count, void *cuda_stream,
                           flusi_ensemble_t *out);
 int flusi_ensemble_step(flusi_ensemble_t e, int n);
 int flusi_ensemble_destroy(flusi_ensemble_t e);
+/* After the first flusi_ensemble_step: the number of groups whose members
+ * share launches, and how many members they hold (both 0 before). */
+int flusi_ensemble_batches(flusi_ensemble_t e, int *groups, int *members);
 
 /* Release the handle (not the caller's workspace).  NULL is a no-op. */
 int flusi_destroy(flusi_t h);

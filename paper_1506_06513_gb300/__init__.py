@@ -130,6 +130,7 @@ def _load():
         "flusi_ensemble_create": ([C.POINTER(h), ip, vp, C.POINTER(h)], ip),
         "flusi_ensemble_step": ([h, ip], ip),
         "flusi_ensemble_destroy": ([h], ip),
+        "flusi_ensemble_batches": ([h, C.POINTER(C.c_int), C.POINTER(C.c_int)], ip),
         "flusi_destroy": ([h], ip),
         "flusi_last_error": ([h], C.c_char_p),
         "flusi_build_id": ([], C.c_char_p),
@@ -602,6 +603,12 @@ class Ensemble:
 
     def step(self, n=1):
         flusi_ensemble_step(self.e, n)
+
+    def batches(self):
+        """(groups sharing launches, members in them) of the captured step."""
+        g, m = C.c_int(), C.c_int()
+        _check(None, lib.flusi_ensemble_batches(self.e, C.byref(g), C.byref(m)))
+        return g.value, m.value
 
     def sync(self):
         self.stream.synchronize()

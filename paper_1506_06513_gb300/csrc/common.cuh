@@ -217,6 +217,23 @@ struct StepCoef {
     double t0;               // time at the start of the step (RK stages)
 };
 
+// One ensemble member's buffers, for launches that cover several members of
+// the same grid, options and tuning at once (blockIdx.z picks the member):
+// everything that differs between such members lives here.
+struct Member {
+    void* W;                 // work fields
+    void* U;                 // state u_hat
+    void* H;                 // AB2 history
+    StepState* st;
+    StepCoef* coef;
+    Frame* fr;
+    flusi_insect* ins;       // device descriptor
+    double* etab;            // integrating-factor tables
+    double* part;            // per-CTA partial sums of the physical pass
+    double* rows;            // force-row ring
+    double nu;
+};
+
 __host__ __device__ inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
 
 // Rows per TMA box for an inverse tile of length n that keeps modes 0..K and

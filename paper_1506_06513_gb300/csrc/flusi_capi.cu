@@ -22,6 +22,13 @@
 
 using namespace flusi;
 
+// the ensemble batch of the launches this host thread makes (see Batch)
+Batch& flusi::current_batch()
+{
+    static thread_local Batch b;
+    return b;
+}
+
 constexpr int kStageSlots = 8;   // pinned insect-descriptor slots per handle
 
 struct flusi_s {
@@ -375,8 +382,9 @@ cudaError_t enqueue_step(flusi_t h, cudaStream_t s, cudaEvent_t* ev, const char*
             if ((e = cudaEventRecord(h->ev_fork, s))) return e;
             if ((e = cudaStreamWaitEvent(sk, h->ev_fork, 0))) return e;
         }
-        k_kinematics<<<1, 32, 0, skq>>>(at<flusi_insect>(h, h->oins), st, coef, at<Frame>(h, h->oframe),
-                                        box_margin(h), frac[q]);
+        k_kinematics<<<dim3(1, 1, current_batch().n), 32, 0, skq>>>(
+            at<flusi_insect>(h, h->oins), st, coef, at<Frame>(h, h->oframe), box_margin(h), frac[q],
+            current_batch().mb);
         if ((e = cudaGetLastError())) return e;
         if (br && (e = cudaEventRecord(h->ev_kin, sk))) return e;
         mark(nm[1]);
@@ -404,9 +412,9 @@ cudaError_t enqueue_step(flusi_t h, cudaStream_t s, cudaEvent_t* ev, const char*
                 if ((e = cudaStreamWaitEvent(sk, h->ev_x, 0))) return e;
             }
             double3 opts = make_double3(h->opt.cfl, h->opt.dt_fixed, h->opt.dt_max);
-            k_scalars<<<1, 256, 0, sk>>>(g, at<double>(h, h->opart), h->xgrid, st, coef, at<double>(h, h->orows),
+            k_scalars<<<dim3(1, 1, current_batch().n), 256, 0, sk>>>(g, at<double>(h, h->opart), h->xgrid, st, coef, at<double>(h, h->orows),
                                          h->opt.force_ring, at<double>(h, h->oetab), opts, rk4_dt_diff(h),
-                                         at<Frame>(h, h->oframe), at<flusi_insect>(h, h->oins));
+                                         at<Frame>(h, h->oframe), at<flusi_insect>(h, h->oins), current_batch().mb);
             if ((e = cudaGetLastError())) return e;
             if (branch && (e = cudaEventRecord(h->ev_sc, sk))) return e;
         }
@@ -1033,7 +1041,7 @@ int flusi_debug_fields(flusi_t h, void* out_dev)
     void* W = h->ws + h->oW;
     StepState* st = at<StepState>(h, h->ostate);
     k_kinematics<<<1, 32, 0, s>>>(at<flusi_insect>(h, h->oins), st, at<StepCoef>(h, h->ocoef),
-                                  at<Frame>(h, h->oframe), box_margin(h), 0.0);
+                                  at<Frame>(h, h->oframe), box_margin(h), 0.0, nullptr);
     CK(cudaGetLastError(), "kinematics");
     CK(launch_zinv(fp64, h->ws + h->oU, W, g, h->pzi, at<double2>(h, h->otz), at<int>(h, h->opzi), 6, nullptr,
                    &h->zmaps.u, h->zmaps.u_bh, status_word(h), s),
@@ -1444,6 +1452,8 @@ struct flusi_ensemble_s {
     cudaEvent_t fork = nullptr, done = nullptr;
     std::vector<cudaEvent_t> join, pre;
     cudaGraphExec_t gexec = nullptr;
+    Member* dev_members = nullptr;         // the batched groups' member tables
+    int batches = 0, batched_members = 0;  // of the captured graph
 };
 
 namespace {
@@ -1464,6 +1474,7 @@ int ens_cuda(cudaError_t e, const char* what)
 void ens_release(flusi_ensemble_t e)
 {
     if (e->gexec) cudaGraphExecDestroy(e->gexec);
+    if (e->dev_members) cudaFree(e->dev_members);
     if (e->cap) cudaStreamDestroy(e->cap);
     if (e->fork) cudaEventDestroy(e->fork);
     if (e->done) cudaEventDestroy(e->done);
@@ -1474,19 +1485,110 @@ void ens_release(flusi_ensemble_t e)
     delete e;
 }
 
-// One graph: fork from the capture origin, one step of every member on the
-// member's own capture stream, join back.
+// Members whose steps can run as one launch per kernel: the same grid, box,
+// C_eta, precision, options (all but nu), tuning, mask shape and x-pass grid,
+// with the AB2 scheme, no vorticity sponge, the CUDA-core x pass and one-CTA
+// y tiles.  nu differs freely (it enters only through the scalars' tables).
+bool batchable(flusi_t h)
+{
+    return h->opt.time_scheme == 0 && !(h->opt.sponge_c > 0) && !h->g.xtc && h->g.ypair == 0;
+}
+
+bool same_batch(flusi_t a, flusi_t b)
+{
+    const Geom &x = a->g, &y = b->g;
+    const bool geom = x.nx == y.nx && x.ny == y.ny && x.nz == y.nz && x.Kx == y.Kx && x.Ky == y.Ky &&
+                      x.Kz == y.Kz && x.Mxp == y.Mxp && x.Lx == y.Lx && x.Ly == y.Ly && x.Lz == y.Lz &&
+                      x.eta == y.eta && x.ycols == y.ycols && x.zcols == y.zcols && x.xgeneric == y.xgeneric &&
+                      x.ypair == y.ypair && x.xtc == y.xtc;
+    const flusi_options &o = a->opt, &q = b->opt;
+    bool opts = o.cfl == q.cfl && o.dt_fixed == q.dt_fixed && o.dt_max == q.dt_max && o.mean_mode == q.mean_mode &&
+                o.dealias_strict == q.dealias_strict && o.force_ring == q.force_ring && o.time_scheme == q.time_scheme &&
+                o.sponge_c == q.sponge_c;
+    for (int i = 0; i < 3; ++i)
+        opts = opts && o.u_inf[i] == q.u_inf[i] && o.layer_width[i] == q.layer_width[i] &&
+               o.sponge_width[i] == q.sponge_width[i];
+    return geom && opts && a->prec == b->prec && a->tune.y_plan == b->tune.y_plan &&
+           a->tune.zf_plan == b->tune.zf_plan && a->xgrid == b->xgrid &&
+           same_shape(make_shape(a), make_shape(b)) && box_margin(a) == box_margin(b);
+}
+
+Member member_of(flusi_t h)
+{
+    Member m;
+    m.W = h->ws + h->oW;
+    m.U = h->ws + h->oU;
+    m.H = h->ws + h->oH;
+    m.st = at<StepState>(h, h->ostate);
+    m.coef = at<StepCoef>(h, h->ocoef);
+    m.fr = at<Frame>(h, h->oframe);
+    m.ins = at<flusi_insect>(h, h->oins);
+    m.etab = at<double>(h, h->oetab);
+    m.part = at<double>(h, h->opart);
+    m.rows = at<double>(h, h->orows);
+    m.nu = h->nu;
+    return m;
+}
+
+// One graph: fork from the capture origin, then per group of members that
+// can share launches (same_batch) one step whose launches cover the whole
+// group (gridDim.z = members, each kernel taking its member's buffers from a
+// device table), and for every other member one step of its own, each on its
+// own capture stream; join back.
 int ens_capture(flusi_ensemble_t e)
 {
+    const size_t M = e->m.size();
+    std::vector<int> group(M, -1);
+    std::vector<std::vector<int>> groups;
+    for (size_t i = 0; i < M; ++i) {
+        if (group[i] >= 0) continue;
+        group[i] = (int)groups.size();
+        groups.push_back({(int)i});
+        if (!batchable(e->m[i])) continue;
+        for (size_t j = i + 1; j < M; ++j)
+            if (group[j] < 0 && batchable(e->m[j]) && same_batch(e->m[i], e->m[j])) {
+                group[j] = group[i];
+                groups.back().push_back((int)j);
+            }
+    }
+    // the member tables of the batched groups, in one device array
+    std::vector<Member> table;
+    std::vector<size_t> first(groups.size(), 0);
+    for (size_t k = 0; k < groups.size(); ++k) {
+        first[k] = table.size();
+        if (groups[k].size() > 1)
+            for (int i : groups[k]) table.push_back(member_of(e->m[i]));
+    }
+    if (e->dev_members) {
+        cudaFree(e->dev_members);
+        e->dev_members = nullptr;
+    }
+    if (!table.empty()) {
+        CKE(cudaMalloc(&e->dev_members, sizeof(Member) * table.size()), "ensemble: member tables");
+        CKE(cudaMemcpy(e->dev_members, table.data(), sizeof(Member) * table.size(), cudaMemcpyHostToDevice),
+            "ensemble: member tables");
+    }
     cudaGraph_t graph = nullptr;
     CKE(cudaStreamBeginCapture(e->cap, cudaStreamCaptureModeThreadLocal), "ensemble: begin capture");
     cudaError_t err = cudaEventRecord(e->fork, e->cap);
-    for (size_t i = 0; i < e->m.size() && err == cudaSuccess; ++i) {
-        flusi_t h = e->m[i];
+    e->batches = e->batched_members = 0;
+    for (size_t k = 0; k < groups.size() && err == cudaSuccess; ++k) {
+        const int lead = groups[k][0];
+        flusi_t h = e->m[lead];
         err = cudaStreamWaitEvent(h->cap_stream, e->fork, 0);
-        if (err == cudaSuccess) err = enqueue_step(h, h->cap_stream, nullptr);
-        if (err == cudaSuccess) err = cudaEventRecord(e->join[i], h->cap_stream);
-        if (err == cudaSuccess) err = cudaStreamWaitEvent(e->cap, e->join[i], 0);
+        if (err == cudaSuccess) {
+            Batch& B = current_batch();
+            if (groups[k].size() > 1) {
+                B.mb = e->dev_members + first[k];
+                B.n = (int)groups[k].size();
+                ++e->batches;
+                e->batched_members += B.n;
+            }
+            err = enqueue_step(h, h->cap_stream, nullptr);
+            B = Batch{};
+        }
+        if (err == cudaSuccess) err = cudaEventRecord(e->join[lead], h->cap_stream);
+        if (err == cudaSuccess) err = cudaStreamWaitEvent(e->cap, e->join[lead], 0);
     }
     cudaError_t err2 = cudaStreamEndCapture(e->cap, &graph);
     if (err != cudaSuccess || err2 != cudaSuccess) {
@@ -1568,6 +1670,14 @@ int flusi_ensemble_step(flusi_ensemble_t e, int n)
     for (flusi_t h : e->m) h->n_enq += n;
     CKE(cudaEventRecord(e->done, e->stream), "ensemble: order members after");
     for (flusi_t h : e->m) CKE(cudaStreamWaitEvent(h->stream, e->done, 0), "ensemble: order members after");
+    return FLUSI_OK;
+}
+
+int flusi_ensemble_batches(flusi_ensemble_t e, int* groups, int* members)
+{
+    if (!e || !groups || !members) return ens_fail(FLUSI_EINVAL, "NULL argument");
+    *groups = e->batches;
+    *members = e->batched_members;
     return FLUSI_OK;
 }
 

@@ -18,14 +18,25 @@
 
 namespace flusi {
 
-// kinematics / scalars (scalars.cu)
+// Ensemble batches.  While an ensemble step is captured, the launches made on
+// this host thread can cover `n` members at once: the launchers then size
+// gridDim.z = n and pass `mb`, the device array of the members' buffers, and
+// each kernel takes its member's pointers from mb[blockIdx.z].  Outside a
+// batch n = 1 and mb = nullptr (the kernels use their own arguments).
+struct Batch {
+    const Member* mb = nullptr;
+    int n = 1;
+};
+Batch& current_batch();
+
+// kinematics / scalars (scalars.cu); mb: see Batch
 __global__ void k_kinematics(const flusi_insect* ins, const StepState* st, const StepCoef* coef, Frame* fr,
-                             double h, double frac);
+                             double h, double frac, const Member* mb);
 __global__ void k_reset_state(StepState* st, StepCoef* coef);
 __global__ void k_wait_probe(int* err, long long max_cycles);
 __global__ void k_scalars(Geom g, const double* part, int nparts, StepState* st, StepCoef* coef,
                           double* rows, int ring, double* etab, double3 opts, double dt_diff,
-                          const Frame* fr, flusi_insect* ins);
+                          const Frame* fr, flusi_insect* ins, const Member* mb);
 
 // y transform (ypass.cu): W[c] for c < ncomp, between A and B form.
 // tw: twiddle table of the axis; pos: digit-reversal table of its plan.

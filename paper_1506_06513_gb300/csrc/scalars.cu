@@ -174,9 +174,16 @@ __device__ void advance_body(flusi_insect* ins, StepState* st, const Frame& F, c
 // frac = 0: at the state's time; frac > 0: at t0 + frac dt of the current
 // step (the later RK4 stages, after k_scalars has written t0 and dt).
 __global__ void k_kinematics(const flusi_insect* ins, const StepState* st, const StepCoef* coef, Frame* fr,
-                             double h, double frac)
+                             double h, double frac, const Member* mb)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (mb) {
+        const Member& m = mb[blockIdx.z];
+        ins = m.ins;
+        st = m.st;
+        coef = m.coef;
+        fr = m.fr;
+    }
     const double t = frac > 0.0 ? coef->t0 + frac * coef->dt : st->t;
     Frame F;
     F.t = t;
@@ -369,8 +376,19 @@ __global__ void k_reset_state(StepState* st, StepCoef* coef)
 // adaptive step (the explicit-diffusion limit of RK4).
 __global__ void k_scalars(Geom g, const double* part, int nparts, StepState* st, StepCoef* coef,
                           double* rows, int ring, double* etab, double3 opts, double dt_diff,
-                          const Frame* fr, flusi_insect* ins)
+                          const Frame* fr, flusi_insect* ins, const Member* mb)
 {
+    if (mb) {
+        const Member& m = mb[blockIdx.z];
+        part = m.part;
+        st = m.st;
+        coef = m.coef;
+        rows = m.rows;
+        etab = m.etab;
+        fr = m.fr;
+        ins = m.ins;
+        g.nu = m.nu;
+    }
     __shared__ double red[kNumSums][33];
     __shared__ double tot[kNumSums];
     const int tid = threadIdx.x, T = blockDim.x;

@@ -156,8 +156,16 @@ __device__ __forceinline__ void x_last_forward_any(const cplx<T>* buf, int C, in
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kThreadsX, sizeof(T) == 4 ? 3 : 1)
 k_xpass(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict__ tw,
-        const int* __restrict__ pos, XExtra ex, int lgRB, const StepState* __restrict__ st)
+        const int* __restrict__ pos, XExtra ex, int lgRB, const StepState* __restrict__ st,
+        const Member* __restrict__ mb)
 {
+    if (mb) {   // one member of an ensemble batch
+        const Member& m = mb[blockIdx.z];
+        W = static_cast<cplx<T>*>(m.W);
+        st = m.st;
+        ex.frame = m.fr;
+        ex.part = m.part;
+    }
     if (st && st->status != 0) return;
     constexpr bool kPhys = (MODE == XP_PHYS || MODE == XP_DUMP);
     const int RB = 1 << lgRB;
@@ -484,8 +492,15 @@ template <int R> __device__ __forceinline__ int sq_slot(int lrow)
 template <typename T, int R, int S, bool LAYER, bool SPONGE>
 __global__ void __launch_bounds__(192, sizeof(T) == 4 ? (S == 1 ? 4 : 3) : 1)
 k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExtra ex,
-           const StepState* __restrict__ st)
+           const StepState* __restrict__ st, const Member* __restrict__ mb)
 {
+    if (mb) {   // one member of an ensemble batch
+        const Member& m = mb[blockIdx.z];
+        W = static_cast<cplx<T>*>(m.W);
+        st = m.st;
+        ex.frame = m.fr;
+        ex.part = m.part;
+    }
     if (st && st->status != 0) return;
     constexpr int L = S * R;               // lanes per line
     constexpr int RB = sq_rows<L>();
@@ -860,14 +875,16 @@ void launch_sq(bool layer, bool sponge, cplx<T>* w, const Geom& g, const double2
                const StepState* st, cudaStream_t s, int grid)
 {
     const size_t smem = sq_smem<T, R, S>(g, sponge);
+    const Batch& B = current_batch();
+    const dim3 gd(grid, 1, B.n);
     if (layer && sponge)
-        k_xpass_sq<T, R, S, true, true><<<grid, 192, smem, s>>>(w, g, tw, ex, st);
+        k_xpass_sq<T, R, S, true, true><<<gd, 192, smem, s>>>(w, g, tw, ex, st, B.mb);
     else if (layer)
-        k_xpass_sq<T, R, S, true, false><<<grid, 192, smem, s>>>(w, g, tw, ex, st);
+        k_xpass_sq<T, R, S, true, false><<<gd, 192, smem, s>>>(w, g, tw, ex, st, B.mb);
     else if (sponge)
-        k_xpass_sq<T, R, S, false, true><<<grid, 192, smem, s>>>(w, g, tw, ex, st);
+        k_xpass_sq<T, R, S, false, true><<<gd, 192, smem, s>>>(w, g, tw, ex, st, B.mb);
     else
-        k_xpass_sq<T, R, S, false, false><<<grid, 192, smem, s>>>(w, g, tw, ex, st);
+        k_xpass_sq<T, R, S, false, false><<<gd, 192, smem, s>>>(w, g, tw, ex, st, B.mb);
 }
 
 // the register-resident kernel for this grid: 10 R + S (R = 16 or 8, S = 1
@@ -955,20 +972,21 @@ cudaError_t launch_x(int mode, void* W, const Geom& g, const FftPlan& plan, cons
         case 162: launch_sq<T, 16, 2>(layer, sponge, w, g, tw, ex, st, s, x_grid<T>(g)); break;
         case 82: launch_sq<T, 8, 2>(layer, sponge, w, g, tw, ex, st, s, x_grid<T>(g)); break;
         default:
-            k_xpass<T, XP_PHYS><<<x_grid<T>(g), kThreadsX, smem, s>>>(w, g, plan, tw, pos, ex, lg, st);
+            k_xpass<T, XP_PHYS><<<dim3(x_grid<T>(g), 1, current_batch().n), kThreadsX, smem, s>>>(
+                w, g, plan, tw, pos, ex, lg, st, current_batch().mb);
         }
         break;
     case XP_R2C:
-        k_xpass<T, XP_R2C><<<ntiles, kThreadsX, smem, s>>>(w, g, plan, tw, pos, ex, lg, st);
+        k_xpass<T, XP_R2C><<<ntiles, kThreadsX, smem, s>>>(w, g, plan, tw, pos, ex, lg, st, nullptr);
         break;
     case XP_C2R:
-        k_xpass<T, XP_C2R><<<ntiles, kThreadsX, smem, s>>>(w, g, plan, tw, pos, ex, lg, st);
+        k_xpass<T, XP_C2R><<<ntiles, kThreadsX, smem, s>>>(w, g, plan, tw, pos, ex, lg, st, nullptr);
         break;
     case XP_SPONGE:
-        k_xpass<T, XP_SPONGE><<<ntiles, kThreadsX, smem, s>>>(w, g, plan, tw, pos, ex, lg, st);
+        k_xpass<T, XP_SPONGE><<<ntiles, kThreadsX, smem, s>>>(w, g, plan, tw, pos, ex, lg, st, nullptr);
         break;
     default:
-        k_xpass<T, XP_DUMP><<<ntiles, kThreadsX, smem, s>>>(w, g, plan, tw, pos, ex, lg, st);
+        k_xpass<T, XP_DUMP><<<ntiles, kThreadsX, smem, s>>>(w, g, plan, tw, pos, ex, lg, st, nullptr);
         break;
     }
     return cudaGetLastError();
@@ -993,6 +1011,9 @@ cudaError_t launch_xpass(int fp64, int mode, void* W, const Geom& g, const FftPl
                          const double2* tw, const int* pos, const XExtra& ex, const StepState* st,
                          cudaStream_t s)
 {
+    // ensemble batches cover the physical pass of the CUDA-core kernels only
+    if (current_batch().mb && (mode != XP_PHYS || (!fp64 && g.xtc) || ex.sponge_fused))
+        return cudaErrorInvalidValue;
     if (!fp64 && g.xtc && mode == XP_PHYS) return launch_xpass_tc(W, g, tw, ex, st, s);
     return fp64 ? launch_x<double>(mode, W, g, plan, tw, pos, ex, st, s)
                 : launch_x<float>(mode, W, g, plan, tw, pos, ex, st, s);
@@ -1317,7 +1338,7 @@ extern "C" int flusi_penalization_sums_noalloc(int nx, int ny, int nz, const dou
     const long long want = (N + kNoallocThreads - 1) / kNoallocThreads;
     const int grid = (int)(want < kNoallocMaxCtas ? want : kNoallocMaxCtas);
     k_noalloc_header<<<1, 1, 0, s>>>(ins, t, d_ins, d_st);
-    k_kinematics<<<1, 32, 0, s>>>(d_ins, d_st, nullptr, d_fr, margin, 0.0);
+    k_kinematics<<<1, 32, 0, s>>>(d_ins, d_st, nullptr, d_fr, margin, 0.0, nullptr);
     k_noalloc_sums<<<grid, kNoallocThreads, 0, s>>>(u_dev, nx, ny, nz, dx, dy, dz, d_fr, sh, part);
     k_noalloc_reduce<<<1, 64, 0, s>>>(part, grid, dx * dy * dz, eta, sums);
     cudaError_t e = cudaGetLastError();

@@ -31,8 +31,13 @@ template <typename T, bool INV, bool TMA, bool R16>
 __global__ void __launch_bounds__(kThreads)
 k_ypass(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict__ tw,
         const int* __restrict__ pos, int ncomp, int lgTX, int lgNP, const StepState* __restrict__ st,
-        const __grid_constant__ CUtensorMap tmap, int bh, int* err)
+        const __grid_constant__ CUtensorMap tmap, int bh, int* err, const Member* __restrict__ mb)
 {
+    if (mb) {   // one member of an ensemble batch (never with TMA)
+        W = static_cast<cplx<T>*>(mb[blockIdx.z].W);
+        st = mb[blockIdx.z].st;
+        err = &mb[blockIdx.z].st->status;
+    }
     if (st && st->status != 0) return;
     // after a TMA wait gave up, the remaining blocks leave at once
     if (TMA && *(volatile int*)err != 0) return;
@@ -264,23 +269,25 @@ cudaError_t launch_y2(bool inverse, cplx<T>* w, const Geom& g, const FftPlan& pl
                       const int* pos, int ncomp, const StepState* st, const YMaps* maps, int* err,
                       const YTile& t, cudaStream_t s)
 {
-    const int bh = maps ? (inverse ? maps->inv_bh : maps->fwd_bh) : 0;
+    const Batch& B = current_batch();
+    const int bh = maps && !B.mb ? (inverse ? maps->inv_bh : maps->fwd_bh) : 0;
+    const dim3 grid(t.blocks, 1, B.n);
     if (bh > 0 && err) {
         const CUtensorMap& m = inverse ? maps->inv : maps->fwd;
         if (inverse)
-            k_ypass<T, true, true, R16><<<t.blocks, kThreads, t.smem, s>>>(w, g, plan, tw, pos, ncomp, t.lgTX,
-                                                                            t.lgNP, st, m, bh, err);
+            k_ypass<T, true, true, R16><<<grid, kThreads, t.smem, s>>>(w, g, plan, tw, pos, ncomp, t.lgTX,
+                                                                        t.lgNP, st, m, bh, err, B.mb);
         else
-            k_ypass<T, false, true, R16><<<t.blocks, kThreads, t.smem, s>>>(w, g, plan, tw, pos, ncomp, t.lgTX,
-                                                                             t.lgNP, st, m, bh, err);
+            k_ypass<T, false, true, R16><<<grid, kThreads, t.smem, s>>>(w, g, plan, tw, pos, ncomp, t.lgTX,
+                                                                         t.lgNP, st, m, bh, err, B.mb);
     } else {
         CUtensorMap none{};
         if (inverse)
-            k_ypass<T, true, false, R16><<<t.blocks, kThreads, t.smem, s>>>(w, g, plan, tw, pos, ncomp, t.lgTX,
-                                                                             t.lgNP, st, none, 0, err);
+            k_ypass<T, true, false, R16><<<grid, kThreads, t.smem, s>>>(w, g, plan, tw, pos, ncomp, t.lgTX,
+                                                                         t.lgNP, st, none, 0, err, B.mb);
         else
-            k_ypass<T, false, false, R16><<<t.blocks, kThreads, t.smem, s>>>(w, g, plan, tw, pos, ncomp, t.lgTX,
-                                                                              t.lgNP, st, none, 0, err);
+            k_ypass<T, false, false, R16><<<grid, kThreads, t.smem, s>>>(w, g, plan, tw, pos, ncomp, t.lgTX,
+                                                                          t.lgNP, st, none, 0, err, B.mb);
     }
     return cudaGetLastError();
 }
@@ -310,6 +317,7 @@ cudaError_t launch_y(bool inverse, void* W, const Geom& g, const FftPlan& plan, 
                      const FftPlan* half, const int* pos_half, cudaStream_t s)
 {
     if (half && pos_half && y_paired<T>(g)) {
+        if (current_batch().mb) return cudaErrorInvalidValue;   // batches take the one-CTA tiles
         const YTile t = y_tile_pair<T>(g, ncomp);
         if (((size_t)(g.ny / 2) << (t.lgTX + t.lgNP)) > (size_t)tile_elems<T>() || half->n != g.ny / 2)
             return cudaErrorInvalidValue;

@@ -215,8 +215,15 @@ template <typename T, bool TMA, bool R16>
 __global__ void __launch_bounds__(kThreadsInv, sizeof(T) == 4 ? 3 : 1)
 k_zinv(const cplx<T>* __restrict__ U, cplx<T>* __restrict__ W, Geom g, FftPlan plan,
        const double2* __restrict__ tw, const int* __restrict__ pos, int nf, int lgTX,
-       const StepState* __restrict__ st, const __grid_constant__ CUtensorMap umap, int bh, int* err)
+       const StepState* __restrict__ st, const __grid_constant__ CUtensorMap umap, int bh, int* err,
+       const Member* __restrict__ mb)
 {
+    if (mb) {   // one member of an ensemble batch (never with TMA)
+        U = static_cast<const cplx<T>*>(mb[blockIdx.z].U);
+        W = static_cast<cplx<T>*>(mb[blockIdx.z].W);
+        st = mb[blockIdx.z].st;
+        err = &mb[blockIdx.z].st->status;
+    }
     if (st && st->status != 0) return;
     if (TMA && *(volatile int*)err != 0) return;   // a TMA wait gave up earlier
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -372,8 +379,13 @@ template <typename T, bool TMA, bool R16>
 __global__ void __launch_bounds__(kThreadsInv)
 k_zfwd(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict__ tw,
        const int* __restrict__ pos, int lgTX, const StepState* __restrict__ st,
-       const __grid_constant__ CUtensorMap wmap, int bh, int* err)
+       const __grid_constant__ CUtensorMap wmap, int bh, int* err, const Member* __restrict__ mb)
 {
+    if (mb) {   // one member of an ensemble batch (never with TMA)
+        W = static_cast<cplx<T>*>(mb[blockIdx.z].W);
+        st = mb[blockIdx.z].st;
+        err = &mb[blockIdx.z].st->status;
+    }
     if (st && st->status != 0) return;
     if (TMA && *(volatile int*)err != 0) return;   // a TMA wait gave up earlier
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -450,8 +462,18 @@ k_zfwd(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict_
 template <typename T, int MODE, bool SPONGE>
 __global__ void __launch_bounds__(256)
 k_zupdate(const cplx<T>* __restrict__ Wn, cplx<T>* __restrict__ U, cplx<T>* __restrict__ H, Geom g,
-          ZfwdExtra ex, const StepState* __restrict__ st)
+          ZfwdExtra ex, const StepState* __restrict__ st, const Member* __restrict__ mb)
 {
+    if (mb) {   // one member of an ensemble batch
+        const Member& m = mb[blockIdx.z];
+        Wn = static_cast<const cplx<T>*>(m.W);
+        U = static_cast<cplx<T>*>(m.U);
+        H = static_cast<cplx<T>*>(m.H);
+        st = m.st;
+        ex.coef = m.coef;
+        ex.etab = m.etab;
+        g.nu = m.nu;
+    }
     if (st && st->status != 0) return;
     constexpr bool RK = MODE >= 2;
     constexpr int STAGE = MODE - 1;        // RK4 stage 1..4
@@ -610,8 +632,12 @@ cudaError_t launch_zi(const void* U, void* W, const Geom& g, const FftPlan& plan
     const int lg = __builtin_ctz(TX);
     // the inverse z pass is built without radix-16 stages (its plan has none)
     if (plan_has_radix16(plan)) return cudaErrorInvalidValue;
-    if (tma) k_zinv<T, true, false><<<blocks, kThreadsInv, smem, s>>>(u, w, g, plan, tw, pos, nf, lg, st, m, bh, err);
-    else k_zinv<T, false, false><<<blocks, kThreadsInv, smem, s>>>(u, w, g, plan, tw, pos, nf, lg, st, m, 0, err);
+    const Batch& B = current_batch();
+    const dim3 grid(blocks, 1, B.n);
+    if (tma && !B.mb)
+        k_zinv<T, true, false><<<grid, kThreadsInv, smem, s>>>(u, w, g, plan, tw, pos, nf, lg, st, m, bh, err, nullptr);
+    else
+        k_zinv<T, false, false><<<grid, kThreadsInv, smem, s>>>(u, w, g, plan, tw, pos, nf, lg, st, m, 0, err, B.mb);
     return cudaGetLastError();
 }
 
@@ -629,12 +655,15 @@ cudaError_t launch_zf(void* W, int nf, const Geom& g, const FftPlan& plan, const
     CUtensorMap none{};
     const CUtensorMap& m = tma ? *map : none;
     const int lg = __builtin_ctz(TX);
+    const Batch& B = current_batch();
+    const dim3 grid(blocks, 1, B.n);
+    const bool use_tma = tma && !B.mb;
     if (plan_has_radix16(plan)) {
-        if (tma) k_zfwd<T, true, true><<<blocks, kThreadsInv, smem, s>>>(w, g, plan, tw, pos, lg, st, m, bh, err);
-        else k_zfwd<T, false, true><<<blocks, kThreadsInv, smem, s>>>(w, g, plan, tw, pos, lg, st, m, 0, err);
+        if (use_tma) k_zfwd<T, true, true><<<grid, kThreadsInv, smem, s>>>(w, g, plan, tw, pos, lg, st, m, bh, err, nullptr);
+        else k_zfwd<T, false, true><<<grid, kThreadsInv, smem, s>>>(w, g, plan, tw, pos, lg, st, m, 0, err, B.mb);
     } else {
-        if (tma) k_zfwd<T, true, false><<<blocks, kThreadsInv, smem, s>>>(w, g, plan, tw, pos, lg, st, m, bh, err);
-        else k_zfwd<T, false, false><<<blocks, kThreadsInv, smem, s>>>(w, g, plan, tw, pos, lg, st, m, 0, err);
+        if (use_tma) k_zfwd<T, true, false><<<grid, kThreadsInv, smem, s>>>(w, g, plan, tw, pos, lg, st, m, bh, err, nullptr);
+        else k_zfwd<T, false, false><<<grid, kThreadsInv, smem, s>>>(w, g, plan, tw, pos, lg, st, m, 0, err, B.mb);
     }
     return cudaGetLastError();
 }
@@ -685,14 +714,16 @@ cudaError_t launch_zu(int mode, const void* Nh, void* U, void* H, const Geom& g,
     cplx<T>* u = (cplx<T>*)U;
     cplx<T>* hh = (cplx<T>*)H;
     const bool sp = ex.sponge_c > 0 && mode != 1;
-#define FLUSI_ZU(M)                                                           \
-    if (sp)                                                                   \
-        k_zupdate<T, M, true><<<blocks, 256, 0, s>>>(n, u, hh, g, ex, st);    \
-    else                                                                      \
-        k_zupdate<T, M, false><<<blocks, 256, 0, s>>>(n, u, hh, g, ex, st);
+    const Batch& B = current_batch();
+    const dim3 grid(blocks, 1, B.n);
+#define FLUSI_ZU(M)                                                              \
+    if (sp)                                                                      \
+        k_zupdate<T, M, true><<<grid, 256, 0, s>>>(n, u, hh, g, ex, st, B.mb);   \
+    else                                                                         \
+        k_zupdate<T, M, false><<<grid, 256, 0, s>>>(n, u, hh, g, ex, st, B.mb);
     switch (mode) {
     case 0: FLUSI_ZU(0) break;
-    case 1: k_zupdate<T, 1, false><<<blocks, 256, 0, s>>>(n, u, hh, g, ex, st); break;
+    case 1: k_zupdate<T, 1, false><<<grid, 256, 0, s>>>(n, u, hh, g, ex, st, B.mb); break;
     case 2: FLUSI_ZU(2) break;
     case 3: FLUSI_ZU(3) break;
     case 4: FLUSI_ZU(4) break;

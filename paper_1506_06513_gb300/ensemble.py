@@ -6,7 +6,8 @@ The members (workloads.config_ensemble: uneven grids, flapping amplitudes,
 frequencies and Reynolds numbers, FP32) are stepped twice from the same
 state: one after another, each to the end with its own step graph, and
 together, with one graph per ensemble step holding a step of every member
-(flusi_ensemble_*).  Throughput is the sum over members of grid points times
+(flusi_ensemble_*), in which members of the same grid share one launch per
+kernel.  Throughput is the sum over members of grid points times
 steps, divided by the wall time between two device synchronizations.  The two
 runs use the same kernels in the same order per member, so their final states
 are compared bit for bit.  Prints one JSON line.
@@ -52,6 +53,7 @@ def run(count=40, steps=200, warmup=3, precision="fp32", seed=1506):
         s.step(warmup)
     ens.step(warmup)
     sync_all()
+    groups, grouped = ens.batches()
 
     # one by one
     _zero_states(solvers, fields)
@@ -90,7 +92,8 @@ def run(count=40, steps=200, warmup=3, precision="fp32", seed=1506):
             "unit": "grid-point steps/s", "steps": steps,
             "batched": work / bat_s, "sequential": work / seq_s,
             "speedup": seq_s / bat_s, "batched_s": bat_s, "sequential_s": seq_s,
-            "identical_to_one_by_one": bool(identical)}
+            "identical_to_one_by_one": bool(identical),
+            "shared_launch_groups": groups, "members_in_groups": grouped}
 
 
 def main():
