@@ -126,3 +126,69 @@ def test_split_form_needs_a_supported_length(fl):
         with pytest.raises(fl.FlusiError) as e:
             fl.flusi_create((nx, 16, 16), (1.0, 1.0, 1.0), 0.1, 1e-2, fl.FLUSI_FP32_SPLITBF16)
         assert e.value.code == fl.FLUSI_EINVAL
+
+
+WIDE_SPLIT = ((512, 16, 12), (8.0, 1.0, 0.75))
+
+
+@pytest.mark.parametrize("scheme", ["ab2_wake", "rk4_wake"])
+def test_split_form_with_the_wake_terms_and_rk4(fl, scheme):
+    """bf16x2 with the vorticity sponge and the Dirichlet layer (the sponge's
+    extra x round trip on the FP32 kernel, the layer's term in the tensor-core
+    pass), with AB2 and with RK4 (four tensor-core x passes per step): five
+    adaptive steps against the oracle."""
+    n, L = WIDE_SPLIT
+    cfg = {"n": n, "L": L, "nu": 0.01, "eta": 1e-2, "cfl": 0.1, "mean_mode": "fixed",
+           "u_inf": (0.3, 0.0, 0.0), "sponge_c": 0.1, "sponge_width": (L[0] / 6, 0.0, 0.0),
+           "layer_width": (L[0] / 16, 0.0, 0.0)}
+    if scheme == "rk4_wake":
+        cfg["time_scheme"] = "rk4"
+    ins = workloads.sphere((L[0] / 2, L[1] / 2, L[2] / 2), 0.3 * min(L[1], L[2]), profile="cos")
+    u0 = workloads.random_smooth_field(n, 9, mean=(0.3, 0.0, 0.0))
+    (u5,), rows, names = _run(fl, cfg, ins, u0, "bf16x2", (5,))
+    assert "xpass_tc" in names and "sponge_x" in names
+    if scheme == "rk4_wake":
+        assert "xpass_tc.4" in names
+    ref = oracle.Simulation(cfg, ins)
+    ref.set_state(u0)
+    ref_rows = ref.step(5)
+    t = TOL["bf16x2"]
+    e, er = rel_l2(u5, ref.get_state()), rows_err(rows, ref_rows)
+    print(f"bf16x2 {scheme} 512x16x12: u rel L2 {e:.2e} after 5 steps, rows {er:.2e}")
+    assert e <= t["u5"] and max_rel(u5, ref.get_state()) <= t["max5"] and er <= t["rows"]
+
+
+def test_split_form_restarts_bit_for_bit(fl):
+    """A checkpoint of a bf16x2 run (state, history, step state in FP32, the
+    same layout as FLUSI_FP32) continues bit for bit, and cannot be loaded into
+    a handle of another precision."""
+    import ctypes as C
+    n, L = WIDE_SPLIT
+    cfg = {"n": n, "L": L, "nu": 0.01, "eta": 1e-2, "cfl": 0.1, "mean_mode": "fixed",
+           "u_inf": (0.3, 0.0, 0.0)}
+    ins = workloads.sphere((L[0] / 2, L[1] / 2, L[2] / 2), 0.35 * min(L[1], L[2]), profile="cos")
+    u0 = workloads.random_smooth_field(n, 7, mean=(0.3, 0.0, 0.0))
+    a = fl.Solver(cfg, ins, precision="bf16x2")
+    a.set_state(u0)
+    a.step(7)
+    ua, rows_a = a.get_state(np.float32)[0], a.forces()[0]
+    a.close()
+    b = fl.Solver(cfg, ins, precision="bf16x2")
+    b.set_state(u0)
+    b.step(4)
+    nbytes = C.c_size_t()
+    assert fl.lib.flusi_checkpoint_bytes(b.h, C.byref(nbytes)) == fl.FLUSI_OK
+    buf = (C.c_char * nbytes.value)()
+    assert fl.lib.flusi_save(b.h, buf, nbytes) == fl.FLUSI_OK
+    rows_b = b.forces()[0]
+    b.close()
+    c = fl.Solver(cfg, ins, precision="bf16x2")
+    assert fl.lib.flusi_load(c.h, buf, nbytes) == fl.FLUSI_OK
+    c.step(3)
+    uc, rows_c = c.get_state(np.float32)[0], c.forces()[0]
+    c.close()
+    assert np.array_equal(uc, ua)
+    assert np.array_equal(np.vstack([rows_b, rows_c]), rows_a)
+    d = fl.Solver(cfg, ins, precision="fp32")
+    assert fl.lib.flusi_load(d.h, buf, nbytes) == fl.FLUSI_EINVAL
+    d.close()
