@@ -310,6 +310,17 @@ int flusi_profile_step(flusi_t h, int n, double *ms, const char **names, int *nk
  * stays usable.  0 < milliseconds <= 1000, else FLUSI_EINVAL. */
 int flusi_debug_wait_timeout(flusi_t h, double milliseconds);
 
+/* Host-side fault injection for testing the failure path (no passage of the
+ * paper; nothing on the device is made to fault): write re + i im into the
+ * state's Fourier coefficient of mode (mx, my, mz) of velocity component
+ * `component` (0..2), after the steps already enqueued.  mx in 0..Kx, my in
+ * -Ky..Ky, mz in -Kz..Kz (the kept modes, K = floor(n/3)), else FLUSI_EINVAL;
+ * FLUSI_ESTATE without a state.  A non-finite value makes the next step set
+ * FLUSI_ENONFINITE in the device status word (reported by the next
+ * synchronizing call; steps are refused until flusi_set_state).  No
+ * projection is applied to the written value.  Synchronizes. */
+int flusi_debug_inject(flusi_t h, int component, int mx, int my, int mz, double re, double im);
+
 /* Kernels launched per step (for launch accounting). */
 int flusi_kernels_per_step(flusi_t h, int *count);
 

@@ -110,6 +110,7 @@ def _load():
         "flusi_set_kinematics": ([h, C.POINTER(Insect)], ip),
         "flusi_get_body": ([h, dp], ip),
         "flusi_debug_wait_timeout": ([h, C.c_double], ip),
+        "flusi_debug_inject": ([h, ip, ip, ip, ip, C.c_double, C.c_double], ip),
         "flusi_step": ([h, ip], ip),
         "flusi_sync": ([h], ip),
         "flusi_forces": ([h, dp, ip, C.POINTER(C.c_int), C.POINTER(C.c_longlong)], ip),
@@ -355,6 +356,15 @@ def flusi_destroy(h):
 
 def flusi_last_error(h):
     return lib.flusi_last_error(h).decode()
+
+
+def flusi_debug_inject(h, component, mode, value):
+    """Write the complex `value` into the state's coefficient of `mode` =
+    (mx, my, mz) of velocity component `component` (a host-side fault
+    injector for the failure path)."""
+    v = complex(value)
+    _check(h, lib.flusi_debug_inject(h, int(component), int(mode[0]), int(mode[1]), int(mode[2]),
+                                     v.real, v.imag))
 
 
 def flusi_divergence(h):

@@ -1030,6 +1030,28 @@ int flusi_debug_wait_timeout(flusi_t h, double milliseconds)
     return FLUSI_OK;
 }
 
+int flusi_debug_inject(flusi_t h, int component, int mx, int my, int mz, double re, double im)
+{
+    int rc = check_ready(h, true);
+    if (rc) return rc;
+    const Geom& g = h->g;
+    if (component < 0 || component > 2 || mx < 0 || mx > g.Kx || my < -g.Ky || my > g.Ky || mz < -g.Kz ||
+        mz > g.Kz)
+        return fail(h, FLUSI_EINVAL, "component or mode outside the kept modes");
+    const int jy = my >= 0 ? my : g.My + my, jz = mz >= 0 ? mz : g.Mz + mz;
+    const size_t idx = (size_t)component * g.Mz * g.My * g.Mxp + ((size_t)jz * g.My + jy) * g.Mxp + mx;
+    // after the enqueued steps; the next step reads it
+    CK(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    if (h->prec == FLUSI_FP64) {
+        const double v[2] = {re, im};
+        CK(cudaMemcpy(h->ws + h->oU + idx * sizeof(v), v, sizeof(v), cudaMemcpyHostToDevice), "inject");
+    } else {
+        const float v[2] = {(float)re, (float)im};
+        CK(cudaMemcpy(h->ws + h->oU + idx * sizeof(v), v, sizeof(v), cudaMemcpyHostToDevice), "inject");
+    }
+    return FLUSI_OK;
+}
+
 int flusi_debug_fields(flusi_t h, void* out_dev)
 {
     int rc = check_ready(h, true);

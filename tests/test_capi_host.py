@@ -348,3 +348,10 @@ def test_fma_peak_validates_arguments(fl):
     for fp64, ms in ((2, 10.0), (0, 0.0), (1, -1.0), (0, 1e5)):
         assert fl.lib.flusi_fma_peak(fp64, ms, C.byref(f), None) == fl.FLUSI_EINVAL
     assert fl.lib.flusi_fma_peak(0, 10.0, None, None) == fl.FLUSI_EINVAL
+
+
+def test_debug_inject_needs_a_state(fl):
+    h = fl.flusi_create((16, 16, 16), (1.0, 1.0, 1.0), 0.1, 1e-2, fl.FLUSI_FP32)
+    assert fl.lib.flusi_debug_inject(h, 0, 1, 1, 1, 0.0, 0.0) == fl.FLUSI_ESTATE
+    assert fl.lib.flusi_debug_inject(None, 0, 1, 1, 1, 0.0, 0.0) == fl.FLUSI_EINVAL
+    fl.flusi_destroy(h)

@@ -275,6 +275,52 @@ def test_nonfinite_state_is_reported(fl):
     sim.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x2"])
+def test_fault_injected_into_a_running_state(fl, prec):
+    """A host-side injector (flusi_debug_inject) writes a coefficient of the
+    live state between steps: a finite value is stepped on (the state then
+    differs from the clean run); a NaN makes the next step report
+    FLUSI_ENONFINITE at the next synchronizing call, later steps are refused
+    with FLUSI_ESTATE, and a new state recovers the handle."""
+    if prec == "bf16x2":
+        n, L = (256, 16, 12), (4.0, 0.25, 0.1875)
+        cfg = {"n": n, "L": L, "nu": 0.01, "eta": 1e-2, "cfl": 0.1, "mean_mode": "fixed",
+               "u_inf": (0.3, 0.0, 0.0)}
+        ins = workloads.sphere((2.0, 0.125, 0.09375), 0.06, profile="cos")
+        u0 = workloads.random_smooth_field(n, 3, mean=(0.3, 0.0, 0.0))
+    else:
+        cfg, ins = CASES["insect_32"]()
+        u0 = _initial(cfg)
+    clean = fl.Solver(cfg, ins, precision=prec)
+    clean.set_state(u0)
+    clean.step(4)
+    u_clean = clean.get_state()[0]
+    clean.close()
+    sim = fl.Solver(cfg, ins, precision=prec)
+    sim.set_state(u0)
+    sim.step(3)
+    fl.flusi_debug_inject(sim.h, 1, (1, -2, 1), 0.01)
+    sim.step(1)
+    u = sim.get_state()[0]
+    assert np.isfinite(u).all() and not np.array_equal(u, u_clean)
+    with pytest.raises(fl.FlusiError) as e:
+        fl.flusi_debug_inject(sim.h, 0, (cfg["n"][0] // 3 + 1, 0, 0), 1.0)
+    assert e.value.code == fl.FLUSI_EINVAL
+    fl.flusi_debug_inject(sim.h, 2, (2, 1, -1), complex(float("nan"), 0.0))
+    sim.step(2)
+    with pytest.raises(fl.FlusiError) as e:
+        sim.sync()
+    assert e.value.code == fl.FLUSI_ENONFINITE
+    with pytest.raises(fl.FlusiError) as e:
+        sim.step(1)
+    assert e.value.code == fl.FLUSI_ESTATE
+    sim.set_state(u0)
+    sim.step(1)
+    rows, _ = sim.forces()
+    assert np.isfinite(rows).all()
+    sim.close()
+
+
 @pytest.mark.parametrize("n", [(32, 32, 32), (48, 36, 24), (24, 96, 64), (16, 1024, 12)])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_tma_tiles_equal_copied_tiles(fl, n, prec):
