@@ -57,27 +57,19 @@ k_ypass(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict
     const int x0 = xb * TX, z0 = zb << lgNP;
     const size_t plane = (size_t)g.ny * g.Mxp;
     cplx<T>* base = W + (size_t)c * g.nz * plane;
-
-    load_tables<T>(tws, nullptr, tw, nullptr, g.ny, 0);
-    load_inverse_pos(sinv, pos, g.ny);
     const int ny = g.ny, My = g.My, Ky = g.Ky;
-    const int ld = g.Mxp;   // row stride; a plane holds fewer than 2^31 values
-    // this thread's two adjacent columns in the transform stages (fft_run's
-    // map with V = 2; TX is even, so both lie in one plane)
-    constexpr int V = 2;
-    const int col = (threadIdx.x % (C / V)) * V;
-    const int z = z0 + (col >> lgTX), x = x0 + (col & (TX - 1));
-    const bool colok = z < g.nz && x < g.Mxp;   // Mxp is a multiple of 4
-    cplx<T>* gcol = base + (size_t)(colok ? z : 0) * plane + (colok ? x : 0);
+
+    // the tile's TMA boxes go out first, so that they are in flight while the
+    // block loads its twiddle and digit-reversal tables
+    __shared__ unsigned long long bar;
     if constexpr (TMA) {
-        __shared__ unsigned long long bar;
-        if (threadIdx.x == 0) mbar_init(&bar, 1);
-        __syncthreads();
-        // coordinates: x in reals (2 x0 sizeof(T) is a multiple of 128 bytes),
-        // plane c nz + z0, row; a box is bh rows of NP planes of TX columns
-        const int xr = 2 * x0, pl = c * g.nz + z0;
-        const unsigned box = (unsigned)(((size_t)bh << lgC) * sizeof(cplx<T>));
         if (threadIdx.x == 0) {
+            mbar_init(&bar, 1);
+            // coordinates: x in reals (2 x0 sizeof(T) is a multiple of 128
+            // bytes), plane c nz + z0, row; a box is bh rows of NP planes of TX
+            // columns
+            const int xr = 2 * x0, pl = c * g.nz + z0;
+            const unsigned box = (unsigned)(((size_t)bh << lgC) * sizeof(cplx<T>));
             if (INV) {
                 // modes 0..Ky to rows 0..Ky; modes Ky..2Ky to rows ny-Ky-1..ny-1
                 // (kb boxes of bh = (Ky + 1)/kb rows each; row ny-Ky-1 is
@@ -94,6 +86,19 @@ k_ypass(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict
                 for (int q = 0; q < nb; ++q) tma_load_3d(buf + ((size_t)(q * bh) << lgC), &tmap, xr, pl, q * bh, &bar);
             }
         }
+    }
+    load_tables<T>(tws, nullptr, tw, nullptr, g.ny, 0);
+    load_inverse_pos(sinv, pos, g.ny);
+    const int ld = g.Mxp;   // row stride; a plane holds fewer than 2^31 values
+    // this thread's two adjacent columns in the transform stages (fft_run's
+    // map with V = 2; TX is even, so both lie in one plane)
+    constexpr int V = 2;
+    const int col = (threadIdx.x % (C / V)) * V;
+    const int z = z0 + (col >> lgTX), x = x0 + (col & (TX - 1));
+    const bool colok = z < g.nz && x < g.Mxp;   // Mxp is a multiple of 4
+    cplx<T>* gcol = base + (size_t)(colok ? z : 0) * plane + (colok ? x : 0);
+    if constexpr (TMA) {
+        __syncthreads();   // the barrier's initialisation, before any thread waits on it
         const bool ok = mbar_wait(&bar, 0);
         if (__syncthreads_or(!ok)) {
             if (threadIdx.x == 0) atomicCAS(err, 0, (int)FLUSI_ETIMEOUT);

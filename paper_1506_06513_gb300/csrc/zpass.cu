@@ -237,6 +237,43 @@ k_zinv(const cplx<T>* __restrict__ U, cplx<T>* __restrict__ W, Geom g, FftPlan p
     const size_t Ustride = (size_t)g.Mz * Q;           // between components of U
     const size_t Wplane = (size_t)g.ny * g.Mxp;        // between z planes of W
     const size_t Wfield = (size_t)g.nz * Wplane;       // between fields of W
+    const int nz = g.nz, Kz = g.Kz, Mz = g.Mz;
+
+    // the TMA boxes of one velocity component into buf (thread 0): modes
+    // 0..Kz to rows 0..Kz, Kz..2Kz to rows nz-Kz-1..nz-1, the duplicate row
+    // cleared with the dropped modes after the wait.
+    // hint: 0 none, 1 keep the lines for a second read, 2 their last read
+    __shared__ unsigned long long bar;
+    unsigned phase = 0;
+    auto issue = [&](int comp, int hint) {
+        const unsigned box = (unsigned)(((size_t)bh << lgTX) * sizeof(cplx<T>));
+        const int kb = (Kz + 1) / bh;   // boxes per part
+        mbar_expect_tx(&bar, 2 * kb * box);
+        if (kZinvHints >= 1 && hint) {
+            const unsigned long long pol = hint == 1 ? l2_evict_last() : l2_evict_first();
+            for (int b = 0; b < kb; ++b) {
+                tma_load_3d_hint(buf + ((size_t)(b * bh) << lgTX), &umap, 2 * q0, b * bh, comp, &bar, pol);
+                tma_load_3d_hint(buf + ((size_t)(nz - Kz - 1 + b * bh) << lgTX), &umap, 2 * q0, Kz + b * bh,
+                                 comp, &bar, pol);
+            }
+        } else {
+            for (int b = 0; b < kb; ++b) {
+                tma_load_3d(buf + ((size_t)(b * bh) << lgTX), &umap, 2 * q0, b * bh, comp, &bar);
+                tma_load_3d(buf + ((size_t)(nz - Kz - 1 + b * bh) << lgTX), &umap, 2 * q0, Kz + b * bh, comp,
+                            &bar);
+            }
+        }
+    };
+    // the first component's boxes go out before the block loads its tables
+    // (u_x for the velocity alone, u_z when the vorticity is formed too)
+    bool pre_issued = false;
+    if constexpr (TMA) {
+        if (threadIdx.x == 0) {
+            mbar_init(&bar, 1);
+            issue(nf < 6 ? 0 : 2, nf < 6 ? 0 : 2);
+        }
+        pre_issued = true;
+    }
     load_tables<T>(tws, nullptr, tw, nullptr, g.nz, 0);
     load_inverse_pos(sinv, pos, g.nz);
 
@@ -251,16 +288,9 @@ k_zinv(const cplx<T>* __restrict__ U, cplx<T>* __restrict__ W, Geom g, FftPlan p
     const T two_pi = T(6.283185307179586476925286766559);
     const T kxv[V] = {two_pi * T(x) / T(g.Lx), two_pi * T(x + 1) / T(g.Lx)};
     const T ky = two_pi * T(mode_of(jy, g.Ky)) / T(g.Ly);
-    const int nz = g.nz, Kz = g.Kz, Mz = g.Mz;
     cplx<T>* Wq = W + (qok ? q : 0);
-    __syncthreads();
+    __syncthreads();   // tables, and the barrier's initialisation before any thread waits on it
 
-    __shared__ unsigned long long bar;
-    unsigned phase = 0;
-    if (TMA) {
-        if (threadIdx.x == 0) mbar_init(&bar, 1);
-        __syncthreads();
-    }
     // component `comp` of the tile into buf: kept modes at their z rows, zeros
     // elsewhere (U's row padding x >= Mx is zero); by two TMA boxes (modes
     // 0..Kz to rows 0..Kz, Kz..2Kz to rows nz-Kz-1..nz-1, the duplicate row
@@ -269,27 +299,12 @@ k_zinv(const cplx<T>* __restrict__ U, cplx<T>* __restrict__ W, Geom g, FftPlan p
     // hint: 0 none, 1 keep the lines for a second read, 2 their last read
     auto stage_in = [&](int comp, int hint) -> bool {
         if constexpr (TMA) {
-            if (threadIdx.x == 0) {
+            if (threadIdx.x == 0 && !pre_issued) {
                 // earlier generic writes to buf before the asynchronous proxy's
                 fence_proxy_async();
-                const unsigned box = (unsigned)(((size_t)bh << lgTX) * sizeof(cplx<T>));
-                const int kb = (Kz + 1) / bh;   // boxes per part
-                mbar_expect_tx(&bar, 2 * kb * box);
-                if (kZinvHints >= 1 && hint) {
-                    const unsigned long long pol = hint == 1 ? l2_evict_last() : l2_evict_first();
-                    for (int b = 0; b < kb; ++b) {
-                        tma_load_3d_hint(buf + ((size_t)(b * bh) << lgTX), &umap, 2 * q0, b * bh, comp, &bar, pol);
-                        tma_load_3d_hint(buf + ((size_t)(nz - Kz - 1 + b * bh) << lgTX), &umap, 2 * q0,
-                                         Kz + b * bh, comp, &bar, pol);
-                    }
-                } else {
-                    for (int b = 0; b < kb; ++b) {
-                        tma_load_3d(buf + ((size_t)(b * bh) << lgTX), &umap, 2 * q0, b * bh, comp, &bar);
-                        tma_load_3d(buf + ((size_t)(nz - Kz - 1 + b * bh) << lgTX), &umap, 2 * q0, Kz + b * bh,
-                                    comp, &bar);
-                    }
-                }
+                issue(comp, hint);
             }
+            pre_issued = false;
             const bool ok = mbar_wait(&bar, phase);
             if (__syncthreads_or(!ok)) {
                 if (threadIdx.x == 0) atomicCAS(err, 0, (int)FLUSI_ETIMEOUT);
@@ -397,19 +412,22 @@ k_zfwd(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict_
     const int nqb = ceil_div(Q, TX);
     const int c = blockIdx.x / nqb, q0 = (blockIdx.x - c * nqb) * TX;
     const size_t Wplane = (size_t)g.ny * g.Mxp;
-    load_tables<T>(tws, nullptr, tw, nullptr, nz, 0);
-    load_inverse_pos(sinv, pos, nz);
+    // the tile's TMA boxes (nz / bh boxes of bh rows of TX columns) go out
+    // first, in flight while the block loads its tables
+    __shared__ unsigned long long bar;
     if constexpr (TMA) {
-        // nz / bh boxes of bh rows of TX columns
-        __shared__ unsigned long long bar;
-        if (threadIdx.x == 0) mbar_init(&bar, 1);
-        __syncthreads();
         if (threadIdx.x == 0) {
+            mbar_init(&bar, 1);
             const unsigned box = (unsigned)(((size_t)bh << lgTX) * sizeof(cplx<T>));
             const int nb = nz / bh;
             mbar_expect_tx(&bar, nb * box);
             for (int b = 0; b < nb; ++b) tma_load_3d(buf + ((size_t)(b * bh) << lgTX), &wmap, 2 * q0, b * bh, c, &bar);
         }
+    }
+    load_tables<T>(tws, nullptr, tw, nullptr, nz, 0);
+    load_inverse_pos(sinv, pos, nz);
+    if constexpr (TMA) {
+        __syncthreads();   // the barrier's initialisation, before any thread waits on it
         const bool ok = mbar_wait(&bar, 0);
         if (__syncthreads_or(!ok)) {
             if (threadIdx.x == 0) atomicCAS(err, 0, (int)FLUSI_ETIMEOUT);
