@@ -238,35 +238,30 @@ __device__ __forceinline__ cplx<T> r2c_post(cplx<T> Zk, cplx<T> Zm, cplx<T> wk)
 template <typename T, int R, int L>
 __device__ __forceinline__ void sq_exchange_pre(cplx<T>* x, int j, const cplx<T>* twx)
 {
-    // x[t] holds X[j + L t]; on return x[t] = Z[j + L t] (c2r pre-processing)
+    // x[t] holds X[j + L t]; on return x[t] = Z[j + L t] (c2r pre-processing).
+    // The mirror nh - k of k = j + L t is element R-1-t of lane L-j for j != 0,
+    // and lane 0's own element R-t (t = 0: X[nh], a dropped mode, zero).  One
+    // branch-free loop serves both: lane 0 "sends itself" elements s+1 and R-s
+    // where the other lanes send elements s and R-1-s.  The pairs (s, R-1-s)
+    // go from the middle outwards, so every element read is still unmodified
+    // (element s+1 was overwritten the iteration before: carried from there).
+    const int partner = (L - j) & (L - 1);
+    const bool self = j == 0;
+    cplx<T> carry = x[R / 2];   // the original element s + 1
 #pragma unroll
-    for (int s = 0; s < R / 2; ++s) {
-        cplx<T> a, b;   // partner's X[s] and X[R-1-s]
-        a.x = __shfl_sync(0xffffffffu, x[s].x, (L - j) & (L - 1), L);
-        a.y = __shfl_sync(0xffffffffu, x[s].y, (L - j) & (L - 1), L);
-        b.x = __shfl_sync(0xffffffffu, x[R - 1 - s].x, (L - j) & (L - 1), L);
-        b.y = __shfl_sync(0xffffffffu, x[R - 1 - s].y, (L - j) & (L - 1), L);
-        if (j != 0) {
-            // mirror of element t is the partner's element R-1-t
-            const cplx<T> zs = c2r_pre<T>(x[s], b, twx[j + L * s]);
-            const cplx<T> zt = c2r_pre<T>(x[R - 1 - s], a, twx[j + L * (R - 1 - s)]);
-            x[s] = zs;
-            x[R - 1 - s] = zt;
-        }
-    }
-    if (j == 0) {
-        // mirror of element t is own element R - t (element 0 mirrors X[nh] = 0)
-        const cplx<T> z0 = c2r_pre<T>(x[0], mkc<T>(0, 0), twx[0]);
-        const cplx<T> zh = c2r_pre<T>(x[R / 2], x[R / 2], twx[L * (R / 2)]);
-#pragma unroll
-        for (int t = 1; t < R / 2; ++t) {
-            const cplx<T> za = c2r_pre<T>(x[t], x[R - t], twx[L * t]);
-            const cplx<T> zb = c2r_pre<T>(x[R - t], x[t], twx[L * (R - t)]);
-            x[t] = za;
-            x[R - t] = zb;
-        }
-        x[0] = z0;
-        x[R / 2] = zh;
+    for (int s = R / 2 - 1; s >= 0; --s) {
+        const cplx<T> xs = x[s], xt = x[R - 1 - s];
+        const cplx<T> up = s == 0 ? mkc<T>(0, 0) : x[(R - s) & (R - 1)];
+        const cplx<T> sa = self ? carry : xs;   // mirror of element R-1-s
+        const cplx<T> sb = self ? up : xt;      // mirror of element s
+        cplx<T> a, b;
+        a.x = __shfl_sync(0xffffffffu, sa.x, partner, L);
+        a.y = __shfl_sync(0xffffffffu, sa.y, partner, L);
+        b.x = __shfl_sync(0xffffffffu, sb.x, partner, L);
+        b.y = __shfl_sync(0xffffffffu, sb.y, partner, L);
+        x[s] = c2r_pre<T>(xs, b, twx[j + L * s]);
+        x[R - 1 - s] = c2r_pre<T>(xt, a, twx[j + L * (R - 1 - s)]);
+        carry = xs;
     }
 }
 
