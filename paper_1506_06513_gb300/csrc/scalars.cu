@@ -374,9 +374,17 @@ __global__ void k_reset_state(StepState* st, StepCoef* coef)
 // One block.  Reduces part[nparts][kNumSums] in a fixed order, then forms the
 // step's scalars.  `opts` = {cfl, dt_fixed, dt_max}; dt_diff > 0 caps the
 // adaptive step (the explicit-diffusion limit of RK4).
-__global__ void k_scalars(Geom g, const double* part, int nparts, StepState* st, StepCoef* coef,
-                          double* rows, int ring, double* etab, double3 opts, double dt_diff,
-                          const Frame* fr, flusi_insect* ins, const Member* mb)
+//
+// FP64 arithmetic is a small fraction of FP32 here, and a warp instruction
+// costs the FP64 units the same with one lane active as with 32: the work is
+// spread over lanes (a slot and segment of CTAs per thread, a force or moment
+// component per lane) and each scalar is computed once, not by every thread.
+constexpr int kScalarSeg = 6;   // CTA segments per slot: kNumSums * 6 = 240 threads
+static_assert(kNumSums * kScalarSeg <= 256, "k_scalars runs 256 threads");
+
+__global__ void k_scalars(Geom g, const double* part, int nparts, StepState* st, StepCoef* coef, double* rows,
+                          int ring, double* etab, double3 opts, double dt_diff, const Frame* fr, flusi_insect* ins,
+                          const Member* mb)
 {
     if (mb) {
         const Member& m = mb[blockIdx.z];
@@ -389,10 +397,10 @@ __global__ void k_scalars(Geom g, const double* part, int nparts, StepState* st,
         ins = m.ins;
         g.nu = m.nu;
     }
-    __shared__ double red[kNumSums][33];
+    __shared__ double seg[kNumSums][kScalarSeg];
     __shared__ double tot[kNumSums];
+    __shared__ double sh_dt;
     const int tid = threadIdx.x, T = blockDim.x;
-    const int warp = tid / 32, lane = tid % 32;
 
     // every thread reads the state before the first barrier; thread 0 writes
     // it only after the last one
@@ -403,25 +411,26 @@ __global__ void k_scalars(Geom g, const double* part, int nparts, StepState* st,
         if (tid == 0) coef->skip = 1;
         return;
     }
-    // per slot: strided partial by thread, warp tree, then warps in order
-    for (int k = 0; k < kNumSums; ++k) {
+    // slot k, segment s: the partials of CTAs [s c, (s + 1) c) in order; then
+    // the segments in order
+    if (tid < kNumSums * kScalarSeg) {
+        const int k = tid % kNumSums, sg = tid / kNumSums;
+        const int chunk = (nparts + kScalarSeg - 1) / kScalarSeg;
+        const int i0 = sg * chunk, i1 = min(nparts, i0 + chunk);
         const bool is_max = (k == kSumUmax2 || k == kSumBad);
         double acc = 0.0;
-        for (int i = tid; i < nparts; i += T) {
-            double v = part[(size_t)i * kNumSums + k];
+#pragma unroll 4
+        for (int i = i0; i < i1; ++i) {
+            const double v = part[(size_t)i * kNumSums + k];
             acc = is_max ? fmax(acc, v) : acc + v;
         }
-        for (int o = 16; o > 0; o >>= 1) {
-            double w = __shfl_down_sync(0xffffffffu, acc, o);
-            acc = is_max ? fmax(acc, w) : acc + w;
-        }
-        if (lane == 0) red[k][warp] = acc;
+        seg[k][sg] = acc;
     }
     __syncthreads();
     if (tid < kNumSums) {
         const bool is_max = (tid == kSumUmax2 || tid == kSumBad);
         double a = 0.0;
-        for (int w = 0; w < T / 32; ++w) a = is_max ? fmax(a, red[tid][w]) : a + red[tid][w];
+        for (int s2 = 0; s2 < kScalarSeg; ++s2) a = is_max ? fmax(a, seg[tid][s2]) : a + seg[tid][s2];
         tot[tid] = a;
     }
     __syncthreads();
@@ -436,16 +445,21 @@ __global__ void k_scalars(Geom g, const double* part, int nparts, StepState* st,
 
     // time step (Algorithm 1 step b)
     const double umax = sqrt(tot[kSumUmax2]);
-    double dt;
-    if (opts.y > 0.0) {
-        dt = opts.y;
-    } else {
-        const double dmin = fmin(g.dx, fmin(g.dy, g.dz));
-        dt = g.eta;
-        if (umax > 0.0) dt = fmin(dt, opts.x * dmin / umax);
-        if (opts.z > 0.0) dt = fmin(dt, opts.z);
-        if (dt_diff > 0.0) dt = fmin(dt, dt_diff);
+    if (tid == 0) {
+        double dt;
+        if (opts.y > 0.0) {
+            dt = opts.y;
+        } else {
+            const double dmin = fmin(g.dx, fmin(g.dy, g.dz));
+            dt = g.eta;
+            if (umax > 0.0) dt = fmin(dt, opts.x * dmin / umax);
+            if (opts.z > 0.0) dt = fmin(dt, opts.z);
+            if (dt_diff > 0.0) dt = fmin(dt, dt_diff);
+        }
+        sh_dt = dt;
     }
+    __syncthreads();
+    const double dt = sh_dt;
     const int first = (n == 0);
 
     // integrating factors, separable per axis: E1 = e^{-nu |k|^2 dt},
@@ -461,7 +475,46 @@ __global__ void k_scalars(Geom g, const double* part, int nparts, StepState* st,
         etab[i] = exp(-g.nu * k * k * tau);
     }
 
-    __syncthreads();
+    // force row: lane 3 p + i of warp 0 takes component i of part p; then the
+    // wing power (lanes 0, 1) and the rest (lane 0)
+    double* row = rows + (size_t)(n % ring) * kRowCols;
+    if (tid < 9) {
+        const int p = tid / 3, i = tid % 3;
+        const double dV = g.dx * g.dy * g.dz;
+        const double* s = tot + 12 * p;
+        double Fv = s[i] * dV / g.eta, Mv = s[3 + i] * dV / g.eta;
+        const double Is = s[6 + i] * dV, Js = s[9 + i] * dV;
+        if (!first) {
+            const double inv_dtp = 1.0 / dt_prev;
+            Fv += (Is - st->Is_prev[p][i]) * inv_dtp;
+            Mv += (Js - st->Js_prev[p][i]) * inv_dtp;
+        }
+        row[2 + 6 * p + i] = Fv;
+        row[5 + 6 * p + i] = Mv;
+        st->Is_prev[p][i] = Is;
+        st->Js_prev[p][i] = Js;
+    }
+    __syncwarp();
+    const Frame& F = *fr;
+    if (tid < 2) {   // wing power at t^n (Sec. 3.5, Eq. insect_power)
+        const int s = tid;
+        double pa = 0.0, pi = 0.0;
+        if (s < ins->nwings) {
+            const double* m = row + 5 + 6 * (1 + s);
+            pa = -(m[0] * F.Ow[s][0] + m[1] * F.Ow[s][1] + m[2] * F.Ow[s][2]);
+            const double* J = ins->J_wing;   // xx yy zz xy xz yz
+            const M3 Jm = {{J[0], J[3], J[4], J[3], J[1], J[5], J[4], J[5], J[2]}};
+            const double* w = F.Oww[s];
+            double Jw[3], Jdw[3], c[3];
+            apply(Jm, w, Jw);
+            apply(Jm, F.dOww[s], Jdw);
+            cross3(w, Jw, c);
+            pi = w[0] * (Jdw[0] + c[0]) + w[1] * (Jdw[1] + c[1]) + w[2] * (Jdw[2] + c[2]);
+        }
+        row[22 + s] = pa;
+        row[24 + s] = pi;
+    }
+    __syncwarp();
     if (tid == 0) {
         StepCoef c;
         c.dt = dt;
@@ -478,49 +531,10 @@ __global__ void k_scalars(Geom g, const double* part, int nparts, StepState* st,
             c.c_old = dt * 0.5 * r;
         }
         *coef = c;
-
-        // force row
-        const double dV = g.dx * g.dy * g.dz;
-        double* row = rows + (size_t)(n % ring) * kRowCols;
         row[0] = st->t;
         row[1] = dt;
-        for (int p = 0; p < 3; ++p) {
-            const double* s = tot + 12 * p;
-            for (int i = 0; i < 3; ++i) {
-                double Fv = s[i] * dV / g.eta, Mv = s[3 + i] * dV / g.eta;
-                double Is = s[6 + i] * dV, Js = s[9 + i] * dV;
-                if (!first) {
-                    Fv += (Is - st->Is_prev[p][i]) / dt_prev;
-                    Mv += (Js - st->Js_prev[p][i]) / dt_prev;
-                }
-                row[2 + 6 * p + i] = Fv;
-                row[5 + 6 * p + i] = Mv;
-                st->Is_prev[p][i] = Is;
-                st->Js_prev[p][i] = Js;
-            }
-        }
-        row[20] = 0.5 * tot[kSumEkin] * dV;
+        row[20] = 0.5 * tot[kSumEkin] * g.dx * g.dy * g.dz;
         row[21] = umax;
-
-        // wing power at t^n (Sec. 3.5, Eq. insect_power)
-        const Frame& F = *fr;
-        for (int s = 0; s < 2; ++s) {
-            double pa = 0.0, pi = 0.0;
-            if (s < ins->nwings) {
-                const double* m = row + 5 + 6 * (1 + s);
-                pa = -(m[0] * F.Ow[s][0] + m[1] * F.Ow[s][1] + m[2] * F.Ow[s][2]);
-                const double* J = ins->J_wing;   // xx yy zz xy xz yz
-                const M3 Jm = {{J[0], J[3], J[4], J[3], J[1], J[5], J[4], J[5], J[2]}};
-                const double* w = F.Oww[s];
-                double Jw[3], Jdw[3], c[3];
-                apply(Jm, w, Jw);
-                apply(Jm, F.dOww[s], Jdw);
-                cross3(w, Jw, c);
-                pi = w[0] * (Jdw[0] + c[0]) + w[1] * (Jdw[1] + c[1]) + w[2] * (Jdw[2] + c[2]);
-            }
-            row[22 + s] = pa;
-            row[24 + s] = pi;
-        }
 
         if (ins->free_flight) advance_body(ins, st, F, row, dt, first ? 0.0 : dt / dt_prev, first);
 
