@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include <cmath>
+#include <cstddef>
 
 #include "../../include/flusi.h"
 
@@ -119,6 +120,74 @@ struct Shape {
     double arc_r, arc_x, arc_z, arc_ux, arc_uz;
     double arc_end[2][2];
 };
+
+// The frame block and mask shape in the x pass's precision T.  The kinematics
+// kernel writes one per precision after the FP64 frame, at fixed offsets of
+// the frame slot (frame_t), so the x-pass blocks only copy bytes.
+template <typename T> struct FrameT {
+    T xc[3], uc[3], Ob[3], Mb[9], Mw[2][9], pv[2][3], Ow[2][3], box[3][6];
+    int active[3];
+    T h, a, b, c_le, c_te, R, ht, inv_eta;
+    int body_type, profile, wing_shape, ncontour;
+    T head_x0[3], head_r, eye_x0[3], eye_r;
+    T cxc, cyc, ca0, ca[FLUSI_MAX_CONTOUR], cb[FLUSI_MAX_CONTOUR];
+    T arc_r, arc_x, arc_z, arc_ux, arc_uz, arc_end[2][2];
+};
+
+constexpr size_t align16(size_t n) { return (n + 15) / 16 * 16; }
+constexpr size_t kFrameT32Off = align16(sizeof(Frame));
+constexpr size_t kFrameT64Off = kFrameT32Off + align16(sizeof(FrameT<float>));
+constexpr size_t kFrameSlot = kFrameT64Off + align16(sizeof(FrameT<double>));   // bytes of a frame slot
+
+template <typename T> __host__ __device__ inline const FrameT<T>* frame_t(const Frame* f)
+{
+    return reinterpret_cast<const FrameT<T>*>(reinterpret_cast<const char*>(f) +
+                                              (sizeof(T) == 4 ? kFrameT32Off : kFrameT64Off));
+}
+
+// Runs of T fields of FrameT that mirror runs of doubles of Frame or Shape,
+// in the same order (checked below), so the lanes of a warp convert them
+// with uniform code.
+template <typename T> struct FrameTRuns {
+    static_assert(offsetof(FrameT<T>, box) == offsetof(FrameT<T>, xc) + 48 * sizeof(T), "FrameT xc..Ow");
+    static_assert(offsetof(Frame, Oww) == offsetof(Frame, xc) + 48 * sizeof(double), "Frame xc..Ow");
+    static_assert(offsetof(FrameT<T>, inv_eta) == offsetof(FrameT<T>, h) + 7 * sizeof(T), "FrameT h..ht");
+    static_assert(offsetof(Shape, head_x0) == offsetof(Shape, h) + 7 * sizeof(double), "Shape h..ht");
+    static_assert(offsetof(FrameT<T>, cxc) == offsetof(FrameT<T>, head_x0) + 8 * sizeof(T), "FrameT head, eyes");
+    static_assert(offsetof(Shape, ncontour) == offsetof(Shape, head_x0) + 8 * sizeof(double), "Shape head, eyes");
+    static_assert(offsetof(FrameT<T>, arc_end) + 4 * sizeof(T) == offsetof(FrameT<T>, cxc) + 76 * sizeof(T),
+                  "FrameT contour..arc");
+    static_assert(sizeof(Shape) == offsetof(Shape, contour_xc) + 76 * sizeof(double), "Shape contour..arc");
+};
+
+// FrameT<T> from the frame block and the shape, by the 32 lanes of one warp
+// (lane = 0..31); `F` and `S` readable by every lane.
+template <typename T>
+__device__ inline void frame_to_t(FrameT<T>* f, const Frame* F, const Shape* S, double inv_eta, int lane)
+{
+    (void)sizeof(FrameTRuns<T>);
+    auto run = [&](size_t dst, const void* base, size_t src, int n) {
+        T* d = reinterpret_cast<T*>(reinterpret_cast<char*>(f) + dst);
+        const double* q = reinterpret_cast<const double*>(reinterpret_cast<const char*>(base) + src);
+        for (int i = lane; i < n; i += 32) d[i] = T(q[i]);
+    };
+    run(offsetof(FrameT<T>, xc), F, offsetof(Frame, xc), 48);
+    run(offsetof(FrameT<T>, box), F, offsetof(Frame, box), 18);
+    run(offsetof(FrameT<T>, h), S, offsetof(Shape, h), 7);
+    run(offsetof(FrameT<T>, head_x0), S, offsetof(Shape, head_x0), 8);
+    run(offsetof(FrameT<T>, cxc), S, offsetof(Shape, contour_xc), 76);
+    if (lane < 3) {
+        const bool absent = (lane == 0 && S->body_type == 0) || (lane == 1 && S->nwings < 1) ||
+                            (lane == 2 && S->nwings < 2);
+        f->active[lane] = absent ? 0 : F->active[lane];
+    } else if (lane == 3) {
+        f->inv_eta = T(inv_eta);
+        f->body_type = S->body_type;
+        f->profile = S->profile;
+        f->wing_shape = S->wing_shape;
+        f->ncontour = S->ncontour;
+    }
+}
 
 // Why a descriptor cannot be used, or nullptr (checks shared by every entry
 // point that takes one; the free-flight fields are checked where they apply).

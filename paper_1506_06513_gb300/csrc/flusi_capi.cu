@@ -231,7 +231,7 @@ void layout(flusi_t h)
     h->opz = o; o = align256(o + sizeof(int) * g.nz);
     h->opzi = o; o = align256(o + sizeof(int) * g.nz);
     h->opyh = o; o = align256(o + sizeof(int) * (g.ny / 2));
-    h->oframe = o; o = align256(o + sizeof(Frame));
+    h->oframe = o; o = align256(o + kFrameSlot);
     h->oins = o; o = align256(o + sizeof(flusi_insect));
     h->ostate = o; o = align256(o + sizeof(StepState));
     h->ocoef = o; o = align256(o + sizeof(StepCoef));
@@ -384,7 +384,7 @@ cudaError_t enqueue_step(flusi_t h, cudaStream_t s, cudaEvent_t* ev, const char*
         }
         k_kinematics<<<dim3(1, 1, current_batch().n), 32, 0, skq>>>(
             at<flusi_insect>(h, h->oins), st, coef, at<Frame>(h, h->oframe), box_margin(h), frac[q],
-            current_batch().mb);
+            current_batch().mb, make_shape(h), 1, 1.0 / g.eta);
         if ((e = cudaGetLastError())) return e;
         if (br && (e = cudaEventRecord(h->ev_kin, sk))) return e;
         mark(nm[1]);
@@ -1063,7 +1063,8 @@ int flusi_debug_fields(flusi_t h, void* out_dev)
     void* W = h->ws + h->oW;
     StepState* st = at<StepState>(h, h->ostate);
     k_kinematics<<<1, 32, 0, s>>>(at<flusi_insect>(h, h->oins), st, at<StepCoef>(h, h->ocoef),
-                                  at<Frame>(h, h->oframe), box_margin(h), 0.0, nullptr);
+                                  at<Frame>(h, h->oframe), box_margin(h), 0.0, nullptr, make_shape(h), 1,
+                                  1.0 / g.eta);
     CK(cudaGetLastError(), "kinematics");
     CK(launch_zinv(fp64, h->ws + h->oU, W, g, h->pzi, at<double2>(h, h->otz), at<int>(h, h->opzi), 6, nullptr,
                    &h->zmaps.u, h->zmaps.u_bh, status_word(h), s),

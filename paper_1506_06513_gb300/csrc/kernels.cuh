@@ -31,7 +31,7 @@ Batch& current_batch();
 
 // kinematics / scalars (scalars.cu); mb: see Batch
 __global__ void k_kinematics(const flusi_insect* ins, const StepState* st, const StepCoef* coef, Frame* fr,
-                             double h, double frac, const Member* mb);
+                             double h, double frac, const Member* mb, Shape S, int with_t, double inv_eta);
 __global__ void k_reset_state(StepState* st, StepCoef* coef);
 __global__ void k_wait_probe(int* err, long long max_cycles);
 __global__ void k_scalars(Geom g, const double* part, int nparts, StepState* st, StepCoef* coef,

@@ -171,12 +171,13 @@ __device__ void advance_body(flusi_insect* ins, StepState* st, const Frame& F, c
 
 }  // namespace
 
-// frac = 0: at the state's time; frac > 0: at t0 + frac dt of the current
-// step (the later RK4 stages, after k_scalars has written t0 and dt).
-__global__ void k_kinematics(const flusi_insect* ins, const StepState* st, const StepCoef* coef, Frame* fr,
-                             double h, double frac, const Member* mb)
+// The FP64 frame block (one thread): body and wing orientations and angular
+// velocities, pivots, and the parts' bounding boxes.  frac = 0: at the state's
+// time; frac > 0: at t0 + frac dt of the current step (the later RK4 stages,
+// after k_scalars has written t0 and dt).
+static __device__ void kinematics_frame(const flusi_insect* ins, const StepState* st, const StepCoef* coef,
+                                        Frame* fr, double h, double frac, const Member* mb)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
     if (mb) {
         const Member& m = mb[blockIdx.z];
         ins = m.ins;
@@ -346,6 +347,27 @@ __global__ void k_kinematics(const flusi_insect* ins, const StepState* st, const
     }
     *fr = F;
 }
+
+// One warp.  Thread 0 forms the FP64 frame block; with `with_t`, the warp
+// then writes its FP32 and FP64 copies with the mask shape S (FrameT, at their
+// offsets of the frame slot) for the x pass.
+__global__ void k_kinematics(const flusi_insect* ins, const StepState* st, const StepCoef* coef, Frame* fr,
+                             double h, double frac, const Member* mb, Shape S, int with_t, double inv_eta)
+{
+    __shared__ Shape sS;
+    if (blockIdx.x != 0) return;
+    if (mb) fr = mb[blockIdx.z].fr;
+    if (threadIdx.x == 0) {
+        kinematics_frame(ins, st, coef, fr, h, frac, mb);
+        if (with_t) sS = S;
+    }
+    if (!with_t || threadIdx.x >= 32) return;
+    __syncwarp();
+    const int lane = threadIdx.x;
+    frame_to_t<float>(const_cast<FrameT<float>*>(frame_t<float>(fr)), fr, &sS, inv_eta, lane);
+    frame_to_t<double>(const_cast<FrameT<double>*>(frame_t<double>(fr)), fr, &sS, inv_eta, lane);
+}
+
 
 // A bounded wait on a barrier that nothing completes (the arrival count is 2
 // and one thread arrives once): gives up after max_cycles and reports as the

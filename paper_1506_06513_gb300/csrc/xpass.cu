@@ -189,7 +189,7 @@ k_xpass(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict
     load_tables<T>(tws, spos, tw, pos, nx, nh);
     if (kPhys) {
         for (int i = tid; i < kWarpsX * 36; i += kThreadsX) wacc[i] = 0.0;
-        if (tid == 0) setup_frame<T>(*Fs, *ex.frame, ex.shape, 1.0 / g.eta);
+        load_frame_t<T>(Fs, ex.frame);
     }
     __syncthreads();
     for (int p = tid; p < nh; p += kThreadsX) ipos[spos[p]] = p;
@@ -532,7 +532,7 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
         tw2[q * L + (jj ^ q)] = mkc<T>(T(w.x), T(w.y));
     }
     for (int i = tid; i < kWarpsX * 36; i += blockDim.x) wacc[i] = 0.0;
-    if (tid == 0) setup_frame<T>(*Fs, *ex.frame, ex.shape, 1.0 / g.eta);
+    load_frame_t<T>(Fs, ex.frame);
     __syncthreads();
 
     double e_acc = 0.0;
@@ -1338,7 +1338,7 @@ extern "C" int flusi_penalization_sums_noalloc(int nx, int ny, int nz, const dou
     const long long want = (N + kNoallocThreads - 1) / kNoallocThreads;
     const int grid = (int)(want < kNoallocMaxCtas ? want : kNoallocMaxCtas);
     k_noalloc_header<<<1, 1, 0, s>>>(ins, t, d_ins, d_st);
-    k_kinematics<<<1, 32, 0, s>>>(d_ins, d_st, nullptr, d_fr, margin, 0.0, nullptr);
+    k_kinematics<<<1, 32, 0, s>>>(d_ins, d_st, nullptr, d_fr, margin, 0.0, nullptr, sh, 0, 0.0);
     k_noalloc_sums<<<grid, kNoallocThreads, 0, s>>>(u_dev, nx, ny, nz, dx, dy, dz, d_fr, sh, part);
     k_noalloc_reduce<<<1, 64, 0, s>>>(part, grid, dx * dy * dz, eta, sums);
     cudaError_t e = cudaGetLastError();

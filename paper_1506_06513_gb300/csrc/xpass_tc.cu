@@ -210,10 +210,9 @@ k_xpass_tc(float2* __restrict__ W, Geom g, const double2* __restrict__ tw, XExtr
         build_dft_b<P>(sm + Lt::oBQ, Lt::kBQ, Q, false, tw, nx);
         build_dft_b<P>(sm + Lt::oBQ + P * Lt::kBQ, Lt::kBQ, Q, true, tw, nx);
     }
-    if (tid == 0) {
-        setup_frame<float>(*Fs, *ex.frame, ex.shape, 1.0 / g.eta);
+    load_frame_t<float>(Fs, ex.frame);
+    if (tid == 0)
         for (int i = 0; i < S + 2; ++i) mbar_init(full + i, 1);
-    }
     if (warp == 0) tc::tmem_alloc(tslot, kTcCols);
     fence_proxy_async();   // the B matrices, written by these threads, before the tensor cores read them
     tc::fence_before_sync();

@@ -12,15 +12,15 @@
 namespace flusi {
 namespace {
 
-template <typename T> struct FrameT {
-    T xc[3], uc[3], Ob[3], Mb[9], Mw[2][9], pv[2][3], Ow[2][3], box[3][6];
-    int active[3];
-    T h, a, b, c_le, c_te, R, ht, inv_eta;
-    int body_type, profile, wing_shape, ncontour;
-    T head_x0[3], head_r, eye_x0[3], eye_r;
-    T cxc, cyc, ca0, ca[FLUSI_MAX_CONTOUR], cb[FLUSI_MAX_CONTOUR];
-    T arc_r, arc_x, arc_z, arc_ux, arc_uz, arc_end[2][2];
-};
+// The block's copy of the frame in T (written by the kinematics kernel),
+// by every thread of the block in 4-byte words.
+template <typename T> __device__ __forceinline__ void load_frame_t(FrameT<T>* dst, const Frame* fr)
+{
+    static_assert(sizeof(FrameT<T>) % 4 == 0, "word copy");
+    const unsigned* src = reinterpret_cast<const unsigned*>(frame_t<T>(fr));
+    unsigned* d = reinterpret_cast<unsigned*>(dst);
+    for (int i = threadIdx.x; i < (int)(sizeof(FrameT<T>) / 4); i += blockDim.x) d[i] = src[i];
+}
 
 // The pass's copy of the frame (FP64 on the device) and mask shape in T.
 template <typename T>
