@@ -134,6 +134,41 @@ template <typename T, bool INV> struct Dft<T, 3, INV> {
     }
 };
 
+// 12-point DFT as 4 x 3: with n = n1 + 3 n2 and k = 4 k1 + k2,
+// X[4 k1 + k2] = sum_n1 w3^{n1 k1} w12^{n1 k2} (sum_n2 x[n1 + 3 n2] w4^{n2 k2}).
+template <typename T, bool INV> struct Dft<T, 12, INV> {
+    __device__ __forceinline__ static void run(cplx<T>* v)
+    {
+        const T h = T(0.5), c = T(0.86602540378443864676372317075293618347);   // cos, sin of pi/6
+        cplx<T> a[3][4];
+#pragma unroll
+        for (int n1 = 0; n1 < 3; ++n1) {
+            cplx<T> b[4] = {v[n1], v[n1 + 3], v[n1 + 6], v[n1 + 9]};
+            Dft<T, 4, INV>::run(b);
+#pragma unroll
+            for (int k2 = 0; k2 < 4; ++k2) a[n1][k2] = b[k2];
+        }
+        // a[n1][k2] *= w12^{n1 k2}: exponents 1, 2, 3 (n1 = 1) and 2, 4, 6 (n1 = 2)
+        const T sg = INV ? T(1) : T(-1);
+        auto rot = [&](cplx<T> x, T cr, T si) {   // x * (cr + i sg si)
+            return mkc<T>(x.x * cr - sg * x.y * si, x.y * cr + sg * x.x * si);
+        };
+        a[1][1] = rot(a[1][1], c, h);
+        a[1][2] = rot(a[1][2], h, c);
+        a[1][3] = INV ? cmuli(a[1][3]) : cmulmi(a[1][3]);
+        a[2][1] = rot(a[2][1], h, c);
+        a[2][2] = rot(a[2][2], -h, c);
+        a[2][3] = mkc<T>(-a[2][3].x, -a[2][3].y);
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) {
+            cplx<T> b[3] = {a[0][k2], a[1][k2], a[2][k2]};
+            Dft<T, 3, INV>::run(b);
+#pragma unroll
+            for (int k1 = 0; k1 < 3; ++k1) v[4 * k1 + k2] = b[k1];
+        }
+    }
+};
+
 // v[t] *= w^(k t) for t = 1..R-1 from the table (conjugated for the inverse):
 // tw[k * step] holds w^k.
 template <typename T, int R, bool INV>

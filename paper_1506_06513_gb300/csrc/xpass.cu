@@ -463,10 +463,22 @@ k_xpass(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict
 // memory straight into registers and outputs are stored from registers.
 // After the inverse, logical row l R + d of a line holds the point pair
 // (l % R) + R d + R^2 (l / R) (SqMap).
+//
+// S = 0 is the rectangular form nh = 4 R (R = 12: nx = 96; R = 8: nx = 64):
+// L = 4 lanes per line, lane j holding Z[j + 4 t]; the radix-R pass over t
+// and the twiddles w_nh^{j n1} as above, then the R radix-4 transforms over
+// j, R/4 per lane (lane j takes n1 = j + 4 m), through one exchange in the
+// line's slice; the pairs n1 + R n2 are then stored in natural order.  Slices
+// are nh + 4 values apart and the exchange slots XOR-swizzled, so the 16
+// lanes (4 lines) of a half-warp meet 16 distinct banks on every access.
 // ---------------------------------------------------------------------------
 // rows per tile: each group of L lanes inverse-transforms two lines (u and
 // omega fields) and forward-transforms one (the three NL fields)
 template <int L> constexpr int sq_rows() { return 384 / (6 * L); }
+
+template <int R, int S> constexpr int sq_lanes() { return S == 0 ? 4 : S * R; }
+template <int R, int S> constexpr int sq_nh() { return S == 0 ? 4 * R : S * R * R; }
+template <int R, int S> constexpr int sq_slice() { return S == 0 ? 4 * R + 4 : S * R * R; }
 
 template <int R, int S> struct SqMap {
     // point pair held by logical row lrow after the inverse, and its inverse map
@@ -489,8 +501,21 @@ template <int R> __device__ __forceinline__ int sq_slot(int lrow)
     return (lrow & ~(R - 1)) | ((lrow ^ (lrow / R)) & (R - 1));
 }
 
+// the rectangular form keeps the point pairs in natural order
+template <int R> struct SqMap<R, 0> {
+    __device__ __forceinline__ static int point(int lrow) { return lrow; }
+    __device__ __forceinline__ static int lrow(int pp) { return pp; }
+};
+
+// slot of logical row lrow in a line slice
+template <int R, int S> __device__ __forceinline__ int sq_line_slot(int lrow)
+{
+    if constexpr (S == 0) return lrow;
+    else return sq_slot<R>(lrow);
+}
+
 template <typename T, int R, int S, bool LAYER, bool SPONGE>
-__global__ void __launch_bounds__(192, sizeof(T) == 4 ? (S == 1 ? 4 : 3) : 1)
+__global__ void __launch_bounds__(192, sizeof(T) == 4 ? (S == 2 ? 3 : 4) : 1)
 k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExtra ex,
            const StepState* __restrict__ st, const Member* __restrict__ mb)
 {
@@ -502,11 +527,11 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
         ex.part = m.part;
     }
     if (st && st->status != 0) return;
-    constexpr int L = S * R;               // lanes per line
+    constexpr int L = sq_lanes<R, S>();    // lanes per line
     constexpr int RB = sq_rows<L>();
-    constexpr int NH = S * R * R;
+    constexpr int NH = sq_nh<R, S>();
     using Map = SqMap<R, S>;
-    constexpr int CS = NH;                 // line slice; logical row R q + j at R q + (j ^ q)
+    constexpr int CS = sq_slice<R, S>();   // line slice (S > 0: logical row R q + j at R q + (j ^ q))
     const int nx = g.nx, Mx = g.Mx, Mxp = g.Mxp;
     const int nrows = g.nz * g.ny;
     const int ntiles = ceil_div(nrows, RB);
@@ -529,7 +554,7 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
     for (int i = tid; i < NH; i += blockDim.x) {
         const int q = i / L, jj = i % L;
         const double2 w = tw[(2 * jj * q) % nx];
-        tw2[q * L + (jj ^ q)] = mkc<T>(T(w.x), T(w.y));
+        tw2[q * L + (S == 0 ? jj : (jj ^ q))] = mkc<T>(T(w.x), T(w.y));
     }
     for (int i = tid; i < kWarpsX * 36; i += blockDim.x) wacc[i] = 0.0;
     load_frame_t<T>(Fs, ex.frame);
@@ -588,8 +613,29 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
             sq_exchange_pre<T, R, L>(v, j, twx);
             Dft<T, R, true>::run(v);
 #pragma unroll
-            for (int q = 1; q < R; ++q) v[q] = cmul(v[q], cconj(tw2[q * L + (j ^ q)]));
-            if constexpr (S == 1) {
+            for (int q = 1; q < R; ++q) v[q] = cmul(v[q], cconj(tw2[q * L + (S == 0 ? j : (j ^ q))]));
+            if constexpr (S == 0) {
+                // Y[j][n1] at n1 L + (j ^ n1 % L); lane j then takes n1 = j + L m
+#pragma unroll
+                for (int q = 0; q < R; ++q) line[q * L + (j ^ (q % L))] = v[q];
+                __syncwarp();
+#pragma unroll
+                for (int m = 0; m < R / L; ++m) {
+                    const int n1 = j + L * m;
+                    cplx<T> a[L];
+#pragma unroll
+                    for (int i = 0; i < L; ++i) a[i] = line[n1 * L + (i ^ j)];
+                    Dft<T, L, true>::run(a);   // over j -> n2: the pair n1 + R n2
+#pragma unroll
+                    for (int i = 0; i < L; ++i) v[m * L + i] = a[i];
+                }
+                __syncwarp();
+#pragma unroll
+                for (int m = 0; m < R / L; ++m) {
+#pragma unroll
+                    for (int i = 0; i < L; ++i) line[j + L * m + R * i] = v[m * L + i];
+                }
+            } else if constexpr (S == 1) {
 #pragma unroll
                 for (int q = 0; q < R; ++q) line[R * q + (j ^ q)] = v[q];
                 __syncwarp();
@@ -635,7 +681,7 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
                 const int i = tid + it * 192;
                 const int rr = i / NH, lrow = i % NH;
                 if (i < items && row0 + rr < nrows) {
-                    const int slot = sq_slot<R>(lrow);
+                    const int slot = sq_line_slot<R, S>(lrow);
                     cplx<T> uv[3], wv[3];
 #pragma unroll
                     for (int q = 0; q < 3; ++q) {
@@ -711,7 +757,7 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
                         // point xi is half h of pair pp, held at logical row Map::lrow(pp)
                         const int pp = xi >> 1, h = xi & 1;
                         const int lrow = Map::lrow(pp);
-                        const int slot = sq_slot<R>(lrow);
+                        const int slot = sq_line_slot<R, S>(lrow);
                         const T pen = chi * F.inv_eta;
 #pragma unroll
                         for (int q = 0; q < 3; ++q) {
@@ -768,7 +814,31 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
         for (int li = 0; li < (SPONGE ? 2 : 1); ++li) {
             cplx<T>* line = buf + (3 * RB + c + li * NG) * CS;
             const int fld = 3 * li + c / RB, lrr = c % RB;
-            if constexpr (S == 1) {
+            if constexpr (S == 0) {
+                // lane j takes n1 = j + L m: radix L over its pairs n1 + R i,
+                // the twiddles w_nh^{n1 jj}, U[n1][jj] at n1 L + (jj ^ j)
+#pragma unroll
+                for (int m = 0; m < R / L; ++m) {
+                    const int n1 = j + L * m;
+                    cplx<T> a[L];
+#pragma unroll
+                    for (int i = 0; i < L; ++i) a[i] = line[n1 + R * i];
+                    Dft<T, L, false>::run(a);
+#pragma unroll
+                    for (int i = 1; i < L; ++i) a[i] = cmul(a[i], tw2[n1 * L + i]);
+#pragma unroll
+                    for (int i = 0; i < L; ++i) v[m * L + i] = a[i];
+                }
+                __syncwarp();
+#pragma unroll
+                for (int m = 0; m < R / L; ++m) {
+#pragma unroll
+                    for (int i = 0; i < L; ++i) line[(j + L * m) * L + (i ^ j)] = v[m * L + i];
+                }
+                __syncwarp();
+#pragma unroll
+                for (int q = 0; q < R; ++q) v[q] = line[q * L + (j ^ (q % L))];
+            } else if constexpr (S == 1) {
 #pragma unroll
                 for (int i = 0; i < R; ++i) v[i] = line[R * j + (i ^ j)];
                 Dft<T, R, false>::run(v);
@@ -822,8 +892,8 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
                         m1 = b;    // Z[nh - k1] = partner's Z[R-1-q1]
                         m2 = a;
                     } else {
-                        m1 = v[(R - q1) & (R - 1)];
-                        m2 = v[(R - q2) & (R - 1)];
+                        m1 = v[(R - q1) % R];
+                        m2 = v[(R - q2) % R];
                     }
                     if (k1 < Mxp) out[k1] = k1 < Mx ? r2c_post<T>(v[q1], m1, twx[k1]) : mkc<T>(0, 0);
                     if (k2 < Mxp) out[k2] = k2 < Mx ? r2c_post<T>(v[q2], m2, twx[k2]) : mkc<T>(0, 0);
@@ -864,9 +934,9 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
 
 template <typename T, int R, int S> size_t sq_smem(const Geom& g, bool sponge = false)
 {
-    const int RB = sq_rows<S * R>(), NH = S * R * R;
+    const int RB = sq_rows<sq_lanes<R, S>()>(), NH = sq_nh<R, S>(), CS = sq_slice<R, S>();
     size_t s = sizeof(double) * kWarpsX * 36 + ((sizeof(FrameT<T>) + 15) / 16) * 16;
-    s += sizeof(cplx<T>) * ((size_t)2 * NH + (size_t)(sponge ? 9 : 6) * RB * NH);
+    s += sizeof(cplx<T>) * ((size_t)2 * NH + (size_t)(sponge ? 9 : 6) * RB * CS);
     return s;
 }
 
@@ -887,8 +957,9 @@ void launch_sq(bool layer, bool sponge, cplx<T>* w, const Geom& g, const double2
         k_xpass_sq<T, R, S, false, false><<<gd, 192, smem, s>>>(w, g, tw, ex, st, B.mb);
 }
 
-// the register-resident kernel for this grid: 10 R + S (R = 16 or 8, S = 1
-// or 2), or 0 for the generic one
+// the register-resident kernel for this grid: 10 R + S (R = 16 or 8 with
+// S = 1 or 2; R = 12 or 8 with S = 0, the rectangular form), or 0 for the
+// generic one
 template <typename T> int sq_kind(const Geom& g)
 {
     if (g.xgeneric) return 0;
@@ -897,6 +968,8 @@ template <typename T> int sq_kind(const Geom& g)
     case 128: return 81;
     case 1024: return 162;
     case 256: return 82;
+    case 96: return 120;
+    case 64: return 80;
     default: return 0;
     }
 }
@@ -927,7 +1000,7 @@ template <typename T> int x_grid(const Geom& g)
     int per_sm = 0, ntiles = 0;
     const int kind = sq_kind<T>(g);
 #define FLUSI_SQ_OCC(R, S)                                                                          \
-    ntiles = ceil_div(g.nz * g.ny, sq_rows<S * R>());                                               \
+    ntiles = ceil_div(g.nz * g.ny, sq_rows<sq_lanes<R, S>()>());                                               \
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_xpass_sq<T, R, S, false, false>, 192, \
                                                   sq_smem<T, R, S>(g));
     if (kind == 161) {
@@ -938,6 +1011,10 @@ template <typename T> int x_grid(const Geom& g)
         FLUSI_SQ_OCC(16, 2)
     } else if (kind == 82) {
         FLUSI_SQ_OCC(8, 2)
+    } else if (kind == 120) {
+        FLUSI_SQ_OCC(12, 0)
+    } else if (kind == 80) {
+        FLUSI_SQ_OCC(8, 0)
     } else {
         const int lg = x_lgrb<T>(g);
         ntiles = ceil_div(g.nz * g.ny, 1 << lg);
@@ -971,6 +1048,8 @@ cudaError_t launch_x(int mode, void* W, const Geom& g, const FftPlan& plan, cons
         case 81: launch_sq<T, 8, 1>(layer, sponge, w, g, tw, ex, st, s, x_grid<T>(g)); break;
         case 162: launch_sq<T, 16, 2>(layer, sponge, w, g, tw, ex, st, s, x_grid<T>(g)); break;
         case 82: launch_sq<T, 8, 2>(layer, sponge, w, g, tw, ex, st, s, x_grid<T>(g)); break;
+        case 120: launch_sq<T, 12, 0>(layer, sponge, w, g, tw, ex, st, s, x_grid<T>(g)); break;
+        case 80: launch_sq<T, 8, 0>(layer, sponge, w, g, tw, ex, st, s, x_grid<T>(g)); break;
         default:
             k_xpass<T, XP_PHYS><<<dim3(x_grid<T>(g), 1, current_batch().n), kThreadsX, smem, s>>>(
                 w, g, plan, tw, pos, ex, lg, st, current_batch().mb);
@@ -1044,6 +1123,10 @@ cudaError_t configure_xpass()
     FLUSI_SMEM_SQ(float, 8, 1)
     FLUSI_SMEM_SQ(float, 16, 2)
     FLUSI_SMEM_SQ(float, 8, 2)
+    FLUSI_SMEM_SQ(float, 12, 0)
+    FLUSI_SMEM_SQ(float, 8, 0)
+    FLUSI_SMEM_SQ(double, 12, 0)
+    FLUSI_SMEM_SQ(double, 8, 0)
     FLUSI_SMEM_SQ(double, 16, 1)
     FLUSI_SMEM_SQ(double, 8, 1)
     FLUSI_SMEM_SQ(double, 16, 2)

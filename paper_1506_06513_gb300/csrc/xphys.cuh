@@ -251,7 +251,7 @@ __device__ __forceinline__ void sq_exchange_pre(cplx<T>* x, int j, const cplx<T>
 #pragma unroll
     for (int s = R / 2 - 1; s >= 0; --s) {
         const cplx<T> xs = x[s], xt = x[R - 1 - s];
-        const cplx<T> up = s == 0 ? mkc<T>(0, 0) : x[(R - s) & (R - 1)];
+        const cplx<T> up = s == 0 ? mkc<T>(0, 0) : x[s == 0 ? 0 : R - s];
         const cplx<T> sa = self ? carry : xs;   // mirror of element R-1-s
         const cplx<T> sb = self ? up : xt;      // mirror of element s
         cplx<T> a, b;

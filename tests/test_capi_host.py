@@ -248,8 +248,13 @@ def test_tuning_is_validated(fl):
     h = fl.flusi_create((64, 64, 64), (1.0, 1.0, 1.0), 0.1, 1e-2, fl.FLUSI_FP64)
     fl.flusi_set_tuning(h, y_cols=2, z_cols=2)   # 32 bytes of FP64 complex values
     t = fl.flusi_get_tuning(h)
-    assert t["y_tile_cols"] == 2 and t["z_tile_cols"] == 2 and t["x_line_kernel"] == 0
+    # nx = 64 and 96 take the rectangular register-resident x pass; 48 the generic one
+    assert t["y_tile_cols"] == 2 and t["z_tile_cols"] == 2 and t["x_line_kernel"] == 1
     fl.flusi_destroy(h)
+    for nx, kind in ((96, 1), (48, 0), (72, 0)):
+        h = fl.flusi_create((nx, 16, 16), (1.0, 1.0, 1.0), 0.1, 1e-2, fl.FLUSI_FP32)
+        assert fl.flusi_get_tuning(h)["x_line_kernel"] == kind, nx
+        fl.flusi_destroy(h)
 
 
 def test_autotune_needs_a_bound_handle(fl):

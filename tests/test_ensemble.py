@@ -112,14 +112,16 @@ def test_ensemble_equals_one_by_one(fl, prec):
         s.close()
 
 
-# two groups of members that share their launches (same grid, box, options;
+# three groups of members that share their launches (same grid, box, options;
 # different kinematics and Reynolds numbers) and one member on its own
 SHARED = [((16, 16, 16), (4.0, 4.0, 4.0), 55.0, 0.9, 120.0),
           ((16, 16, 16), (4.0, 4.0, 4.0), 70.0, 1.1, 300.0),
           ((16, 16, 16), (4.0, 4.0, 4.0), 45.0, 1.0, 80.0),
           ((24, 16, 12), (4.0, 4.0, 4.0), 60.0, 0.8, 200.0),
           ((24, 16, 12), (4.0, 4.0, 4.0), 75.0, 1.2, 50.0),
-          ((128, 16, 12), (8.0, 1.0, 0.75), 50.0, 1.0, 150.0)]
+          ((128, 16, 12), (8.0, 1.0, 0.75), 50.0, 1.0, 150.0),
+          ((64, 16, 12), (4.0, 1.0, 0.75), 60.0, 1.0, 100.0),
+          ((64, 16, 12), (4.0, 1.0, 0.75), 65.0, 0.9, 250.0)]
 
 
 @pytest.mark.gpu
@@ -128,12 +130,15 @@ def test_shared_launches_equal_one_by_one(fl, prec):
     """Members of the same grid step as one launch per kernel (gridDim.z =
     members, each block on its own member's buffers); each member's state and
     force rows equal its solo run's bit for bit after 7 adaptive steps (the
-    register-resident x pass at nx = 128, the shared-memory one at 16 and 24)."""
+    register-resident x pass at nx = 128, its rectangular form at 64, the
+    shared-memory one at 16 and 24)."""
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.fail("GPU tests need a CUDA device")
     members = [_member(*m) for m in SHARED]
     members[5] = (members[5][0], dict(members[5][1], x_cntr=(4.0, 0.5, 0.375)))
+    for i in (6, 7):
+        members[i] = (members[i][0], dict(members[i][1], x_cntr=(2.0, 0.5, 0.375)))
     dt = np.float64 if prec == "fp64" else np.float32
     fields = [workloads.random_smooth_field(cfg["n"], 11 + i, amplitude=0.2).astype(dt)
               for i, (cfg, _) in enumerate(members)]
@@ -149,7 +154,7 @@ def test_shared_launches_equal_one_by_one(fl, prec):
         s.set_state(u0)
     ens = fl.Ensemble(solvers)
     ens.step(3)
-    assert ens.batches() == (2, 5)
+    assert ens.batches() == (3, 7)
     ens.step(4)
     for s, (u, rows) in zip(solvers, solo):
         got, t, step = s.get_state(dt)

@@ -610,9 +610,11 @@ def _check_first_force_row(cfg, ins, row, lo, hi, u_at, parts=(0, 1, 2), tol=2e-
 
 
 WIDE = {"x512": ((512, 16, 12), (8.0, 1.0, 0.75)), "x128": ((128, 24, 16), (4.0, 0.75, 0.5)),
-        "x1024": ((1024, 12, 8), (16.0, 1.0, 0.75)), "x256": ((256, 18, 16), (8.0, 0.75, 0.75))}
-# nx of the register-resident x pass (nh = R^2 or 2 R^2 with R = 16 or 8)
-SQUARE_NX = (128, 256, 512, 1024)
+        "x1024": ((1024, 12, 8), (16.0, 1.0, 0.75)), "x256": ((256, 18, 16), (8.0, 0.75, 0.75)),
+        "x96": ((96, 18, 12), (4.0, 0.75, 0.5)), "x64": ((64, 18, 12), (4.0, 1.125, 0.75))}
+# nx of the register-resident x pass (nh = R^2 or 2 R^2 with R = 16 or 8;
+# nh = 4 R with R = 12 or 8, the rectangular form)
+SQUARE_NX = (64, 96, 128, 256, 512, 1024)
 
 
 @pytest.mark.parametrize("name", sorted(WIDE))
@@ -620,7 +622,9 @@ SQUARE_NX = (128, 256, 512, 1024)
 def test_square_half_length_x_pass(fl, name, prec):
     """Grids with nx = 512 and 128 take the x pass whose half-length transform
     is two register-resident radix-16 (radix-8) passes, nx = 1024 and 256 the
-    one with a radix-2 step between lane pairs after them; full steps with a
+    one with a radix-2 step between lane pairs after them, nx = 96 and 64 the
+    rectangular one (radix 12 or 8 in registers, then radix 4 across four
+    lanes; 216 rows, ragged against 16-row tiles); full steps with a
     sphere, adaptive dt and a mean flow against the oracle."""
     n, L = WIDE[name]
     cfg = {"n": n, "L": L, "nu": 0.01, "eta": 1e-2, "cfl": 0.1, "mean_mode": "fixed",
@@ -645,7 +649,9 @@ WAKE = {"generic_48x36x24": ((48, 36, 24), (4.0, 3.0, 2.0)),
         "square_512x16x12": ((512, 16, 12), (8.0, 1.0, 0.75)),
         "square_128x24x16": ((128, 24, 16), (4.0, 0.75, 0.5)),
         "square_1024x12x8": ((1024, 12, 8), (16.0, 1.0, 0.75)),
-        "square_256x18x16": ((256, 18, 16), (8.0, 0.75, 0.75))}
+        "square_256x18x16": ((256, 18, 16), (8.0, 0.75, 0.75)),
+        "rect_96x18x12": ((96, 18, 12), (4.0, 0.75, 0.5)),
+        "rect_64x18x12": ((64, 18, 12), (4.0, 1.125, 0.75))}
 
 
 @pytest.mark.parametrize("name", sorted(WAKE))
@@ -653,7 +659,7 @@ WAKE = {"generic_48x36x24": ((48, 36, 24), (4.0, 3.0, 2.0)),
 def test_sponge_and_dirichlet_layer(fl, name, prec):
     """Vorticity sponge and Dirichlet inflow layer (Sec. 2.3) with a sphere and
     a mean flow: physical fields at t = 0 and 5 full steps against the oracle,
-    on the generic x pass and on both square ones."""
+    on the generic x pass, the square ones and the rectangular ones."""
     n, L = WAKE[name]
     cfg = {"n": n, "L": L, "nu": 0.01, "eta": 1e-2, "cfl": 0.1, "mean_mode": "fixed",
            "u_inf": (0.3, 0.0, 0.0), "sponge_c": 0.1,
