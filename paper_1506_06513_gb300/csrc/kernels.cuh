@@ -125,6 +125,11 @@ struct XExtra {
     int sponge_fused;        // XP_PHYS: also form chi_sp omega and x-transform it into W[3..5]
     double u_inf[3];
     int* err;                // XP_PHYS on the tensor cores: status word for a wait that gives up
+    // XP_PHYS, register-resident kernels: rows of partial sums ("virtual
+    // CTAs", each taking tiles v, v + nvirt, ... in order); the launch may
+    // run fewer CTAs, each taking virtual CTAs b, b + gridDim.x, ...  0: the
+    // launch's own grid.
+    int nvirt;
 };
 int xpass_fuses_sponge(int fp64, const Geom& g);
 int xpass_grid(int fp64, const Geom& g);   // CTAs of the persistent physical pass

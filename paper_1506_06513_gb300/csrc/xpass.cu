@@ -17,6 +17,7 @@
 //   r x chi u_s per colour, |u|^2, max |u|^2 and a non-finite flag.
 // The grid is persistent (a multiple of the SM count); each CTA writes one
 // row of partial sums, reduced in a fixed order by the scalar kernel.
+#include <algorithm>
 #include <mutex>
 #include <utility>
 
@@ -556,25 +557,30 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
         const double2 w = tw[(2 * jj * q) % nx];
         tw2[q * L + (S == 0 ? jj : (jj ^ q))] = mkc<T>(T(w.x), T(w.y));
     }
-    for (int i = tid; i < kWarpsX * 36; i += blockDim.x) wacc[i] = 0.0;
     load_frame_t<T>(Fs, ex.frame);
-    __syncthreads();
 
-    double e_acc = 0.0;
-    T m_acc = T(0);
-    int bad = 0;
     const T dxT = T(g.dx), dyT = T(g.dy), dzT = T(g.dz);
     const FrameT<T>& F = *Fs;
     constexpr int NG = 192 / L;            // lane groups; group c owns lines c and c + NG
     constexpr bool has_layer = LAYER;   // a Dirichlet layer is set
     const T uinf[3] = {T(ex.u_inf[0]), T(ex.u_inf[1]), T(ex.u_inf[2])};
 
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    // virtual CTA vb: its tiles in order into its own row of partial sums, so
+    // the sums do not depend on how many CTAs the launch runs
+    const int P = ex.nvirt > 0 ? ex.nvirt : (int)gridDim.x;
+#pragma unroll 1
+    for (int vb = blockIdx.x; vb < P; vb += gridDim.x) {
+    for (int i = tid; i < kWarpsX * 36; i += blockDim.x) wacc[i] = 0.0;
+    __syncthreads();
+    double e_acc = 0.0;
+    T m_acc = T(0);
+    int bad = 0;
+    for (int tile = vb; tile < ntiles; tile += P) {
         const int row0 = tile * RB;
         cplx<T> v[R];
         // the six input lines of this block's next tile on their way into L2
         if (tid < 6) {
-            const int next0 = (tile + gridDim.x) * RB;
+            const int next0 = (tile + P) * RB;
             if (next0 < nrows) {
                 const int nr = min(RB, nrows - next0);
                 prefetch_l2_bulk(W + ((size_t)tid * nrows + next0) * Mxp,
@@ -914,7 +920,7 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
         red[warp][2] = anybad ? 1.0 : 0.0;
     }
     __syncthreads();
-    double* outp = ex.part + (size_t)blockIdx.x * kNumSums;
+    double* outp = ex.part + (size_t)vb * kNumSums;
     if (tid < 36) {
         double s2 = 0.0;
         for (int w = 0; w < kWarpsX; ++w) s2 += wacc[w * 36 + tid];
@@ -930,6 +936,8 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
     } else if (tid < kNumSums) {
         outp[tid] = 0.0;
     }
+    __syncthreads();   // wacc and red read before the next virtual CTA clears them
+    }   // virtual CTAs
 }
 
 template <typename T, int R, int S> size_t sq_smem(const Geom& g, bool sponge = false)
@@ -940,13 +948,28 @@ template <typename T, int R, int S> size_t sq_smem(const Geom& g, bool sponge = 
     return s;
 }
 
+// grid = the virtual CTAs (rows of partial sums, x_grid); a batch of n
+// members runs about one resident wave in all, each CTA taking several
+// virtual ones, instead of n full grids of CTAs that each take one or two
+// tiles and pay their table and frame loads for them.
 template <typename T, int R, int S>
-void launch_sq(bool layer, bool sponge, cplx<T>* w, const Geom& g, const double2* tw, const XExtra& ex,
+void launch_sq(bool layer, bool sponge, cplx<T>* w, const Geom& g, const double2* tw, const XExtra& ex0,
                const StepState* st, cudaStream_t s, int grid)
 {
     const size_t smem = sq_smem<T, R, S>(g, sponge);
     const Batch& B = current_batch();
-    const dim3 gd(grid, 1, B.n);
+    XExtra ex = ex0;
+    ex.nvirt = grid;
+    int run = grid;
+    if (B.n > 1) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_xpass_sq<T, R, S, false, false>, 192, smem);
+        const int resident = std::max(1, sms * std::max(1, per_sm));
+        run = std::min(grid, std::max(1, ceil_div(resident, B.n)));
+    }
+    const dim3 gd(run, 1, B.n);
     if (layer && sponge)
         k_xpass_sq<T, R, S, true, true><<<gd, 192, smem, s>>>(w, g, tw, ex, st, B.mb);
     else if (layer)
