@@ -502,6 +502,43 @@ template <int R> __device__ __forceinline__ int sq_slot(int lrow)
     return (lrow & ~(R - 1)) | ((lrow ^ (lrow / R)) & (R - 1));
 }
 
+// FP32 radix-16 lines (nx = 512): column c of row q at c ^ (2 q mod 16), an
+// even mask, so the pairs (2 i, 2 i + 1) of a row stay adjacent and in order
+// and a row moves as eight 16-byte accesses; a quarter-warp (8 lanes, 8
+// rows) meets 8 distinct 16-byte bank groups, a half-warp column access 16
+// distinct 8-byte ones.  Other lines: c ^ q.
+template <typename T, int R, int S> constexpr bool sq_wide() { return S == 1 && R == 16 && sizeof(T) == 4; }
+template <typename T, int R, int S> __device__ __forceinline__ int sq_swz(int q)
+{
+    if constexpr (sq_wide<T, R, S>()) return (2 * q) & (R - 1);
+    else return q;
+}
+template <typename T, int R, int S> __device__ __forceinline__ void sq_ld_row(const cplx<T>* row, int sw, cplx<T>* v)
+{
+    if constexpr (sq_wide<T, R, S>()) {
+#pragma unroll
+        for (int i = 0; i < R; i += 2) {
+            const float4 p = *reinterpret_cast<const float4*>(row + (i ^ sw));
+            v[i] = mkc<T>(p.x, p.y);
+            v[i + 1] = mkc<T>(p.z, p.w);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < R; ++i) v[i] = row[i ^ sw];
+    }
+}
+template <typename T, int R, int S> __device__ __forceinline__ void sq_st_row(cplx<T>* row, int sw, const cplx<T>* v)
+{
+    if constexpr (sq_wide<T, R, S>()) {
+#pragma unroll
+        for (int i = 0; i < R; i += 2)
+            *reinterpret_cast<float4*>(row + (i ^ sw)) = make_float4(v[i].x, v[i].y, v[i + 1].x, v[i + 1].y);
+    } else {
+#pragma unroll
+        for (int i = 0; i < R; ++i) row[i ^ sw] = v[i];
+    }
+}
+
 // the rectangular form keeps the point pairs in natural order
 template <int R> struct SqMap<R, 0> {
     __device__ __forceinline__ static int point(int lrow) { return lrow; }
@@ -509,9 +546,10 @@ template <int R> struct SqMap<R, 0> {
 };
 
 // slot of logical row lrow in a line slice
-template <int R, int S> __device__ __forceinline__ int sq_line_slot(int lrow)
+template <typename T, int R, int S> __device__ __forceinline__ int sq_line_slot(int lrow)
 {
     if constexpr (S == 0) return lrow;
+    else if constexpr (sq_wide<T, R, S>()) return (lrow & ~(R - 1)) | ((lrow ^ sq_swz<T, R, S>(lrow / R)) & (R - 1));
     else return sq_slot<R>(lrow);
 }
 
@@ -643,13 +681,11 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
                 }
             } else if constexpr (S == 1) {
 #pragma unroll
-                for (int q = 0; q < R; ++q) line[R * q + (j ^ q)] = v[q];
+                for (int q = 0; q < R; ++q) line[R * q + (j ^ sq_swz<T, R, S>(q))] = v[q];
                 __syncwarp();
-#pragma unroll
-                for (int i = 0; i < R; ++i) v[i] = line[R * j + (i ^ j)];
+                sq_ld_row<T, R, S>(line + R * j, sq_swz<T, R, S>(j), v);
                 Dft<T, R, true>::run(v);
-#pragma unroll
-                for (int d = 0; d < R; ++d) line[R * j + (d ^ j)] = v[d];
+                sq_st_row<T, R, S>(line + R * j, sq_swz<T, R, S>(j), v);
             } else {
                 // Y[j][k1] at L k1 + (j ^ k1); lane j turns into (k1, p) = (j % R, j / R)
 #pragma unroll
@@ -687,7 +723,7 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
                 const int i = tid + it * 192;
                 const int rr = i / NH, lrow = i % NH;
                 if (i < items && row0 + rr < nrows) {
-                    const int slot = sq_line_slot<R, S>(lrow);
+                    const int slot = sq_line_slot<T, R, S>(lrow);
                     cplx<T> uv[3], wv[3];
 #pragma unroll
                     for (int q = 0; q < 3; ++q) {
@@ -763,7 +799,7 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
                         // point xi is half h of pair pp, held at logical row Map::lrow(pp)
                         const int pp = xi >> 1, h = xi & 1;
                         const int lrow = Map::lrow(pp);
-                        const int slot = sq_line_slot<R, S>(lrow);
+                        const int slot = sq_line_slot<T, R, S>(lrow);
                         const T pen = chi * F.inv_eta;
 #pragma unroll
                         for (int q = 0; q < 3; ++q) {
@@ -845,14 +881,12 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
 #pragma unroll
                 for (int q = 0; q < R; ++q) v[q] = line[q * L + (j ^ (q % L))];
             } else if constexpr (S == 1) {
-#pragma unroll
-                for (int i = 0; i < R; ++i) v[i] = line[R * j + (i ^ j)];
+                sq_ld_row<T, R, S>(line + R * j, sq_swz<T, R, S>(j), v);
                 Dft<T, R, false>::run(v);
-#pragma unroll
-                for (int d = 0; d < R; ++d) line[R * j + (d ^ j)] = v[d];
+                sq_st_row<T, R, S>(line + R * j, sq_swz<T, R, S>(j), v);
                 __syncwarp();
 #pragma unroll
-                for (int t = 0; t < R; ++t) v[t] = line[R * t + (j ^ t)];
+                for (int t = 0; t < R; ++t) v[t] = line[R * t + (j ^ sq_swz<T, R, S>(t))];
 #pragma unroll
                 for (int t = 1; t < R; ++t) v[t] = cmul(v[t], tw2[t * R + (j ^ t)]);
             } else {
