@@ -235,7 +235,7 @@ void layout(flusi_t h)
     h->oins = o; o = align256(o + sizeof(flusi_insect));
     h->ostate = o; o = align256(o + sizeof(StepState));
     h->ocoef = o; o = align256(o + sizeof(StepCoef));
-    h->oetab = o; o = align256(o + sizeof(double) * 2 * (g.Mx + g.My + g.Mz));
+    h->oetab = o; o = align256(o + (sizeof(double) + sizeof(float)) * 2 * (g.Mx + g.My + g.Mz));
     h->opart = o; o = align256(o + sizeof(double) * kNumSums * h->part_cap);
     h->orows = o; o = align256(o + sizeof(double) * kRowCols * h->opt.force_ring);
     h->total = o;

@@ -84,7 +84,7 @@ cudaError_t launch_zinv(int fp64, const void* U, void* W, const Geom& g, const F
 // Extra arguments of the spectral update (launch_zupdate).
 struct ZfwdExtra {
     const StepCoef* coef;     // mode 0
-    const double* etab;       // mode 0: [E1x Mx][E1y My][E1z Mz][E2x][E2y][E2z]
+    const double* etab;       // mode 0: [E1x Mx][E1y My][E1z Mz][E2x][E2y][E2z] in FP64, then in FP32
     double u_inf[3];
     int mean_free;
     double sponge_c;          // modes 0, 2..5: > 0 adds the vorticity sponge of W[3..5]

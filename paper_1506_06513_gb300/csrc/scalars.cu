@@ -486,15 +486,20 @@ __global__ void k_scalars(Geom g, const double* part, int nparts, StepState* st,
 
     // integrating factors, separable per axis: E1 = e^{-nu |k|^2 dt},
     // E2 = e^{-nu |k|^2 (dt + dt_prev)}; layout [E1x Mx][E1y My][E1z Mz][E2x][E2y][E2z]
+    // in FP64, then the same 2 Mt values rounded to FP32 (the FP32 update reads
+    // those and converts nothing per mode)
     const double two_pi = 6.283185307179586476925286766559;
     const int Mt = g.Mx + g.My + g.Mz;
+    float* etab32 = reinterpret_cast<float*>(etab + 2 * Mt);
     for (int i = tid; i < 2 * Mt; i += T) {
         int which = i / Mt, r = i % Mt;
         double k, tau = which == 0 ? dt : dt + dt_prev;
         if (r < g.Mx) k = two_pi * r / g.Lx;
         else if (r < g.Mx + g.My) k = two_pi * mode_of(r - g.Mx, g.Ky) / g.Ly;
         else k = two_pi * mode_of(r - g.Mx - g.My, g.Kz) / g.Lz;
-        etab[i] = exp(-g.nu * k * k * tau);
+        const double e = exp(-g.nu * k * k * tau);
+        etab[i] = e;
+        etab32[i] = float(e);
     }
 
     // force row: lane 3 p + i of warp 0 takes component i of part p; then the

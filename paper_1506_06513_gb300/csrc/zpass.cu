@@ -514,12 +514,15 @@ k_zupdate(const cplx<T>* __restrict__ Wn, cplx<T>* __restrict__ U, cplx<T>* __re
         first = ex.coef->first;
     }
     const T cn = T(c_now), co = T(c_old);
-    const double* E1x = ex.etab;
-    const double* E1y = E1x + g.Mx;
-    const double* E1z = E1y + g.My;
-    const double* E2x = E1z + g.Mz;
-    const double* E2y = E2x + g.Mx;
-    const double* E2z = E2y + g.My;
+    // the factor tables in T: FP64, then their FP32 copy (written together)
+    const int Mt = g.Mx + g.My + g.Mz;
+    const T* E1x = sizeof(T) == 8 ? reinterpret_cast<const T*>(ex.etab)
+                                  : reinterpret_cast<const T*>(ex.etab + 2 * Mt);
+    const T* E1y = E1x + g.Mx;
+    const T* E1z = E1y + g.My;
+    const T* E2x = E1z + g.Mz;
+    const T* E2y = E2x + g.Mx;
+    const T* E2z = E2y + g.My;
     for (size_t gi = (size_t)blockIdx.x * blockDim.x + threadIdx.x; gi < groups;
          gi += (size_t)gridDim.x * blockDim.x) {
         const size_t o = gi * VEC;
@@ -585,8 +588,8 @@ k_zupdate(const cplx<T>* __restrict__ Wn, cplx<T>* __restrict__ U, cplx<T>* __re
             const size_t ov = o + v;
             if (MODE == 0) {
                 // products of the per-axis factors in the state precision
-                const T e1 = T(E1x[x]) * T(E1y[jy]) * T(E1z[jz]);
-                const T e2 = first ? T(0) : T(E2x[x]) * T(E2y[jy]) * T(E2z[jz]);
+                const T e1 = E1x[x] * E1y[jy] * E1z[jz];
+                const T e2 = first ? T(0) : E2x[x] * E2y[jy] * E2z[jz];
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     cplx<T> r;
