@@ -481,15 +481,21 @@ __device__ __forceinline__ void load_inverse_pos(int* sinv, const int* pos_src, 
     for (int f = threadIdx.x; f < n; f += blockDim.x) sinv[pos_src[f]] = f;
 }
 
-// Copy the twiddle table (FP64, global; ntw entries exp(-2 pi i j / ntw))
-// and the n-entry digit-reversal table into shared memory.
+// Copy the twiddle table (global; ntw entries exp(-2 pi i j / ntw) in FP64,
+// followed by the same ntw entries in FP32, read by the FP32 kernels) and the
+// n-entry digit-reversal table into shared memory.
 template <typename T>
 __device__ __forceinline__ void load_tables(cplx<T>* dst, int* pos_dst, const double2* src,
                                             const int* pos_src, int ntw, int n)
 {
-    for (int i = threadIdx.x; i < ntw; i += blockDim.x) {
-        double2 w = src[i];
-        dst[i] = mkc<T>(T(w.x), T(w.y));
+    if constexpr (sizeof(T) == 4) {
+        const float2* f = reinterpret_cast<const float2*>(src + ntw);
+        for (int i = threadIdx.x; i < ntw; i += blockDim.x) dst[i] = mkc<T>(f[i].x, f[i].y);
+    } else {
+        for (int i = threadIdx.x; i < ntw; i += blockDim.x) {
+            double2 w = src[i];
+            dst[i] = mkc<T>(T(w.x), T(w.y));
+        }
     }
     for (int i = threadIdx.x; i < n; i += blockDim.x) pos_dst[i] = pos_src[i];
 }

@@ -186,6 +186,14 @@ std::vector<double2> twiddles(int n)
     return t;
 }
 
+// the table rounded to FP32 (stored after the FP64 one: the FP32 kernels read it)
+std::vector<float2> twiddles32(const std::vector<double2>& t)
+{
+    std::vector<float2> f(t.size());
+    for (size_t j = 0; j < t.size(); ++j) f[j] = make_float2((float)t[j].x, (float)t[j].y);
+    return f;
+}
+
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 int cutoff(int n, int strict) { return (strict && n % 3 == 0) ? n / 3 - 1 : n / 3; }
@@ -223,9 +231,10 @@ void layout(flusi_t h)
     h->oH = o; o = align256(o + spec);
     h->oUt = o; o = align256(o + (h->opt.time_scheme == 1 ? spec : 0));   // RK4 stage state
     h->oW = o; o = align256(o + work);
-    h->otx = o; o = align256(o + sizeof(double2) * g.nx);
-    h->oty = o; o = align256(o + sizeof(double2) * g.ny);
-    h->otz = o; o = align256(o + sizeof(double2) * g.nz);
+    // twiddle tables: n values in FP64, then the same rounded to FP32
+    h->otx = o; o = align256(o + (sizeof(double2) + sizeof(float2)) * g.nx);
+    h->oty = o; o = align256(o + (sizeof(double2) + sizeof(float2)) * g.ny);
+    h->otz = o; o = align256(o + (sizeof(double2) + sizeof(float2)) * g.nz);
     h->opx = o; o = align256(o + sizeof(int) * (g.nx / 2));
     h->opy = o; o = align256(o + sizeof(int) * g.ny);
     h->opz = o; o = align256(o + sizeof(int) * g.nz);
@@ -629,11 +638,22 @@ int flusi_bind(flusi_t h, void* ws, size_t bytes, void* stream)
     if (h->xgrid > h->part_cap) h->xgrid = h->part_cap;
     CK(cudaMemsetAsync(h->ws, 0, h->total, h->stream), "clear workspace");
     auto tx = twiddles(h->nx), ty = twiddles(h->ny), tz = twiddles(h->nz);
+    auto fx = twiddles32(tx), fy = twiddles32(ty), fz = twiddles32(tz);
     auto px = digit_reversal(h->px), py = digit_reversal(h->py), pz = digit_reversal(h->pz);
     auto pzi = digit_reversal(h->pzi);
-    CK(cudaMemcpyAsync(h->ws + h->otx, tx.data(), sizeof(double2) * tx.size(), cudaMemcpyHostToDevice, h->stream), "twiddles");
-    CK(cudaMemcpyAsync(h->ws + h->oty, ty.data(), sizeof(double2) * ty.size(), cudaMemcpyHostToDevice, h->stream), "twiddles");
-    CK(cudaMemcpyAsync(h->ws + h->otz, tz.data(), sizeof(double2) * tz.size(), cudaMemcpyHostToDevice, h->stream), "twiddles");
+    struct Tab {
+        size_t off;
+        const std::vector<double2>* d;
+        const std::vector<float2>* f;
+    };
+    for (const Tab& t : {Tab{h->otx, &tx, &fx}, Tab{h->oty, &ty, &fy}, Tab{h->otz, &tz, &fz}}) {
+        const size_t n = t.d->size();
+        CK(cudaMemcpyAsync(h->ws + t.off, t.d->data(), sizeof(double2) * n, cudaMemcpyHostToDevice, h->stream),
+           "twiddles");
+        CK(cudaMemcpyAsync(h->ws + t.off + sizeof(double2) * n, t.f->data(), sizeof(float2) * n,
+                           cudaMemcpyHostToDevice, h->stream),
+           "twiddles");
+    }
     CK(cudaMemcpyAsync(h->ws + h->opx, px.data(), sizeof(int) * px.size(), cudaMemcpyHostToDevice, h->stream), "digit reversal");
     CK(cudaMemcpyAsync(h->ws + h->opy, py.data(), sizeof(int) * py.size(), cudaMemcpyHostToDevice, h->stream), "digit reversal");
     CK(cudaMemcpyAsync(h->ws + h->opz, pz.data(), sizeof(int) * pz.size(), cudaMemcpyHostToDevice, h->stream), "digit reversal");

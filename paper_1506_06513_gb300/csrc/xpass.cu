@@ -589,11 +589,19 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
     const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
     const int c = tid / L, j = tid % L;    // this lane's line and index within it
     // w_nx^k for k < nh: the c2r/r2c mirror steps use no higher power
-    for (int i = tid; i < NH; i += blockDim.x) twx[i] = mkc<T>(T(tw[i].x), T(tw[i].y));
+    // (the FP32 copy of the table follows the FP64 one)
+    auto twv = [&](int k) -> cplx<T> {
+        if constexpr (sizeof(T) == 4) {
+            const float2 w = reinterpret_cast<const float2*>(tw + nx)[k];
+            return mkc<T>(w.x, w.y);
+        } else {
+            return mkc<T>(tw[k].x, tw[k].y);
+        }
+    };
+    for (int i = tid; i < NH; i += blockDim.x) twx[i] = twv(i);
     for (int i = tid; i < NH; i += blockDim.x) {
         const int q = i / L, jj = i % L;
-        const double2 w = tw[(2 * jj * q) % nx];
-        tw2[q * L + (S == 0 ? jj : (jj ^ q))] = mkc<T>(T(w.x), T(w.y));
+        tw2[q * L + (S == 0 ? jj : (jj ^ q))] = twv((2 * jj * q) % nx);
     }
     load_frame_t<T>(Fs, ex.frame);
 
