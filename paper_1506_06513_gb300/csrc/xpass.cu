@@ -394,10 +394,7 @@ k_xpass(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict
                             }
                         }
                         // a lane's points in T, everything above it in FP64
-                        for (int k = 0; k < 12; ++k) {
-                            const double sv = warp_sum(double(v[k]));
-                            if (lane == 0) wacc[warp * 36 + cc * 12 + k] += sv;
-                        }
+                        warp_sums12<T>(v, wacc + warp * 36 + cc * 12, lane);
                     }
                 }
             }
@@ -846,11 +843,7 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
                         }
                         // one point per lane in T; the sums across lanes, warps
                         // and blocks in FP64
-#pragma unroll
-                        for (int k2 = 0; k2 < 12; ++k2) {
-                            const double sv = warp_sum(double(acc[k2]));
-                            if (lane == 0) wacc[warp * 36 + cc * 12 + k2] += sv;
-                        }
+                        warp_sums12<T>(acc, wacc + warp * 36 + cc * 12, lane);
                     }
                 }
             }

@@ -218,6 +218,33 @@ __device__ __forceinline__ double warp_sum(double v)
 
 // c2r pre-processing: Z[k] = (X[k] + X*[m]) + i (X[k] - X*[m]) w^{-k} with the
 // mirror value Xm = X[nh - k].
+// The warp totals of 12 per-lane values in FP64, added into w[0..11]: a
+// reduce-scatter over 16 slots (12 values, 4 zeros), halving the slots per
+// lane at each of the xor-16, 8, 4, 2 exchanges, then one xor-1 add; lane
+// 2i + 1 (bits 4..1 = i) ends with the total of slot i.  16 FP64 adds a warp
+// instead of the 60 of twelve separate butterflies (FP64 is slow here).
+// Every lane of the warp calls it.
+template <typename T>
+__device__ __forceinline__ void warp_sums12(const T* v, double* w, int lane)
+{
+    double d[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) d[k] = k < 12 ? double(v[k]) : 0.0;
+#pragma unroll
+    for (int h = 8; h >= 1; h >>= 1) {
+        const bool up = (lane & (2 * h)) != 0;   // this lane keeps the upper half
+#pragma unroll
+        for (int k = 0; k < h; ++k) {
+            const double send = up ? d[k] : d[k + h];
+            const double keep = up ? d[k + h] : d[k];
+            d[k] = keep + __shfl_xor_sync(0xffffffffu, send, 2 * h);
+        }
+    }
+    d[0] += __shfl_xor_sync(0xffffffffu, d[0], 1);
+    const int slot = (lane >> 1) & 15;
+    if ((lane & 1) && slot < 12) w[slot] += d[0];
+}
+
 template <typename T>
 __device__ __forceinline__ cplx<T> c2r_pre(cplx<T> Xk, cplx<T> Xm, cplx<T> wk)
 {
