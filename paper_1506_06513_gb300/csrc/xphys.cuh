@@ -216,6 +216,10 @@ __device__ __forceinline__ double warp_sum(double v)
 }
 
 
+// a b + c, rounded once
+__device__ __forceinline__ float fmadd(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmadd(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 // c2r pre-processing: Z[k] = (X[k] + X*[m]) + i (X[k] - X*[m]) w^{-k} with the
 // mirror value Xm = X[nh - k].
 // The warp totals of 12 per-lane values in FP64, added into w[0..11]: a
@@ -248,18 +252,21 @@ __device__ __forceinline__ void warp_sums12(const T* v, double* w, int lane)
 template <typename T>
 __device__ __forceinline__ cplx<T> c2r_pre(cplx<T> Xk, cplx<T> Xm, cplx<T> wk)
 {
-    const cplx<T> s = cadd(Xk, cconj(Xm)), d = csub(Xk, cconj(Xm));
-    return cadd(s, cmuli(cmul(d, cconj(wk))));
+    // s + i d conj(w) with s = Xk + conj(Xm), d = Xk - conj(Xm), as fused
+    // multiply-adds: (s.x - d.y w.x + d.x w.y, s.y + d.x w.x + d.y w.y)
+    const T sx = Xk.x + Xm.x, sy = Xk.y - Xm.y, dx = Xk.x - Xm.x, dy = Xk.y + Xm.y;
+    return mkc<T>(fmadd(dx, wk.y, fmadd(-dy, wk.x, sx)), fmadd(dy, wk.y, fmadd(dx, wk.x, sy)));
 }
 
 // r2c post-processing: X[k] = E + w^k O, E = (Z[k] + Z*[m])/2, O = -i (Z[k] - Z*[m])/2.
 template <typename T>
 __device__ __forceinline__ cplx<T> r2c_post(cplx<T> Zk, cplx<T> Zm, cplx<T> wk)
 {
-    const cplx<T> zc = cconj(Zm);
-    const cplx<T> E = cscale(cadd(Zk, zc), T(0.5));
-    const cplx<T> O = cscale(cmulmi(csub(Zk, zc)), T(0.5));
-    return cadd(E, cmul(wk, O));
+    // with a = Zk + conj(Zm), b = Zk - conj(Zm): E + w O = (a + w (-i b)) / 2
+    // = (a.x + w.x b.y + w.y b.x, a.y + w.y b.y - w.x b.x) / 2, as fused
+    // multiply-adds (the halving is exact)
+    const T ax = Zk.x + Zm.x, ay = Zk.y - Zm.y, bx = Zk.x - Zm.x, by = Zk.y + Zm.y;
+    return mkc<T>(T(0.5) * fmadd(wk.y, bx, fmadd(wk.x, by, ax)), T(0.5) * fmadd(-wk.x, bx, fmadd(wk.y, by, ay)));
 }
 
 template <typename T, int R, int L>
