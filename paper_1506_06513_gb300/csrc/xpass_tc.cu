@@ -199,10 +199,14 @@ k_xpass_tc(float2* __restrict__ W, Geom g, const double2* __restrict__ tw, XExtr
     const int nrows = g.nz * g.ny;
     const int ntiles = ceil_div(nrows, RB);
 
-    // twiddles: w_nx^k (mirror steps) and W_NH^i = w_nx^{2i} (between stages)
+    // twiddles: w_nx^k (mirror steps), and W_NH^{ab} = w_nx^{2ab} (a < 16, b < Q,
+    // between the stages) at a Q + (b ^ a % Q): the 16 lanes that read it with
+    // a fixed b (inverse) or a fixed a (forward) meet distinct banks
     for (int i = tid; i < NH; i += kTcThreads) {
         twx[i] = make_float2((float)tw[i].x, (float)tw[i].y);
-        tw2[i] = make_float2((float)tw[2 * i].x, (float)tw[2 * i].y);
+        const int a = i / Q, b = i % Q;
+        const double2 w = tw[2 * a * b];
+        tw2[a * Q + (b ^ (a % Q))] = make_float2((float)w.x, (float)w.y);
     }
     build_dft_b<P>(sm + Lt::oB16, Lt::kB16, 16, false, tw, nx);
     build_dft_b<P>(sm + Lt::oB16 + P * Lt::kB16, Lt::kB16, 16, true, tw, nx);
@@ -339,7 +343,7 @@ k_xpass_tc(float2* __restrict__ W, Geom g, const double2* __restrict__ tw, XExtr
                     float re[Q], im[Q];
 #pragma unroll
                     for (int k1 = 0; k1 < Q; ++k1) {
-                        const float2 w = tw2[n1 * k1];
+                        const float2 w = tw2[n1 * Q + (k1 ^ (n1 % Q))];
                         re[k1] = y[k1] * w.x + y[Q + k1] * w.y;
                         im[k1] = y[Q + k1] * w.x - y[k1] * w.y;
                     }
@@ -505,7 +509,7 @@ k_xpass_tc(float2* __restrict__ W, Geom g, const double2* __restrict__ tw, XExtr
                 float re[16], im[16];
 #pragma unroll
                 for (int kk = 0; kk < 16; ++kk) {
-                    const float2 w = tw2[n1 * kk];
+                    const float2 w = tw2[kk * Q + (n1 ^ (kk % Q))];
                     re[kk] = y[kk] * w.x - y[16 + kk] * w.y;
                     im[kk] = y[kk] * w.y + y[16 + kk] * w.x;
                 }
