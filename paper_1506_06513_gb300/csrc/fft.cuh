@@ -21,6 +21,13 @@
 #include "common.cuh"
 
 namespace flusi {
+// A row index of a transform (n <= 1024) in the blocks' shared-memory tables:
+// 16 bits, so that a 1024-row tile of 64 KB, its twiddles and this table fit
+// three blocks on an SM.
+using rowidx_t = unsigned short;
+}  // namespace flusi
+
+namespace flusi {
 
 // R-point DFT in registers: forward uses exp(-2 pi i/R), inverse exp(+2 pi i/R).
 template <typename T, int R, bool INV> struct Dft;
@@ -367,7 +374,7 @@ __device__ __forceinline__ void fft_stage_first(cplx<T>* buf, int ld, int col, i
 // (half the registers of holding all R).
 template <typename T, int R, bool INV, int V, bool AUX, class Store>
 __device__ __forceinline__ void fft_stage_last(const cplx<T>* buf, int ld, int col, int jt, int P,
-                                               int nbf, int fstep, const int* sinv, Store& store)
+                                               int nbf, int fstep, const rowidx_t* sinv, Store& store)
 {
     constexpr int kUnroll = V == 1 ? 2 : 1;
     constexpr int H = AUX ? (R + 1) / 2 : 1;
@@ -410,7 +417,7 @@ __device__ __forceinline__ void fft_stage_last(const cplx<T>* buf, int ld, int c
 
 template <typename T, bool INV, int V, bool AUX = false, bool R16 = false, class Store>
 __device__ __forceinline__ void fft_last_to(const cplx<T>* buf, int ld, int col, int jt, int P,
-                                            const FftPlan& plan, const int* sinv, Store& store)
+                                            const FftPlan& plan, const rowidx_t* sinv, Store& store)
 {
     const int last = plan.nst - 1;
     const int R = plan.radix[last], nbf = plan.n / R, fstep = plan.n / R;
@@ -432,7 +439,7 @@ __device__ __forceinline__ void fft_last_to(const cplx<T>* buf, int ld, int col,
 // `store` (sinv[row] = frequency held by that row).  All threads must call.
 template <typename T, bool INV, int V, bool AUX = false, bool R16 = false, class Load, class Store>
 __device__ void fft_dif_io(cplx<T>* buf, int C, int ld, const FftPlan& plan, const cplx<T>* tw,
-                           const int* sinv, Load load, Store store)
+                           const rowidx_t* sinv, Load load, Store store)
 {
     const int G = C / V, P = blockDim.x / G, col = (threadIdx.x % G) * V, jt = threadIdx.x / G;
     const int m = plan.m[0], ts = plan.tstep[0];
@@ -468,7 +475,7 @@ __device__ void fft_dif_io(cplx<T>* buf, int C, int ld, const FftPlan& plan, con
 // last stage to `store`.  All threads must call.
 template <typename T, bool INV, int V, bool AUX = false, bool R16 = false, class Store>
 __device__ void fft_dif_out(cplx<T>* buf, int C, int ld, const FftPlan& plan, const cplx<T>* tw,
-                            const int* sinv, Store store)
+                            const rowidx_t* sinv, Store store)
 {
     const int G = C / V, P = blockDim.x / G, col = (threadIdx.x % G) * V, jt = threadIdx.x / G;
     fft_run<T, INV, true, V, R16>(buf, C, ld, plan, tw, 0, plan.nst - 1);
@@ -476,9 +483,9 @@ __device__ void fft_dif_out(cplx<T>* buf, int C, int ld, const FftPlan& plan, co
 }
 
 // Inverse digit-reversal table in shared memory: sinv[pos[f]] = f.
-__device__ __forceinline__ void load_inverse_pos(int* sinv, const int* pos_src, int n)
+__device__ __forceinline__ void load_inverse_pos(rowidx_t* sinv, const int* pos_src, int n)
 {
-    for (int f = threadIdx.x; f < n; f += blockDim.x) sinv[pos_src[f]] = f;
+    for (int f = threadIdx.x; f < n; f += blockDim.x) sinv[pos_src[f]] = (rowidx_t)f;
 }
 
 // Copy the twiddle table (global; ntw entries exp(-2 pi i j / ntw) in FP64,

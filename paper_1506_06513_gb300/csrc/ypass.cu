@@ -46,7 +46,7 @@ k_ypass(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict
     // the tile at a 128-byte boundary of shared memory (TMA destinations)
     cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127));
     cplx<T>* tws = buf + (g.ny << lgC);
-    int* sinv = reinterpret_cast<int*>(tws + g.ny);
+    rowidx_t* sinv = reinterpret_cast<rowidx_t*>(tws + g.ny);
     const int nxb = ceil_div(g.Mxp, TX), nzb = ceil_div(g.nz, 1 << lgNP);
     int b = blockIdx.x;
     const int xb = b % nxb;
@@ -265,7 +265,7 @@ template <typename T> YTile y_tile(const Geom& g, int ncomp)
     t.lgTX = __builtin_ctz(TX);
     t.lgNP = __builtin_ctz(NP);
     t.blocks = ceil_div(g.Mxp, TX) * ceil_div(g.nz, NP) * ncomp;
-    t.smem = sizeof(cplx<T>) * ((size_t)g.ny + (size_t)g.ny * TX * NP) + sizeof(int) * g.ny + 128;
+    t.smem = sizeof(cplx<T>) * ((size_t)g.ny + (size_t)g.ny * TX * NP) + sizeof(rowidx_t) * g.ny + 128;
     return t;
 }
 

@@ -231,7 +231,7 @@ k_zinv(const cplx<T>* __restrict__ U, cplx<T>* __restrict__ W, Geom g, FftPlan p
     // the tile at a 128-byte boundary of shared memory (TMA destinations)
     cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127));
     cplx<T>* tws = buf + (g.nz << lgTX);
-    int* sinv = reinterpret_cast<int*>(tws + g.nz);
+    rowidx_t* sinv = reinterpret_cast<rowidx_t*>(tws + g.nz);
     const int Q = g.My * g.Mxp;
     const int q0 = blockIdx.x * TX;
     const size_t Ustride = (size_t)g.Mz * Q;           // between components of U
@@ -407,7 +407,7 @@ k_zfwd(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict_
     const int TX = 1 << lgTX;
     cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127));
     cplx<T>* tws = buf + (g.nz << lgTX);
-    int* sinv = reinterpret_cast<int*>(tws + g.nz);
+    rowidx_t* sinv = reinterpret_cast<rowidx_t*>(tws + g.nz);
     const int Q = g.My * g.Mxp, nz = g.nz, Kz = g.Kz, Mz = g.Mz;
     const int nqb = ceil_div(Q, TX);
     const int c = blockIdx.x / nqb, q0 = (blockIdx.x - c * nqb) * TX;
@@ -644,7 +644,7 @@ cudaError_t launch_zi(const void* U, void* W, const Geom& g, const FftPlan& plan
     const int TX = zinv_tx<T>(g);
     if (g.nz * TX > cap_zi<T>() || kThreadsInv % TX != 0) return cudaErrorInvalidValue;
     const int blocks = ceil_div(g.My * g.Mxp, TX);
-    const size_t smem = sizeof(cplx<T>) * ((size_t)g.nz + (size_t)g.nz * TX) + sizeof(int) * g.nz + 128;
+    const size_t smem = sizeof(cplx<T>) * ((size_t)g.nz + (size_t)g.nz * TX) + sizeof(rowidx_t) * g.nz + 128;
     const cplx<T>* u = (const cplx<T>*)U;
     cplx<T>* w = (cplx<T>*)W;
     const bool tma = map && bh > 0 && err;
@@ -670,7 +670,7 @@ cudaError_t launch_zf(void* W, int nf, const Geom& g, const FftPlan& plan, const
     const int TX = zinv_tx<T>(g);
     if (g.nz * TX > cap_zi<T>() || kThreadsInv % TX != 0 || nf < 1 || nf > 6) return cudaErrorInvalidValue;
     const int blocks = nf * ceil_div(g.My * g.Mxp, TX);
-    const size_t smem = sizeof(cplx<T>) * ((size_t)g.nz + (size_t)g.nz * TX) + sizeof(int) * g.nz + 128;
+    const size_t smem = sizeof(cplx<T>) * ((size_t)g.nz + (size_t)g.nz * TX) + sizeof(rowidx_t) * g.nz + 128;
     cplx<T>* w = (cplx<T>*)W;
     const bool tma = map && bh > 0 && err;
     CUtensorMap none{};
