@@ -720,10 +720,53 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
         __syncthreads();
 
         // ---- physical space, every point: NL = u x omega into the omega lines,
-        //      energy and max |u|^2; a non-finite value makes a sum non-finite
-        {
+        //      energy and max |u|^2.  A non-finite velocity makes the energy sum
+        //      non-finite; NL can only be non-finite through u (omega, u_s and
+        //      the penalization are finite for a finite state), so the energy
+        //      sum is the check.
+        //      FP32 radix-16 and rectangular lines without the wake terms: two
+        //      point pairs per thread (logical rows 2m, 2m + 1 sit in adjacent
+        //      slots of those layouts), as 16-byte accesses.
+        if constexpr (sizeof(T) == 4 && (sq_wide<T, R, S>() || S == 0) && !SPONGE && !LAYER) {
+            constexpr int NH2 = NH / 2;
+            const int items = RB * NH2;
+            T e_tile = T(0);
+            for (int it = 0; it < (items + 191) / 192; ++it) {
+                const int i = tid + it * 192;
+                const int rr = i / NH2, lrow = 2 * (i % NH2);
+                if (i < items && row0 + rr < nrows) {
+                    const int slot = sq_line_slot<T, R, S>(lrow);   // even; row lrow + 1 at slot + 1
+                    float4 uq[3], wq[3];
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        uq[q] = *reinterpret_cast<const float4*>(buf + (q * RB + rr) * CS + slot);
+                        wq[q] = *reinterpret_cast<const float4*>(buf + ((3 + q) * RB + rr) * CS + slot);
+                    }
+                    T nl[4][3];
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {
+                        T u[3], om[3];
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) {
+                            u[q] = h == 0 ? uq[q].x : h == 1 ? uq[q].y : h == 2 ? uq[q].z : uq[q].w;
+                            om[q] = h == 0 ? wq[q].x : h == 1 ? wq[q].y : h == 2 ? wq[q].z : wq[q].w;
+                        }
+                        cross3(u, om, nl[h]);
+                        const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+                        e_tile += uu;
+                        m_acc = fmax(m_acc, uu);
+                    }
+#pragma unroll
+                    for (int q = 0; q < 3; ++q)
+                        *reinterpret_cast<float4*>(buf + ((3 + q) * RB + rr) * CS + slot) =
+                            make_float4(nl[0][q], nl[1][q], nl[2][q], nl[3][q]);
+                }
+            }
+            e_acc += double(e_tile);
+            if (!isfinite(e_tile)) bad = 1;
+        } else {
             const int items = RB * NH;
-            T e_tile = T(0), chk = T(0);
+            T e_tile = T(0);
             for (int it = 0; it < (items + 191) / 192; ++it) {
                 const int i = tid + it * 192;
                 const int rr = i / NH, lrow = i % NH;
@@ -766,7 +809,6 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
                         const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
                         e_tile += uu;
                         m_acc = fmax(m_acc, uu);
-                        chk += nl[h][0] + nl[h][1] + nl[h][2];
                     }
 #pragma unroll
                     for (int q = 0; q < 3; ++q)
@@ -774,7 +816,7 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
                 }
             }
             e_acc += double(e_tile);
-            if (!isfinite(e_tile) || !isfinite(chk)) bad = 1;
+            if (!isfinite(e_tile)) bad = 1;
         }
 
         // ---- penalization, only in tiles with a row that meets a part's box:
