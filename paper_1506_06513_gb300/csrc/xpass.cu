@@ -983,7 +983,13 @@ k_xpass_sq(cplx<T>* __restrict__ W, Geom g, const double2* __restrict__ tw, XExt
                 }
             }
         }
-        __syncthreads();
+        // No block barrier before the next tile: its inverse lines go to
+        // slices c and c + NG of group c (3 RB = NG in every layout), that is
+        // a u line, whose last readers (the physical-space phases) are behind
+        // the barrier above, and the group's own forward line; rowmask is
+        // read between the first and the last barrier of a tile only.  The
+        // lanes of a group still order their reads before their writes.
+        __syncwarp();
     }
 
     __shared__ double red[kWarpsX][3];
