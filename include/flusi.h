@@ -342,7 +342,8 @@ int flusi_kernels_per_step(flusi_t h, int *count);
  * for y; columns of the flattened (y, x) plane for z), a power of two of at
  * least 32 bytes of complex values (4 in FP32, 2 in FP64) and at most 256.
  * x_kernel: 0 (default) the register-resident line kernel where one exists
- * (nx = 128, 256, 512, 1024), 1 the shared-memory kernel of every length.
+ * (nx = 128, 256, 512, 1024, and its rectangular form at nx = 64, 96), 1 the
+ * shared-memory kernel of every length.
  * y_pair: 1 the y passes' paired kernel, a cluster of two CTAs per tile,
  * each holding the grid rows of one parity and transforming them at half the
  * length, joined by a radix-2 step through distributed shared memory, so
