@@ -478,7 +478,7 @@ k_zfwd(cplx<T>* __restrict__ W, Geom g, FftPlan plan, const double2* __restrict_
 // The mean (k = 0) is held at u_inf unless it is free.  Row padding x >= Mx
 // is never written (it is zero from the workspace reset on).
 template <typename T, int MODE, bool SPONGE>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
 k_zupdate(const cplx<T>* __restrict__ Wn, cplx<T>* __restrict__ U, cplx<T>* __restrict__ H, Geom g,
           ZfwdExtra ex, const StepState* __restrict__ st, const Member* __restrict__ mb)
 {
